@@ -1,0 +1,365 @@
+"""Benchmark of the minimal-Tersoff hot path on one GB300 (or N replicas under torchrun).
+
+Workload (the GA fitness batch): P = 200 parameter sets (genes uniform within +-30 % of Table 2) x
+C = 300 periodic 64-atom diamond-Si cells (strain +-2 %, displacements sigma = 0.1 A), targets = the
+FP64 E/F/W of the Table 2 parameters plus Gaussian noise (1 meV/atom, 5 meV/atom, 0.02 eV/A).
+
+One step = one GA generation's fitness evaluation done from scratch: neighbour build and geometry
+cache of all 300 cells, then E/F/W and the fitness Z of every parameter set (FP32 pair arithmetic,
+FP64 reductions). metric = atom-evals/s (P x total atoms per step / time).
+
+Prints one JSON line (rank 0). See the design notes for the roofline model.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "atom-evals/sec (E+F+W)"
+UNIT = "atom-evals/s"
+L2_BYTES = 129 * 1024 * 1024
+
+# Algorithmic FP32 operations of one atom evaluation, counted from the formula listing of the
+# batched kernel (FMA = 2 FLOP; SFU transcendentals counted apart as XU ops):
+#   per bond: pair functions 5, bond order + energy terms 20, dU/dd + virial 28, force gather 6
+#   per unordered bond pair: zeta terms 7, dU/dd terms 23
+#   per atom: residual and reductions 16
+FLOP_PER_BOND = 59
+FLOP_PER_PAIR = 30
+FLOP_PER_ATOM = 16
+XU_PER_BOND = 6
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0, t1):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.lines:
+            if ts < t0 or ts > t1:
+                continue
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def flop_model(ctx, P):
+    """Algorithmic FP32 FLOP and XU ops of one fitness evaluation over all (p, c)."""
+    N, B, _ = ctx.build_info()
+    cnt = ctx.export_neighbors()[0].astype(np.int64)
+    pairs = int((cnt * (cnt - 1) // 2).sum())
+    flop = P * (FLOP_PER_BOND * B + FLOP_PER_PAIR * pairs + FLOP_PER_ATOM * N)
+    xu = P * XU_PER_BOND * B
+    return flop, xu, B, pairs
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1909_11474_gb300 import binding
+    from paper_1909_11474_gb300 import inputs as I
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = I.workload_ga_batch(P=args.P, C=args.C)
+    cs = w["configs"]
+    P = len(w["params"])
+    ctx = binding.Context(local)
+    pos = torch.tensor(cs.pos, device=dev)
+    box = torch.tensor(cs.box, device=dev)
+    params = torch.tensor(w["params"], device=dev)
+    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+    # targets: FP64 E/F/W of the hidden (Table 2) parameter set from the library's FP64 path
+    Eh, Fh, Wh = ctx.eval(torch.tensor(w["hidden"][None, :], device=dev), precision=64)
+    natoms = torch.tensor(cs.natoms, device=dev, dtype=torch.float64)
+    ne, nw, nf = w["noise"]
+    tg = {"E": (Eh[0] / natoms + torch.tensor(ne, device=dev)).contiguous(),
+          "W": (Wh[0] / natoms[:, None] + torch.tensor(nw, device=dev)).contiguous(),
+          "F": (Fh[0] + torch.tensor(nf, device=dev)).contiguous(),
+          "mask": torch.full((cs.C,), 7, dtype=torch.uint8, device=dev)}
+    flop, xu, nbonds, npairs = flop_model(ctx, P)
+    atom_evals = P * cs.Ntot
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    Zbuf = (torch.empty(P, dtype=torch.float64, device=dev), torch.empty((P, 3), dtype=torch.float64, device=dev),
+            torch.empty((P, 3), dtype=torch.float64, device=dev))
+
+    def step():
+        ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+        ctx.fitness(params, tg, precision=32, out=Zbuf)
+
+    def fitness_only():
+        ctx.fitness(params, tg, precision=32, out=Zbuf)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+
+    sampler = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    sampler.start()
+    time.sleep(0.5)
+    t_clock0 = time.time()
+    # soak: keep the GPU under the same load for a moment so the clock samples see it
+    t_end = time.time() + args.soak
+    while time.time() < t_end:
+        for _ in range(20):
+            fitness_only()
+        torch.cuda.synchronize()
+
+    def timed(fn, k):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        for a, b in ev:
+            flush.fill_(1.0)                       # L2 flush between timed iterations
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / 1e3
+
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_step = timed(step, args.steps)
+    t_fit = timed(fitness_only, args.steps)
+    torch.cuda.synchronize()
+    t_clock1 = time.time()
+    clocks = sampler.stop(t_clock0, t_clock1)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_step, t_fit], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_fit = float(tt[0]), float(tt[1])
+
+    ms_step = 1e3 * t_step / args.steps
+    value = ws * atom_evals * args.steps / t_step
+    fit_value = ws * atom_evals * args.steps / t_fit
+
+    # end to end: host buffers -> device, full step, Z back to host (pinned memory)
+    h_pos = torch.tensor(cs.pos).pin_memory()
+    h_box = torch.tensor(cs.box).pin_memory()
+    h_par = torch.tensor(w["params"]).pin_memory()
+    h_tg = {k: v.cpu().pin_memory() for k, v in tg.items()}
+    h_Z = torch.empty(P, dtype=torch.float64).pin_memory()
+    d_tg = {k: torch.empty_like(v) for k, v in tg.items()}
+
+    def e2e_step():
+        pos.copy_(h_pos, non_blocking=True)
+        box.copy_(h_box, non_blocking=True)
+        params.copy_(h_par, non_blocking=True)
+        for k in d_tg:
+            d_tg[k].copy_(h_tg[k], non_blocking=True)
+        ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+        ctx.fitness(params, d_tg, precision=32, out=Zbuf)
+        h_Z.copy_(Zbuf[0], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    t_e2e = timed(e2e_step, args.steps)
+    h2d = (h_pos.numel() + h_box.numel() + h_par.numel()) * 8 + sum(v.numel() * v.element_size() for v in h_tg.values())
+    d2h = h_Z.numel() * 8
+
+    # dominant kernel: the batched fitness kernel (+ its finalize), timed alone
+    k_time = t_fit / args.steps
+    peaks, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    achieved = flop / k_time / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
+                "frac": round(achieved / fp32_peak, 4), "traffic": None,
+                "kernel": "batch_kernel<16,4,false,2,float> + fitness_finalize",
+                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                               f"(sm_max_mhz from MEASURED_PEAKS.json, {peak_src})",
+                "xu_ops_per_s": round(xu / k_time / 1e12, 4),
+                "xu_frac": round(xu / k_time / (props.multi_processor_count * 16 * sm_max * 1e6), 4)}
+
+    out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "GA fitness batch: P=200 parameter sets x C=300 periodic 64-atom diamond Si "
+                                  "cells (strain +-2%, sigma=0.1 A), neighbour build + geometry + E/F/W + Z per step",
+                      "P": P, "C": cs.C, "atoms": cs.Ntot, "bonds": nbonds, "bond_pairs": npairs,
+                      "precision": "FP32 pair math, FP64 reductions", "l2": "flushed between timed steps",
+                      "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+           "fitness_evals_per_s": round(ws * P * args.steps / t_step, 1),
+           "fitness_only": {"value": round(fit_value, 1), "unit": UNIT, "ms": round(1e3 * k_time, 4),
+                            "fitness_evals_per_s": round(ws * P / k_time, 1),
+                            "note": "per GA generation after the first: geometry cache resident"},
+           "e2e": {"value": round(ws * atom_evals * args.steps / t_e2e, 1), "unit": UNIT,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+           "gpu_launches": args.steps * (5 + 2), "roofline": roofline, "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(w, tg_host={k: v.cpu().numpy() for k, v in tg.items()},
+                                           budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(w, tg_host, budget_s=15.0):
+    """The FP64 oracle (as it stands) on the host cores, on a bounded sample of the same workload:
+    all P parameter sets on the first configurations, until the time budget is spent."""
+    import torch
+
+    import oracle
+    cs = w["configs"]
+    P = len(w["params"])
+    t0 = time.time()
+    atoms = 0
+    pairs_done = 0
+    c = 0
+    while time.time() - t0 < budget_s and c < cs.C:
+        for p in range(P):
+            pos, box = cs.config(c)
+            oracle.evaluate(pos, box, w["params"][p])
+            atoms += len(pos)
+            pairs_done += 1
+            if time.time() - t0 >= budget_s:
+                break
+        c += 1
+    dt = time.time() - t0
+    return {"value": round(atoms / dt, 1), "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{pairs_done} (parameter set, 64-atom cell) evaluations of the same workload, "
+                      f"{dt:.1f} s, FP64 torch CPU with autograd forces/virial"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import torch
+
+    import oracle
+    from paper_1909_11474_gb300 import inputs as I
+    w = I.workload_ga_batch(P=args.P, C=args.C)
+    cs = w["configs"]
+    P = len(w["params"])
+    n_pairs = max(1, int(args.ref_pairs))
+    order = [(p, c) for c in range(cs.C) for p in range(P)]
+    times = []
+    k = 0
+    for s in range(args.warmup + args.steps):
+        t0 = time.time()
+        atoms = 0
+        for _ in range(n_pairs):
+            p, c = order[k % len(order)]
+            k += 1
+            pos, box = cs.config(c)
+            oracle.evaluate(pos, box, w["params"][p])
+            atoms += len(pos)
+        dt = time.time() - t0
+        if s >= args.warmup:
+            times.append((atoms, dt))
+    atoms = sum(a for a, _ in times)
+    dt = sum(t for _, t in times)
+    v = atoms / dt
+    out = {"metric": METRIC, "value": round(v, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": "GA fitness batch: P=200 x C=300 64-atom cells; each step a bounded sample "
+                                  f"of {n_pairs} (parameter set, cell) evaluations", "P": P, "C": cs.C},
+           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                            "sample": f"{n_pairs} (parameter set, 64-atom cell) evaluations per step"},
+           "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--P", type=int, default=200)
+    ap.add_argument("--C", type=int, default=300)
+    ap.add_argument("--soak", type=float, default=2.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-pairs", type=int, default=200)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,171 @@
+/*
+ * tersoff.h -- C ABI of the GB300 (sm_103a) minimal-Tersoff library.
+ *
+ * The library evaluates the minimal Tersoff potential of Fan et al., "A minimal Tersoff potential
+ * for diamond silicon with improved descriptions of elastic and phonon transport properties"
+ * (arXiv:1909.11474): energy, per-atom forces and virial of many periodic configurations under many
+ * parameter sets, the fitness that drives the paper's genetic-algorithm fit (Sec. III.B, Eq. 15-19),
+ * and the gradient of that loss with respect to the six parameters.
+ *
+ * Conventions shared by every call:
+ *  - Parameter vector x = [D0 (eV), alpha (1/A), r0 (A), beta, n, h], in the order of Eq. 16.
+ *    S is fixed to 2 (Sec. II.B), so Eq. 11-14 give f_R = D0 e^{-2 alpha (r - r0)} and
+ *    f_A = 2 D0 e^{-alpha (r - r0)}. R1 and R2 (Eq. 9) are fixed per neighbour build.
+ *  - Units: eV and Angstrom. E is the total energy of a configuration (Eq. 1). W is the virial
+ *    W_{mu nu} = -dU/d eps_{mu nu} summed over the cell (positive under compression), stored as the
+ *    six components xx, yy, zz, xy, yz, zx.
+ *  - "device" pointers are CUDA device memory owned by the caller; "host" pointers are ordinary host
+ *    memory owned by the caller. The context owns only its own workspace (neighbour lists, geometry
+ *    cache, schedules, scratch) and frees it in tersoff_destroy.
+ *  - Every call is asynchronous and stream-ordered on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) unless its comment says it synchronises. A call returns a nonzero status for errors it
+ *    can see on the host (bad arguments, CUDA launch errors) and then records a message retrievable
+ *    with tersoff_last_error. Conditions detected inside kernels (neighbour overflow, a wait that
+ *    timed out) set bits of a device status word that tersoff_get_status reads.
+ *  - No call falls back to the CPU. A context is not thread-safe; use one context per host thread.
+ */
+#ifndef TERSOFF_GB300_H
+#define TERSOFF_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tersoff_ctx tersoff_ctx;
+typedef void *tersoff_stream; /* cudaStream_t */
+
+enum {
+  TERSOFF_OK = 0,
+  TERSOFF_E_ARG = 1,          /* invalid argument (null pointer, size out of range, bad order)   */
+  TERSOFF_E_NBR_OVERFLOW = 2, /* an atom has more neighbours than max_nbr (device status bit 1)   */
+  TERSOFF_E_CUDA = 3,         /* a CUDA runtime call failed                                       */
+  TERSOFF_E_NONFINITE = 4,    /* non-finite input positions or box (device status bit 4)          */
+  TERSOFF_E_TIMEOUT = 5,      /* a bounded device-side wait gave up (device status bit 8)         */
+  TERSOFF_E_STATE = 6,        /* call made before tersoff_build_neighbors succeeded               */
+  TERSOFF_E_UNSUPPORTED = 7   /* an atom has more neighbours than the evaluation kernels handle   */
+};
+
+/* Device status bits, as returned by tersoff_get_status. */
+#define TERSOFF_STATUS_NBR_OVERFLOW 1u
+#define TERSOFF_STATUS_MANY_NBRS 2u
+#define TERSOFF_STATUS_NONFINITE 4u
+#define TERSOFF_STATUS_TIMEOUT 8u
+
+/* Loss selector of tersoff_param_grad. */
+#define TERSOFF_LOSS_SQ 0 /* L = sum_q w_q S_q / D_q  (smooth)                  */
+#define TERSOFF_LOSS_Z 1  /* L = Z = sum_q w_q sqrt(S_q / D_q)  (Eq. 15, 17-19) */
+
+/* Create a context on CUDA device `device`. *out receives the handle. Returns TERSOFF_OK or
+ * TERSOFF_E_ARG / TERSOFF_E_CUDA. */
+int tersoff_create(tersoff_ctx **out, int device);
+
+/* Free the context and all of its device workspace. Waits for the context's work to finish. */
+void tersoff_destroy(tersoff_ctx *ctx);
+
+/* Message of the last host-visible error of this context ("" if none). Owned by the context. */
+const char *tersoff_last_error(const tersoff_ctx *ctx);
+
+/* Synchronise `stream`, return the device status word (TERSOFF_STATUS_* bits) and clear it.
+ * Returns a negative value if the synchronisation itself failed. */
+int tersoff_get_status(tersoff_ctx *ctx, tersoff_stream stream);
+
+/* A batch of periodic configurations. */
+typedef struct {
+  int32_t C;                /* number of configurations, >= 1                                   */
+  const int32_t *atom_off;  /* host [C+1]: atoms of config c are atom_off[c] .. atom_off[c+1]-1;
+                               atom_off[0] = 0, non-decreasing, each config 1..1024 atoms          */
+  const double *pos;        /* device [Ntot][3], Cartesian positions (A), Ntot = atom_off[C]     */
+  const double *box;        /* device [C][3][3], row k = lattice vector k of config c (A)        */
+} tersoff_configs;
+
+/* Neighbour build for a batch (the index sets of the sums over j in Eq. 2 and over k in Eq. 7).
+ *
+ * For every atom i: all entries (j, n) with |x_j - x_i + n0 a + n1 b + n2 c| < R2 and
+ * (j, n) != (i, 0), where a periodic image of j is a distinct entry. Membership is decided in FP64
+ * with a fixed evaluation order and no fused multiply-add:
+ *     t = (n0*a + n1*b) + n2*c,  d = (x_j - x_i) + t,  r^2 = (dx*dx + dy*dy) + dz*dz < R2*R2.
+ * Entries are kept in ascending (j, n0, n1, n2) order. The call also builds the parameter-independent
+ * geometry cache (bond lengths, unit vectors, f_C and f_C' of Eq. 9, bond-angle cosines) in FP64,
+ * stored in FP32 and FP64, and the evaluation schedule. It copies pos/box into the context (the
+ * caller's buffers are not referenced afterwards) and synchronises `stream` before returning.
+ * R1 < R2 (Eq. 9; Sec. II.B uses R1 = 2.8, R2 = 3.2). 1 <= max_nbr <= 32 bounds the entries kept
+ * per atom; an atom with more sets TERSOFF_STATUS_NBR_OVERFLOW and the call returns
+ * TERSOFF_E_NBR_OVERFLOW. Positions or boxes that are not finite return TERSOFF_E_NONFINITE. */
+int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double R1, double R2,
+                            int32_t max_nbr, tersoff_stream stream);
+
+/* Copy the neighbour list of the last build to host memory: cnt [Ntot], nbr [Ntot][max_nbr]
+ * (global atom index j, -1 padding), shift [Ntot][max_nbr][3] (n0, n1, n2; 0 padding). Synchronous.
+ * Any output pointer may be NULL. */
+int tersoff_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift);
+
+/* Number of atoms, bonds (neighbour entries) and the largest neighbour count of the last build. */
+int tersoff_build_info(const tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t *max_m);
+
+/* Energy, forces and virial for every (parameter set p, configuration c) of the last build
+ * (Eq. 1-14; forces F_i = -dU/dx_i and the virial above).
+ *  params    device [P][6] double (order of Eq. 16), P >= 1
+ *  precision 32: per-pair arithmetic in FP32, energy and virial sums in FP64, F in float;
+ *            64: everything in FP64, F in double
+ *  E         device [P][C] double, total energy (eV)             -- may be NULL
+ *  F         device [P][Ntot][3] float or double (see precision) -- may be NULL
+ *  W         device [P][C][6] double, total virial (eV)          -- may be NULL
+ * Atoms with more than 8 neighbours are not supported by the evaluation kernels: the build reports
+ * them and this call returns TERSOFF_E_UNSUPPORTED. */
+int tersoff_eval(tersoff_ctx *ctx, const double *params, int32_t P, int32_t precision, double *E,
+                 void *F, double *W, tersoff_stream stream);
+
+/* Training targets (Eq. 17-19); energies and virials per atom, forces per atom as they are. */
+typedef struct {
+  const double *E;       /* device [C], target energy per atom (eV/atom)                      */
+  const double *W;       /* device [C][6], target virial per atom (eV/atom), xx yy zz xy yz zx  */
+  const double *F;       /* device [Ntot][3], target forces (eV/A)                             */
+  const uint8_t *mask;   /* device [C]: bit 0 = E, bit 1 = W, bit 2 = F present for config c    */
+} tersoff_targets;
+
+/* Fitness of every parameter set (Eq. 15, 17-19):
+ *   S_e = sum_c (E_c/N_c - E*_c)^2, S_v = sum_c sum_6 (W_c/N_c - W*_c)^2, S_f = sum_i |F_i - F*_i|^2
+ *   over configs whose mask has the bit; D_q = the same sums over the targets alone;
+ *   Zq[p][q] = sqrt(S_q / D_q) (0 if D_q = 0); Z[p] = sum_q w_q Zq[p][q]; +inf if any predicted
+ *   value of parameter set p is not finite.
+ *  params device [P][6]; w host [3] = (w_e, w_v, w_f); precision 32 or 64 as in tersoff_eval;
+ *  Z device [P] double; Zq device [P][3] double (may be NULL); S device [P][3] double (may be NULL).
+ * Residual sums are accumulated in FP64 in a fixed order (deterministic). */
+int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
+                    const double *w, int32_t precision, double *Z, double *Zq, double *S,
+                    tersoff_stream stream);
+
+/* Loss and its gradient with respect to x = [D0, alpha, r0, beta, n, h] for every parameter set.
+ *  loss TERSOFF_LOSS_SQ or TERSOFF_LOSS_Z (the latter has a zero gradient term where S_q = 0);
+ *  L device [P] double; dL device [P][6] double. FP32 per-pair arithmetic with FP64 accumulation of
+ *  the residual sums and of the gradient. Forces enter through the directional derivative
+ *  sum_i v_i . dF_i/dx = -d/dx [ sum_i sum_j (v_j - v_i) . dU_i/dd_ij ] with v_i = dL/dF_i. */
+int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
+                       const double *w, int32_t loss, double *L, double *dL, tersoff_stream stream);
+
+/* Plain FP64 path: the same E, F, W as tersoff_eval(precision = 64), computed with one kernel launch
+ * per (p, c), one thread per atom, bond geometry recomputed from positions (no batching, no
+ * geometry cache). It is the comparison baseline for the batched path.
+ *  params device [P][6]; E device [P][C]; F device [P][Ntot][3] double; W device [P][C][6]. */
+int tersoff_eval_plain(tersoff_ctx *ctx, const double *params, int32_t P, double *E, double *F,
+                       double *W, tersoff_stream stream);
+
+/* MD-scale force call for one large periodic cell: neighbour rebuild (cell list) plus E, F, W.
+ *  N atoms (>= 1, <= 2^24), pos device [N][3] double, box host [3][3] (rows = lattice vectors; every
+ *  plane spacing must exceed 3*R2 so that each atom has at most one image of any other within R2),
+ *  params host [6]; precision 32 or 64; E device [1] double; F device [N][3] float or double;
+ *  W device [6] double. The neighbour list is the same set, in the same canonical order, as
+ *  tersoff_build_neighbors would produce. max_nbr as above. */
+int tersoff_md_force(tersoff_ctx *ctx, int32_t N, const double *pos, const double *box,
+                     const double *params, double R1, double R2, int32_t max_nbr, int32_t precision,
+                     double *E, void *F, double *W, tersoff_stream stream);
+
+/* Neighbour list of the last tersoff_md_force call, like tersoff_export_neighbors. Synchronous. */
+int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TERSOFF_GB300_H */

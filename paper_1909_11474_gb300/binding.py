@@ -1,0 +1,259 @@
+"""Thin Python binding of the C ABI in include/tersoff.h (argument marshalling only).
+
+Every method of `Context` wraps the C function of the same name with the `tersoff_` prefix dropped;
+all arithmetic runs in the CUDA library. PyTorch provides device memory and streams. There is no CPU
+fallback: a missing or unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtersoff_gb300.so")
+
+OK, E_ARG, E_NBR_OVERFLOW, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, E_UNSUPPORTED = range(8)
+STATUS_NBR_OVERFLOW, STATUS_MANY_NBRS, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4, 8
+LOSS_SQ, LOSS_Z = 0, 1
+
+EXPORTED = (
+    "tersoff_create", "tersoff_destroy", "tersoff_last_error", "tersoff_get_status",
+    "tersoff_build_neighbors", "tersoff_export_neighbors", "tersoff_build_info", "tersoff_eval",
+    "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
+    "tersoff_md_export_neighbors",
+)
+
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_f64 = ctypes.c_double
+
+
+class _Configs(ctypes.Structure):
+    _fields_ = [("C", _i32), ("atom_off", _vp), ("pos", _vp), ("box", _vp)]
+
+
+class _Targets(ctypes.Structure):
+    _fields_ = [("E", _vp), ("W", _vp), ("F", _vp), ("mask", _vp)]
+
+
+_lib = None
+
+
+def load():
+    """Open the shared library (built in-tree by paper_1909_11474_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_1909_11474_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "tersoff_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int]),
+        "tersoff_destroy": (None, [_vp]),
+        "tersoff_last_error": (ctypes.c_char_p, [_vp]),
+        "tersoff_get_status": (ctypes.c_int, [_vp, _vp]),
+        "tersoff_build_neighbors": (ctypes.c_int, [_vp, ctypes.POINTER(_Configs), _f64, _f64, _i32, _vp]),
+        "tersoff_export_neighbors": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "tersoff_build_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_i32)]),
+        "tersoff_eval": (ctypes.c_int, [_vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp]),
+        "tersoff_fitness": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _vp, _i32,
+                                           _vp, _vp, _vp, _vp]),
+        "tersoff_param_grad": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _vp, _i32,
+                                              _vp, _vp, _vp]),
+        "tersoff_eval_plain": (ctypes.c_int, [_vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+        "tersoff_md_force": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _f64, _f64, _i32, _i32,
+                                            _vp, _vp, _vp, _vp]),
+        "tersoff_md_export_neighbors": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class TersoffError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"tersoff error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _cuda(t: torch.Tensor, dtype, shape=None, name="tensor") -> torch.Tensor:
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Context:
+    """One tersoff_ctx on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = device
+        h = _vp()
+        rc = self.lib.tersoff_create(ctypes.byref(h), device)
+        if rc != OK:
+            raise TersoffError(rc, "tersoff_create failed")
+        self.h = h
+        self.C = 0
+        self.Ntot = 0
+        self.atom_off = None
+        self.max_nbr = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tersoff_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != OK:
+            raise TersoffError(rc, self.lib.tersoff_last_error(self.h).decode())
+
+    # ---- calls ---------------------------------------------------------------------------------
+    def get_status(self, stream=None) -> int:
+        return int(self.lib.tersoff_get_status(self.h, _stream(stream)))
+
+    def build_neighbors(self, atom_off, pos: torch.Tensor, box: torch.Tensor, R1: float = 2.8,
+                        R2: float = 3.2, max_nbr: int = 16, stream=None):
+        """atom_off: host int32 [C+1]; pos: CUDA float64 [Ntot][3]; box: CUDA float64 [C][3][3]."""
+        off = np.ascontiguousarray(np.asarray(atom_off, dtype=np.int32))
+        C = len(off) - 1
+        N = int(off[-1]) if C >= 0 else 0
+        _cuda(pos, torch.float64, (N, 3), "pos")
+        _cuda(box, torch.float64, (C, 3, 3), "box")
+        cfg = _Configs(C, off.ctypes.data, pos.data_ptr(), box.data_ptr())
+        self._check(self.lib.tersoff_build_neighbors(self.h, ctypes.byref(cfg), R1, R2, max_nbr,
+                                                     _stream(stream)))
+        self.C, self.Ntot, self.atom_off, self.max_nbr = C, N, off, max_nbr
+
+    def build_info(self):
+        n, b, m = ctypes.c_int64(), ctypes.c_int64(), _i32()
+        self._check(self.lib.tersoff_build_info(self.h, ctypes.byref(n), ctypes.byref(b), ctypes.byref(m)))
+        return n.value, b.value, m.value
+
+    def export_neighbors(self):
+        N, M = self.Ntot, self.max_nbr
+        cnt = np.zeros(N, np.int32)
+        nbr = np.zeros((N, M), np.int32)
+        shift = np.zeros((N, M, 3), np.int8)
+        self._check(self.lib.tersoff_export_neighbors(self.h, _ptr(cnt), _ptr(nbr), _ptr(shift)))
+        return cnt, nbr, shift
+
+    def eval(self, params: torch.Tensor, precision: int = 32, want_F: bool = True, stream=None):
+        """E [P][C], F [P][Ntot][3] (float32 or float64), W [P][C][6] on the params' device."""
+        P = params.shape[0]
+        _cuda(params, torch.float64, (P, 6), "params")
+        dev = params.device
+        E = torch.empty((P, self.C), dtype=torch.float64, device=dev)
+        W = torch.empty((P, self.C, 6), dtype=torch.float64, device=dev)
+        F = None
+        if want_F:
+            F = torch.empty((P, self.Ntot, 3), dtype=torch.float32 if precision == 32 else torch.float64,
+                            device=dev)
+        self._check(self.lib.tersoff_eval(self.h, params.data_ptr(), P, precision, E.data_ptr(),
+                                          _ptr(F), W.data_ptr(), _stream(stream)))
+        return E, F, W
+
+    def _targets(self, targets):
+        tE = _cuda(targets["E"], torch.float64, (self.C,), "targets E")
+        tW = _cuda(targets["W"], torch.float64, (self.C, 6), "targets W")
+        tF = _cuda(targets["F"], torch.float64, (self.Ntot, 3), "targets F")
+        tm = _cuda(targets["mask"], torch.uint8, (self.C,), "targets mask")
+        return _Targets(tE.data_ptr(), tW.data_ptr(), tF.data_ptr(), tm.data_ptr())
+
+    def fitness(self, params: torch.Tensor, targets: dict, w=(1.0, 1.0, 1.0), precision: int = 32,
+                stream=None, out=None):
+        """Z [P], Zq [P][3], S [P][3] (FP64) of Eq. 15, 17-19."""
+        P = params.shape[0]
+        _cuda(params, torch.float64, (P, 6), "params")
+        dev = params.device
+        if out is None:
+            out = (torch.empty(P, dtype=torch.float64, device=dev),
+                   torch.empty((P, 3), dtype=torch.float64, device=dev),
+                   torch.empty((P, 3), dtype=torch.float64, device=dev))
+        Z, Zq, S = out
+        t = self._targets(targets)
+        wv = (ctypes.c_double * 3)(*[float(x) for x in w])
+        self._check(self.lib.tersoff_fitness(self.h, params.data_ptr(), P, ctypes.byref(t), ctypes.addressof(wv),
+                                             precision, Z.data_ptr(), _ptr(Zq), _ptr(S), _stream(stream)))
+        return Z, Zq, S
+
+    def param_grad(self, params: torch.Tensor, targets: dict, w=(1.0, 1.0, 1.0), loss: int = LOSS_SQ,
+                   stream=None):
+        """L [P] and dL/dx [P][6] (FP64)."""
+        P = params.shape[0]
+        _cuda(params, torch.float64, (P, 6), "params")
+        dev = params.device
+        L = torch.empty(P, dtype=torch.float64, device=dev)
+        dL = torch.empty((P, 6), dtype=torch.float64, device=dev)
+        t = self._targets(targets)
+        wv = (ctypes.c_double * 3)(*[float(x) for x in w])
+        self._check(self.lib.tersoff_param_grad(self.h, params.data_ptr(), P, ctypes.byref(t), ctypes.addressof(wv),
+                                                loss, L.data_ptr(), dL.data_ptr(), _stream(stream)))
+        return L, dL
+
+    def eval_plain(self, params: torch.Tensor, stream=None):
+        """Plain FP64 path, one launch per (p, c): E [P][C], F [P][Ntot][3] float64, W [P][C][6]."""
+        P = params.shape[0]
+        _cuda(params, torch.float64, (P, 6), "params")
+        dev = params.device
+        E = torch.empty((P, self.C), dtype=torch.float64, device=dev)
+        F = torch.empty((P, self.Ntot, 3), dtype=torch.float64, device=dev)
+        W = torch.empty((P, self.C, 6), dtype=torch.float64, device=dev)
+        self._check(self.lib.tersoff_eval_plain(self.h, params.data_ptr(), P, E.data_ptr(), F.data_ptr(),
+                                                W.data_ptr(), _stream(stream)))
+        return E, F, W
+
+    def md_force(self, pos: torch.Tensor, box, params, R1: float = 2.8, R2: float = 3.2,
+                 max_nbr: int = 16, precision: int = 32, stream=None, out=None):
+        """One large cell: neighbour rebuild + E [1], F [N][3], W [6]."""
+        N = pos.shape[0]
+        _cuda(pos, torch.float64, (N, 3), "pos")
+        boxh = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(3, 3))
+        ph = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(6))
+        dev = pos.device
+        if out is None:
+            out = (torch.empty(1, dtype=torch.float64, device=dev),
+                   torch.empty((N, 3), dtype=torch.float32 if precision == 32 else torch.float64, device=dev),
+                   torch.empty(6, dtype=torch.float64, device=dev))
+        E, F, W = out
+        self._check(self.lib.tersoff_md_force(self.h, N, pos.data_ptr(), boxh.ctypes.data, ph.ctypes.data,
+                                              R1, R2, max_nbr, precision, E.data_ptr(), F.data_ptr(),
+                                              W.data_ptr(), _stream(stream)))
+        self.md_N, self.md_M = N, max_nbr
+        return E, F, W
+
+    def md_export_neighbors(self):
+        N, M = self.md_N, self.md_M
+        cnt = np.zeros(N, np.int32)
+        nbr = np.zeros((N, M), np.int32)
+        shift = np.zeros((N, M, 3), np.int8)
+        self._check(self.lib.tersoff_md_export_neighbors(self.h, _ptr(cnt), _ptr(nbr), _ptr(shift)))
+        return cnt, nbr, shift

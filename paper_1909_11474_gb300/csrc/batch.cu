@@ -1,0 +1,144 @@
+// batch.cu -- launchers of the batched evaluation kernel and the fitness finalisation
+// (Eq. 15, 17-19 of arXiv:1909.11474).
+#include <math.h>
+
+#include "batch_kernel.cuh"
+
+namespace tsf {
+
+constexpr int kPT = 16;   // parameter sets per warp row (lanes per atom slot)
+
+size_t batch_smem_bytes_pt(int precision, int nb, int nq, bool cluster) {
+  const size_t rs = precision == 64 ? 8 : 4;
+  size_t head = cluster ? smem_head_bytes<kPT, true>() : smem_head_bytes<kPT, false>();
+  size_t b = head + (size_t)nb * 3 * kPT * rs + (size_t)nb * 2 * 4 * rs + (size_t)nq * rs;
+  return (b + 15) & ~(size_t)15;
+}
+
+int batch_max_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+template <int MMAX, bool CLUSTER, int MINB, typename R>
+static cudaError_t launch_variant(const BatchParams &bp, int nitems, int cluster, size_t smem,
+                                  cudaStream_t s) {
+  auto kern = batch_kernel<kPT, MMAX, CLUSTER, MINB, R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nitems * (CLUSTER ? cluster : 1)));
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if constexpr (CLUSTER) {
+    if (cluster > 8) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, kern, bp);
+}
+
+cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
+                         int mode, const BatchOut &out, cudaStream_t s) {
+  BatchParams bp = {};
+  bp.P = P;
+  bp.C = ctx.C;
+  bp.Ntot = ctx.Ntot;
+  bp.params = params;
+  bp.atom_off = ctx.atom_off.as<int>();
+  bp.boff = ctx.boff.as<int>();
+  bp.poff = ctx.poff.as<int>();
+  const bool f64 = plan.precision == 64;
+  bp.gA = f64 ? ctx.gA64.p : ctx.gA32.p;
+  bp.gB = f64 ? ctx.gB64.p : ctx.gB32.p;
+  bp.gcos = f64 ? ctx.gcos64.p : ctx.gcos32.p;
+  bp.mode = mode;
+  bp.E = out.E;
+  bp.F = out.F;
+  bp.W = out.W;
+  bp.tE = out.tE;
+  bp.tW = out.tW;
+  bp.tF = out.tF;
+  bp.tmask = out.tmask;
+  bp.part = out.part;
+  bp.dpart = out.dpart;
+  bp.status = ctx.status.as<unsigned>();
+  for (const Bucket &b : plan.buckets) {
+    if (b.nitems == 0) continue;
+    bp.items = plan.items.as<int2>() + b.item_off;
+    cudaError_t e = cudaSuccess;
+    const bool cl = b.cluster > 1;
+    if (!f64) {
+      if (!cl && b.mmax <= 4) e = launch_variant<4, false, 2, float>(bp, b.nitems, 1, b.smem, s);
+      else if (!cl && b.mmax <= 6) e = launch_variant<6, false, 1, float>(bp, b.nitems, 1, b.smem, s);
+      else if (!cl) e = launch_variant<8, false, 1, float>(bp, b.nitems, 1, b.smem, s);
+      else if (b.mmax <= 6) e = launch_variant<6, true, 1, float>(bp, b.nitems, b.cluster, b.smem, s);
+      else e = launch_variant<8, true, 1, float>(bp, b.nitems, b.cluster, b.smem, s);
+    } else {
+      if (!cl) e = launch_variant<8, false, 1, double>(bp, b.nitems, 1, b.smem, s);
+      else e = launch_variant<8, true, 1, double>(bp, b.nitems, b.cluster, b.smem, s);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// One warp per parameter set: S_q = sum_c part[p][c][q] and D_q = sum_c dpart[c][q] in FP64 with a
+// fixed lane-strided order and a fixed xor-shuffle tree, then Zq = sqrt(S_q/D_q) (0 where D_q = 0),
+// Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not finite.
+__global__ void fitness_finalize_kernel(int P, int C, const double *__restrict__ part,
+                                        const double *__restrict__ dpart, double we, double wv,
+                                        double wf, double *__restrict__ Z, double *__restrict__ Zq,
+                                        double *__restrict__ S) {
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (p >= P) return;
+  double s[3] = {0, 0, 0}, d[3] = {0, 0, 0};
+  for (int c = lane; c < C; c += 32)
+    for (int q = 0; q < 3; ++q) {
+      s[q] += part[((size_t)p * C + c) * 3 + q];
+      d[q] += dpart[(size_t)c * 3 + q];
+    }
+  for (int off = 16; off > 0; off >>= 1)
+    for (int q = 0; q < 3; ++q) {
+      s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+      d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
+    }
+  if (lane == 0) {
+    const double w[3] = {we, wv, wf};
+    double z = 0.0, zq[3];
+    bool finite = true;
+    for (int q = 0; q < 3; ++q) {
+      finite = finite && isfinite(s[q]);
+      zq[q] = d[q] > 0.0 ? sqrt(s[q] / d[q]) : 0.0;
+      z += w[q] * zq[q];
+    }
+    Z[p] = finite ? z : INFINITY;
+    if (Zq)
+      for (int q = 0; q < 3; ++q) Zq[(size_t)p * 3 + q] = zq[q];
+    if (S)
+      for (int q = 0; q < 3; ++q) S[(size_t)p * 3 + q] = s[q];
+  }
+}
+
+cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
+                                    double we, double wv, double wf, double *Z, double *Zq,
+                                    double *S, cudaStream_t s) {
+  const int wpb = 8;
+  fitness_finalize_kernel<<<(P + wpb - 1) / wpb, wpb * 32, 0, s>>>(P, C, part, dpart, we, wv, wf, Z,
+                                                                   Zq, S);
+  return cudaGetLastError();
+}
+
+}  // namespace tsf

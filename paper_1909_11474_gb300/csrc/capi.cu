@@ -1,0 +1,352 @@
+// capi.cu -- the C ABI of include/tersoff.h: context, neighbour build, batch planning and the
+// stream-ordered evaluation calls. Host code only; kernels live in the other translation units.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include "ctx.hpp"
+
+using tsf::Ctx;
+
+struct tersoff_ctx {
+  Ctx c;
+};
+
+namespace {
+
+int fail(tersoff_ctx *ctx, int code, const char *fmt, const char *detail = "") {
+  if (ctx) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), fmt, detail);
+    ctx->c.err = buf;
+  }
+  return code;
+}
+
+#define TSF_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(ctx, TERSOFF_E_CUDA, "CUDA error: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+inline cudaStream_t S(tersoff_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// The cluster size and kernel variant of every configuration, and the work items of one launch per
+// (variant, cluster size), longest configurations first.
+int build_plan(tersoff_ctx *ctx, int precision, int P) {
+  Ctx &c = ctx->c;
+  tsf::BatchPlan &plan = precision == 64 ? c.plan64 : c.plan32;
+  if (plan.P == P && plan.precision == precision && !plan.buckets.empty()) return TERSOFF_OK;
+  const int optin = tsf::batch_max_smem_optin();
+  const size_t soft = std::min<size_t>((size_t)optin, 112 * 1024);  // two CTAs per SM
+  const int PT = 16;
+  const int ntiles = (P + PT - 1) / PT;
+  struct Key {
+    int mmax, cl;
+    bool operator<(const Key &o) const { return mmax != o.mmax ? mmax < o.mmax : cl < o.cl; }
+  };
+  std::map<Key, std::vector<int>> groups;
+  std::map<Key, size_t> smem;
+  for (int cf = 0; cf < c.C; ++cf) {
+    const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
+    int chosen = 0;
+    size_t need = 0;
+    for (int cl = 1; cl <= 16 && !chosen; cl *= 2) {
+      if (cl > 1 && (cl / 2) >= nat) break;
+      const int per = (nat + cl - 1) / cl;
+      size_t mx = 0;
+      for (int r = 0; r < cl; ++r) {
+        const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
+        const int nb = c.h_boff[s1] - c.h_boff[s0], nq = c.h_poff[s1] - c.h_poff[s0];
+        mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, cl > 1));
+      }
+      const size_t lim = (cl >= 8) ? (size_t)optin : soft;
+      if (mx <= lim) {
+        chosen = cl;
+        need = mx;
+      }
+    }
+    if (!chosen) return fail(ctx, TERSOFF_E_UNSUPPORTED, "configuration too large for the batched kernels%s");
+    const int mm = c.h_cfg_maxm[cf];
+    int mmax = precision == 64 ? 8 : (mm <= 4 && chosen == 1 ? 4 : (mm <= 6 ? 6 : 8));
+    Key k{mmax, chosen};
+    groups[k].push_back(cf);
+    smem[k] = std::max(smem[k], need);
+  }
+  std::vector<int2> items;
+  plan.buckets.clear();
+  // largest clusters (longest items) first so that they start early
+  std::vector<Key> keys;
+  for (auto &g : groups) keys.push_back(g.first);
+  std::sort(keys.begin(), keys.end(), [](const Key &x, const Key &y) {
+    return x.cl != y.cl ? x.cl > y.cl : x.mmax > y.mmax;
+  });
+  for (const Key &k : keys) {
+    std::vector<int> &cfgs = groups[k];
+    std::stable_sort(cfgs.begin(), cfgs.end(), [&](int x, int y) {
+      return (c.h_boff[c.h_atom_off[x + 1]] - c.h_boff[c.h_atom_off[x]]) >
+             (c.h_boff[c.h_atom_off[y + 1]] - c.h_boff[c.h_atom_off[y]]);
+    });
+    tsf::Bucket b;
+    b.mmax = k.mmax;
+    b.cluster = k.cl;
+    b.precision = precision;
+    b.smem = smem[k];
+    b.item_off = (int)items.size();
+    for (int cf : cfgs)
+      for (int t = 0; t < ntiles; ++t) items.push_back(make_int2(cf, t));
+    b.nitems = (int)items.size() - b.item_off;
+    plan.buckets.push_back(b);
+  }
+  TSF_CUDA(plan.items.ensure(std::max<size_t>(1, items.size()) * sizeof(int2)));
+  TSF_CUDA(cudaMemcpy(plan.items.p, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  plan.P = P;
+  plan.precision = precision;
+  return TERSOFF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tersoff_create(tersoff_ctx **out, int device) {
+  if (!out) return TERSOFF_E_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return TERSOFF_E_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return TERSOFF_E_CUDA;
+  tersoff_ctx *ctx = new tersoff_ctx();
+  ctx->c.device = device;
+  if (ctx->c.status.ensure(sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(ctx->c.status.p, 0, sizeof(unsigned)) != cudaSuccess) {
+    delete ctx;
+    return TERSOFF_E_CUDA;
+  }
+  *out = ctx;
+  return TERSOFF_OK;
+}
+
+void tersoff_destroy(tersoff_ctx *ctx) {
+  if (!ctx) return;
+  Ctx &c = ctx->c;
+  cudaSetDevice(c.device);
+  cudaDeviceSynchronize();
+  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv,
+                         &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
+                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.part, &c.dpart, &c.work,
+                         &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
+                         &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
+                         &c.md_Ui, &c.md_boxd};
+  for (auto *b : bufs) b->release();
+  delete ctx;
+}
+
+const char *tersoff_last_error(const tersoff_ctx *ctx) { return ctx ? ctx->c.err.c_str() : ""; }
+
+int tersoff_get_status(tersoff_ctx *ctx, tersoff_stream stream) {
+  if (!ctx) return -1;
+  cudaSetDevice(ctx->c.device);
+  unsigned v = 0;
+  if (cudaStreamSynchronize(S(stream)) != cudaSuccess) return -1;
+  if (cudaMemcpy(&v, ctx->c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return -1;
+  if (cudaMemset(ctx->c.status.p, 0, sizeof(unsigned)) != cudaSuccess) return -1;
+  return (int)v;
+}
+
+int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double R1, double R2,
+                            int32_t max_nbr, tersoff_stream stream) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  c.built = false;
+  c.plan32 = tsf::BatchPlan();
+  c.plan64 = tsf::BatchPlan();
+  if (!cfg || !cfg->atom_off || !cfg->pos || !cfg->box) return fail(ctx, TERSOFF_E_ARG, "null configuration pointer%s");
+  if (cfg->C < 1) return fail(ctx, TERSOFF_E_ARG, "C must be >= 1%s");
+  if (!(R1 > 0.0 && R2 > R1 && std::isfinite(R2))) return fail(ctx, TERSOFF_E_ARG, "need 0 < R1 < R2%s");
+  if (max_nbr < 1 || max_nbr > 32) return fail(ctx, TERSOFF_E_ARG, "max_nbr must be in [1, 32]%s");
+  const int C = cfg->C;
+  std::vector<int> off(cfg->atom_off, cfg->atom_off + C + 1);
+  if (off[0] != 0) return fail(ctx, TERSOFF_E_ARG, "atom_off[0] must be 0%s");
+  for (int k = 0; k < C; ++k) {
+    const int n = off[k + 1] - off[k];
+    if (n < 1 || n > 1024) return fail(ctx, TERSOFF_E_ARG, "every configuration needs 1..1024 atoms%s");
+  }
+  cudaSetDevice(c.device);
+  cudaStream_t s = S(stream);
+  const int64_t N = off[C];
+  const int M = max_nbr;
+  c.C = C;
+  c.Ntot = N;
+  c.M = M;
+  c.R1 = R1;
+  c.R2 = R2;
+  c.h_atom_off = off;
+  std::vector<int> cfgidx(N);
+  for (int k = 0; k < C; ++k)
+    for (int i = off[k]; i < off[k + 1]; ++i) cfgidx[i] = k;
+  TSF_CUDA(c.atom_off.ensure((C + 1) * sizeof(int)));
+  TSF_CUDA(c.atom_cfg.ensure(N * sizeof(int)));
+  TSF_CUDA(c.pos.ensure(N * 3 * sizeof(double)));
+  TSF_CUDA(c.pos32.ensure(N * sizeof(float4)));
+  TSF_CUDA(c.box.ensure((size_t)C * 9 * sizeof(double)));
+  TSF_CUDA(c.boxinv.ensure((size_t)C * 12 * sizeof(double)));
+  TSF_CUDA(c.cnt.ensure(N * sizeof(int)));
+  TSF_CUDA(c.nbr.ensure(N * M * sizeof(int)));
+  TSF_CUDA(c.shift.ensure(N * M * sizeof(char4)));
+  TSF_CUDA(c.boff.ensure((N + 1) * sizeof(int)));
+  TSF_CUDA(c.poff.ensure((N + 1) * sizeof(int)));
+  TSF_CUDA(cudaMemcpyAsync(c.atom_off.p, off.data(), (C + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  TSF_CUDA(cudaMemcpyAsync(c.atom_cfg.p, cfgidx.data(), N * sizeof(int), cudaMemcpyHostToDevice, s));
+  TSF_CUDA(cudaMemcpyAsync(c.pos.p, cfg->pos, N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TSF_CUDA(cudaMemcpyAsync(c.box.p, cfg->box, (size_t)C * 9 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
+  unsigned *st = c.status.as<unsigned>();
+  TSF_CUDA(tsf::launch_box_prep(C, c.box.as<double>(), c.boxinv.as<double>(), st, s));
+  TSF_CUDA(tsf::launch_pos32(N, c.pos.as<double>(), c.pos32.as<float4>(), nullptr, st, s));
+  TSF_CUDA(tsf::launch_neighbors_batch(N, c.atom_off.as<int>(), c.atom_cfg.as<int>(), c.pos.as<double>(),
+                                       c.pos32.as<float4>(), c.box.as<double>(), c.boxinv.as<double>(),
+                                       R2, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), st, s));
+  c.h_cnt.resize(N);
+  unsigned hst = 0;
+  TSF_CUDA(cudaMemcpyAsync(c.h_cnt.data(), c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, s));
+  TSF_CUDA(cudaMemcpyAsync(&hst, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  TSF_CUDA(cudaStreamSynchronize(s));
+  if (hst & TERSOFF_STATUS_NONFINITE) return fail(ctx, TERSOFF_E_NONFINITE, "non-finite positions or box%s");
+  if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "an atom has more than max_nbr neighbours%s");
+  c.h_boff.assign(N + 1, 0);
+  c.h_poff.assign(N + 1, 0);
+  c.h_cfg_maxm.assign(C, 0);
+  int maxm = 0;
+  for (int64_t i = 0; i < N; ++i) {
+    const int m = c.h_cnt[i];
+    c.h_boff[i + 1] = c.h_boff[i] + m;
+    c.h_poff[i + 1] = c.h_poff[i] + m * (m - 1) / 2;
+    maxm = std::max(maxm, m);
+    int &cm = c.h_cfg_maxm[cfgidx[i]];
+    cm = std::max(cm, m);
+  }
+  c.max_m = maxm;
+  c.Btot = c.h_boff[N];
+  c.Qtot = c.h_poff[N];
+  const size_t B = std::max<int64_t>(1, c.Btot), Q = std::max<int64_t>(1, c.Qtot);
+  TSF_CUDA(c.brev.ensure(B * sizeof(int)));
+  TSF_CUDA(c.gA32.ensure(B * sizeof(float4)));
+  TSF_CUDA(c.gB32.ensure(B * sizeof(float4)));
+  TSF_CUDA(c.gcos32.ensure(Q * sizeof(float)));
+  TSF_CUDA(c.gA64.ensure(B * sizeof(tsf::dvec4)));
+  TSF_CUDA(c.gB64.ensure(B * sizeof(tsf::dvec4)));
+  TSF_CUDA(c.gcos64.ensure(Q * sizeof(double)));
+  TSF_CUDA(cudaMemcpyAsync(c.boff.p, c.h_boff.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  TSF_CUDA(cudaMemcpyAsync(c.poff.p, c.h_poff.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+  TSF_CUDA(tsf::launch_reverse(N, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), c.boff.as<int>(),
+                               c.brev.as<int>(), st, s));
+  TSF_CUDA(tsf::launch_geometry(N, M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
+                                c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
+                                c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), R1, R2,
+                                c.gA32.as<float4>(), c.gB32.as<float4>(), c.gcos32.as<float>(),
+                                c.gA64.as<tsf::dvec4>(), c.gB64.as<tsf::dvec4>(), c.gcos64.as<double>(), s));
+  TSF_CUDA(cudaMemcpyAsync(&hst, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  TSF_CUDA(cudaStreamSynchronize(s));
+  if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "reverse neighbour entry missing%s");
+  c.built = true;
+  return TERSOFF_OK;
+}
+
+int tersoff_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "no neighbour build%s");
+  cudaSetDevice(c.device);
+  const int64_t N = c.Ntot, M = c.M;
+  if (cnt) TSF_CUDA(cudaMemcpy(cnt, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost));
+  if (nbr) TSF_CUDA(cudaMemcpy(nbr, c.nbr.p, N * M * sizeof(int), cudaMemcpyDeviceToHost));
+  if (shift) {
+    std::vector<char4> tmp(N * M);
+    TSF_CUDA(cudaMemcpy(tmp.data(), c.shift.p, N * M * sizeof(char4), cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < N * M; ++k) {
+      shift[3 * k] = tmp[k].x;
+      shift[3 * k + 1] = tmp[k].y;
+      shift[3 * k + 2] = tmp[k].z;
+    }
+  }
+  return TERSOFF_OK;
+}
+
+int tersoff_build_info(const tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t *max_m) {
+  if (!ctx || !ctx->c.built) return TERSOFF_E_STATE;
+  if (ntot) *ntot = ctx->c.Ntot;
+  if (nbonds) *nbonds = ctx->c.Btot;
+  if (max_m) *max_m = ctx->c.max_m;
+  return TERSOFF_OK;
+}
+
+int tersoff_eval(tersoff_ctx *ctx, const double *params, int32_t P, int32_t precision, double *E,
+                 void *F, double *W, tersoff_stream stream) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  if (!params || P < 1) return fail(ctx, TERSOFF_E_ARG, "need params and P >= 1%s");
+  if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
+  if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
+  cudaSetDevice(c.device);
+  int rc = build_plan(ctx, precision, P);
+  if (rc) return rc;
+  tsf::BatchOut o = {};
+  o.E = E;
+  o.F = F;
+  o.W = W;
+  TSF_CUDA(tsf::launch_batch(c, precision == 64 ? c.plan64 : c.plan32, params, P, tsf::kModeEval, o, S(stream)));
+  return TERSOFF_OK;
+}
+
+int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
+                    const double *w, int32_t precision, double *Z, double *Zq, double *Sq,
+                    tersoff_stream stream) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  if (!params || P < 1 || !tg || !w || !Z) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
+  if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
+  if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
+  if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
+  cudaSetDevice(c.device);
+  int rc = build_plan(ctx, precision, P);
+  if (rc) return rc;
+  TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
+  tsf::BatchOut o = {};
+  o.tE = tg->E;
+  o.tW = tg->W;
+  o.tF = tg->F;
+  o.tmask = tg->mask;
+  o.part = c.part.as<double>();
+  o.dpart = c.dpart.as<double>();
+  cudaStream_t s = S(stream);
+  TSF_CUDA(tsf::launch_batch(c, precision == 64 ? c.plan64 : c.plan32, params, P, tsf::kModeFitness, o, s));
+  TSF_CUDA(tsf::launch_fitness_finalize(P, c.C, o.part, o.dpart, w[0], w[1], w[2], Z, Zq, Sq, s));
+  return TERSOFF_OK;
+}
+
+int tersoff_param_grad(tersoff_ctx *ctx, const double *, int32_t, const tersoff_targets *,
+                       const double *, int32_t, double *, double *, tersoff_stream) {
+  return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
+}
+
+int tersoff_eval_plain(tersoff_ctx *ctx, const double *, int32_t, double *, double *, double *,
+                       tersoff_stream) {
+  return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
+}
+
+int tersoff_md_force(tersoff_ctx *ctx, int32_t, const double *, const double *, const double *,
+                     double, double, int32_t, int32_t, double *, void *, double *, tersoff_stream) {
+  return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
+}
+
+int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *, int32_t *, int8_t *) {
+  return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
+}
+
+}  // extern "C"

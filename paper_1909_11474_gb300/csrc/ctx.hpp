@@ -1,0 +1,145 @@
+// ctx.hpp -- host-side context of the minimal-Tersoff library and the launchers each .cu exports.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tersoff.h"
+
+namespace tsf {
+
+// Four doubles, 32-byte aligned (one FP64 bond record).
+struct __align__(32) dvec4 {
+  double x, y, z, w;
+};
+__host__ __device__ inline dvec4 make_dvec4(double x, double y, double z, double w) {
+  dvec4 v;
+  v.x = x;
+  v.y = y;
+  v.z = z;
+  v.w = w;
+  return v;
+}
+
+// Grow-only device buffer owned by the context.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T *as() const {
+    return static_cast<T *>(p);
+  }
+};
+
+// Geometry cache of a neighbour build: compressed bond list (CSR over atoms) with the
+// parameter-independent quantities of every bond and of every unordered pair of bonds of an atom.
+struct Geometry {
+  const int *boff;      // [Ntot+1] first bond of atom i
+  const int *poff;      // [Ntot+1] first unordered bond pair of atom i
+  const int *brev;      // [Btot] bond index of the reverse entry (j; i, -n)
+  const void *gA;       // [Btot] R4: unit vector d/r (x, y, z), r
+  const void *gB;       // [Btot] R4: 1/r, f_C(r), f_C'(r), 0
+  const void *gcos;     // [Qtot] R: cos theta of pair (e, f), e < f, row-major over e
+};
+
+// One work item of the batched evaluation: configuration c, parameter tile t (P-tile of PT sets).
+struct WorkItem {
+  int c;
+  int tile;
+};
+
+// A launch bucket: items with the same kernel variant.
+struct Bucket {
+  int mmax;        // 5 or 8: largest neighbour count the variant handles
+  int cluster;     // CTAs per configuration (1 = no cluster)
+  int precision;   // 32 or 64
+  size_t smem;     // dynamic shared memory per CTA
+  int nitems;
+  int item_off;    // offset into the device item array
+};
+
+struct BatchPlan {
+  int precision = 0;
+  int P = 0;
+  std::vector<Bucket> buckets;
+  DevBuf items;    // int2 [total items]
+};
+
+struct Ctx {
+  int device = 0;
+  std::string err;
+  DevBuf status;   // unsigned
+
+  // --- batch build state ---
+  bool built = false;
+  int C = 0;
+  int64_t Ntot = 0, Btot = 0, Qtot = 0;
+  int M = 0, max_m = 0;
+  double R1 = 0, R2 = 0;
+  std::vector<int> h_atom_off, h_cnt, h_boff, h_poff, h_cfg_maxm;
+  DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, cnt, nbr, shift, boff, poff, brev;
+  DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
+  BatchPlan plan32, plan64;
+  DevBuf part, dpart, work;
+
+  // --- MD state ---
+  int md_N = 0, md_M = 0;
+  DevBuf md_pos, md_cnt, md_nbr, md_shift, md_rev, md_cells, md_cellcnt, md_Pij, md_red, md_Ui;
+  DevBuf md_boxd;
+};
+
+// ---- launchers (defined in the .cu files) ----
+// neighbors.cu
+cudaError_t launch_box_prep(int C, const double *box, double *boxinv, unsigned *status, cudaStream_t s);
+cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg,
+                         unsigned *status, cudaStream_t s);
+cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
+                                   const double *pos, const float4 *pos32, const double *box,
+                                   const double *boxinv, double R2, int M, int *cnt, int *nbr,
+                                   char4 *shift, unsigned *status, cudaStream_t s);
+cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,
+                           const int *boff, int *brev, unsigned *status, cudaStream_t s);
+cudaError_t launch_geometry(int64_t Ntot, int M, const int *atom_cfg, const int *atom_off,
+                            const int *brev, const double *pos,
+                            const double *box, const int *cnt, const int *nbr, const char4 *shift,
+                            const int *boff, const int *poff, double R1, double R2, float4 *gA32,
+                            float4 *gB32, float *gcos32, dvec4 *gA64, dvec4 *gB64,
+                            double *gcos64, cudaStream_t s);
+
+// batch.cu
+struct BatchOut {
+  double *E;          // [P][C]
+  void *F;            // [P][Ntot][3]
+  double *W;          // [P][C][6]
+  const double *tE, *tW, *tF;
+  const uint8_t *tmask;
+  double *part;       // [P][C][3]
+  double *dpart;      // [C][3]
+};
+enum BatchMode { kModeEval = 0, kModeFitness = 1 };
+cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
+                         int mode, const BatchOut &out, cudaStream_t s);
+cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
+                                    double we, double wv, double wf, double *Z, double *Zq,
+                                    double *S, cudaStream_t s);
+size_t batch_smem_bytes_pt(int precision, int nb, int nq, bool cluster);
+int batch_max_smem_optin();
+
+}  // namespace tsf

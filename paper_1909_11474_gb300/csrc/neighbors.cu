@@ -1,0 +1,268 @@
+// neighbors.cu -- neighbour build and parameter-independent geometry cache for batches of small
+// periodic cells (the index sets of the sums over j in Eq. 2 and over k in Eq. 7 of
+// arXiv:1909.11474, and the cutoff function f_C of Eq. 9).
+#include <math.h>
+
+#include "common.cuh"
+#include "ctx.hpp"
+
+namespace tsf {
+
+// Per configuration: the inverse box (fractional coordinates s = x H^-1, rows of H = lattice
+// vectors) and the three lattice-plane spacings, layout boxinv[c][12] = {Hinv (row-major), gap}.
+__global__ void box_prep_kernel(int C, const double *__restrict__ box, double *__restrict__ boxinv,
+                                unsigned *status) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const double *H = box + 9 * c;
+  double a0 = H[0], a1 = H[1], a2 = H[2], b0 = H[3], b1 = H[4], b2 = H[5], c0 = H[6], c1 = H[7],
+         c2 = H[8];
+  // cofactors
+  double bxc0 = b1 * c2 - b2 * c1, bxc1 = b2 * c0 - b0 * c2, bxc2 = b0 * c1 - b1 * c0;
+  double cxa0 = c1 * a2 - c2 * a1, cxa1 = c2 * a0 - c0 * a2, cxa2 = c0 * a1 - c1 * a0;
+  double axb0 = a1 * b2 - a2 * b1, axb1 = a2 * b0 - a0 * b2, axb2 = a0 * b1 - a1 * b0;
+  double det = a0 * bxc0 + a1 * bxc1 + a2 * bxc2;
+  double *o = boxinv + 12 * c;
+  bool ok = isfinite(det) && det != 0.0;
+  for (int k = 0; k < 9; ++k) ok = ok && isfinite(H[k]);
+  if (!ok) {
+    set_status(status, TERSOFF_STATUS_NONFINITE);
+    for (int k = 0; k < 12; ++k) o[k] = 0.0;
+    return;
+  }
+  double id = 1.0 / det;
+  // H^-1 columns are (b x c, c x a, a x b) / det, i.e. Hinv[mu][k] = cross_k[mu] / det
+  o[0] = bxc0 * id; o[1] = cxa0 * id; o[2] = axb0 * id;
+  o[3] = bxc1 * id; o[4] = cxa1 * id; o[5] = axb1 * id;
+  o[6] = bxc2 * id; o[7] = cxa2 * id; o[8] = axb2 * id;
+  double vol = fabs(det);
+  o[9] = vol / sqrt(bxc0 * bxc0 + bxc1 * bxc1 + bxc2 * bxc2);
+  o[10] = vol / sqrt(cxa0 * cxa0 + cxa1 * cxa1 + cxa2 * cxa2);
+  o[11] = vol / sqrt(axb0 * axb0 + axb1 * axb1 + axb2 * axb2);
+}
+
+__global__ void pos32_kernel(int64_t N, const double *__restrict__ pos, float4 *__restrict__ pos32,
+                             unsigned *status) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+  if (!(isfinite(x) && isfinite(y) && isfinite(z))) set_status(status, TERSOFF_STATUS_NONFINITE);
+  pos32[i] = make_float4((float)x, (float)y, (float)z, 0.f);
+}
+
+// Exact FP64 membership test: d = (x_j - x_i) + ((n0 a + n1 b) + n2 c), r^2 = (dx^2 + dy^2) + dz^2,
+// every operation individually rounded (no contraction into FMA).
+struct ExactPair {
+  double dx, dy, dz, r2;
+};
+__device__ __forceinline__ ExactPair exact_pair(double xjx, double xjy, double xjz, double xix,
+                                                double xiy, double xiz, const double *H, int n0,
+                                                int n1, int n2) {
+  double f0 = (double)n0, f1 = (double)n1, f2 = (double)n2;
+  double tx = __dadd_rn(__dadd_rn(__dmul_rn(f0, H[0]), __dmul_rn(f1, H[3])), __dmul_rn(f2, H[6]));
+  double ty = __dadd_rn(__dadd_rn(__dmul_rn(f0, H[1]), __dmul_rn(f1, H[4])), __dmul_rn(f2, H[7]));
+  double tz = __dadd_rn(__dadd_rn(__dmul_rn(f0, H[2]), __dmul_rn(f1, H[5])), __dmul_rn(f2, H[8]));
+  ExactPair e;
+  e.dx = __dadd_rn(__dsub_rn(xjx, xix), tx);
+  e.dy = __dadd_rn(__dsub_rn(xjy, xiy), ty);
+  e.dz = __dadd_rn(__dsub_rn(xjz, xiz), tz);
+  e.r2 = __dadd_rn(__dadd_rn(__dmul_rn(e.dx, e.dx), __dmul_rn(e.dy, e.dy)), __dmul_rn(e.dz, e.dz));
+  return e;
+}
+
+// One thread per atom i. For every atom j of the same configuration (ascending) the candidate
+// images are the integers n_k with |s_j - s_i + n_k| < R2 / gap_k (+ margin), found in FP32
+// fractional coordinates; each candidate is then decided by the exact FP64 test. Scanning j and n in
+// ascending order yields the canonical (j, n0, n1, n2) order directly.
+__global__ void __launch_bounds__(128) neighbors_batch_kernel(
+    int64_t Ntot, const int *__restrict__ atom_off, const int *__restrict__ atom_cfg,
+    const double *__restrict__ pos, const float4 *__restrict__ pos32,
+    const double *__restrict__ box, const double *__restrict__ boxinv, double R2, int M,
+    int *__restrict__ cnt_out, int *__restrict__ nbr, char4 *__restrict__ shift, unsigned *status) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ntot) return;
+  const int c = atom_cfg[i];
+  const int a0 = atom_off[c], a1 = atom_off[c + 1];
+  double H[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) H[k] = box[9 * c + k];
+  const double *bi = boxinv + 12 * c;
+  float Hi[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Hi[k] = (float)bi[k];
+  const float margin = 1e-4f;
+  const float rng0 = (float)(R2 / bi[9]) + margin;
+  const float rng1 = (float)(R2 / bi[10]) + margin;
+  const float rng2 = (float)(R2 / bi[11]) + margin;
+  const double R2sq = R2 * R2;
+  const double xix = pos[3 * i], xiy = pos[3 * i + 1], xiz = pos[3 * i + 2];
+  const float4 xi = pos32[i];
+  int count = 0;
+  for (int j = a0; j < a1; ++j) {
+    const float4 xj = pos32[j];
+    float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+    float s0 = dx * Hi[0] + dy * Hi[3] + dz * Hi[6];
+    float s1 = dx * Hi[1] + dy * Hi[4] + dz * Hi[7];
+    float s2 = dx * Hi[2] + dy * Hi[5] + dz * Hi[8];
+    int lo0 = (int)ceilf(-s0 - rng0), hi0 = (int)floorf(-s0 + rng0);
+    int lo1 = (int)ceilf(-s1 - rng1), hi1 = (int)floorf(-s1 + rng1);
+    int lo2 = (int)ceilf(-s2 - rng2), hi2 = (int)floorf(-s2 + rng2);
+    if (lo0 > hi0 || lo1 > hi1 || lo2 > hi2) continue;
+    const double xjx = pos[3 * j], xjy = pos[3 * j + 1], xjz = pos[3 * j + 2];
+    for (int n0 = lo0; n0 <= hi0; ++n0)
+      for (int n1 = lo1; n1 <= hi1; ++n1)
+        for (int n2 = lo2; n2 <= hi2; ++n2) {
+          if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
+          ExactPair e = exact_pair(xjx, xjy, xjz, xix, xiy, xiz, H, n0, n1, n2);
+          if (e.r2 < R2sq) {
+            if (count < M) {
+              nbr[i * M + count] = j;
+              shift[i * M + count] = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
+            }
+            ++count;
+          }
+        }
+  }
+  cnt_out[i] = count;
+  if (count > M) set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+  for (int e = count; e < M; ++e) {
+    nbr[i * M + e] = -1;
+    shift[i * M + e] = make_char4(0, 0, 0, 0);
+  }
+}
+
+// Reverse entry of every bond: entry (i; j, n) <-> (j; i, -n). The exact test is antisymmetric
+// (x_i - x_j = -(x_j - x_i) and t(-n) = -t(n) exactly), so the reverse entry always exists.
+__global__ void reverse_kernel(int64_t Ntot, int M, const int *__restrict__ cnt,
+                               const int *__restrict__ nbr, const char4 *__restrict__ shift,
+                               const int *__restrict__ boff, int *__restrict__ brev,
+                               unsigned *status) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ntot) return;
+  const int m = min(cnt[i], M);
+  for (int e = 0; e < m; ++e) {
+    const int j = nbr[i * M + e];
+    const char4 n = shift[i * M + e];
+    const int mj = min(cnt[j], M);
+    int found = -1;
+    for (int f = 0; f < mj; ++f) {
+      const char4 q = shift[(int64_t)j * M + f];
+      if (nbr[(int64_t)j * M + f] == (int)i && q.x == -n.x && q.y == -n.y && q.z == -n.z) {
+        found = f;
+        break;
+      }
+    }
+    if (found < 0) {
+      set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+      found = 0;
+    }
+    brev[boff[i] + e] = boff[j] + found;
+  }
+}
+
+// f_C of Eq. 9 and its derivative.
+__device__ __forceinline__ void cutoff_fc(double r, double R1, double R2, double &fc, double &fcp) {
+  if (r <= R1) {
+    fc = 1.0;
+    fcp = 0.0;
+  } else if (r >= R2) {
+    fc = 0.0;
+    fcp = 0.0;
+  } else {
+    const double w = (r - R1) / (R2 - R1);
+    fc = 0.5 * (1.0 + cospi(w));
+    fcp = -0.5 * M_PI / (R2 - R1) * sinpi(w);
+  }
+}
+
+// Per bond: unit vector, r, 1/r, f_C, f_C' and the configuration-local index of the reverse bond
+// (stored in the 4th slot: as a double, or as the bit pattern of an int in the FP32 record);
+// per unordered pair (e < f) of an atom's bonds: cos theta. Computed in FP64 from the same d as the
+// membership test, stored in FP64 and rounded to FP32.
+__global__ void geometry_kernel(int64_t Ntot, int M, const int *__restrict__ atom_cfg,
+                                const int *__restrict__ atom_off, const int *__restrict__ brev,
+                                const double *__restrict__ pos, const double *__restrict__ box,
+                                const int *__restrict__ cnt, const int *__restrict__ nbr,
+                                const char4 *__restrict__ shift, const int *__restrict__ boff,
+                                const int *__restrict__ poff, double R1, double R2,
+                                float4 *__restrict__ gA32, float4 *__restrict__ gB32,
+                                float *__restrict__ gcos32, dvec4 *__restrict__ gA64,
+                                dvec4 *__restrict__ gB64, double *__restrict__ gcos64) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Ntot) return;
+  const int c = atom_cfg[i];
+  double H[9];
+  for (int k = 0; k < 9; ++k) H[k] = box[9 * c + k];
+  const double xix = pos[3 * i], xiy = pos[3 * i + 1], xiz = pos[3 * i + 2];
+  const int m = min(cnt[i], M);
+  const int b0 = boff[i];
+  const int cb0 = boff[atom_off[c]];   // first bond of the configuration
+  for (int e = 0; e < m; ++e) {
+    const int rl = brev[b0 + e] - cb0;  // configuration-local index of the reverse bond
+    const int j = nbr[i * M + e];
+    const char4 n = shift[i * M + e];
+    ExactPair p = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], xix, xiy, xiz, H, n.x, n.y, n.z);
+    const double r = sqrt(p.r2);
+    const double ir = 1.0 / r;
+    double fc, fcp;
+    cutoff_fc(r, R1, R2, fc, fcp);
+    const double ux = p.dx * ir, uy = p.dy * ir, uz = p.dz * ir;
+    gA64[b0 + e] = make_dvec4(ux, uy, uz, r);
+    gB64[b0 + e] = make_dvec4(ir, fc, fcp, (double)rl);
+    gA32[b0 + e] = make_float4((float)ux, (float)uy, (float)uz, (float)r);
+    gB32[b0 + e] = make_float4((float)ir, (float)fc, (float)fcp, __int_as_float(rl));
+  }
+  int q = poff[i];
+  for (int e = 0; e < m; ++e) {
+    const dvec4 ue = gA64[b0 + e];
+    for (int f = e + 1; f < m; ++f) {
+      const dvec4 uf = gA64[b0 + f];
+      const double cs = ue.x * uf.x + ue.y * uf.y + ue.z * uf.z;
+      gcos64[q] = cs;
+      gcos32[q] = (float)cs;
+      ++q;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+cudaError_t launch_box_prep(int C, const double *box, double *boxinv, unsigned *status, cudaStream_t s) {
+  box_prep_kernel<<<nblk(C, 128), 128, 0, s>>>(C, box, boxinv, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *, unsigned *status,
+                         cudaStream_t s) {
+  if (N == 0) return cudaSuccess;
+  pos32_kernel<<<nblk(N, 256), 256, 0, s>>>(N, pos, pos32, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
+                                   const double *pos, const float4 *pos32, const double *box,
+                                   const double *boxinv, double R2, int M, int *cnt, int *nbr,
+                                   char4 *shift, unsigned *status, cudaStream_t s) {
+  if (Ntot == 0) return cudaSuccess;
+  neighbors_batch_kernel<<<nblk(Ntot, 128), 128, 0, s>>>(Ntot, atom_off, atom_cfg, pos, pos32, box,
+                                                         boxinv, R2, M, cnt, nbr, shift, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,
+                           const int *boff, int *brev, unsigned *status, cudaStream_t s) {
+  if (Ntot == 0) return cudaSuccess;
+  reverse_kernel<<<nblk(Ntot, 128), 128, 0, s>>>(Ntot, M, cnt, nbr, shift, boff, brev, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_geometry(int64_t Ntot, int M, const int *atom_cfg, const int *atom_off,
+                            const int *brev, const double *pos,
+                            const double *box, const int *cnt, const int *nbr, const char4 *shift,
+                            const int *boff, const int *poff, double R1, double R2, float4 *gA32,
+                            float4 *gB32, float *gcos32, dvec4 *gA64, dvec4 *gB64,
+                            double *gcos64, cudaStream_t s) {
+  if (Ntot == 0) return cudaSuccess;
+  geometry_kernel<<<nblk(Ntot, 128), 128, 0, s>>>(Ntot, M, atom_cfg, atom_off, brev, pos, box, cnt, nbr, shift, boff,
+                                                  poff, R1, R2, gA32, gB32, gcos32, gA64, gB64, gcos64);
+  return cudaGetLastError();
+}
+
+}  // namespace tsf

@@ -1,0 +1,33 @@
+"""Helpers shared by the tests: device transfer of seeded inputs and the error metrics of the
+parity bar (relative error for E and W with a floor, absolute error for F)."""
+import numpy as np
+import torch
+
+from paper_1909_11474_gb300 import inputs as I
+
+# FP32 parity bar: relative error < 1e-5 for energy and virial, absolute error < 1e-4 eV/A for forces.
+TOL32 = {"E": 1e-5, "W": 1e-5, "F": 1e-4}
+# FP64 mode: the same arithmetic in double precision; differences come only from summation order
+# and the library exp/log/pow implementations (~1e-15 per operation).
+TOL64 = {"E": 1e-11, "W": 1e-10, "F": 1e-10}
+
+
+def to_device(cs: I.ConfigSet, dev="cuda"):
+    return (torch.tensor(cs.pos, dtype=torch.float64, device=dev),
+            torch.tensor(cs.box, dtype=torch.float64, device=dev))
+
+
+def targets_to_device(t, dev="cuda"):
+    return {"E": torch.tensor(t["E"], device=dev), "W": torch.tensor(t["W"], device=dev),
+            "F": torch.tensor(t["F"], device=dev), "mask": torch.tensor(t["mask"], dtype=torch.uint8, device=dev)}
+
+
+def energy_rel_err(E, Eref):
+    return np.abs(E - Eref) / np.maximum(np.abs(Eref), 1e-12)
+
+
+def virial_rel_err(W, Wref, natoms):
+    """Per (p, c): ||W - Wref||_F / max(||Wref||_F, 1e-3 eV * N_c)."""
+    num = np.sqrt(((W - Wref) ** 2).sum(axis=-1))
+    den = np.maximum(np.sqrt((Wref ** 2).sum(axis=-1)), 1e-3 * natoms)
+    return num / den

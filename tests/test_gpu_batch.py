@@ -1,0 +1,150 @@
+"""Parity of the CUDA batched path (neighbour build, E/F/W, fitness) with the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1909_11474_gb300 import inputs as I
+
+from ._util import TOL32, TOL64, energy_rel_err, targets_to_device, to_device, virial_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1909_11474_gb300 import binding
+    return binding.Context(0)
+
+
+def _build(ctx, cs, R1=2.8, R2=3.2, M=16):
+    pos, box = to_device(cs)
+    ctx.build_neighbors(cs.atom_off, pos, box, R1, R2, M)
+    return pos, box
+
+
+def _oracle_lists(cs, R2=3.2):
+    out = []
+    for c in range(cs.C):
+        nl = oracle.neighbor_list(*cs.config(c), R2)
+        a = int(cs.atom_off[c])
+        for i in range(cs.natoms[c]):
+            e = slice(nl["off"][i], nl["off"][i + 1])
+            out.append((nl["j"][e] + a, nl["n"][e]))
+    return out
+
+
+def _mixed_set(seed=5, C=10):
+    rng = np.random.default_rng(seed)
+    sizes = [(1, 1, 1), (2, 2, 2), (1, 2, 3), (3, 2, 2), (2, 1, 1)]
+    return I.make_cells(rng, C, lambda: sizes[rng.integers(0, len(sizes))],
+                        lambda: I.random_strain(rng, 0.03), lambda: float(rng.uniform(0.05, 0.2)),
+                        lambda: int(rng.integers(0, 3)))
+
+
+def _special_set():
+    """Edge cases: a lone atom (no neighbours), a dimer (zeta = 0), one atom whose only neighbours are
+    its own images, a compressed 8-atom cell with several images of the same j."""
+    pos_list, box_list = [], []
+    pos_list.append(np.array([[1.0, 2.0, 3.0]])); box_list.append(np.eye(3) * 12.0)
+    pos_list.append(np.array([[0.0, 0.0, 0.0], [2.3, 0.1, 0.0]])); box_list.append(np.eye(3) * 15.0)
+    pos_list.append(np.array([[0.1, 0.2, 0.3]])); box_list.append(np.eye(3) * 2.5)
+    p, b = I.diamond_supercell((1, 1, 1), a=4.6)
+    pos_list.append(p + np.random.default_rng(3).normal(0, 0.05, p.shape)); box_list.append(b)
+    return I.pack_configs(pos_list, box_list)
+
+
+@pytest.mark.parametrize("which", ["single", "ga", "mixed", "special"])
+def test_neighbor_lists_bit_exact(ctx, which):
+    cs = {"single": lambda: I.workload_single_cell()["configs"],
+          "ga": lambda: I.workload_ga_batch(P=2, C=20)["configs"],
+          "mixed": _mixed_set, "special": _special_set}[which]()
+    _build(ctx, cs)
+    cnt, nbr, shift = ctx.export_neighbors()
+    ref = _oracle_lists(cs)
+    assert len(ref) == cs.Ntot
+    for i, (j, n) in enumerate(ref):
+        assert cnt[i] == len(j), i
+        assert np.array_equal(nbr[i, :cnt[i]], j), i
+        assert np.array_equal(shift[i, :cnt[i]], n), i
+        assert (nbr[i, cnt[i]:] == -1).all()
+
+
+def _compare_eval(ctx, cs, params, precision, tol):
+    P = len(params)
+    pt = torch.tensor(params, dtype=torch.float64, device="cuda")
+    E, F, W = ctx.eval(pt, precision=precision)
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+    Er, Wr, Fr = oracle.evaluate_batch(cs, params)
+    E, F, W = E.cpu().numpy(), F.cpu().double().numpy(), W.cpu().numpy()
+    natoms = cs.natoms[None, :]
+    eE = energy_rel_err(E, Er).max()
+    eW = virial_rel_err(W, Wr, natoms).max()
+    eF = np.abs(F - Fr).max()
+    assert eE < tol["E"], eE
+    assert eW < tol["W"], eW
+    assert eF < tol["F"], eF
+    return eE, eW, eF
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_single_cell_eval(ctx, precision):
+    w = I.workload_single_cell()
+    _build(ctx, w["configs"])
+    _compare_eval(ctx, w["configs"], w["params"], precision, TOL32 if precision == 32 else TOL64)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_ga_batch_eval_ragged_tiles(ctx, precision):
+    """P = 37 spans three parameter tiles of 16 with a ragged tail; 64-atom strained cells."""
+    w = I.workload_ga_batch(P=37, C=6)
+    _build(ctx, w["configs"])
+    _compare_eval(ctx, w["configs"], w["params"], precision, TOL32 if precision == 32 else TOL64)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_mixed_sizes_eval(ctx, precision):
+    """8..96-atom cells with vacancies, strain and pairs inside the switching region."""
+    cs = _mixed_set()
+    _build(ctx, cs)
+    params = I.population(np.random.default_rng(8), 5)[0]
+    _compare_eval(ctx, cs, params, precision, TOL32 if precision == 32 else TOL64)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_special_cases_eval(ctx, precision):
+    cs = _special_set()
+    _build(ctx, cs)
+    _compare_eval(ctx, cs, I.TABLE2_PARAMS[None, :], precision, TOL32 if precision == 32 else TOL64)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_fitness_matches_oracle(ctx, precision):
+    w = I.workload_ga_batch(P=21, C=5)
+    cs = w["configs"]
+    Eh, Wh, Fh = oracle.evaluate_batch(cs, w["hidden"][None, :])
+    t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0],
+                       mask=np.array([7, 3, 5, 6, 1], np.uint8))
+    ref = oracle.fitness(cs, w["params"], t, w=(1.0, 0.7, 0.3))
+    _build(ctx, cs)
+    Z, Zq, S = ctx.fitness(torch.tensor(w["params"], device="cuda"), targets_to_device(t),
+                           w=(1.0, 0.7, 0.3), precision=precision)
+    Z, Zq, S = Z.cpu().numpy(), Zq.cpu().numpy(), S.cpu().numpy()
+    rtol = 1e-5 if precision == 32 else 1e-10
+    assert np.allclose(Z, ref["Z"], rtol=rtol, atol=0)
+    assert np.allclose(Zq, ref["Zq"], rtol=rtol, atol=1e-12)
+    assert np.allclose(S, ref["S"], rtol=10 * rtol, atol=1e-12)
+
+
+def test_fitness_nonfinite_parameters_rank_last(ctx):
+    w = I.workload_ga_batch(P=3, C=2)
+    cs = w["configs"]
+    _build(ctx, cs)
+    params = w["params"].copy()
+    params[1, 0] = np.nan
+    t = {"E": np.full(cs.C, -4.6), "W": np.zeros((cs.C, 6)), "F": np.zeros((cs.Ntot, 3)),
+         "mask": np.full(cs.C, 7, np.uint8)}
+    Z, _, _ = ctx.fitness(torch.tensor(params, device="cuda"), targets_to_device(t))
+    Z = Z.cpu().numpy()
+    assert np.isinf(Z[1]) and np.isfinite(Z[0]) and np.isfinite(Z[2])
