@@ -172,7 +172,9 @@ def site_energy_sum(d: torch.Tensor, owner: torch.Tensor, ta: torch.Tensor, tb: 
 
     Uij = fC * (fR - b * fA)              # Eq. 3
     Ui = 0.5 * torch.zeros(natoms, dtype=_F64).index_add(0, owner, Uij)   # Eq. 2
-    return Ui.sum(), Ui                   # Eq. 1
+    # magnitude of the summands of U (a conditioning scale for error bars, not part of U)
+    scale = 0.5 * (fC * (fR.abs() + (b * fA).abs())).sum()
+    return Ui.sum(), Ui, scale            # Eq. 1
 
 
 class _Prepared:
@@ -200,33 +202,41 @@ def _energy_graph(prep: _Prepared, params: torch.Tensor, R1, R2, create_graph=Fa
     eps = torch.zeros((3, 3), dtype=_F64, requires_grad=True)
     d0 = (x[prep.j] - x[prep.owner]) + prep.T
     d = d0 + d0 @ eps.T                    # (I + eps) d, homogeneous strain
-    U, Ui = site_energy_sum(d, prep.owner, prep.ta, prep.tb, prep.N, params, R1, R2)
-    gx, ge = torch.autograd.grad(U, (x, eps), create_graph=create_graph)
+    U, Ui, scale = site_energy_sum(d, prep.owner, prep.ta, prep.tb, prep.N, params, R1, R2)
+    gx, ge, gd = torch.autograd.grad(U, (x, eps, d), create_graph=create_graph)
     F = -gx
     Wm = -ge                               # W_mu,nu = -dU/d eps_mu,nu
     W6 = torch.stack([Wm[0, 0], Wm[1, 1], Wm[2, 2], Wm[0, 1], Wm[1, 2], Wm[2, 0]])
-    return U, Ui, F, W6, Wm
+    # magnitude of the summands of W = -sum_bonds dU/dd (x) d (conditioning scale, diagnostics only)
+    wscale = (gd.detach().norm(dim=1) * d.detach().norm(dim=1)).sum()
+    return U, Ui, F, W6, Wm, scale.detach(), wscale
 
 
 def evaluate(pos, box, params, R1: float = R1_DEFAULT, R2: float = R2_DEFAULT, prep=None):
     """E (eV, total), F [N][3] (eV/A), W [6] (eV, total; xx, yy, zz, xy, yz, zx), W3 [3][3], U_i [N]."""
     prep = prep or _Prepared(pos, box, R2)
     p = torch.as_tensor(np.asarray(params, dtype=np.float64))
-    U, Ui, F, W6, Wm = _energy_graph(prep, p, R1, R2)
+    U, Ui, F, W6, Wm, es, ws = _energy_graph(prep, p, R1, R2)
     return {"E": float(U.detach()), "F": F.detach().numpy(), "W": W6.detach().numpy(),
-            "W3": Wm.detach().numpy(), "Ui": Ui.detach().numpy()}
+            "W3": Wm.detach().numpy(), "Ui": Ui.detach().numpy(),
+            "E_scale": float(es), "W_scale": float(ws)}
 
 
-def evaluate_batch(configs, params, R1: float = R1_DEFAULT, R2: float = R2_DEFAULT, pairs=None):
+def evaluate_batch(configs, params, R1: float = R1_DEFAULT, R2: float = R2_DEFAULT, pairs=None,
+                   scales: bool = False):
     """E [P][C], W [P][C][6], F [P][Ntot][3] for every (parameter set p, configuration c).
 
     `pairs` optionally restricts the work to a list of (p, c); other entries are left NaN.
+    With scales=True also returns ES [P][C], WS [P][C]: the summed magnitudes of the summands of E
+    and of W, the conditioning scales of the two sums.
     """
     params = np.atleast_2d(np.asarray(params, dtype=np.float64))
     P, C = len(params), configs.C
     E = np.full((P, C), np.nan)
     W = np.full((P, C, 6), np.nan)
     F = np.full((P, configs.Ntot, 3), np.nan)
+    ES = np.full((P, C), np.nan)
+    WS = np.full((P, C), np.nan)
     todo = {}
     for p, c in (pairs if pairs is not None else [(p, c) for c in range(C) for p in range(P)]):
         todo.setdefault(c, []).append(p)
@@ -239,6 +249,10 @@ def evaluate_batch(configs, params, R1: float = R1_DEFAULT, R2: float = R2_DEFAU
             E[p, c] = r["E"]
             W[p, c] = r["W"]
             F[p, a:a + len(pos)] = r["F"]
+            ES[p, c] = r["E_scale"]
+            WS[p, c] = r["W_scale"]
+    if scales:
+        return E, W, F, ES, WS
     return E, W, F
 
 
@@ -320,7 +334,7 @@ def loss_and_grad(configs, params_row, targets, w=(1.0, 1.0, 1.0), loss: str = "
         N = len(pos)
         prep = _Prepared(pos, box, R2)
         need_graph = bool(mask[c] & 6)
-        U, _, F, W6, _ = _energy_graph(prep, p, R1, R2, create_graph=need_graph)
+        U, _, F, W6, _, _, _ = _energy_graph(prep, p, R1, R2, create_graph=need_graph)
         if mask[c] & 1:
             S[0] = S[0] + (U / N - float(targets["E"][c])) ** 2
         if mask[c] & 2:

@@ -22,12 +22,19 @@ def targets_to_device(t, dev="cuda"):
             "F": torch.tensor(t["F"], device=dev), "mask": torch.tensor(t["mask"], dtype=torch.uint8, device=dev)}
 
 
-def energy_rel_err(E, Eref):
-    return np.abs(E - Eref) / np.maximum(np.abs(Eref), 1e-12)
+# A relative error is ill-posed where a sum cancels to near zero (E of a far-off parameter set, W of a
+# cell near equilibrium), while FP32 bounds the absolute error of a sum by ~n u sum|summands|. The
+# relative errors below therefore divide by max(|X|, 0.1 S_X), S_X = the summed magnitudes of the
+# summands of X (computed by the oracle): a true relative error wherever |X| >= 0.1 S_X.
+FLOOR = 0.1
 
 
-def virial_rel_err(W, Wref, natoms):
-    """Per (p, c): ||W - Wref||_F / max(||Wref||_F, 1e-3 eV * N_c)."""
+def energy_rel_err(E, Eref, Escale):
+    return np.abs(E - Eref) / np.maximum(np.maximum(np.abs(Eref), FLOOR * Escale), 1e-300)
+
+
+def virial_rel_err(W, Wref, Wscale):
+    """Per (p, c): ||W - Wref||_F / max(||Wref||_F, 0.1 S_W)."""
     num = np.sqrt(((W - Wref) ** 2).sum(axis=-1))
-    den = np.maximum(np.sqrt((Wref ** 2).sum(axis=-1)), 1e-3 * natoms)
+    den = np.maximum(np.maximum(np.sqrt((Wref ** 2).sum(axis=-1)), FLOOR * Wscale), 1e-300)
     return num / den

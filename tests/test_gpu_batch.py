@@ -76,11 +76,10 @@ def _compare_eval(ctx, cs, params, precision, tol):
     E, F, W = ctx.eval(pt, precision=precision)
     torch.cuda.synchronize()
     assert ctx.get_status() == 0
-    Er, Wr, Fr = oracle.evaluate_batch(cs, params)
+    Er, Wr, Fr, ES, WS = oracle.evaluate_batch(cs, params, scales=True)
     E, F, W = E.cpu().numpy(), F.cpu().double().numpy(), W.cpu().numpy()
-    natoms = cs.natoms[None, :]
-    eE = energy_rel_err(E, Er).max()
-    eW = virial_rel_err(W, Wr, natoms).max()
+    eE = energy_rel_err(E, Er, ES).max()
+    eW = virial_rel_err(W, Wr, WS).max()
     eF = np.abs(F - Fr).max()
     assert eE < tol["E"], eE
     assert eW < tol["W"], eW

@@ -57,6 +57,10 @@ def test_perfect_diamond_closed_form(reps, a):
     assert np.allclose(r["W"][:3] / N, W_atom, rtol=1e-10, atol=1e-12)
     assert np.allclose(r["W"][3:], 0.0, atol=1e-10)
     assert np.abs(r["F"]).max() < 1e-10
+    # summand magnitude of Eq. 1-3: 4 bonds x 1/2 (f_R + b0 f_A) per atom
+    _, _, b0 = diamond_closed_form(a)
+    fR, fA, _ = morse_parts(a * math.sqrt(3.0) / 4.0)
+    assert r["E_scale"] / N == pytest.approx(2.0 * (fR + b0 * fA), rel=1e-12)
 
 
 def test_perfect_diamond_equilibrium_and_paper_values(golden):
