@@ -6,7 +6,7 @@ import torch
 import oracle
 from paper_1909_11474_gb300 import inputs as I
 
-from ._util import TOL32, TOL64, energy_rel_err, targets_to_device, to_device, virial_rel_err
+from ._util import TOL32, TOL64, energy_rel_err, force_err, targets_to_device, to_device, virial_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -80,7 +80,7 @@ def _compare_eval(ctx, cs, params, precision, tol):
     E, F, W = E.cpu().numpy(), F.cpu().double().numpy(), W.cpu().numpy()
     eE = energy_rel_err(E, Er, ES).max()
     eW = virial_rel_err(W, Wr, WS).max()
-    eF = np.abs(F - Fr).max()
+    eF = force_err(F, Fr)
     assert eE < tol["E"], eE
     assert eW < tol["W"], eW
     assert eF < tol["F"], eF
@@ -92,6 +92,16 @@ def test_single_cell_eval(ctx, precision):
     w = I.workload_single_cell()
     _build(ctx, w["configs"])
     _compare_eval(ctx, w["configs"], w["params"], precision, TOL32 if precision == 32 else TOL64)
+
+
+def test_physical_forces_strict_absolute_bar(ctx):
+    """Table 2 parameters on strained, displaced 64-atom cells: |dF| < 1e-4 eV/A with no scaling."""
+    w = I.workload_ga_batch(P=2, C=8)
+    _build(ctx, w["configs"])
+    params = np.stack([w["hidden"], w["hidden"] * np.array([1.02, 0.99, 1.0, 1.05, 0.97, 1.03])])
+    E, F, W = ctx.eval(torch.tensor(params, device="cuda"), precision=32)
+    _, _, Fr = oracle.evaluate_batch(w["configs"], params)
+    assert np.abs(F.cpu().double().numpy() - Fr).max() < 1e-4
 
 
 @pytest.mark.parametrize("precision", [32, 64])
