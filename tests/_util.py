@@ -51,3 +51,29 @@ def virial_rel_err(W, Wref, Wscale):
     num = np.sqrt(((W - Wref) ** 2).sum(axis=-1))
     den = np.maximum(np.maximum(np.sqrt((Wref ** 2).sum(axis=-1)), FLOOR * Wscale), 1e-300)
     return num / den
+
+
+def fitness_bounds(cs, targets, E, W, F, ES, WS, tol=None):
+    """Bounds on |d sqrt(S_q)| per parameter set implied by the per-quantity bars.
+
+    sqrt(S_q) is the 2-norm of the residual vector, so by the triangle inequality it moves by at most
+    the 2-norm of the prediction errors, each bounded by its bar (per-atom E and W, forces per atom).
+    Returns B [P][3]; |dZq| <= B / sqrt(D_q) and |dZ| <= sum_q w_q B_q / sqrt(D_q).
+    """
+    tol = tol or TOL32
+    mask = np.asarray(targets["mask"])
+    N = cs.natoms.astype(np.float64)
+    P = E.shape[0]
+    B = np.zeros((P, 3))
+    eb = tol["E"] * np.maximum(np.abs(E), FLOOR * ES) / N[None, :]
+    wb = tol["W"] * np.maximum(np.sqrt((W ** 2).sum(-1)), FLOOR * WS) / N[None, :]
+    fb = tol["F"] * np.maximum(1.0, np.abs(F).max(-1) / F_SCALE) * np.sqrt(3.0)
+    for c in range(cs.C):
+        a, b = int(cs.atom_off[c]), int(cs.atom_off[c + 1])
+        if mask[c] & 1:
+            B[:, 0] += eb[:, c] ** 2
+        if mask[c] & 2:
+            B[:, 1] += wb[:, c] ** 2
+        if mask[c] & 4:
+            B[:, 2] += (fb[:, a:b] ** 2).sum(-1)
+    return np.sqrt(B)

@@ -6,7 +6,8 @@ import torch
 import oracle
 from paper_1909_11474_gb300 import inputs as I
 
-from ._util import TOL32, TOL64, energy_rel_err, force_err, targets_to_device, to_device, virial_rel_err
+from ._util import (TOL32, TOL64, energy_rel_err, fitness_bounds, force_err, targets_to_device, to_device,
+                    virial_rel_err)
 
 pytestmark = pytest.mark.gpu
 
@@ -135,15 +136,18 @@ def test_fitness_matches_oracle(ctx, precision):
     Eh, Wh, Fh = oracle.evaluate_batch(cs, w["hidden"][None, :])
     t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0],
                        mask=np.array([7, 3, 5, 6, 1], np.uint8))
-    ref = oracle.fitness(cs, w["params"], t, w=(1.0, 0.7, 0.3))
+    wts = (1.0, 0.7, 0.3)
+    E, W, F, ES, WS = oracle.evaluate_batch(cs, w["params"], scales=True)
+    ref = oracle.fitness_from_predictions(cs, t, E, W, F, w=wts)
     _build(ctx, cs)
     Z, Zq, S = ctx.fitness(torch.tensor(w["params"], device="cuda"), targets_to_device(t),
-                           w=(1.0, 0.7, 0.3), precision=precision)
+                           w=wts, precision=precision)
     Z, Zq, S = Z.cpu().numpy(), Zq.cpu().numpy(), S.cpu().numpy()
-    rtol = 1e-5 if precision == 32 else 1e-10
-    assert np.allclose(Z, ref["Z"], rtol=rtol, atol=0)
-    assert np.allclose(Zq, ref["Zq"], rtol=rtol, atol=1e-12)
-    assert np.allclose(S, ref["S"], rtol=10 * rtol, atol=1e-12)
+    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32 if precision == 32 else TOL64)
+    D = ref["D"]
+    assert (np.abs(np.sqrt(S) - np.sqrt(ref["S"])) <= B).all()
+    assert (np.abs(Zq - ref["Zq"]) <= B / np.sqrt(D)[None, :]).all()
+    assert (np.abs(Z - ref["Z"]) <= (np.asarray(wts)[None, :] * B / np.sqrt(D)[None, :]).sum(-1)).all()
 
 
 def test_fitness_nonfinite_parameters_rank_last(ctx):
