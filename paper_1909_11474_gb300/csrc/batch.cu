@@ -2,18 +2,21 @@
 // (Eq. 15, 17-19 of arXiv:1909.11474).
 #include <math.h>
 
+#include <algorithm>
+
 #include "batch_kernel.cuh"
 
 namespace tsf {
 
-constexpr int kPT = 16;   // parameter sets per warp row (lanes per atom slot)
+constexpr int kPT = 32;   // parameter sets per warp: one atom per warp
 
-size_t batch_smem_bytes_pt(int precision, int nb, int nq, bool cluster) {
-  const size_t rs = precision == 64 ? 8 : 4;
-  size_t head = cluster ? smem_head_bytes<kPT, true>() : smem_head_bytes<kPT, false>();
-  size_t b = head + (size_t)nb * 3 * kPT * rs + (size_t)nb * 2 * 4 * rs + (size_t)nq * rs;
-  return (b + 15) & ~(size_t)15;
+size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster) {
+  if (precision == 64)
+    return cluster ? batch_smem<kPT, true, double>(nb, nq, nat) : batch_smem<kPT, false, double>(nb, nq, nat);
+  return cluster ? batch_smem<kPT, true, float>(nb, nq, nat) : batch_smem<kPT, false, float>(nb, nq, nat);
 }
+
+int batch_param_tile() { return kPT; }
 
 int batch_max_smem_optin() {
   int dev = 0, v = 0;
@@ -51,15 +54,28 @@ static cudaError_t launch_variant(const BatchParams &bp, int nitems, int cluster
 
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s) {
+  const bool f64 = plan.precision == 64;
+  // per-call preparation: per-parameter-set constants and the target forces in the working precision
+  {
+    const int64_t n = std::max<int64_t>(P, out.tF ? ctx.Ntot : 0);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (f64)
+      prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts),
+                                                 ctx.Ntot, out.tF, reinterpret_cast<dvec4 *>(out.tF4));
+    else
+      prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts),
+                                                ctx.Ntot, out.tF, reinterpret_cast<float4 *>(out.tF4));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   BatchParams bp = {};
   bp.P = P;
   bp.C = ctx.C;
   bp.Ntot = ctx.Ntot;
-  bp.params = params;
+  bp.consts = out.consts;
   bp.atom_off = ctx.atom_off.as<int>();
   bp.boff = ctx.boff.as<int>();
   bp.poff = ctx.poff.as<int>();
-  const bool f64 = plan.precision == 64;
   bp.gA = f64 ? ctx.gA64.p : ctx.gA32.p;
   bp.gB = f64 ? ctx.gB64.p : ctx.gB32.p;
   bp.gcos = f64 ? ctx.gcos64.p : ctx.gcos32.p;
@@ -69,7 +85,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.W = out.W;
   bp.tE = out.tE;
   bp.tW = out.tW;
-  bp.tF = out.tF;
+  bp.tF4 = out.tF4;
   bp.tmask = out.tmask;
   bp.part = out.part;
   bp.dpart = out.dpart;

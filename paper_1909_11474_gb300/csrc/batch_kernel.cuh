@@ -3,10 +3,11 @@
 // residuals of Eq. 15-19.
 //
 // Work decomposition (one CTA, or one thread-block cluster, per (configuration c, parameter tile)):
-//  * a warp's 32 lanes are APW = 32/PT atom slots x PT parameter sets; lane = slot * PT + pl.
-//    All lanes of a slot read the same bond geometry (shared-memory broadcast) and run the same
-//    control flow; the warp processes max(m) bonds, absent bonds of shorter lists are phantom
-//    bonds with f_C = f_C' = 0, which contribute exactly zero to every sum below.
+//  * a warp's 32 lanes are APW = 32/PT atom slots x PT parameter sets; lane = slot * PT + pl. With
+//    PT = 32 a warp evaluates one atom for 32 parameter sets: every lane reads the same bond geometry
+//    (shared-memory broadcast) and runs the same control flow, specialised at compile time for the
+//    atom's neighbour count. With PT < 32 the warp runs max(m) bonds and the missing bonds of shorter
+//    lists are phantom bonds with f_C = f_C' = 0, which contribute exactly zero to every sum below.
 //  * pass 1 (per atom i, per parameter set): f_R, f_A per bond, zeta_ij over the bond pairs,
 //    b_ij and b'_ij, U_i, and per bond c_ij = dU_i/dzeta_ij = -1/2 f_C f_A b'_ij.
 //  * pass 2: the partial derivative P_ij = dU_i/dd_ij of the site energy with respect to each of
@@ -18,8 +19,8 @@
 //    staged in shared memory, and the atom's virial -sum_j d_ij (x) P_ij.
 //  * pass 3 (after a CTA / cluster barrier): F_i = sum_j (P_ij - P_ji), reading P_ji through the
 //    reverse-bond index (from a peer CTA's shared memory when the configuration spans a cluster).
-//  * per-lane FP32 partial sums over a lane's atoms, converted once to FP64 and reduced across
-//    atom slots, warps and cluster ranks in a fixed order.
+//  * per-lane partial sums over a lane's atoms, reduced over atom slots and warps in a fixed order;
+//    the per-(parameter set, configuration) totals and residuals are formed in FP64.
 #pragma once
 
 #include "common.cuh"
@@ -30,28 +31,14 @@ namespace tsf {
 constexpr int kNW = 8;           // warps per CTA
 constexpr int kThreads = kNW * kWarp;
 constexpr int kNRed = 10;        // reduced quantities: U, W[6], S_f, sum|F|^2, sum|F*|^2
+constexpr int kMaxCluster = 16;
 
+// Per-parameter-set constants (prepared once per call by prep_kernel from the FP64 parameters):
+// x = exp(-alpha (r - r0)) = 2^(k1 r + k0), f_R = D0 x^2, f_A = 2 D0 x (Eq. 4-5, 11-14 at S = 2).
 template <typename R>
 struct PConsts {
   R D0, k1, k0, alpha, beta, h, n, inv2n;
 };
-
-template <typename R>
-__device__ __forceinline__ PConsts<R> load_consts(const double *__restrict__ params, int p) {
-  const double *x = params + 6 * p;
-  const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
-  const double log2e = 1.4426950408889634;
-  PConsts<R> K;
-  K.D0 = (R)D0;
-  K.k1 = (R)(-al * log2e);          // x = exp(-alpha (r - r0)) = 2^(k1 r + k0)
-  K.k0 = (R)(al * r0 * log2e);
-  K.alpha = (R)al;
-  K.beta = (R)be;
-  K.h = (R)h;
-  K.n = (R)n;
-  K.inv2n = (R)(-0.5 / n);
-  return K;
-}
 
 // b = (1 + zeta^n)^(-1/(2n)) and b' = db/dzeta = -1/2 b zeta^(n-1) / (1 + zeta^n)   (Eq. 6);
 // zeta = 0 gives b = 1, b' = 0 without evaluating 0^n.
@@ -74,8 +61,9 @@ struct AtomAcc {
 
 // Passes 1 and 2 for one atom per atom slot, M = the warp's largest neighbour count.
 // sA/sB: bond records (u_x, u_y, u_z, r), (1/r, f_C, f_C', rev); sC: pair cosines; lb/lq: this
-// atom's first bond / pair in shared memory; m: its neighbour count (<= M).
-template <int M, int PT, typename R>
+// atom's first bond / pair in shared memory; m: its neighbour count (<= M). EXACT: every slot has
+// m == M, so no bond is a phantom.
+template <int M, int PT, bool EXACT, typename R>
 __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restrict__ sA,
                                              const typename Vec4<R>::T *__restrict__ sB,
                                              const R *__restrict__ sC, R *__restrict__ stage,
@@ -84,7 +72,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   R ux[M], uy[M], uz[M], r[M], ir[M], fc[M], fcp[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    if (j < m) {
+    if (EXACT || j < m) {
       const auto A = sA[lb + j];
       const auto B = sB[lb + j];
       ux[j] = A.x; uy[j] = A.y; uz[j] = A.z; r[j] = A.w;
@@ -96,7 +84,10 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
   constexpr int NP = M * (M - 1) / 2;
   R cs[NP > 0 ? NP : 1];
-  {
+  if constexpr (EXACT) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) cs[q] = sC[lq + q];
+  } else {
     int q = 0;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
@@ -199,7 +190,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
     const R Px = coef * ux[j] + ir[j] * Ax[j];
     const R Py = coef * uy[j] + ir[j] * Ay[j];
     const R Pz = coef * uz[j] + ir[j] * Az[j];
-    if (store && j < m) {
+    if (store && (EXACT || j < m)) {
       R *st = stage + (size_t)(lb + j) * 3 * PT + pl;
       st[0] = Px;
       st[PT] = Py;
@@ -216,24 +207,22 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
 }
 
-template <int PT, int MMAX, typename R>
+template <int PT, int MMAX, bool EXACT, typename R>
 __device__ __forceinline__ void atom_forward_dispatch(int Mw, const typename Vec4<R>::T *sA,
                                                       const typename Vec4<R>::T *sB, const R *sC,
                                                       R *stage, int lb, int lq, int m, bool store,
                                                       int pl, const PConsts<R> &K, AtomAcc<R> &acc) {
+#define TSF_CASE(MM)                                                                          \
+  case MM:                                                                                    \
+    if constexpr (MMAX >= MM)                                                                 \
+      atom_forward<MM, PT, EXACT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc);        \
+    break;
   switch (Mw) {
-    case 0:
+    TSF_CASE(1) TSF_CASE(2) TSF_CASE(3) TSF_CASE(4) TSF_CASE(5) TSF_CASE(6) TSF_CASE(7) TSF_CASE(8)
+    default:
       break;
-    case 1: atom_forward<1, PT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); break;
-    case 2: atom_forward<2, PT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); break;
-    case 3: atom_forward<3, PT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); break;
-    case 4: atom_forward<4, PT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); break;
-    case 5: if constexpr (MMAX >= 5) atom_forward<5, PT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); break;
-    case 6: if constexpr (MMAX >= 6) atom_forward<6, PT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); break;
-    case 7: if constexpr (MMAX >= 7) atom_forward<7, PT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); break;
-    case 8: if constexpr (MMAX >= 8) atom_forward<8, PT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); break;
-    default: break;
   }
+#undef TSF_CASE
 }
 
 // ---- cluster helpers (distributed shared memory) ----
@@ -268,6 +257,9 @@ __device__ __forceinline__ double ld_cluster(unsigned addr, double) {
   asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr));
   return v;
 }
+__device__ __forceinline__ void st_cluster(unsigned addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
 __device__ __forceinline__ void st_cluster(unsigned addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
@@ -275,7 +267,7 @@ __device__ __forceinline__ void st_cluster(unsigned addr, double v) {
 struct BatchParams {
   int P, C;
   int64_t Ntot;
-  const double *params;
+  const void *consts;              // R [P][8]: PConsts of every parameter set
   const int *atom_off, *boff, *poff;
   const void *gA, *gB, *gcos;
   const int2 *items;
@@ -283,31 +275,44 @@ struct BatchParams {
   double *E;
   void *F;
   double *W;
-  const double *tE, *tW, *tF;
+  const double *tE, *tW;
+  const void *tF4;                 // R4 [Ntot]: target force (x, y, z) and |F*|^2
   const uint8_t *tmask;
   double *part, *dpart;
   unsigned *status;
 };
 
-// Shared memory layout (bytes): [red: kNW*kNRed*PT doubles][cred: 16*kNRed*PT doubles]
-// [stage: nb*3*PT R][sA: nb R4][sB: nb R4][sC: nq R] (cred only in cluster launches, <= 16 ranks). The fixed-size head puts every CTA's stage
-// at the same offset, so a peer's stage is addressed by mapping this CTA's own stage address.
-template <int PT, bool CLUSTER>
-__host__ __device__ constexpr size_t smem_head_bytes() {
-  return (size_t)(kNW + (CLUSTER ? 16 : 0)) * kNRed * PT * sizeof(double);
+// Shared memory of one CTA (R = float or double, R4 its 4-vector):
+//   [region0: max(nb*3*PT, (kNW + (cluster ? 16 : 1)) * kNRed * PT) R]  stage of P_ij, later the
+//    per-warp partial sums and the CTA totals (one row per cluster rank)
+//   [sA: nb R4][sB: nb R4][sC: nq R][satom: natoms int4]
+// region0 sits at offset 0 in every CTA, so a peer's stage is addressed by mapping this CTA's own
+// stage address to the peer rank.
+template <int PT, bool CLUSTER, typename R>
+__host__ __device__ inline size_t region0_elems(int nb) {
+  const size_t st = (size_t)nb * 3 * PT;
+  const size_t rd = (size_t)(kNW + (CLUSTER ? kMaxCluster : 1)) * kNRed * PT;
+  const size_t e = st > rd ? st : rd;
+  return (e * sizeof(R) + 31) / 32 * 32 / sizeof(R);
+}
+template <int PT, bool CLUSTER, typename R>
+__host__ __device__ inline size_t batch_smem(int nb, int nq, int nat) {
+  using R4 = typename Vec4<R>::T;
+  size_t b = region0_elems<PT, CLUSTER, R>(nb) * sizeof(R) + (size_t)nb * 2 * sizeof(R4);
+  b += ((size_t)nq * sizeof(R) + 15) / 16 * 16;
+  b += (size_t)nat * sizeof(int4);
+  return b;
 }
 
 template <int PT, int MMAX, bool CLUSTER, int MINB, typename R>
 __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams a) {
   using R4 = typename Vec4<R>::T;
-  extern __shared__ __align__(16) unsigned char smem[];
-  double *red = reinterpret_cast<double *>(smem);
-  double *cred = red + kNW * kNRed * PT;
-  R *stage = reinterpret_cast<R *>(smem + smem_head_bytes<PT, CLUSTER>());
+  extern __shared__ __align__(32) unsigned char smem[];
+  R *stage = reinterpret_cast<R *>(smem);
+  constexpr int APW = kWarp / PT;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int slot = lane / PT, pl = lane % PT;
-  constexpr int APW = kWarp / PT;
 
   unsigned rank = 0, ncta = 1;
   int item_idx = blockIdx.x;
@@ -320,7 +325,13 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   const int c = item.x;
   const int p = item.y * PT + pl;
   const bool active = p < a.P;
-  const PConsts<R> K = load_consts<R>(a.params, active ? p : a.P - 1);
+  PConsts<R> K;
+  {
+    const R4 *kc = reinterpret_cast<const R4 *>(a.consts) + 2 * (active ? p : a.P - 1);
+    const R4 k0 = kc[0], k1 = kc[1];
+    K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.alpha = k0.w;
+    K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
+  }
 
   // atom slice of this CTA
   const int ca0 = a.atom_off[c], ca1 = a.atom_off[c + 1];
@@ -331,12 +342,14 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   const int cb0 = a.boff[ca0];           // first bond of the configuration
   const int B0 = a.boff[s0], B1 = a.boff[s1];
   const int Q0 = a.poff[s0], Q1 = a.poff[s1];
-  const int nb = B1 - B0, nq = Q1 - Q0;
-  R4 *sA = reinterpret_cast<R4 *>(stage + (size_t)nb * 3 * PT);
+  const int nb = B1 - B0, nq = Q1 - Q0, ns = s1 - s0;
+  R4 *sA = reinterpret_cast<R4 *>(stage + region0_elems<PT, CLUSTER, R>(nb));
   R4 *sB = sA + nb;
   R *sC = reinterpret_cast<R *>(sB + nb);
+  int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) +
+                                         ((size_t)nq * sizeof(R) + 15) / 16 * 16);
 
-  // stage this slice's geometry in shared memory
+  // stage this slice's geometry and atom table in shared memory
   {
     const R4 *gA = reinterpret_cast<const R4 *>(a.gA) + B0;
     const R4 *gB = reinterpret_cast<const R4 *>(a.gB) + B0;
@@ -346,6 +359,10 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
       sB[t] = gB[t];
     }
     for (int t = tid; t < nq; t += kThreads) sC[t] = gC[t];
+    for (int t = tid; t < ns; t += kThreads) {
+      const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
+      satom[t] = make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0);
+    }
   }
   __syncthreads();
 
@@ -355,26 +372,38 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   for (int k = 0; k < 6; ++k) acc.W[k] = R(0);
 
   // ---- passes 1-2
-  for (int base = s0 + warp * APW; base < s1; base += kNW * APW) {
-    const int i = base + slot;
-    const bool valid = i < s1;
-    const int m = valid ? a.boff[i + 1] - a.boff[i] : 0;
-    const int lb = valid ? a.boff[i] - B0 : 0;
-    const int lq = valid ? a.poff[i] - Q0 : 0;
-    const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
-    if (Mw > MMAX) {
-      if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
-      continue;
+  for (int base = warp * APW; base < ns; base += kNW * APW) {
+    const int li = base + slot;
+    const bool valid = li < ns;
+    int4 at = make_int4(0, 0, 0, 0);
+    if (valid) at = satom[li];
+    const int m = at.z;
+    if constexpr (APW == 1) {
+      if (m > MMAX) {
+        if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
+        continue;
+      }
+      atom_forward_dispatch<PT, MMAX, true, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+    } else {
+      const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
+      const bool uniform = __all_sync(0xffffffffu, m == Mw);
+      if (Mw > MMAX) {
+        if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
+        continue;
+      }
+      if (uniform)
+        atom_forward_dispatch<PT, MMAX, true, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+      else
+        atom_forward_dispatch<PT, MMAX, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
     }
-    atom_forward_dispatch<PT, MMAX, R>(Mw, sA, sB, sC, stage, lb, lq, m, valid, pl, K, acc);
   }
   if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
 
   // ---- pass 3: F_i = sum_j (P_ij - P_ji)
   R sf = R(0), sF2 = R(0), sT = R(0);
   const uint8_t mask = (a.mode == kModeFitness) ? a.tmask[c] : 0;
-  unsigned peer_stage[16];
-  int peer_b0[17];
+  unsigned peer_stage[kMaxCluster];
+  int peer_b0[kMaxCluster + 1];
   if constexpr (CLUSTER) {
     const unsigned own = smem_addr(stage);
     for (unsigned r = 0; r < ncta; ++r) {
@@ -383,11 +412,11 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     }
     peer_b0[ncta] = a.boff[ca1] - cb0;
   }
-  for (int base = s0 + warp * APW; base < s1; base += kNW * APW) {
-    const int i = base + slot;
-    if (i >= s1) continue;
-    const int m = a.boff[i + 1] - a.boff[i];
-    const int lb = a.boff[i] - B0;
+  for (int base = warp * APW; base < ns; base += kNW * APW) {
+    const int li = base + slot;
+    if (li >= ns) continue;
+    const int4 at = satom[li];
+    const int m = at.z, lb = at.x;
     R Fx = R(0), Fy = R(0), Fz = R(0);
     for (int e = 0; e < m; ++e) {
       const R *st = stage + (size_t)(lb + e) * 3 * PT + pl;
@@ -412,6 +441,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
       }
     }
     sF2 += Fx * Fx + Fy * Fy + Fz * Fz;
+    const int i = s0 + li;
     if (a.mode == kModeEval) {
       if (active && a.F) {
         const size_t o = ((size_t)p * a.Ntot + i) * 3;
@@ -421,74 +451,74 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
         F[o + 2] = Fz;
       }
     } else if (mask & 4) {
-      const double *t = a.tF + (size_t)i * 3;
-      const R tx = (R)t[0], ty = (R)t[1], tz = (R)t[2];
-      const R ex = Fx - tx, ey = Fy - ty, ez = Fz - tz;
+      const R4 t = reinterpret_cast<const R4 *>(a.tF4)[i];
+      const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
       sf += ex * ex + ey * ey + ez * ez;
-      sT += tx * tx + ty * ty + tz * tz;
+      sT += t.w;
     }
   }
 
-  // ---- reductions: FP32 per lane -> FP64 across atom slots, warps and cluster ranks
-  double v[kNRed];
-  v[0] = (double)acc.U;
+  // ---- reductions: over atom slots (shuffles), warps (shared memory, fixed order), cluster ranks
+  R v[kNRed];
+  v[0] = acc.U;
 #pragma unroll
-  for (int k = 0; k < 6; ++k) v[1 + k] = (double)acc.W[k];
-  v[7] = (double)sf;
-  v[8] = (double)sF2;
-  v[9] = (double)sT;
+  for (int k = 0; k < 6; ++k) v[1 + k] = acc.W[k];
+  v[7] = sf;
+  v[8] = sF2;
+  v[9] = sT;
 #pragma unroll
   for (int k = 0; k < kNRed; ++k) v[k] = sum_over_atom_slots<PT>(v[k]);
+  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();   // stages no longer read
+  R *red = stage;                                   // [kNW][kNRed][PT]
+  R *tot = stage + kNW * kNRed * PT;                // [kMaxCluster][kNRed][PT] (rank 0 collects)
   if (slot == 0) {
 #pragma unroll
     for (int k = 0; k < kNRed; ++k) red[(warp * kNRed + k) * PT + pl] = v[k];
   }
   __syncthreads();
-  double tot = 0.0;
-  const int k_of = tid / PT, pl_of = tid % PT;   // thread -> (quantity, parameter lane)
-  if (tid < kNRed * PT) {
-    for (int w = 0; w < kNW; ++w) tot += red[(w * kNRed + k_of) * PT + pl_of];
+  for (int idx = tid; idx < kNRed * PT; idx += kThreads) {
+    R t = R(0);
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) t += red[w * kNRed * PT + idx];
+    if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(tot + rank * kNRed * PT + idx), 0), t);
+    else tot[idx] = t;
   }
   if constexpr (CLUSTER) {
-    if (tid < kNRed * PT) {
-      const unsigned dst = map_to_rank(smem_addr(cred + (rank * kNRed + k_of) * PT + pl_of), 0);
-      st_cluster(dst, tot);
-    }
     cluster_sync_all();
     if (rank != 0) return;
-    tot = 0.0;
-    if (tid < kNRed * PT)
-      for (unsigned r = 0; r < ncta; ++r) tot += cred[(r * kNRed + k_of) * PT + pl_of];
+  } else {
+    __syncthreads();
   }
-  __syncthreads();
-  if (tid < kNRed * PT) red[k_of * PT + pl_of] = tot;   // totals, [quantity][lane]
-  __syncthreads();
 
   if (tid < PT) {
     const int pp = item.y * PT + tid;
+    double q[kNRed];
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) {
+      double s = 0.0;
+      for (unsigned r = 0; r < ncta; ++r) s += (double)tot[(r * kNRed + k) * PT + tid];
+      q[k] = s;
+    }
     if (pp < a.P) {
-      const double U = red[0 * PT + tid];
-      double Wt[6];
-      for (int k = 0; k < 6; ++k) Wt[k] = red[(1 + k) * PT + tid];
       if (a.mode == kModeEval) {
-        if (a.E) a.E[(size_t)pp * a.C + c] = U;
+        if (a.E) a.E[(size_t)pp * a.C + c] = q[0];
         if (a.W)
-          for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = Wt[k];
+          for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = q[1 + k];
       } else {
-        const double N = (double)nat;
-        bool finite = isfinite(U) && isfinite(red[8 * PT + tid]);
-        for (int k = 0; k < 6; ++k) finite = finite && isfinite(Wt[k]);
+        const double invN = 1.0 / (double)nat;
+        bool finite = isfinite(q[0]) && isfinite(q[8]);
+        for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);
         double se = 0.0, sv = 0.0, sfv = 0.0;
         if (mask & 1) {
-          const double d = U / N - a.tE[c];
+          const double d = q[0] * invN - a.tE[c];
           se = d * d;
         }
         if (mask & 2)
           for (int k = 0; k < 6; ++k) {
-            const double d = Wt[k] / N - a.tW[c * 6 + k];
+            const double d = q[1 + k] * invN - a.tW[c * 6 + k];
             sv += d * d;
           }
-        if (mask & 4) sfv = red[7 * PT + tid];
+        if (mask & 4) sfv = q[7];
         if (!finite) se = sv = sfv = __longlong_as_double(0x7ff8000000000000ll);
         double *o = a.part + ((size_t)pp * a.C + c) * 3;
         o[0] = se;
@@ -503,8 +533,39 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
         for (int k = 0; k < 6; ++k) dv += a.tW[c * 6 + k] * a.tW[c * 6 + k];
       a.dpart[c * 3 + 0] = de;
       a.dpart[c * 3 + 1] = dv;
-      a.dpart[c * 3 + 2] = (mask & 4) ? red[9 * PT + 0] : 0.0;
+      a.dpart[c * 3 + 2] = (mask & 4) ? q[9] : 0.0;
     }
+  }
+}
+
+// Per call: FP32/FP64 constants of every parameter set and the target forces as R4 (x, y, z, |F|^2).
+template <typename R>
+__global__ void prep_kernel(int P, const double *__restrict__ params, R *__restrict__ consts,
+                            int64_t Ntot, const double *__restrict__ tF,
+                            typename Vec4<R>::T *__restrict__ tF4) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < P) {
+    const double *x = params + 6 * t;
+    const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
+    const double log2e = 1.4426950408889634;
+    R *o = consts + 8 * t;
+    o[0] = (R)D0;
+    o[1] = (R)(-al * log2e);
+    o[2] = (R)(al * r0 * log2e);
+    o[3] = (R)al;
+    o[4] = (R)be;
+    o[5] = (R)h;
+    o[6] = (R)n;
+    o[7] = (R)(-0.5 / n);
+  }
+  if (tF && t < Ntot) {
+    const double fx = tF[3 * t], fy = tF[3 * t + 1], fz = tF[3 * t + 2];
+    typename Vec4<R>::T v;
+    v.x = (R)fx;
+    v.y = (R)fy;
+    v.z = (R)fz;
+    v.w = (R)(fx * fx + fy * fy + fz * fz);
+    tF4[t] = v;
   }
 }
 

@@ -42,7 +42,7 @@ int build_plan(tersoff_ctx *ctx, int precision, int P) {
   if (plan.P == P && plan.precision == precision && !plan.buckets.empty()) return TERSOFF_OK;
   const int optin = tsf::batch_max_smem_optin();
   const size_t soft = std::min<size_t>((size_t)optin, 112 * 1024);  // two CTAs per SM
-  const int PT = 16;
+  const int PT = tsf::batch_param_tile();
   const int ntiles = (P + PT - 1) / PT;
   struct Key {
     int mmax, cl;
@@ -61,7 +61,7 @@ int build_plan(tersoff_ctx *ctx, int precision, int P) {
       for (int r = 0; r < cl; ++r) {
         const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
         const int nb = c.h_boff[s1] - c.h_boff[s0], nq = c.h_poff[s1] - c.h_poff[s0];
-        mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, cl > 1));
+        mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, s1 - s0, cl > 1));
       }
       const size_t lim = (cl >= 8) ? (size_t)optin : soft;
       if (mx <= lim) {
@@ -136,7 +136,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   cudaDeviceSynchronize();
   tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
-                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.part, &c.dpart, &c.work,
+                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.part, &c.dpart, &c.work, &c.tf4,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_Ui, &c.md_boxd};
@@ -294,10 +294,12 @@ int tersoff_eval(tersoff_ctx *ctx, const double *params, int32_t P, int32_t prec
   cudaSetDevice(c.device);
   int rc = build_plan(ctx, precision, P);
   if (rc) return rc;
+  TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
   tsf::BatchOut o = {};
   o.E = E;
   o.F = F;
   o.W = W;
+  o.consts = c.work.p;
   TSF_CUDA(tsf::launch_batch(c, precision == 64 ? c.plan64 : c.plan32, params, P, tsf::kModeEval, o, S(stream)));
   return TERSOFF_OK;
 }
@@ -317,7 +319,11 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   if (rc) return rc;
   TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
+  TSF_CUDA(c.tf4.ensure((size_t)c.Ntot * sizeof(tsf::dvec4)));
   tsf::BatchOut o = {};
+  o.consts = c.work.p;
+  o.tF4 = c.tf4.p;
   o.tE = tg->E;
   o.tW = tg->W;
   o.tF = tg->F;

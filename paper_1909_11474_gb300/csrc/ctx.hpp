@@ -97,7 +97,7 @@ struct Ctx {
   DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, cnt, nbr, shift, boff, poff, brev;
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
   BatchPlan plan32, plan64;
-  DevBuf part, dpart, work;
+  DevBuf part, dpart, work, tf4;
 
   // --- MD state ---
   int md_N = 0, md_M = 0;
@@ -132,6 +132,8 @@ struct BatchOut {
   const uint8_t *tmask;
   double *part;       // [P][C][3]
   double *dpart;      // [C][3]
+  void *consts;       // workspace: [P][8] per-parameter-set constants (working precision)
+  void *tF4;          // workspace: [Ntot] target forces as 4-vectors (working precision)
 };
 enum BatchMode { kModeEval = 0, kModeFitness = 1 };
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
@@ -139,7 +141,8 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
 cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
                                     double we, double wv, double wf, double *Z, double *Zq,
                                     double *S, cudaStream_t s);
-size_t batch_smem_bytes_pt(int precision, int nb, int nq, bool cluster);
+size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster);
+int batch_param_tile();
 int batch_max_smem_optin();
 
 }  // namespace tsf
