@@ -92,7 +92,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.status = ctx.status.as<unsigned>();
   for (const Bucket &b : plan.buckets) {
     if (b.nitems == 0) continue;
-    bp.items = plan.items.as<int2>() + b.item_off;
+    bp.recs = plan.items.as<CtaRec>() + b.item_off;
     cudaError_t e = cudaSuccess;
     const bool cl = b.cluster > 1;
     if (!f64) {

@@ -40,18 +40,17 @@ struct PConsts {
   R D0, k1, k0, alpha, beta, h, n, inv2n;
 };
 
-// b = (1 + zeta^n)^(-1/(2n)) and b' = db/dzeta = -1/2 b zeta^(n-1) / (1 + zeta^n)   (Eq. 6);
-// zeta = 0 gives b = 1, b' = 0 without evaluating 0^n.
+// b = (1 + zeta^n)^(-1/(2n)) and b' = db/dzeta = -1/2 b zeta^(n-1) / (1 + zeta^n)   (Eq. 6).
+// zeta is clamped to 1e-30 from below: at zeta = 0 this gives b = 1 to working precision, and b'
+// stays finite; it then only ever multiplies g or g' of the same (vanishing) pairs, so every
+// contribution of a zeta = 0 bond to the forces is exactly zero, as with b' = 0.
 template <typename R>
 __device__ __forceinline__ void bond_order(R zeta, const PConsts<R> &K, R &b, R &bp) {
-  const bool pos = zeta > R(0);
-  const R z = pos ? zeta : R(1);
+  const R z = zeta > R(1e-30) ? zeta : R(1e-30);
   const R zn = ex2(K.n * lg2(z));
   const R u = R(1) + zn;
-  const R bb = ex2(K.inv2n * lg2(u));
-  const R bbp = R(-0.5) * bb * zn * rcp(z * u);
-  b = pos ? bb : R(1);
-  bp = pos ? bbp : R(0);
+  b = ex2(K.inv2n * lg2(u));
+  bp = R(-0.5) * b * zn * rcp(z * u);
 }
 
 template <typename R>
@@ -83,10 +82,15 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
     }
   }
   constexpr int NP = M * (M - 1) / 2;
-  R cs[NP > 0 ? NP : 1];
+  constexpr int NP4 = (NP + 3) / 4;     // 16-byte (float) / 32-byte (double) pair-row vectors
+  R cs[NP4 > 0 ? 4 * NP4 : 4];
   if constexpr (EXACT) {
+    const typename Vec4<R>::T *c4 = reinterpret_cast<const typename Vec4<R>::T *>(sC + lq);
 #pragma unroll
-    for (int q = 0; q < NP; ++q) cs[q] = sC[lq + q];
+    for (int q = 0; q < NP4; ++q) {
+      const auto v = c4[q];
+      cs[4 * q] = v.x; cs[4 * q + 1] = v.y; cs[4 * q + 2] = v.z; cs[4 * q + 3] = v.w;
+    }
   } else {
     int q = 0;
 #pragma unroll
@@ -102,7 +106,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
 
   // ---- pass 1: pair functions (Eq. 4-5 with Eq. 11-14 at S = 2) and zeta (Eq. 7, 10)
-  R fR[M], fA[M], zeta[M];
+  R fR[M], fA[M], zeta[M], tq[NP > 0 ? NP : 1];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     const R x = ex2(r[j] * K.k1 + K.k0);
@@ -118,8 +122,9 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
 #pragma unroll
       for (int k = j + 1; k < M; ++k) {
         const R u = cs[q] - K.h;
-        const R t = K.beta * u;
+        const R t = K.beta * u;                     // g = t u, g' = 2 t
         const R g = t * u;
+        tq[q] = t;
         zeta[j] += fc[k] * g;
         zeta[k] += fc[j] * g;
         ++q;
@@ -151,10 +156,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
     for (int j = 0; j < M; ++j) {
 #pragma unroll
       for (int k = j + 1; k < M; ++k) {
-        const R u = cs[q] - K.h;
-        const R t = K.beta * u;
-        const R gp = t + t;                         // g' = 2 beta (cos - h)
-        const R w = (cc[j] * fc[k] + cc[k] * fc[j]) * gp;
+        const R w = (cc[j] * fc[k] + cc[k] * fc[j]) * tq[q];   // half of the w of the header
         Ax[j] += w * ux[k]; Ay[j] += w * uy[k]; Az[j] += w * uz[k];
         Ax[k] += w * ux[j]; Ay[k] += w * uy[j]; Az[k] += w * uz[j];
         const R wc = w * cs[q];
@@ -175,8 +177,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
     for (int j = 0; j < M; ++j) {
 #pragma unroll
       for (int k = j + 1; k < M; ++k) {
-        const R u = cs[q] - K.h;
-        const R g = K.beta * u * u;
+        const R g = tq[q] * (cs[q] - K.h);
         Rg[j] += cc[k] * g;
         Rg[k] += cc[j] * g;
         ++q;
@@ -186,10 +187,11 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   R W0 = R(0), W1 = R(0), W2 = R(0), W3 = R(0), W4 = R(0), W5 = R(0);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    const R coef = rad[j] + fcp[j] * Rg[j] - s[j] * ir[j];
-    const R Px = coef * ux[j] + ir[j] * Ax[j];
-    const R Py = coef * uy[j] + ir[j] * Ay[j];
-    const R Pz = coef * uz[j] + ir[j] * Az[j];
+    const R ir2 = ir[j] + ir[j];                   // 2/r restores the factor 2 of g' = 2 t
+    const R coef = rad[j] + fcp[j] * Rg[j] - s[j] * ir2;
+    const R Px = coef * ux[j] + ir2 * Ax[j];
+    const R Py = coef * uy[j] + ir2 * Ay[j];
+    const R Pz = coef * uz[j] + ir2 * Az[j];
     if (store && (EXACT || j < m)) {
       R *st = stage + (size_t)(lb + j) * 3 * PT + pl;
       st[0] = Px;
@@ -270,7 +272,7 @@ struct BatchParams {
   const void *consts;              // R [P][8]: PConsts of every parameter set
   const int *atom_off, *boff, *poff;
   const void *gA, *gB, *gcos;
-  const int2 *items;
+  const CtaRec *recs;
   int mode;
   double *E;
   void *F;
@@ -285,7 +287,7 @@ struct BatchParams {
 // Shared memory of one CTA (R = float or double, R4 its 4-vector):
 //   [region0: max(nb*3*PT, (kNW + (cluster ? 16 : 1)) * kNRed * PT) R]  stage of P_ij, later the
 //    per-warp partial sums and the CTA totals (one row per cluster rank)
-//   [sA: nb R4][sB: nb R4][sC: nq R][satom: natoms int4]
+//   [sA: nb R4][sB: nb R4][sC: nq R][satom: natoms int4][stF: natoms R4 (fitness only)]
 // region0 sits at offset 0 in every CTA, so a peer's stage is addressed by mapping this CTA's own
 // stage address to the peer rank.
 template <int PT, bool CLUSTER, typename R>
@@ -299,8 +301,9 @@ template <int PT, bool CLUSTER, typename R>
 __host__ __device__ inline size_t batch_smem(int nb, int nq, int nat) {
   using R4 = typename Vec4<R>::T;
   size_t b = region0_elems<PT, CLUSTER, R>(nb) * sizeof(R) + (size_t)nb * 2 * sizeof(R4);
-  b += ((size_t)nq * sizeof(R) + 15) / 16 * 16;
+  b += ((size_t)nq * sizeof(R) + 31) / 32 * 32;
   b += (size_t)nat * sizeof(int4);
+  b += (size_t)nat * sizeof(R4);
   return b;
 }
 
@@ -315,15 +318,13 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   const int slot = lane / PT, pl = lane % PT;
 
   unsigned rank = 0, ncta = 1;
-  int item_idx = blockIdx.x;
   if constexpr (CLUSTER) {
     rank = cluster_ctarank();
     ncta = cluster_nctarank();
-    item_idx = blockIdx.x / ncta;
   }
-  const int2 item = a.items[item_idx];
-  const int c = item.x;
-  const int p = item.y * PT + pl;
+  const CtaRec rec = a.recs[blockIdx.x];
+  const int c = rec.c;
+  const int p = rec.tile * PT + pl;
   const bool active = p < a.P;
   PConsts<R> K;
   {
@@ -334,22 +335,17 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   }
 
   // atom slice of this CTA
-  const int ca0 = a.atom_off[c], ca1 = a.atom_off[c + 1];
-  const int nat = ca1 - ca0;
-  const int per = (nat + (int)ncta - 1) / (int)ncta;
-  const int s0 = ca0 + min(nat, (int)rank * per);
-  const int s1 = ca0 + min(nat, ((int)rank + 1) * per);
-  const int cb0 = a.boff[ca0];           // first bond of the configuration
-  const int B0 = a.boff[s0], B1 = a.boff[s1];
-  const int Q0 = a.poff[s0], Q1 = a.poff[s1];
-  const int nb = B1 - B0, nq = Q1 - Q0, ns = s1 - s0;
+  const int nat = rec.nat, s0 = rec.s0, ns = rec.ns, cb0 = rec.cb0;
+  const int B0 = rec.B0, nb = rec.nb, Q0 = rec.Q0, nq = rec.nq;
   R4 *sA = reinterpret_cast<R4 *>(stage + region0_elems<PT, CLUSTER, R>(nb));
   R4 *sB = sA + nb;
   R *sC = reinterpret_cast<R *>(sB + nb);
   int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) +
-                                         ((size_t)nq * sizeof(R) + 15) / 16 * 16);
+                                         ((size_t)nq * sizeof(R) + 31) / 32 * 32);
+  R4 *stF = reinterpret_cast<R4 *>(satom + ns);
+  const bool fit = a.mode == kModeFitness;
 
-  // stage this slice's geometry and atom table in shared memory
+  // stage this slice's geometry, atom table and target forces in shared memory
   {
     const R4 *gA = reinterpret_cast<const R4 *>(a.gA) + B0;
     const R4 *gB = reinterpret_cast<const R4 *>(a.gB) + B0;
@@ -362,6 +358,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     for (int t = tid; t < ns; t += kThreads) {
       const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
       satom[t] = make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0);
+      if (fit) stF[t] = reinterpret_cast<const R4 *>(a.tF4)[s0 + t];
     }
   }
   __syncthreads();
@@ -401,16 +398,16 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
 
   // ---- pass 3: F_i = sum_j (P_ij - P_ji)
   R sf = R(0), sF2 = R(0), sT = R(0);
-  const uint8_t mask = (a.mode == kModeFitness) ? a.tmask[c] : 0;
+  const uint8_t mask = fit ? a.tmask[c] : 0;
   unsigned peer_stage[kMaxCluster];
   int peer_b0[kMaxCluster + 1];
   if constexpr (CLUSTER) {
     const unsigned own = smem_addr(stage);
     for (unsigned r = 0; r < ncta; ++r) {
       peer_stage[r] = map_to_rank(own, r);
-      peer_b0[r] = a.boff[ca0 + min(nat, (int)r * per)] - cb0;
+      peer_b0[r] = a.recs[rec.rec0 + r].B0 - cb0;
     }
-    peer_b0[ncta] = a.boff[ca1] - cb0;
+    peer_b0[ncta] = a.recs[rec.rec0 + ncta - 1].B0 + a.recs[rec.rec0 + ncta - 1].nb - cb0;
   }
   for (int base = warp * APW; base < ns; base += kNW * APW) {
     const int li = base + slot;
@@ -451,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
         F[o + 2] = Fz;
       }
     } else if (mask & 4) {
-      const R4 t = reinterpret_cast<const R4 *>(a.tF4)[i];
+      const R4 t = stF[li];
       const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
       sf += ex * ex + ey * ey + ez * ez;
       sT += t.w;
@@ -491,7 +488,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   }
 
   if (tid < PT) {
-    const int pp = item.y * PT + tid;
+    const int pp = rec.tile * PT + tid;
     double q[kNRed];
 #pragma unroll
     for (int k = 0; k < kNRed; ++k) {
@@ -526,7 +523,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
         o[2] = sfv;
       }
     }
-    if (a.mode == kModeFitness && item.y == 0 && tid == 0) {
+    if (fit && rec.tile == 0 && tid == 0) {
       double de = 0.0, dv = 0.0;
       if (mask & 1) de = a.tE[c] * a.tE[c];
       if (mask & 2)

@@ -76,7 +76,7 @@ int build_plan(tersoff_ctx *ctx, int precision, int P) {
     groups[k].push_back(cf);
     smem[k] = std::max(smem[k], need);
   }
-  std::vector<int2> items;
+  std::vector<tsf::CtaRec> recs;
   plan.buckets.clear();
   // largest clusters (longest items) first so that they start early
   std::vector<Key> keys;
@@ -95,14 +95,36 @@ int build_plan(tersoff_ctx *ctx, int precision, int P) {
     b.cluster = k.cl;
     b.precision = precision;
     b.smem = smem[k];
-    b.item_off = (int)items.size();
-    for (int cf : cfgs)
-      for (int t = 0; t < ntiles; ++t) items.push_back(make_int2(cf, t));
-    b.nitems = (int)items.size() - b.item_off;
+    b.item_off = (int)recs.size();
+    for (int cf : cfgs) {
+      const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
+      const int per = (nat + k.cl - 1) / k.cl;
+      for (int t = 0; t < ntiles; ++t) {
+        const int rec0 = (int)recs.size();
+        for (int r = 0; r < k.cl; ++r) {
+          const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
+          tsf::CtaRec q;
+          q.c = cf;
+          q.tile = t;
+          q.s0 = s0;
+          q.ns = s1 - s0;
+          q.B0 = c.h_boff[s0];
+          q.nb = c.h_boff[s1] - c.h_boff[s0];
+          q.Q0 = c.h_poff[s0];
+          q.nq = c.h_poff[s1] - c.h_poff[s0];
+          q.cb0 = c.h_boff[a0];
+          q.nat = nat;
+          q.rec0 = rec0;
+          q.pad = 0;
+          recs.push_back(q);
+        }
+      }
+    }
+    b.nitems = ((int)recs.size() - b.item_off) / k.cl;
     plan.buckets.push_back(b);
   }
-  TSF_CUDA(plan.items.ensure(std::max<size_t>(1, items.size()) * sizeof(int2)));
-  TSF_CUDA(cudaMemcpy(plan.items.p, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  TSF_CUDA(plan.items.ensure(std::max<size_t>(1, recs.size()) * sizeof(tsf::CtaRec)));
+  TSF_CUDA(cudaMemcpy(plan.items.p, recs.data(), recs.size() * sizeof(tsf::CtaRec), cudaMemcpyHostToDevice));
   plan.P = P;
   plan.precision = precision;
   return TERSOFF_OK;
@@ -223,7 +245,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   for (int64_t i = 0; i < N; ++i) {
     const int m = c.h_cnt[i];
     c.h_boff[i + 1] = c.h_boff[i] + m;
-    c.h_poff[i + 1] = c.h_poff[i] + m * (m - 1) / 2;
+    c.h_poff[i + 1] = c.h_poff[i] + tsf::pair_slots(m);
     maxm = std::max(maxm, m);
     int &cm = c.h_cfg_maxm[cfgidx[i]];
     cm = std::max(cm, m);

@@ -59,11 +59,18 @@ struct Geometry {
   const void *gcos;     // [Qtot] R: cos theta of pair (e, f), e < f, row-major over e
 };
 
-// One work item of the batched evaluation: configuration c, parameter tile t (P-tile of PT sets).
-struct WorkItem {
-  int c;
-  int tile;
+// What one CTA of the batched evaluation works on: atoms s0 .. s0+ns-1 of configuration c (its
+// slice when the configuration spans a cluster), bonds B0 .. B0+nb-1, padded pair slots
+// Q0 .. Q0+nq-1, parameter tile `tile`; cb0 = first bond and nat = atom count of the configuration;
+// rec0 = the record of cluster rank 0 of the same work item.
+struct __align__(16) CtaRec {
+  int c, tile, s0, ns;
+  int B0, nb, Q0, nq;
+  int cb0, nat, rec0, pad;
 };
+
+// Pair slots per atom: m(m-1)/2 cosines padded to a multiple of 4 (16-byte vector loads).
+__host__ __device__ inline int pair_slots(int m) { return ((m * (m - 1) / 2) + 3) & ~3; }
 
 // A launch bucket: items with the same kernel variant.
 struct Bucket {
@@ -79,7 +86,7 @@ struct BatchPlan {
   int precision = 0;
   int P = 0;
   std::vector<Bucket> buckets;
-  DevBuf items;    // int2 [total items]
+  DevBuf items;    // CtaRec [total CTAs]
 };
 
 struct Ctx {

@@ -177,7 +177,7 @@ __device__ __forceinline__ void cutoff_fc(double r, double R1, double R2, double
 
 // Per bond: unit vector, r, 1/r, f_C, f_C' and the configuration-local index of the reverse bond
 // (stored in the 4th slot: as a double, or as the bit pattern of an int in the FP32 record);
-// per unordered pair (e < f) of an atom's bonds: cos theta. Computed in FP64 from the same d as the
+// per unordered pair (e < f) of an atom's bonds: cos theta (each atom's row padded to 4 slots). Computed in FP64 from the same d as the
 // membership test, stored in FP64 and rounded to FP32.
 __global__ void geometry_kernel(int64_t Ntot, int M, const int *__restrict__ atom_cfg,
                                 const int *__restrict__ atom_off, const int *__restrict__ brev,
@@ -222,6 +222,10 @@ __global__ void geometry_kernel(int64_t Ntot, int M, const int *__restrict__ ato
       gcos32[q] = (float)cs;
       ++q;
     }
+  }
+  for (; q < poff[i + 1]; ++q) {   // padding slots of the 16-byte aligned pair rows
+    gcos64[q] = 0.0;
+    gcos32[q] = 0.f;
   }
 }
 
