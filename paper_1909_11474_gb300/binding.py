@@ -13,7 +13,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libtersoff_gb300.so")
+# TSF_DEBUG_BOUNDS=1 selects the bounds-checked debug build of the library
+LIB_PATH = os.path.join(_HERE, "libtersoff_gb300_debug.so" if os.environ.get("TSF_DEBUG_BOUNDS") == "1"
+                        else "libtersoff_gb300.so")
 
 OK, E_ARG, E_NBR_OVERFLOW, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, E_UNSUPPORTED = range(8)
 STATUS_NBR_OVERFLOW, STATUS_MANY_NBRS, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4, 8
@@ -73,6 +75,8 @@ def load():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
+    lib.tersoff_debug_bounds.restype = ctypes.c_int
+    lib.tersoff_debug_bounds.argtypes = [_vp]
     _lib = lib
     return lib
 
@@ -139,6 +143,12 @@ class Context:
     # ---- calls ---------------------------------------------------------------------------------
     def get_status(self, stream=None) -> int:
         return int(self.lib.tersoff_get_status(self.h, _stream(stream)))
+
+    def debug_bounds(self):
+        """First shared-memory bounds violation recorded by a TSF_DEBUG_BOUNDS build (zeros if none)."""
+        out = np.zeros(4, np.uint32)
+        self.lib.tersoff_debug_bounds(out.ctypes.data)
+        return out
 
     def build_neighbors(self, atom_off, pos: torch.Tensor, box: torch.Tensor, R1: float = 2.8,
                         R2: float = 3.2, max_nbr: int = 16, stream=None):

@@ -158,3 +158,17 @@ cudaError_t launch_fitness_finalize(int P, int C, const double *part, const doub
 }
 
 }  // namespace tsf
+
+// Debug builds (TSF_DEBUG_BOUNDS): the first out-of-range or misaligned shared-memory access of the
+// batched kernel, as {flag, site, byte offset, window size}; zeros otherwise. Clears the record.
+extern "C" int tersoff_debug_bounds(unsigned *out4) {
+#ifdef TSF_DEBUG_BOUNDS
+  cudaError_t e = cudaMemcpyFromSymbol(out4, tsf::tsf_dbg, 4 * sizeof(unsigned));
+  unsigned z[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(tsf::tsf_dbg, z, sizeof(z));
+  return e == cudaSuccess ? 0 : 3;
+#else
+  for (int k = 0; k < 4; ++k) out4[k] = 0;
+  return 0;
+#endif
+}

@@ -33,6 +33,44 @@ constexpr int kThreads = kNW * kWarp;
 constexpr int kNRed = 10;        // reduced quantities: U, W[6], S_f, sum|F|^2, sum|F*|^2
 constexpr int kMaxCluster = 16;
 
+// ---- checked shared-memory access (TSF_DEBUG_BOUNDS builds) ----
+// In a debug build every shared-memory access of the batched kernel checks that it lies inside the
+// dynamic shared-memory window and is aligned for its type; a violation records (site, byte offset,
+// window size) in tsf_dbg, the first one only, and the access is skipped (loads return zero).
+// Release builds compile these helpers to plain accesses.
+#ifdef TSF_DEBUG_BOUNDS
+static __device__ unsigned tsf_dbg[4];
+#endif
+template <typename T>
+__device__ __forceinline__ bool smem_ok(const T *p, int site) {
+#ifdef TSF_DEBUG_BOUNDS
+  extern __shared__ __align__(32) unsigned char smem[];
+  unsigned dsz;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsz));
+  const long off = reinterpret_cast<const unsigned char *>(p) - smem;
+  const bool ok = off >= 0 && off + (long)sizeof(T) <= (long)dsz && (off % (long)alignof(T)) == 0;
+  if (!ok && atomicCAS(&tsf_dbg[0], 0u, 1u) == 0u) {
+    tsf_dbg[1] = (unsigned)site;
+    tsf_dbg[2] = (unsigned)off;
+    tsf_dbg[3] = dsz;
+  }
+  return ok;
+#else
+  (void)p;
+  (void)site;
+  return true;
+#endif
+}
+template <typename T>
+__device__ __forceinline__ T sld(const T *p, int site) {
+  if (smem_ok(p, site)) return *p;
+  return T{};
+}
+template <typename T>
+__device__ __forceinline__ void sst(T *p, const T &v, int site) {
+  if (smem_ok(p, site)) *p = v;
+}
+
 // Per-parameter-set constants (prepared once per call by prep_kernel from the FP64 parameters):
 // x = exp(-alpha (r - r0)) = 2^(k1 r + k0), f_R = D0 x^2, f_A = 2 D0 x (Eq. 4-5, 11-14 at S = 2).
 template <typename R>
@@ -72,8 +110,8 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     if (EXACT || j < m) {
-      const auto A = sA[lb + j];
-      const auto B = sB[lb + j];
+      const auto A = sld(&sA[lb + j], 1);
+      const auto B = sld(&sB[lb + j], 2);
       ux[j] = A.x; uy[j] = A.y; uz[j] = A.z; r[j] = A.w;
       ir[j] = B.x; fc[j] = B.y; fcp[j] = B.z;
     } else {
@@ -88,7 +126,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
     const typename Vec4<R>::T *c4 = reinterpret_cast<const typename Vec4<R>::T *>(sC + lq);
 #pragma unroll
     for (int q = 0; q < NP4; ++q) {
-      const auto v = c4[q];
+      const auto v = sld(&c4[q], 3);
       cs[4 * q] = v.x; cs[4 * q + 1] = v.y; cs[4 * q + 2] = v.z; cs[4 * q + 3] = v.w;
     }
   } else {
@@ -99,7 +137,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
 #pragma unroll
       for (int k = j + 1; k < M; ++k) {
         cs[q] = R(0);
-        if (k < m) cs[q] = sC[rowbase + k];
+        if (k < m) cs[q] = sld(&sC[rowbase + k], 4);
         ++q;
       }
     }
@@ -194,9 +232,9 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
     const R Pz = coef * uz[j] + ir2 * Az[j];
     if (store && (EXACT || j < m)) {
       R *st = stage + (size_t)(lb + j) * 3 * PT + pl;
-      st[0] = Px;
-      st[PT] = Py;
-      st[2 * PT] = Pz;
+      sst(&st[0], Px, 5);
+      sst(&st[PT], Py, 5);
+      sst(&st[2 * PT], Pz, 5);
     }
     const R dx = r[j] * ux[j], dy = r[j] * uy[j], dz = r[j] * uz[j];
     W0 -= dx * Px; W1 -= dy * Py; W2 -= dz * Pz;
@@ -351,14 +389,14 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     const R4 *gB = reinterpret_cast<const R4 *>(a.gB) + B0;
     const R *gC = reinterpret_cast<const R *>(a.gcos) + Q0;
     for (int t = tid; t < nb; t += kThreads) {
-      sA[t] = gA[t];
-      sB[t] = gB[t];
+      sst(&sA[t], gA[t], 6);
+      sst(&sB[t], gB[t], 7);
     }
-    for (int t = tid; t < nq; t += kThreads) sC[t] = gC[t];
+    for (int t = tid; t < nq; t += kThreads) sst(&sC[t], gC[t], 8);
     for (int t = tid; t < ns; t += kThreads) {
       const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
-      satom[t] = make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0);
-      if (fit) stF[t] = reinterpret_cast<const R4 *>(a.tF4)[s0 + t];
+      sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0), 9);
+      if (fit) sst(&stF[t], reinterpret_cast<const R4 *>(a.tF4)[s0 + t], 10);
     }
   }
   __syncthreads();
@@ -373,7 +411,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     const int li = base + slot;
     const bool valid = li < ns;
     int4 at = make_int4(0, 0, 0, 0);
-    if (valid) at = satom[li];
+    if (valid) at = sld(&satom[li], 11);
     const int m = at.z;
     if constexpr (APW == 1) {
       if (m > MMAX) {
@@ -412,29 +450,39 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   for (int base = warp * APW; base < ns; base += kNW * APW) {
     const int li = base + slot;
     if (li >= ns) continue;
-    const int4 at = satom[li];
+    const int4 at = sld(&satom[li], 12);
     const int m = at.z, lb = at.x;
     R Fx = R(0), Fy = R(0), Fz = R(0);
     for (int e = 0; e < m; ++e) {
       const R *st = stage + (size_t)(lb + e) * 3 * PT + pl;
-      Fx += st[0];
-      Fy += st[PT];
-      Fz += st[2 * PT];
+      Fx += sld(&st[0], 13);
+      Fy += sld(&st[PT], 13);
+      Fz += sld(&st[2 * PT], 13);
       int rb;  // configuration-local bond index of the reverse entry
-      if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sB[lb + e].w);
-      else rb = (int)sB[lb + e].w;
+      if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sld(&sB[lb + e].w, 14));
+      else rb = (int)sld(&sB[lb + e].w, 14);
       if constexpr (CLUSTER) {
         unsigned r = 0;
         while (r + 1 < ncta && rb >= peer_b0[r + 1]) ++r;
+#ifdef TSF_DEBUG_BOUNDS
+        if (rb < peer_b0[r] || rb >= peer_b0[r + 1]) {
+          if (atomicCAS(&tsf_dbg[0], 0u, 1u) == 0u) {
+            tsf_dbg[1] = 21;
+            tsf_dbg[2] = (unsigned)rb;
+            tsf_dbg[3] = (unsigned)peer_b0[ncta];
+          }
+          continue;
+        }
+#endif
         const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * 3 * PT + pl) * sizeof(R));
         Fx -= ld_cluster(addr, R(0));
         Fy -= ld_cluster(addr + PT * sizeof(R), R(0));
         Fz -= ld_cluster(addr + 2 * PT * sizeof(R), R(0));
       } else {
         const R *sr = stage + (size_t)(rb + cb0 - B0) * 3 * PT + pl;
-        Fx -= sr[0];
-        Fy -= sr[PT];
-        Fz -= sr[2 * PT];
+        Fx -= sld(&sr[0], 15);
+        Fy -= sld(&sr[PT], 15);
+        Fz -= sld(&sr[2 * PT], 15);
       }
     }
     sF2 += Fx * Fx + Fy * Fy + Fz * Fz;
@@ -448,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
         F[o + 2] = Fz;
       }
     } else if (mask & 4) {
-      const R4 t = stF[li];
+      const R4 t = sld(&stF[li], 16);
       const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
       sf += ex * ex + ey * ey + ez * ez;
       sT += t.w;
@@ -470,15 +518,15 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   R *tot = stage + kNW * kNRed * PT;                // [kMaxCluster][kNRed][PT] (rank 0 collects)
   if (slot == 0) {
 #pragma unroll
-    for (int k = 0; k < kNRed; ++k) red[(warp * kNRed + k) * PT + pl] = v[k];
+    for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PT + pl], v[k], 17);
   }
   __syncthreads();
   for (int idx = tid; idx < kNRed * PT; idx += kThreads) {
     R t = R(0);
 #pragma unroll
-    for (int w = 0; w < kNW; ++w) t += red[w * kNRed * PT + idx];
+    for (int w = 0; w < kNW; ++w) t += sld(&red[w * kNRed * PT + idx], 18);
     if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(tot + rank * kNRed * PT + idx), 0), t);
-    else tot[idx] = t;
+    else sst(&tot[idx], t, 19);
   }
   if constexpr (CLUSTER) {
     cluster_sync_all();
@@ -493,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
 #pragma unroll
     for (int k = 0; k < kNRed; ++k) {
       double s = 0.0;
-      for (unsigned r = 0; r < ncta; ++r) s += (double)tot[(r * kNRed + k) * PT + tid];
+      for (unsigned r = 0; r < ncta; ++r) s += (double)sld(&tot[(r * kNRed + k) * PT + tid], 20);
       q[k] = s;
     }
     if (pp < a.P) {
