@@ -464,16 +464,19 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
       if constexpr (CLUSTER) {
         unsigned r = 0;
         while (r + 1 < ncta && rb >= peer_b0[r + 1]) ++r;
-#ifdef TSF_DEBUG_BOUNDS
+        // a reverse bond outside the configuration's bond range is an inconsistent schedule: flag it
+        // and skip the peer read rather than touch another CTA's shared memory out of range
         if (rb < peer_b0[r] || rb >= peer_b0[r + 1]) {
+          set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
+#ifdef TSF_DEBUG_BOUNDS
           if (atomicCAS(&tsf_dbg[0], 0u, 1u) == 0u) {
             tsf_dbg[1] = 21;
             tsf_dbg[2] = (unsigned)rb;
             tsf_dbg[3] = (unsigned)peer_b0[ncta];
           }
+#endif
           continue;
         }
-#endif
         const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * 3 * PT + pl) * sizeof(R));
         Fx -= ld_cluster(addr, R(0));
         Fy -= ld_cluster(addr + PT * sizeof(R), R(0));

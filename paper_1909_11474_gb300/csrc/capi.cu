@@ -100,7 +100,7 @@ int build_plan(tersoff_ctx *ctx, int precision, int P) {
       const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
       const int per = (nat + k.cl - 1) / k.cl;
       for (int t = 0; t < ntiles; ++t) {
-        const int rec0 = (int)recs.size();
+        const int rec0 = (int)recs.size() - b.item_off;   // relative to the bucket's first record
         for (int r = 0; r < k.cl; ++r) {
           const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
           tsf::CtaRec q;

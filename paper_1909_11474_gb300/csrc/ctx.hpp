@@ -62,7 +62,7 @@ struct Geometry {
 // What one CTA of the batched evaluation works on: atoms s0 .. s0+ns-1 of configuration c (its
 // slice when the configuration spans a cluster), bonds B0 .. B0+nb-1, padded pair slots
 // Q0 .. Q0+nq-1, parameter tile `tile`; cb0 = first bond and nat = atom count of the configuration;
-// rec0 = the record of cluster rank 0 of the same work item.
+// rec0 = the record of cluster rank 0 of the same work item, counted from the launch's first record.
 struct __align__(16) CtaRec {
   int c, tile, s0, ns;
   int B0, nb, Q0, nq;
