@@ -32,7 +32,7 @@ static cudaError_t launch_variant(const BatchParams &bp, int nitems, int cluster
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nitems * (CLUSTER ? cluster : 1)));
+  cfg.gridDim = dim3((unsigned)(nitems * bp.ntiles * (CLUSTER ? cluster : 1)));
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
@@ -79,6 +79,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.gA = f64 ? ctx.gA64.p : ctx.gA32.p;
   bp.gB = f64 ? ctx.gB64.p : ctx.gB32.p;
   bp.gcos = f64 ? ctx.gcos64.p : ctx.gcos32.p;
+  bp.ntiles = (P + kPT - 1) / kPT;
   bp.mode = mode;
   bp.E = out.E;
   bp.F = out.F;

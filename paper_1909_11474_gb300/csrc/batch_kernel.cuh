@@ -311,6 +311,7 @@ struct BatchParams {
   const int *atom_off, *boff, *poff;
   const void *gA, *gB, *gcos;
   const CtaRec *recs;
+  int ntiles;                      // parameter tiles: ceil(P / PT)
   int mode;
   double *E;
   void *F;
@@ -360,9 +361,13 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     rank = cluster_ctarank();
     ncta = cluster_nctarank();
   }
-  const CtaRec rec = a.recs[blockIdx.x];
+  // blockIdx.x = ((configuration in bucket) * ntiles + tile) * ncta + rank
+  const int item = blockIdx.x / ncta;
+  const int tile = item % a.ntiles;
+  const int rec0 = (item / a.ntiles) * ncta;
+  const CtaRec rec = a.recs[rec0 + rank];
   const int c = rec.c;
-  const int p = rec.tile * PT + pl;
+  const int p = tile * PT + pl;
   const bool active = p < a.P;
   PConsts<R> K;
   {
@@ -443,9 +448,9 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     const unsigned own = smem_addr(stage);
     for (unsigned r = 0; r < ncta; ++r) {
       peer_stage[r] = map_to_rank(own, r);
-      peer_b0[r] = a.recs[rec.rec0 + r].B0 - cb0;
+      peer_b0[r] = a.recs[rec0 + r].B0 - cb0;
     }
-    peer_b0[ncta] = a.recs[rec.rec0 + ncta - 1].B0 + a.recs[rec.rec0 + ncta - 1].nb - cb0;
+    peer_b0[ncta] = a.recs[rec0 + ncta - 1].B0 + a.recs[rec0 + ncta - 1].nb - cb0;
   }
   for (int base = warp * APW; base < ns; base += kNW * APW) {
     const int li = base + slot;
@@ -539,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   }
 
   if (tid < PT) {
-    const int pp = rec.tile * PT + tid;
+    const int pp = tile * PT + tid;
     double q[kNRed];
 #pragma unroll
     for (int k = 0; k < kNRed; ++k) {
@@ -574,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
         o[2] = sfv;
       }
     }
-    if (fit && rec.tile == 0 && tid == 0) {
+    if (fit && tile == 0 && tid == 0) {
       double de = 0.0, dv = 0.0;
       if (mask & 1) de = a.tE[c] * a.tE[c];
       if (mask & 2)

@@ -11,10 +11,6 @@
 
 using tsf::Ctx;
 
-struct tersoff_ctx {
-  Ctx c;
-};
-
 namespace {
 
 int fail(tersoff_ctx *ctx, int code, const char *fmt, const char *detail = "") {
@@ -34,16 +30,15 @@ int fail(tersoff_ctx *ctx, int code, const char *fmt, const char *detail = "") {
 
 inline cudaStream_t S(tersoff_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
-// The cluster size and kernel variant of every configuration, and the work items of one launch per
-// (variant, cluster size), longest configurations first.
-int build_plan(tersoff_ctx *ctx, int precision, int P) {
+// The cluster size and kernel variant of every configuration for one precision, and one record per
+// (configuration, cluster rank) of every launch bucket, longest configurations first. The plan does
+// not depend on the number of parameter sets: a launch covers nconf x ntiles x cluster CTAs.
+int build_plan(tersoff_ctx *ctx, int precision) {
   Ctx &c = ctx->c;
   tsf::BatchPlan &plan = precision == 64 ? c.plan64 : c.plan32;
-  if (plan.P == P && plan.precision == precision && !plan.buckets.empty()) return TERSOFF_OK;
+  if (plan.precision == precision && !plan.buckets.empty()) return TERSOFF_OK;
   const int optin = tsf::batch_max_smem_optin();
   const size_t soft = std::min<size_t>((size_t)optin, 112 * 1024);  // two CTAs per SM
-  const int PT = tsf::batch_param_tile();
-  const int ntiles = (P + PT - 1) / PT;
   struct Key {
     int mmax, cl;
     bool operator<(const Key &o) const { return mmax != o.mmax ? mmax < o.mmax : cl < o.cl; }
@@ -99,33 +94,29 @@ int build_plan(tersoff_ctx *ctx, int precision, int P) {
     for (int cf : cfgs) {
       const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
       const int per = (nat + k.cl - 1) / k.cl;
-      for (int t = 0; t < ntiles; ++t) {
-        const int rec0 = (int)recs.size() - b.item_off;   // relative to the bucket's first record
-        for (int r = 0; r < k.cl; ++r) {
-          const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
-          tsf::CtaRec q;
-          q.c = cf;
-          q.tile = t;
-          q.s0 = s0;
-          q.ns = s1 - s0;
-          q.B0 = c.h_boff[s0];
-          q.nb = c.h_boff[s1] - c.h_boff[s0];
-          q.Q0 = c.h_poff[s0];
-          q.nq = c.h_poff[s1] - c.h_poff[s0];
-          q.cb0 = c.h_boff[a0];
-          q.nat = nat;
-          q.rec0 = rec0;
-          q.pad = 0;
-          recs.push_back(q);
-        }
+      for (int r = 0; r < k.cl; ++r) {
+        const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
+        tsf::CtaRec q;
+        q.c = cf;
+        q.tile = 0;
+        q.s0 = s0;
+        q.ns = s1 - s0;
+        q.B0 = c.h_boff[s0];
+        q.nb = c.h_boff[s1] - c.h_boff[s0];
+        q.Q0 = c.h_poff[s0];
+        q.nq = c.h_poff[s1] - c.h_poff[s0];
+        q.cb0 = c.h_boff[a0];
+        q.nat = nat;
+        q.rec0 = 0;
+        q.pad = 0;
+        recs.push_back(q);
       }
     }
-    b.nitems = ((int)recs.size() - b.item_off) / k.cl;
+    b.nitems = ((int)recs.size() - b.item_off) / k.cl;   // configurations in the bucket
     plan.buckets.push_back(b);
   }
   TSF_CUDA(plan.items.ensure(std::max<size_t>(1, recs.size()) * sizeof(tsf::CtaRec)));
   TSF_CUDA(cudaMemcpy(plan.items.p, recs.data(), recs.size() * sizeof(tsf::CtaRec), cudaMemcpyHostToDevice));
-  plan.P = P;
   plan.precision = precision;
   return TERSOFF_OK;
 }
@@ -273,6 +264,12 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(cudaMemcpyAsync(&hst, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   TSF_CUDA(cudaStreamSynchronize(s));
   if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "reverse neighbour entry missing%s");
+  if (c.max_m <= 8) {
+    int rc = build_plan(ctx, 32);
+    if (rc) return rc;
+    rc = build_plan(ctx, 64);
+    if (rc) return rc;
+  }
   c.built = true;
   return TERSOFF_OK;
 }
@@ -314,7 +311,7 @@ int tersoff_eval(tersoff_ctx *ctx, const double *params, int32_t P, int32_t prec
   if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
   if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
   cudaSetDevice(c.device);
-  int rc = build_plan(ctx, precision, P);
+  int rc = build_plan(ctx, precision);
   if (rc) return rc;
   TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
   tsf::BatchOut o = {};
@@ -337,7 +334,7 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
   if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
   cudaSetDevice(c.device);
-  int rc = build_plan(ctx, precision, P);
+  int rc = build_plan(ctx, precision);
   if (rc) return rc;
   TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));

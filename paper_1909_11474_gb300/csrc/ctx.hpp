@@ -59,10 +59,10 @@ struct Geometry {
   const void *gcos;     // [Qtot] R: cos theta of pair (e, f), e < f, row-major over e
 };
 
-// What one CTA of the batched evaluation works on: atoms s0 .. s0+ns-1 of configuration c (its
-// slice when the configuration spans a cluster), bonds B0 .. B0+nb-1, padded pair slots
-// Q0 .. Q0+nq-1, parameter tile `tile`; cb0 = first bond and nat = atom count of the configuration;
-// rec0 = the record of cluster rank 0 of the same work item, counted from the launch's first record.
+// What one cluster rank of the batched evaluation works on, for every parameter tile: atoms
+// s0 .. s0+ns-1 of configuration c (its slice when the configuration spans a cluster), bonds
+// B0 .. B0+nb-1, padded pair slots Q0 .. Q0+nq-1; cb0 = first bond and nat = atom count of the
+// configuration. tile and rec0 are unused (kept for the 16-byte record layout).
 struct __align__(16) CtaRec {
   int c, tile, s0, ns;
   int B0, nb, Q0, nq;
@@ -78,13 +78,12 @@ struct Bucket {
   int cluster;     // CTAs per configuration (1 = no cluster)
   int precision;   // 32 or 64
   size_t smem;     // dynamic shared memory per CTA
-  int nitems;
-  int item_off;    // offset into the device item array
+  int nitems;      // configurations in the bucket
+  int item_off;    // first record of the bucket (records are per configuration and cluster rank)
 };
 
 struct BatchPlan {
   int precision = 0;
-  int P = 0;
   std::vector<Bucket> buckets;
   DevBuf items;    // CtaRec [total CTAs]
 };
@@ -153,3 +152,8 @@ int batch_param_tile();
 int batch_max_smem_optin();
 
 }  // namespace tsf
+
+// The opaque handle of the C ABI.
+struct tersoff_ctx {
+  tsf::Ctx c;
+};
