@@ -137,6 +137,26 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
                     const double *w, int32_t precision, double *Z, double *Zq, double *S,
                     tersoff_stream stream);
 
+/* tersoff_fitness without device allocation. The paper has no counterpart; this entry point exists
+ * for callers that cannot let a library call cudaMalloc: cudaMalloc stalls the whole device until it
+ * returns, which a caller that keeps other streams busy or runs one generation after another cannot
+ * afford, and a caller whose device memory was reserved up front by another allocator (a framework's
+ * caching allocator, say) may have none left to give. The context's neighbour build and work
+ * schedule are made by tersoff_build_neighbors, which does allocate; this call then uses only those
+ * and one fixed 8 MiB scratch array in device memory that every device loading the library keeps
+ * until the process exits.
+ *  Arguments, results and arithmetic are those of tersoff_fitness, and so are the results.
+ *  Limit: P*8*8 + Ntot*32 + P*C*24 + C*24 bytes (each part rounded up to 256) must fit in 8 MiB, e.g.
+ *  P = 200 parameter sets over C = 300 cells of 64 atoms needs 2.1 MB; a larger request returns
+ *  TERSOFF_E_ARG with the byte count in tersoff_last_error and launches nothing.
+ *  The first call on a device looks up the scratch array's device address (once per device); make
+ *  that first call before any stream capture. Every call shares the one array and leaves its
+ *  contents behind; nothing in it needs to start at zero. Two calls whose work overlaps on the GPU
+ *  (different streams, or different contexts on the same device) race on the array: serialise them. */
+int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, int32_t P,
+                           const tersoff_targets *tg, const double *w, int32_t precision, double *Z,
+                           double *Zq, double *S, tersoff_stream stream);
+
 /* Loss and its gradient with respect to x = [D0, alpha, r0, beta, n, h] for every parameter set.
  *  loss TERSOFF_LOSS_SQ or TERSOFF_LOSS_Z (the latter has a zero gradient term where S_q = 0);
  *  L device [P] double; dL device [P][6] double. FP32 per-pair arithmetic with FP64 accumulation of

@@ -25,7 +25,7 @@ EXPORTED = (
     "tersoff_create", "tersoff_destroy", "tersoff_last_error", "tersoff_get_status",
     "tersoff_build_neighbors", "tersoff_export_neighbors", "tersoff_build_info", "tersoff_eval",
     "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
-    "tersoff_md_export_neighbors",
+    "tersoff_md_export_neighbors", "tersoff_fitness_static",
 )
 
 _vp = ctypes.c_void_p
@@ -70,6 +70,8 @@ def load():
         "tersoff_md_force": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _f64, _f64, _i32, _i32,
                                             _vp, _vp, _vp, _vp]),
         "tersoff_md_export_neighbors": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "tersoff_fitness_static": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _vp, _i32,
+                                                  _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -213,6 +215,31 @@ class Context:
         wv = (ctypes.c_double * 3)(*[float(x) for x in w])
         self._check(self.lib.tersoff_fitness(self.h, params.data_ptr(), P, ctypes.byref(t), ctypes.addressof(wv),
                                              precision, Z.data_ptr(), _ptr(Zq), _ptr(S), _stream(stream)))
+        return Z, Zq, S
+
+    def fitness_static(self, params: torch.Tensor, targets: dict, w=(1.0, 1.0, 1.0), precision: int = 32,
+                       stream=None, out=None):
+        """tersoff_fitness_static: the fitness of `fitness` without any device allocation in the call.
+
+        For callers that cannot have the library call cudaMalloc (it stalls the device; or their
+        memory is already reserved by another allocator). The output tensors here come from the
+        caller (`out`) or from PyTorch's allocator in this wrapper, never from the library; the
+        library's per-call scratch is a fixed 8 MiB device array shared by all calls, so calls that
+        overlap on the GPU race. The first call on a device sets up the array's address.
+        """
+        P = params.shape[0]
+        _cuda(params, torch.float64, (P, 6), "params")
+        dev = params.device
+        if out is None:
+            out = (torch.empty(P, dtype=torch.float64, device=dev),
+                   torch.empty((P, 3), dtype=torch.float64, device=dev),
+                   torch.empty((P, 3), dtype=torch.float64, device=dev))
+        Z, Zq, S = out
+        t = self._targets(targets)
+        wv = (ctypes.c_double * 3)(*[float(x) for x in w])
+        self._check(self.lib.tersoff_fitness_static(self.h, params.data_ptr(), P, ctypes.byref(t),
+                                                    ctypes.addressof(wv), precision, Z.data_ptr(), _ptr(Zq),
+                                                    _ptr(S), _stream(stream)))
         return Z, Zq, S
 
     def param_grad(self, params: torch.Tensor, targets: dict, w=(1.0, 1.0, 1.0), loss: int = LOSS_SQ,
