@@ -99,6 +99,35 @@ def neighbor_list(pos, box, R2: float = R2_DEFAULT):
             "n": np.concatenate(ns).astype(np.int64) if ns else np.zeros((0, 3), np.int64)}
 
 
+def neighbor_list_subset(pos, box, R2: float, atoms):
+    """Neighbour entries of the atoms listed in `atoms` only, for cells whose lattice-plane spacings
+    all exceed 2*R2 (so every (j, n) with |d| < R2 has |s_j - s_i + n_k| < 1/2 on each axis and lies
+    among the candidates n = -round(s_j - s_i) + {-1, 0, 1}^3). Same exact FP64 test and order as
+    neighbor_list. Returns a list of (j [k], n [k][3]) per requested atom."""
+    pos = np.asarray(pos, dtype=np.float64)
+    H = np.asarray(box, dtype=np.float64)
+    s = pos @ np.linalg.inv(H)
+    off = np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)], dtype=np.int64)
+    R2sq = R2 * R2
+    out = []
+    for i in atoms:
+        base = -np.rint(s - s[i]).astype(np.int64)                 # [N][3]
+        cand = base[:, None, :] + off[None, :, :]                   # [N][27][3]
+        g = cand.astype(np.float64)
+        T = (g[..., 0:1] * H[0] + g[..., 1:2] * H[1]) + g[..., 2:3] * H[2]
+        dx = (pos[:, 0] - pos[i, 0])[:, None] + T[..., 0]
+        dy = (pos[:, 1] - pos[i, 1])[:, None] + T[..., 1]
+        dz = (pos[:, 2] - pos[i, 2])[:, None] + T[..., 2]
+        r2 = (dx * dx + dy * dy) + dz * dz
+        keep = r2 < R2sq
+        keep[i] &= ~(cand[i] == 0).all(axis=1)
+        jj, kk = np.nonzero(keep)
+        n = cand[jj, kk]
+        order = np.lexsort((n[:, 2], n[:, 1], n[:, 0], jj))
+        out.append((jj[order], n[order]))
+    return out
+
+
 def padded(nl, M: int):
     """Neighbour list as fixed-width arrays: cnt [N], nbr [N][M] (-1 pad), shift [N][M][3]."""
     off = nl["off"]

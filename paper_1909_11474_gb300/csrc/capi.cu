@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <vector>
 
 #include "ctx.hpp"
@@ -360,18 +361,56 @@ int tersoff_param_grad(tersoff_ctx *ctx, const double *, int32_t, const tersoff_
   return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
 }
 
-int tersoff_eval_plain(tersoff_ctx *ctx, const double *, int32_t, double *, double *, double *,
-                       tersoff_stream) {
-  return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
+int tersoff_eval_plain(tersoff_ctx *ctx, const double *params, int32_t P, double *E, double *F,
+                       double *W, tersoff_stream stream) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  if (!params || P < 1 || !E || !F || !W) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
+  if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
+  cudaSetDevice(c.device);
+  TSF_CUDA(tsf::launch_plain(c, params, P, E, F, W, S(stream)));
+  return TERSOFF_OK;
 }
 
-int tersoff_md_force(tersoff_ctx *ctx, int32_t, const double *, const double *, const double *,
-                     double, double, int32_t, int32_t, double *, void *, double *, tersoff_stream) {
-  return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
+int tersoff_md_force(tersoff_ctx *ctx, int32_t N, const double *pos, const double *box,
+                     const double *params, double R1, double R2, int32_t max_nbr, int32_t precision,
+                     double *E, void *F, double *W, tersoff_stream stream) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (N < 1 || N > (1 << 24) || !pos || !box || !params || !E || !F || !W)
+    return fail(ctx, TERSOFF_E_ARG, "need 1 <= N <= 2^24 and non-null pointers%s");
+  if (!(R1 > 0.0 && R2 > R1 && std::isfinite(R2))) return fail(ctx, TERSOFF_E_ARG, "need 0 < R1 < R2%s");
+  if (max_nbr < 1 || max_nbr > 32) return fail(ctx, TERSOFF_E_ARG, "max_nbr must be in [1, 32]%s");
+  if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
+  for (int k = 0; k < 6; ++k)
+    if (!std::isfinite(params[k])) return fail(ctx, TERSOFF_E_ARG, "non-finite parameters%s");
+  cudaSetDevice(c.device);
+  std::string err;
+  const int rc = tsf::md_force(c, N, pos, box, params, R1, R2, max_nbr, precision, E, F, W, S(stream), err);
+  if (rc != TERSOFF_OK) return fail(ctx, rc, "%s", err.c_str());
+  return TERSOFF_OK;
 }
 
-int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *, int32_t *, int8_t *) {
-  return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
+int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (c.md_N < 1) return fail(ctx, TERSOFF_E_STATE, "no MD force call yet%s");
+  cudaSetDevice(c.device);
+  const int64_t N = c.md_N, M = c.md_M;
+  TSF_CUDA(cudaDeviceSynchronize());
+  if (cnt) TSF_CUDA(cudaMemcpy(cnt, c.md_cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost));
+  if (nbr) TSF_CUDA(cudaMemcpy(nbr, c.md_nbr.p, N * M * sizeof(int), cudaMemcpyDeviceToHost));
+  if (shift) {
+    std::vector<char4> tmp(N * M);
+    TSF_CUDA(cudaMemcpy(tmp.data(), c.md_shift.p, N * M * sizeof(char4), cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < N * M; ++k) {
+      shift[3 * k] = tmp[k].x;
+      shift[3 * k + 1] = tmp[k].y;
+      shift[3 * k + 2] = tmp[k].z;
+    }
+  }
+  return TERSOFF_OK;
 }
 
 }  // extern "C"

@@ -50,6 +50,29 @@ __device__ __forceinline__ void set_status(unsigned *status, unsigned bit) {
   if (status) atomicOr(status, bit);
 }
 
+// Exact FP64 membership test of the neighbour sets (Eq. 2, 7):
+//   d = (x_j - x_i) + ((n0 a + n1 b) + n2 c),  r^2 = (dx^2 + dy^2) + dz^2,
+// every operation individually rounded (no contraction into FMA), so the decision r^2 < R2^2 is
+// reproducible bit for bit by any FP64 implementation that evaluates the same expression.
+struct ExactPair {
+  double dx, dy, dz, r2;
+};
+__device__ __forceinline__ ExactPair exact_pair(double xjx, double xjy, double xjz, double xix,
+                                                double xiy, double xiz, const double *H, int n0,
+                                                int n1, int n2) {
+  double f0 = (double)n0, f1 = (double)n1, f2 = (double)n2;
+  double tx = __dadd_rn(__dadd_rn(__dmul_rn(f0, H[0]), __dmul_rn(f1, H[3])), __dmul_rn(f2, H[6]));
+  double ty = __dadd_rn(__dadd_rn(__dmul_rn(f0, H[1]), __dmul_rn(f1, H[4])), __dmul_rn(f2, H[7]));
+  double tz = __dadd_rn(__dadd_rn(__dmul_rn(f0, H[2]), __dmul_rn(f1, H[5])), __dmul_rn(f2, H[8]));
+  ExactPair e;
+  e.dx = __dadd_rn(__dsub_rn(xjx, xix), tx);
+  e.dy = __dadd_rn(__dsub_rn(xjy, xiy), ty);
+  e.dz = __dadd_rn(__dsub_rn(xjz, xiz), tz);
+  e.r2 = __dadd_rn(__dadd_rn(__dmul_rn(e.dx, e.dx), __dmul_rn(e.dy, e.dy)), __dmul_rn(e.dz, e.dz));
+  return e;
+}
+
+
 // Sums over the lanes of one warp that share `lane % PT` (the lanes handling the same parameter
 // set): xor-shuffle over the atom-slot bits of the lane index.
 template <int PT, typename T>

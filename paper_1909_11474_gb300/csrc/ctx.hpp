@@ -147,6 +147,14 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
 cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
                                     double we, double wv, double wf, double *Z, double *Zq,
                                     double *S, cudaStream_t s);
+// md.cu
+int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double *x, double R1, double R2,
+             int M, int precision, double *E, void *F, double *W, cudaStream_t s, std::string &err);
+
+// plain.cu
+cudaError_t launch_plain(const Ctx &ctx, const double *params, int P, double *E, double *F, double *W,
+                         cudaStream_t s);
+
 size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster);
 int batch_param_tile();
 int batch_max_smem_optin();

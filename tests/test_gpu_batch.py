@@ -161,3 +161,28 @@ def test_fitness_nonfinite_parameters_rank_last(ctx):
     Z, _, _ = ctx.fitness(torch.tensor(params, device="cuda"), targets_to_device(t))
     Z = Z.cpu().numpy()
     assert np.isinf(Z[1]) and np.isfinite(Z[0]) and np.isfinite(Z[2])
+
+
+@pytest.mark.parametrize("which", ["ga", "mixed", "special"])
+def test_plain_fp64_path(ctx, which):
+    """The plain one-launch-per-(p, c) FP64 path against the oracle and the batched FP64 path."""
+    if which == "ga":
+        w = I.workload_ga_batch(P=3, C=4)
+        cs, params = w["configs"], w["params"]
+    elif which == "mixed":
+        cs, params = _mixed_set(C=6), I.population(np.random.default_rng(9), 2)[0]
+    else:
+        cs, params = _special_set(), I.TABLE2_PARAMS[None, :]
+    _build(ctx, cs)
+    pt = torch.tensor(params, device="cuda")
+    E, F, W = ctx.eval_plain(pt)
+    Eb, Fb, Wb = ctx.eval(pt, precision=64)
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+    Er, Wr, Fr, ES, WS = oracle.evaluate_batch(cs, params, scales=True)
+    E, F, W = E.cpu().numpy(), F.cpu().numpy(), W.cpu().numpy()
+    assert energy_rel_err(E, Er, ES).max() < TOL64["E"]
+    assert virial_rel_err(W, Wr, WS).max() < TOL64["W"]
+    assert force_err(F, Fr) < TOL64["F"]
+    assert np.allclose(E, Eb.cpu().numpy(), rtol=1e-12, atol=1e-12)
+    assert np.allclose(F, Fb.cpu().numpy(), rtol=1e-10, atol=1e-11)

@@ -417,3 +417,14 @@ def test_parameter_gradient_central_differences(loss):
     # the loss itself agrees with the fitness routine
     fz = oracle.fitness(cs, x[None, :], tgt, w=(1.0, 0.5, 2.0))
     assert L == pytest.approx(fz["L"][0] if loss == "sq" else fz["Z"][0], rel=1e-12)
+
+
+def test_neighbor_subset_matches_full_list():
+    """The large-cell neighbour helper equals the exhaustive list where its spacing condition holds."""
+    pos, box = _rand_cell(seed=12, reps=(3, 3, 2), sigma=0.2, strain=0.03)
+    full = oracle.neighbor_list(pos, box, 3.2)
+    atoms = [0, 5, 17, 40, 71, len(pos) - 1]
+    sub = oracle.neighbor_list_subset(pos, box, 3.2, atoms)
+    for i, (j, n) in zip(atoms, sub):
+        e = slice(full["off"][i], full["off"][i + 1])
+        assert np.array_equal(j, full["j"][e]) and np.array_equal(n, full["n"][e])
