@@ -1,0 +1,437 @@
+// adjoint.cu -- gradient of the fitness loss with respect to the six parameters
+// x = [D0, alpha, r0, beta, n, h] (Eq. 16) for many parameter sets at once.
+//
+// For one parameter set the loss terms are S_e = sum_c (E_c/N_c - E*_c)^2,
+// S_v = sum_c sum_k (W_ck/N_c - W*_ck)^2 and S_f = sum_i |F_i - F*_i|^2 (Eq. 17-19 before the square
+// root). Their gradients, per configuration, are
+//   dS_e/dx = a_e dE/dx,                     a_e = 2 (E/N - E*) / N,
+//   dS_v/dx = sum_k a_k dW_k/dx = -d/dx sum_ij P_ij . (B d_ij),   a_k = 2 (W_k/N - W*_k) / N,
+//   dS_f/dx = sum_i v_i . dF_i/dx = -d/dx sum_ij P_ij . (v_j - v_i),   v_i = 2 (F_i - F*_i),
+// with P_ij = dU_i/dd_ij and (B d)_nu = sum_{k = (mu, nu)} a_k d_mu: the virial and force terms are
+// directional derivatives of the site energies along fixed bond directions, which keeps the work
+// atom-local. One CTA evaluates a configuration for 32 parameter sets (the forward passes of the
+// batched kernel give F, E, W and the weights), then re-runs the per-atom core in forward-mode dual
+// arithmetic carrying K parameter tangents at a time. FP32 arithmetic, FP64 accumulation across
+// atoms-of-a-CTA totals and configurations.
+#include <math.h>
+
+#include <algorithm>
+
+#include "batch_kernel.cuh"
+
+namespace tsf {
+
+constexpr int kAdjPT = 32;
+constexpr int kAdjK = 2;          // parameter tangents carried per pass (3 passes for 6 parameters)
+constexpr int kAdjG = 18;         // accumulated gradient terms per lane: 3 loss terms x 6 parameters
+
+struct AdjParams {
+  int P, C;
+  int64_t Ntot;
+  const float *consts;            // [P][8] PConsts<float>
+  const int *boff, *poff;
+  const float4 *gA, *gB;
+  const float *gcos;
+  const CtaRec *recs;
+  int ntiles;
+  const double *tE, *tW;
+  const float4 *tF4;
+  const uint8_t *tmask;
+  double *part, *dpart, *gpart;   // [P][C][3], [C][3], [P][C][3][6]
+  unsigned *status;
+};
+
+__host__ __device__ inline size_t adj_region0(int nb) {
+  const size_t st = (size_t)nb * 3 * kAdjPT;
+  const size_t rd = std::max<size_t>((size_t)(kNW + 1) * kNRed * kAdjPT, (size_t)kNW * kAdjG * kAdjPT);
+  return ((st > rd ? st : rd) * sizeof(float) + 31) / 32 * 32 / sizeof(float);
+}
+size_t adjoint_smem_bytes(int nb, int nq, int nat) {
+  size_t b = adj_region0(nb) * sizeof(float) + (size_t)nb * 2 * sizeof(float4);
+  b += ((size_t)nq * sizeof(float) + 31) / 32 * 32;
+  b += (size_t)nat * sizeof(int4) + (size_t)nat * sizeof(float4);
+  b += (size_t)nat * 3 * kAdjPT * sizeof(float) + 7 * kAdjPT * sizeof(float);
+  return b;
+}
+
+// Dual constants for tangents of parameters q0 .. q0+K-1 (order D0, alpha, r0, beta, n, h).
+template <int K>
+__device__ __forceinline__ PConsts<Dual<K, float>> seed_consts(const PConsts<float> &k, int q0) {
+  PConsts<Dual<K, float>> D;
+  D.D0 = Dual<K, float>(k.D0);
+  D.k1 = Dual<K, float>(k.k1);
+  D.k0 = Dual<K, float>(k.k0);
+  D.alpha = Dual<K, float>(k.alpha);
+  D.beta = Dual<K, float>(k.beta);
+  D.h = Dual<K, float>(k.h);
+  D.n = Dual<K, float>(k.n);
+  D.inv2n = Dual<K, float>(k.inv2n);
+  const float log2e = 1.4426950408889634f;
+  const float r0log2e = k.k0 / k.alpha;            // r0 log2 e
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const int q = q0 + t;
+    if (q == 0) D.D0.d[t] = 1.f;
+    if (q == 1) {                                  // k1 = -alpha log2e, k0 = alpha r0 log2e
+      D.k1.d[t] = -log2e;
+      D.k0.d[t] = r0log2e;
+      D.alpha.d[t] = 1.f;
+    }
+    if (q == 2) D.k0.d[t] = -k.k1;                 // alpha log2e
+    if (q == 3) D.beta.d[t] = 1.f;
+    if (q == 4) {                                  // inv2n = -1/(2n): d/dn = 1/(2 n^2)
+      D.n.d[t] = 1.f;
+      D.inv2n.d[t] = 2.f * k.inv2n * k.inv2n;
+    }
+    if (q == 5) D.h.d[t] = 1.f;
+  }
+  return D;
+}
+
+// One atom's tangent contribution for parameters q0.. (q0+K-1): accumulates dS_q/dx into G[q][x].
+template <int M, int K, int Q0>
+__device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB, const float *sC, int lb,
+                                             int lq, const float *vi, const float *vsm, int pl,
+                                             const float *aw, const PConsts<float> &Kf,
+                                             float (&G)[kAdjG]) {
+  constexpr int q0 = Q0;
+  float ux[M], uy[M], uz[M], r[M], ir[M], fc[M], fcp[M];
+  int jl[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float4 A = sld(&sA[lb + j], 31);
+    const float4 B = sld(&sB[lb + j], 32);
+    ux[j] = A.x; uy[j] = A.y; uz[j] = A.z; r[j] = A.w;
+    ir[j] = B.x; fc[j] = B.y; fcp[j] = B.z;
+    jl[j] = __float_as_int(B.w) >> 16;
+  }
+  constexpr int NP = M * (M - 1) / 2;
+  constexpr int NP4 = (NP + 3) / 4;
+  float cs[NP4 > 0 ? 4 * NP4 : 4];
+  {
+    const float4 *c4 = reinterpret_cast<const float4 *>(sC + lq);
+#pragma unroll
+    for (int q = 0; q < NP4; ++q) {
+      const float4 v = sld(&c4[q], 33);
+      cs[4 * q] = v.x; cs[4 * q + 1] = v.y; cs[4 * q + 2] = v.z; cs[4 * q + 3] = v.w;
+    }
+  }
+  using D = Dual<K, float>;
+  const PConsts<D> KD = seed_consts<K>(Kf, q0);
+  D U, Px[M], Py[M], Pz[M];
+  atom_core<M, D, float>(ux, uy, uz, r, ir, fc, fcp, cs, KD, U, Px, Py, Pz);
+  const float ae = aw[0 * kAdjPT + pl];
+  const float a0 = aw[1 * kAdjPT + pl], a1 = aw[2 * kAdjPT + pl], a2 = aw[3 * kAdjPT + pl];
+  const float a3 = aw[4 * kAdjPT + pl], a4 = aw[5 * kAdjPT + pl], a5 = aw[6 * kAdjPT + pl];
+#pragma unroll
+  for (int t = 0; t < K; ++t) G[0 * 6 + q0 + t] += 0.5f * ae * U.d[t];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float dx = r[j] * ux[j], dy = r[j] * uy[j], dz = r[j] * uz[j];
+    // virial direction B d: W_xx, W_yy, W_zz, W_xy, W_yz, W_zx = -sum d_mu P_nu
+    const float bx = a0 * dx + a5 * dz, by = a1 * dy + a3 * dx, bz = a2 * dz + a4 * dy;
+    const float *vj = vsm + (size_t)jl[j] * 3 * kAdjPT + pl;
+    const float fx = sld(&vj[0], 34) - vi[0], fy = sld(&vj[kAdjPT], 34) - vi[1], fz = sld(&vj[2 * kAdjPT], 34) - vi[2];
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+      G[1 * 6 + q0 + t] -= Px[j].d[t] * bx + Py[j].d[t] * by + Pz[j].d[t] * bz;
+      G[2 * 6 + q0 + t] -= Px[j].d[t] * fx + Py[j].d[t] * fy + Pz[j].d[t] * fz;
+    }
+  }
+}
+
+template <int MMAX>
+__global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a) {
+  constexpr int PT = kAdjPT;
+  extern __shared__ __align__(32) unsigned char smem[];
+  float *stage = reinterpret_cast<float *>(smem);
+  const int tid = threadIdx.x, warp = tid >> 5, pl = tid & 31;
+  const int item = blockIdx.x;
+  const int tile = item % a.ntiles;
+  const CtaRec rec = a.recs[item / a.ntiles];
+  const int c = rec.c;
+  const int p = tile * PT + pl;
+  const bool active = p < a.P;
+  PConsts<float> K;
+  {
+    const float4 *kc = reinterpret_cast<const float4 *>(a.consts) + 2 * (active ? p : a.P - 1);
+    const float4 k0 = kc[0], k1 = kc[1];
+    K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.alpha = k0.w;
+    K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
+  }
+  const int nat = rec.nat, s0 = rec.s0, ns = rec.ns;
+  const int B0 = rec.B0, nb = rec.nb, Q0 = rec.Q0, nq = rec.nq;
+  float4 *sA = reinterpret_cast<float4 *>(stage + adj_region0(nb));
+  float4 *sB = sA + nb;
+  float *sC = reinterpret_cast<float *>(sB + nb);
+  int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) + ((size_t)nq * 4 + 31) / 32 * 32);
+  float4 *stF = reinterpret_cast<float4 *>(satom + ns);
+  float *vsm = reinterpret_cast<float *>(stF + ns);          // [ns][3][PT]: v_i = 2 (F_i - F*_i)
+  float *aw = vsm + (size_t)ns * 3 * PT;                     // [7][PT]: a_e, a_k (k = xx..zx)
+  {
+    for (int t = tid; t < nb; t += kThreads) {
+      sst(&sA[t], a.gA[B0 + t], 6);
+      sst(&sB[t], a.gB[B0 + t], 7);
+    }
+    for (int t = tid; t < nq; t += kThreads) sst(&sC[t], a.gcos[Q0 + t], 8);
+    for (int t = tid; t < ns; t += kThreads) {
+      const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
+      sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0), 9);
+      sst(&stF[t], a.tF4[s0 + t], 10);
+    }
+  }
+  __syncthreads();
+
+  // ---- forward passes 1-2 (the batched kernel's atom code)
+  AtomAcc<float> acc;
+  acc.U = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc.W[k] = 0.f;
+  for (int li = warp; li < ns; li += kNW) {
+    const int4 at = sld(&satom[li], 11);
+    const int m = at.z;
+    if (m > MMAX) {
+      if (pl == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
+      continue;
+    }
+    atom_forward_dispatch<PT, MMAX, true, float>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+  }
+  __syncthreads();
+
+  // ---- pass 3: forces, residuals and v_i
+  const uint8_t mask = a.tmask[c];
+  float sf = 0.f, sF2 = 0.f, sT = 0.f;
+  for (int li = warp; li < ns; li += kNW) {
+    const int4 at = sld(&satom[li], 12);
+    const int m = at.z, lb = at.x;
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f;
+    for (int e = 0; e < m; ++e) {
+      const float *st = stage + (size_t)(lb + e) * 3 * PT + pl;
+      Fx += sld(&st[0], 13);
+      Fy += sld(&st[PT], 13);
+      Fz += sld(&st[2 * PT], 13);
+      const int rb = __float_as_int(sld(&sB[lb + e].w, 14)) & 0xffff;
+      const float *sr = stage + (size_t)(rb + rec.cb0 - B0) * 3 * PT + pl;
+      Fx -= sld(&sr[0], 15);
+      Fy -= sld(&sr[PT], 15);
+      Fz -= sld(&sr[2 * PT], 15);
+    }
+    sF2 += Fx * Fx + Fy * Fy + Fz * Fz;
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+    if (mask & 4) {
+      const float4 t = sld(&stF[li], 16);
+      const float ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
+      sf += ex * ex + ey * ey + ez * ez;
+      sT += t.w;
+      vx = 2.f * ex;
+      vy = 2.f * ey;
+      vz = 2.f * ez;
+    }
+    float *vv = vsm + (size_t)li * 3 * PT + pl;
+    sst(&vv[0], vx, 35);
+    sst(&vv[PT], vy, 35);
+    sst(&vv[2 * PT], vz, 35);
+  }
+
+  // ---- forward reductions (as the batched kernel) and the per-parameter-set weights
+  float v[kNRed];
+  v[0] = acc.U;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) v[1 + k] = acc.W[k];
+  v[7] = sf;
+  v[8] = sF2;
+  v[9] = sT;
+  __syncthreads();
+  float *red = stage;
+  float *tot = stage + kNW * kNRed * PT;
+#pragma unroll
+  for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PT + pl], v[k], 17);
+  __syncthreads();
+  for (int idx = tid; idx < kNRed * PT; idx += kThreads) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) t += sld(&red[w * kNRed * PT + idx], 18);
+    sst(&tot[idx], t, 19);
+  }
+  __syncthreads();
+  if (tid < PT) {
+    double q[kNRed];
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) q[k] = (double)sld(&tot[k * PT + tid], 20);
+    const double invN = 1.0 / (double)nat;
+    bool finite = isfinite(q[0]) && isfinite(q[8]);
+    for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);
+    double se = 0.0, sv = 0.0, sfv = 0.0, ae = 0.0, ak[6] = {0, 0, 0, 0, 0, 0};
+    if (mask & 1) {
+      const double d = q[0] * invN - a.tE[c];
+      se = d * d;
+      ae = 2.0 * d * invN;
+    }
+    if (mask & 2)
+      for (int k = 0; k < 6; ++k) {
+        const double d = q[1 + k] * invN - a.tW[c * 6 + k];
+        sv += d * d;
+        ak[k] = 2.0 * d * invN;
+      }
+    if (mask & 4) sfv = q[7];
+    if (!finite) se = sv = sfv = __longlong_as_double(0x7ff8000000000000ll);
+    const int pp = tile * PT + tid;
+    if (pp < a.P) {
+      double *o = a.part + ((size_t)pp * a.C + c) * 3;
+      o[0] = se;
+      o[1] = sv;
+      o[2] = sfv;
+    }
+    sst(&aw[0 * PT + tid], (float)ae, 36);
+    for (int k = 0; k < 6; ++k) sst(&aw[(1 + k) * PT + tid], (float)ak[k], 36);
+    if (tile == 0 && tid == 0) {
+      double de = 0.0, dv = 0.0;
+      if (mask & 1) de = a.tE[c] * a.tE[c];
+      if (mask & 2)
+        for (int k = 0; k < 6; ++k) dv += a.tW[c * 6 + k] * a.tW[c * 6 + k];
+      a.dpart[c * 3 + 0] = de;
+      a.dpart[c * 3 + 1] = dv;
+      a.dpart[c * 3 + 2] = (mask & 4) ? q[9] : 0.0;
+    }
+  }
+  __syncthreads();
+
+  // ---- tangent passes: K parameters at a time
+  float G[kAdjG];
+#pragma unroll
+  for (int k = 0; k < kAdjG; ++k) G[k] = 0.f;
+  for (int li = warp; li < ns; li += kNW) {
+    const int4 at = sld(&satom[li], 21);
+    const int m = at.z;
+    if (m > MMAX) continue;
+    const float *vp = vsm + (size_t)li * 3 * PT + pl;
+    const float vi[3] = {sld(&vp[0], 22), sld(&vp[PT], 22), sld(&vp[2 * PT], 22)};
+#define TSF_TAN(MM)                                                                           \
+  case MM:                                                                                    \
+    if constexpr (MMAX >= MM) {                                                               \
+      atom_tangent<MM, kAdjK, 0>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, G);              \
+      atom_tangent<MM, kAdjK, 2>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, G);              \
+      atom_tangent<MM, kAdjK, 4>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, G);              \
+    }                                                                                         \
+    break;
+    switch (m) {
+      TSF_TAN(1) TSF_TAN(2) TSF_TAN(3) TSF_TAN(4) TSF_TAN(5) TSF_TAN(6) TSF_TAN(7) TSF_TAN(8)
+      default: break;
+    }
+#undef TSF_TAN
+  }
+  // reduce G over warps (region0 is free again) and write the per-(p, c) gradient partial sums
+  __syncthreads();
+  float *gred = stage;                                       // [kNW][kAdjG][PT]
+#pragma unroll
+  for (int k = 0; k < kAdjG; ++k) sst(&gred[(warp * kAdjG + k) * PT + pl], G[k], 23);
+  __syncthreads();
+  for (int idx = tid; idx < kAdjG * PT; idx += kThreads) {
+    const int k = idx / PT, lp = idx % PT;
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) t += (double)sld(&gred[(w * kAdjG + k) * PT + lp], 24);
+    const int pp = tile * PT + lp;
+    if (pp < a.P) a.gpart[((size_t)pp * a.C + c) * kAdjG + k] = t;
+  }
+}
+
+// One warp per parameter set: S_q, D_q and G_q = dS_q/dx summed over configurations (FP64, fixed
+// order); L and dL/dx for the squared loss (w_q S_q / D_q) or Z (w_q sqrt(S_q / D_q)).
+__global__ void grad_finalize_kernel(int P, int C, const double *__restrict__ part,
+                                     const double *__restrict__ dpart, const double *__restrict__ gpart,
+                                     double we, double wv, double wf, int loss, double *__restrict__ L,
+                                     double *__restrict__ dL) {
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (p >= P) return;
+  double s[3] = {0, 0, 0}, d[3] = {0, 0, 0}, g[kAdjG];
+  for (int k = 0; k < kAdjG; ++k) g[k] = 0.0;
+  for (int c = lane; c < C; c += 32) {
+    for (int q = 0; q < 3; ++q) {
+      s[q] += part[((size_t)p * C + c) * 3 + q];
+      d[q] += dpart[(size_t)c * 3 + q];
+    }
+    for (int k = 0; k < kAdjG; ++k) g[k] += gpart[((size_t)p * C + c) * kAdjG + k];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    for (int q = 0; q < 3; ++q) {
+      s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+      d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
+    }
+    for (int k = 0; k < kAdjG; ++k) g[k] += __shfl_xor_sync(0xffffffffu, g[k], off);
+  }
+  if (lane == 0) {
+    const double w[3] = {we, wv, wf};
+    double l = 0.0, cq[3];
+    bool finite = true;
+    for (int q = 0; q < 3; ++q) {
+      finite = finite && isfinite(s[q]);
+      cq[q] = 0.0;
+      if (d[q] > 0.0) {
+        if (loss == TERSOFF_LOSS_SQ) {
+          l += w[q] * s[q] / d[q];
+          cq[q] = w[q] / d[q];
+        } else {
+          l += w[q] * sqrt(s[q] / d[q]);
+          cq[q] = s[q] > 0.0 ? w[q] / (2.0 * sqrt(s[q] * d[q])) : 0.0;
+        }
+      }
+    }
+    L[p] = finite ? l : INFINITY;
+    for (int x = 0; x < 6; ++x) {
+      double gx = 0.0;
+      for (int q = 0; q < 3; ++q) gx += cq[q] * g[q * 6 + x];
+      dL[(size_t)p * 6 + x] = finite ? gx : __longlong_as_double(0x7ff8000000000000ll);
+    }
+  }
+}
+
+cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const double *tE, const double *tW,
+                              const double *tF, const uint8_t *tmask, const double *w, int loss, double *L,
+                              double *dL, void *consts, void *tf4, double *part, double *dpart, double *gpart,
+                              cudaStream_t s) {
+  const BatchPlan &plan = ctx.plan32;
+  {
+    const int64_t n = std::max<int64_t>(P, ctx.Ntot);
+    prep_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, params, reinterpret_cast<float *>(consts),
+                                                                   ctx.Ntot, tF, reinterpret_cast<float4 *>(tf4));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  AdjParams ap = {};
+  ap.P = P;
+  ap.C = ctx.C;
+  ap.Ntot = ctx.Ntot;
+  ap.consts = reinterpret_cast<const float *>(consts);
+  ap.boff = ctx.boff.as<int>();
+  ap.poff = ctx.poff.as<int>();
+  ap.gA = ctx.gA32.as<float4>();
+  ap.gB = ctx.gB32.as<float4>();
+  ap.gcos = ctx.gcos32.as<float>();
+  ap.ntiles = (P + kAdjPT - 1) / kAdjPT;
+  ap.tE = tE;
+  ap.tW = tW;
+  ap.tF4 = reinterpret_cast<const float4 *>(tf4);
+  ap.tmask = tmask;
+  ap.part = part;
+  ap.dpart = dpart;
+  ap.gpart = gpart;
+  ap.status = ctx.status.as<unsigned>();
+  for (const Bucket &b : plan.buckets) {
+    if (b.nitems == 0) continue;
+    if (b.cluster != 1) return cudaErrorNotSupported;   // the host rejects such builds first
+    const size_t smem = b.adj_smem;
+    ap.recs = plan.items.as<CtaRec>() + b.item_off;
+    auto kern = b.mmax <= 4 ? adjoint_kernel<4> : (b.mmax <= 6 ? adjoint_kernel<6> : adjoint_kernel<8>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(b.nitems * ap.ntiles), kThreads, smem, s>>>(ap);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  grad_finalize_kernel<<<(P + 7) / 8, 256, 0, s>>>(P, ctx.C, part, dpart, gpart, w[0], w[1], w[2], loss, L, dL);
+  return cudaGetLastError();
+}
+
+}  // namespace tsf

@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "ctx.hpp"
+#include "dual.cuh"
 
 namespace tsf {
 
@@ -82,13 +83,13 @@ struct PConsts {
 // zeta is clamped to 1e-30 from below: at zeta = 0 this gives b = 1 to working precision, and b'
 // stays finite; it then only ever multiplies g or g' of the same (vanishing) pairs, so every
 // contribution of a zeta = 0 bond to the forces is exactly zero, as with b' = 0.
-template <typename R>
-__device__ __forceinline__ void bond_order(R zeta, const PConsts<R> &K, R &b, R &bp) {
-  const R z = zeta > R(1e-30) ? zeta : R(1e-30);
-  const R zn = ex2(K.n * lg2(z));
-  const R u = R(1) + zn;
+template <typename T>
+__device__ __forceinline__ void bond_order(T zeta, const PConsts<T> &K, T &b, T &bp) {
+  const T z = zeta > T(1e-30f) ? zeta : T(1e-30f);
+  const T zn = ex2(K.n * lg2(z));
+  const T u = T(1.0f) + zn;
   b = ex2(K.inv2n * lg2(u));
-  bp = R(-0.5) * b * zn * rcp(z * u);
+  bp = T(-0.5f) * b * zn * rcp(z * u);
 }
 
 template <typename R>
@@ -96,8 +97,107 @@ struct AtomAcc {
   R U, W[6];
 };
 
+// The per-atom core of passes 1 and 2: from the bond geometry (unit vectors, r, 1/r, f_C, f_C', the
+// cosines of the bond pairs; R) and the parameter constants (T: R itself, or a dual number carrying
+// parameter tangents), U = sum_j f_C (f_R - b f_A), which is twice the site energy U_i of Eq. 2,
+// and P_ij = dU_i/dd_ij of every bond (the derivative of U_i itself, 1/2 included).
+template <int M, typename T, typename R>
+__device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], const R (&uz)[M],
+                                          const R (&r)[M], const R (&ir)[M], const R (&fc)[M],
+                                          const R (&fcp)[M], const R *cs, const PConsts<T> &K, T &U,
+                                          T (&Px)[M], T (&Py)[M], T (&Pz)[M]) {
+  // ---- pass 1: pair functions (Eq. 4-5 with Eq. 11-14 at S = 2) and zeta (Eq. 7, 10)
+  constexpr int NP = M * (M - 1) / 2;
+  T fR[M], fA[M], zeta[M], tq[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const T x = ex2(r[j] * K.k1 + K.k0);
+    const T Dx = K.D0 * x;
+    fR[j] = Dx * x;
+    fA[j] = Dx + Dx;
+    zeta[j] = T(0.0f);
+  }
+  {
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+#pragma unroll
+      for (int k = j + 1; k < M; ++k) {
+        const T u = cs[q] - K.h;
+        const T t = K.beta * u;                     // g = t u, g' = 2 t
+        const T g = t * u;
+        tq[q] = t;
+        zeta[j] += fc[k] * g;
+        zeta[k] += fc[j] * g;
+        ++q;
+      }
+    }
+  }
+  T cc[M], rad[M];
+  U = T(0.0f);
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    T b, bp;
+    bond_order(zeta[j], K, b, bp);
+    const T e = fR[j] - b * fA[j];                 // f_R - b f_A
+    U += fc[j] * e;                                // Eq. 3 (the 1/2 of Eq. 2 is applied by callers)
+    cc[j] = (R(-0.5) * fc[j]) * fA[j] * bp;        // dU_i / dzeta_ij
+    const T de = -K.alpha * (fR[j] + e);           // f_R' - b f_A' = -alpha (2 f_R - b f_A)
+    rad[j] = R(0.5) * (fcp[j] * e + fc[j] * de);
+  }
+
+  // ---- pass 2: dU_i/dd_ij
+  T Ax[M], Ay[M], Az[M], s[M], Rg[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    Ax[j] = T(0.0f); Ay[j] = T(0.0f); Az[j] = T(0.0f); s[j] = T(0.0f); Rg[j] = T(0.0f);
+  }
+  {
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+#pragma unroll
+      for (int k = j + 1; k < M; ++k) {
+        const T w = (cc[j] * fc[k] + cc[k] * fc[j]) * tq[q];   // half of the w of the header
+        Ax[j] += w * ux[k]; Ay[j] += w * uy[k]; Az[j] += w * uz[k];
+        Ax[k] += w * ux[j]; Ay[k] += w * uy[j]; Az[k] += w * uz[j];
+        const T wc = w * cs[q];
+        s[j] += wc;
+        s[k] += wc;
+        ++q;
+      }
+    }
+  }
+  // bonds inside the switching region (R1 < r < R2) carry the f_C'(r_ij) g term; the vote keeps
+  // this loop off the common path where no bond of the warp is in that region
+  bool sw = false;
+#pragma unroll
+  for (int j = 0; j < M; ++j) sw |= (fcp[j] != R(0));
+  if (__any_sync(0xffffffffu, sw)) {
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+#pragma unroll
+      for (int k = j + 1; k < M; ++k) {
+        const T g = tq[q] * (cs[q] - K.h);
+        Rg[j] += cc[k] * g;
+        Rg[k] += cc[j] * g;
+        ++q;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const R ir2 = ir[j] + ir[j];                   // 2/r restores the factor 2 of g' = 2 t
+    const T coef = rad[j] + fcp[j] * Rg[j] - s[j] * ir2;
+    Px[j] = coef * ux[j] + ir2 * Ax[j];
+    Py[j] = coef * uy[j] + ir2 * Ay[j];
+    Pz[j] = coef * uz[j] + ir2 * Az[j];
+  }
+}
+
 // Passes 1 and 2 for one atom per atom slot, M = the warp's largest neighbour count.
-// sA/sB: bond records (u_x, u_y, u_z, r), (1/r, f_C, f_C', rev); sC: pair cosines; lb/lq: this
+// sA/sB: bond records (u_x, u_y, u_z, r), (1/r, f_C, f_C', rev | j << 16); sC: pair cosines; lb/lq: this
 // atom's first bond / pair in shared memory; m: its neighbour count (<= M). EXACT: every slot has
 // m == M, so no bond is a phantom.
 template <int M, int PT, bool EXACT, typename R>
@@ -143,102 +243,20 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
     }
   }
 
-  // ---- pass 1: pair functions (Eq. 4-5 with Eq. 11-14 at S = 2) and zeta (Eq. 7, 10)
-  R fR[M], fA[M], zeta[M], tq[NP > 0 ? NP : 1];
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    const R x = ex2(r[j] * K.k1 + K.k0);
-    const R Dx = K.D0 * x;
-    fR[j] = Dx * x;
-    fA[j] = Dx + Dx;
-    zeta[j] = R(0);
-  }
-  {
-    int q = 0;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-#pragma unroll
-      for (int k = j + 1; k < M; ++k) {
-        const R u = cs[q] - K.h;
-        const R t = K.beta * u;                     // g = t u, g' = 2 t
-        const R g = t * u;
-        tq[q] = t;
-        zeta[j] += fc[k] * g;
-        zeta[k] += fc[j] * g;
-        ++q;
-      }
-    }
-  }
-  R cc[M], rad[M];
-  R U = R(0);
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    R b, bp;
-    bond_order(zeta[j], K, b, bp);
-    const R e = fR[j] - b * fA[j];                 // f_R - b f_A
-    U += fc[j] * e;                                // Eq. 3 (the 1/2 of Eq. 2 is applied below)
-    cc[j] = R(-0.5) * fc[j] * fA[j] * bp;          // dU_i / dzeta_ij
-    const R de = -K.alpha * (fR[j] + e);           // f_R' - b f_A' = -alpha (2 f_R - b f_A)
-    rad[j] = R(0.5) * (fcp[j] * e + fc[j] * de);
-  }
-
-  // ---- pass 2: dU_i/dd_ij
-  R Ax[M], Ay[M], Az[M], s[M], Rg[M];
-#pragma unroll
-  for (int j = 0; j < M; ++j) {
-    Ax[j] = R(0); Ay[j] = R(0); Az[j] = R(0); s[j] = R(0); Rg[j] = R(0);
-  }
-  {
-    int q = 0;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-#pragma unroll
-      for (int k = j + 1; k < M; ++k) {
-        const R w = (cc[j] * fc[k] + cc[k] * fc[j]) * tq[q];   // half of the w of the header
-        Ax[j] += w * ux[k]; Ay[j] += w * uy[k]; Az[j] += w * uz[k];
-        Ax[k] += w * ux[j]; Ay[k] += w * uy[j]; Az[k] += w * uz[j];
-        const R wc = w * cs[q];
-        s[j] += wc;
-        s[k] += wc;
-        ++q;
-      }
-    }
-  }
-  // bonds inside the switching region (R1 < r < R2) carry the f_C'(r_ij) g term; the vote keeps
-  // this loop off the common path where no bond of the warp is in that region
-  bool sw = false;
-#pragma unroll
-  for (int j = 0; j < M; ++j) sw |= (fcp[j] != R(0));
-  if (__any_sync(0xffffffffu, sw)) {
-    int q = 0;
-#pragma unroll
-    for (int j = 0; j < M; ++j) {
-#pragma unroll
-      for (int k = j + 1; k < M; ++k) {
-        const R g = tq[q] * (cs[q] - K.h);
-        Rg[j] += cc[k] * g;
-        Rg[k] += cc[j] * g;
-        ++q;
-      }
-    }
-  }
+  R U, Px[M], Py[M], Pz[M];
+  atom_core<M, R, R>(ux, uy, uz, r, ir, fc, fcp, cs, K, U, Px, Py, Pz);
   R W0 = R(0), W1 = R(0), W2 = R(0), W3 = R(0), W4 = R(0), W5 = R(0);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    const R ir2 = ir[j] + ir[j];                   // 2/r restores the factor 2 of g' = 2 t
-    const R coef = rad[j] + fcp[j] * Rg[j] - s[j] * ir2;
-    const R Px = coef * ux[j] + ir2 * Ax[j];
-    const R Py = coef * uy[j] + ir2 * Ay[j];
-    const R Pz = coef * uz[j] + ir2 * Az[j];
     if (store && (EXACT || j < m)) {
       R *st = stage + (size_t)(lb + j) * 3 * PT + pl;
-      sst(&st[0], Px, 5);
-      sst(&st[PT], Py, 5);
-      sst(&st[2 * PT], Pz, 5);
+      sst(&st[0], Px[j], 5);
+      sst(&st[PT], Py[j], 5);
+      sst(&st[2 * PT], Pz[j], 5);
     }
     const R dx = r[j] * ux[j], dy = r[j] * uy[j], dz = r[j] * uz[j];
-    W0 -= dx * Px; W1 -= dy * Py; W2 -= dz * Pz;
-    W3 -= dx * Py; W4 -= dy * Pz; W5 -= dz * Px;
+    W0 -= dx * Px[j]; W1 -= dy * Py[j]; W2 -= dz * Pz[j];
+    W3 -= dx * Py[j]; W4 -= dy * Pz[j]; W5 -= dz * Px[j];
   }
   if (store) {
     acc.U += R(0.5) * U;
@@ -464,8 +482,8 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
       Fy += sld(&st[PT], 13);
       Fz += sld(&st[2 * PT], 13);
       int rb;  // configuration-local bond index of the reverse entry
-      if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sld(&sB[lb + e].w, 14));
-      else rb = (int)sld(&sB[lb + e].w, 14);
+      if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sld(&sB[lb + e].w, 14)) & 0xffff;
+      else rb = (int)sld(&sB[lb + e].w, 14) & 0xffff;
       if constexpr (CLUSTER) {
         unsigned r = 0;
         while (r + 1 < ncta && rb >= peer_b0[r + 1]) ++r;

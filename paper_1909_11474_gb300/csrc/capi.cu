@@ -45,7 +45,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     bool operator<(const Key &o) const { return mmax != o.mmax ? mmax < o.mmax : cl < o.cl; }
   };
   std::map<Key, std::vector<int>> groups;
-  std::map<Key, size_t> smem;
+  std::map<Key, size_t> smem, adj_smem;
   for (int cf = 0; cf < c.C; ++cf) {
     const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
     int chosen = 0;
@@ -71,6 +71,10 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     Key k{mmax, chosen};
     groups[k].push_back(cf);
     smem[k] = std::max(smem[k], need);
+    if (chosen == 1) {
+      const int nb = c.h_boff[a1] - c.h_boff[a0], nq = c.h_poff[a1] - c.h_poff[a0];
+      adj_smem[k] = std::max(adj_smem[k], tsf::adjoint_smem_bytes(nb, nq, nat));
+    }
   }
   std::vector<tsf::CtaRec> recs;
   plan.buckets.clear();
@@ -91,6 +95,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     b.cluster = k.cl;
     b.precision = precision;
     b.smem = smem[k];
+    b.adj_smem = adj_smem[k];
     b.item_off = (int)recs.size();
     for (int cf : cfgs) {
       const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
@@ -150,7 +155,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   cudaDeviceSynchronize();
   tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
-                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.part, &c.dpart, &c.work, &c.tf4,
+                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_Ui, &c.md_boxd};
@@ -356,9 +361,27 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   return TERSOFF_OK;
 }
 
-int tersoff_param_grad(tersoff_ctx *ctx, const double *, int32_t, const tersoff_targets *,
-                       const double *, int32_t, double *, double *, tersoff_stream) {
-  return fail(ctx, TERSOFF_E_UNSUPPORTED, "not built yet%s");
+int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
+                       const double *w, int32_t loss, double *L, double *dL, tersoff_stream stream) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  if (!params || P < 1 || !tg || !w || !L || !dL) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
+  if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
+  if (loss != TERSOFF_LOSS_SQ && loss != TERSOFF_LOSS_Z) return fail(ctx, TERSOFF_E_ARG, "unknown loss%s");
+  if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
+  for (const tsf::Bucket &b : c.plan32.buckets)
+    if (b.cluster != 1)
+      return fail(ctx, TERSOFF_E_UNSUPPORTED, "the gradient kernel needs every configuration to fit one CTA%s");
+  cudaSetDevice(c.device);
+  TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.gpart.ensure((size_t)P * c.C * 18 * sizeof(double)));
+  TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
+  TSF_CUDA(c.tf4.ensure((size_t)c.Ntot * sizeof(tsf::dvec4)));
+  TSF_CUDA(tsf::launch_param_grad(c, params, P, tg->E, tg->W, tg->F, tg->mask, w, loss, L, dL, c.work.p, c.tf4.p,
+                                  c.part.as<double>(), c.dpart.as<double>(), c.gpart.as<double>(), S(stream)));
+  return TERSOFF_OK;
 }
 
 int tersoff_eval_plain(tersoff_ctx *ctx, const double *params, int32_t P, double *E, double *F,

@@ -78,6 +78,7 @@ struct Bucket {
   int cluster;     // CTAs per configuration (1 = no cluster)
   int precision;   // 32 or 64
   size_t smem;     // dynamic shared memory per CTA
+  size_t adj_smem; // dynamic shared memory per CTA of the adjoint kernel (FP32, single-CTA buckets)
   int nitems;      // configurations in the bucket
   int item_off;    // first record of the bucket (records are per configuration and cluster rank)
 };
@@ -103,7 +104,7 @@ struct Ctx {
   DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, cnt, nbr, shift, boff, poff, brev;
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
   BatchPlan plan32, plan64;
-  DevBuf part, dpart, work, tf4;
+  DevBuf part, dpart, work, tf4, gpart;
 
   // --- MD state ---
   int md_N = 0, md_M = 0;
@@ -150,6 +151,13 @@ cudaError_t launch_fitness_finalize(int P, int C, const double *part, const doub
 // md.cu
 int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double *x, double R1, double R2,
              int M, int precision, double *E, void *F, double *W, cudaStream_t s, std::string &err);
+
+// adjoint.cu
+size_t adjoint_smem_bytes(int nb, int nq, int nat);
+cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const double *tE, const double *tW,
+                              const double *tF, const uint8_t *tmask, const double *w, int loss, double *L,
+                              double *dL, void *consts, void *tf4, double *part, double *dpart, double *gpart,
+                              cudaStream_t s);
 
 // plain.cu
 cudaError_t launch_plain(const Ctx &ctx, const double *params, int P, double *E, double *F, double *W,

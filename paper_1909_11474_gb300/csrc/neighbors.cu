@@ -155,8 +155,9 @@ __device__ __forceinline__ void cutoff_fc(double r, double R1, double R2, double
   }
 }
 
-// Per bond: unit vector, r, 1/r, f_C, f_C' and the configuration-local index of the reverse bond
-// (stored in the 4th slot: as a double, or as the bit pattern of an int in the FP32 record);
+// Per bond: unit vector, r, 1/r, f_C, f_C' and, packed into one int (rev | j << 16), the
+// configuration-local indices of the reverse bond and of the neighbour atom (stored in the 4th slot:
+// as a double, or as the bit pattern of the int in the FP32 record);
 // per unordered pair (e < f) of an atom's bonds: cos theta (each atom's row padded to 4 slots). Computed in FP64 from the same d as the
 // membership test, stored in FP64 and rounded to FP32.
 __global__ void geometry_kernel(int64_t Ntot, int M, const int *__restrict__ atom_cfg,
@@ -178,8 +179,9 @@ __global__ void geometry_kernel(int64_t Ntot, int M, const int *__restrict__ ato
   const int b0 = boff[i];
   const int cb0 = boff[atom_off[c]];   // first bond of the configuration
   for (int e = 0; e < m; ++e) {
-    const int rl = brev[b0 + e] - cb0;  // configuration-local index of the reverse bond
     const int j = nbr[i * M + e];
+    // packed: configuration-local index of the reverse bond (bits 0-15) and of atom j (bits 16-31)
+    const int rl = (brev[b0 + e] - cb0) | ((j - atom_off[c]) << 16);
     const char4 n = shift[i * M + e];
     ExactPair p = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], xix, xiy, xiz, H, n.x, n.y, n.z);
     const double r = sqrt(p.r2);
