@@ -110,7 +110,7 @@ def test_md_full_size_sampled(ctx):
 
 def test_md_rejects_small_box(ctx):
     from paper_1909_11474_gb300 import binding
-    pos, box = I.diamond_supercell((2, 2, 2))
+    pos, box = I.diamond_supercell((1, 1, 1))     # plane spacing 5.43 A < 3 R2 = 9.6 A
     with pytest.raises(binding.TersoffError) as ei:
         ctx.md_force(torch.tensor(pos, device="cuda"), box, I.TABLE2_PARAMS)
     assert ei.value.code == binding.E_ARG
