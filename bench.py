@@ -264,6 +264,13 @@ def run_ours(args):
            "e2e": {"value": round(ws * atom_evals * args.steps / t_e2e, 1), "unit": UNIT,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": args.steps * (5 + 2), "roofline": roofline, "clocks": clocks}
+    if not args.quick:
+        out["rows"] = {
+            "adjoint": bench_adjoint(ctx_dev=dev, steps=max(3, args.steps // 5), flush=flush, stream=stream),
+            "plain_fp64_vs_batched": bench_plain(ctx, params, tg, dev, cs, flush, stream, k_time),
+            "uneven_batch": bench_uneven(dev, flush, stream),
+            "md_force": bench_md(dev, flush, stream, steps=max(3, args.steps // 5)),
+        }
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, tg_host={k: v.cpu().numpy() for k, v in tg.items()},
                                            budget_s=args.cpu_seconds)
@@ -272,6 +279,115 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _time(fn, k, flush, stream, warmup=2):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+    for a, b in ev:
+        flush.fill_(1.0)
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / 1e3 / k
+
+
+def _targets_from_fp64(ctx, w, cs, dev):
+    """Targets = the library's FP64 E/F/W at the hidden (Table 2) parameters + the workload's noise."""
+    import torch
+    Eh, Fh, Wh = ctx.eval(torch.tensor(w["hidden"][None, :], device=dev), precision=64)
+    natoms = torch.tensor(cs.natoms, device=dev, dtype=torch.float64)
+    ne, nw, nf = w["noise"]
+    return {"E": (Eh[0] / natoms + torch.tensor(ne, device=dev)).contiguous(),
+            "W": (Wh[0] / natoms[:, None] + torch.tensor(nw, device=dev)).contiguous(),
+            "F": (Fh[0] + torch.tensor(nf, device=dev)).contiguous(),
+            "mask": torch.full((cs.C,), 7, dtype=torch.uint8, device=dev)}
+
+
+def bench_adjoint(ctx_dev, steps, flush, stream):
+    """Loss gradient over the six parameters: P = 64 x C = 100 64-atom cells (FP32, FP64 accumulation)."""
+    import torch
+
+    from paper_1909_11474_gb300 import binding
+    from paper_1909_11474_gb300 import inputs as I
+    w = I.workload_adjoint()
+    cs = w["configs"]
+    ctx = binding.Context(ctx_dev.index or 0)
+    ctx.build_neighbors(cs.atom_off, torch.tensor(cs.pos, device=ctx_dev), torch.tensor(cs.box, device=ctx_dev))
+    tg = _targets_from_fp64(ctx, w, cs, ctx_dev)
+    params = torch.tensor(w["params"], device=ctx_dev)
+    t = _time(lambda: ctx.param_grad(params, tg), steps, flush, stream)
+    tf = _time(lambda: ctx.fitness(params, tg), steps, flush, stream)
+    P = len(w["params"])
+    return {"workload": "P=64 x C=100 64-atom cells, dL/dx over 6 parameters", "ms": round(1e3 * t, 4),
+            "value": round(P * cs.Ntot / t, 1), "unit": "atom-evals/s (forward + 6-parameter gradient)",
+            "gradients_per_s": round(P / t, 1), "cost_vs_fitness": round(t / tf, 2)}
+
+
+def bench_plain(ctx, params, tg, dev, cs, flush, stream, t_fit32):
+    """The plain FP64 path (one launch per (p, c), no cache) on a sample of the GA batch, and the
+    batched path in FP64 and FP32 on the whole batch."""
+    import torch
+    Ps = 2
+    sub = params[:Ps].contiguous()
+    t_plain = _time(lambda: ctx.eval_plain(sub), 2, flush, stream, warmup=1)
+    t_b64 = _time(lambda: ctx.eval(params, precision=64), 3, flush, stream)
+    t_b32 = _time(lambda: ctx.eval(params, precision=32), 5, flush, stream)
+    P = params.shape[0]
+    v_plain = Ps * cs.Ntot / t_plain
+    return {"plain_fp64": {"value": round(v_plain, 1), "unit": "atom-evals/s",
+                           "sample": f"{Ps} parameter sets x {cs.C} cells = {Ps * cs.C} launches"},
+            "batched_fp64_eval": {"value": round(P * cs.Ntot / t_b64, 1), "unit": "atom-evals/s"},
+            "batched_fp32_eval": {"value": round(P * cs.Ntot / t_b32, 1), "unit": "atom-evals/s"},
+            "batched_fp32_fitness": {"value": round(P * cs.Ntot / t_fit32, 1), "unit": "atom-evals/s"},
+            "speedup_fitness_vs_plain_fp64": round(P * cs.Ntot / t_fit32 / v_plain, 1)}
+
+
+def bench_uneven(dev, flush, stream):
+    """Uneven batch: P = 1000 x C = 500 cells of 8..512 atoms (thread-block clusters for large cells)."""
+    import torch
+
+    from paper_1909_11474_gb300 import binding
+    from paper_1909_11474_gb300 import inputs as I
+    w = I.workload_uneven()
+    cs = w["configs"]
+    ctx = binding.Context(dev.index or 0)
+    ctx.build_neighbors(cs.atom_off, torch.tensor(cs.pos, device=dev), torch.tensor(cs.box, device=dev))
+    tg = _targets_from_fp64(ctx, w, cs, dev)
+    params = torch.tensor(w["params"], device=dev)
+    t32 = _time(lambda: ctx.fitness(params, tg, precision=32), 3, flush, stream)
+    t64 = _time(lambda: ctx.fitness(params, tg, precision=64), 1, flush, stream, warmup=1)
+    P = len(w["params"])
+    return {"workload": "P=1000 x C=500 cells of 7..512 atoms", "atoms": cs.Ntot,
+            "fp32": {"value": round(P * cs.Ntot / t32, 1), "unit": "atom-evals/s", "ms": round(1e3 * t32, 3),
+                     "fitness_evals_per_s": round(P / t32, 1)},
+            "fp64": {"value": round(P * cs.Ntot / t64, 1), "unit": "atom-evals/s", "ms": round(1e3 * t64, 3)}}
+
+
+def bench_md(dev, flush, stream, steps):
+    """MD-scale force call: 512,000 atoms, cell-list rebuild + E/F/W per call."""
+    import torch
+
+    from paper_1909_11474_gb300 import binding
+    from paper_1909_11474_gb300 import inputs as I
+    w = I.workload_md()
+    cs = w["configs"]
+    ctx = binding.Context(dev.index or 0)
+    pos = torch.tensor(cs.pos, device=dev)
+    N = cs.Ntot
+    out32 = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty((N, 3), dtype=torch.float32, device=dev),
+             torch.empty(6, dtype=torch.float64, device=dev))
+    out64 = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty((N, 3), dtype=torch.float64, device=dev),
+             torch.empty(6, dtype=torch.float64, device=dev))
+    t32 = _time(lambda: ctx.md_force(pos, cs.box[0], w["params"][0], precision=32, out=out32), steps, flush, stream)
+    t64 = _time(lambda: ctx.md_force(pos, cs.box[0], w["params"][0], precision=64, out=out64), steps, flush, stream)
+    return {"workload": "40^3 conventional cells = 512,000 atoms, sigma = 0.08 A", "unit": "atom-steps/s",
+            "fp32": {"value": round(N / t32, 1), "ms": round(1e3 * t32, 4)},
+            "fp64": {"value": round(N / t64, 1), "ms": round(1e3 * t64, 4)}}
 
 
 def cpu_baseline(w, tg_host, budget_s=15.0):
@@ -354,6 +470,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-pairs", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="main step only (no per-row measurements)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -89,7 +89,10 @@ typedef struct {
  * Entries are kept in ascending (j, n0, n1, n2) order. The call also builds the parameter-independent
  * geometry cache (bond lengths, unit vectors, f_C and f_C' of Eq. 9, bond-angle cosines) in FP64,
  * stored in FP32 and FP64, and the evaluation schedule. It copies pos/box into the context (the
- * caller's buffers are not referenced afterwards) and synchronises `stream` before returning.
+ * caller's buffers are not referenced after the call returns). It synchronises `stream` once, to
+ * read the neighbour counts back, and returns with the geometry kernels enqueued on `stream`; a
+ * rebuild of configurations of the same sizes whose neighbour counts are all unchanged reuses the
+ * previous schedule.
  * R1 < R2 (Eq. 9; Sec. II.B uses R1 = 2.8, R2 = 3.2). 1 <= max_nbr <= 32 bounds the entries kept
  * per atom; an atom with more sets TERSOFF_STATUS_NBR_OVERFLOW and the call returns
  * TERSOFF_E_NBR_OVERFLOW. Positions or boxes that are not finite return TERSOFF_E_NONFINITE. */

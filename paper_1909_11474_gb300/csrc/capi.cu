@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/tersoff.h: context, neighbour build, batch planning and the
 // stream-ordered evaluation calls. Host code only; kernels live in the other translation units.
 #include <algorithm>
+#include <iterator>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -160,6 +161,8 @@ void tersoff_destroy(tersoff_ctx *ctx) {
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_Ui, &c.md_boxd};
   for (auto *b : bufs) b->release();
+  c.hp_stage.release();
+  if (c.stage_event) cudaEventDestroy(c.stage_event);
   delete ctx;
 }
 
@@ -179,35 +182,50 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
                             int32_t max_nbr, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
+  const bool was_built = c.built;
   c.built = false;
-  c.plan32 = tsf::BatchPlan();
-  c.plan64 = tsf::BatchPlan();
   if (!cfg || !cfg->atom_off || !cfg->pos || !cfg->box) return fail(ctx, TERSOFF_E_ARG, "null configuration pointer%s");
   if (cfg->C < 1) return fail(ctx, TERSOFF_E_ARG, "C must be >= 1%s");
   if (!(R1 > 0.0 && R2 > R1 && std::isfinite(R2))) return fail(ctx, TERSOFF_E_ARG, "need 0 < R1 < R2%s");
   if (max_nbr < 1 || max_nbr > 32) return fail(ctx, TERSOFF_E_ARG, "max_nbr must be in [1, 32]%s");
   const int C = cfg->C;
-  std::vector<int> off(cfg->atom_off, cfg->atom_off + C + 1);
-  if (off[0] != 0) return fail(ctx, TERSOFF_E_ARG, "atom_off[0] must be 0%s");
+  if (cfg->atom_off[0] != 0) return fail(ctx, TERSOFF_E_ARG, "atom_off[0] must be 0%s");
   for (int k = 0; k < C; ++k) {
-    const int n = off[k + 1] - off[k];
+    const int n = cfg->atom_off[k + 1] - cfg->atom_off[k];
     if (n < 1 || n > 1024) return fail(ctx, TERSOFF_E_ARG, "every configuration needs 1..1024 atoms%s");
   }
   cudaSetDevice(c.device);
   cudaStream_t s = S(stream);
-  const int64_t N = off[C];
+  const int64_t N = cfg->atom_off[C];
   const int M = max_nbr;
+  // the atom table (and the plans, if every neighbour count turns out unchanged) of the previous
+  // build are reused when this build has the same configuration sizes, cutoffs and list width
+  const bool same_layout = was_built && c.C == C && c.M == M && c.R1 == R1 && c.R2 == R2 &&
+                           (int64_t)c.h_atom_off.size() == C + 1 &&
+                           std::equal(c.h_atom_off.begin(), c.h_atom_off.end(), cfg->atom_off);
+  // the pinned staging buffer is reused: wait for the uploads of the previous build to finish
+  if (c.stage_event) TSF_CUDA(cudaEventSynchronize(c.stage_event));
+  else TSF_CUDA(cudaEventCreateWithFlags(&c.stage_event, cudaEventDisableTiming));
   c.C = C;
   c.Ntot = N;
   c.M = M;
   c.R1 = R1;
   c.R2 = R2;
-  c.h_atom_off = off;
-  std::vector<int> cfgidx(N);
-  for (int k = 0; k < C; ++k)
-    for (int i = off[k]; i < off[k + 1]; ++i) cfgidx[i] = k;
-  TSF_CUDA(c.atom_off.ensure((C + 1) * sizeof(int)));
-  TSF_CUDA(c.atom_cfg.ensure(N * sizeof(int)));
+  TSF_CUDA(c.hp_stage.ensure((size_t)(2 * N + C + 8) * sizeof(int)));
+  int *hp = c.hp_stage.as<int>();
+  if (!same_layout) {
+    c.h_atom_off.assign(cfg->atom_off, cfg->atom_off + C + 1);
+    c.plan32 = tsf::BatchPlan();
+    c.plan64 = tsf::BatchPlan();
+    TSF_CUDA(c.atom_off.ensure((C + 1) * sizeof(int)));
+    TSF_CUDA(c.atom_cfg.ensure(N * sizeof(int)));
+    int *h_off = hp, *h_cfg = hp + (C + 1);
+    std::copy(cfg->atom_off, cfg->atom_off + C + 1, h_off);
+    for (int k = 0; k < C; ++k)
+      for (int i = cfg->atom_off[k]; i < cfg->atom_off[k + 1]; ++i) h_cfg[i] = k;
+    TSF_CUDA(cudaMemcpyAsync(c.atom_off.p, h_off, (C + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    TSF_CUDA(cudaMemcpyAsync(c.atom_cfg.p, h_cfg, N * sizeof(int), cudaMemcpyHostToDevice, s));
+  }
   TSF_CUDA(c.pos.ensure(N * 3 * sizeof(double)));
   TSF_CUDA(c.pos32.ensure(N * sizeof(float4)));
   TSF_CUDA(c.box.ensure((size_t)C * 9 * sizeof(double)));
@@ -217,8 +235,6 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.shift.ensure(N * M * sizeof(char4)));
   TSF_CUDA(c.boff.ensure((N + 1) * sizeof(int)));
   TSF_CUDA(c.poff.ensure((N + 1) * sizeof(int)));
-  TSF_CUDA(cudaMemcpyAsync(c.atom_off.p, off.data(), (C + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-  TSF_CUDA(cudaMemcpyAsync(c.atom_cfg.p, cfgidx.data(), N * sizeof(int), cudaMemcpyHostToDevice, s));
   TSF_CUDA(cudaMemcpyAsync(c.pos.p, cfg->pos, N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   TSF_CUDA(cudaMemcpyAsync(c.box.p, cfg->box, (size_t)C * 9 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
@@ -228,28 +244,43 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(tsf::launch_neighbors_batch(N, c.atom_off.as<int>(), c.atom_cfg.as<int>(), c.pos.as<double>(),
                                        c.pos32.as<float4>(), c.box.as<double>(), c.boxinv.as<double>(),
                                        R2, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), st, s));
-  c.h_cnt.resize(N);
-  unsigned hst = 0;
-  TSF_CUDA(cudaMemcpyAsync(c.h_cnt.data(), c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, s));
-  TSF_CUDA(cudaMemcpyAsync(&hst, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  // one synchronisation: neighbour counts and status back to pinned host memory
+  int *h_cnt = hp;
+  unsigned *h_st = reinterpret_cast<unsigned *>(hp + N);
+  TSF_CUDA(cudaMemcpyAsync(h_cnt, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, s));
+  TSF_CUDA(cudaMemcpyAsync(h_st, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   TSF_CUDA(cudaStreamSynchronize(s));
+  const unsigned hst = *h_st;
   if (hst & TERSOFF_STATUS_NONFINITE) return fail(ctx, TERSOFF_E_NONFINITE, "non-finite positions or box%s");
   if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "an atom has more than max_nbr neighbours%s");
-  c.h_boff.assign(N + 1, 0);
-  c.h_poff.assign(N + 1, 0);
-  c.h_cfg_maxm.assign(C, 0);
-  int maxm = 0;
-  for (int64_t i = 0; i < N; ++i) {
-    const int m = c.h_cnt[i];
-    c.h_boff[i + 1] = c.h_boff[i] + m;
-    c.h_poff[i + 1] = c.h_poff[i] + tsf::pair_slots(m);
-    maxm = std::max(maxm, m);
-    int &cm = c.h_cfg_maxm[cfgidx[i]];
-    cm = std::max(cm, m);
+  const bool same_counts = same_layout && (int64_t)c.h_cnt.size() == N && std::equal(c.h_cnt.begin(), c.h_cnt.end(), h_cnt);
+  if (!same_counts) {
+    c.h_cnt.assign(h_cnt, h_cnt + N);
+    c.plan32 = tsf::BatchPlan();
+    c.plan64 = tsf::BatchPlan();
+    c.h_boff.assign(N + 1, 0);
+    c.h_poff.assign(N + 1, 0);
+    c.h_cfg_maxm.assign(C, 0);
+    int maxm = 0;
+    for (int k = 0; k < C; ++k)
+      for (int i = c.h_atom_off[k]; i < c.h_atom_off[k + 1]; ++i) {
+        const int m = c.h_cnt[i];
+        c.h_boff[i + 1] = c.h_boff[i] + m;
+        c.h_poff[i + 1] = c.h_poff[i] + tsf::pair_slots(m);
+        maxm = std::max(maxm, m);
+        c.h_cfg_maxm[k] = std::max(c.h_cfg_maxm[k], m);
+      }
+    c.max_m = maxm;
+    c.Btot = c.h_boff[N];
+    c.Qtot = c.h_poff[N];
+    TSF_CUDA(c.hp_stage.ensure((size_t)(2 * N + 2) * sizeof(int)));
+    int *h_off2 = c.hp_stage.as<int>();
+    std::copy(c.h_boff.begin(), c.h_boff.end(), h_off2);
+    std::copy(c.h_poff.begin(), c.h_poff.end(), h_off2 + (N + 1));
+    TSF_CUDA(cudaMemcpyAsync(c.boff.p, h_off2, (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    TSF_CUDA(cudaMemcpyAsync(c.poff.p, h_off2 + (N + 1), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   }
-  c.max_m = maxm;
-  c.Btot = c.h_boff[N];
-  c.Qtot = c.h_poff[N];
+  TSF_CUDA(cudaEventRecord(c.stage_event, s));
   const size_t B = std::max<int64_t>(1, c.Btot), Q = std::max<int64_t>(1, c.Qtot);
   TSF_CUDA(c.brev.ensure(B * sizeof(int)));
   TSF_CUDA(c.gA32.ensure(B * sizeof(float4)));
@@ -258,8 +289,6 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.gA64.ensure(B * sizeof(tsf::dvec4)));
   TSF_CUDA(c.gB64.ensure(B * sizeof(tsf::dvec4)));
   TSF_CUDA(c.gcos64.ensure(Q * sizeof(double)));
-  TSF_CUDA(cudaMemcpyAsync(c.boff.p, c.h_boff.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-  TSF_CUDA(cudaMemcpyAsync(c.poff.p, c.h_poff.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   TSF_CUDA(tsf::launch_reverse(N, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), c.boff.as<int>(),
                                c.brev.as<int>(), st, s));
   TSF_CUDA(tsf::launch_geometry(N, M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
@@ -267,9 +296,6 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
                                 c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), R1, R2,
                                 c.gA32.as<float4>(), c.gB32.as<float4>(), c.gcos32.as<float>(),
                                 c.gA64.as<tsf::dvec4>(), c.gB64.as<tsf::dvec4>(), c.gcos64.as<double>(), s));
-  TSF_CUDA(cudaMemcpyAsync(&hst, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  TSF_CUDA(cudaStreamSynchronize(s));
-  if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "reverse neighbour entry missing%s");
   if (c.max_m <= 8) {
     int rc = build_plan(ctx, 32);
     if (rc) return rc;

@@ -48,6 +48,30 @@ struct DevBuf {
   }
 };
 
+// Grow-only pinned host buffer (staging of host <-> device copies).
+struct PinnedBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaHostAlloc(&p, n, cudaHostAllocDefault);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T *as() const {
+    return static_cast<T *>(p);
+  }
+};
+
 // Geometry cache of a neighbour build: compressed bond list (CSR over atoms) with the
 // parameter-independent quantities of every bond and of every unordered pair of bonds of an atom.
 struct Geometry {
@@ -101,6 +125,8 @@ struct Ctx {
   int M = 0, max_m = 0;
   double R1 = 0, R2 = 0;
   std::vector<int> h_atom_off, h_cnt, h_boff, h_poff, h_cfg_maxm;
+  PinnedBuf hp_stage;   // pinned staging: atom table uploads, neighbour-count readback, offsets
+  cudaEvent_t stage_event = nullptr;   // recorded after the staging buffer's last upload
   DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, cnt, nbr, shift, boff, poff, brev;
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
   BatchPlan plan32, plan64;
