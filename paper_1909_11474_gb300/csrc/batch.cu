@@ -26,13 +26,27 @@ int batch_max_smem_optin() {
 }
 
 template <int MMAX, bool CLUSTER, int MINB, typename R>
-static cudaError_t launch_variant(const BatchParams &bp, int nitems, int cluster, size_t smem,
-                                  cudaStream_t s) {
+static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t smem, cudaStream_t s) {
   auto kern = batch_kernel<kPT, MMAX, CLUSTER, MINB, R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  const int ncta = CLUSTER ? cluster : 1;
+  // resident CTAs of this variant, rounded down to whole clusters
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int slots = std::max(1, per_sm * nsm / ncta);
+  // work items: each configuration's tiles split into chunks so that there are enough items
+  const int per_conf = std::min(bp.ntiles, std::max(1, (slots + nconf - 1) / nconf));
+  bp.nconf = nconf;
+  bp.chunk_tiles = (bp.ntiles + per_conf - 1) / per_conf;
+  bp.nchunks = (bp.ntiles + bp.chunk_tiles - 1) / bp.chunk_tiles;
+  const int nitems = nconf * bp.nchunks;
+  const int grid_clusters = std::min(nitems, slots);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nitems * bp.ntiles * (CLUSTER ? cluster : 1)));
+  cfg.gridDim = dim3((unsigned)(grid_clusters * ncta));
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;

@@ -330,6 +330,7 @@ struct BatchParams {
   const void *gA, *gB, *gcos;
   const CtaRec *recs;
   int ntiles;                      // parameter tiles: ceil(P / PT)
+  int nconf, nchunks, chunk_tiles; // work items: nconf configurations x nchunks chunks of tiles
   int mode;
   double *E;
   void *F;
@@ -364,10 +365,42 @@ __host__ __device__ inline size_t batch_smem(int nb, int nq, int nat) {
   return b;
 }
 
+// ---- TMA bulk copies into shared memory, completed on an mbarrier ----
+__device__ __forceinline__ void mbar_init(unsigned long long *mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *mbar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 1D bulk copy global -> shared (both addresses 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
+}
+constexpr unsigned kMbarSpins = 1u << 22;   // bound of a wait for one configuration's copies
+
+// Persistent work loop. The launch covers nconf configurations of one bucket, each split into
+// nchunks chunks of chunk_tiles parameter tiles; a CTA (or cluster) takes items
+// it = blockIdx/ncta, + gridDim/ncta, ... in a fixed order, stages the configuration's geometry once
+// (single-CTA launches: one TMA bulk copy per array, completed on an mbarrier) and runs its tiles.
 template <int PT, int MMAX, bool CLUSTER, int MINB, typename R>
 __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams a) {
   using R4 = typename Vec4<R>::T;
   extern __shared__ __align__(32) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long mbar;
+  __shared__ int abort_flag;
   R *stage = reinterpret_cast<R *>(smem);
   constexpr int APW = kWarp / PT;
 
@@ -379,232 +412,271 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     rank = cluster_ctarank();
     ncta = cluster_nctarank();
   }
-  // blockIdx.x = ((configuration in bucket) * ntiles + tile) * ncta + rank
-  const int item = blockIdx.x / ncta;
-  const int tile = item % a.ntiles;
-  const int rec0 = (item / a.ntiles) * ncta;
-  const CtaRec rec = a.recs[rec0 + rank];
-  const int c = rec.c;
-  const int p = tile * PT + pl;
-  const bool active = p < a.P;
-  PConsts<R> K;
-  {
-    const R4 *kc = reinterpret_cast<const R4 *>(a.consts) + 2 * (active ? p : a.P - 1);
-    const R4 k0 = kc[0], k1 = kc[1];
-    K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.alpha = k0.w;
-    K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
-  }
-
-  // atom slice of this CTA
-  const int nat = rec.nat, s0 = rec.s0, ns = rec.ns, cb0 = rec.cb0;
-  const int B0 = rec.B0, nb = rec.nb, Q0 = rec.Q0, nq = rec.nq;
-  R4 *sA = reinterpret_cast<R4 *>(stage + region0_elems<PT, CLUSTER, R>(nb));
-  R4 *sB = sA + nb;
-  R *sC = reinterpret_cast<R *>(sB + nb);
-  int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) +
-                                         ((size_t)nq * sizeof(R) + 31) / 32 * 32);
-  R4 *stF = reinterpret_cast<R4 *>(satom + ns);
   const bool fit = a.mode == kModeFitness;
-
-  // stage this slice's geometry, atom table and target forces in shared memory
-  {
-    const R4 *gA = reinterpret_cast<const R4 *>(a.gA) + B0;
-    const R4 *gB = reinterpret_cast<const R4 *>(a.gB) + B0;
-    const R *gC = reinterpret_cast<const R *>(a.gcos) + Q0;
-    for (int t = tid; t < nb; t += kThreads) {
-      sst(&sA[t], gA[t], 6);
-      sst(&sB[t], gB[t], 7);
+  if constexpr (!CLUSTER) {
+    if (tid == 0) {
+      mbar_init(&mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int t = tid; t < nq; t += kThreads) sst(&sC[t], gC[t], 8);
-    for (int t = tid; t < ns; t += kThreads) {
-      const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
-      sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0), 9);
-      if (fit) sst(&stF[t], reinterpret_cast<const R4 *>(a.tF4)[s0 + t], 10);
-    }
-  }
-  __syncthreads();
-
-  AtomAcc<R> acc;
-  acc.U = R(0);
-#pragma unroll
-  for (int k = 0; k < 6; ++k) acc.W[k] = R(0);
-
-  // ---- passes 1-2
-  for (int base = warp * APW; base < ns; base += kNW * APW) {
-    const int li = base + slot;
-    const bool valid = li < ns;
-    int4 at = make_int4(0, 0, 0, 0);
-    if (valid) at = sld(&satom[li], 11);
-    const int m = at.z;
-    if constexpr (APW == 1) {
-      if (m > MMAX) {
-        if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
-        continue;
-      }
-      atom_forward_dispatch<PT, MMAX, true, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
-    } else {
-      const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
-      const bool uniform = __all_sync(0xffffffffu, m == Mw);
-      if (Mw > MMAX) {
-        if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
-        continue;
-      }
-      if (uniform)
-        atom_forward_dispatch<PT, MMAX, true, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
-      else
-        atom_forward_dispatch<PT, MMAX, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
-    }
-  }
-  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
-
-  // ---- pass 3: F_i = sum_j (P_ij - P_ji)
-  R sf = R(0), sF2 = R(0), sT = R(0);
-  const uint8_t mask = fit ? a.tmask[c] : 0;
-  unsigned peer_stage[kMaxCluster];
-  int peer_b0[kMaxCluster + 1];
-  if constexpr (CLUSTER) {
-    const unsigned own = smem_addr(stage);
-    for (unsigned r = 0; r < ncta; ++r) {
-      peer_stage[r] = map_to_rank(own, r);
-      peer_b0[r] = a.recs[rec0 + r].B0 - cb0;
-    }
-    peer_b0[ncta] = a.recs[rec0 + ncta - 1].B0 + a.recs[rec0 + ncta - 1].nb - cb0;
-  }
-  for (int base = warp * APW; base < ns; base += kNW * APW) {
-    const int li = base + slot;
-    if (li >= ns) continue;
-    const int4 at = sld(&satom[li], 12);
-    const int m = at.z, lb = at.x;
-    R Fx = R(0), Fy = R(0), Fz = R(0);
-    for (int e = 0; e < m; ++e) {
-      const R *st = stage + (size_t)(lb + e) * 3 * PT + pl;
-      Fx += sld(&st[0], 13);
-      Fy += sld(&st[PT], 13);
-      Fz += sld(&st[2 * PT], 13);
-      int rb;  // configuration-local bond index of the reverse entry
-      if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sld(&sB[lb + e].w, 14)) & 0xffff;
-      else rb = (int)sld(&sB[lb + e].w, 14) & 0xffff;
-      if constexpr (CLUSTER) {
-        unsigned r = 0;
-        while (r + 1 < ncta && rb >= peer_b0[r + 1]) ++r;
-        // a reverse bond outside the configuration's bond range is an inconsistent schedule: flag it
-        // and skip the peer read rather than touch another CTA's shared memory out of range
-        if (rb < peer_b0[r] || rb >= peer_b0[r + 1]) {
-          set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
-#ifdef TSF_DEBUG_BOUNDS
-          if (atomicCAS(&tsf_dbg[0], 0u, 1u) == 0u) {
-            tsf_dbg[1] = 21;
-            tsf_dbg[2] = (unsigned)rb;
-            tsf_dbg[3] = (unsigned)peer_b0[ncta];
-          }
-#endif
-          continue;
-        }
-        const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * 3 * PT + pl) * sizeof(R));
-        Fx -= ld_cluster(addr, R(0));
-        Fy -= ld_cluster(addr + PT * sizeof(R), R(0));
-        Fz -= ld_cluster(addr + 2 * PT * sizeof(R), R(0));
-      } else {
-        const R *sr = stage + (size_t)(rb + cb0 - B0) * 3 * PT + pl;
-        Fx -= sld(&sr[0], 15);
-        Fy -= sld(&sr[PT], 15);
-        Fz -= sld(&sr[2 * PT], 15);
-      }
-    }
-    sF2 += Fx * Fx + Fy * Fy + Fz * Fz;
-    const int i = s0 + li;
-    if (a.mode == kModeEval) {
-      if (active && a.F) {
-        const size_t o = ((size_t)p * a.Ntot + i) * 3;
-        R *F = reinterpret_cast<R *>(a.F);
-        F[o] = Fx;
-        F[o + 1] = Fy;
-        F[o + 2] = Fz;
-      }
-    } else if (mask & 4) {
-      const R4 t = sld(&stF[li], 16);
-      const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
-      sf += ex * ex + ey * ey + ez * ez;
-      sT += t.w;
-    }
-  }
-
-  // ---- reductions: over atom slots (shuffles), warps (shared memory, fixed order), cluster ranks
-  R v[kNRed];
-  v[0] = acc.U;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) v[1 + k] = acc.W[k];
-  v[7] = sf;
-  v[8] = sF2;
-  v[9] = sT;
-#pragma unroll
-  for (int k = 0; k < kNRed; ++k) v[k] = sum_over_atom_slots<PT>(v[k]);
-  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();   // stages no longer read
-  R *red = stage;                                   // [kNW][kNRed][PT]
-  R *tot = stage + kNW * kNRed * PT;                // [kMaxCluster][kNRed][PT] (rank 0 collects)
-  if (slot == 0) {
-#pragma unroll
-    for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PT + pl], v[k], 17);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < kNRed * PT; idx += kThreads) {
-    R t = R(0);
-#pragma unroll
-    for (int w = 0; w < kNW; ++w) t += sld(&red[w * kNRed * PT + idx], 18);
-    if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(tot + rank * kNRed * PT + idx), 0), t);
-    else sst(&tot[idx], t, 19);
-  }
-  if constexpr (CLUSTER) {
-    cluster_sync_all();
-    if (rank != 0) return;
-  } else {
     __syncthreads();
   }
+  unsigned phase = 0;
+  const int nitems = a.nconf * a.nchunks;
+  for (int it = blockIdx.x / (int)ncta; it < nitems; it += gridDim.x / ncta) {
+    const int ci = it / a.nchunks, chunk = it % a.nchunks;
+    const int tile0 = chunk * a.chunk_tiles;
+    const int tile1 = min(a.ntiles, tile0 + a.chunk_tiles);
+    const int rec0 = ci * (int)ncta;
+    const CtaRec rec = a.recs[rec0 + rank];
+    const int c = rec.c;
 
-  if (tid < PT) {
-    const int pp = tile * PT + tid;
-    double q[kNRed];
-#pragma unroll
-    for (int k = 0; k < kNRed; ++k) {
-      double s = 0.0;
-      for (unsigned r = 0; r < ncta; ++r) s += (double)sld(&tot[(r * kNRed + k) * PT + tid], 20);
-      q[k] = s;
-    }
-    if (pp < a.P) {
-      if (a.mode == kModeEval) {
-        if (a.E) a.E[(size_t)pp * a.C + c] = q[0];
-        if (a.W)
-          for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = q[1 + k];
-      } else {
-        const double invN = 1.0 / (double)nat;
-        bool finite = isfinite(q[0]) && isfinite(q[8]);
-        for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);
-        double se = 0.0, sv = 0.0, sfv = 0.0;
-        if (mask & 1) {
-          const double d = q[0] * invN - a.tE[c];
-          se = d * d;
-        }
-        if (mask & 2)
-          for (int k = 0; k < 6; ++k) {
-            const double d = q[1 + k] * invN - a.tW[c * 6 + k];
-            sv += d * d;
+    // atom slice of this CTA
+    const int nat = rec.nat, s0 = rec.s0, ns = rec.ns, cb0 = rec.cb0;
+    const int B0 = rec.B0, nb = rec.nb, Q0 = rec.Q0, nq = rec.nq;
+    R4 *sA = reinterpret_cast<R4 *>(stage + region0_elems<PT, CLUSTER, R>(nb));
+    R4 *sB = sA + nb;
+    R *sC = reinterpret_cast<R *>(sB + nb);
+    int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) +
+                                           ((size_t)nq * sizeof(R) + 31) / 32 * 32);
+    R4 *stF = reinterpret_cast<R4 *>(satom + ns);
+
+    // stage this slice's geometry, atom table and target forces in shared memory
+    {
+      const R4 *gA = reinterpret_cast<const R4 *>(a.gA) + B0;
+      const R4 *gB = reinterpret_cast<const R4 *>(a.gB) + B0;
+      const R *gC = reinterpret_cast<const R *>(a.gcos) + Q0;
+      if constexpr (!CLUSTER) {
+        if (tid == 0) {
+          const unsigned bA = (unsigned)(nb * sizeof(R4)), bC = (unsigned)(nq * sizeof(R));
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_expect_tx(&mbar, 2 * bA + bC);
+          if (bA) {
+            bulk_g2s(sA, gA, bA, &mbar);
+            bulk_g2s(sB, gB, bA, &mbar);
           }
-        if (mask & 4) sfv = q[7];
-        if (!finite) se = sv = sfv = __longlong_as_double(0x7ff8000000000000ll);
-        double *o = a.part + ((size_t)pp * a.C + c) * 3;
-        o[0] = se;
-        o[1] = sv;
-        o[2] = sfv;
+          if (bC) bulk_g2s(sC, gC, bC, &mbar);
+        }
+      } else {
+        for (int t = tid; t < nb; t += kThreads) {
+          sst(&sA[t], gA[t], 6);
+          sst(&sB[t], gB[t], 7);
+        }
+        for (int t = tid; t < nq; t += kThreads) sst(&sC[t], gC[t], 8);
+      }
+      for (int t = tid; t < ns; t += kThreads) {
+        const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
+        sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0), 9);
+        if (fit) sst(&stF[t], reinterpret_cast<const R4 *>(a.tF4)[s0 + t], 10);
+      }
+      if constexpr (!CLUSTER) {
+        // thread 0 waits (bounded) for the bulk copies; the barrier below publishes them
+        if (tid == 0) {
+          bool done = false;
+          for (unsigned k = 0; k < kMbarSpins && !done; ++k) done = mbar_try_wait(&mbar, phase);
+          abort_flag = done ? 0 : 1;
+          if (!done) {
+            set_status(a.status, TERSOFF_STATUS_TIMEOUT);
+            for (unsigned k = 0; k < kMbarSpins && !done; ++k) done = mbar_try_wait(&mbar, phase);
+          }
+        }
+        phase ^= 1u;
+        __syncthreads();
+        if (abort_flag) return;
+      } else {
+        __syncthreads();
       }
     }
-    if (fit && tile == 0 && tid == 0) {
-      double de = 0.0, dv = 0.0;
-      if (mask & 1) de = a.tE[c] * a.tE[c];
-      if (mask & 2)
-        for (int k = 0; k < 6; ++k) dv += a.tW[c * 6 + k] * a.tW[c * 6 + k];
-      a.dpart[c * 3 + 0] = de;
-      a.dpart[c * 3 + 1] = dv;
-      a.dpart[c * 3 + 2] = (mask & 4) ? q[9] : 0.0;
+    const uint8_t mask = fit ? a.tmask[c] : 0;
+    unsigned peer_stage[kMaxCluster];
+    int peer_b0[kMaxCluster + 1];
+    if constexpr (CLUSTER) {
+      const unsigned own = smem_addr(stage);
+      for (unsigned r = 0; r < ncta; ++r) {
+        peer_stage[r] = map_to_rank(own, r);
+        peer_b0[r] = a.recs[rec0 + r].B0 - cb0;
+      }
+      peer_b0[ncta] = a.recs[rec0 + ncta - 1].B0 + a.recs[rec0 + ncta - 1].nb - cb0;
+    }
+
+    for (int tile = tile0; tile < tile1; ++tile) {
+      const int p = tile * PT + pl;
+      const bool active = p < a.P;
+      PConsts<R> K;
+      {
+        const R4 *kc = reinterpret_cast<const R4 *>(a.consts) + 2 * (active ? p : a.P - 1);
+        const R4 k0 = kc[0], k1 = kc[1];
+        K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.alpha = k0.w;
+        K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
+      }
+      AtomAcc<R> acc;
+      acc.U = R(0);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc.W[k] = R(0);
+
+      // ---- passes 1-2
+      for (int base = warp * APW; base < ns; base += kNW * APW) {
+        const int li = base + slot;
+        const bool valid = li < ns;
+        int4 at = make_int4(0, 0, 0, 0);
+        if (valid) at = sld(&satom[li], 11);
+        const int m = at.z;
+        if constexpr (APW == 1) {
+          if (m > MMAX) {
+            if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
+            continue;
+          }
+          atom_forward_dispatch<PT, MMAX, true, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+        } else {
+          const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
+          const bool uniform = __all_sync(0xffffffffu, m == Mw);
+          if (Mw > MMAX) {
+            if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
+            continue;
+          }
+          if (uniform)
+            atom_forward_dispatch<PT, MMAX, true, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+          else
+            atom_forward_dispatch<PT, MMAX, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+        }
+      }
+      if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
+
+      // ---- pass 3: F_i = sum_j (P_ij - P_ji)
+      R sf = R(0), sF2 = R(0), sT = R(0);
+      for (int base = warp * APW; base < ns; base += kNW * APW) {
+        const int li = base + slot;
+        if (li >= ns) continue;
+        const int4 at = sld(&satom[li], 12);
+        const int m = at.z, lb = at.x;
+        R Fx = R(0), Fy = R(0), Fz = R(0);
+        for (int e = 0; e < m; ++e) {
+          const R *st = stage + (size_t)(lb + e) * 3 * PT + pl;
+          Fx += sld(&st[0], 13);
+          Fy += sld(&st[PT], 13);
+          Fz += sld(&st[2 * PT], 13);
+          int rb;  // configuration-local bond index of the reverse entry
+          if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sld(&sB[lb + e].w, 14)) & 0xffff;
+          else rb = (int)sld(&sB[lb + e].w, 14) & 0xffff;
+          if constexpr (CLUSTER) {
+            unsigned r = 0;
+            while (r + 1 < ncta && rb >= peer_b0[r + 1]) ++r;
+            // a reverse bond outside the configuration's bond range is an inconsistent schedule:
+            // flag it and skip the peer read rather than touch another CTA's shared memory
+            if (rb < peer_b0[r] || rb >= peer_b0[r + 1]) {
+              set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
+#ifdef TSF_DEBUG_BOUNDS
+              if (atomicCAS(&tsf_dbg[0], 0u, 1u) == 0u) {
+                tsf_dbg[1] = 21;
+                tsf_dbg[2] = (unsigned)rb;
+                tsf_dbg[3] = (unsigned)peer_b0[ncta];
+              }
+#endif
+              continue;
+            }
+            const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * 3 * PT + pl) * sizeof(R));
+            Fx -= ld_cluster(addr, R(0));
+            Fy -= ld_cluster(addr + PT * sizeof(R), R(0));
+            Fz -= ld_cluster(addr + 2 * PT * sizeof(R), R(0));
+          } else {
+            const R *sr = stage + (size_t)(rb + cb0 - B0) * 3 * PT + pl;
+            Fx -= sld(&sr[0], 15);
+            Fy -= sld(&sr[PT], 15);
+            Fz -= sld(&sr[2 * PT], 15);
+          }
+        }
+        sF2 += Fx * Fx + Fy * Fy + Fz * Fz;
+        const int i = s0 + li;
+        if (a.mode == kModeEval) {
+          if (active && a.F) {
+            const size_t o = ((size_t)p * a.Ntot + i) * 3;
+            R *F = reinterpret_cast<R *>(a.F);
+            F[o] = Fx;
+            F[o + 1] = Fy;
+            F[o + 2] = Fz;
+          }
+        } else if (mask & 4) {
+          const R4 t = sld(&stF[li], 16);
+          const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
+          sf += ex * ex + ey * ey + ez * ez;
+          sT += t.w;
+        }
+      }
+
+      // ---- reductions: over atom slots (shuffles), warps (shared memory, fixed order), ranks
+      R v[kNRed];
+      v[0] = acc.U;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) v[1 + k] = acc.W[k];
+      v[7] = sf;
+      v[8] = sF2;
+      v[9] = sT;
+#pragma unroll
+      for (int k = 0; k < kNRed; ++k) v[k] = sum_over_atom_slots<PT>(v[k]);
+      if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();   // stages no longer read
+      R *red = stage;                                   // [kNW][kNRed][PT]
+      R *tot = stage + kNW * kNRed * PT;                // [ranks][kNRed][PT] (rank 0 collects)
+      if (slot == 0) {
+#pragma unroll
+        for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PT + pl], v[k], 17);
+      }
+      __syncthreads();
+      for (int idx = tid; idx < kNRed * PT; idx += kThreads) {
+        R t = R(0);
+#pragma unroll
+        for (int w = 0; w < kNW; ++w) t += sld(&red[w * kNRed * PT + idx], 18);
+        if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(tot + rank * kNRed * PT + idx), 0), t);
+        else sst(&tot[idx], t, 19);
+      }
+      if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
+
+      if (rank == 0 && tid < PT) {
+        const int pp = tile * PT + tid;
+        double q[kNRed];
+#pragma unroll
+        for (int k = 0; k < kNRed; ++k) {
+          double s = 0.0;
+          for (unsigned r = 0; r < ncta; ++r) s += (double)sld(&tot[(r * kNRed + k) * PT + tid], 20);
+          q[k] = s;
+        }
+        if (pp < a.P) {
+          if (a.mode == kModeEval) {
+            if (a.E) a.E[(size_t)pp * a.C + c] = q[0];
+            if (a.W)
+              for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = q[1 + k];
+          } else {
+            const double invN = 1.0 / (double)nat;
+            bool finite = isfinite(q[0]) && isfinite(q[8]);
+            for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);
+            double se = 0.0, sv = 0.0, sfv = 0.0;
+            if (mask & 1) {
+              const double d = q[0] * invN - a.tE[c];
+              se = d * d;
+            }
+            if (mask & 2)
+              for (int k = 0; k < 6; ++k) {
+                const double d = q[1 + k] * invN - a.tW[c * 6 + k];
+                sv += d * d;
+              }
+            if (mask & 4) sfv = q[7];
+            if (!finite) se = sv = sfv = __longlong_as_double(0x7ff8000000000000ll);
+            double *o = a.part + ((size_t)pp * a.C + c) * 3;
+            o[0] = se;
+            o[1] = sv;
+            o[2] = sfv;
+          }
+        }
+        if (fit && tile == 0 && tid == 0) {
+          double de = 0.0, dv = 0.0;
+          if (mask & 1) de = a.tE[c] * a.tE[c];
+          if (mask & 2)
+            for (int k = 0; k < 6; ++k) dv += a.tW[c * 6 + k] * a.tW[c * 6 + k];
+          a.dpart[c * 3 + 0] = de;
+          a.dpart[c * 3 + 1] = dv;
+          a.dpart[c * 3 + 2] = (mask & 4) ? q[9] : 0.0;
+        }
+      }
+      // the next tile (or item) reuses the stage and, in rank 0, the collected totals
+      if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
     }
   }
 }
