@@ -295,7 +295,8 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
                                 c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
                                 c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), R1, R2,
                                 c.gA32.as<float4>(), c.gB32.as<float4>(), c.gcos32.as<float>(),
-                                c.gA64.as<tsf::dvec4>(), c.gB64.as<tsf::dvec4>(), c.gcos64.as<double>(), s));
+                                c.gA64.as<tsf::dvec4>(), c.gB64.as<tsf::dvec4>(), c.gcos64.as<double>(),
+                                tsf::pair_slots(std::min(c.max_m, M)), s));
   if (c.max_m <= 8) {
     int rc = build_plan(ctx, 32);
     if (rc) return rc;

@@ -154,7 +154,7 @@ cudaError_t launch_geometry(int64_t Ntot, int M, const int *atom_cfg, const int 
                             const double *box, const int *cnt, const int *nbr, const char4 *shift,
                             const int *boff, const int *poff, double R1, double R2, float4 *gA32,
                             float4 *gB32, float *gcos32, dvec4 *gA64, dvec4 *gB64,
-                            double *gcos64, cudaStream_t s);
+                            double *gcos64, int max_slots, cudaStream_t s);
 
 // batch.cu
 struct BatchOut {

@@ -50,17 +50,25 @@ __global__ void pos32_kernel(int64_t N, const double *__restrict__ pos, float4 *
   pos32[i] = make_float4((float)x, (float)y, (float)z, 0.f);
 }
 
-// One thread per atom i. For every atom j of the same configuration (ascending) the candidate
-// images are the integers n_k with |s_j - s_i + n_k| < R2 / gap_k (+ margin), found in FP32
-// fractional coordinates; each candidate is then decided by the exact FP64 test. Scanning j and n in
-// ascending order yields the canonical (j, n0, n1, n2) order directly.
+// Candidate image range of one (i, j) pair on one axis: integers n with |s_j - s_i + n| < rng.
+__device__ __forceinline__ void image_range(float ds, float rng, int &lo, int &hi) {
+  lo = (int)ceilf(-ds - rng);
+  hi = (int)floorf(-ds + rng);
+}
+
+// One warp per atom i; lane l tests atoms j = a0 + l, a0 + 32 + l, ... of the same configuration.
+// Candidate images are the integers n_k with |s_j - s_i + n_k| < R2 / gap_k (+ margin), found in FP32
+// fractional coordinates; each candidate is then decided by the exact FP64 test. The warp runs each
+// block of 32 j twice: first every lane counts its accepted entries, then an exclusive warp scan
+// gives each lane its output position, so entries land in ascending (j, n0, n1, n2) order.
 __global__ void __launch_bounds__(128) neighbors_batch_kernel(
     int64_t Ntot, const int *__restrict__ atom_off, const int *__restrict__ atom_cfg,
     const double *__restrict__ pos, const float4 *__restrict__ pos32,
     const double *__restrict__ box, const double *__restrict__ boxinv, double R2, int M,
     int *__restrict__ cnt_out, int *__restrict__ nbr, char4 *__restrict__ shift, unsigned *status) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= Ntot) return;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= Ntot) return;   // whole warps only
   const int c = atom_cfg[i];
   const int a0 = atom_off[c], a1 = atom_off[c + 1];
   double H[9];
@@ -78,34 +86,56 @@ __global__ void __launch_bounds__(128) neighbors_batch_kernel(
   const double xix = pos[3 * i], xiy = pos[3 * i + 1], xiz = pos[3 * i + 2];
   const float4 xi = pos32[i];
   int count = 0;
-  for (int j = a0; j < a1; ++j) {
-    const float4 xj = pos32[j];
-    float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
-    float s0 = dx * Hi[0] + dy * Hi[3] + dz * Hi[6];
-    float s1 = dx * Hi[1] + dy * Hi[4] + dz * Hi[7];
-    float s2 = dx * Hi[2] + dy * Hi[5] + dz * Hi[8];
-    int lo0 = (int)ceilf(-s0 - rng0), hi0 = (int)floorf(-s0 + rng0);
-    int lo1 = (int)ceilf(-s1 - rng1), hi1 = (int)floorf(-s1 + rng1);
-    int lo2 = (int)ceilf(-s2 - rng2), hi2 = (int)floorf(-s2 + rng2);
-    if (lo0 > hi0 || lo1 > hi1 || lo2 > hi2) continue;
-    const double xjx = pos[3 * j], xjy = pos[3 * j + 1], xjz = pos[3 * j + 2];
+  for (int jb = a0; jb < a1; jb += 32) {
+    const int j = jb + lane;
+    int lo0 = 1, hi0 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0;
+    double xjx = 0, xjy = 0, xjz = 0;
+    if (j < a1) {
+      const float4 xj = pos32[j];
+      const float dx = xj.x - xi.x, dy = xj.y - xi.y, dz = xj.z - xi.z;
+      image_range(dx * Hi[0] + dy * Hi[3] + dz * Hi[6], rng0, lo0, hi0);
+      image_range(dx * Hi[1] + dy * Hi[4] + dz * Hi[7], rng1, lo1, hi1);
+      image_range(dx * Hi[2] + dy * Hi[5] + dz * Hi[8], rng2, lo2, hi2);
+      xjx = pos[3 * j];
+      xjy = pos[3 * j + 1];
+      xjz = pos[3 * j + 2];
+    }
+    int mine = 0;
     for (int n0 = lo0; n0 <= hi0; ++n0)
       for (int n1 = lo1; n1 <= hi1; ++n1)
         for (int n2 = lo2; n2 <= hi2; ++n2) {
           if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
-          ExactPair e = exact_pair(xjx, xjy, xjz, xix, xiy, xiz, H, n0, n1, n2);
-          if (e.r2 < R2sq) {
-            if (count < M) {
-              nbr[i * M + count] = j;
-              shift[i * M + count] = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
-            }
-            ++count;
-          }
+          if (exact_pair(xjx, xjy, xjz, xix, xiy, xiz, H, n0, n1, n2).r2 < R2sq) ++mine;
         }
+    int incl = mine;   // inclusive warp scan of the per-lane counts
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (mine) {
+      int w = count + incl - mine;
+      for (int n0 = lo0; n0 <= hi0; ++n0)
+        for (int n1 = lo1; n1 <= hi1; ++n1)
+          for (int n2 = lo2; n2 <= hi2; ++n2) {
+            if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
+            if (exact_pair(xjx, xjy, xjz, xix, xiy, xiz, H, n0, n1, n2).r2 < R2sq) {
+              if (w < M) {
+                nbr[i * M + w] = j;
+                shift[i * M + w] = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
+              }
+              ++w;
+            }
+          }
+    }
+    count += total;
   }
-  cnt_out[i] = count;
-  if (count > M) set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
-  for (int e = count; e < M; ++e) {
+  if (lane == 0) {
+    cnt_out[i] = count;
+    if (count > M) set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+  }
+  for (int e = count + lane; e < M; e += 32) {
     nbr[i * M + e] = -1;
     shift[i * M + e] = make_char4(0, 0, 0, 0);
   }
@@ -113,31 +143,33 @@ __global__ void __launch_bounds__(128) neighbors_batch_kernel(
 
 // Reverse entry of every bond: entry (i; j, n) <-> (j; i, -n). The exact test is antisymmetric
 // (x_i - x_j = -(x_j - x_i) and t(-n) = -t(n) exactly), so the reverse entry always exists.
+// One thread per (atom, list slot).
 __global__ void reverse_kernel(int64_t Ntot, int M, const int *__restrict__ cnt,
                                const int *__restrict__ nbr, const char4 *__restrict__ shift,
                                const int *__restrict__ boff, int *__restrict__ brev,
                                unsigned *status) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / M;
+  const int e = (int)(t % M);
   if (i >= Ntot) return;
   const int m = min(cnt[i], M);
-  for (int e = 0; e < m; ++e) {
-    const int j = nbr[i * M + e];
-    const char4 n = shift[i * M + e];
-    const int mj = min(cnt[j], M);
-    int found = -1;
-    for (int f = 0; f < mj; ++f) {
-      const char4 q = shift[(int64_t)j * M + f];
-      if (nbr[(int64_t)j * M + f] == (int)i && q.x == -n.x && q.y == -n.y && q.z == -n.z) {
-        found = f;
-        break;
-      }
+  if (e >= m) return;
+  const int j = nbr[i * M + e];
+  const char4 n = shift[i * M + e];
+  const int mj = min(cnt[j], M);
+  int found = -1;
+  for (int f = 0; f < mj; ++f) {
+    const char4 q = shift[(int64_t)j * M + f];
+    if (nbr[(int64_t)j * M + f] == (int)i && q.x == -n.x && q.y == -n.y && q.z == -n.z) {
+      found = f;
+      break;
     }
-    if (found < 0) {
-      set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
-      found = 0;
-    }
-    brev[boff[i] + e] = boff[j] + found;
   }
+  if (found < 0) {
+    set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+    found = 0;
+  }
+  brev[boff[i] + e] = boff[j] + found;
 }
 
 // f_C of Eq. 9 and its derivative.
@@ -157,58 +189,71 @@ __device__ __forceinline__ void cutoff_fc(double r, double R1, double R2, double
 
 // Per bond: unit vector, r, 1/r, f_C, f_C' and, packed into one int (rev | j << 16), the
 // configuration-local indices of the reverse bond and of the neighbour atom (stored in the 4th slot:
-// as a double, or as the bit pattern of the int in the FP32 record);
-// per unordered pair (e < f) of an atom's bonds: cos theta (each atom's row padded to 4 slots). Computed in FP64 from the same d as the
-// membership test, stored in FP64 and rounded to FP32.
-__global__ void geometry_kernel(int64_t Ntot, int M, const int *__restrict__ atom_cfg,
-                                const int *__restrict__ atom_off, const int *__restrict__ brev,
-                                const double *__restrict__ pos, const double *__restrict__ box,
-                                const int *__restrict__ cnt, const int *__restrict__ nbr,
-                                const char4 *__restrict__ shift, const int *__restrict__ boff,
-                                const int *__restrict__ poff, double R1, double R2,
-                                float4 *__restrict__ gA32, float4 *__restrict__ gB32,
-                                float *__restrict__ gcos32, dvec4 *__restrict__ gA64,
-                                dvec4 *__restrict__ gB64, double *__restrict__ gcos64) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// as a double, or as the bit pattern of the int in the FP32 record). Computed in FP64 from the same
+// d as the membership test, stored in FP64 and rounded to FP32. One thread per (atom, list slot).
+__global__ void geometry_bond_kernel(int64_t Ntot, int M, const int *__restrict__ atom_cfg,
+                                     const int *__restrict__ atom_off, const int *__restrict__ brev,
+                                     const double *__restrict__ pos, const double *__restrict__ box,
+                                     const int *__restrict__ cnt, const int *__restrict__ nbr,
+                                     const char4 *__restrict__ shift, const int *__restrict__ boff,
+                                     double R1, double R2, float4 *__restrict__ gA32,
+                                     float4 *__restrict__ gB32, dvec4 *__restrict__ gA64,
+                                     dvec4 *__restrict__ gB64) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / M;
+  const int e = (int)(t % M);
   if (i >= Ntot) return;
+  if (e >= min(cnt[i], M)) return;
   const int c = atom_cfg[i];
   double H[9];
+#pragma unroll
   for (int k = 0; k < 9; ++k) H[k] = box[9 * c + k];
-  const double xix = pos[3 * i], xiy = pos[3 * i + 1], xiz = pos[3 * i + 2];
-  const int m = min(cnt[i], M);
-  const int b0 = boff[i];
+  const int b = boff[i] + e;
   const int cb0 = boff[atom_off[c]];   // first bond of the configuration
-  for (int e = 0; e < m; ++e) {
-    const int j = nbr[i * M + e];
-    // packed: configuration-local index of the reverse bond (bits 0-15) and of atom j (bits 16-31)
-    const int rl = (brev[b0 + e] - cb0) | ((j - atom_off[c]) << 16);
-    const char4 n = shift[i * M + e];
-    ExactPair p = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], xix, xiy, xiz, H, n.x, n.y, n.z);
-    const double r = sqrt(p.r2);
-    const double ir = 1.0 / r;
-    double fc, fcp;
-    cutoff_fc(r, R1, R2, fc, fcp);
-    const double ux = p.dx * ir, uy = p.dy * ir, uz = p.dz * ir;
-    gA64[b0 + e] = make_dvec4(ux, uy, uz, r);
-    gB64[b0 + e] = make_dvec4(ir, fc, fcp, (double)rl);
-    gA32[b0 + e] = make_float4((float)ux, (float)uy, (float)uz, (float)r);
-    gB32[b0 + e] = make_float4((float)ir, (float)fc, (float)fcp, __int_as_float(rl));
+  const int j = nbr[i * M + e];
+  // packed: configuration-local index of the reverse bond (bits 0-15) and of atom j (bits 16-31)
+  const int rl = (brev[b] - cb0) | ((j - atom_off[c]) << 16);
+  const char4 n = shift[i * M + e];
+  ExactPair p = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], pos[3 * i], pos[3 * i + 1],
+                           pos[3 * i + 2], H, n.x, n.y, n.z);
+  const double r = sqrt(p.r2);
+  const double ir = 1.0 / r;
+  double fc, fcp;
+  cutoff_fc(r, R1, R2, fc, fcp);
+  const double ux = p.dx * ir, uy = p.dy * ir, uz = p.dz * ir;
+  gA64[b] = make_dvec4(ux, uy, uz, r);
+  gB64[b] = make_dvec4(ir, fc, fcp, (double)rl);
+  gA32[b] = make_float4((float)ux, (float)uy, (float)uz, (float)r);
+  gB32[b] = make_float4((float)ir, (float)fc, (float)fcp, __int_as_float(rl));
+}
+
+// Per unordered pair (e < f) of an atom's bonds: cos theta from the FP64 unit vectors; each atom's
+// row is padded to 4 slots with zeros. One thread per (atom, pair slot).
+__global__ void geometry_pair_kernel(int64_t Ntot, int slots, const int *__restrict__ cnt, int M,
+                                     const int *__restrict__ boff, const int *__restrict__ poff,
+                                     const dvec4 *__restrict__ gA64, float *__restrict__ gcos32,
+                                     double *__restrict__ gcos64) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / slots;
+  const int q = (int)(t % slots);
+  if (i >= Ntot) return;
+  const int q0 = poff[i], nslot = poff[i + 1] - q0;
+  if (q >= nslot) return;
+  const int m = min(cnt[i], M);
+  // slot q -> (e, f), e < f, row-major over e
+  int e = 0, rem = q;
+  while (e < m && rem >= m - 1 - e) {
+    rem -= m - 1 - e;
+    ++e;
   }
-  int q = poff[i];
-  for (int e = 0; e < m; ++e) {
-    const dvec4 ue = gA64[b0 + e];
-    for (int f = e + 1; f < m; ++f) {
-      const dvec4 uf = gA64[b0 + f];
-      const double cs = ue.x * uf.x + ue.y * uf.y + ue.z * uf.z;
-      gcos64[q] = cs;
-      gcos32[q] = (float)cs;
-      ++q;
-    }
+  double cs = 0.0;
+  if (e < m - 1) {
+    const int f = e + 1 + rem;
+    const dvec4 ue = gA64[boff[i] + e], uf = gA64[boff[i] + f];
+    cs = ue.x * uf.x + ue.y * uf.y + ue.z * uf.z;
   }
-  for (; q < poff[i + 1]; ++q) {   // padding slots of the 16-byte aligned pair rows
-    gcos64[q] = 0.0;
-    gcos32[q] = 0.f;
-  }
+  gcos64[q0 + q] = cs;
+  gcos32[q0 + q] = (float)cs;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -229,14 +274,14 @@ cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int 
                                    const double *boxinv, double R2, int M, int *cnt, int *nbr,
                                    char4 *shift, unsigned *status, cudaStream_t s) {
   if (Ntot == 0) return cudaSuccess;
-  neighbors_batch_kernel<<<nblk(Ntot, 128), 128, 0, s>>>(Ntot, atom_off, atom_cfg, pos, pos32, box,
-                                                         boxinv, R2, M, cnt, nbr, shift, status);
+  neighbors_batch_kernel<<<nblk(Ntot * 32, 128), 128, 0, s>>>(Ntot, atom_off, atom_cfg, pos, pos32, box,
+                                                              boxinv, R2, M, cnt, nbr, shift, status);
   return cudaGetLastError();
 }
 cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,
                            const int *boff, int *brev, unsigned *status, cudaStream_t s) {
   if (Ntot == 0) return cudaSuccess;
-  reverse_kernel<<<nblk(Ntot, 128), 128, 0, s>>>(Ntot, M, cnt, nbr, shift, boff, brev, status);
+  reverse_kernel<<<nblk(Ntot * M, 256), 256, 0, s>>>(Ntot, M, cnt, nbr, shift, boff, brev, status);
   return cudaGetLastError();
 }
 cudaError_t launch_geometry(int64_t Ntot, int M, const int *atom_cfg, const int *atom_off,
@@ -244,10 +289,13 @@ cudaError_t launch_geometry(int64_t Ntot, int M, const int *atom_cfg, const int 
                             const double *box, const int *cnt, const int *nbr, const char4 *shift,
                             const int *boff, const int *poff, double R1, double R2, float4 *gA32,
                             float4 *gB32, float *gcos32, dvec4 *gA64, dvec4 *gB64,
-                            double *gcos64, cudaStream_t s) {
+                            double *gcos64, int max_slots, cudaStream_t s) {
   if (Ntot == 0) return cudaSuccess;
-  geometry_kernel<<<nblk(Ntot, 128), 128, 0, s>>>(Ntot, M, atom_cfg, atom_off, brev, pos, box, cnt, nbr, shift, boff,
-                                                  poff, R1, R2, gA32, gB32, gcos32, gA64, gB64, gcos64);
+  geometry_bond_kernel<<<nblk(Ntot * M, 256), 256, 0, s>>>(Ntot, M, atom_cfg, atom_off, brev, pos, box, cnt,
+                                                           nbr, shift, boff, R1, R2, gA32, gB32, gA64, gB64);
+  if (max_slots > 0)
+    geometry_pair_kernel<<<nblk(Ntot * max_slots, 256), 256, 0, s>>>(Ntot, max_slots, cnt, M, boff, poff, gA64,
+                                                                      gcos32, gcos64);
   return cudaGetLastError();
 }
 
