@@ -26,7 +26,8 @@ int batch_max_smem_optin() {
 }
 
 template <int MMAX, bool CLUSTER, int MINB, typename R>
-static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t smem, cudaStream_t s) {
+static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t smem, bool uniform,
+                                  cudaStream_t s) {
   auto kern = batch_kernel<kPT, MMAX, CLUSTER, MINB, R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -38,8 +39,11 @@ static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
   if (e != cudaSuccess) return e;
   const int slots = std::max(1, per_sm * nsm / ncta);
-  // work items: each configuration's tiles split into chunks so that there are enough items
-  const int per_conf = std::min(bp.ntiles, std::max(1, (slots + nconf - 1) / nconf));
+  // work items: whole configurations when they are all alike and fit in one wave of CTAs (the
+  // geometry is then staged once per configuration); otherwise each configuration's tiles are split
+  // into chunks so that about four items per CTA slot balance the dynamically claimed work
+  int per_conf = 1;
+  if (!(uniform && nconf <= slots)) per_conf = std::min(bp.ntiles, std::max(1, (4 * slots + nconf - 1) / nconf));
   bp.nconf = nconf;
   bp.chunk_tiles = (bp.ntiles + per_conf - 1) / per_conf;
   bp.nchunks = (bp.ntiles + bp.chunk_tiles - 1) / bp.chunk_tiles;
@@ -105,20 +109,24 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.part = out.part;
   bp.dpart = out.dpart;
   bp.status = ctx.status.as<unsigned>();
+  cudaError_t ez = cudaMemsetAsync(out.counters, 0, plan.buckets.size() * sizeof(int), s);
+  if (ez != cudaSuccess) return ez;
+  int bi = 0;
   for (const Bucket &b : plan.buckets) {
+    bp.counter = out.counters + bi++;
     if (b.nitems == 0) continue;
     bp.recs = plan.items.as<CtaRec>() + b.item_off;
     cudaError_t e = cudaSuccess;
     const bool cl = b.cluster > 1;
     if (!f64) {
-      if (!cl && b.mmax <= 4) e = launch_variant<4, false, 2, float>(bp, b.nitems, 1, b.smem, s);
-      else if (!cl && b.mmax <= 6) e = launch_variant<6, false, 1, float>(bp, b.nitems, 1, b.smem, s);
-      else if (!cl) e = launch_variant<8, false, 1, float>(bp, b.nitems, 1, b.smem, s);
-      else if (b.mmax <= 6) e = launch_variant<6, true, 1, float>(bp, b.nitems, b.cluster, b.smem, s);
-      else e = launch_variant<8, true, 1, float>(bp, b.nitems, b.cluster, b.smem, s);
+      if (!cl && b.mmax <= 4) e = launch_variant<4, false, 2, float>(bp, b.nitems, 1, b.smem, b.uniform, s);
+      else if (!cl && b.mmax <= 6) e = launch_variant<6, false, 1, float>(bp, b.nitems, 1, b.smem, b.uniform, s);
+      else if (!cl) e = launch_variant<8, false, 1, float>(bp, b.nitems, 1, b.smem, b.uniform, s);
+      else if (b.mmax <= 6) e = launch_variant<6, true, 1, float>(bp, b.nitems, b.cluster, b.smem, b.uniform, s);
+      else e = launch_variant<8, true, 1, float>(bp, b.nitems, b.cluster, b.smem, b.uniform, s);
     } else {
-      if (!cl) e = launch_variant<8, false, 1, double>(bp, b.nitems, 1, b.smem, s);
-      else e = launch_variant<8, true, 1, double>(bp, b.nitems, b.cluster, b.smem, s);
+      if (!cl) e = launch_variant<8, false, 1, double>(bp, b.nitems, 1, b.smem, b.uniform, s);
+      else e = launch_variant<8, true, 1, double>(bp, b.nitems, b.cluster, b.smem, b.uniform, s);
     }
     if (e != cudaSuccess) return e;
   }

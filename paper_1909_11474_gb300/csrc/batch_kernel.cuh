@@ -321,6 +321,9 @@ __device__ __forceinline__ void st_cluster(unsigned addr, float v) {
 __device__ __forceinline__ void st_cluster(unsigned addr, double v) {
   asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
 }
+__device__ __forceinline__ void st_cluster(unsigned addr, int v) {
+  asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
 
 struct BatchParams {
   int P, C;
@@ -331,6 +334,7 @@ struct BatchParams {
   const CtaRec *recs;
   int ntiles;                      // parameter tiles: ceil(P / PT)
   int nconf, nchunks, chunk_tiles; // work items: nconf configurations x nchunks chunks of tiles
+  int *counter;                    // work-claiming counter of the launch, zero at launch
   int mode;
   double *E;
   void *F;
@@ -391,16 +395,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 }
 constexpr unsigned kMbarSpins = 1u << 22;   // bound of a wait for one configuration's copies
 
-// Persistent work loop. The launch covers nconf configurations of one bucket, each split into
-// nchunks chunks of chunk_tiles parameter tiles; a CTA (or cluster) takes items
-// it = blockIdx/ncta, + gridDim/ncta, ... in a fixed order, stages the configuration's geometry once
-// (single-CTA launches: one TMA bulk copy per array, completed on an mbarrier) and runs its tiles.
+// Persistent work loop. The launch covers nconf configurations of one bucket (longest first), each
+// split into nchunks chunks of chunk_tiles parameter tiles; a CTA (or cluster) claims the next item
+// from an atomic counter, stages the configuration's geometry once (single-CTA launches: one TMA
+// bulk copy per array, completed on an mbarrier) and runs the chunk's tiles.
 template <int PT, int MMAX, bool CLUSTER, int MINB, typename R>
 __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams a) {
   using R4 = typename Vec4<R>::T;
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ int abort_flag;
+  __shared__ int s_item;
   R *stage = reinterpret_cast<R *>(smem);
   constexpr int APW = kWarp / PT;
 
@@ -422,7 +427,19 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   }
   unsigned phase = 0;
   const int nitems = a.nconf * a.nchunks;
-  for (int it = blockIdx.x / (int)ncta; it < nitems; it += gridDim.x / ncta) {
+  for (;;) {
+    if constexpr (CLUSTER) {
+      if (rank == 0 && tid == 0) {
+        const int v = atomicAdd(a.counter, 1);
+        for (unsigned r = 0; r < ncta; ++r) st_cluster(map_to_rank(smem_addr(&s_item), r), v);
+      }
+      cluster_sync_all();
+    } else {
+      if (tid == 0) s_item = atomicAdd(a.counter, 1);
+      __syncthreads();
+    }
+    const int it = s_item;
+    if (it >= nitems) break;
     const int ci = it / a.nchunks, chunk = it % a.nchunks;
     const int tile0 = chunk * a.chunk_tiles;
     const int tile1 = min(a.ntiles, tile0 + a.chunk_tiles);

@@ -98,6 +98,14 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     b.smem = smem[k];
     b.adj_smem = adj_smem[k];
     b.item_off = (int)recs.size();
+    b.uniform = true;
+    for (int cf : cfgs) {
+      const int f0 = cfgs.front();
+      const int na = c.h_atom_off[cf + 1] - c.h_atom_off[cf], nf = c.h_atom_off[f0 + 1] - c.h_atom_off[f0];
+      const int ba = c.h_boff[c.h_atom_off[cf + 1]] - c.h_boff[c.h_atom_off[cf]];
+      const int bf = c.h_boff[c.h_atom_off[f0 + 1]] - c.h_boff[c.h_atom_off[f0]];
+      if (na != nf || ba != bf) b.uniform = false;
+    }
     for (int cf : cfgs) {
       const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
       const int per = (nat + k.cl - 1) / k.cl;
@@ -154,7 +162,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   Ctx &c = ctx->c;
   cudaSetDevice(c.device);
   cudaDeviceSynchronize();
-  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv,
+  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv, &c.pre32, &c.counters,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
                          &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
@@ -230,6 +238,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.pos32.ensure(N * sizeof(float4)));
   TSF_CUDA(c.box.ensure((size_t)C * 9 * sizeof(double)));
   TSF_CUDA(c.boxinv.ensure((size_t)C * 12 * sizeof(double)));
+  TSF_CUDA(c.pre32.ensure((size_t)C * 12 * sizeof(float)));
   TSF_CUDA(c.cnt.ensure(N * sizeof(int)));
   TSF_CUDA(c.nbr.ensure(N * M * sizeof(int)));
   TSF_CUDA(c.shift.ensure(N * M * sizeof(char4)));
@@ -239,10 +248,10 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(cudaMemcpyAsync(c.box.p, cfg->box, (size_t)C * 9 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
   unsigned *st = c.status.as<unsigned>();
-  TSF_CUDA(tsf::launch_box_prep(C, c.box.as<double>(), c.boxinv.as<double>(), st, s));
+  TSF_CUDA(tsf::launch_box_prep(C, c.box.as<double>(), c.boxinv.as<double>(), c.pre32.as<float>(), R2, st, s));
   TSF_CUDA(tsf::launch_pos32(N, c.pos.as<double>(), c.pos32.as<float4>(), nullptr, st, s));
   TSF_CUDA(tsf::launch_neighbors_batch(N, c.atom_off.as<int>(), c.atom_cfg.as<int>(), c.pos.as<double>(),
-                                       c.pos32.as<float4>(), c.box.as<double>(), c.boxinv.as<double>(),
+                                       c.pos32.as<float4>(), c.box.as<double>(), c.pre32.as<float>(),
                                        R2, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), st, s));
   // one synchronisation: neighbour counts and status back to pinned host memory
   int *h_cnt = hp;
@@ -347,7 +356,9 @@ int tersoff_eval(tersoff_ctx *ctx, const double *params, int32_t P, int32_t prec
   int rc = build_plan(ctx, precision);
   if (rc) return rc;
   TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
+  TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
+  o.counters = c.counters.as<int>();
   o.E = E;
   o.F = F;
   o.W = W;
@@ -373,7 +384,9 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
   TSF_CUDA(c.tf4.ensure((size_t)c.Ntot * sizeof(tsf::dvec4)));
+  TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
+  o.counters = c.counters.as<int>();
   o.consts = c.work.p;
   o.tF4 = c.tf4.p;
   o.tE = tg->E;

@@ -103,6 +103,7 @@ struct Bucket {
   int precision;   // 32 or 64
   size_t smem;     // dynamic shared memory per CTA
   size_t adj_smem; // dynamic shared memory per CTA of the adjoint kernel (FP32, single-CTA buckets)
+  bool uniform;    // every configuration of the bucket has the same atom and bond counts
   int nitems;      // configurations in the bucket
   int item_off;    // first record of the bucket (records are per configuration and cluster rank)
 };
@@ -127,7 +128,8 @@ struct Ctx {
   std::vector<int> h_atom_off, h_cnt, h_boff, h_poff, h_cfg_maxm;
   PinnedBuf hp_stage;   // pinned staging: atom table uploads, neighbour-count readback, offsets
   cudaEvent_t stage_event = nullptr;   // recorded after the staging buffer's last upload
-  DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, cnt, nbr, shift, boff, poff, brev;
+  DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, pre32, cnt, nbr, shift, boff, poff, brev;
+  DevBuf counters;   // per-launch work counters of the persistent batched kernels
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
   BatchPlan plan32, plan64;
   DevBuf part, dpart, work, tf4, gpart;
@@ -140,12 +142,13 @@ struct Ctx {
 
 // ---- launchers (defined in the .cu files) ----
 // neighbors.cu
-cudaError_t launch_box_prep(int C, const double *box, double *boxinv, unsigned *status, cudaStream_t s);
+cudaError_t launch_box_prep(int C, const double *box, double *boxinv, float *pre32, double R2, unsigned *status,
+                            cudaStream_t s);
 cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg,
                          unsigned *status, cudaStream_t s);
 cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
                                    const double *pos, const float4 *pos32, const double *box,
-                                   const double *boxinv, double R2, int M, int *cnt, int *nbr,
+                                   const float *pre32, double R2, int M, int *cnt, int *nbr,
                                    char4 *shift, unsigned *status, cudaStream_t s);
 cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,
                            const int *boff, int *brev, unsigned *status, cudaStream_t s);
@@ -167,6 +170,7 @@ struct BatchOut {
   double *dpart;      // [C][3]
   void *consts;       // workspace: [P][8] per-parameter-set constants (working precision)
   void *tF4;          // workspace: [Ntot] target forces as 4-vectors (working precision)
+  int *counters;      // workspace: one work counter per launch bucket
 };
 enum BatchMode { kModeEval = 0, kModeFitness = 1 };
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,

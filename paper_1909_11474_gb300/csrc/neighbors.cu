@@ -9,9 +9,10 @@
 namespace tsf {
 
 // Per configuration: the inverse box (fractional coordinates s = x H^-1, rows of H = lattice
-// vectors) and the three lattice-plane spacings, layout boxinv[c][12] = {Hinv (row-major), gap}.
+// vectors) and the three lattice-plane spacings, boxinv[c][0..11] = {Hinv (row-major), gap}, and the
+// FP32 constants of the neighbour prefilter, pre32[c][0..11] = {Hinv, R2/gap + margin}.
 __global__ void box_prep_kernel(int C, const double *__restrict__ box, double *__restrict__ boxinv,
-                                unsigned *status) {
+                                float *__restrict__ pre32, double R2, unsigned *status) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const double *H = box + 9 * c;
@@ -39,6 +40,9 @@ __global__ void box_prep_kernel(int C, const double *__restrict__ box, double *_
   o[9] = vol / sqrt(bxc0 * bxc0 + bxc1 * bxc1 + bxc2 * bxc2);
   o[10] = vol / sqrt(cxa0 * cxa0 + cxa1 * cxa1 + cxa2 * cxa2);
   o[11] = vol / sqrt(axb0 * axb0 + axb1 * axb1 + axb2 * axb2);
+  float *f = pre32 + 12 * c;
+  for (int k = 0; k < 9; ++k) f[k] = (float)o[k];
+  for (int k = 0; k < 3; ++k) f[9 + k] = (float)(R2 / o[9 + k]) + 1e-4f;
 }
 
 __global__ void pos32_kernel(int64_t N, const double *__restrict__ pos, float4 *__restrict__ pos32,
@@ -64,7 +68,7 @@ __device__ __forceinline__ void image_range(float ds, float rng, int &lo, int &h
 __global__ void __launch_bounds__(128) neighbors_batch_kernel(
     int64_t Ntot, const int *__restrict__ atom_off, const int *__restrict__ atom_cfg,
     const double *__restrict__ pos, const float4 *__restrict__ pos32,
-    const double *__restrict__ box, const double *__restrict__ boxinv, double R2, int M,
+    const double *__restrict__ box, const float *__restrict__ pre32, double R2, int M,
     int *__restrict__ cnt_out, int *__restrict__ nbr, char4 *__restrict__ shift, unsigned *status) {
   const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -74,14 +78,11 @@ __global__ void __launch_bounds__(128) neighbors_batch_kernel(
   double H[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) H[k] = box[9 * c + k];
-  const double *bi = boxinv + 12 * c;
+  const float *bi = pre32 + 12 * c;   // no FP64 arithmetic per warp: FP32 prefilter constants
   float Hi[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) Hi[k] = (float)bi[k];
-  const float margin = 1e-4f;
-  const float rng0 = (float)(R2 / bi[9]) + margin;
-  const float rng1 = (float)(R2 / bi[10]) + margin;
-  const float rng2 = (float)(R2 / bi[11]) + margin;
+  for (int k = 0; k < 9; ++k) Hi[k] = bi[k];
+  const float rng0 = bi[9], rng1 = bi[10], rng2 = bi[11];
   const double R2sq = R2 * R2;
   const double xix = pos[3 * i], xiy = pos[3 * i + 1], xiz = pos[3 * i + 2];
   const float4 xi = pos32[i];
@@ -216,8 +217,8 @@ __global__ void geometry_bond_kernel(int64_t Ntot, int M, const int *__restrict_
   const char4 n = shift[i * M + e];
   ExactPair p = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], pos[3 * i], pos[3 * i + 1],
                            pos[3 * i + 2], H, n.x, n.y, n.z);
-  const double r = sqrt(p.r2);
-  const double ir = 1.0 / r;
+  const double ir = rsqrt(p.r2);
+  const double r = p.r2 * ir;
   double fc, fcp;
   cutoff_fc(r, R1, R2, fc, fcp);
   const double ux = p.dx * ir, uy = p.dy * ir, uz = p.dz * ir;
@@ -259,8 +260,9 @@ __global__ void geometry_pair_kernel(int64_t Ntot, int slots, const int *__restr
 // ---------------------------------------------------------------------------------------------
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_box_prep(int C, const double *box, double *boxinv, unsigned *status, cudaStream_t s) {
-  box_prep_kernel<<<nblk(C, 128), 128, 0, s>>>(C, box, boxinv, status);
+cudaError_t launch_box_prep(int C, const double *box, double *boxinv, float *pre32, double R2, unsigned *status,
+                            cudaStream_t s) {
+  box_prep_kernel<<<nblk(C, 128), 128, 0, s>>>(C, box, boxinv, pre32, R2, status);
   return cudaGetLastError();
 }
 cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *, unsigned *status,
@@ -271,11 +273,11 @@ cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int 
 }
 cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
                                    const double *pos, const float4 *pos32, const double *box,
-                                   const double *boxinv, double R2, int M, int *cnt, int *nbr,
+                                   const float *pre32, double R2, int M, int *cnt, int *nbr,
                                    char4 *shift, unsigned *status, cudaStream_t s) {
   if (Ntot == 0) return cudaSuccess;
   neighbors_batch_kernel<<<nblk(Ntot * 32, 128), 128, 0, s>>>(Ntot, atom_off, atom_cfg, pos, pos32, box,
-                                                              boxinv, R2, M, cnt, nbr, shift, status);
+                                                              pre32, R2, M, cnt, nbr, shift, status);
   return cudaGetLastError();
 }
 cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,

@@ -50,7 +50,8 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   const size_t b_tf4 = align256((size_t)c.Ntot * sizeof(tsf::dvec4));
   const size_t b_part = align256((size_t)P * c.C * 3 * sizeof(double));
   const size_t b_dpart = align256((size_t)c.C * 3 * sizeof(double));
-  const size_t need = b_consts + b_tf4 + b_part + b_dpart;
+  const size_t b_count = align256(64 * sizeof(int));
+  const size_t need = b_consts + b_tf4 + b_part + b_dpart + b_count;
   if (need > kScratchBytes) {
     char buf[200];
     std::snprintf(buf, sizeof(buf), "tersoff_fitness_static needs %zu bytes of scratch for P=%d, C=%d, Ntot=%lld; "
@@ -77,7 +78,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
 
   // every scratch element read by the kernels is written earlier in the same call (constants and
   // targets by the prep kernel, every (p, c) residual and every configuration's norms by the batch
-  // kernel), so nothing needs clearing between calls
+  // kernel); the work counters, which must start at zero, are cleared by the launch itself
   tsf::BatchOut o = {};
   o.tE = tg->E;
   o.tW = tg->W;
@@ -87,6 +88,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   o.tF4 = base + b_consts;
   o.part = reinterpret_cast<double *>(base + b_consts + b_tf4);
   o.dpart = reinterpret_cast<double *>(base + b_consts + b_tf4 + b_part);
+  o.counters = reinterpret_cast<int *>(base + b_consts + b_tf4 + b_part + b_dpart);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
   if (e == cudaSuccess) e = tsf::launch_fitness_finalize(P, c.C, o.part, o.dpart, w[0], w[1], w[2], Z, Zq, S, s);
