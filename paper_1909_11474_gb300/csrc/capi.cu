@@ -138,6 +138,20 @@ int build_plan(tersoff_ctx *ctx, int precision) {
 
 }  // namespace
 
+namespace tsf {
+// FP64 geometry records, built on the first FP64 evaluation after a neighbour build (stream-ordered).
+int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s) {
+  Ctx &c = ctx->c;
+  if (c.geom64) return TERSOFF_OK;
+  TSF_CUDA(launch_geometry(64, c.Ntot, c.Btot, c.M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
+                           c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
+                           c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), c.R1, c.R2, c.gA64.p,
+                           c.gB64.p, c.gcos64.p, pair_slots(std::min(c.max_m, c.M)), s));
+  c.geom64 = true;
+  return TERSOFF_OK;
+}
+}  // namespace tsf
+
 extern "C" {
 
 int tersoff_create(tersoff_ctx **out, int device) {
@@ -238,7 +252,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.pos32.ensure(N * sizeof(float4)));
   TSF_CUDA(c.box.ensure((size_t)C * 9 * sizeof(double)));
   TSF_CUDA(c.boxinv.ensure((size_t)C * 12 * sizeof(double)));
-  TSF_CUDA(c.pre32.ensure((size_t)C * 12 * sizeof(float)));
+  TSF_CUDA(c.pre32.ensure((size_t)C * 24 * sizeof(float)));
   TSF_CUDA(c.cnt.ensure(N * sizeof(int)));
   TSF_CUDA(c.nbr.ensure(N * M * sizeof(int)));
   TSF_CUDA(c.shift.ensure(N * M * sizeof(char4)));
@@ -248,7 +262,8 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(cudaMemcpyAsync(c.box.p, cfg->box, (size_t)C * 9 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
   unsigned *st = c.status.as<unsigned>();
-  TSF_CUDA(tsf::launch_box_prep(C, c.box.as<double>(), c.boxinv.as<double>(), c.pre32.as<float>(), R2, st, s));
+  TSF_CUDA(tsf::launch_box_prep(C, c.box.as<double>(), c.pos.as<double>(), c.atom_off.as<int>(),
+                                c.boxinv.as<double>(), c.pre32.as<float>(), R2, st, s));
   TSF_CUDA(tsf::launch_pos32(N, c.pos.as<double>(), c.pos32.as<float4>(), nullptr, st, s));
   TSF_CUDA(tsf::launch_neighbors_batch(N, c.atom_off.as<int>(), c.atom_cfg.as<int>(), c.pos.as<double>(),
                                        c.pos32.as<float4>(), c.box.as<double>(), c.pre32.as<float>(),
@@ -300,12 +315,11 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.gcos64.ensure(Q * sizeof(double)));
   TSF_CUDA(tsf::launch_reverse(N, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), c.boff.as<int>(),
                                c.brev.as<int>(), st, s));
-  TSF_CUDA(tsf::launch_geometry(N, M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
+  TSF_CUDA(tsf::launch_geometry(32, N, c.Btot, M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
                                 c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
-                                c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), R1, R2,
-                                c.gA32.as<float4>(), c.gB32.as<float4>(), c.gcos32.as<float>(),
-                                c.gA64.as<tsf::dvec4>(), c.gB64.as<tsf::dvec4>(), c.gcos64.as<double>(),
-                                tsf::pair_slots(std::min(c.max_m, M)), s));
+                                c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), R1, R2, c.gA32.p,
+                                c.gB32.p, c.gcos32.p, tsf::pair_slots(std::min(c.max_m, M)), s));
+  c.geom64 = false;
   if (c.max_m <= 8) {
     int rc = build_plan(ctx, 32);
     if (rc) return rc;
@@ -355,6 +369,7 @@ int tersoff_eval(tersoff_ctx *ctx, const double *params, int32_t P, int32_t prec
   cudaSetDevice(c.device);
   int rc = build_plan(ctx, precision);
   if (rc) return rc;
+  if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
   TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
   TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
@@ -380,6 +395,7 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   cudaSetDevice(c.device);
   int rc = build_plan(ctx, precision);
   if (rc) return rc;
+  if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
   TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));

@@ -121,6 +121,7 @@ struct Ctx {
 
   // --- batch build state ---
   bool built = false;
+  bool geom64 = false;   // FP64 geometry records built for the current neighbour build
   int C = 0;
   int64_t Ntot = 0, Btot = 0, Qtot = 0;
   int M = 0, max_m = 0;
@@ -142,8 +143,8 @@ struct Ctx {
 
 // ---- launchers (defined in the .cu files) ----
 // neighbors.cu
-cudaError_t launch_box_prep(int C, const double *box, double *boxinv, float *pre32, double R2, unsigned *status,
-                            cudaStream_t s);
+cudaError_t launch_box_prep(int C, const double *box, const double *pos, const int *atom_off, double *boxinv,
+                            float *pre32, double R2, unsigned *status, cudaStream_t s);
 cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg,
                          unsigned *status, cudaStream_t s);
 cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
@@ -152,12 +153,11 @@ cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int 
                                    char4 *shift, unsigned *status, cudaStream_t s);
 cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,
                            const int *boff, int *brev, unsigned *status, cudaStream_t s);
-cudaError_t launch_geometry(int64_t Ntot, int M, const int *atom_cfg, const int *atom_off,
-                            const int *brev, const double *pos,
-                            const double *box, const int *cnt, const int *nbr, const char4 *shift,
-                            const int *boff, const int *poff, double R1, double R2, float4 *gA32,
-                            float4 *gB32, float *gcos32, dvec4 *gA64, dvec4 *gB64,
-                            double *gcos64, int max_slots, cudaStream_t s);
+cudaError_t launch_geometry(int precision, int64_t Ntot, int64_t Btot, int M, const int *atom_cfg,
+                            const int *atom_off, const int *brev, const double *pos, const double *box,
+                            const int *cnt, const int *nbr, const char4 *shift, const int *boff,
+                            const int *poff, double R1, double R2, void *gA, void *gB, void *gcos,
+                            int max_slots, cudaStream_t s);
 
 // batch.cu
 struct BatchOut {
@@ -178,6 +178,9 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
 cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
                                     double we, double wv, double wf, double *Z, double *Zq,
                                     double *S, cudaStream_t s);
+// capi.cu: FP64 geometry records on demand
+int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s);
+
 // md.cu
 int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double *x, double R1, double R2,
              int M, int precision, double *E, void *F, double *W, cudaStream_t s, std::string &err);

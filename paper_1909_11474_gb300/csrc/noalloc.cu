@@ -90,6 +90,10 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   o.dpart = reinterpret_cast<double *>(base + b_consts + b_tf4 + b_part);
   o.counters = reinterpret_cast<int *>(base + b_consts + b_tf4 + b_part + b_dpart);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == 64) {
+    const int rc = tsf::ensure_geom64(ctx, s);   // kernels into buffers made by the neighbour build
+    if (rc) return rc;
+  }
   cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
   if (e == cudaSuccess) e = tsf::launch_fitness_finalize(P, c.C, o.part, o.dpart, w[0], w[1], w[2], Z, Zq, S, s);
   if (e != cudaSuccess) {
