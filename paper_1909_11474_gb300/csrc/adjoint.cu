@@ -119,7 +119,7 @@ __device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB,
   using D = Dual<K, float>;
   const PConsts<D> KD = seed_consts<K>(Kf, q0);
   D U, Px[M], Py[M], Pz[M];
-  atom_core<M, D, float>(ux, uy, uz, r, ir, fc, fcp, cs, KD, U, Px, Py, Pz);
+  atom_core<M, false, D, float>(ux, uy, uz, r, ir, fc, fcp, cs, KD, U, Px, Py, Pz);
   const float ae = aw[0 * kAdjPT + pl];
   const float a0 = aw[1 * kAdjPT + pl], a1 = aw[2 * kAdjPT + pl], a2 = aw[3 * kAdjPT + pl];
   const float a3 = aw[4 * kAdjPT + pl], a4 = aw[5 * kAdjPT + pl], a5 = aw[6 * kAdjPT + pl];
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
       if (pl == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
       continue;
     }
-    atom_forward_dispatch<PT, MMAX, true, float>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+    atom_forward_dispatch<PT, MMAX, true, false, float>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
   }
   __syncthreads();
 

@@ -100,8 +100,9 @@ struct AtomAcc {
 // The per-atom core of passes 1 and 2: from the bond geometry (unit vectors, r, 1/r, f_C, f_C', the
 // cosines of the bond pairs; R) and the parameter constants (T: R itself, or a dual number carrying
 // parameter tangents), U = sum_j f_C (f_R - b f_A), which is twice the site energy U_i of Eq. 2,
-// and P_ij = dU_i/dd_ij of every bond (the derivative of U_i itself, 1/2 included).
-template <int M, typename T, typename R>
+// and P_ij = dU_i/dd_ij of every bond (the derivative of U_i itself, 1/2 included). INNER: every bond
+// is inside R1 (callers pass f_C = 1 and f_C' = 0 as constants, which the compiler folds away).
+template <int M, bool INNER, typename T, typename R>
 __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], const R (&uz)[M],
                                           const R (&r)[M], const R (&ir)[M], const R (&fc)[M],
                                           const R (&fcp)[M], const R *cs, const PConsts<T> &K, T &U,
@@ -147,10 +148,10 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
   }
 
   // ---- pass 2: dU_i/dd_ij
-  T Ax[M], Ay[M], Az[M], s[M], Rg[M];
+  T Ax[M], Ay[M], Az[M], Rg[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    Ax[j] = T(0.0f); Ay[j] = T(0.0f); Az[j] = T(0.0f); s[j] = T(0.0f); Rg[j] = T(0.0f);
+    Ax[j] = T(0.0f); Ay[j] = T(0.0f); Az[j] = T(0.0f); Rg[j] = T(0.0f);
   }
   {
     int q = 0;
@@ -161,9 +162,6 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
         const T w = (cc[j] * fc[k] + cc[k] * fc[j]) * tq[q];   // half of the w of the header
         Ax[j] += w * ux[k]; Ay[j] += w * uy[k]; Az[j] += w * uz[k];
         Ax[k] += w * ux[j]; Ay[k] += w * uy[j]; Az[k] += w * uz[j];
-        const T wc = w * cs[q];
-        s[j] += wc;
-        s[k] += wc;
         ++q;
       }
     }
@@ -171,9 +169,12 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
   // bonds inside the switching region (R1 < r < R2) carry the f_C'(r_ij) g term; the vote keeps
   // this loop off the common path where no bond of the warp is in that region
   bool sw = false;
+  if constexpr (!INNER) {
 #pragma unroll
-  for (int j = 0; j < M; ++j) sw |= (fcp[j] != R(0));
-  if (__any_sync(0xffffffffu, sw)) {
+    for (int j = 0; j < M; ++j) sw |= (fcp[j] != R(0));
+    sw = __any_sync(0xffffffffu, sw);
+  }
+  if (sw) {
     int q = 0;
 #pragma unroll
     for (int j = 0; j < M; ++j) {
@@ -189,7 +190,9 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     const R ir2 = ir[j] + ir[j];                   // 2/r restores the factor 2 of g' = 2 t
-    const T coef = rad[j] + fcp[j] * Rg[j] - s[j] * ir2;
+    // s_ij = sum_k w_jk cos_jk = u_ij . A_ij, since cos_jk = u_ij . u_ik
+    const T sj = ux[j] * Ax[j] + uy[j] * Ay[j] + uz[j] * Az[j];
+    const T coef = rad[j] + fcp[j] * Rg[j] - sj * ir2;
     Px[j] = coef * ux[j] + ir2 * Ax[j];
     Py[j] = coef * uy[j] + ir2 * Ay[j];
     Pz[j] = coef * uz[j] + ir2 * Az[j];
@@ -200,7 +203,7 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
 // sA/sB: bond records (u_x, u_y, u_z, r), (1/r, f_C, f_C', rev | j << 16); sC: pair cosines; lb/lq: this
 // atom's first bond / pair in shared memory; m: its neighbour count (<= M). EXACT: every slot has
 // m == M, so no bond is a phantom.
-template <int M, int PT, bool EXACT, typename R>
+template <int M, int PT, bool EXACT, bool INNER, typename R>
 __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restrict__ sA,
                                              const typename Vec4<R>::T *__restrict__ sB,
                                              const R *__restrict__ sC, R *__restrict__ stage,
@@ -213,7 +216,14 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
       const auto A = sld(&sA[lb + j], 1);
       const auto B = sld(&sB[lb + j], 2);
       ux[j] = A.x; uy[j] = A.y; uz[j] = A.z; r[j] = A.w;
-      ir[j] = B.x; fc[j] = B.y; fcp[j] = B.z;
+      ir[j] = B.x;
+      if constexpr (INNER) {
+        fc[j] = R(1);
+        fcp[j] = R(0);
+      } else {
+        fc[j] = B.y;
+        fcp[j] = B.z;
+      }
     } else {
       ux[j] = R(0); uy[j] = R(0); uz[j] = R(0); r[j] = R(1);
       ir[j] = R(0); fc[j] = R(0); fcp[j] = R(0);
@@ -244,7 +254,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
 
   R U, Px[M], Py[M], Pz[M];
-  atom_core<M, R, R>(ux, uy, uz, r, ir, fc, fcp, cs, K, U, Px, Py, Pz);
+  atom_core<M, INNER, R, R>(ux, uy, uz, r, ir, fc, fcp, cs, K, U, Px, Py, Pz);
   R W0 = R(0), W1 = R(0), W2 = R(0), W3 = R(0), W4 = R(0), W5 = R(0);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
@@ -265,7 +275,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
 }
 
-template <int PT, int MMAX, bool EXACT, typename R>
+template <int PT, int MMAX, bool EXACT, bool INNER, typename R>
 __device__ __forceinline__ void atom_forward_dispatch(int Mw, const typename Vec4<R>::T *sA,
                                                       const typename Vec4<R>::T *sB, const R *sC,
                                                       R *stage, int lb, int lq, int m, bool store,
@@ -273,7 +283,7 @@ __device__ __forceinline__ void atom_forward_dispatch(int Mw, const typename Vec
 #define TSF_CASE(MM)                                                                          \
   case MM:                                                                                    \
     if constexpr (MMAX >= MM)                                                                 \
-      atom_forward<MM, PT, EXACT, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc);        \
+      atom_forward<MM, PT, EXACT, INNER, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); \
     break;
   switch (Mw) {
     TSF_CASE(1) TSF_CASE(2) TSF_CASE(3) TSF_CASE(4) TSF_CASE(5) TSF_CASE(6) TSF_CASE(7) TSF_CASE(8)
@@ -330,6 +340,7 @@ struct BatchParams {
   int64_t Ntot;
   const void *consts;              // R [P][8]: PConsts of every parameter set
   const int *atom_off, *boff, *poff;
+  const int *outer;                // [Ntot] nonzero if the atom has a bond beyond R1
   const void *gA, *gB, *gcos;
   const CtaRec *recs;
   int ntiles;                      // parameter tiles: ceil(P / PT)
@@ -482,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
       }
       for (int t = tid; t < ns; t += kThreads) {
         const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
-        sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0), 9);
+        sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, a.outer[s0 + t]), 9);
         if (fit) sst(&stF[t], reinterpret_cast<const R4 *>(a.tF4)[s0 + t], 10);
       }
       if constexpr (!CLUSTER) {
@@ -542,7 +553,10 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
             if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
             continue;
           }
-          atom_forward_dispatch<PT, MMAX, true, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+          if (sizeof(R) == 4 && at.w == 0)
+            atom_forward_dispatch<PT, MMAX, true, sizeof(R) == 4, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+          else
+            atom_forward_dispatch<PT, MMAX, true, false, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
         } else {
           const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
           const bool uniform = __all_sync(0xffffffffu, m == Mw);
@@ -551,9 +565,9 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
             continue;
           }
           if (uniform)
-            atom_forward_dispatch<PT, MMAX, true, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+            atom_forward_dispatch<PT, MMAX, true, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
           else
-            atom_forward_dispatch<PT, MMAX, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+            atom_forward_dispatch<PT, MMAX, false, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
         }
       }
       if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
@@ -601,7 +615,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
             Fz -= sld(&sr[2 * PT], 15);
           }
         }
-        sF2 += Fx * Fx + Fy * Fy + Fz * Fz;
+        if (!(mask & 4)) sF2 += Fx * Fx + Fy * Fy + Fz * Fz;   // finiteness of F when no residual checks it
         const int i = s0 + li;
         if (a.mode == kModeEval) {
           if (active && a.F) {

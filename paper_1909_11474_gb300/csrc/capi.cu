@@ -146,7 +146,7 @@ int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s) {
   TSF_CUDA(launch_geometry(64, c.Ntot, c.Btot, c.M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
                            c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
                            c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), c.R1, c.R2, c.gA64.p,
-                           c.gB64.p, c.gcos64.p, pair_slots(std::min(c.max_m, c.M)), s));
+                           c.gB64.p, c.gcos64.p, pair_slots(std::min(c.max_m, c.M)), nullptr, s));
   c.geom64 = true;
   return TERSOFF_OK;
 }
@@ -176,9 +176,9 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   Ctx &c = ctx->c;
   cudaSetDevice(c.device);
   cudaDeviceSynchronize();
-  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv, &c.pre32, &c.counters,
+  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv, &c.pre32, &c.xmax, &c.counters,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
-                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
+                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.outer, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_Ui, &c.md_boxd};
@@ -253,6 +253,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.box.ensure((size_t)C * 9 * sizeof(double)));
   TSF_CUDA(c.boxinv.ensure((size_t)C * 12 * sizeof(double)));
   TSF_CUDA(c.pre32.ensure((size_t)C * 24 * sizeof(float)));
+  TSF_CUDA(c.xmax.ensure((size_t)C * sizeof(float)));
   TSF_CUDA(c.cnt.ensure(N * sizeof(int)));
   TSF_CUDA(c.nbr.ensure(N * M * sizeof(int)));
   TSF_CUDA(c.shift.ensure(N * M * sizeof(char4)));
@@ -262,9 +263,11 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(cudaMemcpyAsync(c.box.p, cfg->box, (size_t)C * 9 * sizeof(double), cudaMemcpyDeviceToDevice, s));
   TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
   unsigned *st = c.status.as<unsigned>();
-  TSF_CUDA(tsf::launch_box_prep(C, c.box.as<double>(), c.pos.as<double>(), c.atom_off.as<int>(),
-                                c.boxinv.as<double>(), c.pre32.as<float>(), R2, st, s));
-  TSF_CUDA(tsf::launch_pos32(N, c.pos.as<double>(), c.pos32.as<float4>(), nullptr, st, s));
+  TSF_CUDA(cudaMemsetAsync(c.xmax.p, 0, (size_t)C * sizeof(float), s));
+  TSF_CUDA(tsf::launch_pos32(N, c.pos.as<double>(), c.pos32.as<float4>(), c.atom_cfg.as<int>(), c.xmax.as<float>(),
+                             st, s));
+  TSF_CUDA(tsf::launch_box_prep(C, c.box.as<double>(), c.xmax.as<float>(), c.boxinv.as<double>(),
+                                c.pre32.as<float>(), R2, st, s));
   TSF_CUDA(tsf::launch_neighbors_batch(N, c.atom_off.as<int>(), c.atom_cfg.as<int>(), c.pos.as<double>(),
                                        c.pos32.as<float4>(), c.box.as<double>(), c.pre32.as<float>(),
                                        R2, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), st, s));
@@ -307,6 +310,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(cudaEventRecord(c.stage_event, s));
   const size_t B = std::max<int64_t>(1, c.Btot), Q = std::max<int64_t>(1, c.Qtot);
   TSF_CUDA(c.brev.ensure(B * sizeof(int)));
+  TSF_CUDA(c.outer.ensure(std::max<int64_t>(1, N) * sizeof(int)));
   TSF_CUDA(c.gA32.ensure(B * sizeof(float4)));
   TSF_CUDA(c.gB32.ensure(B * sizeof(float4)));
   TSF_CUDA(c.gcos32.ensure(Q * sizeof(float)));
@@ -318,7 +322,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(tsf::launch_geometry(32, N, c.Btot, M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
                                 c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
                                 c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), R1, R2, c.gA32.p,
-                                c.gB32.p, c.gcos32.p, tsf::pair_slots(std::min(c.max_m, M)), s));
+                                c.gB32.p, c.gcos32.p, tsf::pair_slots(std::min(c.max_m, M)), c.outer.as<int>(), s));
   c.geom64 = false;
   if (c.max_m <= 8) {
     int rc = build_plan(ctx, 32);

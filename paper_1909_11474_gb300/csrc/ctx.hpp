@@ -129,9 +129,10 @@ struct Ctx {
   std::vector<int> h_atom_off, h_cnt, h_boff, h_poff, h_cfg_maxm;
   PinnedBuf hp_stage;   // pinned staging: atom table uploads, neighbour-count readback, offsets
   cudaEvent_t stage_event = nullptr;   // recorded after the staging buffer's last upload
-  DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, pre32, cnt, nbr, shift, boff, poff, brev;
+  DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, pre32, xmax, cnt, nbr, shift, boff, poff, brev;
   DevBuf counters;   // per-launch work counters of the persistent batched kernels
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
+  DevBuf outer;   // [Ntot] int: nonzero if the atom has a bond beyond R1 (f_C != 1)
   BatchPlan plan32, plan64;
   DevBuf part, dpart, work, tf4, gpart;
 
@@ -143,9 +144,9 @@ struct Ctx {
 
 // ---- launchers (defined in the .cu files) ----
 // neighbors.cu
-cudaError_t launch_box_prep(int C, const double *box, const double *pos, const int *atom_off, double *boxinv,
-                            float *pre32, double R2, unsigned *status, cudaStream_t s);
-cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg,
+cudaError_t launch_box_prep(int C, const double *box, const float *xmax, double *boxinv, float *pre32,
+                            double R2, unsigned *status, cudaStream_t s);
+cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg, float *xmax,
                          unsigned *status, cudaStream_t s);
 cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
                                    const double *pos, const float4 *pos32, const double *box,
@@ -157,7 +158,7 @@ cudaError_t launch_geometry(int precision, int64_t Ntot, int64_t Btot, int M, co
                             const int *atom_off, const int *brev, const double *pos, const double *box,
                             const int *cnt, const int *nbr, const char4 *shift, const int *boff,
                             const int *poff, double R1, double R2, void *gA, void *gB, void *gcos,
-                            int max_slots, cudaStream_t s);
+                            int max_slots, int *outer, cudaStream_t s);
 
 // batch.cu
 struct BatchOut {

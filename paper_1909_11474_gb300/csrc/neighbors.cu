@@ -17,9 +17,9 @@ namespace tsf {
 // image index a candidate can have, each FP32 component of d = (x_j - x_i) + n.H is within
 // delta = 2^-23 (4X + 6 nmax |H|) of the exact value, so |r^2 - r32^2| < 3.5 R2 delta + 12 2^-24 R2^2;
 // the band is four times that.
-__global__ void box_prep_kernel(int C, const double *__restrict__ box, const double *__restrict__ pos,
-                                const int *__restrict__ atom_off, double *__restrict__ boxinv,
-                                float *__restrict__ pre32, double R2, unsigned *status) {
+__global__ void box_prep_kernel(int C, const double *__restrict__ box, const float *__restrict__ xmax,
+                                double *__restrict__ boxinv, float *__restrict__ pre32, double R2,
+                                unsigned *status) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= C) return;
   const double *H = box + 9 * c;
@@ -49,9 +49,9 @@ __global__ void box_prep_kernel(int C, const double *__restrict__ box, const dou
   o[9] = vol / sqrt(bxc0 * bxc0 + bxc1 * bxc1 + bxc2 * bxc2);
   o[10] = vol / sqrt(cxa0 * cxa0 + cxa1 * cxa1 + cxa2 * cxa2);
   o[11] = vol / sqrt(axb0 * axb0 + axb1 * axb1 + axb2 * axb2);
-  double X = 0.0, Hm = 0.0;
-  for (int i = atom_off[c]; i < atom_off[c + 1]; ++i)
-    for (int k = 0; k < 3; ++k) X = fmax(X, fabs(pos[3 * i + k]));
+  // largest coordinate magnitude (from the FP32 copies: widened by 2^-22 for their rounding)
+  const double X = (double)xmax[c] * (1.0 + ldexp(1.0, -22));
+  double Hm = 0.0;
   for (int k = 0; k < 9; ++k) Hm = fmax(Hm, fabs(H[k]));
   double nmax = 0.0;
   for (int k = 0; k < 3; ++k) {
@@ -68,13 +68,18 @@ __global__ void box_prep_kernel(int C, const double *__restrict__ box, const dou
   f[23] = 0.f;
 }
 
-__global__ void pos32_kernel(int64_t N, const double *__restrict__ pos, float4 *__restrict__ pos32,
-                             unsigned *status) {
+// FP32 copies of the positions and, per configuration, the largest coordinate magnitude (xmax must
+// be zero on entry; non-negative floats order like their bit patterns, so an integer max suffices).
+__global__ void pos32_kernel(int64_t N, const double *__restrict__ pos, const int *__restrict__ atom_cfg,
+                             float4 *__restrict__ pos32, float *__restrict__ xmax, unsigned *status) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
   if (!(isfinite(x) && isfinite(y) && isfinite(z))) set_status(status, TERSOFF_STATUS_NONFINITE);
-  pos32[i] = make_float4((float)x, (float)y, (float)z, 0.f);
+  const float4 v = make_float4((float)x, (float)y, (float)z, 0.f);
+  pos32[i] = v;
+  const float m = fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)));
+  atomicMax(reinterpret_cast<int *>(xmax) + atom_cfg[i], __float_as_int(m));
 }
 
 // Candidate image range of one (i, j) pair on one axis: integers n with |s_j - s_i + n| < rng.
@@ -255,7 +260,8 @@ __global__ void geometry_bond_kernel(int64_t Ntot, int Btot, int M, const int *_
                                      const double *__restrict__ pos, const double *__restrict__ box,
                                      const int *__restrict__ nbr, const char4 *__restrict__ shift,
                                      const int *__restrict__ boff, double R1, double R2,
-                                     typename Vec4<R>::T *__restrict__ gA, typename Vec4<R>::T *__restrict__ gB) {
+                                     typename Vec4<R>::T *__restrict__ gA, typename Vec4<R>::T *__restrict__ gB,
+                                     int *__restrict__ outer) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Btot) return;
   const int64_t i = bond_owner(boff, Ntot, b);
@@ -275,6 +281,7 @@ __global__ void geometry_bond_kernel(int64_t Ntot, int Btot, int M, const int *_
     const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
     const float r = (dx * dx + dy * dy + dz * dz) * ir;
     float fc = 1.f, fcp = 0.f;
+    if (r > (float)R1) atomicOr(outer + i, 1);   // the atom has a bond beyond R1 (f_C != 1)
     if (r >= (float)R2) {
       fc = 0.f;
     } else if (r > (float)R1) {
@@ -327,15 +334,15 @@ __global__ void geometry_pair_kernel(int64_t Ntot, int slots, const int *__restr
 // ---------------------------------------------------------------------------------------------
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_box_prep(int C, const double *box, const double *pos, const int *atom_off, double *boxinv,
-                            float *pre32, double R2, unsigned *status, cudaStream_t s) {
-  box_prep_kernel<<<nblk(C, 128), 128, 0, s>>>(C, box, pos, atom_off, boxinv, pre32, R2, status);
+cudaError_t launch_box_prep(int C, const double *box, const float *xmax, double *boxinv, float *pre32,
+                            double R2, unsigned *status, cudaStream_t s) {
+  box_prep_kernel<<<nblk(C, 128), 128, 0, s>>>(C, box, xmax, boxinv, pre32, R2, status);
   return cudaGetLastError();
 }
-cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *, unsigned *status,
-                         cudaStream_t s) {
+cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg, float *xmax,
+                         unsigned *status, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
-  pos32_kernel<<<nblk(N, 256), 256, 0, s>>>(N, pos, pos32, status);
+  pos32_kernel<<<nblk(N, 256), 256, 0, s>>>(N, pos, atom_cfg, pos32, xmax, status);
   return cudaGetLastError();
 }
 cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
@@ -357,17 +364,21 @@ cudaError_t launch_geometry(int precision, int64_t Ntot, int64_t Btot, int M, co
                             const int *atom_off, const int *brev, const double *pos, const double *box,
                             const int *cnt, const int *nbr, const char4 *shift, const int *boff,
                             const int *poff, double R1, double R2, void *gA, void *gB, void *gcos,
-                            int max_slots, cudaStream_t s) {
+                            int max_slots, int *outer, cudaStream_t s) {
   if (Ntot == 0) return cudaSuccess;
+  if (outer) {
+    cudaError_t e = cudaMemsetAsync(outer, 0, Ntot * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+  }
   if (Btot > 0) {
     if (precision == 64)
       geometry_bond_kernel<double><<<nblk(Btot, 256), 256, 0, s>>>(
           Ntot, (int)Btot, M, atom_cfg, atom_off, brev, pos, box, nbr, shift, boff, R1, R2,
-          static_cast<dvec4 *>(gA), static_cast<dvec4 *>(gB));
+          static_cast<dvec4 *>(gA), static_cast<dvec4 *>(gB), nullptr);
     else
       geometry_bond_kernel<float><<<nblk(Btot, 256), 256, 0, s>>>(
           Ntot, (int)Btot, M, atom_cfg, atom_off, brev, pos, box, nbr, shift, boff, R1, R2,
-          static_cast<float4 *>(gA), static_cast<float4 *>(gB));
+          static_cast<float4 *>(gA), static_cast<float4 *>(gB), outer);
   }
   if (max_slots > 0) {
     if (precision == 64)
