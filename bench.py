@@ -8,13 +8,17 @@ One step = one GA generation's fitness evaluation done from scratch: neighbour b
 cache of all 300 cells, then E/F/W and the fitness Z of every parameter set (FP32 pair arithmetic,
 FP64 reductions). metric = atom-evals/s (P x total atoms per step / time).
 
-Prints one JSON line (rank 0). See the design notes for the roofline model.
+Prints one JSON line (rank 0). The roofline block rates the batched E/F/W kernel, timed alone by CUDA
+events on its stream, against the FP32 ALU peak (the kernel does no dense contraction and reads a few
+MB of geometry per launch).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -40,6 +44,10 @@ FLOP_PER_BOND = 59
 FLOP_PER_PAIR = 30
 FLOP_PER_ATOM = 16
 XU_PER_BOND = 6
+
+# ncu summary holding the batched kernel's DRAM bytes per launch, valid while these sources are unchanged
+TRAFFIC_PROFILE = "batch_kernel_ga_fitness_P200_C300.md"
+TRAFFIC_SOURCES = ("batch_kernel.cuh", "batch.cu", "common.cuh")
 
 
 def _dist():
@@ -108,6 +116,29 @@ def measured_peaks():
         with open(p) as f:
             return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def kernel_sources_digest():
+    """SHA-256 over the sources the batched kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1909_11474_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the batched kernel from the committed ncu summary, or None when the
+    kernel's sources changed after that capture."""
+    p = os.path.join(ROOT, "profiles", TRAFFIC_PROFILE)
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        for line in f:
+            m = re.match(r"^traffic: dram_bytes_per_launch=(\d+) kernel_sources_sha256=([0-9a-f]{64})\s*$", line)
+            if m:
+                return int(m.group(1)) if m.group(2) == kernel_sources_digest() else None
+    return None
 
 
 def flop_model(ctx, P):
@@ -194,8 +225,13 @@ def run_ours(args):
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
+    n0 = ctx.kernel_launches()
     t_step = timed(step, args.steps)
+    launches = ctx.kernel_launches() - n0
+    ctx.profile(True)                             # CUDA events around the batched kernel alone
     t_fit = timed(fitness_only, args.steps)
+    n_kern, ms_kern = ctx.profile_read()
+    ctx.profile(False)
     torch.cuda.synchronize()
     t_clock1 = time.time()
     clocks = sampler.stop(t_clock0, t_clock1)
@@ -234,20 +270,26 @@ def run_ours(args):
     h2d = (h_pos.numel() + h_box.numel() + h_par.numel()) * 8 + sum(v.numel() * v.element_size() for v in h_tg.values())
     d2h = h_Z.numel() * 8
 
-    # dominant kernel: the batched fitness kernel (+ its finalize), timed alone
-    k_time = t_fit / args.steps
+    # dominant kernel: the batched E/F/W + residual kernel, its launches timed by CUDA events that the
+    # library records on the launching stream
+    k_time = t_fit / args.steps                   # whole fitness call: prep + batched kernel + finalize
+    if n_kern != args.steps:
+        raise RuntimeError(f"expected {args.steps} timed batched-kernel launches, got {n_kern}")
+    b_time = ms_kern / 1e3 / n_kern
     peaks, peak_src = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
-    achieved = flop / k_time / 1e12
+    achieved = flop / b_time / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
-                "frac": round(achieved / fp32_peak, 4), "traffic": None,
-                "kernel": "batch_kernel<16,4,false,2,float> + fitness_finalize",
+                "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(),
+                "kernel": "tsf::batch_kernel<32,4,0,2,float> (every cell of the workload has m <= 4)",
+                "kernel_ms": round(1e3 * b_time, 4), "flop_per_launch": flop,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                f"(sm_max_mhz from MEASURED_PEAKS.json, {peak_src})",
-                "xu_ops_per_s": round(xu / k_time / 1e12, 4),
-                "xu_frac": round(xu / k_time / (props.multi_processor_count * 16 * sm_max * 1e6), 4)}
+                "xu_ops_per_s": round(xu / b_time / 1e12, 4),
+                "xu_frac": round(xu / b_time / (props.multi_processor_count * 16 * sm_max * 1e6), 4),
+                "fitness_call_frac": round(flop / k_time / 1e12 / fp32_peak, 4)}
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
@@ -263,7 +305,7 @@ def run_ours(args):
                             "note": "per GA generation after the first: geometry cache resident"},
            "e2e": {"value": round(ws * atom_evals * args.steps / t_e2e, 1), "unit": UNIT,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-           "gpu_launches": args.steps * (5 + 2), "roofline": roofline, "clocks": clocks}
+           "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks}
     if not args.quick:
         out["rows"] = {
             "adjoint": bench_adjoint(ctx_dev=dev, steps=max(3, args.steps // 5), flush=flush, stream=stream),

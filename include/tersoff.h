@@ -189,6 +189,22 @@ int tersoff_md_force(tersoff_ctx *ctx, int32_t N, const double *pos, const doubl
 /* Neighbour list of the last tersoff_md_force call, like tersoff_export_neighbors. Synchronous. */
 int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift);
 
+/* Measurement helpers; the paper has no counterpart.
+ * tersoff_kernel_launches: number of kernels the library has launched in this process, all contexts
+ * and devices together (a count kept on the host when each launch is accepted). */
+int64_t tersoff_kernel_launches(void);
+
+/* Start (enable = 1) or stop (enable = 0) timing the batched E/F/W kernel of this context: while on,
+ * every tersoff_eval / tersoff_fitness / tersoff_fitness_static records a CUDA event pair on its own
+ * stream around its batched-kernel launches (prep and finalize kernels excluded). Enabling clears
+ * earlier records. At most 4096 launch sequences are timed between two reads; later ones are not.
+ * Returns TERSOFF_E_ARG for a null context, TERSOFF_E_CUDA if an event cannot be created. */
+int tersoff_profile(tersoff_ctx *ctx, int32_t enable);
+
+/* Synchronise on the recorded events and return, in host memory, the number of timed launch
+ * sequences (*count) and their summed duration in milliseconds (*ms); clears the records. */
+int tersoff_profile_read(tersoff_ctx *ctx, int64_t *count, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ EXPORTED = (
     "tersoff_create", "tersoff_destroy", "tersoff_last_error", "tersoff_get_status",
     "tersoff_build_neighbors", "tersoff_export_neighbors", "tersoff_build_info", "tersoff_eval",
     "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
-    "tersoff_md_export_neighbors", "tersoff_fitness_static",
+    "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
+    "tersoff_profile", "tersoff_profile_read",
 )
 
 _vp = ctypes.c_void_p
@@ -72,6 +73,9 @@ def load():
         "tersoff_md_export_neighbors": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
         "tersoff_fitness_static": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _vp, _i32,
                                                   _vp, _vp, _vp, _vp]),
+        "tersoff_kernel_launches": (ctypes.c_int64, []),
+        "tersoff_profile": (ctypes.c_int, [_vp, _i32]),
+        "tersoff_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_f64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -145,6 +149,21 @@ class Context:
     # ---- calls ---------------------------------------------------------------------------------
     def get_status(self, stream=None) -> int:
         return int(self.lib.tersoff_get_status(self.h, _stream(stream)))
+
+    def kernel_launches(self) -> int:
+        """Kernels launched by the library in this process so far (all contexts)."""
+        return int(self.lib.tersoff_kernel_launches())
+
+    def profile(self, enable: bool = True):
+        """Start or stop CUDA-event timing of the batched E/F/W kernel (clears earlier records)."""
+        self._check(self.lib.tersoff_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """(timed launch sequences, summed milliseconds) since the last read; clears the records."""
+        n = ctypes.c_int64()
+        ms = _f64()
+        self._check(self.lib.tersoff_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms)))
+        return int(n.value), float(ms.value)
 
     def debug_bounds(self):
         """First shared-memory bounds violation recorded by a TSF_DEBUG_BOUNDS build (zeros if none)."""

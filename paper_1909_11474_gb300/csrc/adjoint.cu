@@ -396,7 +396,7 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
     const int64_t n = std::max<int64_t>(P, ctx.Ntot);
     prep_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, params, reinterpret_cast<float *>(consts),
                                                                    ctx.Ntot, tF, reinterpret_cast<float4 *>(tf4));
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
   AdjParams ap = {};
@@ -427,11 +427,11 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)(b.nitems * ap.ntiles), kThreads, smem, s>>>(ap);
-    e = cudaGetLastError();
+    e = launched(1);
     if (e != cudaSuccess) return e;
   }
   grad_finalize_kernel<<<(P + 7) / 8, 256, 0, s>>>(P, ctx.C, part, dpart, gpart, w[0], w[1], w[2], loss, L, dL);
-  return cudaGetLastError();
+  return launched(1);
 }
 
 }  // namespace tsf

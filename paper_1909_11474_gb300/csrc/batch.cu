@@ -67,7 +67,9 @@ static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t
     cfg.attrs = attr;
     cfg.numAttrs = 1;
   }
-  return cudaLaunchKernelEx(&cfg, kern, bp);
+  const cudaError_t el = cudaLaunchKernelEx(&cfg, kern, bp);
+  if (el == cudaSuccess) count_launches(1);
+  return el;
 }
 
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
@@ -83,7 +85,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
     else
       prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts),
                                                 ctx.Ntot, out.tF, reinterpret_cast<float4 *>(out.tF4));
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
   BatchParams bp = {};
@@ -112,6 +114,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.status = ctx.status.as<unsigned>();
   cudaError_t ez = cudaMemsetAsync(out.counters, 0, plan.buckets.size() * sizeof(int), s);
   if (ez != cudaSuccess) return ez;
+  const bool timed = ctx.timer.begin(s);
   int bi = 0;
   for (const Bucket &b : plan.buckets) {
     bp.counter = out.counters + bi++;
@@ -131,6 +134,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
     }
     if (e != cudaSuccess) return e;
   }
+  if (timed) ctx.timer.end(s);
   return cudaSuccess;
 }
 
@@ -178,7 +182,7 @@ cudaError_t launch_fitness_finalize(int P, int C, const double *part, const doub
   const int wpb = 8;
   fitness_finalize_kernel<<<(P + wpb - 1) / wpb, wpb * 32, 0, s>>>(P, C, part, dpart, we, wv, wf, Z,
                                                                    Zq, S);
-  return cudaGetLastError();
+  return launched(1);
 }
 
 }  // namespace tsf

@@ -1,6 +1,7 @@
 // capi.cu -- the C ABI of include/tersoff.h: context, neighbour build, batch planning and the
 // stream-ordered evaluation calls. Host code only; kernels live in the other translation units.
 #include <algorithm>
+#include <atomic>
 #include <iterator>
 #include <cmath>
 #include <cstdio>
@@ -12,6 +13,13 @@
 #include "ctx.hpp"
 
 using tsf::Ctx;
+
+namespace tsf {
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace tsf
 
 namespace {
 
@@ -185,7 +193,43 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   for (auto *b : bufs) b->release();
   c.hp_stage.release();
   if (c.stage_event) cudaEventDestroy(c.stage_event);
+  for (cudaEvent_t ev : c.timer.ev) cudaEventDestroy(ev);
   delete ctx;
+}
+
+int64_t tersoff_kernel_launches(void) { return (int64_t)tsf::g_launches.load(); }
+
+int tersoff_profile(tersoff_ctx *ctx, int32_t enable) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  TSF_CUDA(cudaSetDevice(c.device));
+  c.timer.on = false;
+  c.timer.n = 0;
+  if (!enable) return TERSOFF_OK;
+  while (c.timer.ev.size() < 2 * (size_t)tsf::KernelTimer::kCap) {
+    cudaEvent_t ev = nullptr;
+    TSF_CUDA(cudaEventCreate(&ev));
+    c.timer.ev.push_back(ev);
+  }
+  c.timer.on = true;
+  return TERSOFF_OK;
+}
+
+int tersoff_profile_read(tersoff_ctx *ctx, int64_t *count, double *ms) {
+  if (!ctx || !count || !ms) return fail(ctx, TERSOFF_E_ARG, "null argument%s");
+  Ctx &c = ctx->c;
+  TSF_CUDA(cudaSetDevice(c.device));
+  double total = 0.0;
+  for (int i = 0; i < c.timer.n; ++i) {
+    float t = 0.f;
+    TSF_CUDA(cudaEventSynchronize(c.timer.ev[2 * i + 1]));
+    TSF_CUDA(cudaEventElapsedTime(&t, c.timer.ev[2 * i], c.timer.ev[2 * i + 1]));
+    total += t;
+  }
+  *count = c.timer.n;
+  *ms = total;
+  c.timer.n = 0;
+  return TERSOFF_OK;
 }
 
 const char *tersoff_last_error(const tersoff_ctx *ctx) { return ctx ? ctx->c.err.c_str() : ""; }

@@ -108,6 +108,31 @@ struct Bucket {
   int item_off;    // first record of the bucket (records are per configuration and cluster rank)
 };
 
+// Start/stop event pairs recorded around the launches of one kernel family while enabled; read and
+// cleared by tersoff_profile_read. Capacity is fixed at enable time; launches past it go untimed.
+struct KernelTimer {
+  static constexpr int kCap = 4096;
+  bool on = false;
+  std::vector<cudaEvent_t> ev;   // [2 * kCap]: start, stop, start, stop, ...
+  int n = 0;                     // pairs recorded since the last read
+  bool begin(cudaStream_t s) {
+    if (!on || n >= kCap) return false;
+    return cudaEventRecord(ev[2 * n], s) == cudaSuccess;
+  }
+  void end(cudaStream_t s) {
+    if (cudaEventRecord(ev[2 * n + 1], s) == cudaSuccess) ++n;
+  }
+};
+
+// Process-wide count of kernels launched by the library (every launch site adds to it).
+void count_launches(int n);
+// cudaGetLastError after n kernel launches; the launches are counted when they were accepted.
+inline cudaError_t launched(int n) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) count_launches(n);
+  return e;
+}
+
 struct BatchPlan {
   int precision = 0;
   std::vector<Bucket> buckets;
@@ -140,6 +165,9 @@ struct Ctx {
   int md_N = 0, md_M = 0;
   DevBuf md_pos, md_cnt, md_nbr, md_shift, md_rev, md_cells, md_cellcnt, md_Pij, md_red, md_Ui;
   DevBuf md_boxd;
+
+  // --- measurement: CUDA events around each batched-kernel launch sequence, on its stream ---
+  mutable KernelTimer timer;
 };
 
 // ---- launchers (defined in the .cu files) ----

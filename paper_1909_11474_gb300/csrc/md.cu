@@ -500,7 +500,7 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
                                                         c.md_Pij.as<float4>(), reinterpret_cast<float *>(F));
   }
   md_reduce_kernel<<<1, 7 * 32, 0, s>>>(nblk, c.md_red.as<double>(), E, W);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launched(6);   // cells, neighbours, reverse, force, gather, reduce
   if (e != cudaSuccess) {
     err = std::string("CUDA error: ") + cudaGetErrorString(e);
     return TERSOFF_E_CUDA;

@@ -337,13 +337,13 @@ static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / 
 cudaError_t launch_box_prep(int C, const double *box, const float *xmax, double *boxinv, float *pre32,
                             double R2, unsigned *status, cudaStream_t s) {
   box_prep_kernel<<<nblk(C, 128), 128, 0, s>>>(C, box, xmax, boxinv, pre32, R2, status);
-  return cudaGetLastError();
+  return launched(1);
 }
 cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg, float *xmax,
                          unsigned *status, cudaStream_t s) {
   if (N == 0) return cudaSuccess;
   pos32_kernel<<<nblk(N, 256), 256, 0, s>>>(N, pos, atom_cfg, pos32, xmax, status);
-  return cudaGetLastError();
+  return launched(1);
 }
 cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
                                    const double *pos, const float4 *pos32, const double *box,
@@ -352,13 +352,13 @@ cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int 
   if (Ntot == 0) return cudaSuccess;
   neighbors_batch_kernel<<<nblk(Ntot * 32, 128), 128, 0, s>>>(Ntot, atom_off, atom_cfg, pos, pos32, box,
                                                               pre32, R2, M, cnt, nbr, shift, status);
-  return cudaGetLastError();
+  return launched(1);
 }
 cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,
                            const int *boff, int *brev, unsigned *status, cudaStream_t s) {
   if (Ntot == 0) return cudaSuccess;
   reverse_kernel<<<nblk(Ntot * M, 256), 256, 0, s>>>(Ntot, M, cnt, nbr, shift, boff, brev, status);
-  return cudaGetLastError();
+  return launched(1);
 }
 cudaError_t launch_geometry(int precision, int64_t Ntot, int64_t Btot, int M, const int *atom_cfg,
                             const int *atom_off, const int *brev, const double *pos, const double *box,
@@ -388,7 +388,7 @@ cudaError_t launch_geometry(int precision, int64_t Ntot, int64_t Btot, int M, co
       geometry_pair_kernel<float><<<nblk(Ntot * max_slots, 256), 256, 0, s>>>(
           Ntot, max_slots, cnt, M, boff, poff, static_cast<const float4 *>(gA), static_cast<float *>(gcos));
   }
-  return cudaGetLastError();
+  return launched((Btot > 0) + (max_slots > 0));
 }
 
 }  // namespace tsf

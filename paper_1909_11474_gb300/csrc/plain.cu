@@ -168,7 +168,7 @@ cudaError_t launch_plain(const Ctx &ctx, const double *params, int P, double *E,
                                             W + ((size_t)p * ctx.C + c) * 6);
     }
   }
-  return cudaGetLastError();
+  return launched(ctx.C * P);
 }
 
 }  // namespace tsf

@@ -186,3 +186,28 @@ def test_plain_fp64_path(ctx, which):
     assert force_err(F, Fr) < TOL64["F"]
     assert np.allclose(E, Eb.cpu().numpy(), rtol=1e-12, atol=1e-12)
     assert np.allclose(F, Fb.cpu().numpy(), rtol=1e-10, atol=1e-11)
+
+
+def test_kernel_timer_and_launch_count(ctx):
+    """The measurement hooks: one timed batched-kernel sequence per fitness call while enabled, none
+    after disabling, and a launch count that grows by the same amount for identical calls."""
+    w = I.workload_ga_batch(P=40, C=6)
+    cs = w["configs"]
+    _build(ctx, cs)
+    t = {"E": np.full(cs.C, -4.6), "W": np.zeros((cs.C, 6)), "F": np.zeros((cs.Ntot, 3)),
+         "mask": np.full(cs.C, 7, np.uint8)}
+    params, tg = torch.tensor(w["params"], device="cuda"), targets_to_device(t)
+    ctx.profile(True)
+    n0 = ctx.kernel_launches()
+    ctx.fitness(params, tg)
+    n1 = ctx.kernel_launches()
+    ctx.fitness(params, tg)
+    ctx.fitness(params, tg)
+    n3 = ctx.kernel_launches()
+    count, ms = ctx.profile_read()
+    assert count == 3 and ms > 0.0
+    assert n1 - n0 >= 3 and n3 - n1 == 2 * (n1 - n0)   # prep + batched kernel(s) + finalize per call
+    ctx.profile(False)
+    ctx.fitness(params, tg)
+    assert ctx.profile_read() == (0, 0.0)
+    assert ctx.get_status() == 0
