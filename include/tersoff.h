@@ -149,7 +149,7 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
  * and one fixed 8 MiB scratch array in device memory that every device loading the library keeps
  * until the process exits.
  *  Arguments, results and arithmetic are those of tersoff_fitness, and so are the results.
- *  Limit: P*8*8 + Ntot*32 + P*C*24 + C*24 + 256 bytes (each part rounded up to 256) must fit in 8 MiB, e.g.
+ *  Limit: P*8*8 + Ntot*32 + P*C*24 + C*24 + C*64 + 256 bytes (each part rounded up to 256) must fit in 8 MiB, e.g.
  *  P = 200 parameter sets over C = 300 cells of 64 atoms needs 2.1 MB; a larger request returns
  *  TERSOFF_E_ARG with the byte count in tersoff_last_error and launches nothing.
  *  The first call on a device looks up the scratch array's device address (once per device); make

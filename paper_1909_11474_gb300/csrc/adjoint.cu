@@ -61,21 +61,21 @@ __device__ __forceinline__ PConsts<Dual<K, float>> seed_consts(const PConsts<flo
   D.D0 = Dual<K, float>(k.D0);
   D.k1 = Dual<K, float>(k.k1);
   D.k0 = Dual<K, float>(k.k0);
-  D.alpha = Dual<K, float>(k.alpha);
+  D.mha = Dual<K, float>(k.mha);
   D.beta = Dual<K, float>(k.beta);
   D.h = Dual<K, float>(k.h);
   D.n = Dual<K, float>(k.n);
   D.inv2n = Dual<K, float>(k.inv2n);
   const float log2e = 1.4426950408889634f;
-  const float r0log2e = k.k0 / k.alpha;            // r0 log2 e
+  const float r0log2e = -0.5f * k.k0 / k.mha;     // r0 log2 e = k0 / alpha
 #pragma unroll
   for (int t = 0; t < K; ++t) {
     const int q = q0 + t;
     if (q == 0) D.D0.d[t] = 1.f;
-    if (q == 1) {                                  // k1 = -alpha log2e, k0 = alpha r0 log2e
+    if (q == 1) {                                  // k1 = -alpha log2e, k0 = alpha r0 log2e, mha = -alpha/2
       D.k1.d[t] = -log2e;
       D.k0.d[t] = r0log2e;
-      D.alpha.d[t] = 1.f;
+      D.mha.d[t] = -0.5f;
     }
     if (q == 2) D.k0.d[t] = -k.k1;                 // alpha log2e
     if (q == 3) D.beta.d[t] = 1.f;
@@ -95,14 +95,14 @@ __device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB,
                                              const float *aw, const PConsts<float> &Kf,
                                              float (&G)[kAdjG]) {
   constexpr int q0 = Q0;
-  float ux[M], uy[M], uz[M], r[M], ir[M], fc[M], fcp[M];
+  float ux[M], uy[M], uz[M], r[M], ir2[M], fc[M], fcp[M];
   int jl[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     const float4 A = sld(&sA[lb + j], 31);
     const float4 B = sld(&sB[lb + j], 32);
     ux[j] = A.x; uy[j] = A.y; uz[j] = A.z; r[j] = A.w;
-    ir[j] = B.x; fc[j] = B.y; fcp[j] = B.z;
+    ir2[j] = B.x; fc[j] = B.y; fcp[j] = B.z;
     jl[j] = __float_as_int(B.w) >> 16;
   }
   constexpr int NP = M * (M - 1) / 2;
@@ -119,7 +119,7 @@ __device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB,
   using D = Dual<K, float>;
   const PConsts<D> KD = seed_consts<K>(Kf, q0);
   D U, Px[M], Py[M], Pz[M];
-  atom_core<M, false, D, float>(ux, uy, uz, r, ir, fc, fcp, cs, KD, U, Px, Py, Pz);
+  atom_core<M, false, D, float>(ux, uy, uz, r, ir2, fc, fcp, cs, KD, U, Px, Py, Pz);
   const float ae = aw[0 * kAdjPT + pl];
   const float a0 = aw[1 * kAdjPT + pl], a1 = aw[2 * kAdjPT + pl], a2 = aw[3 * kAdjPT + pl];
   const float a3 = aw[4 * kAdjPT + pl], a4 = aw[5 * kAdjPT + pl], a5 = aw[6 * kAdjPT + pl];
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
   {
     const float4 *kc = reinterpret_cast<const float4 *>(a.consts) + 2 * (active ? p : a.P - 1);
     const float4 k0 = kc[0], k1 = kc[1];
-    K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.alpha = k0.w;
+    K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.mha = k0.w;
     K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
   }
   const int nat = rec.nat, s0 = rec.s0, ns = rec.ns;

@@ -77,14 +77,19 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   const bool f64 = plan.precision == 64;
   // per-call preparation: per-parameter-set constants and the target forces in the working precision
   {
-    const int64_t n = std::max<int64_t>(P, out.tF ? ctx.Ntot : 0);
+    const int64_t n = std::max<int64_t>(std::max<int64_t>(P, ctx.C), out.tF ? ctx.Ntot : 0);
     const unsigned blocks = (unsigned)((n + 255) / 256);
+    const bool tew = mode == kModeFitness && out.tEW;
     if (f64)
       prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts),
-                                                 ctx.Ntot, out.tF, reinterpret_cast<dvec4 *>(out.tF4));
+                                                 ctx.Ntot, out.tF, reinterpret_cast<dvec4 *>(out.tF4), ctx.C,
+                                                 ctx.atom_off.as<int>(), out.tE, out.tW,
+                                                 tew ? reinterpret_cast<double *>(out.tEW) : nullptr);
     else
       prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts),
-                                                ctx.Ntot, out.tF, reinterpret_cast<float4 *>(out.tF4));
+                                                ctx.Ntot, out.tF, reinterpret_cast<float4 *>(out.tF4), ctx.C,
+                                                ctx.atom_off.as<int>(), out.tE, out.tW,
+                                                tew ? reinterpret_cast<float *>(out.tEW) : nullptr);
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
@@ -109,6 +114,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.tW = out.tW;
   bp.tF4 = out.tF4;
   bp.tmask = out.tmask;
+  bp.tEW = out.tEW;
   bp.part = out.part;
   bp.dpart = out.dpart;
   bp.status = ctx.status.as<unsigned>();
@@ -138,36 +144,67 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   return cudaSuccess;
 }
 
-// One warp per parameter set: S_q = sum_c part[p][c][q] and D_q = sum_c dpart[c][q] in FP64 with a
-// fixed lane-strided order and a fixed xor-shuffle tree, then Zq = sqrt(S_q/D_q) (0 where D_q = 0),
-// Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not finite.
-__global__ void fitness_finalize_kernel(int P, int C, const double *__restrict__ part,
-                                        const double *__restrict__ dpart, double we, double wv,
-                                        double wf, double *__restrict__ Z, double *__restrict__ Zq,
-                                        double *__restrict__ S) {
-  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (p >= P) return;
-  double s[3] = {0, 0, 0}, d[3] = {0, 0, 0};
-  for (int c = lane; c < C; c += 32)
+// Fitness of every parameter set from the per-(p, c) residual terms of the batched kernel
+// (Eq. 15-19): S_q[p] = sum_c part[p][c][q]; D_e = sum_c E*_c^2 and D_v = sum_c |W*_c|^2 over the
+// configurations whose mask has the quantity; D_f = sum_c of the per-configuration |F*|^2 sums.
+// All sums in FP64 in a fixed order (threads strided over c, then a fixed xor-shuffle tree and the
+// warps in index order). Zq = sqrt(S_q/D_q) (0 where D_q = 0), Z = sum_q w_q Zq, and Z = +inf when
+// any residual sum of p is not finite. One block per kFinPB parameter sets.
+constexpr int kFinPB = 4;
+constexpr int kFinThreads = 256;
+
+template <typename R>
+__global__ void __launch_bounds__(kFinThreads) fitness_finalize_kernel(
+    int P, int C, const R *__restrict__ part, const R *__restrict__ dpart, const double *__restrict__ tE,
+    const double *__restrict__ tW, const uint8_t *__restrict__ tmask, double we, double wv, double wf,
+    double *__restrict__ Z, double *__restrict__ Zq, double *__restrict__ S) {
+  constexpr int NV = 3 * kFinPB + 3;   // S_q of the block's parameter sets, then D_q
+  constexpr int NWARP = kFinThreads / 32;
+  __shared__ double red[NWARP][NV];
+  const int p0 = blockIdx.x * kFinPB;
+  const int np = min(kFinPB, P - p0);
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  for (int c = threadIdx.x; c < C; c += kFinThreads) {
+    const uint8_t m = tmask[c];
+    if (m & 1) v[3 * kFinPB] += tE[c] * tE[c];
+    if (m & 2)
+      for (int k = 0; k < 6; ++k) v[3 * kFinPB + 1] += tW[6 * c + k] * tW[6 * c + k];
+    if (m & 4) v[3 * kFinPB + 2] += (double)dpart[c];
+#pragma unroll
+    for (int j = 0; j < kFinPB; ++j)
+      if (j < np)
+        for (int q = 0; q < 3; ++q) v[3 * j + q] += (double)part[((size_t)(p0 + j) * C + c) * 3 + q];
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x < np) {
+    const int j = threadIdx.x;
+    double s[3], d[3];
     for (int q = 0; q < 3; ++q) {
-      s[q] += part[((size_t)p * C + c) * 3 + q];
-      d[q] += dpart[(size_t)c * 3 + q];
+      s[q] = 0.0;
+      d[q] = 0.0;
+      for (int w = 0; w < NWARP; ++w) {
+        s[q] += red[w][3 * j + q];
+        d[q] += red[w][3 * kFinPB + q];
+      }
     }
-  for (int off = 16; off > 0; off >>= 1)
-    for (int q = 0; q < 3; ++q) {
-      s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-      d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
-    }
-  if (lane == 0) {
-    const double w[3] = {we, wv, wf};
+    const double wq[3] = {we, wv, wf};
     double z = 0.0, zq[3];
     bool finite = true;
     for (int q = 0; q < 3; ++q) {
       finite = finite && isfinite(s[q]);
       zq[q] = d[q] > 0.0 ? sqrt(s[q] / d[q]) : 0.0;
-      z += w[q] * zq[q];
+      z += wq[q] * zq[q];
     }
+    const int p = p0 + j;
     Z[p] = finite ? z : INFINITY;
     if (Zq)
       for (int q = 0; q < 3; ++q) Zq[(size_t)p * 3 + q] = zq[q];
@@ -176,12 +213,19 @@ __global__ void fitness_finalize_kernel(int P, int C, const double *__restrict__
   }
 }
 
-cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
+cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *part, const void *dpart,
+                                    const double *tE, const double *tW, const uint8_t *tmask,
                                     double we, double wv, double wf, double *Z, double *Zq,
                                     double *S, cudaStream_t s) {
-  const int wpb = 8;
-  fitness_finalize_kernel<<<(P + wpb - 1) / wpb, wpb * 32, 0, s>>>(P, C, part, dpart, we, wv, wf, Z,
-                                                                   Zq, S);
+  const unsigned blocks = (unsigned)((P + kFinPB - 1) / kFinPB);
+  if (precision == 64)
+    fitness_finalize_kernel<double><<<blocks, kFinThreads, 0, s>>>(
+        P, C, static_cast<const double *>(part), static_cast<const double *>(dpart), tE, tW, tmask, we, wv,
+        wf, Z, Zq, S);
+  else
+    fitness_finalize_kernel<float><<<blocks, kFinThreads, 0, s>>>(
+        P, C, static_cast<const float *>(part), static_cast<const float *>(dpart), tE, tW, tmask, we, wv,
+        wf, Z, Zq, S);
   return launched(1);
 }
 

@@ -73,10 +73,11 @@ __device__ __forceinline__ void sst(T *p, const T &v, int site) {
 }
 
 // Per-parameter-set constants (prepared once per call by prep_kernel from the FP64 parameters):
-// x = exp(-alpha (r - r0)) = 2^(k1 r + k0), f_R = D0 x^2, f_A = 2 D0 x (Eq. 4-5, 11-14 at S = 2).
+// x = exp(-alpha (r - r0)) = 2^(k1 r + k0), f_R = D0 x^2, f_A = 2 D0 x (Eq. 4-5, 11-14 at S = 2);
+// mha = -alpha/2; inv2n = -1/(2n).
 template <typename R>
 struct PConsts {
-  R D0, k1, k0, alpha, beta, h, n, inv2n;
+  R D0, k1, k0, mha, beta, h, n, inv2n;
 };
 
 // b = (1 + zeta^n)^(-1/(2n)) and b' = db/dzeta = -1/2 b zeta^(n-1) / (1 + zeta^n)   (Eq. 6).
@@ -97,25 +98,30 @@ struct AtomAcc {
   R U, W[6];
 };
 
-// The per-atom core of passes 1 and 2: from the bond geometry (unit vectors, r, 1/r, f_C, f_C', the
+// The per-atom core of passes 1 and 2: from the bond geometry (unit vectors, r, 2/r, f_C, f_C', the
 // cosines of the bond pairs; R) and the parameter constants (T: R itself, or a dual number carrying
 // parameter tangents), U = sum_j f_C (f_R - b f_A), which is twice the site energy U_i of Eq. 2,
 // and P_ij = dU_i/dd_ij of every bond (the derivative of U_i itself, 1/2 included). INNER: every bond
 // is inside R1 (callers pass f_C = 1 and f_C' = 0 as constants, which the compiler folds away).
+//
+// Per bond, with h_A = f_A/2 = D0 x and u2 = 2 (1 + zeta^n):
+//   b = 2^(-(log2 u2 - 1)/(2n)),   f_R - b f_A = f_R - 2 b h_A,
+//   c_ij = dU_i/dzeta_ij = -1/2 f_C f_A b' = f_C (b h_A) zeta^n / (zeta u2),
+//   rad_ij = 1/2 [f_C' (f_R - b f_A) + f_C (f_R' - b f_A')],   f_R' - b f_A' = -alpha (2 f_R - b f_A),
+// the same quantities as Eq. 3-6 and their derivatives, with the constant factors folded.
 template <int M, bool INNER, typename T, typename R>
 __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], const R (&uz)[M],
-                                          const R (&r)[M], const R (&ir)[M], const R (&fc)[M],
+                                          const R (&r)[M], const R (&ir2)[M], const R (&fc)[M],
                                           const R (&fcp)[M], const R *cs, const PConsts<T> &K, T &U,
                                           T (&Px)[M], T (&Py)[M], T (&Pz)[M]) {
   // ---- pass 1: pair functions (Eq. 4-5 with Eq. 11-14 at S = 2) and zeta (Eq. 7, 10)
   constexpr int NP = M * (M - 1) / 2;
-  T fR[M], fA[M], zeta[M], tq[NP > 0 ? NP : 1];
+  T fR[M], hA[M], zeta[M], tq[NP > 0 ? NP : 1];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     const T x = ex2(r[j] * K.k1 + K.k0);
-    const T Dx = K.D0 * x;
-    fR[j] = Dx * x;
-    fA[j] = Dx + Dx;
+    hA[j] = K.D0 * x;                              // f_A / 2
+    fR[j] = hA[j] * x;
     zeta[j] = T(0.0f);
   }
   {
@@ -138,13 +144,16 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
   U = T(0.0f);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    T b, bp;
-    bond_order(zeta[j], K, b, bp);
-    const T e = fR[j] - b * fA[j];                 // f_R - b f_A
+    const T z = zeta[j] > T(1e-30f) ? zeta[j] : T(1e-30f);   // see bond_order
+    const T zn = ex2(K.n * lg2(z));                // zeta^n
+    const T u2 = zn * R(2) + R(2);
+    const T b = ex2(K.inv2n * lg2(u2) - K.inv2n);  // (1 + zeta^n)^(-1/(2n))
+    const T bh = b * hA[j];                        // b f_A / 2
+    const T e = bh * R(-2) + fR[j];                // f_R - b f_A
     U += fc[j] * e;                                // Eq. 3 (the 1/2 of Eq. 2 is applied by callers)
-    cc[j] = (R(-0.5) * fc[j]) * fA[j] * bp;        // dU_i / dzeta_ij
-    const T de = -K.alpha * (fR[j] + e);           // f_R' - b f_A' = -alpha (2 f_R - b f_A)
-    rad[j] = R(0.5) * (fcp[j] * e + fc[j] * de);
+    cc[j] = fc[j] * bh * zn * rcp(z * u2);         // dU_i / dzeta_ij
+    const T mde = K.mha * (fR[j] + e);             // (f_R' - b f_A') / 2
+    rad[j] = R(0.5) * fcp[j] * e + fc[j] * mde;
   }
 
   // ---- pass 2: dU_i/dd_ij
@@ -189,18 +198,18 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
   }
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    const R ir2 = ir[j] + ir[j];                   // 2/r restores the factor 2 of g' = 2 t
-    // s_ij = sum_k w_jk cos_jk = u_ij . A_ij, since cos_jk = u_ij . u_ik
+    // 2/r restores the factor 2 of g' = 2 t; s_ij = sum_k w_jk cos_jk = u_ij . A_ij, since
+    // cos_jk = u_ij . u_ik
     const T sj = ux[j] * Ax[j] + uy[j] * Ay[j] + uz[j] * Az[j];
-    const T coef = rad[j] + fcp[j] * Rg[j] - sj * ir2;
-    Px[j] = coef * ux[j] + ir2 * Ax[j];
-    Py[j] = coef * uy[j] + ir2 * Ay[j];
-    Pz[j] = coef * uz[j] + ir2 * Az[j];
+    const T coef = rad[j] + fcp[j] * Rg[j] - sj * ir2[j];
+    Px[j] = coef * ux[j] + ir2[j] * Ax[j];
+    Py[j] = coef * uy[j] + ir2[j] * Ay[j];
+    Pz[j] = coef * uz[j] + ir2[j] * Az[j];
   }
 }
 
 // Passes 1 and 2 for one atom per atom slot, M = the warp's largest neighbour count.
-// sA/sB: bond records (u_x, u_y, u_z, r), (1/r, f_C, f_C', rev | j << 16); sC: pair cosines; lb/lq: this
+// sA/sB: bond records (u_x, u_y, u_z, r), (2/r, f_C, f_C', rev | j << 16); sC: pair cosines; lb/lq: this
 // atom's first bond / pair in shared memory; m: its neighbour count (<= M). EXACT: every slot has
 // m == M, so no bond is a phantom.
 template <int M, int PT, bool EXACT, bool INNER, typename R>
@@ -209,14 +218,14 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
                                              const R *__restrict__ sC, R *__restrict__ stage,
                                              int lb, int lq, int m, bool store, int pl,
                                              const PConsts<R> &K, AtomAcc<R> &acc) {
-  R ux[M], uy[M], uz[M], r[M], ir[M], fc[M], fcp[M];
+  R ux[M], uy[M], uz[M], r[M], ir2[M], fc[M], fcp[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     if (EXACT || j < m) {
       const auto A = sld(&sA[lb + j], 1);
       const auto B = sld(&sB[lb + j], 2);
       ux[j] = A.x; uy[j] = A.y; uz[j] = A.z; r[j] = A.w;
-      ir[j] = B.x;
+      ir2[j] = B.x;
       if constexpr (INNER) {
         fc[j] = R(1);
         fcp[j] = R(0);
@@ -226,7 +235,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
       }
     } else {
       ux[j] = R(0); uy[j] = R(0); uz[j] = R(0); r[j] = R(1);
-      ir[j] = R(0); fc[j] = R(0); fcp[j] = R(0);
+      ir2[j] = R(0); fc[j] = R(0); fcp[j] = R(0);
     }
   }
   constexpr int NP = M * (M - 1) / 2;
@@ -254,7 +263,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
 
   R U, Px[M], Py[M], Pz[M];
-  atom_core<M, INNER, R, R>(ux, uy, uz, r, ir, fc, fcp, cs, K, U, Px, Py, Pz);
+  atom_core<M, INNER, R, R>(ux, uy, uz, r, ir2, fc, fcp, cs, K, U, Px, Py, Pz);
   R W0 = R(0), W1 = R(0), W2 = R(0), W3 = R(0), W4 = R(0), W5 = R(0);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
@@ -353,7 +362,9 @@ struct BatchParams {
   const double *tE, *tW;
   const void *tF4;                 // R4 [Ntot]: target force (x, y, z) and |F*|^2
   const uint8_t *tmask;
-  double *part, *dpart;
+  const void *tEW;                 // R [C][8]: E*, W*[6], 1/N of every configuration (fitness)
+  void *part;                      // R [P][C][3]: S_e, S_v, S_f terms of every (p, c) (fitness)
+  void *dpart;                     // R [C]: sum of |F*|^2 over the configuration's atoms (fitness)
   unsigned *status;
 };
 
@@ -533,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
       {
         const R4 *kc = reinterpret_cast<const R4 *>(a.consts) + 2 * (active ? p : a.P - 1);
         const R4 k0 = kc[0], k1 = kc[1];
-        K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.alpha = k0.w;
+        K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.mha = k0.w;
         K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
       }
       AtomAcc<R> acc;
@@ -662,49 +673,47 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
 
       if (rank == 0 && tid < PT) {
         const int pp = tile * PT + tid;
-        double q[kNRed];
+        R q[kNRed];
 #pragma unroll
         for (int k = 0; k < kNRed; ++k) {
-          double s = 0.0;
-          for (unsigned r = 0; r < ncta; ++r) s += (double)sld(&tot[(r * kNRed + k) * PT + tid], 20);
+          R s = R(0);
+          for (unsigned r = 0; r < ncta; ++r) s += sld(&tot[(r * kNRed + k) * PT + tid], 20);
           q[k] = s;
         }
         if (pp < a.P) {
           if (a.mode == kModeEval) {
-            if (a.E) a.E[(size_t)pp * a.C + c] = q[0];
+            if (a.E) a.E[(size_t)pp * a.C + c] = (double)q[0];
             if (a.W)
-              for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = q[1 + k];
+              for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = (double)q[1 + k];
           } else {
-            const double invN = 1.0 / (double)nat;
+            // per-atom residuals of Eq. 17-18 in the working precision (the FP64 sums over
+            // configurations are formed by the finalize kernel)
+            const R *tw = reinterpret_cast<const R *>(a.tEW) + (size_t)c * 8;
+            const R invN = tw[7];
             bool finite = isfinite(q[0]) && isfinite(q[8]);
+#pragma unroll
             for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);
-            double se = 0.0, sv = 0.0, sfv = 0.0;
+            R se = R(0), sv = R(0), sfv = R(0);
             if (mask & 1) {
-              const double d = q[0] * invN - a.tE[c];
+              const R d = q[0] * invN - tw[0];
               se = d * d;
             }
-            if (mask & 2)
+            if (mask & 2) {
+#pragma unroll
               for (int k = 0; k < 6; ++k) {
-                const double d = q[1 + k] * invN - a.tW[c * 6 + k];
+                const R d = q[1 + k] * invN - tw[1 + k];
                 sv += d * d;
               }
+            }
             if (mask & 4) sfv = q[7];
-            if (!finite) se = sv = sfv = __longlong_as_double(0x7ff8000000000000ll);
-            double *o = a.part + ((size_t)pp * a.C + c) * 3;
+            if (!finite) se = sv = sfv = R(NAN);
+            R *o = reinterpret_cast<R *>(a.part) + ((size_t)pp * a.C + c) * 3;
             o[0] = se;
             o[1] = sv;
             o[2] = sfv;
           }
         }
-        if (fit && tile == 0 && tid == 0) {
-          double de = 0.0, dv = 0.0;
-          if (mask & 1) de = a.tE[c] * a.tE[c];
-          if (mask & 2)
-            for (int k = 0; k < 6; ++k) dv += a.tW[c * 6 + k] * a.tW[c * 6 + k];
-          a.dpart[c * 3 + 0] = de;
-          a.dpart[c * 3 + 1] = dv;
-          a.dpart[c * 3 + 2] = (mask & 4) ? q[9] : 0.0;
-        }
+        if (fit && tile == 0 && tid == 0) reinterpret_cast<R *>(a.dpart)[c] = (mask & 4) ? q[9] : R(0);
       }
       // the next tile (or item) reuses the stage and, in rank 0, the collected totals
       if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
@@ -712,12 +721,21 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
   }
 }
 
-// Per call: FP32/FP64 constants of every parameter set and the target forces as R4 (x, y, z, |F|^2).
+// Per call: FP32/FP64 constants of every parameter set, the target forces as R4 (x, y, z, |F|^2) and,
+// when tEW is given, each configuration's targets and atom count as R [C][8] (E*, W*[6], 1/N).
 template <typename R>
 __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restrict__ consts,
                             int64_t Ntot, const double *__restrict__ tF,
-                            typename Vec4<R>::T *__restrict__ tF4) {
+                            typename Vec4<R>::T *__restrict__ tF4, int C = 0,
+                            const int *__restrict__ atom_off = nullptr, const double *__restrict__ tE = nullptr,
+                            const double *__restrict__ tW = nullptr, R *__restrict__ tEW = nullptr) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tEW && t < C) {
+    R *o = tEW + 8 * t;
+    o[0] = (R)tE[t];
+    for (int k = 0; k < 6; ++k) o[1 + k] = (R)tW[6 * t + k];
+    o[7] = (R)(1.0 / (double)(atom_off[t + 1] - atom_off[t]));
+  }
   if (t < P) {
     const double *x = params + 6 * t;
     const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
@@ -726,7 +744,7 @@ __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restr
     o[0] = (R)D0;
     o[1] = (R)(-al * log2e);
     o[2] = (R)(al * r0 * log2e);
-    o[3] = (R)al;
+    o[3] = (R)(-0.5 * al);
     o[4] = (R)be;
     o[5] = (R)h;
     o[6] = (R)n;

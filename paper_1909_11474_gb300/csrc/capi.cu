@@ -186,7 +186,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   cudaDeviceSynchronize();
   tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv, &c.pre32, &c.xmax, &c.counters,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
-                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.outer, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
+                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.outer, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart, &c.tew,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_Ui, &c.md_boxd};
@@ -446,6 +446,7 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
   TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
   TSF_CUDA(c.tf4.ensure((size_t)c.Ntot * sizeof(tsf::dvec4)));
   TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
@@ -453,15 +454,17 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   o.counters = c.counters.as<int>();
   o.consts = c.work.p;
   o.tF4 = c.tf4.p;
+  o.tEW = c.tew.p;
   o.tE = tg->E;
   o.tW = tg->W;
   o.tF = tg->F;
   o.tmask = tg->mask;
-  o.part = c.part.as<double>();
-  o.dpart = c.dpart.as<double>();
+  o.part = c.part.p;
+  o.dpart = c.dpart.p;
   cudaStream_t s = S(stream);
   TSF_CUDA(tsf::launch_batch(c, precision == 64 ? c.plan64 : c.plan32, params, P, tsf::kModeFitness, o, s));
-  TSF_CUDA(tsf::launch_fitness_finalize(P, c.C, o.part, o.dpart, w[0], w[1], w[2], Z, Zq, Sq, s));
+  TSF_CUDA(tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, tg->E, tg->W, tg->mask, w[0], w[1],
+                                        w[2], Z, Zq, Sq, s));
   return TERSOFF_OK;
 }
 

@@ -79,7 +79,7 @@ struct Geometry {
   const int *poff;      // [Ntot+1] first unordered bond pair of atom i
   const int *brev;      // [Btot] bond index of the reverse entry (j; i, -n)
   const void *gA;       // [Btot] R4: unit vector d/r (x, y, z), r
-  const void *gB;       // [Btot] R4: 1/r, f_C(r), f_C'(r), 0
+  const void *gB;       // [Btot] R4: 2/r, f_C(r), f_C'(r), rev | j << 16
   const void *gcos;     // [Qtot] R: cos theta of pair (e, f), e < f, row-major over e
 };
 
@@ -159,7 +159,7 @@ struct Ctx {
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
   DevBuf outer;   // [Ntot] int: nonzero if the atom has a bond beyond R1 (f_C != 1)
   BatchPlan plan32, plan64;
-  DevBuf part, dpart, work, tf4, gpart;
+  DevBuf part, dpart, work, tf4, gpart, tew;
 
   // --- MD state ---
   int md_N = 0, md_M = 0;
@@ -195,8 +195,9 @@ struct BatchOut {
   double *W;          // [P][C][6]
   const double *tE, *tW, *tF;
   const uint8_t *tmask;
-  double *part;       // [P][C][3]
-  double *dpart;      // [C][3]
+  void *part;         // workspace: [P][C][3] residual sums per (p, c) (working precision)
+  void *dpart;        // workspace: [C] sum of |F*|^2 per configuration (working precision)
+  void *tEW;          // workspace: [C][8] E*, W*[6], 1/N per configuration (working precision)
   void *consts;       // workspace: [P][8] per-parameter-set constants (working precision)
   void *tF4;          // workspace: [Ntot] target forces as 4-vectors (working precision)
   int *counters;      // workspace: one work counter per launch bucket
@@ -204,7 +205,8 @@ struct BatchOut {
 enum BatchMode { kModeEval = 0, kModeFitness = 1 };
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s);
-cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
+cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *part, const void *dpart,
+                                    const double *tE, const double *tW, const uint8_t *tmask,
                                     double we, double wv, double wf, double *Z, double *Zq,
                                     double *S, cudaStream_t s);
 // capi.cu: FP64 geometry records on demand

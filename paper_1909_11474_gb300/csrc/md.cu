@@ -220,7 +220,7 @@ __device__ __forceinline__ void md_atom(const R (&ux)[kMdMaxM], const R (&uy)[kM
     const R e = fR[j] - b * fA[j];
     U += R(0.5) * fc[j] * e;
     cc[j] = R(-0.5) * fc[j] * fA[j] * bp;
-    const R de = -K.alpha * (fR[j] + e);
+    const R de = R(2) * K.mha * (fR[j] + e);    // f_R' - b f_A' = -alpha (f_R + e)
     rad[j] = R(0.5) * (fcp[j] * e + fc[j] * de);
   }
   R Ax[M], Ay[M], Az[M], s[M], Rg[M];
@@ -484,14 +484,14 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
   const double log2e = 1.4426950408889634;
   if (precision == 64) {
-    PConsts<double> K{D0, -al * log2e, al * r0 * log2e, al, be, h, n, -0.5 / n};
+    PConsts<double> K{D0, -al * log2e, al * r0 * log2e, -0.5 * al, be, h, n, -0.5 / n};
     md_force_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, u4, m4, c.md_cnt.as<int>(),
                                                         c.md_nbr.as<int>(), c.md_shift.as<char4>(),
                                                         c.md_Pij.as<dvec4>(), c.md_red.as<double>(), st);
     md_gather_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, c.md_cnt.as<int>(), c.md_rev.as<int>(),
                                                          c.md_Pij.as<dvec4>(), reinterpret_cast<double *>(F));
   } else {
-    PConsts<float> K{(float)D0, (float)(-al * log2e), (float)(al * r0 * log2e), (float)al, (float)be, (float)h,
+    PConsts<float> K{(float)D0, (float)(-al * log2e), (float)(al * r0 * log2e), (float)(-0.5 * al), (float)be, (float)h,
                      (float)n, (float)(-0.5 / n)};
     md_force_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, u4, m4, c.md_cnt.as<int>(),
                                                        c.md_nbr.as<int>(), c.md_shift.as<char4>(),

@@ -249,7 +249,7 @@ __device__ __forceinline__ int64_t bond_owner(const int *__restrict__ boff, int6
   return lo;
 }
 
-// Per bond: unit vector, r, 1/r, f_C, f_C' and, packed into one int (rev | j << 16), the
+// Per bond: unit vector, r, 2/r, f_C, f_C' and, packed into one int (rev | j << 16), the
 // configuration-local indices of the reverse bond and of the neighbour atom (4th slot: as a double,
 // or as the bit pattern of the int in the FP32 record). The bond vector d is formed in FP64 by the
 // expression of the membership test (where the cancellation happens); FP32 records round it and then
@@ -290,14 +290,14 @@ __global__ void geometry_bond_kernel(int64_t Ntot, int Btot, int M, const int *_
       fcp = (float)(-0.5 * M_PI / (R2 - R1)) * sinpif(w);
     }
     A = make_float4(dx * ir, dy * ir, dz * ir, r);
-    Bv = make_float4(ir, fc, fcp, __int_as_float(rl));
+    Bv = make_float4(ir + ir, fc, fcp, __int_as_float(rl));
   } else {
     const double ir = rsqrt(p.r2);
     const double r = p.r2 * ir;
     double fc, fcp;
     cutoff_fc(r, R1, R2, fc, fcp);
     A = make_dvec4(p.dx * ir, p.dy * ir, p.dz * ir, r);
-    Bv = make_dvec4(ir, fc, fcp, (double)rl);
+    Bv = make_dvec4(ir + ir, fc, fcp, (double)rl);
   }
   gA[b] = A;
   gB[b] = Bv;

@@ -1,8 +1,8 @@
 // noalloc.cu -- tersoff_fitness_static: the fitness call of tersoff_fitness with no device
-// allocation at call time. Its per-call scratch (per-parameter-set constants, target forces in the
-// working precision, the per-(parameter set, configuration) residual sums and the per-configuration
-// target norms) lives in one file-scope __device__ array of fixed size instead of context buffers
-// that grow on demand.
+// allocation at call time. Its per-call scratch (per-parameter-set constants, targets in the working
+// precision, the per-(parameter set, configuration) residual terms and the per-configuration target
+// force norms) lives in one file-scope __device__ array of fixed size instead of context buffers that
+// grow on demand.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -50,8 +50,9 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   const size_t b_tf4 = align256((size_t)c.Ntot * sizeof(tsf::dvec4));
   const size_t b_part = align256((size_t)P * c.C * 3 * sizeof(double));
   const size_t b_dpart = align256((size_t)c.C * 3 * sizeof(double));
+  const size_t b_tew = align256((size_t)c.C * 8 * sizeof(double));
   const size_t b_count = align256(64 * sizeof(int));
-  const size_t need = b_consts + b_tf4 + b_part + b_dpart + b_count;
+  const size_t need = b_consts + b_tf4 + b_part + b_dpart + b_tew + b_count;
   if (need > kScratchBytes) {
     char buf[200];
     std::snprintf(buf, sizeof(buf), "tersoff_fitness_static needs %zu bytes of scratch for P=%d, C=%d, Ntot=%lld; "
@@ -77,8 +78,8 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   }
 
   // every scratch element read by the kernels is written earlier in the same call (constants and
-  // targets by the prep kernel, every (p, c) residual and every configuration's norms by the batch
-  // kernel); the work counters, which must start at zero, are cleared by the launch itself
+  // targets by the prep kernel, every (p, c) residual and every configuration's force norm by the
+  // batch kernel); the work counters, which must start at zero, are cleared by the launch itself
   tsf::BatchOut o = {};
   o.tE = tg->E;
   o.tW = tg->W;
@@ -86,16 +87,19 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   o.tmask = tg->mask;
   o.consts = base;
   o.tF4 = base + b_consts;
-  o.part = reinterpret_cast<double *>(base + b_consts + b_tf4);
-  o.dpart = reinterpret_cast<double *>(base + b_consts + b_tf4 + b_part);
-  o.counters = reinterpret_cast<int *>(base + b_consts + b_tf4 + b_part + b_dpart);
+  o.part = base + b_consts + b_tf4;
+  o.dpart = base + b_consts + b_tf4 + b_part;
+  o.tEW = base + b_consts + b_tf4 + b_part + b_dpart;
+  o.counters = reinterpret_cast<int *>(base + b_consts + b_tf4 + b_part + b_dpart + b_tew);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (precision == 64) {
     const int rc = tsf::ensure_geom64(ctx, s);   // kernels into buffers made by the neighbour build
     if (rc) return rc;
   }
   cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
-  if (e == cudaSuccess) e = tsf::launch_fitness_finalize(P, c.C, o.part, o.dpart, w[0], w[1], w[2], Z, Zq, S, s);
+  if (e == cudaSuccess)
+    e = tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, tg->E, tg->W, tg->mask, w[0], w[1], w[2],
+                                     Z, Zq, S, s);
   if (e != cudaSuccess) {
     char buf[160];
     std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));
