@@ -24,6 +24,11 @@ __host__ __device__ inline dvec4 make_dvec4(double x, double y, double z, double
   return v;
 }
 
+// Process-wide count of device-buffer (re)allocations: a captured launch sequence is valid only while
+// none of the buffers it was captured with has moved.
+uint64_t buffer_generation();
+void bump_buffer_generation();
+
 // Grow-only device buffer owned by the context.
 struct DevBuf {
   void *p = nullptr;
@@ -33,6 +38,7 @@ struct DevBuf {
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
+    bump_buffer_generation();
     cudaError_t e = cudaMalloc(&p, n);
     if (e == cudaSuccess) bytes = n;
     return e;
@@ -135,8 +141,17 @@ inline cudaError_t launched(int n) {
 
 struct BatchPlan {
   int precision = 0;
+  uint64_t gen = 0;  // distinct for every plan built (part of the key of captured launch sequences)
   std::vector<Bucket> buckets;
   DevBuf items;    // CtaRec [total CTAs]
+};
+
+// A launch sequence captured into a CUDA graph and the key it was captured under (every pointer and
+// scalar its launches depend on); replayed while the key matches.
+struct GraphCache {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+  int kernels = 0;   // kernel launches in the sequence
 };
 
 struct Ctx {
@@ -154,7 +169,9 @@ struct Ctx {
   std::vector<int> h_atom_off, h_cnt, h_boff, h_poff, h_cfg_maxm;
   PinnedBuf hp_stage;   // pinned staging: atom table uploads, neighbour-count readback, offsets
   cudaEvent_t stage_event = nullptr;   // recorded after the staging buffer's last upload
-  DevBuf atom_off, atom_cfg, pos, pos32, box, boxinv, pre32, xmax, cnt, nbr, shift, boff, poff, brev;
+  DevBuf atom_off, atom_cfg, pos, box, cnt, nbr, shift, boff, poff, brev;
+  DevBuf cfg_tot, grid_bar;   // per-configuration totals and the grid barrier of the fused build
+  int build_resident = 0;     // resident CTAs of the fused build kernel on this device
   DevBuf counters;   // per-launch work counters of the persistent batched kernels
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
   DevBuf outer;   // [Ntot] int: nonzero if the atom has a bond beyond R1 (f_C != 1)
@@ -168,25 +185,39 @@ struct Ctx {
 
   // --- measurement: CUDA events around each batched-kernel launch sequence, on its stream ---
   mutable KernelTimer timer;
+
+  // --- CUDA graphs of the per-call launch sequences ---
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;   // private stream the sequences are captured on
+  GraphCache g_fitness;
 };
 
 // ---- launchers (defined in the .cu files) ----
 // neighbors.cu
-cudaError_t launch_box_prep(int C, const double *box, const float *xmax, double *boxinv, float *pre32,
-                            double R2, unsigned *status, cudaStream_t s);
-cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg, float *xmax,
-                         unsigned *status, cudaStream_t s);
-cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
-                                   const double *pos, const float4 *pos32, const double *box,
-                                   const float *pre32, double R2, int M, int *cnt, int *nbr,
-                                   char4 *shift, unsigned *status, cudaStream_t s);
-cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,
-                           const int *boff, int *brev, unsigned *status, cudaStream_t s);
-cudaError_t launch_geometry(int precision, int64_t Ntot, int64_t Btot, int M, const int *atom_cfg,
-                            const int *atom_off, const int *brev, const double *pos, const double *box,
-                            const int *cnt, const int *nbr, const char4 *shift, const int *boff,
-                            const int *poff, double R1, double R2, void *gA, void *gB, void *gcos,
-                            int max_slots, int *outer, cudaStream_t s);
+// Arguments of the fused neighbour build (one cooperative launch over all configurations).
+struct BuildLaunch {
+  int C, M;
+  int64_t Ntot, bond_cap, slot_cap;
+  double R1, R2;
+  const int *atom_off;
+  const double *pos_in, *box_in;
+  double *pos, *box;
+  int *cnt, *nbr;
+  char4 *shift;
+  int *cfg_tot, *boff, *poff, *brev;
+  float4 *gA, *gB;
+  float *gcos;
+  int *outer;
+  unsigned *barrier, *status;
+  int resident;   // CTAs of the build kernel that can be resident at once (build_batch_resident)
+};
+cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s);
+int build_batch_resident();
+// FP64 bond records and pair cosines of the current build (on the first FP64 evaluation)
+cudaError_t launch_geometry64(int64_t Ntot, int64_t Btot, int M, const int *atom_cfg, const int *atom_off,
+                              const int *brev, const double *pos, const double *box, const int *cnt,
+                              const int *nbr, const char4 *shift, const int *boff, const int *poff, double R1,
+                              double R2, void *gA, void *gB, void *gcos, int max_slots, cudaStream_t s);
 
 // batch.cu
 struct BatchOut {

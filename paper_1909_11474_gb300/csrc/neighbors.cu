@@ -3,84 +3,12 @@
 // arXiv:1909.11474, and the cutoff function f_C of Eq. 9).
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "ctx.hpp"
 
 namespace tsf {
-
-// Per configuration: the inverse box (fractional coordinates s = x H^-1, rows of H = lattice
-// vectors) and the three lattice-plane spacings, boxinv[c][0..11] = {Hinv (row-major), gap}, and the
-// FP32 constants of the neighbour search, pre32[c][0..23] = {Hinv, R2/gap + margin, H, band}:
-// a candidate whose FP32 squared distance is farther than `band` from R2^2 is decided in FP32, the
-// rest by the exact FP64 test. `band` bounds the FP32 error of the squared distance: with X the
-// largest coordinate magnitude of the configuration, |H| its largest box entry and nmax the largest
-// image index a candidate can have, each FP32 component of d = (x_j - x_i) + n.H is within
-// delta = 2^-23 (4X + 6 nmax |H|) of the exact value, so |r^2 - r32^2| < 3.5 R2 delta + 12 2^-24 R2^2;
-// the band is four times that.
-__global__ void box_prep_kernel(int C, const double *__restrict__ box, const float *__restrict__ xmax,
-                                double *__restrict__ boxinv, float *__restrict__ pre32, double R2,
-                                unsigned *status) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  const double *H = box + 9 * c;
-  double a0 = H[0], a1 = H[1], a2 = H[2], b0 = H[3], b1 = H[4], b2 = H[5], c0 = H[6], c1 = H[7],
-         c2 = H[8];
-  // cofactors
-  double bxc0 = b1 * c2 - b2 * c1, bxc1 = b2 * c0 - b0 * c2, bxc2 = b0 * c1 - b1 * c0;
-  double cxa0 = c1 * a2 - c2 * a1, cxa1 = c2 * a0 - c0 * a2, cxa2 = c0 * a1 - c1 * a0;
-  double axb0 = a1 * b2 - a2 * b1, axb1 = a2 * b0 - a0 * b2, axb2 = a0 * b1 - a1 * b0;
-  double det = a0 * bxc0 + a1 * bxc1 + a2 * bxc2;
-  double *o = boxinv + 12 * c;
-  float *f = pre32 + 24 * c;
-  bool ok = isfinite(det) && det != 0.0;
-  for (int k = 0; k < 9; ++k) ok = ok && isfinite(H[k]);
-  if (!ok) {
-    set_status(status, TERSOFF_STATUS_NONFINITE);
-    for (int k = 0; k < 12; ++k) o[k] = 0.0;
-    for (int k = 0; k < 24; ++k) f[k] = 0.f;
-    return;
-  }
-  double id = 1.0 / det;
-  // H^-1 columns are (b x c, c x a, a x b) / det, i.e. Hinv[mu][k] = cross_k[mu] / det
-  o[0] = bxc0 * id; o[1] = cxa0 * id; o[2] = axb0 * id;
-  o[3] = bxc1 * id; o[4] = cxa1 * id; o[5] = axb1 * id;
-  o[6] = bxc2 * id; o[7] = cxa2 * id; o[8] = axb2 * id;
-  double vol = fabs(det);
-  o[9] = vol / sqrt(bxc0 * bxc0 + bxc1 * bxc1 + bxc2 * bxc2);
-  o[10] = vol / sqrt(cxa0 * cxa0 + cxa1 * cxa1 + cxa2 * cxa2);
-  o[11] = vol / sqrt(axb0 * axb0 + axb1 * axb1 + axb2 * axb2);
-  // largest coordinate magnitude (from the FP32 copies: widened by 2^-22 for their rounding)
-  const double X = (double)xmax[c] * (1.0 + ldexp(1.0, -22));
-  double Hm = 0.0;
-  for (int k = 0; k < 9; ++k) Hm = fmax(Hm, fabs(H[k]));
-  double nmax = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    const double col = fabs(o[k]) + fabs(o[3 + k]) + fabs(o[6 + k]);
-    nmax = fmax(nmax, ceil(2.0 * X * col + R2 / o[9 + k] + 1.0));
-  }
-  const double delta = ldexp(4.0 * X + 6.0 * nmax * Hm, -23);
-  const double band = 4.0 * (3.5 * R2 * delta + 12.0 * ldexp(R2 * R2, -24));
-  for (int k = 0; k < 9; ++k) f[k] = (float)o[k];
-  for (int k = 0; k < 3; ++k) f[9 + k] = (float)(R2 / o[9 + k]) + 1e-4f;
-  for (int k = 0; k < 9; ++k) f[12 + k] = (float)H[k];
-  f[21] = (float)band;
-  f[22] = (float)(R2 * R2);
-  f[23] = 0.f;
-}
-
-// FP32 copies of the positions and, per configuration, the largest coordinate magnitude (xmax must
-// be zero on entry; non-negative floats order like their bit patterns, so an integer max suffices).
-__global__ void pos32_kernel(int64_t N, const double *__restrict__ pos, const int *__restrict__ atom_cfg,
-                             float4 *__restrict__ pos32, float *__restrict__ xmax, unsigned *status) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-  if (!(isfinite(x) && isfinite(y) && isfinite(z))) set_status(status, TERSOFF_STATUS_NONFINITE);
-  const float4 v = make_float4((float)x, (float)y, (float)z, 0.f);
-  pos32[i] = v;
-  const float m = fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z)));
-  atomicMax(reinterpret_cast<int *>(xmax) + atom_cfg[i], __float_as_int(m));
-}
 
 // Candidate image range of one (i, j) pair on one axis: integers n with |s_j - s_i + n| < rng.
 __device__ __forceinline__ void image_range(float ds, float rng, int &lo, int &hi) {
@@ -108,119 +36,6 @@ __device__ __forceinline__ bool member(const Pre32 &q, float dx, float dy, float
   if (r2 < q.R2sq - q.band) return true;
   if (r2 > q.R2sq + q.band) return false;
   return exact_pair(xj[0], xj[1], xj[2], xi[0], xi[1], xi[2], H, n0, n1, n2).r2 < R2sq;
-}
-
-__global__ void __launch_bounds__(128) neighbors_batch_kernel(
-    int64_t Ntot, const int *__restrict__ atom_off, const int *__restrict__ atom_cfg,
-    const double *__restrict__ pos, const float4 *__restrict__ pos32,
-    const double *__restrict__ box, const float *__restrict__ pre32, double R2, int M,
-    int *__restrict__ cnt_out, int *__restrict__ nbr, char4 *__restrict__ shift, unsigned *status) {
-  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (i >= Ntot) return;   // whole warps only
-  const int c = atom_cfg[i];
-  const int a0 = atom_off[c], a1 = atom_off[c + 1];
-  Pre32 q;
-  {
-    const float *f = pre32 + 24 * c;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) q.Hi[k] = f[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) q.rng[k] = f[9 + k];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) q.H[k] = f[12 + k];
-    q.band = f[21];
-    q.R2sq = f[22];
-  }
-  const double *H = box + 9 * c;
-  const double R2sq = R2 * R2;
-  const double *xi = pos + 3 * i;
-  const float4 xi32 = pos32[i];
-  int count = 0;
-  for (int jb = a0; jb < a1; jb += 32) {
-    const int j = jb + lane;
-    int lo0 = 1, hi0 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0;
-    float dx = 0.f, dy = 0.f, dz = 0.f;
-    if (j < a1) {
-      const float4 xj = pos32[j];
-      dx = xj.x - xi32.x;
-      dy = xj.y - xi32.y;
-      dz = xj.z - xi32.z;
-      image_range(dx * q.Hi[0] + dy * q.Hi[3] + dz * q.Hi[6], q.rng[0], lo0, hi0);
-      image_range(dx * q.Hi[1] + dy * q.Hi[4] + dz * q.Hi[7], q.rng[1], lo1, hi1);
-      image_range(dx * q.Hi[2] + dy * q.Hi[5] + dz * q.Hi[8], q.rng[2], lo2, hi2);
-    }
-    const double *xj = pos + 3 * (j < a1 ? j : a0);
-    int mine = 0;
-    for (int n0 = lo0; n0 <= hi0; ++n0)
-      for (int n1 = lo1; n1 <= hi1; ++n1)
-        for (int n2 = lo2; n2 <= hi2; ++n2) {
-          if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
-          if (member(q, dx, dy, dz, n0, n1, n2, xj, xi, H, R2sq)) ++mine;
-        }
-    int incl = mine;   // inclusive warp scan of the per-lane counts
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, incl, off);
-      if (lane >= off) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (mine) {
-      int w = count + incl - mine;
-      for (int n0 = lo0; n0 <= hi0; ++n0)
-        for (int n1 = lo1; n1 <= hi1; ++n1)
-          for (int n2 = lo2; n2 <= hi2; ++n2) {
-            if (j == i && n0 == 0 && n1 == 0 && n2 == 0) continue;
-            if (member(q, dx, dy, dz, n0, n1, n2, xj, xi, H, R2sq)) {
-              if (w < M) {
-                nbr[i * M + w] = j;
-                shift[i * M + w] = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
-              }
-              ++w;
-            }
-          }
-    }
-    count += total;
-  }
-  if (lane == 0) {
-    cnt_out[i] = count;
-    if (count > M) set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
-  }
-  for (int e = count + lane; e < M; e += 32) {
-    nbr[i * M + e] = -1;
-    shift[i * M + e] = make_char4(0, 0, 0, 0);
-  }
-}
-
-// Reverse entry of every bond: entry (i; j, n) <-> (j; i, -n). The exact test is antisymmetric
-// (x_i - x_j = -(x_j - x_i) and t(-n) = -t(n) exactly), so the reverse entry always exists.
-// One thread per (atom, list slot).
-__global__ void reverse_kernel(int64_t Ntot, int M, const int *__restrict__ cnt,
-                               const int *__restrict__ nbr, const char4 *__restrict__ shift,
-                               const int *__restrict__ boff, int *__restrict__ brev,
-                               unsigned *status) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = t / M;
-  const int e = (int)(t % M);
-  if (i >= Ntot) return;
-  const int m = min(cnt[i], M);
-  if (e >= m) return;
-  const int j = nbr[i * M + e];
-  const char4 n = shift[i * M + e];
-  const int mj = min(cnt[j], M);
-  int found = -1;
-  for (int f = 0; f < mj; ++f) {
-    const char4 q = shift[(int64_t)j * M + f];
-    if (nbr[(int64_t)j * M + f] == (int)i && q.x == -n.x && q.y == -n.y && q.z == -n.z) {
-      found = f;
-      break;
-    }
-  }
-  if (found < 0) {
-    set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
-    found = 0;
-  }
-  brev[boff[i] + e] = boff[j] + found;
 }
 
 // f_C of Eq. 9 and its derivative.
@@ -253,15 +68,46 @@ __device__ __forceinline__ int64_t bond_owner(const int *__restrict__ boff, int6
 // configuration-local indices of the reverse bond and of the neighbour atom (4th slot: as a double,
 // or as the bit pattern of the int in the FP32 record). The bond vector d is formed in FP64 by the
 // expression of the membership test (where the cancellation happens); FP32 records round it and then
-// normalise in FP32, FP64 records (built on the first FP64 evaluation) stay in FP64. One thread per bond.
+// normalise in FP32 (built by the fused build kernel), FP64 records stay in FP64 (built on the first
+// FP64 evaluation by geometry_bond_kernel, one thread per bond).
+// The record of one bond from its exact FP64 bond vector: A = (unit vector, r), B = (2/r, f_C, f_C',
+// packed indices rl). Returns whether r > R1 (f_C may differ from 1).
+template <typename R>
+__device__ __forceinline__ bool bond_record(const ExactPair &p, double R1, double R2, int rl,
+                                            typename Vec4<R>::T &A, typename Vec4<R>::T &Bv) {
+  if constexpr (sizeof(R) == 4) {
+    const float dx = (float)p.dx, dy = (float)p.dy, dz = (float)p.dz;
+    const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+    const float r = (dx * dx + dy * dy + dz * dz) * ir;
+    float fc = 1.f, fcp = 0.f;
+    if (r >= (float)R2) {
+      fc = 0.f;
+    } else if (r > (float)R1) {
+      const float w = (r - (float)R1) / (float)(R2 - R1);
+      fc = 0.5f * (1.f + cospif(w));
+      fcp = (float)(-0.5 * M_PI / (R2 - R1)) * sinpif(w);
+    }
+    A = make_float4(dx * ir, dy * ir, dz * ir, r);
+    Bv = make_float4(ir + ir, fc, fcp, __int_as_float(rl));
+    return r > (float)R1;
+  } else {
+    const double ir = rsqrt(p.r2);
+    const double r = p.r2 * ir;
+    double fc, fcp;
+    cutoff_fc(r, R1, R2, fc, fcp);
+    A = make_dvec4(p.dx * ir, p.dy * ir, p.dz * ir, r);
+    Bv = make_dvec4(ir + ir, fc, fcp, (double)rl);
+    return r > R1;
+  }
+}
+
 template <typename R>
 __global__ void geometry_bond_kernel(int64_t Ntot, int Btot, int M, const int *__restrict__ atom_cfg,
                                      const int *__restrict__ atom_off, const int *__restrict__ brev,
                                      const double *__restrict__ pos, const double *__restrict__ box,
                                      const int *__restrict__ nbr, const char4 *__restrict__ shift,
                                      const int *__restrict__ boff, double R1, double R2,
-                                     typename Vec4<R>::T *__restrict__ gA, typename Vec4<R>::T *__restrict__ gB,
-                                     int *__restrict__ outer) {
+                                     typename Vec4<R>::T *__restrict__ gA, typename Vec4<R>::T *__restrict__ gB) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= Btot) return;
   const int64_t i = bond_owner(boff, Ntot, b);
@@ -276,29 +122,7 @@ __global__ void geometry_bond_kernel(int64_t Ntot, int Btot, int M, const int *_
   const ExactPair p = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], pos[3 * i], pos[3 * i + 1],
                                  pos[3 * i + 2], H, n.x, n.y, n.z);
   typename Vec4<R>::T A, Bv;
-  if constexpr (sizeof(R) == 4) {
-    const float dx = (float)p.dx, dy = (float)p.dy, dz = (float)p.dz;
-    const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
-    const float r = (dx * dx + dy * dy + dz * dz) * ir;
-    float fc = 1.f, fcp = 0.f;
-    if (r > (float)R1) atomicOr(outer + i, 1);   // the atom has a bond beyond R1 (f_C != 1)
-    if (r >= (float)R2) {
-      fc = 0.f;
-    } else if (r > (float)R1) {
-      const float w = (r - (float)R1) / (float)(R2 - R1);
-      fc = 0.5f * (1.f + cospif(w));
-      fcp = (float)(-0.5 * M_PI / (R2 - R1)) * sinpif(w);
-    }
-    A = make_float4(dx * ir, dy * ir, dz * ir, r);
-    Bv = make_float4(ir + ir, fc, fcp, __int_as_float(rl));
-  } else {
-    const double ir = rsqrt(p.r2);
-    const double r = p.r2 * ir;
-    double fc, fcp;
-    cutoff_fc(r, R1, R2, fc, fcp);
-    A = make_dvec4(p.dx * ir, p.dy * ir, p.dz * ir, r);
-    Bv = make_dvec4(ir + ir, fc, fcp, (double)rl);
-  }
+  bond_record<R>(p, R1, R2, rl, A, Bv);
   gA[b] = A;
   gB[b] = Bv;
 }
@@ -332,62 +156,470 @@ __global__ void geometry_pair_kernel(int64_t Ntot, int slots, const int *__restr
 }
 
 // ---------------------------------------------------------------------------------------------
+// Fused neighbour build of a batch of configurations: one launch, cooperative (every CTA resident),
+// CTAs over contiguous chunks of configurations, two phases separated by a grid barrier.
+//  phase 1, per configuration: FP64 and FP32 copies of the positions, the box constants of the FP32
+//    membership test, the neighbour lists (warp per atom, as described at `member`) and the totals
+//    (bonds, pair slots, largest neighbour count) of the configuration;
+//  phase 2, per configuration: its first bond and pair slot (sums of the totals of the configurations
+//    before it), the bond CSR of its atoms (block scans), the reverse bond of every bond, the FP32
+//    bond records and the pair cosines.
+// The bond and pair arrays are written with the capacity Ntot*M and Ntot*pair_slots(M) they were
+// allocated with; an index beyond it is reported as a neighbour overflow and not written.
+constexpr int kBuildThreads = 256;
+constexpr int kBuildWarps = kBuildThreads / 32;
+constexpr int kBuildMaxAtoms = 1024;
+constexpr unsigned kGridSpins = 1u << 22;   // bound of the grid barrier wait (with 128 ns sleeps)
+
+struct BuildParams {
+  int C, M;
+  int64_t Ntot, bond_cap, slot_cap;
+  double R1, R2;
+  const int *atom_off;
+  const double *pos_in, *box_in;   // caller's positions [Ntot][3] and boxes [C][3][3]
+  double *pos, *box;               // the context's copies
+  int *cnt, *nbr;
+  char4 *shift;
+  int *cfg_tot;                    // [C][4]: bonds, pair slots, largest neighbour count, 0
+  int *boff, *poff, *brev;
+  float4 *gA, *gB;
+  float *gcos;
+  int *outer;
+  unsigned *barrier;               // zero at launch
+  unsigned *status;
+};
+
+// Sum / max / exclusive scan over the threads of a block (kBuildThreads), in a fixed order.
+__device__ __forceinline__ long long block_sum_ll(long long v, long long *red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  long long t = 0;
+  for (int w = 0; w < kBuildWarps; ++w) t += red[w];
+  return t;
+}
+__device__ __forceinline__ float block_max_f(float v, float *red) {
+  for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float t = 0.f;
+  for (int w = 0; w < kBuildWarps; ++w) t = fmaxf(t, red[w]);
+  return t;
+}
+__device__ __forceinline__ int block_excl_scan(int v, int *red, int &total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+  for (int off = 1; off < 32; off <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += u;
+  }
+  __syncthreads();
+  if (lane == 31) red[warp] = incl;
+  __syncthreads();
+  int before = 0;
+  total = 0;
+  for (int w = 0; w < kBuildWarps; ++w) {
+    if (w < warp) before += red[w];
+    total += red[w];
+  }
+  return before + incl - v;
+}
+
+// Grid-wide barrier of a cooperative launch; the wait is bounded, and a timeout is reported in the
+// status word (the second phase then runs on whatever the first phase has written, within bounds).
+__device__ __forceinline__ void grid_barrier(unsigned *ctr, unsigned *status) {
+  __threadfence();   // this thread's global writes, before the arrival below
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(ctr, 1u);
+    unsigned k = 0;
+    while (*reinterpret_cast<volatile unsigned *>(ctr) < gridDim.x) {
+      if (++k >= kGridSpins) {
+        set_status(status, TERSOFF_STATUS_TIMEOUT);
+        break;
+      }
+      __nanosleep(128);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// Box constants of one configuration for the FP32 membership test (computed by one thread):
+// Hinv, the image search range R2/gap (+ margin), H and the decision band. `band` bounds the FP32
+// error of the squared distance: with X the largest coordinate magnitude of the configuration, |H|
+// its largest box entry and nmax the largest image index a candidate can have, each FP32 component
+// of d = (x_j - x_i) + n.H is within delta = 2^-23 (4X + 6 nmax |H|) of the exact value, so
+// |r^2 - r32^2| < 3.5 R2 delta + 12 2^-24 R2^2; the band is four times that. Returns false for a
+// singular or non-finite box.
+__device__ bool box_constants(const double *H, float xm, double R2, Pre32 &q, int &nmax_out) {
+  const double a0 = H[0], a1 = H[1], a2 = H[2], b0 = H[3], b1 = H[4], b2 = H[5], c0 = H[6], c1 = H[7],
+               c2 = H[8];
+  const double bxc0 = b1 * c2 - b2 * c1, bxc1 = b2 * c0 - b0 * c2, bxc2 = b0 * c1 - b1 * c0;
+  const double cxa0 = c1 * a2 - c2 * a1, cxa1 = c2 * a0 - c0 * a2, cxa2 = c0 * a1 - c1 * a0;
+  const double axb0 = a1 * b2 - a2 * b1, axb1 = a2 * b0 - a0 * b2, axb2 = a0 * b1 - a1 * b0;
+  const double det = a0 * bxc0 + a1 * bxc1 + a2 * bxc2;
+  bool ok = isfinite(det) && det != 0.0;
+  for (int k = 0; k < 9; ++k) ok = ok && isfinite(H[k]);
+  if (!ok) return false;
+  const double id = 1.0 / det;
+  // H^-1 columns are (b x c, c x a, a x b) / det, i.e. Hinv[mu][k] = cross_k[mu] / det
+  const double o[9] = {bxc0 * id, cxa0 * id, axb0 * id, bxc1 * id, cxa1 * id, axb1 * id,
+                       bxc2 * id, cxa2 * id, axb2 * id};
+  const double vol = fabs(det);
+  const double gap[3] = {vol / sqrt(bxc0 * bxc0 + bxc1 * bxc1 + bxc2 * bxc2),
+                         vol / sqrt(cxa0 * cxa0 + cxa1 * cxa1 + cxa2 * cxa2),
+                         vol / sqrt(axb0 * axb0 + axb1 * axb1 + axb2 * axb2)};
+  // largest coordinate magnitude (from the FP32 copies: widened by 2^-22 for their rounding)
+  const double X = (double)xm * (1.0 + ldexp(1.0, -22));
+  double Hm = 0.0;
+  for (int k = 0; k < 9; ++k) Hm = fmax(Hm, fabs(H[k]));
+  double nmax = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double col = fabs(o[k]) + fabs(o[3 + k]) + fabs(o[6 + k]);
+    nmax = fmax(nmax, ceil(2.0 * X * col + R2 / gap[k] + 1.0));
+  }
+  const double delta = ldexp(4.0 * X + 6.0 * nmax * Hm, -23);
+  const double band = 4.0 * (3.5 * R2 * delta + 12.0 * ldexp(R2 * R2, -24));
+  for (int k = 0; k < 9; ++k) q.Hi[k] = (float)o[k];
+  for (int k = 0; k < 3; ++k) q.rng[k] = (float)(R2 / gap[k]) + 1e-4f;
+  for (int k = 0; k < 9; ++k) q.H[k] = (float)H[k];
+  q.band = (float)band;
+  q.R2sq = (float)(R2 * R2);
+  nmax_out = (int)fmin(nmax, 127.0);
+  return isfinite(band) && nmax <= 127.0;
+}
+
+__global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildParams a) {
+  __shared__ float4 s_p32[kBuildMaxAtoms];
+  __shared__ int s_m[kBuildMaxAtoms];
+  __shared__ int s_boff[kBuildMaxAtoms + 1];
+  __shared__ int s_poff[kBuildMaxAtoms + 1];
+  __shared__ int s_outer[kBuildMaxAtoms];
+  __shared__ Pre32 s_q;
+  __shared__ double s_H[9];
+  __shared__ int s_ok, s_nmax;
+  __shared__ long long s_red[kBuildWarps];
+  __shared__ int s_ired[kBuildWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int M = a.M;
+  // contiguous chunk of configurations of this CTA
+  const int per = (a.C + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int c_begin = min(a.C, (int)blockIdx.x * per), c_end = min(a.C, c_begin + per);
+
+  // ---- phase 1: positions, box constants, neighbour lists, totals
+  for (int c = c_begin; c < c_end; ++c) {
+    const int a0 = a.atom_off[c], nat = a.atom_off[c + 1] - a0;
+    float xm = 0.f;
+    int finite = 1;
+    for (int t = tid; t < nat; t += kBuildThreads) {
+      const double *x = a.pos_in + 3 * (int64_t)(a0 + t);
+      const double x0 = x[0], x1 = x[1], x2 = x[2];
+      double *y = a.pos + 3 * (int64_t)(a0 + t);
+      y[0] = x0;
+      y[1] = x1;
+      y[2] = x2;
+      finite &= (isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 1 : 0;
+      const float4 v = make_float4((float)x0, (float)x1, (float)x2, 0.f);
+      s_p32[t] = v;
+      xm = fmaxf(xm, fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
+    }
+    xm = block_max_f(xm, reinterpret_cast<float *>(s_red));
+    finite = __syncthreads_and(finite);
+    if (tid < 9) {
+      s_H[tid] = a.box_in[9 * c + tid];
+      a.box[9 * c + tid] = s_H[tid];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      Pre32 q;
+      int nmax = 0;
+      const bool ok = finite && box_constants(s_H, xm, a.R2, q, nmax);
+      if (!ok) set_status(a.status, TERSOFF_STATUS_NONFINITE);
+      s_q = q;
+      s_ok = ok ? 1 : 0;
+      s_nmax = nmax;
+    }
+    __syncthreads();
+    const Pre32 q = s_q;
+    const bool ok = s_ok != 0;
+    const int nmax = s_nmax;
+    const double R2sq = a.R2 * a.R2;
+    // one warp per atom i, lanes over j (two passes per block of 32 j, ordered by a warp scan)
+    for (int li = warp; li < nat; li += kBuildWarps) {
+      const int64_t i = a0 + li;
+      const double *xi = a.pos_in + 3 * i;
+      const float4 xi32 = s_p32[li];
+      int count = 0;
+      for (int jb = 0; ok && jb < nat; jb += 32) {
+        const int jl = jb + lane;
+        int lo0 = 1, hi0 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0;
+        float dx = 0.f, dy = 0.f, dz = 0.f;
+        if (jl < nat) {
+          const float4 xj = s_p32[jl];
+          dx = xj.x - xi32.x;
+          dy = xj.y - xi32.y;
+          dz = xj.z - xi32.z;
+          image_range(dx * q.Hi[0] + dy * q.Hi[3] + dz * q.Hi[6], q.rng[0], lo0, hi0);
+          image_range(dx * q.Hi[1] + dy * q.Hi[4] + dz * q.Hi[7], q.rng[1], lo1, hi1);
+          image_range(dx * q.Hi[2] + dy * q.Hi[5] + dz * q.Hi[8], q.rng[2], lo2, hi2);
+          // every valid image index lies within +-nmax; the clamp only bounds the loops
+          lo0 = max(lo0, -nmax); hi0 = min(hi0, nmax);
+          lo1 = max(lo1, -nmax); hi1 = min(hi1, nmax);
+          lo2 = max(lo2, -nmax); hi2 = min(hi2, nmax);
+        }
+        const int j = a0 + (jl < nat ? jl : 0);
+        const double *xj = a.pos_in + 3 * (int64_t)j;
+        int mine = 0;
+        for (int n0 = lo0; n0 <= hi0; ++n0)
+          for (int n1 = lo1; n1 <= hi1; ++n1)
+            for (int n2 = lo2; n2 <= hi2; ++n2) {
+              if (jl == li && n0 == 0 && n1 == 0 && n2 == 0) continue;
+              if (member(q, dx, dy, dz, n0, n1, n2, xj, xi, s_H, R2sq)) ++mine;
+            }
+        int incl = mine;   // inclusive warp scan of the per-lane counts
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const int v = __shfl_up_sync(0xffffffffu, incl, off);
+          if (lane >= off) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (mine) {
+          int w = count + incl - mine;
+          for (int n0 = lo0; n0 <= hi0; ++n0)
+            for (int n1 = lo1; n1 <= hi1; ++n1)
+              for (int n2 = lo2; n2 <= hi2; ++n2) {
+                if (jl == li && n0 == 0 && n1 == 0 && n2 == 0) continue;
+                if (member(q, dx, dy, dz, n0, n1, n2, xj, xi, s_H, R2sq)) {
+                  if (w < M) {
+                    a.nbr[i * M + w] = j;
+                    a.shift[i * M + w] = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
+                  }
+                  ++w;
+                }
+              }
+        }
+        count += total;
+      }
+      if (lane == 0) {
+        a.cnt[i] = count;
+        if (count > M) set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
+        s_m[li] = min(count, M);
+      }
+      for (int e = count + lane; e < M; e += 32) {
+        a.nbr[i * M + e] = -1;
+        a.shift[i * M + e] = make_char4(0, 0, 0, 0);
+      }
+    }
+    __syncthreads();
+    long long nb = 0, nq = 0;
+    float mm = 0.f;
+    for (int t = tid; t < nat; t += kBuildThreads) {
+      nb += s_m[t];
+      nq += pair_slots(s_m[t]);
+      mm = fmaxf(mm, (float)s_m[t]);
+    }
+    nb = block_sum_ll(nb, s_red);
+    nq = block_sum_ll(nq, s_red);
+    mm = block_max_f(mm, reinterpret_cast<float *>(s_ired));
+    if (tid == 0) {
+      int *o = a.cfg_tot + 4 * c;
+      o[0] = (int)nb;
+      o[1] = (int)nq;
+      o[2] = (int)mm;
+      o[3] = 0;
+    }
+    __syncthreads();
+  }
+
+  grid_barrier(a.barrier, a.status);
+
+  // ---- phase 2: bond CSR, reverse bonds, FP32 bond records, pair cosines
+  long long base_b = 0, base_q = 0;
+  {
+    long long sb = 0, sq = 0;
+    for (int k = tid; k < c_begin; k += kBuildThreads) {   // written by other CTAs: read from L2
+      sb += __ldcg(a.cfg_tot + 4 * k);
+      sq += __ldcg(a.cfg_tot + 4 * k + 1);
+    }
+    base_b = block_sum_ll(sb, s_red);
+    base_q = block_sum_ll(sq, s_red);
+  }
+  for (int c = c_begin; c < c_end; ++c) {
+    const int a0 = a.atom_off[c], nat = a.atom_off[c + 1] - a0;
+    int nb = 0, nq = 0;
+    for (int cb = 0; cb < nat; cb += kBuildThreads) {
+      const int t = cb + tid;
+      const int m = t < nat ? min(a.cnt[a0 + t], M) : 0;
+      int tb, tq;
+      const int xb = block_excl_scan(m, s_ired, tb);
+      const int xq = block_excl_scan(t < nat ? pair_slots(m) : 0, s_ired, tq);
+      if (t < nat) {
+        s_m[t] = m;
+        s_boff[t] = nb + xb;
+        s_poff[t] = nq + xq;
+        s_outer[t] = 0;
+      }
+      nb += tb;
+      nq += tq;
+    }
+    if (tid == 0) {
+      s_boff[nat] = nb;
+      s_poff[nat] = nq;
+    }
+    __syncthreads();
+    const bool fits = base_b >= 0 && base_q >= 0 && base_b + nb <= a.bond_cap && base_q + nq <= a.slot_cap;
+    if (!fits && tid == 0) set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
+    for (int t = tid; t <= nat; t += kBuildThreads) {
+      if (t < nat || c == a.C - 1) {
+        a.boff[a0 + t] = (int)(base_b + s_boff[t]);
+        a.poff[a0 + t] = (int)(base_q + s_poff[t]);
+      }
+    }
+    if (fits) {
+      const double *H = s_H;
+      if (tid < 9) s_H[tid] = a.box_in[9 * c + tid];
+      __syncthreads();
+      // one thread per bond: owner atom, reverse entry (j; i, -n), record
+      for (int bl = tid; bl < nb; bl += kBuildThreads) {
+        int lo = 0, hi = nat;   // last atom t with s_boff[t] <= bl
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_boff[mid] <= bl) lo = mid;
+          else hi = mid;
+        }
+        const int il = lo, e = bl - s_boff[il];
+        const int64_t i = a0 + il;
+        const int j = a.nbr[i * M + e];
+        const char4 n = a.shift[i * M + e];
+        const int jl = j - a0;
+        const int mj = s_m[jl];
+        int found = -1;
+        for (int f = 0; f < mj; ++f) {
+          const char4 r = a.shift[(int64_t)j * M + f];
+          if (a.nbr[(int64_t)j * M + f] == (int)i && r.x == -n.x && r.y == -n.y && r.z == -n.z) {
+            found = f;
+            break;
+          }
+        }
+        if (found < 0) {   // the exact test is antisymmetric, so this means an overflowing list
+          set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
+          found = 0;
+        }
+        const int rev = s_boff[jl] + found;
+        a.brev[base_b + bl] = (int)(base_b + rev);
+        const ExactPair p = exact_pair(a.pos_in[3 * (int64_t)j], a.pos_in[3 * (int64_t)j + 1],
+                                       a.pos_in[3 * (int64_t)j + 2], a.pos_in[3 * i], a.pos_in[3 * i + 1],
+                                       a.pos_in[3 * i + 2], H, n.x, n.y, n.z);
+        float4 A, Bv;
+        if (bond_record<float>(p, a.R1, a.R2, rev | (jl << 16), A, Bv)) atomicOr(&s_outer[il], 1);
+        a.gA[base_b + bl] = A;
+        a.gB[base_b + bl] = Bv;
+      }
+      __syncthreads();
+      for (int t = tid; t < nat; t += kBuildThreads) a.outer[a0 + t] = s_outer[t];
+      // one thread per pair slot: cos theta of bonds (e, f), e < f, row-major over e; padding 0
+      for (int ql = tid; ql < nq; ql += kBuildThreads) {
+        int lo = 0, hi = nat;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_poff[mid] <= ql) lo = mid;
+          else hi = mid;
+        }
+        const int il = lo, m = s_m[il];
+        int e = 0, rem = ql - s_poff[il];
+        while (e < m && rem >= m - 1 - e) {
+          rem -= m - 1 - e;
+          ++e;
+        }
+        float cs = 0.f;
+        if (e < m - 1) {
+          const int f = e + 1 + rem;
+          const float4 ue = a.gA[base_b + s_boff[il] + e], uf = a.gA[base_b + s_boff[il] + f];
+          cs = ue.x * uf.x + ue.y * uf.y + ue.z * uf.z;
+        }
+        a.gcos[base_q + ql] = cs;
+      }
+    }
+    __syncthreads();
+    base_b += nb;
+    base_q += nq;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 static inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-cudaError_t launch_box_prep(int C, const double *box, const float *xmax, double *boxinv, float *pre32,
-                            double R2, unsigned *status, cudaStream_t s) {
-  box_prep_kernel<<<nblk(C, 128), 128, 0, s>>>(C, box, xmax, boxinv, pre32, R2, status);
-  return launched(1);
+cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s) {
+  if (L.C < 1) return cudaSuccess;
+  BuildParams a = {};
+  a.C = L.C;
+  a.M = L.M;
+  a.Ntot = L.Ntot;
+  a.bond_cap = L.bond_cap;
+  a.slot_cap = L.slot_cap;
+  a.R1 = L.R1;
+  a.R2 = L.R2;
+  a.atom_off = L.atom_off;
+  a.pos_in = L.pos_in;
+  a.box_in = L.box_in;
+  a.pos = L.pos;
+  a.box = L.box;
+  a.cnt = L.cnt;
+  a.nbr = L.nbr;
+  a.shift = L.shift;
+  a.cfg_tot = L.cfg_tot;
+  a.boff = L.boff;
+  a.poff = L.poff;
+  a.brev = L.brev;
+  a.gA = L.gA;
+  a.gB = L.gB;
+  a.gcos = L.gcos;
+  a.outer = L.outer;
+  a.barrier = L.barrier;
+  a.status = L.status;
+  cudaError_t e = cudaMemsetAsync(L.barrier, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  // every CTA must be resident for the grid barrier: grid = min(C, resident CTAs)
+  const int grid = std::max(1, std::min(L.C, L.resident));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBuildThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, build_batch_kernel, a);
+  if (e == cudaSuccess) count_launches(1);
+  return e;
 }
-cudaError_t launch_pos32(int64_t N, const double *pos, float4 *pos32, const int *atom_cfg, float *xmax,
-                         unsigned *status, cudaStream_t s) {
-  if (N == 0) return cudaSuccess;
-  pos32_kernel<<<nblk(N, 256), 256, 0, s>>>(N, pos, atom_cfg, pos32, xmax, status);
-  return launched(1);
+
+int build_batch_resident() {
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_batch_kernel, kBuildThreads, 0) != cudaSuccess)
+    return 0;
+  return per_sm * nsm;
 }
-cudaError_t launch_neighbors_batch(int64_t Ntot, const int *atom_off, const int *atom_cfg,
-                                   const double *pos, const float4 *pos32, const double *box,
-                                   const float *pre32, double R2, int M, int *cnt, int *nbr,
-                                   char4 *shift, unsigned *status, cudaStream_t s) {
+
+cudaError_t launch_geometry64(int64_t Ntot, int64_t Btot, int M, const int *atom_cfg, const int *atom_off,
+                              const int *brev, const double *pos, const double *box, const int *cnt,
+                              const int *nbr, const char4 *shift, const int *boff, const int *poff, double R1,
+                              double R2, void *gA, void *gB, void *gcos, int max_slots, cudaStream_t s) {
   if (Ntot == 0) return cudaSuccess;
-  neighbors_batch_kernel<<<nblk(Ntot * 32, 128), 128, 0, s>>>(Ntot, atom_off, atom_cfg, pos, pos32, box,
-                                                              pre32, R2, M, cnt, nbr, shift, status);
-  return launched(1);
-}
-cudaError_t launch_reverse(int64_t Ntot, int M, const int *cnt, const int *nbr, const char4 *shift,
-                           const int *boff, int *brev, unsigned *status, cudaStream_t s) {
-  if (Ntot == 0) return cudaSuccess;
-  reverse_kernel<<<nblk(Ntot * M, 256), 256, 0, s>>>(Ntot, M, cnt, nbr, shift, boff, brev, status);
-  return launched(1);
-}
-cudaError_t launch_geometry(int precision, int64_t Ntot, int64_t Btot, int M, const int *atom_cfg,
-                            const int *atom_off, const int *brev, const double *pos, const double *box,
-                            const int *cnt, const int *nbr, const char4 *shift, const int *boff,
-                            const int *poff, double R1, double R2, void *gA, void *gB, void *gcos,
-                            int max_slots, int *outer, cudaStream_t s) {
-  if (Ntot == 0) return cudaSuccess;
-  if (outer) {
-    cudaError_t e = cudaMemsetAsync(outer, 0, Ntot * sizeof(int), s);
-    if (e != cudaSuccess) return e;
-  }
-  if (Btot > 0) {
-    if (precision == 64)
-      geometry_bond_kernel<double><<<nblk(Btot, 256), 256, 0, s>>>(
-          Ntot, (int)Btot, M, atom_cfg, atom_off, brev, pos, box, nbr, shift, boff, R1, R2,
-          static_cast<dvec4 *>(gA), static_cast<dvec4 *>(gB), nullptr);
-    else
-      geometry_bond_kernel<float><<<nblk(Btot, 256), 256, 0, s>>>(
-          Ntot, (int)Btot, M, atom_cfg, atom_off, brev, pos, box, nbr, shift, boff, R1, R2,
-          static_cast<float4 *>(gA), static_cast<float4 *>(gB), outer);
-  }
-  if (max_slots > 0) {
-    if (precision == 64)
-      geometry_pair_kernel<double><<<nblk(Ntot * max_slots, 256), 256, 0, s>>>(
-          Ntot, max_slots, cnt, M, boff, poff, static_cast<const dvec4 *>(gA), static_cast<double *>(gcos));
-    else
-      geometry_pair_kernel<float><<<nblk(Ntot * max_slots, 256), 256, 0, s>>>(
-          Ntot, max_slots, cnt, M, boff, poff, static_cast<const float4 *>(gA), static_cast<float *>(gcos));
-  }
+  if (Btot > 0)
+    geometry_bond_kernel<double><<<nblk(Btot, 256), 256, 0, s>>>(
+        Ntot, (int)Btot, M, atom_cfg, atom_off, brev, pos, box, nbr, shift, boff, R1, R2,
+        static_cast<dvec4 *>(gA), static_cast<dvec4 *>(gB));
+  if (max_slots > 0)
+    geometry_pair_kernel<double><<<nblk(Ntot * max_slots, 256), 256, 0, s>>>(
+        Ntot, max_slots, cnt, M, boff, poff, static_cast<const dvec4 *>(gA), static_cast<double *>(gcos));
   return launched((Btot > 0) + (max_slots > 0));
 }
 
