@@ -26,7 +26,7 @@ EXPORTED = (
     "tersoff_build_neighbors", "tersoff_export_neighbors", "tersoff_build_info", "tersoff_eval",
     "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
     "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
-    "tersoff_profile", "tersoff_profile_read",
+    "tersoff_profile", "tersoff_profile_read", "tersoff_set_graphs",
 )
 
 _vp = ctypes.c_void_p
@@ -75,6 +75,7 @@ def load():
                                                   _vp, _vp, _vp, _vp]),
         "tersoff_kernel_launches": (ctypes.c_int64, []),
         "tersoff_profile": (ctypes.c_int, [_vp, _i32]),
+        "tersoff_set_graphs": (ctypes.c_int, [_vp, _i32]),
         "tersoff_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_f64)]),
     }
     for name, (res, args) in sig.items():
@@ -153,6 +154,10 @@ class Context:
     def kernel_launches(self) -> int:
         """Kernels launched by the library in this process so far (all contexts)."""
         return int(self.lib.tersoff_kernel_launches())
+
+    def set_graphs(self, enable: bool = True):
+        """Replay the fitness call's launch sequence from a cached CUDA graph (default) or launch it directly."""
+        self._check(self.lib.tersoff_set_graphs(self.h, 1 if enable else 0))
 
     def profile(self, enable: bool = True):
         """Start or stop CUDA-event timing of the batched E/F/W kernel (clears earlier records)."""

@@ -19,6 +19,11 @@ namespace {
 std::atomic<long long> g_launches{0};
 }
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+namespace {
+std::atomic<uint64_t> g_buf_gen{0}, g_plan_gen{0};
+}
+uint64_t buffer_generation() { return g_buf_gen.load(); }
+void bump_buffer_generation() { g_buf_gen.fetch_add(1); }
 }  // namespace tsf
 
 namespace {
@@ -141,6 +146,59 @@ int build_plan(tersoff_ctx *ctx, int precision) {
   TSF_CUDA(plan.items.ensure(std::max<size_t>(1, recs.size()) * sizeof(tsf::CtaRec)));
   TSF_CUDA(cudaMemcpy(plan.items.p, recs.data(), recs.size() * sizeof(tsf::CtaRec), cudaMemcpyHostToDevice));
   plan.precision = precision;
+  plan.gen = ++tsf::g_plan_gen;
+  return TERSOFF_OK;
+}
+
+uint64_t bits(double x) {
+  uint64_t u;
+  std::memcpy(&u, &x, sizeof(u));
+  return u;
+}
+
+// Run a per-call launch sequence through a CUDA graph: captured on the context's private stream the
+// first time (or whenever the key changed), then replayed on `s` with one graph launch. Direct
+// launches while kernel timing is on, while graphs are off, or when `s` is itself being captured.
+template <typename Issue>
+int run_graphed(tersoff_ctx *ctx, tsf::GraphCache &g, std::vector<uint64_t> key, cudaStream_t s, Issue &&issue) {
+  Ctx &c = ctx->c;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TSF_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (!c.graphs || c.timer.on || cs != cudaStreamCaptureStatusNone) {
+    TSF_CUDA(issue(s));
+    return TERSOFF_OK;
+  }
+  key.push_back(tsf::buffer_generation());
+  key.push_back((uint64_t)c.device);
+  if (!g.exec || g.key != key) {
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    if (!c.cap_stream) TSF_CUDA(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+    const int64_t n0 = tersoff_kernel_launches();
+    TSF_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+    const cudaError_t ei = issue(c.cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c.cap_stream, &graph);
+    const int kernels = (int)(tersoff_kernel_launches() - n0);
+    tsf::count_launches(-kernels);   // captured, not executed
+    if (ei != cudaSuccess || ec != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(ctx, TERSOFF_E_CUDA, "CUDA error while capturing: %s",
+                  cudaGetErrorString(ei != cudaSuccess ? ei : ec));
+    }
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g.exec = nullptr;
+      return fail(ctx, TERSOFF_E_CUDA, "CUDA error: %s", cudaGetErrorString(e));
+    }
+    g.key = std::move(key);
+    g.kernels = kernels;
+  }
+  TSF_CUDA(cudaGraphLaunch(g.exec, s));
+  tsf::count_launches(g.kernels);
   return TERSOFF_OK;
 }
 
@@ -151,10 +209,14 @@ namespace tsf {
 int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s) {
   Ctx &c = ctx->c;
   if (c.geom64) return TERSOFF_OK;
-  TSF_CUDA(launch_geometry(64, c.Ntot, c.Btot, c.M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
-                           c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
-                           c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), c.R1, c.R2, c.gA64.p,
-                           c.gB64.p, c.gcos64.p, pair_slots(std::min(c.max_m, c.M)), nullptr, s));
+  const size_t B = std::max<int64_t>(1, c.Btot), Q = std::max<int64_t>(1, c.Qtot);
+  TSF_CUDA(c.gA64.ensure(B * sizeof(tsf::dvec4)));
+  TSF_CUDA(c.gB64.ensure(B * sizeof(tsf::dvec4)));
+  TSF_CUDA(c.gcos64.ensure(Q * sizeof(double)));
+  TSF_CUDA(launch_geometry64(c.Ntot, c.Btot, c.M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
+                             c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
+                             c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), c.R1, c.R2, c.gA64.p,
+                             c.gB64.p, c.gcos64.p, pair_slots(std::min(c.max_m, c.M)), s));
   c.geom64 = true;
   return TERSOFF_OK;
 }
@@ -184,7 +246,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   Ctx &c = ctx->c;
   cudaSetDevice(c.device);
   cudaDeviceSynchronize();
-  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.pos32, &c.box, &c.boxinv, &c.pre32, &c.xmax, &c.counters,
+  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.box, &c.cfg_tot, &c.grid_bar, &c.counters,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
                          &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.outer, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart, &c.tew,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
@@ -194,10 +256,18 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   c.hp_stage.release();
   if (c.stage_event) cudaEventDestroy(c.stage_event);
   for (cudaEvent_t ev : c.timer.ev) cudaEventDestroy(ev);
+  if (c.g_fitness.exec) cudaGraphExecDestroy(c.g_fitness.exec);
+  if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   delete ctx;
 }
 
 int64_t tersoff_kernel_launches(void) { return (int64_t)tsf::g_launches.load(); }
+
+int tersoff_set_graphs(tersoff_ctx *ctx, int32_t enable) {
+  if (!ctx) return TERSOFF_E_ARG;
+  ctx->c.graphs = enable != 0;
+  return TERSOFF_OK;
+}
 
 int tersoff_profile(tersoff_ctx *ctx, int32_t enable) {
   if (!ctx) return TERSOFF_E_ARG;
@@ -292,40 +362,70 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
     TSF_CUDA(cudaMemcpyAsync(c.atom_off.p, h_off, (C + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
     TSF_CUDA(cudaMemcpyAsync(c.atom_cfg.p, h_cfg, N * sizeof(int), cudaMemcpyHostToDevice, s));
   }
+  // bond and pair-slot arrays are written by the device before the host knows the counts: they get
+  // the capacity of full lists (M bonds and pair_slots(M) slots per atom)
+  const int64_t bond_cap = std::max<int64_t>(1, N * M), slot_cap = std::max<int64_t>(1, N * tsf::pair_slots(M));
   TSF_CUDA(c.pos.ensure(N * 3 * sizeof(double)));
-  TSF_CUDA(c.pos32.ensure(N * sizeof(float4)));
   TSF_CUDA(c.box.ensure((size_t)C * 9 * sizeof(double)));
-  TSF_CUDA(c.boxinv.ensure((size_t)C * 12 * sizeof(double)));
-  TSF_CUDA(c.pre32.ensure((size_t)C * 24 * sizeof(float)));
-  TSF_CUDA(c.xmax.ensure((size_t)C * sizeof(float)));
   TSF_CUDA(c.cnt.ensure(N * sizeof(int)));
   TSF_CUDA(c.nbr.ensure(N * M * sizeof(int)));
   TSF_CUDA(c.shift.ensure(N * M * sizeof(char4)));
   TSF_CUDA(c.boff.ensure((N + 1) * sizeof(int)));
   TSF_CUDA(c.poff.ensure((N + 1) * sizeof(int)));
-  TSF_CUDA(cudaMemcpyAsync(c.pos.p, cfg->pos, N * 3 * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  TSF_CUDA(cudaMemcpyAsync(c.box.p, cfg->box, (size_t)C * 9 * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  TSF_CUDA(c.cfg_tot.ensure((size_t)C * 4 * sizeof(int)));
+  TSF_CUDA(c.grid_bar.ensure(sizeof(unsigned)));
+  TSF_CUDA(c.brev.ensure(bond_cap * sizeof(int)));
+  TSF_CUDA(c.outer.ensure(std::max<int64_t>(1, N) * sizeof(int)));
+  TSF_CUDA(c.gA32.ensure(bond_cap * sizeof(float4)));
+  TSF_CUDA(c.gB32.ensure(bond_cap * sizeof(float4)));
+  TSF_CUDA(c.gcos32.ensure(slot_cap * sizeof(float)));
+  if (c.build_resident <= 0) c.build_resident = tsf::build_batch_resident();
+  if (c.build_resident <= 0) return fail(ctx, TERSOFF_E_CUDA, "occupancy query of the build kernel failed%s");
   TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
   unsigned *st = c.status.as<unsigned>();
-  TSF_CUDA(cudaMemsetAsync(c.xmax.p, 0, (size_t)C * sizeof(float), s));
-  TSF_CUDA(tsf::launch_pos32(N, c.pos.as<double>(), c.pos32.as<float4>(), c.atom_cfg.as<int>(), c.xmax.as<float>(),
-                             st, s));
-  TSF_CUDA(tsf::launch_box_prep(C, c.box.as<double>(), c.xmax.as<float>(), c.boxinv.as<double>(),
-                                c.pre32.as<float>(), R2, st, s));
-  TSF_CUDA(tsf::launch_neighbors_batch(N, c.atom_off.as<int>(), c.atom_cfg.as<int>(), c.pos.as<double>(),
-                                       c.pos32.as<float4>(), c.box.as<double>(), c.pre32.as<float>(),
-                                       R2, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), st, s));
-  // one synchronisation: neighbour counts and status back to pinned host memory
+  tsf::BuildLaunch L = {};
+  L.C = C;
+  L.M = M;
+  L.Ntot = N;
+  L.bond_cap = bond_cap;
+  L.slot_cap = slot_cap;
+  L.R1 = R1;
+  L.R2 = R2;
+  L.atom_off = c.atom_off.as<int>();
+  L.pos_in = cfg->pos;
+  L.box_in = cfg->box;
+  L.pos = c.pos.as<double>();
+  L.box = c.box.as<double>();
+  L.cnt = c.cnt.as<int>();
+  L.nbr = c.nbr.as<int>();
+  L.shift = c.shift.as<char4>();
+  L.cfg_tot = c.cfg_tot.as<int>();
+  L.boff = c.boff.as<int>();
+  L.poff = c.poff.as<int>();
+  L.brev = c.brev.as<int>();
+  L.gA = c.gA32.as<float4>();
+  L.gB = c.gB32.as<float4>();
+  L.gcos = c.gcos32.as<float>();
+  L.outer = c.outer.as<int>();
+  L.barrier = c.grid_bar.as<unsigned>();
+  L.status = st;
+  L.resident = c.build_resident;
+  TSF_CUDA(tsf::launch_build_batch(L, s));
+  // one synchronisation: neighbour counts and status back to pinned host memory (the device already
+  // holds the complete build; the host needs the counts for the work schedule)
   int *h_cnt = hp;
   unsigned *h_st = reinterpret_cast<unsigned *>(hp + N);
   TSF_CUDA(cudaMemcpyAsync(h_cnt, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, s));
   TSF_CUDA(cudaMemcpyAsync(h_st, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  TSF_CUDA(cudaEventRecord(c.stage_event, s));
   TSF_CUDA(cudaStreamSynchronize(s));
   const unsigned hst = *h_st;
   if (hst & TERSOFF_STATUS_NONFINITE) return fail(ctx, TERSOFF_E_NONFINITE, "non-finite positions or box%s");
   if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "an atom has more than max_nbr neighbours%s");
+  if (hst & TERSOFF_STATUS_TIMEOUT) return fail(ctx, TERSOFF_E_TIMEOUT, "the grid barrier of the neighbour build timed out%s");
   const bool same_counts = same_layout && (int64_t)c.h_cnt.size() == N && std::equal(c.h_cnt.begin(), c.h_cnt.end(), h_cnt);
   if (!same_counts) {
+    // host copy of the CSR the device built (same prefix sums over the configurations in order)
     c.h_cnt.assign(h_cnt, h_cnt + N);
     c.plan32 = tsf::BatchPlan();
     c.plan64 = tsf::BatchPlan();
@@ -344,29 +444,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
     c.max_m = maxm;
     c.Btot = c.h_boff[N];
     c.Qtot = c.h_poff[N];
-    TSF_CUDA(c.hp_stage.ensure((size_t)(2 * N + 2) * sizeof(int)));
-    int *h_off2 = c.hp_stage.as<int>();
-    std::copy(c.h_boff.begin(), c.h_boff.end(), h_off2);
-    std::copy(c.h_poff.begin(), c.h_poff.end(), h_off2 + (N + 1));
-    TSF_CUDA(cudaMemcpyAsync(c.boff.p, h_off2, (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
-    TSF_CUDA(cudaMemcpyAsync(c.poff.p, h_off2 + (N + 1), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
   }
-  TSF_CUDA(cudaEventRecord(c.stage_event, s));
-  const size_t B = std::max<int64_t>(1, c.Btot), Q = std::max<int64_t>(1, c.Qtot);
-  TSF_CUDA(c.brev.ensure(B * sizeof(int)));
-  TSF_CUDA(c.outer.ensure(std::max<int64_t>(1, N) * sizeof(int)));
-  TSF_CUDA(c.gA32.ensure(B * sizeof(float4)));
-  TSF_CUDA(c.gB32.ensure(B * sizeof(float4)));
-  TSF_CUDA(c.gcos32.ensure(Q * sizeof(float)));
-  TSF_CUDA(c.gA64.ensure(B * sizeof(tsf::dvec4)));
-  TSF_CUDA(c.gB64.ensure(B * sizeof(tsf::dvec4)));
-  TSF_CUDA(c.gcos64.ensure(Q * sizeof(double)));
-  TSF_CUDA(tsf::launch_reverse(N, M, c.cnt.as<int>(), c.nbr.as<int>(), c.shift.as<char4>(), c.boff.as<int>(),
-                               c.brev.as<int>(), st, s));
-  TSF_CUDA(tsf::launch_geometry(32, N, c.Btot, M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
-                                c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
-                                c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), R1, R2, c.gA32.p,
-                                c.gB32.p, c.gcos32.p, tsf::pair_slots(std::min(c.max_m, M)), c.outer.as<int>(), s));
   c.geom64 = false;
   if (c.max_m <= 8) {
     int rc = build_plan(ctx, 32);
@@ -461,11 +539,20 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   o.tmask = tg->mask;
   o.part = c.part.p;
   o.dpart = c.dpart.p;
-  cudaStream_t s = S(stream);
-  TSF_CUDA(tsf::launch_batch(c, precision == 64 ? c.plan64 : c.plan32, params, P, tsf::kModeFitness, o, s));
-  TSF_CUDA(tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, tg->E, tg->W, tg->mask, w[0], w[1],
-                                        w[2], Z, Zq, Sq, s));
-  return TERSOFF_OK;
+  const tsf::BatchPlan &plan = precision == 64 ? c.plan64 : c.plan32;
+  const double w0 = w[0], w1 = w[1], w2 = w[2];
+  const tersoff_targets t = *tg;
+  std::vector<uint64_t> key = {(uint64_t)precision, (uint64_t)P, (uint64_t)(uintptr_t)params,
+                               (uint64_t)(uintptr_t)t.E, (uint64_t)(uintptr_t)t.W, (uint64_t)(uintptr_t)t.F,
+                               (uint64_t)(uintptr_t)t.mask, bits(w0), bits(w1), bits(w2), (uint64_t)(uintptr_t)Z,
+                               (uint64_t)(uintptr_t)Zq, (uint64_t)(uintptr_t)Sq, plan.gen, (uint64_t)c.C,
+                               (uint64_t)c.Ntot};
+  return run_graphed(ctx, c.g_fitness, std::move(key), S(stream), [&](cudaStream_t s) {
+    cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
+    if (e == cudaSuccess)
+      e = tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, t.E, t.W, t.mask, w0, w1, w2, Z, Zq, Sq, s);
+    return e;
+  });
 }
 
 int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,

@@ -211,3 +211,38 @@ def test_kernel_timer_and_launch_count(ctx):
     ctx.fitness(params, tg)
     assert ctx.profile_read() == (0, 0.0)
     assert ctx.get_status() == 0
+
+
+def test_fitness_graph_replay_matches_direct_launches(ctx):
+    """The fitness call replayed from its captured CUDA graph gives the results of direct launches,
+    and a change of arguments (targets, weights, P) or of the neighbour build re-captures."""
+    w = I.workload_ga_batch(P=45, C=7)
+    cs = w["configs"]
+    _build(ctx, cs)
+    rng = np.random.default_rng(11)
+    t1 = {"E": np.full(cs.C, -4.6), "W": rng.normal(0, 0.01, (cs.C, 6)), "F": rng.normal(0, 0.3, (cs.Ntot, 3)),
+          "mask": np.array([7, 1, 2, 4, 7, 3, 6], np.uint8)}
+    t2 = dict(t1, E=np.full(cs.C, -4.5))
+    params = torch.tensor(w["params"], device="cuda")
+    tg1, tg2 = targets_to_device(t1), targets_to_device(t2)
+
+    def run(graphs, tg, wts, P=None):
+        ctx.set_graphs(graphs)
+        Z, Zq, S = ctx.fitness(params[:P], tg, w=wts)
+        return torch.cat([Z[:, None], Zq, S], 1).cpu().numpy()
+
+    for tg, wts in [(tg1, (1.0, 1.0, 1.0)), (tg2, (1.0, 1.0, 1.0)), (tg2, (0.5, 2.0, 1.0)), (tg1, (1.0, 1.0, 1.0))]:
+        direct = run(False, tg, wts)
+        first = run(True, tg, wts)       # captures
+        again = run(True, tg, wts)       # replays
+        assert np.array_equal(direct, first) and np.array_equal(direct, again)
+    assert np.array_equal(run(False, tg1, (1, 1, 1), P=33), run(True, tg1, (1, 1, 1), P=33))
+    # a new neighbour build of other configurations: the replay must not reuse the old schedule
+    w2 = I.workload_ga_batch(P=45, C=4)
+    cs2 = w2["configs"]
+    _build(ctx, cs2)
+    t3 = targets_to_device({"E": np.full(cs2.C, -4.6), "W": np.zeros((cs2.C, 6)),
+                            "F": np.zeros((cs2.Ntot, 3)), "mask": np.full(cs2.C, 7, np.uint8)})
+    assert np.array_equal(run(False, t3, (1, 1, 1)), run(True, t3, (1, 1, 1)))
+    ctx.set_graphs(True)
+    assert ctx.get_status() == 0
