@@ -189,14 +189,19 @@ int tersoff_md_force(tersoff_ctx *ctx, int32_t N, const double *pos, const doubl
 /* Neighbour list of the last tersoff_md_force call, like tersoff_export_neighbors. Synchronous. */
 int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift);
 
-/* Launch mode of the per-call kernel sequences; the paper has no counterpart. With graphs on (the
- * default) tersoff_fitness captures its launch sequence (preparation, batched kernel, finalize) into a
- * CUDA graph on a private stream the first time and replays it with one graph launch while the
- * arguments (pointers, P, weights, precision), the neighbour build's work schedule and the context's
- * buffers are unchanged; any change re-captures. Results are identical either way. Calls made while
- * kernel timing (tersoff_profile) is on, or on a stream that is being captured, launch directly.
- * Returns TERSOFF_E_ARG for a null context. */
-int tersoff_set_graphs(tersoff_ctx *ctx, int32_t enable);
+/* Launch mode of the per-call kernel sequences (bits, default both); the paper has no counterpart.
+ *  TERSOFF_LAUNCH_GRAPHS: tersoff_fitness captures its launch sequence (preparation, batched kernel,
+ *    finalize) into a CUDA graph on a private stream the first time and replays it with one graph
+ *    launch while the arguments (pointers, P, weights, precision), the neighbour build's work
+ *    schedule and the context's buffers are unchanged; any change re-captures. Calls made while
+ *    kernel timing (tersoff_profile) is on, or on a stream that is being captured, launch directly.
+ *  TERSOFF_LAUNCH_PDL: the batched and finalize kernels are launched with programmatic stream
+ *    serialization, so each may start while its predecessor finishes (it waits before reading the
+ *    predecessor's results).
+ * Results are identical in every mode. Returns TERSOFF_E_ARG for a null context or unknown bits. */
+#define TERSOFF_LAUNCH_GRAPHS 1
+#define TERSOFF_LAUNCH_PDL 2
+int tersoff_set_launch_mode(tersoff_ctx *ctx, int32_t mode);
 
 /* Measurement helpers; the paper has no counterpart.
  * tersoff_kernel_launches: number of kernels the library has launched in this process, all contexts

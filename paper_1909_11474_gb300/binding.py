@@ -21,12 +21,15 @@ OK, E_ARG, E_NBR_OVERFLOW, E_CUDA, E_NONFINITE, E_TIMEOUT, E_STATE, E_UNSUPPORTE
 STATUS_NBR_OVERFLOW, STATUS_MANY_NBRS, STATUS_NONFINITE, STATUS_TIMEOUT = 1, 2, 4, 8
 LOSS_SQ, LOSS_Z = 0, 1
 
+LAUNCH_GRAPHS = 1
+LAUNCH_PDL = 2
+
 EXPORTED = (
     "tersoff_create", "tersoff_destroy", "tersoff_last_error", "tersoff_get_status",
     "tersoff_build_neighbors", "tersoff_export_neighbors", "tersoff_build_info", "tersoff_eval",
     "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
     "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
-    "tersoff_profile", "tersoff_profile_read", "tersoff_set_graphs",
+    "tersoff_profile", "tersoff_profile_read", "tersoff_set_launch_mode",
 )
 
 _vp = ctypes.c_void_p
@@ -75,7 +78,7 @@ def load():
                                                   _vp, _vp, _vp, _vp]),
         "tersoff_kernel_launches": (ctypes.c_int64, []),
         "tersoff_profile": (ctypes.c_int, [_vp, _i32]),
-        "tersoff_set_graphs": (ctypes.c_int, [_vp, _i32]),
+        "tersoff_set_launch_mode": (ctypes.c_int, [_vp, _i32]),
         "tersoff_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_f64)]),
     }
     for name, (res, args) in sig.items():
@@ -155,9 +158,10 @@ class Context:
         """Kernels launched by the library in this process so far (all contexts)."""
         return int(self.lib.tersoff_kernel_launches())
 
-    def set_graphs(self, enable: bool = True):
-        """Replay the fitness call's launch sequence from a cached CUDA graph (default) or launch it directly."""
-        self._check(self.lib.tersoff_set_graphs(self.h, 1 if enable else 0))
+    def set_launch_mode(self, graphs: bool = True, pdl: bool = True):
+        """Replay the fitness call's launch sequence from a cached CUDA graph (graphs) and/or launch its
+        kernels with programmatic dependent launch (pdl); both on by default."""
+        self._check(self.lib.tersoff_set_launch_mode(self.h, (LAUNCH_GRAPHS if graphs else 0) | (LAUNCH_PDL if pdl else 0)))
 
     def profile(self, enable: bool = True):
         """Start or stop CUDA-event timing of the batched E/F/W kernel (clears earlier records)."""

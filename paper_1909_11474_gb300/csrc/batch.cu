@@ -26,7 +26,7 @@ int batch_max_smem_optin() {
 }
 
 template <int MMAX, bool CLUSTER, int MINB, typename R>
-static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t smem, bool uniform,
+static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t smem, bool uniform, bool pdl,
                                   cudaStream_t s) {
   auto kern = batch_kernel<kPT, MMAX, CLUSTER, MINB, R>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -54,18 +54,23 @@ static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  // programmatic dependent launch: the kernel may start while its predecessor (the preparation kernel
+  // or the previous bucket) runs; it waits for it before reading the per-call constants
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if constexpr (CLUSTER) {
     if (cluster > 8) {
       e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
     }
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = cluster;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.numAttrs = 2;
   }
   const cudaError_t el = cudaLaunchKernelEx(&cfg, kern, bp);
   if (el == cudaSuccess) count_launches(1);
@@ -83,13 +88,13 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
     if (f64)
       prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts),
                                                  ctx.Ntot, out.tF, reinterpret_cast<dvec4 *>(out.tF4), ctx.C,
-                                                 ctx.atom_off.as<int>(), out.tE, out.tW,
-                                                 tew ? reinterpret_cast<double *>(out.tEW) : nullptr);
+                                                 ctx.atom_off.as<int>(), out.tE, out.tW, out.tmask,
+                                                 tew ? reinterpret_cast<double *>(out.tEW) : nullptr, out.dpart);
     else
       prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts),
                                                 ctx.Ntot, out.tF, reinterpret_cast<float4 *>(out.tF4), ctx.C,
-                                                ctx.atom_off.as<int>(), out.tE, out.tW,
-                                                tew ? reinterpret_cast<float *>(out.tEW) : nullptr);
+                                                ctx.atom_off.as<int>(), out.tE, out.tW, out.tmask,
+                                                tew ? reinterpret_cast<float *>(out.tEW) : nullptr, out.dpart);
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
@@ -129,14 +134,14 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
     cudaError_t e = cudaSuccess;
     const bool cl = b.cluster > 1;
     if (!f64) {
-      if (!cl && b.mmax <= 4) e = launch_variant<4, false, 2, float>(bp, b.nitems, 1, b.smem, b.uniform, s);
-      else if (!cl && b.mmax <= 6) e = launch_variant<6, false, 1, float>(bp, b.nitems, 1, b.smem, b.uniform, s);
-      else if (!cl) e = launch_variant<8, false, 1, float>(bp, b.nitems, 1, b.smem, b.uniform, s);
-      else if (b.mmax <= 6) e = launch_variant<6, true, 1, float>(bp, b.nitems, b.cluster, b.smem, b.uniform, s);
-      else e = launch_variant<8, true, 1, float>(bp, b.nitems, b.cluster, b.smem, b.uniform, s);
+      if (!cl && b.mmax <= 4) e = launch_variant<4, false, 2, float>(bp, b.nitems, 1, b.smem, b.uniform, out.pdl, s);
+      else if (!cl && b.mmax <= 6) e = launch_variant<6, false, 1, float>(bp, b.nitems, 1, b.smem, b.uniform, out.pdl, s);
+      else if (!cl) e = launch_variant<8, false, 1, float>(bp, b.nitems, 1, b.smem, b.uniform, out.pdl, s);
+      else if (b.mmax <= 6) e = launch_variant<6, true, 1, float>(bp, b.nitems, b.cluster, b.smem, b.uniform, out.pdl, s);
+      else e = launch_variant<8, true, 1, float>(bp, b.nitems, b.cluster, b.smem, b.uniform, out.pdl, s);
     } else {
-      if (!cl) e = launch_variant<8, false, 1, double>(bp, b.nitems, 1, b.smem, b.uniform, s);
-      else e = launch_variant<8, true, 1, double>(bp, b.nitems, b.cluster, b.smem, b.uniform, s);
+      if (!cl) e = launch_variant<8, false, 1, double>(bp, b.nitems, 1, b.smem, b.uniform, out.pdl, s);
+      else e = launch_variant<8, true, 1, double>(bp, b.nitems, b.cluster, b.smem, b.uniform, out.pdl, s);
     }
     if (e != cudaSuccess) return e;
   }
@@ -145,57 +150,35 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
 }
 
 // Fitness of every parameter set from the per-(p, c) residual terms of the batched kernel
-// (Eq. 15-19): S_q[p] = sum_c part[p][c][q]; D_e = sum_c E*_c^2 and D_v = sum_c |W*_c|^2 over the
-// configurations whose mask has the quantity; D_f = sum_c of the per-configuration |F*|^2 sums.
-// All sums in FP64 in a fixed order (threads strided over c, then a fixed xor-shuffle tree and the
-// warps in index order). Zq = sqrt(S_q/D_q) (0 where D_q = 0), Z = sum_q w_q Zq, and Z = +inf when
-// any residual sum of p is not finite. One block per kFinPB parameter sets.
-constexpr int kFinPB = 4;
-constexpr int kFinThreads = 256;
+// (Eq. 15-19): S_q[p] = sum_c part[p][c][q] and D_q = sum_c dpart[c][q], both in FP64 in a fixed
+// order (lanes strided over c, then a fixed xor-shuffle tree). Zq = sqrt(S_q/D_q) (0 where D_q = 0),
+// Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not finite. One warp per parameter set.
+constexpr int kFinWarps = 8;
 
 template <typename R>
-__global__ void __launch_bounds__(kFinThreads) fitness_finalize_kernel(
-    int P, int C, const R *__restrict__ part, const R *__restrict__ dpart, const double *__restrict__ tE,
-    const double *__restrict__ tW, const uint8_t *__restrict__ tmask, double we, double wv, double wf,
+__global__ void __launch_bounds__(kFinWarps * 32) fitness_finalize_kernel(
+    int P, int C, const R *__restrict__ part, const double *__restrict__ dpart, double we, double wv, double wf,
     double *__restrict__ Z, double *__restrict__ Zq, double *__restrict__ S) {
-  constexpr int NV = 3 * kFinPB + 3;   // S_q of the block's parameter sets, then D_q
-  constexpr int NWARP = kFinThreads / 32;
-  __shared__ double red[NWARP][NV];
-  const int p0 = blockIdx.x * kFinPB;
-  const int np = min(kFinPB, P - p0);
-  double v[NV];
+  pdl_wait();   // launched while the batched kernel may still run: wait for its results
+  const int p = blockIdx.x * kFinWarps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (p >= P) return;
+  double s[3] = {0.0, 0.0, 0.0}, d[3] = {0.0, 0.0, 0.0};
+  const R *pp = part + (size_t)p * C * 3;
+  for (int c = lane; c < C; c += 32) {
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = 0.0;
-  for (int c = threadIdx.x; c < C; c += kFinThreads) {
-    const uint8_t m = tmask[c];
-    if (m & 1) v[3 * kFinPB] += tE[c] * tE[c];
-    if (m & 2)
-      for (int k = 0; k < 6; ++k) v[3 * kFinPB + 1] += tW[6 * c + k] * tW[6 * c + k];
-    if (m & 4) v[3 * kFinPB + 2] += (double)dpart[c];
-#pragma unroll
-    for (int j = 0; j < kFinPB; ++j)
-      if (j < np)
-        for (int q = 0; q < 3; ++q) v[3 * j + q] += (double)part[((size_t)(p0 + j) * C + c) * 3 + q];
+    for (int q = 0; q < 3; ++q) {
+      s[q] += (double)pp[3 * c + q];
+      d[q] += dpart[3 * c + q];
+    }
   }
 #pragma unroll
-  for (int k = 0; k < NV; ++k)
-    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
-  __syncthreads();
-  if (threadIdx.x < np) {
-    const int j = threadIdx.x;
-    double s[3], d[3];
-    for (int q = 0; q < 3; ++q) {
-      s[q] = 0.0;
-      d[q] = 0.0;
-      for (int w = 0; w < NWARP; ++w) {
-        s[q] += red[w][3 * j + q];
-        d[q] += red[w][3 * kFinPB + q];
-      }
+  for (int q = 0; q < 3; ++q)
+    for (int off = 16; off > 0; off >>= 1) {
+      s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
+      d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
     }
+  if (lane == 0) {
     const double wq[3] = {we, wv, wf};
     double z = 0.0, zq[3];
     bool finite = true;
@@ -204,7 +187,6 @@ __global__ void __launch_bounds__(kFinThreads) fitness_finalize_kernel(
       zq[q] = d[q] > 0.0 ? sqrt(s[q] / d[q]) : 0.0;
       z += wq[q] * zq[q];
     }
-    const int p = p0 + j;
     Z[p] = finite ? z : INFINITY;
     if (Zq)
       for (int q = 0; q < 3; ++q) Zq[(size_t)p * 3 + q] = zq[q];
@@ -213,20 +195,29 @@ __global__ void __launch_bounds__(kFinThreads) fitness_finalize_kernel(
   }
 }
 
-cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *part, const void *dpart,
-                                    const double *tE, const double *tW, const uint8_t *tmask,
-                                    double we, double wv, double wf, double *Z, double *Zq,
-                                    double *S, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((P + kFinPB - 1) / kFinPB);
+cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *part, const double *dpart,
+                                    double we, double wv, double wf, double *Z, double *Zq, double *S, bool pdl,
+                                    cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)((P + kFinWarps - 1) / kFinWarps));
+  cfg.blockDim = dim3(kFinWarps * 32);
+  cfg.stream = s;
+  // the batched kernel gives no early trigger, so this launch starts when it completes; the attribute
+  // only shortens the hand-over
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
   if (precision == 64)
-    fitness_finalize_kernel<double><<<blocks, kFinThreads, 0, s>>>(
-        P, C, static_cast<const double *>(part), static_cast<const double *>(dpart), tE, tW, tmask, we, wv,
-        wf, Z, Zq, S);
+    e = cudaLaunchKernelEx(&cfg, fitness_finalize_kernel<double>, P, C, static_cast<const double *>(part), dpart, we,
+                           wv, wf, Z, Zq, S);
   else
-    fitness_finalize_kernel<float><<<blocks, kFinThreads, 0, s>>>(
-        P, C, static_cast<const float *>(part), static_cast<const float *>(dpart), tE, tW, tmask, we, wv,
-        wf, Z, Zq, S);
-  return launched(1);
+    e = cudaLaunchKernelEx(&cfg, fitness_finalize_kernel<float>, P, C, static_cast<const float *>(part), dpart, we,
+                           wv, wf, Z, Zq, S);
+  if (e == cudaSuccess) count_launches(1);
+  return e;
 }
 
 }  // namespace tsf

@@ -364,7 +364,7 @@ struct BatchParams {
   const uint8_t *tmask;
   const void *tEW;                 // R [C][8]: E*, W*[6], 1/N of every configuration (fitness)
   void *part;                      // R [P][C][3]: S_e, S_v, S_f terms of every (p, c) (fitness)
-  void *dpart;                     // R [C]: sum of |F*|^2 over the configuration's atoms (fitness)
+  double *dpart;                   // [C][3]: target-norm terms; [c][2] = sum of |F*|^2 (fitness)
   unsigned *status;
 };
 
@@ -416,6 +416,229 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
       : "memory");
 }
 constexpr unsigned kMbarSpins = 1u << 22;   // bound of a wait for one configuration's copies
+
+// One parameter tile of PTT parameter sets (PTT = 32: one atom per warp; 16 or 8: 2 or 4 atoms per
+// warp, used for the last, partly filled tile) of the item staged in shared memory: passes 1-3, the
+// reductions and the per-(parameter set, configuration) outputs. `tile` counts tiles of the launch's
+// full width PTW, so the tile's parameter sets are tile * PTW + (0 .. PTT-1).
+template <typename R>
+struct TileEnv {
+  R *stage;
+  const typename Vec4<R>::T *sA, *sB;
+  const R *sC;
+  const int4 *satom;
+  const typename Vec4<R>::T *stF;
+  int ns, s0, nat, c, cb0, B0;
+  uint8_t mask;
+  bool fit;
+  unsigned rank, ncta;
+  const unsigned *peer_stage;
+  const int *peer_b0;
+};
+
+template <int PTT, int PTW, int MMAX, bool CLUSTER, typename R>
+__device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R> &env, int tile) {
+  using R4 = typename Vec4<R>::T;
+  constexpr int APW = kWarp / PTT;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int slot = lane / PTT, pl = lane % PTT;
+  R *stage = env.stage;
+  const R4 *sA = env.sA, *sB = env.sB, *stF = env.stF;
+  const R *sC = env.sC;
+  const int4 *satom = env.satom;
+  const int ns = env.ns, s0 = env.s0, nat = env.nat, c = env.c, cb0 = env.cb0, B0 = env.B0;
+  const uint8_t mask = env.mask;
+  const bool fit = env.fit;
+  const unsigned rank = env.rank, ncta = env.ncta;
+  const unsigned *peer_stage = env.peer_stage;
+  const int *peer_b0 = env.peer_b0;
+  (void)B0;
+  (void)peer_stage;
+  (void)peer_b0;
+  (void)rank;
+  (void)ncta;
+  const int p = tile * PTW + pl;
+  const bool active = p < a.P;
+  PConsts<R> K;
+  {
+    const R4 *kc = reinterpret_cast<const R4 *>(a.consts) + 2 * (active ? p : a.P - 1);
+    const R4 k0 = kc[0], k1 = kc[1];
+    K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.mha = k0.w;
+    K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
+  }
+  AtomAcc<R> acc;
+  acc.U = R(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc.W[k] = R(0);
+
+  // ---- passes 1-2
+  for (int base = warp * APW; base < ns; base += kNW * APW) {
+    const int li = base + slot;
+    const bool valid = li < ns;
+    int4 at = make_int4(0, 0, 0, 0);
+    if (valid) at = sld(&satom[li], 11);
+    const int m = at.z;
+    if constexpr (APW == 1) {
+      if (m > MMAX) {
+        if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
+        continue;
+      }
+      if (sizeof(R) == 4 && at.w == 0)
+        atom_forward_dispatch<PTT, MMAX, true, sizeof(R) == 4, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+      else
+        atom_forward_dispatch<PTT, MMAX, true, false, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+    } else {
+      const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
+      const bool uniform = __all_sync(0xffffffffu, m == Mw);
+      if (Mw > MMAX) {
+        if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
+        continue;
+      }
+      if (uniform && sizeof(R) == 4 && __all_sync(0xffffffffu, at.w == 0))
+        atom_forward_dispatch<PTT, MMAX, true, sizeof(R) == 4, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+      else if (uniform)
+        atom_forward_dispatch<PTT, MMAX, true, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+      else
+        atom_forward_dispatch<PTT, MMAX, false, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+    }
+  }
+  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
+
+  // ---- pass 3: F_i = sum_j (P_ij - P_ji)
+  R sf = R(0), sF2 = R(0), sT = R(0);
+  for (int base = warp * APW; base < ns; base += kNW * APW) {
+    const int li = base + slot;
+    if (li >= ns) continue;
+    const int4 at = sld(&satom[li], 12);
+    const int m = at.z, lb = at.x;
+    R Fx = R(0), Fy = R(0), Fz = R(0);
+    for (int e = 0; e < m; ++e) {
+      const R *st = stage + (size_t)(lb + e) * 3 * PTT + pl;
+      Fx += sld(&st[0], 13);
+      Fy += sld(&st[PTT], 13);
+      Fz += sld(&st[2 * PTT], 13);
+      int rb;  // configuration-local bond index of the reverse entry
+      if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sld(&sB[lb + e].w, 14)) & 0xffff;
+      else rb = (int)sld(&sB[lb + e].w, 14) & 0xffff;
+      if constexpr (CLUSTER) {
+        unsigned r = 0;
+        while (r + 1 < ncta && rb >= peer_b0[r + 1]) ++r;
+        // a reverse bond outside the configuration's bond range is an inconsistent schedule:
+        // flag it and skip the peer read rather than touch another CTA's shared memory
+        if (rb < peer_b0[r] || rb >= peer_b0[r + 1]) {
+          set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
+#ifdef TSF_DEBUG_BOUNDS
+          if (atomicCAS(&tsf_dbg[0], 0u, 1u) == 0u) {
+            tsf_dbg[1] = 21;
+            tsf_dbg[2] = (unsigned)rb;
+            tsf_dbg[3] = (unsigned)peer_b0[ncta];
+          }
+#endif
+          continue;
+        }
+        const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * 3 * PTT + pl) * sizeof(R));
+        Fx -= ld_cluster(addr, R(0));
+        Fy -= ld_cluster(addr + PTT * sizeof(R), R(0));
+        Fz -= ld_cluster(addr + 2 * PTT * sizeof(R), R(0));
+      } else {
+        const R *sr = stage + (size_t)(rb + cb0 - B0) * 3 * PTT + pl;
+        Fx -= sld(&sr[0], 15);
+        Fy -= sld(&sr[PTT], 15);
+        Fz -= sld(&sr[2 * PTT], 15);
+      }
+    }
+    if (!(mask & 4)) sF2 += Fx * Fx + Fy * Fy + Fz * Fz;   // finiteness of F when no residual checks it
+    const int i = s0 + li;
+    if (a.mode == kModeEval) {
+      if (active && a.F) {
+        const size_t o = ((size_t)p * a.Ntot + i) * 3;
+        R *F = reinterpret_cast<R *>(a.F);
+        F[o] = Fx;
+        F[o + 1] = Fy;
+        F[o + 2] = Fz;
+      }
+    } else if (mask & 4) {
+      const R4 t = sld(&stF[li], 16);
+      const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
+      sf += ex * ex + ey * ey + ez * ez;
+      sT += t.w;
+    }
+  }
+
+  // ---- reductions: over atom slots (shuffles), warps (shared memory, fixed order), ranks
+  R v[kNRed];
+  v[0] = acc.U;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) v[1 + k] = acc.W[k];
+  v[7] = sf;
+  v[8] = sF2;
+  v[9] = sT;
+#pragma unroll
+  for (int k = 0; k < kNRed; ++k) v[k] = sum_over_atom_slots<PTT>(v[k]);
+  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();   // stages no longer read
+  R *red = stage;                                   // [kNW][kNRed][PTT]
+  R *tot = stage + kNW * kNRed * PTT;                // [ranks][kNRed][PTT] (rank 0 collects)
+  if (slot == 0) {
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PTT + pl], v[k], 17);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < kNRed * PTT; idx += kThreads) {
+    R t = R(0);
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) t += sld(&red[w * kNRed * PTT + idx], 18);
+    if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(tot + rank * kNRed * PTT + idx), 0), t);
+    else sst(&tot[idx], t, 19);
+  }
+  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
+
+  if (rank == 0 && tid < PTT) {
+    const int pp = tile * PTW + tid;
+    R q[kNRed];
+#pragma unroll
+    for (int k = 0; k < kNRed; ++k) {
+      R s = R(0);
+      for (unsigned r = 0; r < ncta; ++r) s += sld(&tot[(r * kNRed + k) * PTT + tid], 20);
+      q[k] = s;
+    }
+    if (pp < a.P) {
+      if (a.mode == kModeEval) {
+        if (a.E) a.E[(size_t)pp * a.C + c] = (double)q[0];
+        if (a.W)
+          for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = (double)q[1 + k];
+      } else {
+        // per-atom residuals of Eq. 17-18 in the working precision (the FP64 sums over
+        // configurations are formed by the finalize kernel)
+        const R *tw = reinterpret_cast<const R *>(a.tEW) + (size_t)c * 8;
+        const R invN = tw[7];
+        bool finite = isfinite(q[0]) && isfinite(q[8]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);
+        R se = R(0), sv = R(0), sfv = R(0);
+        if (mask & 1) {
+          const R d = q[0] * invN - tw[0];
+          se = d * d;
+        }
+        if (mask & 2) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const R d = q[1 + k] * invN - tw[1 + k];
+            sv += d * d;
+          }
+        }
+        if (mask & 4) sfv = q[7];
+        if (!finite) se = sv = sfv = R(NAN);
+        R *o = reinterpret_cast<R *>(a.part) + ((size_t)pp * a.C + c) * 3;
+        o[0] = se;
+        o[1] = sv;
+        o[2] = sfv;
+      }
+    }
+    if (fit && tile == 0 && tid == 0) a.dpart[3 * c + 2] = (mask & 4) ? (double)q[9] : 0.0;
+  }
+  // the next tile (or item) reuses the stage and, in rank 0, the collected totals
+  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
+}
 
 // Persistent work loop. The launch covers nconf configurations of one bucket (longest first), each
 // split into nchunks chunks of chunk_tiles parameter tiles; a CTA (or cluster) claims the next item
@@ -502,6 +725,7 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
         }
         for (int t = tid; t < nq; t += kThreads) sst(&sC[t], gC[t], 8);
       }
+      pdl_wait();   // constants and targets of the preparation kernel (a no-op after the first item)
       for (int t = tid; t < ns; t += kThreads) {
         const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
         sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, a.outer[s0 + t]), 9);
@@ -537,204 +761,44 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
       peer_b0[ncta] = a.recs[rec0 + ncta - 1].B0 + a.recs[rec0 + ncta - 1].nb - cb0;
     }
 
+    const TileEnv<R> env = {stage, sA, sB, sC, satom, stF, ns, s0, nat, c, cb0, B0, mask, fit, rank, ncta,
+                             peer_stage, peer_b0};
+    // the last tile may hold fewer parameter sets: the FP32 single-CTA variant for up to 4 neighbours
+    // runs it with 2 or 4 atoms in a warp (tiles of 16 or 8 parameter sets); other variants keep the
+    // full width
+    constexpr bool kNarrow = !CLUSTER && MMAX <= 4 && sizeof(R) == 4 && PT == 32;
     for (int tile = tile0; tile < tile1; ++tile) {
-      const int p = tile * PT + pl;
-      const bool active = p < a.P;
-      PConsts<R> K;
-      {
-        const R4 *kc = reinterpret_cast<const R4 *>(a.consts) + 2 * (active ? p : a.P - 1);
-        const R4 k0 = kc[0], k1 = kc[1];
-        K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.mha = k0.w;
-        K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
-      }
-      AtomAcc<R> acc;
-      acc.U = R(0);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) acc.W[k] = R(0);
-
-      // ---- passes 1-2
-      for (int base = warp * APW; base < ns; base += kNW * APW) {
-        const int li = base + slot;
-        const bool valid = li < ns;
-        int4 at = make_int4(0, 0, 0, 0);
-        if (valid) at = sld(&satom[li], 11);
-        const int m = at.z;
-        if constexpr (APW == 1) {
-          if (m > MMAX) {
-            if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
-            continue;
-          }
-          if (sizeof(R) == 4 && at.w == 0)
-            atom_forward_dispatch<PT, MMAX, true, sizeof(R) == 4, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
-          else
-            atom_forward_dispatch<PT, MMAX, true, false, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
-        } else {
-          const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
-          const bool uniform = __all_sync(0xffffffffu, m == Mw);
-          if (Mw > MMAX) {
-            if (lane == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
-            continue;
-          }
-          if (uniform)
-            atom_forward_dispatch<PT, MMAX, true, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
-          else
-            atom_forward_dispatch<PT, MMAX, false, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
-        }
-      }
-      if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
-
-      // ---- pass 3: F_i = sum_j (P_ij - P_ji)
-      R sf = R(0), sF2 = R(0), sT = R(0);
-      for (int base = warp * APW; base < ns; base += kNW * APW) {
-        const int li = base + slot;
-        if (li >= ns) continue;
-        const int4 at = sld(&satom[li], 12);
-        const int m = at.z, lb = at.x;
-        R Fx = R(0), Fy = R(0), Fz = R(0);
-        for (int e = 0; e < m; ++e) {
-          const R *st = stage + (size_t)(lb + e) * 3 * PT + pl;
-          Fx += sld(&st[0], 13);
-          Fy += sld(&st[PT], 13);
-          Fz += sld(&st[2 * PT], 13);
-          int rb;  // configuration-local bond index of the reverse entry
-          if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sld(&sB[lb + e].w, 14)) & 0xffff;
-          else rb = (int)sld(&sB[lb + e].w, 14) & 0xffff;
-          if constexpr (CLUSTER) {
-            unsigned r = 0;
-            while (r + 1 < ncta && rb >= peer_b0[r + 1]) ++r;
-            // a reverse bond outside the configuration's bond range is an inconsistent schedule:
-            // flag it and skip the peer read rather than touch another CTA's shared memory
-            if (rb < peer_b0[r] || rb >= peer_b0[r + 1]) {
-              set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
-#ifdef TSF_DEBUG_BOUNDS
-              if (atomicCAS(&tsf_dbg[0], 0u, 1u) == 0u) {
-                tsf_dbg[1] = 21;
-                tsf_dbg[2] = (unsigned)rb;
-                tsf_dbg[3] = (unsigned)peer_b0[ncta];
-              }
-#endif
-              continue;
-            }
-            const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * 3 * PT + pl) * sizeof(R));
-            Fx -= ld_cluster(addr, R(0));
-            Fy -= ld_cluster(addr + PT * sizeof(R), R(0));
-            Fz -= ld_cluster(addr + 2 * PT * sizeof(R), R(0));
-          } else {
-            const R *sr = stage + (size_t)(rb + cb0 - B0) * 3 * PT + pl;
-            Fx -= sld(&sr[0], 15);
-            Fy -= sld(&sr[PT], 15);
-            Fz -= sld(&sr[2 * PT], 15);
-          }
-        }
-        if (!(mask & 4)) sF2 += Fx * Fx + Fy * Fy + Fz * Fz;   // finiteness of F when no residual checks it
-        const int i = s0 + li;
-        if (a.mode == kModeEval) {
-          if (active && a.F) {
-            const size_t o = ((size_t)p * a.Ntot + i) * 3;
-            R *F = reinterpret_cast<R *>(a.F);
-            F[o] = Fx;
-            F[o + 1] = Fy;
-            F[o + 2] = Fz;
-          }
-        } else if (mask & 4) {
-          const R4 t = sld(&stF[li], 16);
-          const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
-          sf += ex * ex + ey * ey + ez * ez;
-          sT += t.w;
-        }
-      }
-
-      // ---- reductions: over atom slots (shuffles), warps (shared memory, fixed order), ranks
-      R v[kNRed];
-      v[0] = acc.U;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) v[1 + k] = acc.W[k];
-      v[7] = sf;
-      v[8] = sF2;
-      v[9] = sT;
-#pragma unroll
-      for (int k = 0; k < kNRed; ++k) v[k] = sum_over_atom_slots<PT>(v[k]);
-      if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();   // stages no longer read
-      R *red = stage;                                   // [kNW][kNRed][PT]
-      R *tot = stage + kNW * kNRed * PT;                // [ranks][kNRed][PT] (rank 0 collects)
-      if (slot == 0) {
-#pragma unroll
-        for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PT + pl], v[k], 17);
-      }
-      __syncthreads();
-      for (int idx = tid; idx < kNRed * PT; idx += kThreads) {
-        R t = R(0);
-#pragma unroll
-        for (int w = 0; w < kNW; ++w) t += sld(&red[w * kNRed * PT + idx], 18);
-        if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(tot + rank * kNRed * PT + idx), 0), t);
-        else sst(&tot[idx], t, 19);
-      }
-      if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
-
-      if (rank == 0 && tid < PT) {
-        const int pp = tile * PT + tid;
-        R q[kNRed];
-#pragma unroll
-        for (int k = 0; k < kNRed; ++k) {
-          R s = R(0);
-          for (unsigned r = 0; r < ncta; ++r) s += sld(&tot[(r * kNRed + k) * PT + tid], 20);
-          q[k] = s;
-        }
-        if (pp < a.P) {
-          if (a.mode == kModeEval) {
-            if (a.E) a.E[(size_t)pp * a.C + c] = (double)q[0];
-            if (a.W)
-              for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = (double)q[1 + k];
-          } else {
-            // per-atom residuals of Eq. 17-18 in the working precision (the FP64 sums over
-            // configurations are formed by the finalize kernel)
-            const R *tw = reinterpret_cast<const R *>(a.tEW) + (size_t)c * 8;
-            const R invN = tw[7];
-            bool finite = isfinite(q[0]) && isfinite(q[8]);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);
-            R se = R(0), sv = R(0), sfv = R(0);
-            if (mask & 1) {
-              const R d = q[0] * invN - tw[0];
-              se = d * d;
-            }
-            if (mask & 2) {
-#pragma unroll
-              for (int k = 0; k < 6; ++k) {
-                const R d = q[1 + k] * invN - tw[1 + k];
-                sv += d * d;
-              }
-            }
-            if (mask & 4) sfv = q[7];
-            if (!finite) se = sv = sfv = R(NAN);
-            R *o = reinterpret_cast<R *>(a.part) + ((size_t)pp * a.C + c) * 3;
-            o[0] = se;
-            o[1] = sv;
-            o[2] = sfv;
-          }
-        }
-        if (fit && tile == 0 && tid == 0) reinterpret_cast<R *>(a.dpart)[c] = (mask & 4) ? q[9] : R(0);
-      }
-      // the next tile (or item) reuses the stage and, in rank 0, the collected totals
-      if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
+      const int width = min(PT, a.P - tile * PT);
+      if (kNarrow && width <= 8) tile_pass<(kNarrow ? 8 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
+      else if (kNarrow && width <= 16) tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
+      else tile_pass<PT, PT, MMAX, CLUSTER, R>(a, env, tile);
     }
   }
 }
 
 // Per call: FP32/FP64 constants of every parameter set, the target forces as R4 (x, y, z, |F|^2) and,
-// when tEW is given, each configuration's targets and atom count as R [C][8] (E*, W*[6], 1/N).
+// when tEW is given, each configuration's targets and atom count as R [C][8] (E*, W*[6], 1/N) and its
+// terms of the target norms D_e and D_v of Eq. 17-18 in FP64 (dpart[c][0..1]; masked-off quantities
+// contribute 0).
 template <typename R>
 __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restrict__ consts,
                             int64_t Ntot, const double *__restrict__ tF,
                             typename Vec4<R>::T *__restrict__ tF4, int C = 0,
                             const int *__restrict__ atom_off = nullptr, const double *__restrict__ tE = nullptr,
-                            const double *__restrict__ tW = nullptr, R *__restrict__ tEW = nullptr) {
+                            const double *__restrict__ tW = nullptr, const uint8_t *__restrict__ tmask = nullptr,
+                            R *__restrict__ tEW = nullptr, double *__restrict__ dpart = nullptr) {
+  pdl_trigger();   // the batched kernel may start staging geometry; it waits before reading our output
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tEW && t < C) {
     R *o = tEW + 8 * t;
     o[0] = (R)tE[t];
     for (int k = 0; k < 6; ++k) o[1 + k] = (R)tW[6 * t + k];
     o[7] = (R)(1.0 / (double)(atom_off[t + 1] - atom_off[t]));
+    const uint8_t m = tmask[t];
+    double dv = 0.0;
+    for (int k = 0; k < 6; ++k) dv += tW[6 * t + k] * tW[6 * t + k];
+    dpart[3 * t] = (m & 1) ? tE[t] * tE[t] : 0.0;
+    dpart[3 * t + 1] = (m & 2) ? dv : 0.0;
   }
   if (t < P) {
     const double *x = params + 6 * t;

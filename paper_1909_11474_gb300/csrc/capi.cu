@@ -263,9 +263,11 @@ void tersoff_destroy(tersoff_ctx *ctx) {
 
 int64_t tersoff_kernel_launches(void) { return (int64_t)tsf::g_launches.load(); }
 
-int tersoff_set_graphs(tersoff_ctx *ctx, int32_t enable) {
+int tersoff_set_launch_mode(tersoff_ctx *ctx, int32_t mode) {
   if (!ctx) return TERSOFF_E_ARG;
-  ctx->c.graphs = enable != 0;
+  if (mode & ~(TERSOFF_LAUNCH_GRAPHS | TERSOFF_LAUNCH_PDL)) return fail(ctx, TERSOFF_E_ARG, "unknown launch mode bits%s");
+  ctx->c.graphs = (mode & TERSOFF_LAUNCH_GRAPHS) != 0;
+  ctx->c.pdl = (mode & TERSOFF_LAUNCH_PDL) != 0;
   return TERSOFF_OK;
 }
 
@@ -538,7 +540,8 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   o.tF = tg->F;
   o.tmask = tg->mask;
   o.part = c.part.p;
-  o.dpart = c.dpart.p;
+  o.dpart = c.dpart.as<double>();
+  o.pdl = c.pdl;
   const tsf::BatchPlan &plan = precision == 64 ? c.plan64 : c.plan32;
   const double w0 = w[0], w1 = w[1], w2 = w[2];
   const tersoff_targets t = *tg;
@@ -546,11 +549,11 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
                                (uint64_t)(uintptr_t)t.E, (uint64_t)(uintptr_t)t.W, (uint64_t)(uintptr_t)t.F,
                                (uint64_t)(uintptr_t)t.mask, bits(w0), bits(w1), bits(w2), (uint64_t)(uintptr_t)Z,
                                (uint64_t)(uintptr_t)Zq, (uint64_t)(uintptr_t)Sq, plan.gen, (uint64_t)c.C,
-                               (uint64_t)c.Ntot};
+                               (uint64_t)c.Ntot, (uint64_t)c.pdl};
   return run_graphed(ctx, c.g_fitness, std::move(key), S(stream), [&](cudaStream_t s) {
     cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
     if (e == cudaSuccess)
-      e = tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, t.E, t.W, t.mask, w0, w1, w2, Z, Zq, Sq, s);
+      e = tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, w0, w1, w2, Z, Zq, Sq, o.pdl, s);
     return e;
   });
 }

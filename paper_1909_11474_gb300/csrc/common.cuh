@@ -46,6 +46,13 @@ struct Vec4<double> {
   using T = dvec4;
 };
 
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization may start
+// before its predecessor in the stream has finished; it waits here before reading that predecessor's
+// results. The predecessor lets its dependents launch early with pdl_trigger. Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ void set_status(unsigned *status, unsigned bit) {
   if (status) atomicOr(status, bit);
 }

@@ -186,8 +186,9 @@ struct Ctx {
   // --- measurement: CUDA events around each batched-kernel launch sequence, on its stream ---
   mutable KernelTimer timer;
 
-  // --- CUDA graphs of the per-call launch sequences ---
+  // --- launch mode of the per-call launch sequences (CUDA graphs, programmatic dependent launch) ---
   bool graphs = true;
+  bool pdl = true;
   cudaStream_t cap_stream = nullptr;   // private stream the sequences are captured on
   GraphCache g_fitness;
 };
@@ -227,19 +228,19 @@ struct BatchOut {
   const double *tE, *tW, *tF;
   const uint8_t *tmask;
   void *part;         // workspace: [P][C][3] residual sums per (p, c) (working precision)
-  void *dpart;        // workspace: [C] sum of |F*|^2 per configuration (working precision)
+  double *dpart;      // workspace: [C][3] per-configuration terms of the target norms D_q (FP64)
   void *tEW;          // workspace: [C][8] E*, W*[6], 1/N per configuration (working precision)
   void *consts;       // workspace: [P][8] per-parameter-set constants (working precision)
   void *tF4;          // workspace: [Ntot] target forces as 4-vectors (working precision)
   int *counters;      // workspace: one work counter per launch bucket
+  bool pdl = false;   // launch the batched kernels with programmatic stream serialization
 };
 enum BatchMode { kModeEval = 0, kModeFitness = 1 };
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s);
-cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *part, const void *dpart,
-                                    const double *tE, const double *tW, const uint8_t *tmask,
-                                    double we, double wv, double wf, double *Z, double *Zq,
-                                    double *S, cudaStream_t s);
+cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *part, const double *dpart,
+                                    double we, double wv, double wf, double *Z, double *Zq, double *S, bool pdl,
+                                    cudaStream_t s);
 // capi.cu: FP64 geometry records on demand
 int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s);
 

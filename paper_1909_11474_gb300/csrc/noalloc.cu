@@ -88,9 +88,10 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   o.consts = base;
   o.tF4 = base + b_consts;
   o.part = base + b_consts + b_tf4;
-  o.dpart = base + b_consts + b_tf4 + b_part;
+  o.dpart = reinterpret_cast<double *>(base + b_consts + b_tf4 + b_part);
   o.tEW = base + b_consts + b_tf4 + b_part + b_dpart;
   o.counters = reinterpret_cast<int *>(base + b_consts + b_tf4 + b_part + b_dpart + b_tew);
+  o.pdl = c.pdl;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (precision == 64) {
     const int rc = tsf::ensure_geom64(ctx, s);   // kernels into buffers made by the neighbour build
@@ -98,8 +99,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   }
   cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
   if (e == cudaSuccess)
-    e = tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, tg->E, tg->W, tg->mask, w[0], w[1], w[2],
-                                     Z, Zq, S, s);
+    e = tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, w[0], w[1], w[2], Z, Zq, S, o.pdl, s);
   if (e != cudaSuccess) {
     char buf[160];
     std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));

@@ -214,8 +214,9 @@ def test_kernel_timer_and_launch_count(ctx):
 
 
 def test_fitness_graph_replay_matches_direct_launches(ctx):
-    """The fitness call replayed from its captured CUDA graph gives the results of direct launches,
-    and a change of arguments (targets, weights, P) or of the neighbour build re-captures."""
+    """The fitness call replayed from its captured CUDA graph (with programmatic dependent launch)
+    gives the results of plain direct launches, and a change of arguments (targets, weights, P) or of
+    the neighbour build re-captures."""
     w = I.workload_ga_batch(P=45, C=7)
     cs = w["configs"]
     _build(ctx, cs)
@@ -227,7 +228,7 @@ def test_fitness_graph_replay_matches_direct_launches(ctx):
     tg1, tg2 = targets_to_device(t1), targets_to_device(t2)
 
     def run(graphs, tg, wts, P=None):
-        ctx.set_graphs(graphs)
+        ctx.set_launch_mode(graphs=graphs, pdl=graphs)
         Z, Zq, S = ctx.fitness(params[:P], tg, w=wts)
         return torch.cat([Z[:, None], Zq, S], 1).cpu().numpy()
 
@@ -244,5 +245,5 @@ def test_fitness_graph_replay_matches_direct_launches(ctx):
     t3 = targets_to_device({"E": np.full(cs2.C, -4.6), "W": np.zeros((cs2.C, 6)),
                             "F": np.zeros((cs2.Ntot, 3)), "mask": np.full(cs2.C, 7, np.uint8)})
     assert np.array_equal(run(False, t3, (1, 1, 1)), run(True, t3, (1, 1, 1)))
-    ctx.set_graphs(True)
+    ctx.set_launch_mode()
     assert ctx.get_status() == 0
