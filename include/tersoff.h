@@ -87,15 +87,19 @@ typedef struct {
  * with a fixed evaluation order and no fused multiply-add:
  *     t = (n0*a + n1*b) + n2*c,  d = (x_j - x_i) + t,  r^2 = (dx*dx + dy*dy) + dz*dz < R2*R2.
  * Entries are kept in ascending (j, n0, n1, n2) order. The call also builds the parameter-independent
- * geometry cache (bond lengths, unit vectors, f_C and f_C' of Eq. 9, bond-angle cosines) in FP64,
- * stored in FP32 and FP64, and the evaluation schedule. It copies pos/box into the context (the
- * caller's buffers are not referenced after the call returns). It synchronises `stream` once, to
- * read the neighbour counts back, and returns with the geometry kernels enqueued on `stream`; a
- * rebuild of configurations of the same sizes whose neighbour counts are all unchanged reuses the
- * previous schedule.
+ * geometry cache (bond lengths, unit vectors, f_C and f_C' of Eq. 9, bond-angle cosines; FP32 now,
+ * FP64 on the first FP64 evaluation) and the evaluation schedule.
+ * The build runs as one kernel queued on `stream`, which copies pos/box into the context: the
+ * caller's pos/box must stay unchanged until that kernel has run (stream order suffices). The call
+ * returns once the work is queued. The neighbour counts come back to the host with it; the next
+ * call that uses the build (evaluation, fitness, gradient, export, build_info) waits for them,
+ * checks them and builds the schedule; a rebuild of configurations of the same sizes whose
+ * neighbour counts are all unchanged reuses the previous schedule.
  * R1 < R2 (Eq. 9; Sec. II.B uses R1 = 2.8, R2 = 3.2). 1 <= max_nbr <= 32 bounds the entries kept
- * per atom; an atom with more sets TERSOFF_STATUS_NBR_OVERFLOW and the call returns
- * TERSOFF_E_NBR_OVERFLOW. Positions or boxes that are not finite return TERSOFF_E_NONFINITE. */
+ * per atom. Argument errors are returned by this call. Errors found by the build kernel are
+ * returned by that next call (and set bits of the status word): an atom with more than max_nbr
+ * entries TERSOFF_E_NBR_OVERFLOW (TERSOFF_STATUS_NBR_OVERFLOW), positions or boxes that are not
+ * finite TERSOFF_E_NONFINITE. */
 int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double R1, double R2,
                             int32_t max_nbr, tersoff_stream stream);
 
@@ -104,8 +108,9 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
  * Any output pointer may be NULL. */
 int tersoff_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift);
 
-/* Number of atoms, bonds (neighbour entries) and the largest neighbour count of the last build. */
-int tersoff_build_info(const tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t *max_m);
+/* Number of atoms, bonds (neighbour entries) and the largest neighbour count of the last build
+ * (waits for the build as described at tersoff_build_neighbors). */
+int tersoff_build_info(tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t *max_m);
 
 /* Energy, forces and virial for every (parameter set p, configuration c) of the last build
  * (Eq. 1-14; forces F_i = -dU/dx_i and the virial above).
@@ -149,8 +154,8 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
  * and one fixed 8 MiB scratch array in device memory that every device loading the library keeps
  * until the process exits.
  *  Arguments, results and arithmetic are those of tersoff_fitness, and so are the results.
- *  Limit: P*8*8 + Ntot*32 + P*C*24 + C*24 + C*64 + 256 bytes (each part rounded up to 256) must fit in 8 MiB, e.g.
- *  P = 200 parameter sets over C = 300 cells of 64 atoms needs 2.1 MB; a larger request returns
+ *  Limit: P*8*8 + P*C*24 + C*24 + C*64 + 256 bytes (each part rounded up to 256) must fit in 8 MiB, e.g.
+ *  P = 200 parameter sets over C = 300 cells of 64 atoms needs 1.5 MB; a larger request returns
  *  TERSOFF_E_ARG with the byte count in tersoff_last_error and launches nothing.
  *  The first call on a device looks up the scratch array's device address (once per device); make
  *  that first call before any stream capture. Every call shares the one array and leaves its
@@ -160,6 +165,20 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
 int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, int32_t P,
                            const tersoff_targets *tg, const double *w, int32_t precision, double *Z,
                            double *Zq, double *S, tersoff_stream stream);
+
+/* Autotuner of the batched schedule; the paper has no counterpart. For the current build and these
+ * tersoff_fitness arguments (P, targets, precision; params is read as the workload), times every
+ * candidate schedule of each launch bucket -- work items per configuration (chunks of the parameter
+ * tiles claimed by the persistent CTAs) and, for the FP32 single-CTA variant of up to 4 neighbours,
+ * whether a partly filled last tile runs 2 or 4 atoms per warp -- over whole launches (the best of
+ * `reps` timed launches after one warm-up, CUDA events on `stream`), and keeps the fastest in the
+ * context. Later tersoff_fitness / tersoff_fitness_static / tersoff_eval calls with the same P use
+ * it until a rebuild changes the neighbour counts. Results of a tuned schedule equal the untuned
+ * ones up to the FP32 summation order of a narrow last tile. Synchronises `stream`.
+ *  reps 1..100; best_ms (host, may be NULL) receives the tuned launch time in ms; tried (host, may
+ *  be NULL) the number of candidates timed. Writes only the context's workspace. */
+int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
+                     int32_t precision, int32_t reps, double *best_ms, int32_t *tried, tersoff_stream stream);
 
 /* Loss and its gradient with respect to x = [D0, alpha, r0, beta, n, h] for every parameter set.
  *  loss TERSOFF_LOSS_SQ or TERSOFF_LOSS_Z (the latter has a zero gradient term where S_q = 0);

@@ -29,7 +29,7 @@ EXPORTED = (
     "tersoff_build_neighbors", "tersoff_export_neighbors", "tersoff_build_info", "tersoff_eval",
     "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
     "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
-    "tersoff_profile", "tersoff_profile_read", "tersoff_set_launch_mode",
+    "tersoff_profile", "tersoff_profile_read", "tersoff_set_launch_mode", "tersoff_autotune",
 )
 
 _vp = ctypes.c_void_p
@@ -79,6 +79,8 @@ def load():
         "tersoff_kernel_launches": (ctypes.c_int64, []),
         "tersoff_profile": (ctypes.c_int, [_vp, _i32]),
         "tersoff_set_launch_mode": (ctypes.c_int, [_vp, _i32]),
+        "tersoff_autotune": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _i32, _i32,
+                                            ctypes.POINTER(_f64), ctypes.POINTER(_i32), _vp]),
         "tersoff_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_f64)]),
     }
     for name, (res, args) in sig.items():
@@ -269,6 +271,17 @@ class Context:
                                                     ctypes.addressof(wv), precision, Z.data_ptr(), _ptr(Zq),
                                                     _ptr(S), _stream(stream)))
         return Z, Zq, S
+
+    def autotune(self, params: torch.Tensor, targets: dict, precision: int = 32, reps: int = 3, stream=None):
+        """Time the candidate schedules of the batched fitness launch for this P and keep the fastest
+        (tersoff_autotune). Returns (tuned launch time in ms, candidates timed)."""
+        P = params.shape[0]
+        _cuda(params, torch.float64, (P, 6), "params")
+        t = self._targets(targets)
+        ms, n = _f64(), _i32()
+        self._check(self.lib.tersoff_autotune(self.h, params.data_ptr(), P, ctypes.byref(t), precision, reps,
+                                              ctypes.byref(ms), ctypes.byref(n), _stream(stream)))
+        return float(ms.value), int(n.value)
 
     def param_grad(self, params: torch.Tensor, targets: dict, w=(1.0, 1.0, 1.0), loss: int = LOSS_SQ,
                    stream=None):

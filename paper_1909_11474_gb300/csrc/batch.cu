@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "batch_kernel.cuh"
 
@@ -18,6 +19,8 @@ size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster)
 
 int batch_param_tile() { return kPT; }
 
+static int precision_of(const BatchPlan &plan) { return plan.precision; }
+
 int batch_max_smem_optin() {
   int dev = 0, v = 0;
   cudaGetDevice(&dev);
@@ -26,24 +29,33 @@ int batch_max_smem_optin() {
 }
 
 template <int MMAX, bool CLUSTER, int MINB, typename R>
-static cudaError_t launch_variant(BatchParams bp, int nconf, int cluster, size_t smem, bool uniform, bool pdl,
-                                  cudaStream_t s) {
+static cudaError_t launch_variant(BatchParams bp, const Bucket &b, bool pdl, cudaStream_t s) {
   auto kern = batch_kernel<kPT, MMAX, CLUSTER, MINB, R>;
+  const size_t smem = b.smem;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int ncta = CLUSTER ? cluster : 1;
+  const int cluster = CLUSTER ? b.cluster : 1, ncta = cluster;
   // resident CTAs of this variant, rounded down to whole clusters
-  int dev = 0, nsm = 0, per_sm = 0;
+  int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
-  if (e != cudaSuccess) return e;
-  const int slots = std::max(1, per_sm * nsm / ncta);
+  if (b.per_sm == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b.per_sm, kern, kThreads, smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int slots = std::max(1, b.per_sm * nsm / ncta);
+  const int nconf = b.nitems;
   // work items: whole configurations when they are all alike and fit in one wave of CTAs (the
   // geometry is then staged once per configuration); otherwise each configuration's tiles are split
-  // into chunks so that about four items per CTA slot balance the dynamically claimed work
+  // into chunks so that about four items per CTA slot balance the dynamically claimed work; the
+  // autotuner's choice for this (P, mode) overrides both
   int per_conf = 1;
-  if (!(uniform && nconf <= slots)) per_conf = std::min(bp.ntiles, std::max(1, (4 * slots + nconf - 1) / nconf));
+  if (!(b.uniform && nconf <= slots)) per_conf = std::min(bp.ntiles, std::max(1, (4 * slots + nconf - 1) / nconf));
+  bp.narrow = 1;
+  if (b.tune_P == bp.P && b.tune_mode == bp.mode && b.tune_per_conf > 0) {
+    per_conf = std::min(bp.ntiles, b.tune_per_conf);
+    bp.narrow = b.tune_narrow;
+  }
   bp.nconf = nconf;
   bp.chunk_tiles = (bp.ntiles + per_conf - 1) / per_conf;
   bp.nchunks = (bp.ntiles + bp.chunk_tiles - 1) / bp.chunk_tiles;
@@ -82,17 +94,17 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   const bool f64 = plan.precision == 64;
   // per-call preparation: per-parameter-set constants and the target forces in the working precision
   {
-    const int64_t n = std::max<int64_t>(std::max<int64_t>(P, ctx.C), out.tF ? ctx.Ntot : 0);
+    const int64_t n = std::max<int64_t>(P, ctx.C);
     const unsigned blocks = (unsigned)((n + 255) / 256);
     const bool tew = mode == kModeFitness && out.tEW;
     if (f64)
       prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts),
-                                                 ctx.Ntot, out.tF, reinterpret_cast<dvec4 *>(out.tF4), ctx.C,
+                                                 ctx.Ntot, nullptr, nullptr, ctx.C,
                                                  ctx.atom_off.as<int>(), out.tE, out.tW, out.tmask,
                                                  tew ? reinterpret_cast<double *>(out.tEW) : nullptr, out.dpart);
     else
       prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts),
-                                                ctx.Ntot, out.tF, reinterpret_cast<float4 *>(out.tF4), ctx.C,
+                                                ctx.Ntot, nullptr, nullptr, ctx.C,
                                                 ctx.atom_off.as<int>(), out.tE, out.tW, out.tmask,
                                                 tew ? reinterpret_cast<float *>(out.tEW) : nullptr, out.dpart);
     cudaError_t e = launched(1);
@@ -117,7 +129,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.W = out.W;
   bp.tE = out.tE;
   bp.tW = out.tW;
-  bp.tF4 = out.tF4;
+  bp.tF = out.tF;
   bp.tmask = out.tmask;
   bp.tEW = out.tEW;
   bp.part = out.part;
@@ -134,14 +146,14 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
     cudaError_t e = cudaSuccess;
     const bool cl = b.cluster > 1;
     if (!f64) {
-      if (!cl && b.mmax <= 4) e = launch_variant<4, false, 2, float>(bp, b.nitems, 1, b.smem, b.uniform, out.pdl, s);
-      else if (!cl && b.mmax <= 6) e = launch_variant<6, false, 1, float>(bp, b.nitems, 1, b.smem, b.uniform, out.pdl, s);
-      else if (!cl) e = launch_variant<8, false, 1, float>(bp, b.nitems, 1, b.smem, b.uniform, out.pdl, s);
-      else if (b.mmax <= 6) e = launch_variant<6, true, 1, float>(bp, b.nitems, b.cluster, b.smem, b.uniform, out.pdl, s);
-      else e = launch_variant<8, true, 1, float>(bp, b.nitems, b.cluster, b.smem, b.uniform, out.pdl, s);
+      if (!cl && b.mmax <= 4) e = launch_variant<4, false, 2, float>(bp, b, out.pdl, s);
+      else if (!cl && b.mmax <= 6) e = launch_variant<6, false, 1, float>(bp, b, out.pdl, s);
+      else if (!cl) e = launch_variant<8, false, 1, float>(bp, b, out.pdl, s);
+      else if (b.mmax <= 6) e = launch_variant<6, true, 1, float>(bp, b, out.pdl, s);
+      else e = launch_variant<8, true, 1, float>(bp, b, out.pdl, s);
     } else {
-      if (!cl) e = launch_variant<8, false, 1, double>(bp, b.nitems, 1, b.smem, b.uniform, out.pdl, s);
-      else e = launch_variant<8, true, 1, double>(bp, b.nitems, b.cluster, b.smem, b.uniform, out.pdl, s);
+      if (!cl) e = launch_variant<8, false, 1, double>(bp, b, out.pdl, s);
+      else e = launch_variant<8, true, 1, double>(bp, b, out.pdl, s);
     }
     if (e != cudaSuccess) return e;
   }
@@ -149,42 +161,116 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   return cudaSuccess;
 }
 
+// Autotuner of the batched launch: for each bucket in turn, times every candidate schedule (work
+// items per configuration, and 2-or-4-atoms-per-warp last tiles on or off where the variant has
+// them) over whole launches with CUDA events on `s`, keeps the fastest, and leaves the choices in the
+// plan for this (P, mode). Synchronises `s`.
+cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params, int P, int mode,
+                           const BatchOut &out, int reps, cudaStream_t s, float *best_ms, int *tried) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const bool timer_on = ctx.timer.on;
+  ctx.timer.on = false;   // the tuner's launches are not measurements
+  auto time_launch = [&](float &best) -> cudaError_t {
+    best = 3.4e38f;
+    for (int r = 0; r < reps + 1; ++r) {   // the first launch warms up
+      cudaError_t er = cudaEventRecord(e0, s);
+      if (er == cudaSuccess) er = launch_batch(ctx, plan, params, P, mode, out, s);
+      if (er == cudaSuccess) er = cudaEventRecord(e1, s);
+      if (er == cudaSuccess) er = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (er == cudaSuccess) er = cudaEventElapsedTime(&ms, e0, e1);
+      if (er != cudaSuccess) return er;
+      if (r > 0) best = std::min(best, ms);
+    }
+    return cudaSuccess;
+  };
+  const int ntiles = (P + kPT - 1) / kPT;
+  int count = 0;
+  float best = 0.f;
+  for (size_t bi = 0; e == cudaSuccess && bi < plan.buckets.size(); ++bi) {
+    Bucket &b = plan.buckets[bi];
+    if (b.nitems == 0) continue;
+    std::vector<int> cands;
+    for (int v : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
+      if (v <= ntiles) cands.push_back(v);
+    if (cands.empty() || cands.back() != ntiles) cands.push_back(ntiles);
+    const bool narrow_capable = precision_of(plan) == 32 && b.cluster == 1 && b.mmax <= 4 && P % kPT != 0 &&
+                                P % kPT <= 16;
+    b.tune_P = P;
+    b.tune_mode = mode;
+    int best_pc = 0, best_nw = 1;
+    float bt = 3.4e38f;
+    for (int pc : cands)
+      for (int nw = 1; nw >= (narrow_capable ? 0 : 1) && e == cudaSuccess; --nw) {
+        b.tune_per_conf = pc;
+        b.tune_narrow = nw;
+        float t = 0.f;
+        e = time_launch(t);
+        ++count;
+        if (e == cudaSuccess && t < bt) {
+          bt = t;
+          best_pc = pc;
+          best_nw = nw;
+        }
+      }
+    b.tune_per_conf = best_pc;
+    b.tune_narrow = best_nw;
+  }
+  if (e == cudaSuccess) e = time_launch(best);
+  ctx.timer.on = timer_on;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (best_ms) *best_ms = best;
+  if (tried) *tried = count;
+  return e;
+}
+
 // Fitness of every parameter set from the per-(p, c) residual terms of the batched kernel
 // (Eq. 15-19): S_q[p] = sum_c part[p][c][q] and D_q = sum_c dpart[c][q], both in FP64 in a fixed
 // order (lanes strided over c, then a fixed xor-shuffle tree). Zq = sqrt(S_q/D_q) (0 where D_q = 0),
-// Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not finite. One warp per parameter set.
-constexpr int kFinWarps = 8;
+// Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not finite. One warp per parameter
+// set; small blocks spread the FP64 work over many SMs, and each block's first warp sums D_q once.
+constexpr int kFinWarps = 2;
 
-template <typename R>
 __global__ void __launch_bounds__(kFinWarps * 32) fitness_finalize_kernel(
-    int P, int C, const R *__restrict__ part, const double *__restrict__ dpart, double we, double wv, double wf,
-    double *__restrict__ Z, double *__restrict__ Zq, double *__restrict__ S) {
-  pdl_wait();   // launched while the batched kernel may still run: wait for its results
-  const int p = blockIdx.x * kFinWarps + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (p >= P) return;
-  double s[3] = {0.0, 0.0, 0.0}, d[3] = {0.0, 0.0, 0.0};
-  const R *pp = part + (size_t)p * C * 3;
-  for (int c = lane; c < C; c += 32) {
+    int P, int C, const double *__restrict__ part, const double *__restrict__ dpart, double we, double wv,
+    double wf, double *__restrict__ Z, double *__restrict__ Zq, double *__restrict__ S) {
+  __shared__ double s_d[3];
+  pdl_wait();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    double d[3] = {0.0, 0.0, 0.0};
+#pragma unroll 4
+    for (int c = lane; c < C; c += 32)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) d[q] += dpart[3 * c + q];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      s[q] += (double)pp[3 * c + q];
-      d[q] += dpart[3 * c + q];
+      for (int off = 16; off > 0; off >>= 1) d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
+      if (lane == 0) s_d[q] = d[q];
     }
   }
+  __syncthreads();
+  const int p = blockIdx.x * kFinWarps + warp;
+  if (p >= P) return;
+  double s[3] = {0.0, 0.0, 0.0};
+  const double *pp = part + (size_t)p * C * 3;
+#pragma unroll 4
+  for (int c = lane; c < C; c += 32)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s[q] += pp[3 * c + q];
 #pragma unroll
   for (int q = 0; q < 3; ++q)
-    for (int off = 16; off > 0; off >>= 1) {
-      s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-      d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
-    }
+    for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
   if (lane == 0) {
     const double wq[3] = {we, wv, wf};
     double z = 0.0, zq[3];
     bool finite = true;
     for (int q = 0; q < 3; ++q) {
       finite = finite && isfinite(s[q]);
-      zq[q] = d[q] > 0.0 ? sqrt(s[q] / d[q]) : 0.0;
+      zq[q] = s_d[q] > 0.0 ? sqrt(s[q] / s_d[q]) : 0.0;
       z += wq[q] * zq[q];
     }
     Z[p] = finite ? z : INFINITY;
@@ -195,7 +281,7 @@ __global__ void __launch_bounds__(kFinWarps * 32) fitness_finalize_kernel(
   }
 }
 
-cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *part, const double *dpart,
+cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
                                     double we, double wv, double wf, double *Z, double *Zq, double *S, bool pdl,
                                     cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
@@ -209,13 +295,7 @@ cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *par
   attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e;
-  if (precision == 64)
-    e = cudaLaunchKernelEx(&cfg, fitness_finalize_kernel<double>, P, C, static_cast<const double *>(part), dpart, we,
-                           wv, wf, Z, Zq, S);
-  else
-    e = cudaLaunchKernelEx(&cfg, fitness_finalize_kernel<float>, P, C, static_cast<const float *>(part), dpart, we,
-                           wv, wf, Z, Zq, S);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, fitness_finalize_kernel, P, C, part, dpart, we, wv, wf, Z, Zq, S);
   if (e == cudaSuccess) count_launches(1);
   return e;
 }

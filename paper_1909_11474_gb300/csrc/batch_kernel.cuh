@@ -98,6 +98,14 @@ struct AtomAcc {
   R U, W[6];
 };
 
+// Row stride of the P_ij stage [bond][3][PT] (elements). With 2 or 4 atoms in a warp (PT = 16, 8) the
+// atoms' rows start m bonds apart; the padding puts the rows of consecutive 4-neighbour atoms on
+// disjoint bank groups (4 S = PT mod 32), so the stage accesses are conflict-free.
+template <int PT>
+__host__ __device__ constexpr int stage_stride() {
+  return PT == 8 ? 26 : PT == 16 ? 52 : 3 * PT;
+}
+
 // The per-atom core of passes 1 and 2: from the bond geometry (unit vectors, r, 2/r, f_C, f_C', the
 // cosines of the bond pairs; R) and the parameter constants (T: R itself, or a dual number carrying
 // parameter tangents), U = sum_j f_C (f_R - b f_A), which is twice the site energy U_i of Eq. 2,
@@ -268,7 +276,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     if (store && (EXACT || j < m)) {
-      R *st = stage + (size_t)(lb + j) * 3 * PT + pl;
+      R *st = stage + (size_t)(lb + j) * stage_stride<PT>() + pl;
       sst(&st[0], Px[j], 5);
       sst(&st[PT], Py[j], 5);
       sst(&st[2 * PT], Pz[j], 5);
@@ -354,16 +362,17 @@ struct BatchParams {
   const CtaRec *recs;
   int ntiles;                      // parameter tiles: ceil(P / PT)
   int nconf, nchunks, chunk_tiles; // work items: nconf configurations x nchunks chunks of tiles
+  int narrow;                      // run a partly filled last tile with 2 or 4 atoms per warp
   int *counter;                    // work-claiming counter of the launch, zero at launch
   int mode;
   double *E;
   void *F;
   double *W;
   const double *tE, *tW;
-  const void *tF4;                 // R4 [Ntot]: target force (x, y, z) and |F*|^2
+  const double *tF;                // [Ntot][3]: target forces (fitness)
   const uint8_t *tmask;
   const void *tEW;                 // R [C][8]: E*, W*[6], 1/N of every configuration (fitness)
-  void *part;                      // R [P][C][3]: S_e, S_v, S_f terms of every (p, c) (fitness)
+  double *part;                    // [P][C][3]: S_e, S_v, S_f terms of every (p, c) (fitness)
   double *dpart;                   // [C][3]: target-norm terms; [c][2] = sum of |F*|^2 (fitness)
   unsigned *status;
 };
@@ -513,7 +522,7 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
     const int m = at.z, lb = at.x;
     R Fx = R(0), Fy = R(0), Fz = R(0);
     for (int e = 0; e < m; ++e) {
-      const R *st = stage + (size_t)(lb + e) * 3 * PTT + pl;
+      const R *st = stage + (size_t)(lb + e) * stage_stride<PTT>() + pl;
       Fx += sld(&st[0], 13);
       Fy += sld(&st[PTT], 13);
       Fz += sld(&st[2 * PTT], 13);
@@ -536,12 +545,12 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 #endif
           continue;
         }
-        const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * 3 * PTT + pl) * sizeof(R));
+        const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * stage_stride<PTT>() + pl) * sizeof(R));
         Fx -= ld_cluster(addr, R(0));
         Fy -= ld_cluster(addr + PTT * sizeof(R), R(0));
         Fz -= ld_cluster(addr + 2 * PTT * sizeof(R), R(0));
       } else {
-        const R *sr = stage + (size_t)(rb + cb0 - B0) * 3 * PTT + pl;
+        const R *sr = stage + (size_t)(rb + cb0 - B0) * stage_stride<PTT>() + pl;
         Fx -= sld(&sr[0], 15);
         Fy -= sld(&sr[PTT], 15);
         Fz -= sld(&sr[2 * PTT], 15);
@@ -628,10 +637,10 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
         }
         if (mask & 4) sfv = q[7];
         if (!finite) se = sv = sfv = R(NAN);
-        R *o = reinterpret_cast<R *>(a.part) + ((size_t)pp * a.C + c) * 3;
-        o[0] = se;
-        o[1] = sv;
-        o[2] = sfv;
+        double *o = a.part + ((size_t)pp * a.C + c) * 3;
+        o[0] = (double)se;
+        o[1] = (double)sv;
+        o[2] = (double)sfv;
       }
     }
     if (fit && tile == 0 && tid == 0) a.dpart[3 * c + 2] = (mask & 4) ? (double)q[9] : 0.0;
@@ -725,11 +734,19 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
         }
         for (int t = tid; t < nq; t += kThreads) sst(&sC[t], gC[t], 8);
       }
-      pdl_wait();   // constants and targets of the preparation kernel (a no-op after the first item)
       for (int t = tid; t < ns; t += kThreads) {
         const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
         sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, a.outer[s0 + t]), 9);
-        if (fit) sst(&stF[t], reinterpret_cast<const R4 *>(a.tF4)[s0 + t], 10);
+        if (fit) {   // target force in the working precision and |F*|^2 (from the FP64 components)
+          const double *f = a.tF + 3 * (int64_t)(s0 + t);
+          const double fx = f[0], fy = f[1], fz = f[2];
+          R4 v;
+          v.x = (R)fx;
+          v.y = (R)fy;
+          v.z = (R)fz;
+          v.w = (R)(fx * fx + fy * fy + fz * fz);
+          sst(&stF[t], v, 10);
+        }
       }
       if constexpr (!CLUSTER) {
         // thread 0 waits (bounded) for the bulk copies; the barrier below publishes them
@@ -763,21 +780,22 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
 
     const TileEnv<R> env = {stage, sA, sB, sC, satom, stF, ns, s0, nat, c, cb0, B0, mask, fit, rank, ncta,
                              peer_stage, peer_b0};
+    pdl_wait();   // per-call constants of the preparation kernel (a no-op after the first item)
     // the last tile may hold fewer parameter sets: the FP32 single-CTA variant for up to 4 neighbours
     // runs it with 2 or 4 atoms in a warp (tiles of 16 or 8 parameter sets); other variants keep the
     // full width
     constexpr bool kNarrow = !CLUSTER && MMAX <= 4 && sizeof(R) == 4 && PT == 32;
     for (int tile = tile0; tile < tile1; ++tile) {
       const int width = min(PT, a.P - tile * PT);
-      if (kNarrow && width <= 8) tile_pass<(kNarrow ? 8 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
-      else if (kNarrow && width <= 16) tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
+      if (kNarrow && a.narrow && width <= 8) tile_pass<(kNarrow ? 8 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
+      else if (kNarrow && a.narrow && width <= 16) tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
       else tile_pass<PT, PT, MMAX, CLUSTER, R>(a, env, tile);
     }
   }
 }
 
-// Per call: FP32/FP64 constants of every parameter set, the target forces as R4 (x, y, z, |F|^2) and,
-// when tEW is given, each configuration's targets and atom count as R [C][8] (E*, W*[6], 1/N) and its
+// Per call: FP32/FP64 constants of every parameter set, when tF4 is given the target forces as R4
+// (x, y, z, |F|^2), and when tEW is given each configuration's targets and atom count as R [C][8] (E*, W*[6], 1/N) and its
 // terms of the target norms D_e and D_v of Eq. 17-18 in FP64 (dpart[c][0..1]; masked-off quantities
 // contribute 0).
 template <typename R>

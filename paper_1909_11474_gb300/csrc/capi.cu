@@ -205,6 +205,54 @@ int run_graphed(tersoff_ctx *ctx, tsf::GraphCache &g, std::vector<uint64_t> key,
 }  // namespace
 
 namespace tsf {
+// Host side of a neighbour build whose kernel is queued: wait for its counts and status (copied to
+// pinned memory by the build), report its errors, and build or keep the work schedules.
+int finish_build(tersoff_ctx *ctx) {
+  Ctx &c = ctx->c;
+  if (!c.pending) return c.built ? TERSOFF_OK : fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  c.pending = false;
+  TSF_CUDA(cudaSetDevice(c.device));
+  TSF_CUDA(cudaEventSynchronize(c.stage_event));
+  const int64_t N = c.Ntot;
+  const int C = c.C;
+  const int *h_cnt = c.hp_stage.as<int>();
+  const unsigned hst = *reinterpret_cast<const unsigned *>(h_cnt + N);
+  if (hst & TERSOFF_STATUS_NONFINITE) return fail(ctx, TERSOFF_E_NONFINITE, "non-finite positions or box%s");
+  if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "an atom has more than max_nbr neighbours%s");
+  if (hst & TERSOFF_STATUS_TIMEOUT) return fail(ctx, TERSOFF_E_TIMEOUT, "the grid barrier of the neighbour build timed out%s");
+  const bool same_counts = c.pending_same_layout && (int64_t)c.h_cnt.size() == N &&
+                           std::equal(c.h_cnt.begin(), c.h_cnt.end(), h_cnt);
+  if (!same_counts) {
+    // host copy of the CSR the device built (same prefix sums over the configurations in order)
+    c.h_cnt.assign(h_cnt, h_cnt + N);
+    c.plan32 = BatchPlan();
+    c.plan64 = BatchPlan();
+    c.h_boff.assign(N + 1, 0);
+    c.h_poff.assign(N + 1, 0);
+    c.h_cfg_maxm.assign(C, 0);
+    int maxm = 0;
+    for (int k = 0; k < C; ++k)
+      for (int i = c.h_atom_off[k]; i < c.h_atom_off[k + 1]; ++i) {
+        const int m = c.h_cnt[i];
+        c.h_boff[i + 1] = c.h_boff[i] + m;
+        c.h_poff[i + 1] = c.h_poff[i] + pair_slots(m);
+        maxm = std::max(maxm, m);
+        c.h_cfg_maxm[k] = std::max(c.h_cfg_maxm[k], m);
+      }
+    c.max_m = maxm;
+    c.Btot = c.h_boff[N];
+    c.Qtot = c.h_poff[N];
+  }
+  if (c.max_m <= 8) {
+    int rc = build_plan(ctx, 32);
+    if (rc) return rc;
+    rc = build_plan(ctx, 64);
+    if (rc) return rc;
+  }
+  c.built = true;
+  return TERSOFF_OK;
+}
+
 // FP64 geometry records, built on the first FP64 evaluation after a neighbour build (stream-ordered).
 int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s) {
   Ctx &c = ctx->c;
@@ -320,6 +368,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
                             int32_t max_nbr, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
+  if (c.pending) tsf::finish_build(ctx);   // a previous build still unchecked: settle it (errors dropped)
   const bool was_built = c.built;
   c.built = false;
   if (!cfg || !cfg->atom_off || !cfg->pos || !cfg->box) return fail(ctx, TERSOFF_E_ARG, "null configuration pointer%s");
@@ -413,55 +462,22 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   L.status = st;
   L.resident = c.build_resident;
   TSF_CUDA(tsf::launch_build_batch(L, s));
-  // one synchronisation: neighbour counts and status back to pinned host memory (the device already
-  // holds the complete build; the host needs the counts for the work schedule)
-  int *h_cnt = hp;
-  unsigned *h_st = reinterpret_cast<unsigned *>(hp + N);
-  TSF_CUDA(cudaMemcpyAsync(h_cnt, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, s));
-  TSF_CUDA(cudaMemcpyAsync(h_st, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  // neighbour counts and status go back to pinned host memory; the host reads them (and builds or
+  // keeps the work schedule) when the next call needs the build, so the caller's own work overlaps
+  // the build kernel
+  TSF_CUDA(cudaMemcpyAsync(hp, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, s));
+  TSF_CUDA(cudaMemcpyAsync(hp + N, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   TSF_CUDA(cudaEventRecord(c.stage_event, s));
-  TSF_CUDA(cudaStreamSynchronize(s));
-  const unsigned hst = *h_st;
-  if (hst & TERSOFF_STATUS_NONFINITE) return fail(ctx, TERSOFF_E_NONFINITE, "non-finite positions or box%s");
-  if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "an atom has more than max_nbr neighbours%s");
-  if (hst & TERSOFF_STATUS_TIMEOUT) return fail(ctx, TERSOFF_E_TIMEOUT, "the grid barrier of the neighbour build timed out%s");
-  const bool same_counts = same_layout && (int64_t)c.h_cnt.size() == N && std::equal(c.h_cnt.begin(), c.h_cnt.end(), h_cnt);
-  if (!same_counts) {
-    // host copy of the CSR the device built (same prefix sums over the configurations in order)
-    c.h_cnt.assign(h_cnt, h_cnt + N);
-    c.plan32 = tsf::BatchPlan();
-    c.plan64 = tsf::BatchPlan();
-    c.h_boff.assign(N + 1, 0);
-    c.h_poff.assign(N + 1, 0);
-    c.h_cfg_maxm.assign(C, 0);
-    int maxm = 0;
-    for (int k = 0; k < C; ++k)
-      for (int i = c.h_atom_off[k]; i < c.h_atom_off[k + 1]; ++i) {
-        const int m = c.h_cnt[i];
-        c.h_boff[i + 1] = c.h_boff[i] + m;
-        c.h_poff[i + 1] = c.h_poff[i] + tsf::pair_slots(m);
-        maxm = std::max(maxm, m);
-        c.h_cfg_maxm[k] = std::max(c.h_cfg_maxm[k], m);
-      }
-    c.max_m = maxm;
-    c.Btot = c.h_boff[N];
-    c.Qtot = c.h_poff[N];
-  }
   c.geom64 = false;
-  if (c.max_m <= 8) {
-    int rc = build_plan(ctx, 32);
-    if (rc) return rc;
-    rc = build_plan(ctx, 64);
-    if (rc) return rc;
-  }
-  c.built = true;
+  c.pending = true;
+  c.pending_same_layout = same_layout;
   return TERSOFF_OK;
 }
 
 int tersoff_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
-  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "no neighbour build%s");
+  if (int rc = tsf::finish_build(ctx)) return rc;
   cudaSetDevice(c.device);
   const int64_t N = c.Ntot, M = c.M;
   if (cnt) TSF_CUDA(cudaMemcpy(cnt, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost));
@@ -478,8 +494,9 @@ int tersoff_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_
   return TERSOFF_OK;
 }
 
-int tersoff_build_info(const tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t *max_m) {
-  if (!ctx || !ctx->c.built) return TERSOFF_E_STATE;
+int tersoff_build_info(tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t *max_m) {
+  if (!ctx) return TERSOFF_E_ARG;
+  if (int rc = tsf::finish_build(ctx)) return rc;
   if (ntot) *ntot = ctx->c.Ntot;
   if (nbonds) *nbonds = ctx->c.Btot;
   if (max_m) *max_m = ctx->c.max_m;
@@ -490,7 +507,7 @@ int tersoff_eval(tersoff_ctx *ctx, const double *params, int32_t P, int32_t prec
                  void *F, double *W, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
-  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1) return fail(ctx, TERSOFF_E_ARG, "need params and P >= 1%s");
   if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
   if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
@@ -515,7 +532,7 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
                     tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
-  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !tg || !w || !Z) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
   if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
   if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
@@ -528,18 +545,16 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
   TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
-  TSF_CUDA(c.tf4.ensure((size_t)c.Ntot * sizeof(tsf::dvec4)));
   TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
   o.counters = c.counters.as<int>();
   o.consts = c.work.p;
-  o.tF4 = c.tf4.p;
   o.tEW = c.tew.p;
   o.tE = tg->E;
   o.tW = tg->W;
   o.tF = tg->F;
   o.tmask = tg->mask;
-  o.part = c.part.p;
+  o.part = c.part.as<double>();
   o.dpart = c.dpart.as<double>();
   o.pdl = c.pdl;
   const tsf::BatchPlan &plan = precision == 64 ? c.plan64 : c.plan32;
@@ -553,16 +568,56 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
   return run_graphed(ctx, c.g_fitness, std::move(key), S(stream), [&](cudaStream_t s) {
     cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
     if (e == cudaSuccess)
-      e = tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, w0, w1, w2, Z, Zq, Sq, o.pdl, s);
+      e = tsf::launch_fitness_finalize(P, c.C, o.part, o.dpart, w0, w1, w2, Z, Zq, Sq, o.pdl, s);
     return e;
   });
+}
+
+int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
+                     int32_t precision, int32_t reps, double *best_ms, int32_t *tried, tersoff_stream stream) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (int rc = tsf::finish_build(ctx)) return rc;
+  if (!params || P < 1 || !tg) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
+  if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
+  if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
+  if (reps < 1 || reps > 100) return fail(ctx, TERSOFF_E_ARG, "reps must be in [1, 100]%s");
+  if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
+  cudaSetDevice(c.device);
+  int rc = build_plan(ctx, precision);
+  if (rc) return rc;
+  if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
+  TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
+  TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
+  TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
+  tsf::BatchOut o = {};
+  o.counters = c.counters.as<int>();
+  o.consts = c.work.p;
+  o.tEW = c.tew.p;
+  o.tE = tg->E;
+  o.tW = tg->W;
+  o.tF = tg->F;
+  o.tmask = tg->mask;
+  o.part = c.part.as<double>();
+  o.dpart = c.dpart.as<double>();
+  o.pdl = c.pdl;
+  tsf::BatchPlan &plan = precision == 64 ? c.plan64 : c.plan32;
+  float ms = 0.f;
+  int n = 0;
+  TSF_CUDA(tsf::autotune_batch(c, plan, params, P, tsf::kModeFitness, o, reps, S(stream), &ms, &n));
+  plan.gen = ++tsf::g_plan_gen;   // captured launch sequences of the old schedule are stale
+  if (best_ms) *best_ms = ms;
+  if (tried) *tried = n;
+  return TERSOFF_OK;
 }
 
 int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
                        const double *w, int32_t loss, double *L, double *dL, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
-  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !tg || !w || !L || !dL) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
   if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
   if (loss != TERSOFF_LOSS_SQ && loss != TERSOFF_LOSS_Z) return fail(ctx, TERSOFF_E_ARG, "unknown loss%s");
@@ -585,7 +640,7 @@ int tersoff_eval_plain(tersoff_ctx *ctx, const double *params, int32_t P, double
                        double *W, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
-  if (!c.built) return fail(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first%s");
+  if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !E || !F || !W) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
   if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
   cudaSetDevice(c.device);

@@ -112,6 +112,10 @@ struct Bucket {
   bool uniform;    // every configuration of the bucket has the same atom and bond counts
   int nitems;      // configurations in the bucket
   int item_off;    // first record of the bucket (records are per configuration and cluster rank)
+  mutable int per_sm = 0;   // resident CTAs per SM of the bucket's kernel variant (0: not queried yet)
+  // schedule chosen by the autotuner for one (P, mode): work items per configuration and whether the
+  // last, partly filled parameter tile runs 2 or 4 atoms per warp; otherwise the built-in heuristic
+  int tune_P = 0, tune_mode = -1, tune_per_conf = 0, tune_narrow = 1;
 };
 
 // Start/stop event pairs recorded around the launches of one kernel family while enabled; read and
@@ -161,6 +165,8 @@ struct Ctx {
 
   // --- batch build state ---
   bool built = false;
+  bool pending = false;               // a build is queued whose counts the host has not checked yet
+  bool pending_same_layout = false;   // that build has the previous build's layout
   bool geom64 = false;   // FP64 geometry records built for the current neighbour build
   int C = 0;
   int64_t Ntot = 0, Btot = 0, Qtot = 0;
@@ -227,21 +233,23 @@ struct BatchOut {
   double *W;          // [P][C][6]
   const double *tE, *tW, *tF;
   const uint8_t *tmask;
-  void *part;         // workspace: [P][C][3] residual sums per (p, c) (working precision)
+  double *part;       // workspace: [P][C][3] residual terms per (p, c), formed in the working precision
   double *dpart;      // workspace: [C][3] per-configuration terms of the target norms D_q (FP64)
   void *tEW;          // workspace: [C][8] E*, W*[6], 1/N per configuration (working precision)
   void *consts;       // workspace: [P][8] per-parameter-set constants (working precision)
-  void *tF4;          // workspace: [Ntot] target forces as 4-vectors (working precision)
   int *counters;      // workspace: one work counter per launch bucket
   bool pdl = false;   // launch the batched kernels with programmatic stream serialization
 };
 enum BatchMode { kModeEval = 0, kModeFitness = 1 };
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s);
-cudaError_t launch_fitness_finalize(int precision, int P, int C, const void *part, const double *dpart,
+cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params, int P, int mode,
+                           const BatchOut &out, int reps, cudaStream_t s, float *best_ms, int *tried);
+cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
                                     double we, double wv, double wf, double *Z, double *Zq, double *S, bool pdl,
                                     cudaStream_t s);
-// capi.cu: FP64 geometry records on demand
+// capi.cu: host side of a queued neighbour build; FP64 geometry records on demand
+int finish_build(tersoff_ctx *ctx);
 int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s);
 
 // md.cu

@@ -1,7 +1,7 @@
 // noalloc.cu -- tersoff_fitness_static: the fitness call of tersoff_fitness with no device
-// allocation at call time. Its per-call scratch (per-parameter-set constants, targets in the working
-// precision, the per-(parameter set, configuration) residual terms and the per-configuration target
-// force norms) lives in one file-scope __device__ array of fixed size instead of context buffers that
+// allocation at call time. Its per-call scratch (per-parameter-set constants, per-configuration targets
+// in the working precision, the per-(parameter set, configuration) residual terms and the
+// per-configuration target-norm terms) lives in one file-scope __device__ array of fixed size instead of context buffers that
 // grow on demand.
 #include <cuda_runtime.h>
 
@@ -36,7 +36,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
                                       double *Z, double *Zq, double *S, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   tsf::Ctx &c = ctx->c;
-  if (!c.built) return set_error(ctx, TERSOFF_E_STATE, "call tersoff_build_neighbors first");
+  if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !tg || !w || !Z) return set_error(ctx, TERSOFF_E_ARG, "null argument or P < 1");
   if (!tg->E || !tg->W || !tg->F || !tg->mask) return set_error(ctx, TERSOFF_E_ARG, "null target pointer");
   if (precision != 32 && precision != 64) return set_error(ctx, TERSOFF_E_ARG, "precision must be 32 or 64");
@@ -47,16 +47,15 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
 
   // scratch layout, each part 256-byte aligned
   const size_t b_consts = align256((size_t)P * 8 * sizeof(double));
-  const size_t b_tf4 = align256((size_t)c.Ntot * sizeof(tsf::dvec4));
   const size_t b_part = align256((size_t)P * c.C * 3 * sizeof(double));
   const size_t b_dpart = align256((size_t)c.C * 3 * sizeof(double));
   const size_t b_tew = align256((size_t)c.C * 8 * sizeof(double));
   const size_t b_count = align256(64 * sizeof(int));
-  const size_t need = b_consts + b_tf4 + b_part + b_dpart + b_tew + b_count;
+  const size_t need = b_consts + b_part + b_dpart + b_tew + b_count;
   if (need > kScratchBytes) {
     char buf[200];
-    std::snprintf(buf, sizeof(buf), "tersoff_fitness_static needs %zu bytes of scratch for P=%d, C=%d, Ntot=%lld; "
-                  "the static limit is %zu", need, (int)P, c.C, (long long)c.Ntot, kScratchBytes);
+    std::snprintf(buf, sizeof(buf), "tersoff_fitness_static needs %zu bytes of scratch for P=%d, C=%d; "
+                  "the static limit is %zu", need, (int)P, c.C, kScratchBytes);
     return set_error(ctx, TERSOFF_E_ARG, buf);
   }
 
@@ -86,11 +85,10 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   o.tF = tg->F;
   o.tmask = tg->mask;
   o.consts = base;
-  o.tF4 = base + b_consts;
-  o.part = base + b_consts + b_tf4;
-  o.dpart = reinterpret_cast<double *>(base + b_consts + b_tf4 + b_part);
-  o.tEW = base + b_consts + b_tf4 + b_part + b_dpart;
-  o.counters = reinterpret_cast<int *>(base + b_consts + b_tf4 + b_part + b_dpart + b_tew);
+  o.part = reinterpret_cast<double *>(base + b_consts);
+  o.dpart = reinterpret_cast<double *>(base + b_consts + b_part);
+  o.tEW = base + b_consts + b_part + b_dpart;
+  o.counters = reinterpret_cast<int *>(base + b_consts + b_part + b_dpart + b_tew);
   o.pdl = c.pdl;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (precision == 64) {
@@ -99,7 +97,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   }
   cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
   if (e == cudaSuccess)
-    e = tsf::launch_fitness_finalize(precision, P, c.C, o.part, o.dpart, w[0], w[1], w[2], Z, Zq, S, o.pdl, s);
+    e = tsf::launch_fitness_finalize(P, c.C, o.part, o.dpart, w[0], w[1], w[2], Z, Zq, S, o.pdl, s);
   if (e != cudaSuccess) {
     char buf[160];
     std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));

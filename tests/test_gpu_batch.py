@@ -247,3 +247,47 @@ def test_fitness_graph_replay_matches_direct_launches(ctx):
     assert np.array_equal(run(False, t3, (1, 1, 1)), run(True, t3, (1, 1, 1)))
     ctx.set_launch_mode()
     assert ctx.get_status() == 0
+
+
+def test_build_errors_reported_by_next_call(ctx):
+    """The neighbour build is queued and checked by the next call that uses it: a list overflow and
+    non-finite positions come back from that call, and a valid rebuild afterwards works."""
+    from paper_1909_11474_gb300 import binding
+    cs = I.workload_single_cell()["configs"]
+    params = torch.tensor(I.TABLE2_PARAMS[None, :], device="cuda")
+    _build(ctx, cs, M=2)                      # diamond has 4 neighbours per atom
+    with pytest.raises(binding.TersoffError) as ei:
+        ctx.eval(params)
+    assert ei.value.code == binding.E_NBR_OVERFLOW
+    pos, box = to_device(cs)
+    pos[5, 1] = float("nan")
+    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+    with pytest.raises(binding.TersoffError) as ei:
+        ctx.build_info()
+    assert ei.value.code == binding.E_NONFINITE
+    ctx.get_status()                           # clear the status bits of the failed builds
+    _build(ctx, cs)
+    E, F, W = ctx.eval(params, precision=64)
+    r = oracle.evaluate(*cs.config(0), I.TABLE2_PARAMS)
+    assert abs(float(E[0, 0]) - r["E"]) < 1e-9 * abs(r["E"])
+    assert ctx.get_status() == 0
+
+
+def test_autotune_keeps_results_within_the_bars(ctx):
+    """The schedule autotuner times its candidates, keeps the fastest, and the tuned fitness still
+    meets the oracle bounds (a partly filled last tile here: P = 45 = 32 + 13)."""
+    w = I.workload_ga_batch(P=45, C=5)
+    cs = w["configs"]
+    Eh, Wh, Fh = oracle.evaluate_batch(cs, w["hidden"][None, :])
+    t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0])
+    E, W, F, ES, WS = oracle.evaluate_batch(cs, w["params"], scales=True)
+    ref = oracle.fitness_from_predictions(cs, t, E, W, F)
+    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32)
+    _build(ctx, cs)
+    params, tg = torch.tensor(w["params"], device="cuda"), targets_to_device(t)
+    ms, tried = ctx.autotune(params, tg, reps=2)
+    assert ms > 0.0 and tried >= 4             # chunkings 1, 2 x narrow last tile on / off
+    Z, Zq, S = ctx.fitness(params, tg)
+    S = S.cpu().numpy()
+    assert (np.abs(np.sqrt(S) - np.sqrt(ref["S"])) <= B).all()
+    assert ctx.get_status() == 0
