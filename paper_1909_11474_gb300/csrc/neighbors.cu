@@ -247,14 +247,18 @@ __device__ __forceinline__ void grid_barrier(unsigned *ctr, unsigned *status) {
   __syncthreads();
 }
 
-// Box constants of one configuration for the FP32 membership test (computed by one thread):
-// Hinv, the image search range R2/gap (+ margin), H and the decision band. `band` bounds the FP32
-// error of the squared distance: with X the largest coordinate magnitude of the configuration, |H|
-// its largest box entry and nmax the largest image index a candidate can have, each FP32 component
-// of d = (x_j - x_i) + n.H is within delta = 2^-23 (4X + 6 nmax |H|) of the exact value, so
-// |r^2 - r32^2| < 3.5 R2 delta + 12 2^-24 R2^2; the band is four times that. Returns false for a
-// singular or non-finite box.
-__device__ bool box_constants(const double *H, float xm, double R2, Pre32 &q, int &nmax_out) {
+// Box constants of one configuration for the FP32 membership test: Hinv, the image search range
+// R2/gap (+ margin), H and the decision band. `band` bounds the FP32 error of the squared distance:
+// with X the largest coordinate magnitude of the configuration, |H| its largest box entry and nmax the
+// largest image index a candidate can have, each FP32 component of d = (x_j - x_i) + n.H is within
+// delta = 2^-23 (4X + 6 nmax |H|) of the exact value, so |r^2 - r32^2| < 3.5 R2 delta + 12 2^-24 R2^2;
+// the band is four times that. Computed by one thread in two parts: box_part1 from the box alone
+// (while the other threads load the positions), box_part2 once X is known.
+struct BoxPart1 {
+  double Hinv[9], rgap[3], col[3], Hm;   // rgap = R2 / gap per axis; col = column sums of |Hinv|
+  int ok;                                // box finite and non-singular
+};
+__device__ void box_part1(const double *H, double R2, BoxPart1 &o) {
   const double a0 = H[0], a1 = H[1], a2 = H[2], b0 = H[3], b1 = H[4], b2 = H[5], c0 = H[6], c1 = H[7],
                c2 = H[8];
   const double bxc0 = b1 * c2 - b2 * c1, bxc1 = b2 * c0 - b0 * c2, bxc2 = b0 * c1 - b1 * c0;
@@ -263,28 +267,36 @@ __device__ bool box_constants(const double *H, float xm, double R2, Pre32 &q, in
   const double det = a0 * bxc0 + a1 * bxc1 + a2 * bxc2;
   bool ok = isfinite(det) && det != 0.0;
   for (int k = 0; k < 9; ++k) ok = ok && isfinite(H[k]);
-  if (!ok) return false;
+  o.ok = ok ? 1 : 0;
+  if (!ok) return;
   const double id = 1.0 / det;
   // H^-1 columns are (b x c, c x a, a x b) / det, i.e. Hinv[mu][k] = cross_k[mu] / det
-  const double o[9] = {bxc0 * id, cxa0 * id, axb0 * id, bxc1 * id, cxa1 * id, axb1 * id,
+  const double h[9] = {bxc0 * id, cxa0 * id, axb0 * id, bxc1 * id, cxa1 * id, axb1 * id,
                        bxc2 * id, cxa2 * id, axb2 * id};
+  for (int k = 0; k < 9; ++k) o.Hinv[k] = h[k];
   const double vol = fabs(det);
   const double gap[3] = {vol / sqrt(bxc0 * bxc0 + bxc1 * bxc1 + bxc2 * bxc2),
                          vol / sqrt(cxa0 * cxa0 + cxa1 * cxa1 + cxa2 * cxa2),
                          vol / sqrt(axb0 * axb0 + axb1 * axb1 + axb2 * axb2)};
-  // largest coordinate magnitude (from the FP32 copies: widened by 2^-22 for their rounding)
-  const double X = (double)xm * (1.0 + ldexp(1.0, -22));
+  for (int k = 0; k < 3; ++k) {
+    o.rgap[k] = R2 / gap[k];
+    o.col[k] = fabs(h[k]) + fabs(h[3 + k]) + fabs(h[6 + k]);
+  }
   double Hm = 0.0;
   for (int k = 0; k < 9; ++k) Hm = fmax(Hm, fabs(H[k]));
+  o.Hm = Hm;
+}
+// Returns false for a bad box or an image range beyond the shift encoding.
+__device__ bool box_part2(const BoxPart1 &o, const double *H, float xm, double R2, Pre32 &q, int &nmax_out) {
+  if (!o.ok) return false;
+  // largest coordinate magnitude (from the FP32 copies: widened by 2^-22 for their rounding)
+  const double X = (double)xm * (1.0 + ldexp(1.0, -22));
   double nmax = 0.0;
-  for (int k = 0; k < 3; ++k) {
-    const double col = fabs(o[k]) + fabs(o[3 + k]) + fabs(o[6 + k]);
-    nmax = fmax(nmax, ceil(2.0 * X * col + R2 / gap[k] + 1.0));
-  }
-  const double delta = ldexp(4.0 * X + 6.0 * nmax * Hm, -23);
+  for (int k = 0; k < 3; ++k) nmax = fmax(nmax, ceil(2.0 * X * o.col[k] + o.rgap[k] + 1.0));
+  const double delta = ldexp(4.0 * X + 6.0 * nmax * o.Hm, -23);
   const double band = 4.0 * (3.5 * R2 * delta + 12.0 * ldexp(R2 * R2, -24));
-  for (int k = 0; k < 9; ++k) q.Hi[k] = (float)o[k];
-  for (int k = 0; k < 3; ++k) q.rng[k] = (float)(R2 / gap[k]) + 1e-4f;
+  for (int k = 0; k < 9; ++k) q.Hi[k] = (float)o.Hinv[k];
+  for (int k = 0; k < 3; ++k) q.rng[k] = (float)o.rgap[k] + 1e-4f;
   for (int k = 0; k < 9; ++k) q.H[k] = (float)H[k];
   q.band = (float)band;
   q.R2sq = (float)(R2 * R2);
@@ -299,6 +311,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
   __shared__ int s_poff[kBuildMaxAtoms + 1];
   __shared__ int s_outer[kBuildMaxAtoms];
   __shared__ Pre32 s_q;
+  __shared__ BoxPart1 s_b1;
   __shared__ double s_H[9];
   __shared__ int s_ok, s_nmax;
   __shared__ long long s_red[kBuildWarps];
@@ -312,9 +325,21 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
   // ---- phase 1: positions, box constants, neighbour lists, totals
   for (int c = c_begin; c < c_end; ++c) {
     const int a0 = a.atom_off[c], nat = a.atom_off[c + 1] - a0;
+    // the last warp's first thread works out the box-only constants while the other warps load
+    // the positions
+    constexpr int kLoadThreads = kBuildThreads - 32;
+    if (tid == kLoadThreads) {
+      double H[9];
+      for (int k = 0; k < 9; ++k) {
+        H[k] = a.box_in[9 * c + k];
+        s_H[k] = H[k];
+        a.box[9 * c + k] = H[k];
+      }
+      box_part1(H, a.R2, s_b1);
+    }
     float xm = 0.f;
     int finite = 1;
-    for (int t = tid; t < nat; t += kBuildThreads) {
+    for (int t = tid; tid < kLoadThreads && t < nat; t += kLoadThreads) {
       const double *x = a.pos_in + 3 * (int64_t)(a0 + t);
       const double x0 = x[0], x1 = x[1], x2 = x[2];
       double *y = a.pos + 3 * (int64_t)(a0 + t);
@@ -328,15 +353,10 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
     }
     xm = block_max_f(xm, reinterpret_cast<float *>(s_red));
     finite = __syncthreads_and(finite);
-    if (tid < 9) {
-      s_H[tid] = a.box_in[9 * c + tid];
-      a.box[9 * c + tid] = s_H[tid];
-    }
-    __syncthreads();
     if (tid == 0) {
       Pre32 q;
       int nmax = 0;
-      const bool ok = finite && box_constants(s_H, xm, a.R2, q, nmax);
+      const bool ok = finite && box_part2(s_b1, s_H, xm, a.R2, q, nmax);
       if (!ok) set_status(a.status, TERSOFF_STATUS_NONFINITE);
       s_q = q;
       s_ok = ok ? 1 : 0;
@@ -347,7 +367,11 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
     const bool ok = s_ok != 0;
     const int nmax = s_nmax;
     const double R2sq = a.R2 * a.R2;
-    // one warp per atom i, lanes over j (two passes per block of 32 j, ordered by a warp scan)
+    // one warp per atom i, lanes over j; each lane keeps up to kNbrBuf accepted images of its j in
+    // registers, so one enumeration suffices (a lane with more enumerates again for the rest); a warp
+    // scan of the per-lane counts gives the output positions, so entries land in ascending
+    // (j, n0, n1, n2) order
+    constexpr int kNbrBuf = 4;
     for (int li = warp; li < nat; li += kBuildWarps) {
       const int64_t i = a0 + li;
       const double *xi = a.pos_in + 3 * i;
@@ -373,11 +397,18 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
         const int j = a0 + (jl < nat ? jl : 0);
         const double *xj = a.pos_in + 3 * (int64_t)j;
         int mine = 0;
+        int buf[kNbrBuf];
         for (int n0 = lo0; n0 <= hi0; ++n0)
           for (int n1 = lo1; n1 <= hi1; ++n1)
             for (int n2 = lo2; n2 <= hi2; ++n2) {
               if (jl == li && n0 == 0 && n1 == 0 && n2 == 0) continue;
-              if (member(q, dx, dy, dz, n0, n1, n2, xj, xi, s_H, R2sq)) ++mine;
+              if (member(q, dx, dy, dz, n0, n1, n2, xj, xi, s_H, R2sq)) {
+                const char4 sh = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
+#pragma unroll
+                for (int u = 0; u < kNbrBuf; ++u)
+                  if (u == mine) buf[u] = *reinterpret_cast<const int *>(&sh);
+                ++mine;
+              }
             }
         int incl = mine;   // inclusive warp scan of the per-lane counts
 #pragma unroll
@@ -386,18 +417,25 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
           if (lane >= off) incl += v;
         }
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (mine) {
-          int w = count + incl - mine;
+        const int w0 = count + incl - mine;
+#pragma unroll
+        for (int u = 0; u < kNbrBuf; ++u)
+          if (u < mine && w0 + u < M) {
+            a.nbr[i * M + w0 + u] = j;
+            a.shift[i * M + w0 + u] = *reinterpret_cast<const char4 *>(&buf[u]);
+          }
+        if (mine > kNbrBuf) {   // rare (small cells): enumerate again for the entries past the buffer
+          int u = 0;
           for (int n0 = lo0; n0 <= hi0; ++n0)
             for (int n1 = lo1; n1 <= hi1; ++n1)
               for (int n2 = lo2; n2 <= hi2; ++n2) {
                 if (jl == li && n0 == 0 && n1 == 0 && n2 == 0) continue;
                 if (member(q, dx, dy, dz, n0, n1, n2, xj, xi, s_H, R2sq)) {
-                  if (w < M) {
-                    a.nbr[i * M + w] = j;
-                    a.shift[i * M + w] = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
+                  if (u >= kNbrBuf && w0 + u < M) {
+                    a.nbr[i * M + w0 + u] = j;
+                    a.shift[i * M + w0 + u] = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
                   }
-                  ++w;
+                  ++u;
                 }
               }
         }
