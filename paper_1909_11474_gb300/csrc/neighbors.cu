@@ -252,56 +252,62 @@ __device__ __forceinline__ void grid_barrier(unsigned *ctr, unsigned *status) {
 // with X the largest coordinate magnitude of the configuration, |H| its largest box entry and nmax the
 // largest image index a candidate can have, each FP32 component of d = (x_j - x_i) + n.H is within
 // delta = 2^-23 (4X + 6 nmax |H|) of the exact value, so |r^2 - r32^2| < 3.5 R2 delta + 12 2^-24 R2^2;
-// the band is four times that. Computed by one thread in two parts: box_part1 from the box alone
-// (while the other threads load the positions), box_part2 once X is known.
+// the band is four times that. Computed by one thread in FP32 (the band is a bound with a factor-4
+// margin, the image range has a 1e-4 margin, so FP32 rounding of these constants is immaterial), in
+// two parts: box_part1 from the box alone (while the other threads load the positions), box_part2
+// once X is known.
 struct BoxPart1 {
-  double Hinv[9], rgap[3], col[3], Hm;   // rgap = R2 / gap per axis; col = column sums of |Hinv|
+  float Hinv[9], rgap[3], col[3], Hm;    // rgap = R2 / gap per axis; col = column sums of |Hinv|
   int ok;                                // box finite and non-singular
 };
-__device__ void box_part1(const double *H, double R2, BoxPart1 &o) {
-  const double a0 = H[0], a1 = H[1], a2 = H[2], b0 = H[3], b1 = H[4], b2 = H[5], c0 = H[6], c1 = H[7],
-               c2 = H[8];
-  const double bxc0 = b1 * c2 - b2 * c1, bxc1 = b2 * c0 - b0 * c2, bxc2 = b0 * c1 - b1 * c0;
-  const double cxa0 = c1 * a2 - c2 * a1, cxa1 = c2 * a0 - c0 * a2, cxa2 = c0 * a1 - c1 * a0;
-  const double axb0 = a1 * b2 - a2 * b1, axb1 = a2 * b0 - a0 * b2, axb2 = a0 * b1 - a1 * b0;
-  const double det = a0 * bxc0 + a1 * bxc1 + a2 * bxc2;
-  bool ok = isfinite(det) && det != 0.0;
-  for (int k = 0; k < 9; ++k) ok = ok && isfinite(H[k]);
+__device__ void box_part1(const double *Hd, double R2, BoxPart1 &o) {
+  bool ok = true;
+  for (int k = 0; k < 9; ++k) ok = ok && isfinite(Hd[k]);
+  float H[9];
+  for (int k = 0; k < 9; ++k) H[k] = (float)Hd[k];
+  const float a0 = H[0], a1 = H[1], a2 = H[2], b0 = H[3], b1 = H[4], b2 = H[5], c0 = H[6], c1 = H[7],
+              c2 = H[8];
+  const float bxc0 = b1 * c2 - b2 * c1, bxc1 = b2 * c0 - b0 * c2, bxc2 = b0 * c1 - b1 * c0;
+  const float cxa0 = c1 * a2 - c2 * a1, cxa1 = c2 * a0 - c0 * a2, cxa2 = c0 * a1 - c1 * a0;
+  const float axb0 = a1 * b2 - a2 * b1, axb1 = a2 * b0 - a0 * b2, axb2 = a0 * b1 - a1 * b0;
+  const float det = a0 * bxc0 + a1 * bxc1 + a2 * bxc2;
+  ok = ok && isfinite(det) && det != 0.f;
   o.ok = ok ? 1 : 0;
   if (!ok) return;
-  const double id = 1.0 / det;
+  const float id = 1.f / det;
   // H^-1 columns are (b x c, c x a, a x b) / det, i.e. Hinv[mu][k] = cross_k[mu] / det
-  const double h[9] = {bxc0 * id, cxa0 * id, axb0 * id, bxc1 * id, cxa1 * id, axb1 * id,
-                       bxc2 * id, cxa2 * id, axb2 * id};
+  const float h[9] = {bxc0 * id, cxa0 * id, axb0 * id, bxc1 * id, cxa1 * id, axb1 * id,
+                      bxc2 * id, cxa2 * id, axb2 * id};
   for (int k = 0; k < 9; ++k) o.Hinv[k] = h[k];
-  const double vol = fabs(det);
-  const double gap[3] = {vol / sqrt(bxc0 * bxc0 + bxc1 * bxc1 + bxc2 * bxc2),
-                         vol / sqrt(cxa0 * cxa0 + cxa1 * cxa1 + cxa2 * cxa2),
-                         vol / sqrt(axb0 * axb0 + axb1 * axb1 + axb2 * axb2)};
+  const float vol = fabsf(det);
+  const float gap[3] = {vol / sqrtf(bxc0 * bxc0 + bxc1 * bxc1 + bxc2 * bxc2),
+                        vol / sqrtf(cxa0 * cxa0 + cxa1 * cxa1 + cxa2 * cxa2),
+                        vol / sqrtf(axb0 * axb0 + axb1 * axb1 + axb2 * axb2)};
   for (int k = 0; k < 3; ++k) {
-    o.rgap[k] = R2 / gap[k];
-    o.col[k] = fabs(h[k]) + fabs(h[3 + k]) + fabs(h[6 + k]);
+    o.rgap[k] = (float)R2 / gap[k];
+    o.col[k] = fabsf(h[k]) + fabsf(h[3 + k]) + fabsf(h[6 + k]);
   }
-  double Hm = 0.0;
-  for (int k = 0; k < 9; ++k) Hm = fmax(Hm, fabs(H[k]));
+  float Hm = 0.f;
+  for (int k = 0; k < 9; ++k) Hm = fmaxf(Hm, fabsf(H[k]));
   o.Hm = Hm;
 }
 // Returns false for a bad box or an image range beyond the shift encoding.
 __device__ bool box_part2(const BoxPart1 &o, const double *H, float xm, double R2, Pre32 &q, int &nmax_out) {
   if (!o.ok) return false;
   // largest coordinate magnitude (from the FP32 copies: widened by 2^-22 for their rounding)
-  const double X = (double)xm * (1.0 + ldexp(1.0, -22));
-  double nmax = 0.0;
-  for (int k = 0; k < 3; ++k) nmax = fmax(nmax, ceil(2.0 * X * o.col[k] + o.rgap[k] + 1.0));
-  const double delta = ldexp(4.0 * X + 6.0 * nmax * o.Hm, -23);
-  const double band = 4.0 * (3.5 * R2 * delta + 12.0 * ldexp(R2 * R2, -24));
-  for (int k = 0; k < 9; ++k) q.Hi[k] = (float)o.Hinv[k];
-  for (int k = 0; k < 3; ++k) q.rng[k] = (float)o.rgap[k] + 1e-4f;
+  const float X = xm * (1.f + 0x1p-22f);
+  float nmax = 0.f;
+  for (int k = 0; k < 3; ++k) nmax = fmaxf(nmax, ceilf(2.f * X * o.col[k] + o.rgap[k] + 1.f));
+  const float R2f = (float)R2;
+  const float delta = (4.f * X + 6.f * nmax * o.Hm) * 0x1p-23f;
+  const float band = 4.f * (3.5f * R2f * delta + 12.f * 0x1p-24f * R2f * R2f);
+  for (int k = 0; k < 9; ++k) q.Hi[k] = o.Hinv[k];
+  for (int k = 0; k < 3; ++k) q.rng[k] = o.rgap[k] + 1e-4f;
   for (int k = 0; k < 9; ++k) q.H[k] = (float)H[k];
-  q.band = (float)band;
+  q.band = band;
   q.R2sq = (float)(R2 * R2);
-  nmax_out = (int)fmin(nmax, 127.0);
-  return isfinite(band) && nmax <= 127.0;
+  nmax_out = (int)fminf(nmax, 127.f);
+  return isfinite(band) && nmax <= 127.f;
 }
 
 __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildParams a) {
