@@ -411,7 +411,12 @@ def bench_uneven(dev, flush, stream):
     t32 = _time(lambda: ctx.fitness(params, tg, precision=32), 3, flush, stream)
     t64 = _time(lambda: ctx.fitness(params, tg, precision=64), 1, flush, stream, warmup=1)
     P = len(w["params"])
+    flop, _, _, _ = flop_model(ctx, P)
+    peaks, _ = measured_peaks()
+    fp32_peak = torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * \
+        float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     return {"workload": "P=1000 x C=500 cells of 7..512 atoms", "atoms": cs.Ntot,
+            "fitness_call_roofline_frac": round(flop / t32 / fp32_peak, 4),
             "fp32": {"value": round(P * cs.Ntot / t32, 1), "unit": "atom-evals/s", "ms": round(1e3 * t32, 3),
                      "fitness_evals_per_s": round(P / t32, 1), "ms_before_autotune": round(1e3 * t_untuned, 3),
                      "autotune": {"candidates": tried, "tuned_launch_ms": round(tuned_ms, 3)}},
