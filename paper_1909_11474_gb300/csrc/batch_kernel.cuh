@@ -426,6 +426,55 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 }
 constexpr unsigned kMbarSpins = 1u << 22;   // bound of a wait for one configuration's copies
 
+// Pass 3 of one atom with a compile-time neighbour count M from a single-CTA stage: F_i = sum_j P_ij
+// over the atom's own rows minus sum_j P_ji over the rows of the reverse bonds (roff maps a
+// configuration-local bond index to a stage row).
+template <int M, int PTT, typename R>
+__device__ __forceinline__ void gather_atom(const R *__restrict__ stage, const typename Vec4<R>::T *__restrict__ sB,
+                                            int lb, int roff, int pl, R &Fx, R &Fy, R &Fz) {
+  constexpr int S = stage_stride<PTT>();
+  int rb[M];
+#pragma unroll
+  for (int e = 0; e < M; ++e) {
+    if constexpr (sizeof(R) == 4) rb[e] = __float_as_int((float)sld(&sB[lb + e].w, 14)) & 0xffff;
+    else rb[e] = (int)sld(&sB[lb + e].w, 14) & 0xffff;
+  }
+  const R *st = stage + (size_t)lb * S + pl;
+#pragma unroll
+  for (int e = 0; e < M; ++e) {
+    Fx += sld(&st[e * S], 13);
+    Fy += sld(&st[e * S + PTT], 13);
+    Fz += sld(&st[e * S + 2 * PTT], 13);
+  }
+#pragma unroll
+  for (int e = 0; e < M; ++e) {
+    const R *sr = stage + (size_t)(rb[e] + roff) * S + pl;
+    Fx -= sld(&sr[0], 15);
+    Fy -= sld(&sr[PTT], 15);
+    Fz -= sld(&sr[2 * PTT], 15);
+  }
+}
+// Dispatch on the atom's neighbour count; false when it exceeds MMAX (the caller's loop handles it).
+template <int PTT, int MMAX, typename R>
+__device__ __forceinline__ bool gather_dispatch(int m, const R *stage, const typename Vec4<R>::T *sB, int lb,
+                                                int roff, int pl, R &Fx, R &Fy, R &Fz) {
+#define TSF_GCASE(MM)                                                              \
+  case MM:                                                                         \
+    if constexpr (MMAX >= MM) {                                                    \
+      gather_atom<MM, PTT, R>(stage, sB, lb, roff, pl, Fx, Fy, Fz);                \
+      return true;                                                                 \
+    }                                                                              \
+    return false;
+  switch (m) {
+    case 0:
+      return true;
+    TSF_GCASE(1) TSF_GCASE(2) TSF_GCASE(3) TSF_GCASE(4) TSF_GCASE(5) TSF_GCASE(6) TSF_GCASE(7) TSF_GCASE(8)
+    default:
+      return false;
+  }
+#undef TSF_GCASE
+}
+
 // One parameter tile of PTT parameter sets (PTT = 32: one atom per warp; 16 or 8: 2 or 4 atoms per
 // warp, used for the last, partly filled tile) of the item staged in shared memory: passes 1-3, the
 // reductions and the per-(parameter set, configuration) outputs. `tile` counts tiles of the launch's
@@ -521,7 +570,9 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
     const int4 at = sld(&satom[li], 12);
     const int m = at.z, lb = at.x;
     R Fx = R(0), Fy = R(0), Fz = R(0);
-    for (int e = 0; e < m; ++e) {
+    bool gathered = false;
+    if constexpr (APW == 1 && !CLUSTER) gathered = gather_dispatch<PTT, MMAX, R>(m, stage, sB, lb, cb0 - B0, pl, Fx, Fy, Fz);
+    for (int e = 0; !gathered && e < m; ++e) {
       const R *st = stage + (size_t)(lb + e) * stage_stride<PTT>() + pl;
       Fx += sld(&st[0], 13);
       Fy += sld(&st[PTT], 13);
