@@ -288,7 +288,9 @@ def run_ours(args):
     achieved = flop / b_time / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(),
-                "kernel": "tsf::batch_kernel<32,4,0,2,float> (every cell of the workload has m <= 4)",
+                "kernel": "tsf::batch_kernel<{t},4,0,{m},float> (every cell of the workload has m <= 4; tile "
+                          "chosen by the autotuner)".format(t=ctx.schedule_info(32)[0]["tile"],
+                                                            m=3 if ctx.schedule_info(32)[0]["tile"] == 16 else 2),
                 "kernel_ms": round(1e3 * b_time, 4), "flop_per_launch": flop,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                f"(sm_max_mhz from MEASURED_PEAKS.json, {peak_src})",
@@ -310,7 +312,8 @@ def run_ours(args):
            "e2e": {"value": round(ws * atom_evals * args.steps / t_e2e, 1), "unit": UNIT,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
-           "autotune": {"candidates": tuned_tried, "tuned_launch_ms": round(tuned_ms, 4)}}
+           "autotune": {"candidates": tuned_tried, "tuned_launch_ms": round(tuned_ms, 4),
+                        "schedule": ctx.schedule_info(32)}}
     if not args.quick:
         out["rows"] = {
             "adjoint": bench_adjoint(ctx_dev=dev, steps=max(3, args.steps // 5), flush=flush, stream=stream),

@@ -30,6 +30,7 @@ EXPORTED = (
     "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
     "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
     "tersoff_profile", "tersoff_profile_read", "tersoff_set_launch_mode", "tersoff_autotune",
+    "tersoff_set_schedule", "tersoff_schedule_info",
 )
 
 _vp = ctypes.c_void_p
@@ -79,6 +80,8 @@ def load():
         "tersoff_kernel_launches": (ctypes.c_int64, []),
         "tersoff_profile": (ctypes.c_int, [_vp, _i32]),
         "tersoff_set_launch_mode": (ctypes.c_int, [_vp, _i32]),
+        "tersoff_set_schedule": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32]),
+        "tersoff_schedule_info": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
         "tersoff_autotune": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _i32, _i32,
                                             ctypes.POINTER(_f64), ctypes.POINTER(_i32), _vp]),
         "tersoff_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_f64)]),
@@ -282,6 +285,23 @@ class Context:
         self._check(self.lib.tersoff_autotune(self.h, params.data_ptr(), P, ctypes.byref(t), precision, reps,
                                               ctypes.byref(ms), ctypes.byref(n), _stream(stream)))
         return float(ms.value), int(n.value)
+
+    def set_schedule(self, P: int, tile: int = 32, items_per_config: int = 1, narrow: bool = True,
+                     precision: int = 32):
+        """Fix the batched fitness schedule for this P (tersoff_set_schedule)."""
+        self._check(self.lib.tersoff_set_schedule(self.h, precision, P, tile, items_per_config, 1 if narrow else 0))
+
+    def schedule_info(self, precision: int = 32):
+        """Per launch bucket: dict of mmax, cluster, configs, tuned_P, tile, items_per_config, narrow."""
+        n = np.zeros(7, np.int32)
+        self._check(self.lib.tersoff_schedule_info(self.h, precision, -1, n.ctypes.data))
+        out = []
+        for b in range(int(n[0])):
+            v = np.zeros(7, np.int32)
+            self._check(self.lib.tersoff_schedule_info(self.h, precision, b, v.ctypes.data))
+            out.append(dict(zip(("mmax", "cluster", "configs", "tuned_P", "tile", "items_per_config", "narrow"),
+                                (int(x) for x in v))))
+        return out
 
     def param_grad(self, params: torch.Tensor, targets: dict, w=(1.0, 1.0, 1.0), loss: int = LOSS_SQ,
                    stream=None):

@@ -19,6 +19,8 @@ size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster)
 
 int batch_param_tile() { return kPT; }
 
+size_t batch_smem_bytes_pt16(int nb, int nq, int nat) { return batch_smem<16, false, float>(nb, nq, nat); }
+
 static int precision_of(const BatchPlan &plan) { return plan.precision; }
 
 int batch_max_smem_optin() {
@@ -28,10 +30,12 @@ int batch_max_smem_optin() {
   return v;
 }
 
-template <int MMAX, bool CLUSTER, int MINB, typename R>
+template <int PTV, int MMAX, bool CLUSTER, int MINB, typename R>
 static cudaError_t launch_variant(BatchParams bp, const Bucket &b, bool pdl, cudaStream_t s) {
-  auto kern = batch_kernel<kPT, MMAX, CLUSTER, MINB, R>;
-  const size_t smem = b.smem;
+  auto kern = batch_kernel<PTV, MMAX, CLUSTER, MINB, R>;
+  const size_t smem = PTV == kPT ? b.smem : b.smem16;
+  int &per_sm = PTV == kPT ? b.per_sm : b.per_sm16;
+  bp.ntiles = (bp.P + PTV - 1) / PTV;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int cluster = CLUSTER ? b.cluster : 1, ncta = cluster;
@@ -39,11 +43,11 @@ static cudaError_t launch_variant(BatchParams bp, const Bucket &b, bool pdl, cud
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (b.per_sm == 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b.per_sm, kern, kThreads, smem);
+  if (per_sm == 0) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
   }
-  const int slots = std::max(1, b.per_sm * nsm / ncta);
+  const int slots = std::max(1, per_sm * nsm / ncta);
   const int nconf = b.nitems;
   // work items: whole configurations when they are all alike and fit in one wave of CTAs (the
   // geometry is then staged once per configuration); otherwise each configuration's tiles are split
@@ -146,14 +150,17 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
     cudaError_t e = cudaSuccess;
     const bool cl = b.cluster > 1;
     if (!f64) {
-      if (!cl && b.mmax <= 4) e = launch_variant<4, false, 2, float>(bp, b, out.pdl, s);
-      else if (!cl && b.mmax <= 6) e = launch_variant<6, false, 1, float>(bp, b, out.pdl, s);
-      else if (!cl) e = launch_variant<8, false, 1, float>(bp, b, out.pdl, s);
-      else if (b.mmax <= 6) e = launch_variant<6, true, 1, float>(bp, b, out.pdl, s);
-      else e = launch_variant<8, true, 1, float>(bp, b, out.pdl, s);
+      const bool tuned = b.tune_P == P && b.tune_mode == mode;
+      if (!cl && b.mmax <= 4 && tuned && b.tune_pt == 16 && b.smem16 > 0)
+        e = launch_variant<16, 4, false, 3, float>(bp, b, out.pdl, s);
+      else if (!cl && b.mmax <= 4) e = launch_variant<kPT, 4, false, 2, float>(bp, b, out.pdl, s);
+      else if (!cl && b.mmax <= 6) e = launch_variant<kPT, 6, false, 1, float>(bp, b, out.pdl, s);
+      else if (!cl) e = launch_variant<kPT, 8, false, 1, float>(bp, b, out.pdl, s);
+      else if (b.mmax <= 6) e = launch_variant<kPT, 6, true, 1, float>(bp, b, out.pdl, s);
+      else e = launch_variant<kPT, 8, true, 1, float>(bp, b, out.pdl, s);
     } else {
-      if (!cl) e = launch_variant<8, false, 1, double>(bp, b, out.pdl, s);
-      else e = launch_variant<8, true, 1, double>(bp, b, out.pdl, s);
+      if (!cl) e = launch_variant<kPT, 8, false, 1, double>(bp, b, out.pdl, s);
+      else e = launch_variant<kPT, 8, true, 1, double>(bp, b, out.pdl, s);
     }
     if (e != cudaSuccess) return e;
   }
@@ -186,35 +193,42 @@ cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params
     }
     return cudaSuccess;
   };
-  const int ntiles = (P + kPT - 1) / kPT;
   int count = 0;
   float best = 0.f;
   for (size_t bi = 0; e == cudaSuccess && bi < plan.buckets.size(); ++bi) {
     Bucket &b = plan.buckets[bi];
     if (b.nitems == 0) continue;
-    std::vector<int> cands;
-    for (int v : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
-      if (v <= ntiles) cands.push_back(v);
-    if (cands.empty() || cands.back() != ntiles) cands.push_back(ntiles);
-    const bool narrow_capable = precision_of(plan) == 32 && b.cluster == 1 && b.mmax <= 4 && P % kPT != 0 &&
-                                P % kPT <= 16;
     b.tune_P = P;
     b.tune_mode = mode;
-    int best_pc = 0, best_nw = 1;
+    int best_pc = 0, best_nw = 1, best_pt = kPT;
     float bt = 3.4e38f;
-    for (int pc : cands)
-      for (int nw = 1; nw >= (narrow_capable ? 0 : 1) && e == cudaSuccess; --nw) {
-        b.tune_per_conf = pc;
-        b.tune_narrow = nw;
-        float t = 0.f;
-        e = time_launch(t);
-        ++count;
-        if (e == cudaSuccess && t < bt) {
-          bt = t;
-          best_pc = pc;
-          best_nw = nw;
+    const bool small_tiles = b.smem16 > 0;   // the 16-parameter-set tile variant exists for this bucket
+    for (int pt : {kPT, 16}) {
+      if (pt == 16 && !small_tiles) continue;
+      const int ntiles = (P + pt - 1) / pt;
+      std::vector<int> cands;
+      for (int v : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
+        if (v <= ntiles) cands.push_back(v);
+      if (cands.empty() || cands.back() != ntiles) cands.push_back(ntiles);
+      const bool narrow_capable = precision_of(plan) == 32 && b.cluster == 1 && b.mmax <= 4 && P % pt != 0 &&
+                                  P % pt <= pt / 2;
+      for (int pc : cands)
+        for (int nw = 1; nw >= (narrow_capable ? 0 : 1) && e == cudaSuccess; --nw) {
+          b.tune_pt = pt;
+          b.tune_per_conf = pc;
+          b.tune_narrow = nw;
+          float t = 0.f;
+          e = time_launch(t);
+          ++count;
+          if (e == cudaSuccess && t < bt) {
+            bt = t;
+            best_pc = pc;
+            best_nw = nw;
+            best_pt = pt;
+          }
         }
-      }
+    }
+    b.tune_pt = best_pt;
     b.tune_per_conf = best_pc;
     b.tune_narrow = best_nw;
   }

@@ -385,7 +385,7 @@ struct BatchParams {
 // stage address to the peer rank.
 template <int PT, bool CLUSTER, typename R>
 __host__ __device__ inline size_t region0_elems(int nb) {
-  const size_t st = (size_t)nb * 3 * PT;
+  const size_t st = (size_t)nb * stage_stride<PT>();
   const size_t rd = (size_t)(kNW + (CLUSTER ? kMaxCluster : 1)) * kNRed * PT;
   const size_t e = st > rd ? st : rd;
   return (e * sizeof(R) + 31) / 32 * 32 / sizeof(R);
@@ -832,14 +832,15 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     const TileEnv<R> env = {stage, sA, sB, sC, satom, stF, ns, s0, nat, c, cb0, B0, mask, fit, rank, ncta,
                              peer_stage, peer_b0};
     pdl_wait();   // per-call constants of the preparation kernel (a no-op after the first item)
-    // the last tile may hold fewer parameter sets: the FP32 single-CTA variant for up to 4 neighbours
-    // runs it with 2 or 4 atoms in a warp (tiles of 16 or 8 parameter sets); other variants keep the
+    // the last tile may hold fewer parameter sets: the FP32 single-CTA variants for up to 4 neighbours
+    // run it with more atoms in a warp (tiles of 16 or 8 parameter sets); other variants keep the
     // full width
-    constexpr bool kNarrow = !CLUSTER && MMAX <= 4 && sizeof(R) == 4 && PT == 32;
+    constexpr bool kNarrow = !CLUSTER && MMAX <= 4 && sizeof(R) == 4 && PT >= 16;
     for (int tile = tile0; tile < tile1; ++tile) {
       const int width = min(PT, a.P - tile * PT);
       if (kNarrow && a.narrow && width <= 8) tile_pass<(kNarrow ? 8 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
-      else if (kNarrow && a.narrow && width <= 16) tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
+      else if (kNarrow && PT > 16 && a.narrow && width <= 16)
+        tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
       else tile_pass<PT, PT, MMAX, CLUSTER, R>(a, env, tile);
     }
   }

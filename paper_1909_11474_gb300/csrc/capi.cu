@@ -59,7 +59,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     bool operator<(const Key &o) const { return mmax != o.mmax ? mmax < o.mmax : cl < o.cl; }
   };
   std::map<Key, std::vector<int>> groups;
-  std::map<Key, size_t> smem, adj_smem;
+  std::map<Key, size_t> smem, adj_smem, smem16;
   for (int cf = 0; cf < c.C; ++cf) {
     const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
     int chosen = 0;
@@ -88,6 +88,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     if (chosen == 1) {
       const int nb = c.h_boff[a1] - c.h_boff[a0], nq = c.h_poff[a1] - c.h_poff[a0];
       adj_smem[k] = std::max(adj_smem[k], tsf::adjoint_smem_bytes(nb, nq, nat));
+      if (precision == 32 && mmax == 4) smem16[k] = std::max(smem16[k], tsf::batch_smem_bytes_pt16(nb, nq, nat));
     }
   }
   std::vector<tsf::CtaRec> recs;
@@ -110,6 +111,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     b.precision = precision;
     b.smem = smem[k];
     b.adj_smem = adj_smem[k];
+    b.smem16 = (k.cl == 1 && k.mmax == 4 && precision == 32) ? smem16[k] : 0;
     b.item_off = (int)recs.size();
     b.uniform = true;
     for (int cf : cfgs) {
@@ -610,6 +612,55 @@ int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const te
   plan.gen = ++tsf::g_plan_gen;   // captured launch sequences of the old schedule are stale
   if (best_ms) *best_ms = ms;
   if (tried) *tried = n;
+  return TERSOFF_OK;
+}
+
+int tersoff_set_schedule(tersoff_ctx *ctx, int32_t precision, int32_t P, int32_t tile, int32_t items_per_config,
+                         int32_t narrow) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (int rc = tsf::finish_build(ctx)) return rc;
+  if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
+  if (P < 1 || items_per_config < 1 || (tile != 32 && tile != 16) || (narrow != 0 && narrow != 1))
+    return fail(ctx, TERSOFF_E_ARG, "need P >= 1, tile 32 or 16, items_per_config >= 1, narrow 0 or 1%s");
+  if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
+  int rc = build_plan(ctx, precision);
+  if (rc) return rc;
+  tsf::BatchPlan &plan = precision == 64 ? c.plan64 : c.plan32;
+  for (tsf::Bucket &b : plan.buckets) {
+    b.tune_P = P;
+    b.tune_mode = tsf::kModeFitness;
+    b.tune_pt = (tile == 16 && b.smem16 > 0) ? 16 : 32;
+    b.tune_per_conf = items_per_config;
+    b.tune_narrow = narrow;
+  }
+  plan.gen = ++tsf::g_plan_gen;
+  return TERSOFF_OK;
+}
+
+int tersoff_schedule_info(tersoff_ctx *ctx, int32_t precision, int32_t bucket, int32_t *info) {
+  if (!ctx || !info) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (int rc = tsf::finish_build(ctx)) return rc;
+  if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
+  if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
+  int rc = build_plan(ctx, precision);
+  if (rc) return rc;
+  const tsf::BatchPlan &plan = precision == 64 ? c.plan64 : c.plan32;
+  if (bucket < 0) {
+    info[0] = (int32_t)plan.buckets.size();
+    return TERSOFF_OK;
+  }
+  if (bucket >= (int)plan.buckets.size()) return fail(ctx, TERSOFF_E_ARG, "bucket index out of range%s");
+  const tsf::Bucket &b = plan.buckets[bucket];
+  const bool tuned = b.tune_mode >= 0;
+  info[0] = b.mmax;
+  info[1] = b.cluster;
+  info[2] = b.nitems;
+  info[3] = tuned ? b.tune_P : 0;
+  info[4] = tuned ? b.tune_pt : 32;
+  info[5] = tuned ? b.tune_per_conf : 0;
+  info[6] = tuned ? b.tune_narrow : 1;
   return TERSOFF_OK;
 }
 

@@ -112,10 +112,12 @@ struct Bucket {
   bool uniform;    // every configuration of the bucket has the same atom and bond counts
   int nitems;      // configurations in the bucket
   int item_off;    // first record of the bucket (records are per configuration and cluster rank)
+  size_t smem16 = 0;        // shared memory per CTA of the 16-parameter-set tile variant (0: none)
   mutable int per_sm = 0;   // resident CTAs per SM of the bucket's kernel variant (0: not queried yet)
+  mutable int per_sm16 = 0; // the same for the 16-parameter-set tile variant
   // schedule chosen by the autotuner for one (P, mode): work items per configuration and whether the
   // last, partly filled parameter tile runs 2 or 4 atoms per warp; otherwise the built-in heuristic
-  int tune_P = 0, tune_mode = -1, tune_per_conf = 0, tune_narrow = 1;
+  int tune_P = 0, tune_mode = -1, tune_per_conf = 0, tune_narrow = 1, tune_pt = 32;
 };
 
 // Start/stop event pairs recorded around the launches of one kernel family while enabled; read and
@@ -268,6 +270,7 @@ cudaError_t launch_plain(const Ctx &ctx, const double *params, int P, double *E,
                          cudaStream_t s);
 
 size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster);
+size_t batch_smem_bytes_pt16(int nb, int nq, int nat);   // FP32 single-CTA, 16 parameter sets per tile
 int batch_param_tile();
 int batch_max_smem_optin();
 

@@ -291,3 +291,23 @@ def test_autotune_keeps_results_within_the_bars(ctx):
     S = S.cpu().numpy()
     assert (np.abs(np.sqrt(S) - np.sqrt(ref["S"])) <= B).all()
     assert ctx.get_status() == 0
+
+
+@pytest.mark.parametrize("P", [45, 40, 7])
+@pytest.mark.parametrize("tile,items,narrow", [(32, 1, 1), (32, 3, 0), (16, 1, 1), (16, 2, 0), (16, 5, 1)])
+def test_every_schedule_meets_the_oracle_bars(ctx, P, tile, items, narrow):
+    """Each schedule the autotuner can choose (tile width, work items per configuration, narrow last
+    tile) gives a fitness within the oracle bounds, for full, half and small last tiles."""
+    w = I.workload_ga_batch(P=P, C=5)
+    cs = w["configs"]
+    Eh, Wh, Fh = oracle.evaluate_batch(cs, w["hidden"][None, :])
+    t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0])
+    E, W, F, ES, WS = oracle.evaluate_batch(cs, w["params"], scales=True)
+    ref = oracle.fitness_from_predictions(cs, t, E, W, F)
+    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32)
+    _build(ctx, cs)
+    ctx.set_schedule(P, tile=tile, items_per_config=items, narrow=bool(narrow))
+    Z, Zq, S = ctx.fitness(torch.tensor(w["params"], device="cuda"), targets_to_device(t))
+    S = S.cpu().numpy()
+    assert (np.abs(np.sqrt(S) - np.sqrt(ref["S"])) <= B).all()
+    assert ctx.get_status() == 0
