@@ -288,9 +288,10 @@ def run_ours(args):
     achieved = flop / b_time / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(),
-                "kernel": "tsf::batch_kernel<{t},4,0,{m},float> (every cell of the workload has m <= 4; tile "
-                          "chosen by the autotuner)".format(t=ctx.schedule_info(32)[0]["tile"],
-                                                            m=3 if ctx.schedule_info(32)[0]["tile"] == 16 else 2),
+                "kernel": "tsf::batch_kernel<{t},4,0,{m},float,{w}> (every cell of the workload has m <= 4; "
+                          "variant chosen by the autotuner)".format(
+                              t=ctx.schedule_info(32)[0]["tile"], w=ctx.schedule_info(32)[0]["warps"],
+                              m=3 if ctx.schedule_info(32)[0]["tile"] == 16 else 2),
                 "kernel_ms": round(1e3 * b_time, 4), "flop_per_launch": flop,
                 "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                f"(sm_max_mhz from MEASURED_PEAKS.json, {peak_src})",

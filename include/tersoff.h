@@ -170,7 +170,8 @@ int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, int32_t P,
  * tersoff_fitness arguments (P, targets, precision; params is read as the workload), times every
  * candidate schedule of each launch bucket -- work items per configuration (chunks of the parameter
  * tiles claimed by the persistent CTAs) and, for the FP32 single-CTA variant of up to 4 neighbours,
- * the tile width (32 parameter sets, or 16 with two atoms per warp and three CTAs per SM) and
+ * the tile width and warps per CTA (32 parameter sets with 8 or 12 warps, or 16 with two atoms per
+ * warp and three CTAs per SM) and
  * whether a partly filled last tile runs more atoms per warp -- over whole launches (the best of
  * `reps` timed launches after one warm-up, CUDA events on `stream`), and keeps the fastest in the
  * context. Later tersoff_fitness / tersoff_fitness_static / tersoff_eval calls with the same P use
@@ -184,18 +185,19 @@ int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const te
 /* Set the batched fitness schedule by hand (what tersoff_autotune would choose); the paper has no
  * counterpart. For every launch bucket of `precision` and calls with this P: tile = 32 parameter
  * sets per tile (one atom per warp), or 16 (two atoms per warp, three CTAs per SM; only for the FP32
- * single-CTA variant of up to 4 neighbours, others keep 32); items_per_config >= 1 work items per
+ * single-CTA variant of up to 4 neighbours, others keep 32); warps = 8 or 12 per CTA (12: 32-wide
+ * tiles of that same variant only, at most 80 registers, two CTAs per SM); items_per_config >= 1 work items per
  * configuration (the parameter tiles split into that many chunks, capped at the tile count);
  * narrow = 1 lets a partly filled last tile run with more atoms per warp. Kept until a rebuild
  * changes the neighbour counts or tersoff_autotune runs. */
-int tersoff_set_schedule(tersoff_ctx *ctx, int32_t precision, int32_t P, int32_t tile, int32_t items_per_config,
-                         int32_t narrow);
+int tersoff_set_schedule(tersoff_ctx *ctx, int32_t precision, int32_t P, int32_t tile, int32_t warps,
+                         int32_t items_per_config, int32_t narrow);
 
 /* The batched work schedule of the current build; the paper has no counterpart. bucket < 0: info[0]
- * receives the number of launch buckets. Otherwise info (host, 7 int32) receives for that bucket:
+ * receives the number of launch buckets. Otherwise info (host, 8 int32) receives for that bucket:
  * largest neighbour count of its kernel variant, CTAs per configuration (cluster size), number of
  * configurations, the P its fitness schedule was set for (0: none, built-in heuristic), tile width,
- * work items per configuration (0: heuristic), narrow last tile (0/1). */
+ * work items per configuration (0: heuristic), narrow last tile (0/1), warps per CTA. */
 int tersoff_schedule_info(tersoff_ctx *ctx, int32_t precision, int32_t bucket, int32_t *info);
 
 /* Loss and its gradient with respect to x = [D0, alpha, r0, beta, n, h] for every parameter set.

@@ -80,7 +80,7 @@ def load():
         "tersoff_kernel_launches": (ctypes.c_int64, []),
         "tersoff_profile": (ctypes.c_int, [_vp, _i32]),
         "tersoff_set_launch_mode": (ctypes.c_int, [_vp, _i32]),
-        "tersoff_set_schedule": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32]),
+        "tersoff_set_schedule": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
         "tersoff_schedule_info": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
         "tersoff_autotune": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _i32, _i32,
                                             ctypes.POINTER(_f64), ctypes.POINTER(_i32), _vp]),
@@ -287,19 +287,21 @@ class Context:
         return float(ms.value), int(n.value)
 
     def set_schedule(self, P: int, tile: int = 32, items_per_config: int = 1, narrow: bool = True,
-                     precision: int = 32):
+                     precision: int = 32, warps: int = 8):
         """Fix the batched fitness schedule for this P (tersoff_set_schedule)."""
-        self._check(self.lib.tersoff_set_schedule(self.h, precision, P, tile, items_per_config, 1 if narrow else 0))
+        self._check(self.lib.tersoff_set_schedule(self.h, precision, P, tile, warps, items_per_config,
+                                                  1 if narrow else 0))
 
     def schedule_info(self, precision: int = 32):
         """Per launch bucket: dict of mmax, cluster, configs, tuned_P, tile, items_per_config, narrow."""
-        n = np.zeros(7, np.int32)
+        n = np.zeros(8, np.int32)
         self._check(self.lib.tersoff_schedule_info(self.h, precision, -1, n.ctypes.data))
         out = []
         for b in range(int(n[0])):
-            v = np.zeros(7, np.int32)
+            v = np.zeros(8, np.int32)
             self._check(self.lib.tersoff_schedule_info(self.h, precision, b, v.ctypes.data))
-            out.append(dict(zip(("mmax", "cluster", "configs", "tuned_P", "tile", "items_per_config", "narrow"),
+            out.append(dict(zip(("mmax", "cluster", "configs", "tuned_P", "tile", "items_per_config", "narrow",
+                                 "warps"),
                                 (int(x) for x in v))))
         return out
 

@@ -20,6 +20,7 @@ size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster)
 int batch_param_tile() { return kPT; }
 
 size_t batch_smem_bytes_pt16(int nb, int nq, int nat) { return batch_smem<16, false, float>(nb, nq, nat); }
+size_t batch_smem_bytes_nw12(int nb, int nq, int nat) { return batch_smem<kPT, false, float, 12>(nb, nq, nat); }
 
 static int precision_of(const BatchPlan &plan) { return plan.precision; }
 
@@ -30,11 +31,12 @@ int batch_max_smem_optin() {
   return v;
 }
 
-template <int PTV, int MMAX, bool CLUSTER, int MINB, typename R>
+template <int PTV, int MMAX, bool CLUSTER, int MINB, typename R, int NW = kNW>
 static cudaError_t launch_variant(BatchParams bp, const Bucket &b, bool pdl, cudaStream_t s) {
-  auto kern = batch_kernel<PTV, MMAX, CLUSTER, MINB, R>;
-  const size_t smem = PTV == kPT ? b.smem : b.smem16;
-  int &per_sm = PTV == kPT ? b.per_sm : b.per_sm16;
+  auto kern = batch_kernel<PTV, MMAX, CLUSTER, MINB, R, NW>;
+  const size_t smem = PTV != kPT ? b.smem16 : NW != kNW ? b.smem12 : b.smem;
+  int &per_sm = PTV != kPT ? b.per_sm16 : NW != kNW ? b.per_sm12 : b.per_sm;
+  constexpr int kThr = NW * kWarp;
   bp.ntiles = (bp.P + PTV - 1) / PTV;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -44,7 +46,7 @@ static cudaError_t launch_variant(BatchParams bp, const Bucket &b, bool pdl, cud
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (per_sm == 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThr, smem);
     if (e != cudaSuccess) return e;
   }
   const int slots = std::max(1, per_sm * nsm / ncta);
@@ -67,7 +69,7 @@ static cudaError_t launch_variant(BatchParams bp, const Bucket &b, bool pdl, cud
   const int grid_clusters = std::min(nitems, slots);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(grid_clusters * ncta));
-  cfg.blockDim = dim3(kThreads);
+  cfg.blockDim = dim3(kThr);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   // programmatic dependent launch: the kernel may start while its predecessor (the preparation kernel
@@ -153,6 +155,8 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
       const bool tuned = b.tune_P == P && b.tune_mode == mode;
       if (!cl && b.mmax <= 4 && tuned && b.tune_pt == 16 && b.smem16 > 0)
         e = launch_variant<16, 4, false, 3, float>(bp, b, out.pdl, s);
+      else if (!cl && b.mmax <= 4 && tuned && b.tune_nw == 12 && b.smem12 > 0)
+        e = launch_variant<kPT, 4, false, 2, float, 12>(bp, b, out.pdl, s);
       else if (!cl && b.mmax <= 4) e = launch_variant<kPT, 4, false, 2, float>(bp, b, out.pdl, s);
       else if (!cl && b.mmax <= 6) e = launch_variant<kPT, 6, false, 1, float>(bp, b, out.pdl, s);
       else if (!cl) e = launch_variant<kPT, 8, false, 1, float>(bp, b, out.pdl, s);
@@ -200,11 +204,12 @@ cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params
     if (b.nitems == 0) continue;
     b.tune_P = P;
     b.tune_mode = mode;
-    int best_pc = 0, best_nw = 1, best_pt = kPT;
+    int best_pc = 0, best_nw = 1, best_pt = kPT, best_warps = kNW;
     float bt = 3.4e38f;
-    const bool small_tiles = b.smem16 > 0;   // the 16-parameter-set tile variant exists for this bucket
-    for (int pt : {kPT, 16}) {
-      if (pt == 16 && !small_tiles) continue;
+    // variants: 32-wide tiles with 8 or 12 warps per CTA, 16-wide tiles with 8 (where they exist)
+    for (int var = 0; var < 3; ++var) {
+      const int pt = var == 2 ? 16 : kPT, warps = var == 1 ? 12 : kNW;
+      if ((var == 1 && b.smem12 == 0) || (var == 2 && b.smem16 == 0)) continue;
       const int ntiles = (P + pt - 1) / pt;
       std::vector<int> cands;
       for (int v : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64})
@@ -215,6 +220,7 @@ cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params
       for (int pc : cands)
         for (int nw = 1; nw >= (narrow_capable ? 0 : 1) && e == cudaSuccess; --nw) {
           b.tune_pt = pt;
+          b.tune_nw = warps;
           b.tune_per_conf = pc;
           b.tune_narrow = nw;
           float t = 0.f;
@@ -225,10 +231,12 @@ cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params
             best_pc = pc;
             best_nw = nw;
             best_pt = pt;
+            best_warps = warps;
           }
         }
     }
     b.tune_pt = best_pt;
+    b.tune_nw = best_warps;
     b.tune_per_conf = best_pc;
     b.tune_narrow = best_nw;
   }

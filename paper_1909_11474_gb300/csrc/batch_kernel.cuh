@@ -383,17 +383,17 @@ struct BatchParams {
 //   [sA: nb R4][sB: nb R4][sC: nq R][satom: natoms int4][stF: natoms R4 (fitness only)]
 // region0 sits at offset 0 in every CTA, so a peer's stage is addressed by mapping this CTA's own
 // stage address to the peer rank.
-template <int PT, bool CLUSTER, typename R>
+template <int PT, bool CLUSTER, typename R, int NW = kNW>
 __host__ __device__ inline size_t region0_elems(int nb) {
   const size_t st = (size_t)nb * stage_stride<PT>();
-  const size_t rd = (size_t)(kNW + (CLUSTER ? kMaxCluster : 1)) * kNRed * PT;
+  const size_t rd = (size_t)(NW + (CLUSTER ? kMaxCluster : 1)) * kNRed * PT;
   const size_t e = st > rd ? st : rd;
   return (e * sizeof(R) + 31) / 32 * 32 / sizeof(R);
 }
-template <int PT, bool CLUSTER, typename R>
+template <int PT, bool CLUSTER, typename R, int NW = kNW>
 __host__ __device__ inline size_t batch_smem(int nb, int nq, int nat) {
   using R4 = typename Vec4<R>::T;
-  size_t b = region0_elems<PT, CLUSTER, R>(nb) * sizeof(R) + (size_t)nb * 2 * sizeof(R4);
+  size_t b = region0_elems<PT, CLUSTER, R, NW>(nb) * sizeof(R) + (size_t)nb * 2 * sizeof(R4);
   b += ((size_t)nq * sizeof(R) + 31) / 32 * 32;
   b += (size_t)nat * sizeof(int4);
   b += (size_t)nat * sizeof(R4);
@@ -494,7 +494,7 @@ struct TileEnv {
   const int *peer_b0;
 };
 
-template <int PTT, int PTW, int MMAX, bool CLUSTER, typename R>
+template <int PTT, int PTW, int MMAX, bool CLUSTER, typename R, int NW>
 __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R> &env, int tile) {
   using R4 = typename Vec4<R>::T;
   constexpr int APW = kWarp / PTT;
@@ -530,7 +530,7 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
   for (int k = 0; k < 6; ++k) acc.W[k] = R(0);
 
   // ---- passes 1-2
-  for (int base = warp * APW; base < ns; base += kNW * APW) {
+  for (int base = warp * APW; base < ns; base += NW * APW) {
     const int li = base + slot;
     const bool valid = li < ns;
     int4 at = make_int4(0, 0, 0, 0);
@@ -564,7 +564,7 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 
   // ---- pass 3: F_i = sum_j (P_ij - P_ji)
   R sf = R(0), sF2 = R(0), sT = R(0);
-  for (int base = warp * APW; base < ns; base += kNW * APW) {
+  for (int base = warp * APW; base < ns; base += NW * APW) {
     const int li = base + slot;
     if (li >= ns) continue;
     const int4 at = sld(&satom[li], 12);
@@ -636,17 +636,17 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 #pragma unroll
   for (int k = 0; k < kNRed; ++k) v[k] = sum_over_atom_slots<PTT>(v[k]);
   if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();   // stages no longer read
-  R *red = stage;                                   // [kNW][kNRed][PTT]
-  R *tot = stage + kNW * kNRed * PTT;                // [ranks][kNRed][PTT] (rank 0 collects)
+  R *red = stage;                                   // [NW][kNRed][PTT]
+  R *tot = stage + NW * kNRed * PTT;                // [ranks][kNRed][PTT] (rank 0 collects)
   if (slot == 0) {
 #pragma unroll
     for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PTT + pl], v[k], 17);
   }
   __syncthreads();
-  for (int idx = tid; idx < kNRed * PTT; idx += kThreads) {
+  for (int idx = tid; idx < kNRed * PTT; idx += (NW * kWarp)) {
     R t = R(0);
 #pragma unroll
-    for (int w = 0; w < kNW; ++w) t += sld(&red[w * kNRed * PTT + idx], 18);
+    for (int w = 0; w < NW; ++w) t += sld(&red[w * kNRed * PTT + idx], 18);
     if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(tot + rank * kNRed * PTT + idx), 0), t);
     else sst(&tot[idx], t, 19);
   }
@@ -704,8 +704,8 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 // split into nchunks chunks of chunk_tiles parameter tiles; a CTA (or cluster) claims the next item
 // from an atomic counter, stages the configuration's geometry once (single-CTA launches: one TMA
 // bulk copy per array, completed on an mbarrier) and runs the chunk's tiles.
-template <int PT, int MMAX, bool CLUSTER, int MINB, typename R>
-__global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams a) {
+template <int PT, int MMAX, bool CLUSTER, int MINB, typename R, int NW = kNW>
+__global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchParams a) {
   using R4 = typename Vec4<R>::T;
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ __align__(8) unsigned long long mbar;
@@ -751,11 +751,24 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     const int rec0 = ci * (int)ncta;
     const CtaRec rec = a.recs[rec0 + rank];
     const int c = rec.c;
+    // the schedule record must match the device's bond CSR: a fitness launch may be queued on the
+    // previous schedule before the host has checked a rebuild's neighbour counts, and then every
+    // item whose configuration changed is skipped (the host launches again on the new schedule).
+    // Every rank checks the records of all ranks of the item, so a cluster decides alike.
+    {
+      bool match = true;
+      for (unsigned r = 0; r < ncta; ++r) {
+        const CtaRec q = r == rank ? rec : a.recs[rec0 + r];
+        match = match && a.boff[q.s0] == q.B0 && a.boff[q.s0 + q.ns] == q.B0 + q.nb && a.poff[q.s0] == q.Q0 &&
+                a.poff[q.s0 + q.ns] == q.Q0 + q.nq;
+      }
+      if (!match) continue;
+    }
 
     // atom slice of this CTA
     const int nat = rec.nat, s0 = rec.s0, ns = rec.ns, cb0 = rec.cb0;
     const int B0 = rec.B0, nb = rec.nb, Q0 = rec.Q0, nq = rec.nq;
-    R4 *sA = reinterpret_cast<R4 *>(stage + region0_elems<PT, CLUSTER, R>(nb));
+    R4 *sA = reinterpret_cast<R4 *>(stage + region0_elems<PT, CLUSTER, R, NW>(nb));
     R4 *sB = sA + nb;
     R *sC = reinterpret_cast<R *>(sB + nb);
     int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) +
@@ -779,13 +792,13 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
           if (bC) bulk_g2s(sC, gC, bC, &mbar);
         }
       } else {
-        for (int t = tid; t < nb; t += kThreads) {
+        for (int t = tid; t < nb; t += (NW * kWarp)) {
           sst(&sA[t], gA[t], 6);
           sst(&sB[t], gB[t], 7);
         }
-        for (int t = tid; t < nq; t += kThreads) sst(&sC[t], gC[t], 8);
+        for (int t = tid; t < nq; t += (NW * kWarp)) sst(&sC[t], gC[t], 8);
       }
-      for (int t = tid; t < ns; t += kThreads) {
+      for (int t = tid; t < ns; t += (NW * kWarp)) {
         const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
         sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, a.outer[s0 + t]), 9);
         if (fit) {   // target force in the working precision and |F*|^2 (from the FP64 components)
@@ -838,10 +851,10 @@ __global__ void __launch_bounds__(kThreads, MINB) batch_kernel(const BatchParams
     constexpr bool kNarrow = !CLUSTER && MMAX <= 4 && sizeof(R) == 4 && PT >= 16;
     for (int tile = tile0; tile < tile1; ++tile) {
       const int width = min(PT, a.P - tile * PT);
-      if (kNarrow && a.narrow && width <= 8) tile_pass<(kNarrow ? 8 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
+      if (kNarrow && a.narrow && width <= 8) tile_pass<(kNarrow ? 8 : PT), PT, MMAX, CLUSTER, R, NW>(a, env, tile);
       else if (kNarrow && PT > 16 && a.narrow && width <= 16)
-        tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R>(a, env, tile);
-      else tile_pass<PT, PT, MMAX, CLUSTER, R>(a, env, tile);
+        tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R, NW>(a, env, tile);
+      else tile_pass<PT, PT, MMAX, CLUSTER, R, NW>(a, env, tile);
     }
   }
 }

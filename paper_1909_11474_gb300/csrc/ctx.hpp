@@ -113,11 +113,13 @@ struct Bucket {
   int nitems;      // configurations in the bucket
   int item_off;    // first record of the bucket (records are per configuration and cluster rank)
   size_t smem16 = 0;        // shared memory per CTA of the 16-parameter-set tile variant (0: none)
+  size_t smem12 = 0;        // shared memory per CTA of the 12-warp variant (0: none)
   mutable int per_sm = 0;   // resident CTAs per SM of the bucket's kernel variant (0: not queried yet)
   mutable int per_sm16 = 0; // the same for the 16-parameter-set tile variant
+  mutable int per_sm12 = 0; // the same for the 12-warp variant
   // schedule chosen by the autotuner for one (P, mode): work items per configuration and whether the
   // last, partly filled parameter tile runs 2 or 4 atoms per warp; otherwise the built-in heuristic
-  int tune_P = 0, tune_mode = -1, tune_per_conf = 0, tune_narrow = 1, tune_pt = 32;
+  int tune_P = 0, tune_mode = -1, tune_per_conf = 0, tune_narrow = 1, tune_pt = 32, tune_nw = 8;
 };
 
 // Start/stop event pairs recorded around the launches of one kernel family while enabled; read and
@@ -271,6 +273,7 @@ cudaError_t launch_plain(const Ctx &ctx, const double *params, int P, double *E,
 
 size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster);
 size_t batch_smem_bytes_pt16(int nb, int nq, int nat);   // FP32 single-CTA, 16 parameter sets per tile
+size_t batch_smem_bytes_nw12(int nb, int nq, int nat);   // FP32 single-CTA, 12 warps per CTA
 int batch_param_tile();
 int batch_max_smem_optin();
 

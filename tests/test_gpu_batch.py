@@ -294,8 +294,9 @@ def test_autotune_keeps_results_within_the_bars(ctx):
 
 
 @pytest.mark.parametrize("P", [45, 40, 7])
-@pytest.mark.parametrize("tile,items,narrow", [(32, 1, 1), (32, 3, 0), (16, 1, 1), (16, 2, 0), (16, 5, 1)])
-def test_every_schedule_meets_the_oracle_bars(ctx, P, tile, items, narrow):
+@pytest.mark.parametrize("tile,warps,items,narrow", [(32, 8, 1, 1), (32, 8, 3, 0), (16, 8, 1, 1), (16, 8, 2, 0),
+                                                     (16, 8, 5, 1), (32, 12, 1, 1), (32, 12, 2, 0)])
+def test_every_schedule_meets_the_oracle_bars(ctx, P, tile, warps, items, narrow):
     """Each schedule the autotuner can choose (tile width, work items per configuration, narrow last
     tile) gives a fitness within the oracle bounds, for full, half and small last tiles."""
     w = I.workload_ga_batch(P=P, C=5)
@@ -306,8 +307,42 @@ def test_every_schedule_meets_the_oracle_bars(ctx, P, tile, items, narrow):
     ref = oracle.fitness_from_predictions(cs, t, E, W, F)
     B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32)
     _build(ctx, cs)
-    ctx.set_schedule(P, tile=tile, items_per_config=items, narrow=bool(narrow))
+    ctx.set_schedule(P, tile=tile, items_per_config=items, narrow=bool(narrow), warps=warps)
     Z, Zq, S = ctx.fitness(torch.tensor(w["params"], device="cuda"), targets_to_device(t))
     S = S.cpu().numpy()
     assert (np.abs(np.sqrt(S) - np.sqrt(ref["S"])) <= B).all()
     assert ctx.get_status() == 0
+
+
+@pytest.mark.parametrize("change_counts", [False, True])
+def test_fitness_queued_before_rebuild_check(ctx, change_counts):
+    """A fitness call right after a rebuild of the same layout is queued before the host has checked
+    the new neighbour counts. Whether the counts stayed or changed, its results equal those of a fresh
+    context built once on the new positions."""
+    from paper_1909_11474_gb300 import binding
+    w = I.workload_ga_batch(P=37, C=6)
+    cs = w["configs"]
+    t = {"E": np.full(cs.C, -4.6), "W": np.zeros((cs.C, 6)), "F": np.zeros((cs.Ntot, 3)),
+         "mask": np.full(cs.C, 7, np.uint8)}
+    params, tg = torch.tensor(w["params"], device="cuda"), targets_to_device(t)
+    ctx.set_launch_mode()
+    _build(ctx, cs)
+    ctx.fitness(params, tg)
+    pos2 = cs.pos.copy() + np.random.default_rng(4).normal(0, 0.01, cs.pos.shape)
+    box2 = cs.box.copy()
+    if change_counts:   # move one atom of configuration 2 by 0.7 A along <110>: it gains second-shell bonds
+        a0 = cs.atom_off[2]
+        pos2[a0] += 0.7 * np.array([1.0, 1.0, 0.0]) / np.sqrt(2.0)
+    p2, b2 = torch.tensor(pos2, device="cuda"), torch.tensor(box2, device="cuda")
+    n_before = ctx.export_neighbors()[0].copy()
+    ctx.build_neighbors(cs.atom_off, p2, b2, 2.8, 3.2, 16)
+    Z, Zq, S = ctx.fitness(params, tg)
+    got = torch.cat([Z[:, None], Zq, S], 1).cpu().numpy()
+    assert ctx.get_status() == 0
+    n_after = ctx.export_neighbors()[0]
+    assert (not np.array_equal(n_before, n_after)) == change_counts
+    fresh = binding.Context(0)
+    fresh.build_neighbors(cs.atom_off, p2, b2, 2.8, 3.2, 16)
+    Z2, Zq2, S2 = fresh.fitness(params, tg)
+    ref = torch.cat([Z2[:, None], Zq2, S2], 1).cpu().numpy()
+    assert np.array_equal(got, ref)
