@@ -1,0 +1,89 @@
+"""The device GA generation against the oracle (bit for bit: ranks, genes and parameters), and a short
+end-to-end fit with the gradient polish on synthetic data of a hidden parameter set."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ga as oga
+from paper_1909_11474_gb300 import inputs as I
+
+from ._util import targets_to_device, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(seed, P, n_par, bad=0, ties=0):
+    rng = np.random.default_rng(seed)
+    Z = rng.uniform(0.0, 2.0, P)
+    for k in range(ties):
+        Z[(7 * k + 1) % P] = Z[(3 * k) % P]
+    for k in range(bad):
+        Z[(5 * k + 2) % P] = [np.nan, np.inf, -np.inf][k % 3]
+    genes = rng.uniform(0.0, 1.0, (P, 6))
+    u = rng.uniform(0.0, 1.0, oga.n_uniforms(P, n_par) + 5)
+    lo = I.TABLE2_PARAMS - 0.3 * np.abs(I.TABLE2_PARAMS)
+    hi = I.TABLE2_PARAMS + 0.3 * np.abs(I.TABLE2_PARAMS)
+    return Z, genes, u, lo, hi
+
+
+@pytest.mark.parametrize("P,n_par,rate,bad,ties", [(200, 100, 0.2, 0, 0), (200, 100, 0.05, 4, 6), (7, 3, 0.5, 1, 2),
+                                                    (33, 33, 0.3, 0, 3), (1, 1, 1.0, 0, 0), (4096, 1000, 0.1, 9, 20)])
+def test_ga_step_matches_the_oracle_bit_for_bit(P, n_par, rate, bad, ties):
+    from paper_1909_11474_gb300 import binding
+    Z, genes, u, lo, hi = _case(P + n_par, P, n_par, bad, ties)
+    want, order = oga.ga_step(Z, genes, u, n_par, rate)
+    d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    g_out = torch.empty((P, 6), dtype=torch.float64, device="cuda")
+    x_out = torch.empty((P, 6), dtype=torch.float64, device="cuda")
+    o_out = torch.empty(P, dtype=torch.int32, device="cuda")
+    binding.ga_step(d(Z), d(genes), d(u), d(lo), d(hi), n_par, rate, g_out, x_out, o_out)
+    assert np.array_equal(o_out.cpu().numpy(), order)
+    assert np.array_equal(g_out.cpu().numpy(), want)
+    assert np.array_equal(x_out.cpu().numpy(), oga.phenotype(want, lo, hi))
+
+
+def test_ga_step_rejects_bad_arguments():
+    from paper_1909_11474_gb300 import binding
+    Z, genes, u, lo, hi = _case(1, 8, 4)
+    d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    g = d(genes)
+    out = torch.empty((8, 6), dtype=torch.float64, device="cuda")
+    with pytest.raises(binding.TersoffError):
+        binding.ga_step(d(Z), g, d(u), d(lo), d(hi), 9, 0.1, out, out.clone())   # n_par > P
+    with pytest.raises(binding.TersoffError):
+        binding.ga_step(d(Z), g, d(u), d(lo), d(hi), 4, 1.5, out, out.clone())   # rate > 1
+    with pytest.raises(binding.TersoffError):
+        binding.ga_step(d(Z), g, d(u), d(lo), d(hi), 4, 0.1, g, out)             # in place
+
+
+def test_ga_fit_then_polish_on_a_hidden_parameter_set():
+    """20 configurations, noise-free targets of the Table 2 parameters: the elite never worsens (up to
+    FP32 rounding), the GA cuts the best fitness by an order of magnitude, and the gradient polish
+    lowers the loss."""
+    from paper_1909_11474_gb300 import binding
+    from paper_1909_11474_gb300.ga import GeneticFit, polish
+    w = I.workload_ga_batch(P=4, C=20)
+    cs = w["configs"]
+    ctx = binding.Context(0)
+    pos, box = to_device(cs)
+    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+    E, F, W = ctx.eval(torch.tensor(w["hidden"][None, :], device="cuda"), precision=64)
+    natoms = cs.natoms.astype(np.float64)
+    t = {"E": (E[0].cpu().numpy() / natoms), "W": W[0].cpu().numpy() / natoms[:, None],
+         "F": F[0].cpu().numpy(), "mask": np.full(cs.C, 7, np.uint8)}
+    tg = targets_to_device(t)
+    lo = I.TABLE2_PARAMS - 0.3 * np.abs(I.TABLE2_PARAMS)
+    hi = I.TABLE2_PARAMS + 0.3 * np.abs(I.TABLE2_PARAMS)
+    fit = GeneticFit(ctx, tg, lo, hi, n_pop=200, n_par=100, seed=7)
+    first = float(fit.evaluate().min())
+    res = fit.run(n_gen=300, history=True)
+    h = res["history"]
+    # the elite is kept unaltered; its fitness is recomputed in whatever row it lands, and rows in a
+    # narrow last tile sum their atoms in another FP32 order: near the optimum the force residuals are
+    # small differences of FP32 forces, so equal up to 1e-4 relative
+    worst = float(np.max(h[1:] / h[:-1] - 1.0))
+    assert worst <= 1e-4, worst
+    assert res["Z"] < 0.1 * first
+    x, L0, L1 = polish(ctx, res["params"], tg, lo, hi, steps=150)
+    assert L1 < L0
+    assert ctx.get_status() == 0
