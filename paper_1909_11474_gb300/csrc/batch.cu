@@ -158,10 +158,11 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
       else if (!cl && b.mmax <= 4 && tuned && b.tune_nw == 12 && b.smem12 > 0)
         e = launch_variant<kPT, 4, false, 2, float, 12>(bp, b, out.pdl, s);
       else if (!cl && b.mmax <= 4) e = launch_variant<kPT, 4, false, 2, float>(bp, b, out.pdl, s);
-      else if (!cl && b.mmax <= 6) e = launch_variant<kPT, 6, false, 1, float>(bp, b, out.pdl, s);
-      else if (!cl) e = launch_variant<kPT, 8, false, 1, float>(bp, b, out.pdl, s);
-      else if (b.mmax <= 6) e = launch_variant<kPT, 6, true, 1, float>(bp, b, out.pdl, s);
-      else e = launch_variant<kPT, 8, true, 1, float>(bp, b, out.pdl, s);
+      else if (!cl && b.mmax <= 6) e = launch_variant<kPT, 6, false, 2, float>(bp, b, out.pdl, s);
+      else if (!cl) e = launch_variant<kPT, 8, false, 2, float>(bp, b, out.pdl, s);
+      else if (b.mmax <= 4) e = launch_variant<kPT, 4, true, 2, float>(bp, b, out.pdl, s);
+      else if (b.mmax <= 6) e = launch_variant<kPT, 6, true, 2, float>(bp, b, out.pdl, s);
+      else e = launch_variant<kPT, 8, true, 2, float>(bp, b, out.pdl, s);
     } else {
       if (!cl) e = launch_variant<kPT, 8, false, 1, double>(bp, b, out.pdl, s);
       else e = launch_variant<kPT, 8, true, 1, double>(bp, b, out.pdl, s);

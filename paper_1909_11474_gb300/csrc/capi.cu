@@ -81,7 +81,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     }
     if (!chosen) return fail(ctx, TERSOFF_E_UNSUPPORTED, "configuration too large for the batched kernels%s");
     const int mm = c.h_cfg_maxm[cf];
-    int mmax = precision == 64 ? 8 : (mm <= 4 && chosen == 1 ? 4 : (mm <= 6 ? 6 : 8));
+    int mmax = precision == 64 ? 8 : (mm <= 4 ? 4 : (mm <= 6 ? 6 : 8));
     Key k{mmax, chosen};
     groups[k].push_back(cf);
     smem[k] = std::max(smem[k], need);
