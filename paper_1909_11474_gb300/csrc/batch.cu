@@ -95,6 +95,25 @@ static cudaError_t launch_variant(BatchParams bp, const Bucket &b, bool pdl, cud
   return el;
 }
 
+// Side streams (at most kSide) and their events, created on first use.
+constexpr int kSide = 4;
+static cudaError_t ensure_side(const Ctx &ctx, int nbuckets) {
+  const size_t want = (size_t)std::min(kSide, nbuckets);
+  while (ctx.side.size() < want) {
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    ctx.side.push_back(st);
+  }
+  while (ctx.side_ev.size() < 1 + ctx.side.size()) {
+    cudaEvent_t ev = nullptr;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    ctx.side_ev.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s) {
   const bool f64 = plan.precision == 64;
@@ -144,12 +163,25 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   cudaError_t ez = cudaMemsetAsync(out.counters, 0, plan.buckets.size() * sizeof(int), s);
   if (ez != cudaSuccess) return ez;
   const bool timed = ctx.timer.begin(s);
+  // several buckets run side by side on the context's side streams (forked from and joined back into
+  // `s` by events), so one bucket's last items overlap the next bucket's first ones
+  int nlaunch = 0;
+  for (const Bucket &b : plan.buckets) nlaunch += b.nitems > 0;
+  const bool fork = nlaunch > 1 && ensure_side(ctx, (int)plan.buckets.size()) == cudaSuccess;
+  if (fork) {
+    cudaError_t e = cudaEventRecord(ctx.side_ev[0], s);
+    for (size_t k = 0; e == cudaSuccess && k < ctx.side.size(); ++k) e = cudaStreamWaitEvent(ctx.side[k], ctx.side_ev[0], 0);
+    if (e != cudaSuccess) return e;
+  }
   int bi = 0;
   for (const Bucket &b : plan.buckets) {
+    const int k = bi;
     bp.counter = out.counters + bi++;
     if (b.nitems == 0) continue;
     bp.recs = plan.items.as<CtaRec>() + b.item_off;
     cudaError_t e = cudaSuccess;
+    const cudaStream_t bs = s;
+    cudaStream_t s = fork ? ctx.side[k % ctx.side.size()] : bs;
     const bool cl = b.cluster > 1;
     if (!f64) {
       const bool tuned = b.tune_P == P && b.tune_mode == mode;
@@ -168,6 +200,13 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
       else e = launch_variant<kPT, 8, true, 1, double>(bp, b, out.pdl, s);
     }
     if (e != cudaSuccess) return e;
+  }
+  if (fork) {
+    for (size_t k = 0; k < ctx.side.size(); ++k) {
+      cudaError_t e = cudaEventRecord(ctx.side_ev[1 + k], ctx.side[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx.side_ev[1 + k], 0);
+      if (e != cudaSuccess) return e;
+    }
   }
   if (timed) ctx.timer.end(s);
   return cudaSuccess;

@@ -357,6 +357,8 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   if (c.stage_event) cudaEventDestroy(c.stage_event);
   for (cudaEvent_t ev : c.timer.ev) cudaEventDestroy(ev);
   if (c.g_fitness.exec) cudaGraphExecDestroy(c.g_fitness.exec);
+  for (cudaStream_t st : c.side) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : c.side_ev) cudaEventDestroy(ev);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   delete ctx;
 }

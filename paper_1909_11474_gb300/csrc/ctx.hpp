@@ -196,6 +196,10 @@ struct Ctx {
   // --- measurement: CUDA events around each batched-kernel launch sequence, on its stream ---
   mutable KernelTimer timer;
 
+  // --- side streams on which the launch buckets of one call run side by side (fork/join by events) ---
+  mutable std::vector<cudaStream_t> side;
+  mutable std::vector<cudaEvent_t> side_ev;   // [0]: fork, [1 + k]: bucket k done
+
   // --- launch mode of the per-call launch sequences (CUDA graphs, programmatic dependent launch) ---
   bool graphs = true;
   bool pdl = true;
