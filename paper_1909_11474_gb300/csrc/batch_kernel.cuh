@@ -508,6 +508,8 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
   const uint8_t mask = env.mask;
   const bool fit = env.fit;
   const unsigned rank = env.rank, ncta = env.ncta;
+  const int per = (nat + (int)ncta - 1) / (int)ncta;   // atoms per cluster rank (the schedule's split)
+  (void)per;
   const unsigned *peer_stage = env.peer_stage;
   const int *peer_b0 = env.peer_b0;
   (void)B0;
@@ -577,12 +579,13 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
       Fx += sld(&st[0], 13);
       Fy += sld(&st[PTT], 13);
       Fz += sld(&st[2 * PTT], 13);
-      int rb;  // configuration-local bond index of the reverse entry
-      if constexpr (sizeof(R) == 4) rb = __float_as_int((float)sld(&sB[lb + e].w, 14)) & 0xffff;
-      else rb = (int)sld(&sB[lb + e].w, 14) & 0xffff;
+      int packed;  // configuration-local indices of the reverse entry (bits 0-15) and of atom j (16-31)
+      if constexpr (sizeof(R) == 4) packed = __float_as_int((float)sld(&sB[lb + e].w, 14));
+      else packed = (int)sld(&sB[lb + e].w, 14);
+      const int rb = packed & 0xffff;
       if constexpr (CLUSTER) {
-        unsigned r = 0;
-        while (r + 1 < ncta && rb >= peer_b0[r + 1]) ++r;
+        // the reverse entry belongs to atom j, whose rank is its slice of the configuration's atoms
+        const unsigned r = min((unsigned)(packed >> 16) / (unsigned)per, ncta - 1);
         // a reverse bond outside the configuration's bond range is an inconsistent schedule:
         // flag it and skip the peer read rather than touch another CTA's shared memory
         if (rb < peer_b0[r] || rb >= peer_b0[r + 1]) {
