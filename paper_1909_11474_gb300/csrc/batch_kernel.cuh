@@ -699,8 +699,11 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
     }
     if (fit && tile == 0 && tid == 0) a.dpart[3 * c + 2] = (mask & 4) ? (double)q[9] : 0.0;
   }
-  // the next tile (or item) reuses the stage and, in rank 0, the collected totals
-  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
+  // the next tile (or item) reuses the stage, where rank 0 keeps the collected totals that its first
+  // warp reads above. A CTA barrier suffices in a cluster too: peers read a CTA's stage only between
+  // the next tile's first cluster barrier, which this CTA reaches after the barrier below, and its
+  // second, and they write rank 0's totals only after that
+  __syncthreads();
 }
 
 // Persistent work loop. The launch covers nconf configurations of one bucket (longest first), each
