@@ -238,7 +238,8 @@ int tersoff_eval_plain(tersoff_ctx *ctx, const double *params, int32_t P, double
  *  plane spacing must exceed 3*R2 so that each atom has at most one image of any other within R2),
  *  params host [6]; precision 32 or 64; E device [1] double; F device [N][3] float or double;
  *  W device [6] double. The neighbour list is the same set, in the same canonical order, as
- *  tersoff_build_neighbors would produce. max_nbr as above. */
+ *  tersoff_build_neighbors would produce. max_nbr as above, except that when an atom has more than
+ *  max_nbr neighbours (flagged) which of them are kept is unspecified. */
 int tersoff_md_force(tersoff_ctx *ctx, int32_t N, const double *pos, const double *box,
                      const double *params, double R1, double R2, int32_t max_nbr, int32_t precision,
                      double *E, void *F, double *W, tersoff_stream stream);

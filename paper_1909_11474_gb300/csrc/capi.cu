@@ -351,7 +351,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
                          &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.outer, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart, &c.tew,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
-                         &c.md_Ui, &c.md_boxd};
+                         &c.md_keys, &c.md_boxd};
   for (auto *b : bufs) b->release();
   c.hp_stage.release();
   if (c.stage_event) cudaEventDestroy(c.stage_event);
@@ -769,16 +769,29 @@ int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, in
   cudaSetDevice(c.device);
   const int64_t N = c.md_N, M = c.md_M;
   TSF_CUDA(cudaDeviceSynchronize());
-  if (cnt) TSF_CUDA(cudaMemcpy(cnt, c.md_cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost));
-  if (nbr) TSF_CUDA(cudaMemcpy(nbr, c.md_nbr.p, N * M * sizeof(int), cudaMemcpyDeviceToHost));
+  // the device list is slot-major ([max_nbr][N]) and holds the first min(count, max_nbr) entries of
+  // each atom; the transpose and the padding are done here
+  std::vector<int> count(N);
+  TSF_CUDA(cudaMemcpy(count.data(), c.md_cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost));
+  if (cnt) std::memcpy(cnt, count.data(), N * sizeof(int));
+  if (nbr) {
+    std::vector<int> tmp(N * M);
+    TSF_CUDA(cudaMemcpy(tmp.data(), c.md_nbr.p, N * M * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < N; ++i)
+      for (int64_t e = 0; e < M; ++e) nbr[i * M + e] = e < count[i] ? tmp[e * N + i] : -1;
+  }
   if (shift) {
     std::vector<char4> tmp(N * M);
     TSF_CUDA(cudaMemcpy(tmp.data(), c.md_shift.p, N * M * sizeof(char4), cudaMemcpyDeviceToHost));
-    for (int64_t k = 0; k < N * M; ++k) {
-      shift[3 * k] = tmp[k].x;
-      shift[3 * k + 1] = tmp[k].y;
-      shift[3 * k + 2] = tmp[k].z;
-    }
+    for (int64_t i = 0; i < N; ++i)
+      for (int64_t e = 0; e < M; ++e) {
+        const int64_t k = i * M + e;
+        const bool kept = e < count[i];
+        const char4 v = tmp[e * N + i];
+        shift[3 * k] = kept ? v.x : 0;
+        shift[3 * k + 1] = kept ? v.y : 0;
+        shift[3 * k + 2] = kept ? v.z : 0;
+      }
   }
   return TERSOFF_OK;
 }

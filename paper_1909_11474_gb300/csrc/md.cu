@@ -24,35 +24,52 @@ namespace tsf {
 constexpr int kMdCap = 16;    // atom slots per cell
 constexpr int kMdMaxM = 8;    // neighbours per atom handled by the force kernel
 constexpr int kMdThreads = 128;
+constexpr int kBrick = 4;                                      // interior cells per brick edge
+constexpr int kHaloEdge = kBrick + 2;                          // brick plus one cell on each side
+constexpr int kHaloCells = kHaloEdge * kHaloEdge * kHaloEdge;  // 216
+constexpr int kBrickCells = kBrick * kBrick * kBrick;          // 64
+constexpr int kStageCap = 1024;                                // halo atoms staged in shared memory
+constexpr int kListCap = 32;                                   // list entries kept per atom (max_nbr <= 32)
 
 struct MdGeom {
   double H[9], Hinv[9];
   int nc[3];
+  int diag;                   // H (and so H^-1) diagonal: fractional coordinates need 3 products, not 9
+  double ncd[3];
   float E[9];                 // cell edge vectors, row k = H_k / nc_k
   float cut2_lo, cut2_hi;     // FP32 decision band around R2^2
   double R1, R2, R2sq;
+  double inv_w, fcp_k;        // 1 / (R2 - R1) and -pi / (2 (R2 - R1)) (Eq. 9)
+  float R1f, R2f, inv_wf, fcp_kf;
 };
 
+// Cell of every atom; the cell's slots hold (u, atom index) so the pair search reads one record per
+// candidate. Every atom's neighbour count starts at zero here; an atom that gets no slot (non-finite
+// position, full cell) keeps an empty list and the call is flagged.
 __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdGeom G,
-                                int *__restrict__ cellcnt, int *__restrict__ cellatoms,
-                                float4 *__restrict__ u4, int4 *__restrict__ m4, unsigned *status) {
+                                int *__restrict__ cellcnt, float4 *__restrict__ cellu,
+                                float4 *__restrict__ u4, int4 *__restrict__ m4, int *__restrict__ cnt,
+                                unsigned *status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  cnt[i] = 0;
   const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
   if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
     set_status(status, TERSOFF_STATUS_NONFINITE);
-    m4[i] = make_int4(0, 0, 0, -1);
+    u4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    m4[i] = make_int4(0, 0, 0, 0);
     return;
   }
   int mm[3], cc[3];
   float uu[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double s = x * G.Hinv[k] + y * G.Hinv[3 + k] + z * G.Hinv[6 + k];
+    const double s = G.diag ? (k == 0 ? x : (k == 1 ? y : z)) * G.Hinv[4 * k]
+                            : x * G.Hinv[k] + y * G.Hinv[3 + k] + z * G.Hinv[6 + k];
     const double f = floor(s);
-    const double w = (s - f) * (double)G.nc[k];
-    int c = (int)floor(w);
-    c = c < 0 ? 0 : (c >= G.nc[k] ? G.nc[k] - 1 : c);
+    const double w = (s - f) * G.ncd[k];          // in [0, nc]: truncation is the floor
+    int c = (int)w;
+    c = c >= G.nc[k] ? G.nc[k] - 1 : c;
     mm[k] = (int)f;
     cc[k] = c;
     uu[k] = (float)(w - (double)c);
@@ -61,119 +78,295 @@ __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdG
   u4[i] = make_float4(uu[0], uu[1], uu[2], 0.f);
   m4[i] = make_int4(mm[0], mm[1], mm[2], cell);
   const int slot = atomicAdd(&cellcnt[cell], 1);
-  if (slot < kMdCap) cellatoms[cell * kMdCap + slot] = i;
+  if (slot < kMdCap) cellu[cell * kMdCap + slot] = make_float4(uu[0], uu[1], uu[2], __int_as_float(i));
   else set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
 }
 
-__global__ void __launch_bounds__(kMdThreads) md_neighbors_kernel(
-    int N, const double *__restrict__ pos, const MdGeom G, const float4 *__restrict__ u4,
-    const int4 *__restrict__ m4, const int *__restrict__ cellcnt, const int *__restrict__ cellatoms,
-    int M, int *__restrict__ cnt_out, int *__restrict__ nbr, char4 *__restrict__ shift,
-    unsigned *status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int4 mi = m4[i];
-  if (mi.w < 0) {
-    cnt_out[i] = 0;
-    return;
+// Code of the periodic wrap of cell coordinates c (each in [-1, nc]): (w0+1) << 4 | (w1+1) << 2 | (w2+1).
+// The code of the opposite wrap is 42 - code.
+__device__ __forceinline__ unsigned wrap_code(const MdGeom &G, int c0, int c1, int c2) {
+  const int w0 = c0 < 0 ? 0 : (c0 >= G.nc[0] ? 2 : 1), w1 = c1 < 0 ? 0 : (c1 >= G.nc[1] ? 2 : 1),
+            w2 = c2 < 0 ? 0 : (c2 >= G.nc[2] ? 2 : 1);
+  return (unsigned)((w0 << 4) | (w1 << 2) | w2);
+}
+constexpr unsigned kWrapNeg = 42u;
+
+// One candidate pair at cell-unit separation v: the FP32 distance decides outside the rounding band,
+// the exact FP64 test inside it. The test is symmetric (the FP64 separation of (j, i, -n) is exactly
+// the negated one of (i, j, n)), so deciding a pair once decides both of its entries.
+__device__ __forceinline__ bool md_pair_in(const MdGeom &G, const double *__restrict__ pos,
+                                           const int4 *__restrict__ m4, int i, int j, unsigned code,
+                                           float v0, float v1, float v2) {
+  const float dx = v0 * G.E[0] + v1 * G.E[3] + v2 * G.E[6];
+  const float dy = v0 * G.E[1] + v1 * G.E[4] + v2 * G.E[7];
+  const float dz = v0 * G.E[2] + v1 * G.E[5] + v2 * G.E[8];
+  const float r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 > G.cut2_hi) return false;
+  if (r2 < G.cut2_lo) return true;
+  const int4 mi = m4[i], mj = m4[j];
+  const ExactPair e = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], pos[3 * i], pos[3 * i + 1],
+                                 pos[3 * i + 2], G.H, (int)(code >> 4) - 1 + mi.x - mj.x,
+                                 (int)((code >> 2) & 3) - 1 + mi.y - mj.y, (int)(code & 3) - 1 + mi.z - mj.z);
+  return e.r2 < G.R2sq;
+}
+
+// The entries of the pairs one thread accepted, keys (partner << 6 | wrap code) in slot-major
+// [M][N] rows: the thread's own nf entries take one atomic on its count, each partner's entry one on
+// the partner's; all are issued after the search so that their round trips overlap. The order of
+// appends is undone by the sort of the rows kernel.
+__device__ __forceinline__ void md_flush_pairs(int i, int N, int M, const unsigned *list, int nf,
+                                               int *__restrict__ cnt, unsigned *__restrict__ keys) {
+  if (nf == 0) return;
+  const int kept = min(nf, kListCap);
+  const int p0 = atomicAdd(&cnt[i], nf);
+  for (int e = 0; e < kept && p0 + e < M; ++e) keys[(size_t)(p0 + e) * N + i] = list[e * kMdThreads];
+#pragma unroll 4
+  for (int e = 0; e < kept; ++e) {
+    const unsigned key = list[e * kMdThreads];
+    const int j = (int)(key >> 6);
+    const int q = atomicAdd(&cnt[j], 1);
+    if (q < M) keys[(size_t)q * N + j] = ((unsigned)i << 6) | (kWrapNeg - (key & 63u));
   }
-  const float4 ui = u4[i];
-  const int ci2 = mi.w % G.nc[2], ci1 = (mi.w / G.nc[2]) % G.nc[1], ci0 = mi.w / (G.nc[2] * G.nc[1]);
-  int ej[32];
-  int en[32];    // packed shift: (n0+128) << 16 | (n1+128) << 8 | (n2+128)
-  int count = 0;
-  const double xix = pos[3 * i], xiy = pos[3 * i + 1], xiz = pos[3 * i + 2];
-  for (int o0 = -1; o0 <= 1; ++o0) {
-    int a0 = ci0 + o0, w0 = 0;
-    if (a0 < 0) { a0 += G.nc[0]; w0 = -1; } else if (a0 >= G.nc[0]) { a0 -= G.nc[0]; w0 = 1; }
-    for (int o1 = -1; o1 <= 1; ++o1) {
-      int a1 = ci1 + o1, w1 = 0;
-      if (a1 < 0) { a1 += G.nc[1]; w1 = -1; } else if (a1 >= G.nc[1]) { a1 -= G.nc[1]; w1 = 1; }
-      for (int o2 = -1; o2 <= 1; ++o2) {
-        int a2 = ci2 + o2, w2 = 0;
-        if (a2 < 0) { a2 += G.nc[2]; w2 = -1; } else if (a2 >= G.nc[2]) { a2 -= G.nc[2]; w2 = 1; }
-        const int cell = (a0 * G.nc[1] + a1) * G.nc[2] + a2;
-        const int ncell = min(cellcnt[cell], kMdCap);
-        for (int q = 0; q < ncell; ++q) {
-          const int j = cellatoms[cell * kMdCap + q];
-          if (j == i && o0 == 0 && o1 == 0 && o2 == 0) continue;
-          const float4 uj = u4[j];
-          const float v0 = (float)o0 + (uj.x - ui.x), v1 = (float)o1 + (uj.y - ui.y), v2 = (float)o2 + (uj.z - ui.z);
-          const float dx = v0 * G.E[0] + v1 * G.E[3] + v2 * G.E[6];
-          const float dy = v0 * G.E[1] + v1 * G.E[4] + v2 * G.E[7];
-          const float dz = v0 * G.E[2] + v1 * G.E[5] + v2 * G.E[8];
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 > G.cut2_hi) continue;
-          const int4 mj = m4[j];
-          const int n0 = w0 + mi.x - mj.x, n1 = w1 + mi.y - mj.y, n2 = w2 + mi.z - mj.z;
-          bool in = r2 < G.cut2_lo;
-          if (!in) {
-            const ExactPair e = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], xix, xiy, xiz, G.H, n0, n1, n2);
-            in = e.r2 < G.R2sq;
+}
+
+// Neighbour pairs by bricks of 4x4x4 cells: a CTA stages the records of its brick and of the cells
+// around it (6x6x6) in shared memory, in brick coordinates U = u + (halo cell - 1) with the halo
+// cell's periodic wrap packed above the atom index. One thread per atom of the brick tests the half
+// shell: the 13 forward cells (offset d0 = 1; d0 = 0, d1 = 1; d0 = d1 = 0, d2 = 1) and the records
+// after its own in its cell, each pair once. In the stage the three cells along z of one (d0, d1) are
+// consecutive, so the half shell is 5 runs of records. A brick whose surroundings hold more than
+// kStageCap atoms reads the records from global memory, cell by cell.
+__global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
+    int N, const double *__restrict__ pos, const MdGeom G, const int4 *__restrict__ m4,
+    const int *__restrict__ cellcnt, const float4 *__restrict__ cellu, int M, int *__restrict__ cnt,
+    unsigned *__restrict__ keys) {
+  __shared__ float4 s_u[kStageCap];
+  __shared__ unsigned s_list[kListCap * kMdThreads];
+  __shared__ int s_cnt[kHaloCells], s_start[kHaloCells], s_gcell[kHaloCells], s_info[kHaloCells];
+  __shared__ int s_ipre[kBrickCells + 1];
+  __shared__ int s_total;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int nb2 = (G.nc[2] + kBrick - 1) / kBrick, nb1 = (G.nc[1] + kBrick - 1) / kBrick;
+  const int o0 = (blockIdx.x / (nb2 * nb1)) * kBrick, o1 = ((blockIdx.x / nb2) % nb1) * kBrick,
+            o2 = (blockIdx.x % nb2) * kBrick;   // first interior cell of the brick
+  // 1. counts of the halo cells; a halo cell beyond nc is next to no interior cell and stays empty
+  for (int h = tid; h < kHaloCells; h += kMdThreads) {
+    const int h0 = h / (kHaloEdge * kHaloEdge), h1 = (h / kHaloEdge) % kHaloEdge, h2 = h % kHaloEdge;
+    const int c0 = o0 + h0 - 1, c1 = o1 + h1 - 1, c2 = o2 + h2 - 1;
+    int n = 0, g = 0;
+    if (c0 <= G.nc[0] && c1 <= G.nc[1] && c2 <= G.nc[2]) {
+      const int g0 = c0 < 0 ? c0 + G.nc[0] : (c0 >= G.nc[0] ? c0 - G.nc[0] : c0);
+      const int g1 = c1 < 0 ? c1 + G.nc[1] : (c1 >= G.nc[1] ? c1 - G.nc[1] : c1);
+      const int g2 = c2 < 0 ? c2 + G.nc[2] : (c2 >= G.nc[2] ? c2 - G.nc[2] : c2);
+      g = (g0 * G.nc[1] + g1) * G.nc[2] + g2;
+      n = min(cellcnt[g], kMdCap);
+    }
+    s_cnt[h] = n;
+    s_gcell[h] = g;
+    s_info[h] = h0 | (h1 << 3) | (h2 << 6) | (int)(wrap_code(G, c0, c1, c2) << 9);
+  }
+  __syncthreads();
+  // 2. warp 0: exclusive sums over the halo cells (7 per lane) and over the interior cells (2 per lane)
+  if (tid < 32) {
+    int a[7], tot = 0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int h = 7 * lane + k;
+      a[k] = h < kHaloCells ? s_cnt[h] : 0;
+      tot += a[k];
+    }
+    int inc = tot;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, off);
+      if (lane >= off) inc += v;
+    }
+    int run = inc - tot;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int h = 7 * lane + k;
+      if (h < kHaloCells) s_start[h] = run;
+      run += a[k];
+    }
+    if (lane == 31) s_total = inc;
+    int b[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int q = 2 * lane + k, q0 = q / (kBrick * kBrick), q1 = (q / kBrick) % kBrick, q2 = q % kBrick;
+      const bool in = o0 + q0 < G.nc[0] && o1 + q1 < G.nc[1] && o2 + q2 < G.nc[2];
+      b[k] = in ? s_cnt[((q0 + 1) * kHaloEdge + q1 + 1) * kHaloEdge + q2 + 1] : 0;
+    }
+    const int t2 = b[0] + b[1];
+    int inc2 = t2;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc2, off);
+      if (lane >= off) inc2 += v;
+    }
+    s_ipre[2 * lane] = inc2 - t2;
+    s_ipre[2 * lane + 1] = inc2 - t2 + b[0];
+    if (lane == 31) s_ipre[kBrickCells] = inc2;
+  }
+  __syncthreads();
+  // 3. stage the records, one thread per record (its cell by binary search over the starts)
+  const int total = s_total;
+  const bool staged = total <= kStageCap;
+  if (staged) {
+    for (int t = tid; t < total; t += kMdThreads) {
+      int h = 0;
+      for (int step = 128; step > 0; step >>= 1)
+        if (h + step < kHaloCells && s_start[h + step] <= t) h += step;
+      const int info = s_info[h];
+      const float4 r = cellu[s_gcell[h] * kMdCap + (t - s_start[h])];
+      s_u[t] = make_float4(r.x + (float)((info & 7) - 1), r.y + (float)(((info >> 3) & 7) - 1),
+                           r.z + (float)(((info >> 6) & 7) - 1),
+                           __int_as_float(__float_as_int(r.w) | ((info >> 9) << 24)));
+    }
+  } else {
+    for (int h = tid; h < kHaloCells; h += kMdThreads) s_start[h] = s_gcell[h] * kMdCap;
+  }
+  __syncthreads();
+  // 4. one thread per atom of the brick
+  const int A = s_ipre[kBrickCells];
+  unsigned *list = s_list + tid;
+  for (int a = tid; a < A; a += kMdThreads) {
+    int k = 0;                                     // interior cell of atom a
+    for (int step = kBrickCells / 2; step > 0; step >>= 1)
+      if (s_ipre[k + step] <= a) k += step;
+    const int k0 = k / (kBrick * kBrick), k1 = (k / kBrick) % kBrick, k2 = k % kBrick;
+    const int hi = ((k0 + 1) * kHaloEdge + k1 + 1) * kHaloEdge + k2 + 1;
+    const int own = a - s_ipre[k];
+    if (staged) {
+      const int slot = s_start[hi] + own;
+      const float4 ei = s_u[slot];
+      const int i = __float_as_int(ei.w) & 0xffffff;
+      int run = 0, p = 0, pend = 0, nf = 0;
+      for (;;) {
+        while (p >= pend && run < 5) {
+          if (run < 4) {                           // (d0, d1) = (1,-1), (1,0), (1,1), (0,1)
+            const int h = hi + (run < 3 ? (kHaloEdge + run - 1) : 1) * kHaloEdge;
+            p = s_start[h - 1];
+            pend = s_start[h + 1] + s_cnt[h + 1];
+          } else {                                 // rest of the own cell, then (0, 0, 1)
+            p = slot + 1;
+            pend = s_start[hi + 1] + s_cnt[hi + 1];
           }
-          if (!in) continue;
-          if (count < 32) {
-            ej[count] = j;
-            en[count] = ((n0 + 128) << 16) | ((n1 + 128) << 8) | (n2 + 128);
-          }
-          ++count;
+          ++run;
+        }
+        if (p >= pend) break;
+        const float4 ej = s_u[p++];
+        const unsigned tag = (unsigned)__float_as_int(ej.w);
+        const int j = (int)(tag & 0xffffffu);
+        if (md_pair_in(G, pos, m4, i, j, tag >> 24, ej.x - ei.x, ej.y - ei.y, ej.z - ei.z)) {
+          if (nf < kListCap) list[nf * kMdThreads] = (tag & 0xffffffu) << 6 | (tag >> 24);
+          ++nf;
         }
       }
-    }
-  }
-  cnt_out[i] = count;
-  if (count > M) {
-    set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
-    count = M;
-  }
-  // canonical order: ascending (j, n0, n1, n2); the packed shift sorts like (n0, n1, n2)
-  for (int a = 1; a < count; ++a) {
-    const int kj = ej[a], kn = en[a];
-    int b = a - 1;
-    while (b >= 0 && (ej[b] > kj || (ej[b] == kj && en[b] > kn))) {
-      ej[b + 1] = ej[b];
-      en[b + 1] = en[b];
-      --b;
-    }
-    ej[b + 1] = kj;
-    en[b + 1] = kn;
-  }
-  for (int e = 0; e < M; ++e) {
-    if (e < count) {
-      nbr[(size_t)i * M + e] = ej[e];
-      shift[(size_t)i * M + e] = make_char4((signed char)(((en[e] >> 16) & 255) - 128),
-                                            (signed char)(((en[e] >> 8) & 255) - 128),
-                                            (signed char)((en[e] & 255) - 128), 0);
+      md_flush_pairs(i, N, M, list, nf, cnt, keys);
     } else {
-      nbr[(size_t)i * M + e] = -1;
-      shift[(size_t)i * M + e] = make_char4(0, 0, 0, 0);
+      const float4 ei = cellu[s_start[hi] + own];
+      const int i = __float_as_int(ei.w);
+      int nf = 0;
+      for (int l = 0; l < 14; ++l) {
+        // l < 9: d0 = 1; l < 12: d0 = 0, d1 = 1; l = 12: (0, 0, 1); l = 13: own cell after own record
+        const int d0 = l < 9 ? 1 : 0, d1 = l < 9 ? l / 3 - 1 : (l < 12 ? 1 : 0),
+                  d2 = l < 9 ? l % 3 - 1 : (l < 12 ? l - 10 : (l == 12 ? 1 : 0));
+        const int h = hi + (d0 * kHaloEdge + d1) * kHaloEdge + d2;
+        const unsigned code = wrap_code(G, o0 + k0 + d0, o1 + k1 + d1, o2 + k2 + d2);
+        const int n = s_cnt[h], st = s_start[h];
+        for (int q = l == 13 ? own + 1 : 0; q < n; ++q) {
+          const float4 ej = cellu[st + q];
+          const int j = __float_as_int(ej.w);
+          if (md_pair_in(G, pos, m4, i, j, code, (float)d0 + (ej.x - ei.x), (float)d1 + (ej.y - ei.y),
+                         (float)d2 + (ej.z - ei.z))) {
+            if (nf < kListCap) list[nf * kMdThreads] = ((unsigned)j << 6) | code;
+            ++nf;
+          }
+        }
+      }
+      md_flush_pairs(i, N, M, list, nf, cnt, keys);
     }
   }
 }
 
-// Reverse entry of every bond as a slot of the [N][kMdMaxM] partial-force array.
-__global__ void md_reverse_kernel(int N, int M, const int *__restrict__ cnt, const int *__restrict__ nbr,
-                                  const char4 *__restrict__ shift, int *__restrict__ rev, unsigned *status) {
+__device__ __forceinline__ void cas(unsigned &a, unsigned &b) {
+  const unsigned lo = min(a, b), hi = max(a, b);
+  a = lo;
+  b = hi;
+}
+
+// Entry (j, n) of a key (j << 6 | wrap code), n = wrap + m_i - m_j.
+__device__ __forceinline__ void md_write_entry(const int4 *__restrict__ m4, int4 mi, unsigned key, size_t at,
+                                               int *__restrict__ nbr, char4 *__restrict__ shift) {
+  const int j = (int)(key >> 6);
+  const int4 mj = m4[j];
+  nbr[at] = j;
+  shift[at] = make_char4((signed char)((int)((key >> 4) & 3) - 1 + mi.x - mj.x),
+                         (signed char)((int)((key >> 2) & 3) - 1 + mi.y - mj.y),
+                         (signed char)((int)(key & 3) - 1 + mi.z - mj.z), 0);
+}
+
+// One thread per atom: the appended keys in ascending (j, n) order (for one j the shift is the wrap
+// plus a constant, so both orders agree) as the list (j, n); for an atom with at most kMdMaxM entries
+// also the slot of each reverse bond in the partner's list, i.e. the rank of (i, -wrap) among the
+// partner's keys.
+__global__ void md_rows_kernel(int N, int M, const int4 *__restrict__ m4, const int *__restrict__ cnt,
+                               const unsigned *__restrict__ keys, int *__restrict__ nbr,
+                               char4 *__restrict__ shift, int *__restrict__ rev, unsigned *status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int m = min(cnt[i], M);
-  for (int e = 0; e < m && e < kMdMaxM; ++e) {
-    const int j = nbr[(size_t)i * M + e];
-    const char4 n = shift[(size_t)i * M + e];
-    const int mj = min(cnt[j], M);
-    int found = -1;
-    for (int f = 0; f < mj; ++f) {
-      const char4 q = shift[(size_t)j * M + f];
-      if (nbr[(size_t)j * M + f] == i && q.x == -n.x && q.y == -n.y && q.z == -n.z) {
-        found = f;
-        break;
+  const int count = cnt[i];
+  if (count > M) set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+  const int c = min(count, M);
+  const int4 mi = m4[i];
+  const unsigned *row = keys + i;                // entry e at row[e * N]
+  if (c <= kMdMaxM) {
+    unsigned k[kMdMaxM];
+#pragma unroll
+    for (int e = 0; e < kMdMaxM; ++e) k[e] = e < c ? row[(size_t)e * N] : 0xffffffffu;
+    // Batcher's odd-even merge sort of 8 keys (19 compare-exchanges)
+    cas(k[0], k[1]); cas(k[2], k[3]); cas(k[4], k[5]); cas(k[6], k[7]);
+    cas(k[0], k[2]); cas(k[1], k[3]); cas(k[4], k[6]); cas(k[5], k[7]);
+    cas(k[1], k[2]); cas(k[5], k[6]);
+    cas(k[0], k[4]); cas(k[1], k[5]); cas(k[2], k[6]); cas(k[3], k[7]);
+    cas(k[2], k[4]); cas(k[3], k[5]);
+    cas(k[1], k[2]); cas(k[3], k[4]); cas(k[5], k[6]);
+#pragma unroll
+    for (int e = 0; e < kMdMaxM; ++e) {
+      if (e < c) {
+        md_write_entry(m4, mi, k[e], (size_t)e * N + i, nbr, shift);
+        const int j = (int)(k[e] >> 6);
+        const int cj = min(cnt[j], M);
+        int slot = e * N + i;                      // partner beyond kMdMaxM: flagged by the force kernel
+        if (cj <= kMdMaxM) {
+          const unsigned want = ((unsigned)i << 6) | (kWrapNeg - (k[e] & 63u));
+          const unsigned *rj = keys + j;
+          int rank = 0;
+          bool found = false;
+#pragma unroll
+          for (int f = 0; f < kMdMaxM; ++f) {
+            if (f < cj) {
+              const unsigned q = rj[(size_t)f * N];
+              rank += q < want ? 1 : 0;
+              found = found || q == want;
+            }
+          }
+          if (!found) {
+            set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+            rank = 0;
+          }
+          slot = rank * N + j;
+        }
+        rev[(size_t)e * N + i] = slot;
       }
     }
-    if (found < 0 || found >= kMdMaxM) {
-      set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
-      found = 0;
+  } else {
+    for (int e = 0; e < c; ++e) {                  // more than kMdMaxM entries: rank by counting
+      const unsigned key = row[(size_t)e * N];
+      int rank = 0;
+      for (int f = 0; f < c; ++f) rank += row[(size_t)f * N] < key ? 1 : 0;
+      md_write_entry(m4, mi, key, (size_t)rank * N + i, nbr, shift);
     }
-    rev[(size_t)i * kMdMaxM + e] = j * kMdMaxM + found;
+#pragma unroll
+    for (int e = 0; e < kMdMaxM; ++e) rev[(size_t)e * N + i] = e * N + i;
   }
 }
 
@@ -260,7 +453,7 @@ __device__ __forceinline__ void md_atom(const R (&ux)[kMdMaxM], const R (&uy)[kM
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kMdThreads) md_force_kernel(
+__global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 4 : 1) md_force_kernel(
     int N, int M, const MdGeom G, const PConsts<R> K, const double *__restrict__ pos,
     const float4 *__restrict__ u4, const int4 *__restrict__ m4, const int *__restrict__ cnt,
     const int *__restrict__ nbr, const char4 *__restrict__ shift, typename Vec4<R>::T *__restrict__ Pst,
@@ -269,7 +462,7 @@ __global__ void __launch_bounds__(kMdThreads) md_force_kernel(
   __shared__ double red[kMdThreads / 32][7];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < N;
-  int m = valid ? cnt[i] : 0;
+  int m = valid ? min(cnt[i], M) : 0;   // a truncated list (count > M) is flagged; its row holds M entries
   if (m > kMdMaxM) {
     set_status(status, TERSOFF_STATUS_MANY_NBRS);
     m = 0;
@@ -286,8 +479,8 @@ __global__ void __launch_bounds__(kMdThreads) md_force_kernel(
   for (int e = 0; e < kMdMaxM; ++e) {
     ux[e] = R(0); uy[e] = R(0); uz[e] = R(0); r[e] = R(1); ir[e] = R(0); fc[e] = R(0); fcp[e] = R(0);
     if (e < m) {
-      const int j = nbr[(size_t)i * M + e];
-      const char4 n = shift[(size_t)i * M + e];
+      const int j = nbr[(size_t)e * N + i];
+      const char4 n = shift[(size_t)e * N + i];
       R dx, dy, dz;
       if constexpr (sizeof(R) == 4) {
         // cell offset of j's image relative to i's cell, then the in-cell FP32 construction
@@ -313,19 +506,22 @@ __global__ void __launch_bounds__(kMdThreads) md_force_kernel(
       ux[e] = dx * ir[e];
       uy[e] = dy * ir[e];
       uz[e] = dz * ir[e];
-      if (rr <= (R)G.R1) {
-        fc[e] = R(1);
-      } else if (rr < (R)G.R2) {
-        const R w = (rr - (R)G.R1) / (R)(G.R2 - G.R1);
-        if constexpr (sizeof(R) == 4) {
+      if constexpr (sizeof(R) == 4) {
+        if (rr <= G.R1f) {
+          fc[e] = 1.f;
+        } else if (rr < G.R2f) {
+          const float w = (rr - G.R1f) * G.inv_wf;
           fc[e] = 0.5f * (1.f + cospif(w));
-          fcp[e] = (float)(-0.5 * M_PI / (G.R2 - G.R1)) * sinpif(w);
-        } else {
-          fc[e] = 0.5 * (1.0 + cospi(w));
-          fcp[e] = -0.5 * M_PI / (G.R2 - G.R1) * sinpi(w);
+          fcp[e] = G.fcp_kf * sinpif(w);
         }
       } else {
-        fc[e] = R(0);
+        if (rr <= G.R1) {
+          fc[e] = 1.0;
+        } else if (rr < G.R2) {
+          const double w = (rr - G.R1) * G.inv_w;
+          fc[e] = 0.5 * (1.0 + cospi(w));
+          fcp[e] = G.fcp_k * sinpi(w);
+        }
       }
     }
   }
@@ -351,30 +547,22 @@ __global__ void __launch_bounds__(kMdThreads) md_force_kernel(
       v.y = Py[e];
       v.z = Pz[e];
       v.w = R(0);
-      Pst[(size_t)i * kMdMaxM + e] = v;
+      Pst[(size_t)e * N + i] = v;
     }
-  // per-block FP64 partial sums of U and W
-  double v[7] = {(double)U, (double)Wv[0], (double)Wv[1], (double)Wv[2], (double)Wv[3], (double)Wv[4], (double)Wv[5]};
+  // per-warp sums in R, per-block FP64 partial sums of U and W, stored [7][blocks]
+  R v[7] = {U, Wv[0], Wv[1], Wv[2], Wv[3], Wv[4], Wv[5]};
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    float f = (float)v[k];
-    if constexpr (sizeof(R) == 8) {
-      double d = v[k];
-      for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
-      v[k] = d;
-    } else {
-      for (int off = 16; off > 0; off >>= 1) f += __shfl_xor_sync(0xffffffffu, f, off);
-      v[k] = (double)f;
-    }
-  }
+  for (int k = 0; k < 7; ++k)
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
   const int warp = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0)
-    for (int k = 0; k < 7; ++k) red[warp][k] = v[k];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) red[warp][k] = (double)v[k];
   __syncthreads();
   if (threadIdx.x < 7) {
     double s = 0.0;
     for (int w = 0; w < kMdThreads / 32; ++w) s += red[w][threadIdx.x];
-    partial[(size_t)blockIdx.x * 7 + threadIdx.x] = s;
+    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
   }
 }
 
@@ -386,8 +574,8 @@ __global__ void md_gather_kernel(int N, int M, const int *__restrict__ cnt, cons
   const int m = min(min(cnt[i], M), kMdMaxM);
   R Fx = R(0), Fy = R(0), Fz = R(0);
   for (int e = 0; e < m; ++e) {
-    const auto a = Pst[(size_t)i * kMdMaxM + e];
-    const auto b = Pst[rev[(size_t)i * kMdMaxM + e]];
+    const auto a = Pst[(size_t)e * N + i];
+    const auto b = Pst[rev[(size_t)e * N + i]];
     Fx += a.x - b.x;
     Fy += a.y - b.y;
     Fz += a.z - b.z;
@@ -397,16 +585,28 @@ __global__ void md_gather_kernel(int N, int M, const int *__restrict__ cnt, cons
   F[3 * (size_t)i + 2] = Fz;
 }
 
-// Sum of the per-block partials in a fixed order (one warp per quantity).
-__global__ void md_reduce_kernel(int nblocks, const double *__restrict__ partial, double *E, double *W) {
-  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (k >= 7) return;
-  double s = 0.0;
-  for (int b = lane; b < nblocks; b += 32) s += partial[(size_t)b * 7 + k];
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) {
-    if (k == 0) *E = s;
-    else W[k - 1] = s;
+// Sum of the per-block partials [7][nblocks] in a fixed order: a strided sum per thread, then the
+// warps' and the block's sums in lane and warp order.
+constexpr int kMdReduceThreads = 1024;
+__global__ void __launch_bounds__(kMdReduceThreads) md_reduce_kernel(int nblocks, const double *__restrict__ partial,
+                                                                      double *E, double *W) {
+  __shared__ double red[kMdReduceThreads / 32][7];
+  double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += kMdReduceThreads)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc[k] += partial[(size_t)k * nblocks + b];
+#pragma unroll
+  for (int k = 0; k < 7; ++k)
+    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) red[threadIdx.x >> 5][k] = acc[k];
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double s = 0.0;
+    for (int w = 0; w < kMdReduceThreads / 32; ++w) s += red[w][threadIdx.x];
+    if (threadIdx.x == 0) *E = s;
+    else W[threadIdx.x - 1] = s;
   }
 }
 
@@ -449,9 +649,20 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   }
   // FP32 distance error <= a few ulp of the cell edge lengths; the band is 64x wider
   const double margin = 64.0 * 1.2e-7 * esum * 2.0 * R2 + 1e-6;
+  G.diag = 1;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      if (a != b && (H[3 * a + b] != 0.0 || G.Hinv[3 * a + b] != 0.0)) G.diag = 0;
+  for (int k = 0; k < 3; ++k) G.ncd[k] = (double)G.nc[k];
   G.R1 = R1;
   G.R2 = R2;
   G.R2sq = R2 * R2;
+  G.inv_w = 1.0 / (R2 - R1);
+  G.fcp_k = -0.5 * M_PI / (R2 - R1);
+  G.R1f = (float)R1;
+  G.R2f = (float)R2;
+  G.inv_wf = (float)G.inv_w;
+  G.fcp_kf = (float)G.fcp_k;
   G.cut2_lo = (float)(R2 * R2 - margin);
   G.cut2_hi = (float)(R2 * R2 + margin);
   const long ncells = (long)G.nc[0] * G.nc[1] * G.nc[2];
@@ -461,9 +672,10 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   }
   const int nblk = (N + kMdThreads - 1) / kMdThreads;
   const size_t rs = precision == 64 ? 8 : 4;
-  if (c.md_cellcnt.ensure(ncells * sizeof(int)) || c.md_cells.ensure(ncells * kMdCap * sizeof(int)) ||
+  if (c.md_cellcnt.ensure(ncells * sizeof(int)) || c.md_cells.ensure(ncells * kMdCap * sizeof(float4)) ||
       c.md_pos.ensure((size_t)N * (sizeof(float4) + sizeof(int4))) || c.md_cnt.ensure((size_t)N * sizeof(int)) ||
       c.md_nbr.ensure((size_t)N * M * sizeof(int)) || c.md_shift.ensure((size_t)N * M * sizeof(char4)) ||
+      c.md_keys.ensure((size_t)N * M * sizeof(unsigned)) ||
       c.md_rev.ensure((size_t)N * kMdMaxM * sizeof(int)) || c.md_Pij.ensure((size_t)N * kMdMaxM * 4 * rs) ||
       c.md_red.ensure((size_t)nblk * 7 * sizeof(double))) {
     err = "device allocation failed";
@@ -475,12 +687,14 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   int4 *m4 = reinterpret_cast<int4 *>(u4 + N);
   unsigned *st = c.status.as<unsigned>();
   cudaMemsetAsync(c.md_cellcnt.p, 0, ncells * sizeof(int), s);
-  md_cells_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, c.md_cellcnt.as<int>(), c.md_cells.as<int>(), u4, m4, st);
-  md_neighbors_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, u4, m4, c.md_cellcnt.as<int>(), c.md_cells.as<int>(),
-                                                  M, c.md_cnt.as<int>(), c.md_nbr.as<int>(),
-                                                  c.md_shift.as<char4>(), st);
-  md_reverse_kernel<<<nblk, kMdThreads, 0, s>>>(N, M, c.md_cnt.as<int>(), c.md_nbr.as<int>(),
-                                                c.md_shift.as<char4>(), c.md_rev.as<int>(), st);
+  md_cells_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(), u4, m4,
+                                              c.md_cnt.as<int>(), st);
+  const long nbricks = (long)((G.nc[0] + kBrick - 1) / kBrick) * ((G.nc[1] + kBrick - 1) / kBrick) *
+                       ((G.nc[2] + kBrick - 1) / kBrick);
+  md_pairs_kernel<<<(unsigned)nbricks, kMdThreads, 0, s>>>(N, pos, G, m4, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(),
+                                                           M, c.md_cnt.as<int>(), c.md_keys.as<unsigned>());
+  md_rows_kernel<<<nblk, kMdThreads, 0, s>>>(N, M, m4, c.md_cnt.as<int>(), c.md_keys.as<unsigned>(),
+                                             c.md_nbr.as<int>(), c.md_shift.as<char4>(), c.md_rev.as<int>(), st);
   const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
   const double log2e = 1.4426950408889634;
   if (precision == 64) {
@@ -499,8 +713,8 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
     md_gather_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, c.md_cnt.as<int>(), c.md_rev.as<int>(),
                                                         c.md_Pij.as<float4>(), reinterpret_cast<float *>(F));
   }
-  md_reduce_kernel<<<1, 7 * 32, 0, s>>>(nblk, c.md_red.as<double>(), E, W);
-  cudaError_t e = launched(6);   // cells, neighbours, reverse, force, gather, reduce
+  md_reduce_kernel<<<1, kMdReduceThreads, 0, s>>>(nblk, c.md_red.as<double>(), E, W);
+  cudaError_t e = launched(6);   // cells, pairs, rows, force, gather, reduce
   if (e != cudaSuccess) {
     err = std::string("CUDA error: ") + cudaGetErrorString(e);
     return TERSOFF_E_CUDA;

@@ -114,3 +114,39 @@ def test_md_rejects_small_box(ctx):
     with pytest.raises(binding.TersoffError) as ei:
         ctx.md_force(torch.tensor(pos, device="cuda"), box, I.TABLE2_PARAMS)
     assert ei.value.code == binding.E_ARG
+
+
+def test_md_neighbor_lists_wide_cutoff_read_from_global(ctx):
+    """R2 = 5 A in a 4x4x4 diamond cell: the cells are the conventional cells (8 atoms each), so the
+    surroundings of a brick of cells hold more atoms than the shared-memory stage and the records are
+    read from global memory; lists of 28 entries. The force kernel flags more than 8 neighbours and
+    nothing else."""
+    from paper_1909_11474_gb300 import binding
+    pos, box = _cell((4, 4, 4), 0.05, 0.0, 9)
+    ctx.md_force(torch.tensor(pos, device="cuda"), box, I.TABLE2_PARAMS, R1=4.6, R2=5.0, max_nbr=32)
+    assert ctx.get_status() == binding.STATUS_MANY_NBRS
+    cnt, nbr, shift = ctx.md_export_neighbors()
+    nl = oracle.neighbor_list(pos, box, 5.0)
+    assert (np.diff(nl["off"]) == 28).all()
+    for i in range(len(pos)):
+        e = slice(nl["off"][i], nl["off"][i + 1])
+        assert cnt[i] == nl["off"][i + 1] - nl["off"][i]
+        assert np.array_equal(nbr[i, :cnt[i]], nl["j"][e])
+        assert np.array_equal(shift[i, :cnt[i]], nl["n"][e])
+
+
+def test_md_short_lists_flag_overflow_and_count_every_neighbour(ctx):
+    """max_nbr = 2 with 4 neighbours per atom: the overflow bit is set, the true count is returned and
+    the kept entries are true neighbours in ascending order (which of them are kept is unspecified)."""
+    from paper_1909_11474_gb300 import binding
+    pos, box = _cell((3, 3, 3), 0.08, 0.0, 3)
+    ctx.md_force(torch.tensor(pos, device="cuda"), box, I.TABLE2_PARAMS, max_nbr=2)
+    assert ctx.get_status() & binding.STATUS_NBR_OVERFLOW
+    cnt, nbr, shift = ctx.md_export_neighbors()
+    nl = oracle.neighbor_list(pos, box, 3.2)
+    for i in range(len(pos)):
+        e = slice(nl["off"][i], nl["off"][i + 1])
+        assert cnt[i] == nl["off"][i + 1] - nl["off"][i]
+        full = {(int(j), tuple(n)) for j, n in zip(nl["j"][e], nl["n"][e])}
+        kept = [(int(j), tuple(n)) for j, n in zip(nbr[i], shift[i])]
+        assert all(k in full for k in kept) and kept == sorted(kept)
