@@ -1,14 +1,16 @@
 // md.cu -- MD-scale force call: one large periodic cell, one parameter set, neighbour rebuild by a
 // cell list plus energy, forces and virial (Eq. 1-14 of arXiv:1909.11474), every call.
 //
-// Coordinates. Every atom's fractional coordinate s = x H^-1 is split, in FP64, into an integer
-// wrap m = floor(s), a cell index c = floor((s - m) nc) and an in-cell coordinate u = (s - m) nc - c
-// in [0, 1), stored in FP32. A bond to an atom of a neighbouring cell (offset o in {-1,0,1}^3) is then
-// d = sum_k (o_k + u_j,k - u_i,k) E_k with the cell edge vectors E_k = H_k / nc_k, all in FP32 and
-// accurate to ~1e-6 A whatever the box size; its image shift is n = kw + m_i - m_j (kw = the
-// periodic wrap of the neighbouring cell). Neighbour membership uses this FP32 distance where it is
-// farther than a rounding margin from R2, and the exact FP64 test of the batched build otherwise, so
-// the lists equal the batched build's bit for bit; they are sorted to the same (j, n) order.
+// Coordinates. Every atom's cell coordinate w = x H^-1 nc is split, in FP64, into its floor C and an
+// in-cell coordinate u = w - C in [0, 1), stored in FP32, and C into an integer wrap m and a cell
+// index c (C = m nc + c). The force kernel builds a bond to an atom of a neighbouring cell (offset o
+// in {-1,0,1}^3) as d = sum_k (o_k + u_j,k - u_i,k) E_k with the cell edge vectors E_k = H_k / nc_k,
+// all in FP32 and accurate to ~1e-6 A whatever the box size; its image shift is n = kw + m_i - m_j
+// (kw = the periodic wrap of the neighbouring cell). The pair search works in Cartesian coordinates
+// relative to a brick of cells (a few cell edges long, so equally accurate). Membership uses the FP32
+// distance where it is farther than a rounding margin from R2, and the exact FP64 test of the batched
+// build otherwise, so the lists equal the batched build's bit for bit; they are sorted to the same
+// (j, n) order.
 #include <math.h>
 
 #include <algorithm>
@@ -29,13 +31,12 @@ constexpr int kHaloEdge = kBrick + 2;                          // brick plus one
 constexpr int kHaloCells = kHaloEdge * kHaloEdge * kHaloEdge;  // 216
 constexpr int kBrickCells = kBrick * kBrick * kBrick;          // 64
 constexpr int kStageCap = 1024;                                // halo atoms staged in shared memory
-constexpr int kListCap = 32;                                   // list entries kept per atom (max_nbr <= 32)
 
 struct MdGeom {
   double H[9], Hinv[9];
   int nc[3];
-  int diag;                   // H (and so H^-1) diagonal: fractional coordinates need 3 products, not 9
-  double ncd[3];
+  int diag;                   // H (and so H^-1) diagonal: cell coordinates need 3 products, not 9
+  double Hn[9];               // H^-1 with column k scaled by nc_k: x Hn = cell coordinates
   float E[9];                 // cell edge vectors, row k = H_k / nc_k
   float cut2_lo, cut2_hi;     // FP32 decision band around R2^2
   double R1, R2, R2sq;
@@ -54,7 +55,17 @@ __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdG
   if (i >= N) return;
   cnt[i] = 0;
   const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-  if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+  // per dimension: the cell coordinate w = s nc (nc folded into the inverse box), its floor C, the
+  // in-cell coordinate u = w - C (exact in FP64), and the integer split C = m nc + c
+  double w[3];
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    w[k] = G.diag ? (k == 0 ? x : (k == 1 ? y : z)) * G.Hn[4 * k]
+                  : x * G.Hn[k] + y * G.Hn[3 + k] + z * G.Hn[6 + k];
+    ok = ok && fabs(w[k]) < 1e9;                   // false for NaN and inf
+  }
+  if (!ok) {
     set_status(status, TERSOFF_STATUS_NONFINITE);
     u4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     m4[i] = make_int4(0, 0, 0, 0);
@@ -64,15 +75,12 @@ __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdG
   float uu[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double s = G.diag ? (k == 0 ? x : (k == 1 ? y : z)) * G.Hinv[4 * k]
-                            : x * G.Hinv[k] + y * G.Hinv[3 + k] + z * G.Hinv[6 + k];
-    const double f = floor(s);
-    const double w = (s - f) * G.ncd[k];          // in [0, nc]: truncation is the floor
-    int c = (int)w;
-    c = c >= G.nc[k] ? G.nc[k] - 1 : c;
-    mm[k] = (int)f;
-    cc[k] = c;
-    uu[k] = (float)(w - (double)c);
+    const double C = floor(w[k]);
+    uu[k] = (float)(w[k] - C);
+    const int Ci = (int)C, n = G.nc[k];
+    const int m = Ci >= 0 ? Ci / n : -((n - 1 - Ci) / n);
+    mm[k] = m;
+    cc[k] = Ci - m * n;
   }
   const int cell = (cc[0] * G.nc[1] + cc[1]) * G.nc[2] + cc[2];
   u4[i] = make_float4(uu[0], uu[1], uu[2], 0.f);
@@ -91,15 +99,12 @@ __device__ __forceinline__ unsigned wrap_code(const MdGeom &G, int c0, int c1, i
 }
 constexpr unsigned kWrapNeg = 42u;
 
-// One candidate pair at cell-unit separation v: the FP32 distance decides outside the rounding band,
-// the exact FP64 test inside it. The test is symmetric (the FP64 separation of (j, i, -n) is exactly
-// the negated one of (i, j, n)), so deciding a pair once decides both of its entries.
+// One candidate pair at Cartesian separation d (FP32): the FP32 distance decides outside the
+// rounding band, the exact FP64 test inside it. The test is symmetric (the FP64 separation of
+// (j, i, -n) is exactly the negated one of (i, j, n)), so deciding a pair once decides both entries.
 __device__ __forceinline__ bool md_pair_in(const MdGeom &G, const double *__restrict__ pos,
                                            const int4 *__restrict__ m4, int i, int j, unsigned code,
-                                           float v0, float v1, float v2) {
-  const float dx = v0 * G.E[0] + v1 * G.E[3] + v2 * G.E[6];
-  const float dy = v0 * G.E[1] + v1 * G.E[4] + v2 * G.E[7];
-  const float dz = v0 * G.E[2] + v1 * G.E[5] + v2 * G.E[8];
+                                           float dx, float dy, float dz) {
   const float r2 = dx * dx + dy * dy + dz * dz;
   if (r2 > G.cut2_hi) return false;
   if (r2 < G.cut2_lo) return true;
@@ -110,14 +115,22 @@ __device__ __forceinline__ bool md_pair_in(const MdGeom &G, const double *__rest
   return e.r2 < G.R2sq;
 }
 
+// Cartesian vector of a separation v in cell units: v0 E_0 + v1 E_1 + v2 E_2.
+__device__ __forceinline__ float3 md_cart(const MdGeom &G, float v0, float v1, float v2) {
+  return make_float3(v0 * G.E[0] + v1 * G.E[3] + v2 * G.E[6], v0 * G.E[1] + v1 * G.E[4] + v2 * G.E[7],
+                     v0 * G.E[2] + v1 * G.E[5] + v2 * G.E[8]);
+}
+
 // The entries of the pairs one thread accepted, keys (partner << 6 | wrap code) in slot-major
 // [M][N] rows: the thread's own nf entries take one atomic on its count, each partner's entry one on
 // the partner's; all are issued after the search so that their round trips overlap. The order of
-// appends is undone by the sort of the rows kernel.
+// appends is undone by the sort of the rows kernel. A thread keeps at most kFwdCap pairs: more means
+// more than max_nbr (<= 32) neighbours, which the count records and the rows kernel flags.
+constexpr int kFwdCap = 32;
 __device__ __forceinline__ void md_flush_pairs(int i, int N, int M, const unsigned *list, int nf,
                                                int *__restrict__ cnt, unsigned *__restrict__ keys) {
   if (nf == 0) return;
-  const int kept = min(nf, kListCap);
+  const int kept = min(nf, kFwdCap);
   const int p0 = atomicAdd(&cnt[i], nf);
   for (int e = 0; e < kept && p0 + e < M; ++e) keys[(size_t)(p0 + e) * N + i] = list[e * kMdThreads];
 #pragma unroll 4
@@ -130,8 +143,8 @@ __device__ __forceinline__ void md_flush_pairs(int i, int N, int M, const unsign
 }
 
 // Neighbour pairs by bricks of 4x4x4 cells: a CTA stages the records of its brick and of the cells
-// around it (6x6x6) in shared memory, in brick coordinates U = u + (halo cell - 1) with the halo
-// cell's periodic wrap packed above the atom index. One thread per atom of the brick tests the half
+// around it (6x6x6) in shared memory, as Cartesian brick coordinates X = (u + halo cell - 1) E with
+// the halo cell's periodic wrap packed above the atom index. One thread per atom of the brick tests the half
 // shell: the 13 forward cells (offset d0 = 1; d0 = 0, d1 = 1; d0 = d1 = 0, d2 = 1) and the records
 // after its own in its cell, each pair once. In the stage the three cells along z of one (d0, d1) are
 // consecutive, so the half shell is 5 runs of records. A brick whose surroundings hold more than
@@ -141,7 +154,7 @@ __global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
     const int *__restrict__ cellcnt, const float4 *__restrict__ cellu, int M, int *__restrict__ cnt,
     unsigned *__restrict__ keys) {
   __shared__ float4 s_u[kStageCap];
-  __shared__ unsigned s_list[kListCap * kMdThreads];
+  __shared__ unsigned s_list[kFwdCap * kMdThreads];
   __shared__ int s_cnt[kHaloCells], s_start[kHaloCells], s_gcell[kHaloCells], s_info[kHaloCells];
   __shared__ int s_ipre[kBrickCells + 1];
   __shared__ int s_total;
@@ -216,9 +229,9 @@ __global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
         if (h + step < kHaloCells && s_start[h + step] <= t) h += step;
       const int info = s_info[h];
       const float4 r = cellu[s_gcell[h] * kMdCap + (t - s_start[h])];
-      s_u[t] = make_float4(r.x + (float)((info & 7) - 1), r.y + (float)(((info >> 3) & 7) - 1),
-                           r.z + (float)(((info >> 6) & 7) - 1),
-                           __int_as_float(__float_as_int(r.w) | ((info >> 9) << 24)));
+      const float3 X = md_cart(G, r.x + (float)((info & 7) - 1), r.y + (float)(((info >> 3) & 7) - 1),
+                               r.z + (float)(((info >> 6) & 7) - 1));
+      s_u[t] = make_float4(X.x, X.y, X.z, __int_as_float(__float_as_int(r.w) | ((info >> 9) << 24)));
     }
   } else {
     for (int h = tid; h < kHaloCells; h += kMdThreads) s_start[h] = s_gcell[h] * kMdCap;
@@ -256,7 +269,7 @@ __global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
         const unsigned tag = (unsigned)__float_as_int(ej.w);
         const int j = (int)(tag & 0xffffffu);
         if (md_pair_in(G, pos, m4, i, j, tag >> 24, ej.x - ei.x, ej.y - ei.y, ej.z - ei.z)) {
-          if (nf < kListCap) list[nf * kMdThreads] = (tag & 0xffffffu) << 6 | (tag >> 24);
+          if (nf < kFwdCap) list[nf * kMdThreads] = (tag & 0xffffffu) << 6 | (tag >> 24);
           ++nf;
         }
       }
@@ -275,9 +288,9 @@ __global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
         for (int q = l == 13 ? own + 1 : 0; q < n; ++q) {
           const float4 ej = cellu[st + q];
           const int j = __float_as_int(ej.w);
-          if (md_pair_in(G, pos, m4, i, j, code, (float)d0 + (ej.x - ei.x), (float)d1 + (ej.y - ei.y),
-                         (float)d2 + (ej.z - ei.z))) {
-            if (nf < kListCap) list[nf * kMdThreads] = ((unsigned)j << 6) | code;
+          const float3 d = md_cart(G, (float)d0 + (ej.x - ei.x), (float)d1 + (ej.y - ei.y), (float)d2 + (ej.z - ei.z));
+          if (md_pair_in(G, pos, m4, i, j, code, d.x, d.y, d.z)) {
+            if (nf < kFwdCap) list[nf * kMdThreads] = ((unsigned)j << 6) | code;
             ++nf;
           }
         }
@@ -452,12 +465,68 @@ __device__ __forceinline__ void md_atom(const R (&ux)[kMdMaxM], const R (&uy)[kM
   }
 }
 
+// Fixed-order block sum of n values per quantity, src[k * stride + q] (q < n, k < 7): a strided sum
+// per thread (loads in flight together), a butterfly over each warp's lanes, then the warps in order
+// (through `red`, [warps][7]); thread k < 7 returns quantity k.
+__device__ __forceinline__ double md_block_sum7(const double *src, size_t stride, int n, double (*red)[7]) {
+  const int tid = threadIdx.x;
+  double acc[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    acc[k] = 0.0;
+#pragma unroll 4
+    for (int q = tid; q < n; q += kMdThreads) acc[k] += __ldcg(&src[k * stride + q]);
+    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
+  }
+  __syncthreads();                                 // earlier readers of red are done
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) red[tid >> 5][k] = acc[k];
+  __syncthreads();
+  double s = 0.0;
+  if (tid < 7)
+    for (int w = 0; w < kMdThreads / 32; ++w) s += red[w][tid];
+  return s;
+}
+
+// Deterministic in-kernel sum of the per-block partials [7][nblk] (U and the six virial components,
+// FP64): the last block of each group of kMdGroup blocks to finish sums its group into [7][ngroups],
+// and the last group to finish sums the groups into E and W, both in a fixed order. Counters
+// [ngroups + 1] follow the group sums and are zeroed before the launch.
+constexpr int kMdGroup = 64;
+__device__ __forceinline__ void md_grouped_sum(double *partial, int nblk, int b, double *E, double *W,
+                                               double (*red)[7]) {
+  __shared__ int s_last;
+  const int tid = threadIdx.x, ngroups = (nblk + kMdGroup - 1) / kMdGroup;
+  double *gpart = partial + (size_t)7 * nblk;
+  unsigned *counter = reinterpret_cast<unsigned *>(gpart + (size_t)7 * ngroups);
+  const int g = b / kMdGroup, g0 = g * kMdGroup, gn = min(kMdGroup, nblk - g0);
+  __syncthreads();                                 // the writers of the partials have fenced
+  if (tid == 0) s_last = atomicAdd(&counter[g], 1u) == (unsigned)(gn - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double t = md_block_sum7(partial + g0, (size_t)nblk, gn, red);
+  if (tid < 7) {
+    gpart[(size_t)tid * ngroups + g] = t;
+    __threadfence();
+  }
+  __syncthreads();
+  if (tid == 0) s_last = atomicAdd(&counter[ngroups], 1u) == (unsigned)(ngroups - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double u = md_block_sum7(gpart, (size_t)ngroups, ngroups, red);
+  if (tid == 0) *E = u;
+  else if (tid < 7) W[tid - 1] = u;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 4 : 1) md_force_kernel(
     int N, int M, const MdGeom G, const PConsts<R> K, const double *__restrict__ pos,
     const float4 *__restrict__ u4, const int4 *__restrict__ m4, const int *__restrict__ cnt,
     const int *__restrict__ nbr, const char4 *__restrict__ shift, typename Vec4<R>::T *__restrict__ Pst,
-    double *__restrict__ partial, unsigned *status) {
+    double *__restrict__ partial, double *__restrict__ E, double *__restrict__ W, unsigned *status) {
   using R4 = typename Vec4<R>::T;
   __shared__ double red[kMdThreads / 32][7];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -559,11 +628,14 @@ __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 4 : 1) md_force_k
 #pragma unroll
     for (int k = 0; k < 7; ++k) red[warp][k] = (double)v[k];
   __syncthreads();
-  if (threadIdx.x < 7) {
+  const int nblk = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  if (tid < 7) {
     double s = 0.0;
-    for (int w = 0; w < kMdThreads / 32; ++w) s += red[w][threadIdx.x];
-    partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    for (int w = 0; w < kMdThreads / 32; ++w) s += red[w][tid];
+    partial[(size_t)tid * nblk + b] = s;
+    __threadfence();                               // the partial before this block's count
   }
+  md_grouped_sum(partial, nblk, b, E, W, red);
 }
 
 template <typename R>
@@ -583,31 +655,6 @@ __global__ void md_gather_kernel(int N, int M, const int *__restrict__ cnt, cons
   F[3 * (size_t)i] = Fx;
   F[3 * (size_t)i + 1] = Fy;
   F[3 * (size_t)i + 2] = Fz;
-}
-
-// Sum of the per-block partials [7][nblocks] in a fixed order: a strided sum per thread, then the
-// warps' and the block's sums in lane and warp order.
-constexpr int kMdReduceThreads = 1024;
-__global__ void __launch_bounds__(kMdReduceThreads) md_reduce_kernel(int nblocks, const double *__restrict__ partial,
-                                                                      double *E, double *W) {
-  __shared__ double red[kMdReduceThreads / 32][7];
-  double acc[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  for (int b = threadIdx.x; b < nblocks; b += kMdReduceThreads)
-#pragma unroll
-    for (int k = 0; k < 7; ++k) acc[k] += partial[(size_t)k * nblocks + b];
-#pragma unroll
-  for (int k = 0; k < 7; ++k)
-    for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], off);
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int k = 0; k < 7; ++k) red[threadIdx.x >> 5][k] = acc[k];
-  __syncthreads();
-  if (threadIdx.x < 7) {
-    double s = 0.0;
-    for (int w = 0; w < kMdReduceThreads / 32; ++w) s += red[w][threadIdx.x];
-    if (threadIdx.x == 0) *E = s;
-    else W[threadIdx.x - 1] = s;
-  }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -647,13 +694,15 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
     }
     esum += std::sqrt(en);
   }
-  // FP32 distance error <= a few ulp of the cell edge lengths; the band is 64x wider
-  const double margin = 64.0 * 1.2e-7 * esum * 2.0 * R2 + 1e-6;
+  // FP32 distance error: brick coordinates of up to 6 cell edges, rounded once each and subtracted,
+  // stay within ~12 ulp of the cell edge lengths; the band is 128 ulp wide
+  const double margin = 128.0 * 1.2e-7 * esum * 2.0 * R2 + 1e-6;
   G.diag = 1;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b)
       if (a != b && (H[3 * a + b] != 0.0 || G.Hinv[3 * a + b] != 0.0)) G.diag = 0;
-  for (int k = 0; k < 3; ++k) G.ncd[k] = (double)G.nc[k];
+  for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 3; ++k) G.Hn[3 * a + k] = G.Hinv[3 * a + k] * (double)G.nc[k];
   G.R1 = R1;
   G.R2 = R2;
   G.R2sq = R2 * R2;
@@ -671,13 +720,14 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
     return TERSOFF_E_ARG;
   }
   const int nblk = (N + kMdThreads - 1) / kMdThreads;
+  const int ngroups = (nblk + kMdGroup - 1) / kMdGroup;
   const size_t rs = precision == 64 ? 8 : 4;
   if (c.md_cellcnt.ensure(ncells * sizeof(int)) || c.md_cells.ensure(ncells * kMdCap * sizeof(float4)) ||
       c.md_pos.ensure((size_t)N * (sizeof(float4) + sizeof(int4))) || c.md_cnt.ensure((size_t)N * sizeof(int)) ||
       c.md_nbr.ensure((size_t)N * M * sizeof(int)) || c.md_shift.ensure((size_t)N * M * sizeof(char4)) ||
       c.md_keys.ensure((size_t)N * M * sizeof(unsigned)) ||
       c.md_rev.ensure((size_t)N * kMdMaxM * sizeof(int)) || c.md_Pij.ensure((size_t)N * kMdMaxM * 4 * rs) ||
-      c.md_red.ensure((size_t)nblk * 7 * sizeof(double))) {
+      c.md_red.ensure(((size_t)nblk + ngroups) * 7 * sizeof(double) + (ngroups + 1) * sizeof(unsigned))) {
     err = "device allocation failed";
     return TERSOFF_E_CUDA;
   }
@@ -687,6 +737,7 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   int4 *m4 = reinterpret_cast<int4 *>(u4 + N);
   unsigned *st = c.status.as<unsigned>();
   cudaMemsetAsync(c.md_cellcnt.p, 0, ncells * sizeof(int), s);
+  cudaMemsetAsync(c.md_red.as<double>() + ((size_t)nblk + ngroups) * 7, 0, (ngroups + 1) * sizeof(unsigned), s);
   md_cells_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(), u4, m4,
                                               c.md_cnt.as<int>(), st);
   const long nbricks = (long)((G.nc[0] + kBrick - 1) / kBrick) * ((G.nc[1] + kBrick - 1) / kBrick) *
@@ -701,7 +752,7 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
     PConsts<double> K{D0, -al * log2e, al * r0 * log2e, -0.5 * al, be, h, n, -0.5 / n};
     md_force_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, u4, m4, c.md_cnt.as<int>(),
                                                         c.md_nbr.as<int>(), c.md_shift.as<char4>(),
-                                                        c.md_Pij.as<dvec4>(), c.md_red.as<double>(), st);
+                                                        c.md_Pij.as<dvec4>(), c.md_red.as<double>(), E, W, st);
     md_gather_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, c.md_cnt.as<int>(), c.md_rev.as<int>(),
                                                          c.md_Pij.as<dvec4>(), reinterpret_cast<double *>(F));
   } else {
@@ -709,12 +760,11 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
                      (float)n, (float)(-0.5 / n)};
     md_force_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, u4, m4, c.md_cnt.as<int>(),
                                                        c.md_nbr.as<int>(), c.md_shift.as<char4>(),
-                                                       c.md_Pij.as<float4>(), c.md_red.as<double>(), st);
+                                                       c.md_Pij.as<float4>(), c.md_red.as<double>(), E, W, st);
     md_gather_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, c.md_cnt.as<int>(), c.md_rev.as<int>(),
                                                         c.md_Pij.as<float4>(), reinterpret_cast<float *>(F));
   }
-  md_reduce_kernel<<<1, kMdReduceThreads, 0, s>>>(nblk, c.md_red.as<double>(), E, W);
-  cudaError_t e = launched(6);   // cells, pairs, rows, force, gather, reduce
+  cudaError_t e = launched(5);   // cells, pairs, rows, force (with the sums), gather
   if (e != cudaSuccess) {
     err = std::string("CUDA error: ") + cudaGetErrorString(e);
     return TERSOFF_E_CUDA;

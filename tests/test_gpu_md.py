@@ -116,18 +116,20 @@ def test_md_rejects_small_box(ctx):
     assert ei.value.code == binding.E_ARG
 
 
-def test_md_neighbor_lists_wide_cutoff_read_from_global(ctx):
-    """R2 = 5 A in a 4x4x4 diamond cell: the cells are the conventional cells (8 atoms each), so the
-    surroundings of a brick of cells hold more atoms than the shared-memory stage and the records are
-    read from global memory; lists of 28 entries. The force kernel flags more than 8 neighbours and
+@pytest.mark.parametrize("R2,per_atom", [(4.2, 16), (5.0, 28)])
+def test_md_neighbor_lists_wide_cutoffs(ctx, R2, per_atom):
+    """Long lists in a 4x4x4 diamond cell. R2 = 4.2 A: 16 neighbours, the records of a brick of cells
+    and its surroundings staged in shared memory. R2 = 5 A: 28 neighbours, and the cells are the
+    conventional cells (8 atoms each), so the surroundings of a brick hold more atoms than the stage
+    and the records are read from global memory. The force kernel flags more than 8 neighbours and
     nothing else."""
     from paper_1909_11474_gb300 import binding
     pos, box = _cell((4, 4, 4), 0.05, 0.0, 9)
-    ctx.md_force(torch.tensor(pos, device="cuda"), box, I.TABLE2_PARAMS, R1=4.6, R2=5.0, max_nbr=32)
+    ctx.md_force(torch.tensor(pos, device="cuda"), box, I.TABLE2_PARAMS, R1=R2 - 0.4, R2=R2, max_nbr=32)
     assert ctx.get_status() == binding.STATUS_MANY_NBRS
     cnt, nbr, shift = ctx.md_export_neighbors()
-    nl = oracle.neighbor_list(pos, box, 5.0)
-    assert (np.diff(nl["off"]) == 28).all()
+    nl = oracle.neighbor_list(pos, box, R2)
+    assert (np.diff(nl["off"]) == per_atom).all()
     for i in range(len(pos)):
         e = slice(nl["off"][i], nl["off"][i + 1])
         assert cnt[i] == nl["off"][i + 1] - nl["off"][i]
