@@ -199,8 +199,14 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     assert ctx.get_status() == 0
-    # the library's schedule autotuner, once per (build, P), before the timed region
-    tuned_ms, tuned_tried = ctx.autotune(params, tg, precision=32, reps=3)
+    # the library's schedule autotuner, once per (build, P), before the timed region; or a fixed
+    # schedule (tile, warps, items per configuration, narrow), e.g. to profile one variant
+    if args.schedule:
+        tile, warps, items, narrow = (int(v) for v in args.schedule.split(","))
+        ctx.set_schedule(P, tile=tile, items_per_config=items, narrow=bool(narrow), precision=32, warps=warps)
+        tuned_ms, tuned_tried = float("nan"), 0
+    else:
+        tuned_ms, tuned_tried = ctx.autotune(params, tg, precision=32, reps=3)
     for _ in range(2):
         step()
     torch.cuda.synchronize()
@@ -289,7 +295,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(),
                 "kernel": "tsf::batch_kernel<{t},4,0,{m},float,{w}> (every cell of the workload has m <= 4; "
-                          "variant chosen by the autotuner)".format(
+                          "variant {how})".format(how="fixed by --schedule" if args.schedule else "chosen by the autotuner",
                               t=ctx.schedule_info(32)[0]["tile"], w=ctx.schedule_info(32)[0]["warps"],
                               m=3 if ctx.schedule_info(32)[0]["tile"] == 16 else 2),
                 "kernel_ms": round(1e3 * b_time, 4), "flop_per_launch": flop,
@@ -313,16 +319,21 @@ def run_ours(args):
            "e2e": {"value": round(ws * atom_evals * args.steps / t_e2e, 1), "unit": UNIT,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
-           "autotune": {"candidates": tuned_tried, "tuned_launch_ms": round(tuned_ms, 4),
+           "autotune": {"candidates": tuned_tried, "tuned_launch_ms": None if args.schedule else round(tuned_ms, 4),
                         "schedule": ctx.schedule_info(32)}}
     if not args.quick:
-        out["rows"] = {
-            "adjoint": bench_adjoint(ctx_dev=dev, steps=max(3, args.steps // 5), flush=flush, stream=stream),
-            "plain_fp64_vs_batched": bench_plain(ctx, params, tg, dev, cs, flush, stream, k_time),
-            "uneven_batch": bench_uneven(dev, flush, stream),
-            "md_force": bench_md(dev, flush, stream, steps=max(3, args.steps // 5)),
-            "ga_fit": bench_ga(ctx, tg, w),
+        rows = {
+            "adjoint": lambda: bench_adjoint(ctx_dev=dev, steps=max(3, args.steps // 5), flush=flush, stream=stream),
+            "plain_fp64_vs_batched": lambda: bench_plain(ctx, params, tg, dev, cs, flush, stream, k_time),
+            "uneven_batch": lambda: bench_uneven(dev, flush, stream),
+            "md_force": lambda: bench_md(dev, flush, stream, steps=max(3, args.steps // 5)),
+            "ga_fit": lambda: bench_ga(ctx, tg, w),
         }
+        pick = [r for r in args.rows.split(",") if r] or list(rows)
+        unknown = [r for r in pick if r not in rows]
+        if unknown:
+            raise SystemExit(f"unknown rows {unknown}; choose from {list(rows)}")
+        out["rows"] = {r: rows[r]() for r in pick}
     if rank == 0 and ws == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w, tg_host={k: v.cpu().numpy() for k, v in tg.items()},
                                            budget_s=args.cpu_seconds)
@@ -562,6 +573,9 @@ def main():
     ap.add_argument("--ref-pairs", type=int, default=200)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main step only (no per-row measurements)")
+    ap.add_argument("--rows", default="", help="comma-separated subset of the extra rows (default: all)")
+    ap.add_argument("--schedule", default="", help="fixed batched schedule 'tile,warps,items,narrow' instead of "
+                                                   "the autotuner (e.g. 32,12,1,1)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
