@@ -442,7 +442,7 @@ def bench_uneven(dev, flush, stream):
 def bench_ga(ctx, tg, w):
     """The paper's GA run on the bench workload (Sec. III.B): N_pop = 200, N_par = 100, 1000 generations,
     mutation rate 0.2 -> 0, each generation one fitness call plus one GA kernel on the device; then
-    200 Adam steps of the gradient polish on the best individual."""
+    the damped-Newton gradient polish of the best individual (30 iterations, adjoint gradients)."""
     import torch
 
     from paper_1909_11474_gb300 import inputs as I
@@ -458,15 +458,23 @@ def bench_ga(ctx, tg, w):
     torch.cuda.synchronize()
     t_ga = time.perf_counter() - t0
     t0 = time.perf_counter()
-    x, L0, L1 = polish(ctx, res["params"], tg, lo, hi, steps=200)
+    x, L0, L1 = polish(ctx, res["params"], tg, lo, hi, steps=30)
     torch.cuda.synchronize()
     t_pol = time.perf_counter() - t0
-    rel = np.abs(x - w["hidden"]) / np.abs(w["hidden"])
+    hidden = torch.tensor(w["hidden"][None, :], device="cuda")
+    L_hidden = float(ctx.param_grad(hidden, tg)[0][0])
+    Z_hidden = float(ctx.fitness(hidden, tg, precision=32)[0][0])
+    Z_pol = float(ctx.fitness(torch.tensor(x[None, :], device="cuda"), tg, precision=32)[0][0])
+    rel = (x - w["hidden"]) / np.abs(w["hidden"])
     return {"workload": "P=200 x C=300 64-atom cells, noisy targets of the Table 2 parameters",
             "generations": 1000, "wall_s": round(t_ga, 3), "ms_per_generation": round(1e3 * t_ga / 1000, 4),
-            "best_Z": round(res["Z"], 6), "polish": {"steps": 200, "wall_s": round(t_pol, 3),
-                                                    "loss_before": L0, "loss_after": L1},
-            "max_rel_error_vs_hidden": round(float(rel.max()), 5),
+            "best_Z": round(res["Z"], 6),
+            "polish": {"method": "damped Newton, 30 iterations", "wall_s": round(t_pol, 3), "loss_before": L0,
+                       "loss_after": L1, "loss_at_hidden": L_hidden, "Z_after": round(Z_pol, 6),
+                       "Z_at_hidden": round(Z_hidden, 6)},
+            "rel_error_vs_hidden": [round(float(v), 6) for v in rel],
+            "max_rel_error_vs_hidden": round(float(np.abs(rel).max()), 6),
+            "note": "targets carry noise, so the loss minimum sits near, not at, the hidden parameters",
             "paper": "1000 generations take a few minutes on one Tesla P100 (Sec. III.C; context only)"}
 
 

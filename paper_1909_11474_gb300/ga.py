@@ -4,8 +4,9 @@ device, and a gradient polish of the best individual.
 Each generation evaluates the fitness Z of the whole population with `Context.fitness` and forms the
 next population with one `tersoff_ga_step` kernel (rank, elite, parents, uniform crossover,
 mutation); the uniform random numbers come from a seeded torch generator on the device. Nothing is
-copied to the host inside the loop. `polish` then refines the best parameter set with the adjoint
-gradient of the smooth loss (`TersoffLoss`), the use the gradient kernel serves beside the GA.
+copied to the host inside the loop. A run can be saved and resumed bit for bit (`save`, `load`).
+`polish` then refines the best parameter set with the adjoint gradient of the smooth loss
+(`TersoffLoss`), the use the gradient kernel serves beside the GA.
 """
 from __future__ import annotations
 
@@ -41,16 +42,20 @@ class GeneticFit:
         self.n_u = 8 * (self.n_pop - self.n_par) + 2 * N_GENES * (self.n_pop - 1)
         self.u = torch.empty(self.n_u, dtype=torch.float64, device=device)
         self.cur = 0
+        self.k = 0                      # generations done
 
     def evaluate(self):
         self.ctx.fitness(self.params, self.targets, w=self.w, out=(self.Z, None, None))
         return self.Z
 
-    def run(self, n_gen: int = 1000, rate0: float = 0.2, history: bool = False):
-        """n_gen generations; returns the best parameter set, its fitness and (optionally) the best
-        fitness of every generation (all device tensors until the end)."""
+    def run(self, n_gen: int = 1000, rate0: float = 0.2, history: bool = False, until: int | None = None):
+        """Generations self.k .. min(until, n_gen) - 1 of an n_gen-generation schedule (mutation rate
+        rate0 (1 - k / (n_gen - 1))); returns the best parameter set of the current population, its
+        fitness and (optionally) the best fitness of every generation run. A run stopped by `until`
+        continues, bit for bit, from where it stopped (also after `save` and `load`)."""
         best = []
-        for k in range(n_gen):
+        stop = n_gen if until is None else min(int(until), n_gen)
+        for k in range(self.k, stop):
             self.evaluate()
             if history:
                 best.append(self.Z.min())
@@ -60,33 +65,129 @@ class GeneticFit:
             binding.ga_step(self.Z, self.genes[self.cur], self.u, self.lo, self.hi, self.n_par, rate,
                             self.genes[nxt], self.params, self.order)
             self.cur = nxt
+            self.k = k + 1
         Z = self.evaluate()
         i = int(torch.argmin(Z))
-        out = {"params": self.params[i].detach().cpu().numpy(), "Z": float(Z[i]), "genes": self.genes[self.cur][i].cpu().numpy()}
+        out = {"params": self.params[i].detach().cpu().numpy(), "Z": float(Z[i]), "genes": self.genes[self.cur][i].cpu().numpy(),
+               "generations": self.k}
         if history:
-            out["history"] = torch.stack(best).cpu().numpy()
+            out["history"] = torch.stack(best).cpu().numpy() if best else torch.zeros(0).numpy()
         return out
 
+    # -- checkpoint / resume ------------------------------------------------------------------------
+    def state_dict(self) -> dict:
+        """Everything the next generations depend on: population (genes and parameters), generation
+        count, random-number generator state, and the settings it was made with."""
+        return {"genes": self.genes[self.cur].detach().cpu().clone(), "params": self.params.detach().cpu().clone(),
+                "k": self.k, "rng": self.gen.get_state().cpu().clone(), "n_pop": self.n_pop, "n_par": self.n_par,
+                "lo": self.lo.cpu().clone(), "hi": self.hi.cpu().clone(), "w": self.w}
 
-def polish(ctx: binding.Context, params, targets: dict, lo, hi, steps: int = 200, lr: float = 2e-3,
-           w=(1.0, 1.0, 1.0), loss: int = binding.LOSS_SQ):
-    """Refine one parameter set by Adam in gene space on the smooth loss L = sum_q w_q S_q / D_q,
-    with gradients from the adjoint kernel. Returns (params, loss before, loss after)."""
+    def load_state_dict(self, st: dict):
+        if (int(st["n_pop"]), int(st["n_par"])) != (self.n_pop, self.n_par):
+            raise ValueError("checkpoint of another population size")
+        if not (torch.equal(st["lo"], self.lo.cpu()) and torch.equal(st["hi"], self.hi.cpu())):
+            raise ValueError("checkpoint of other parameter limits")
+        self.cur = 0
+        self.genes[0].copy_(st["genes"])
+        self.params.copy_(st["params"])
+        self.k = int(st["k"])
+        self.gen.set_state(st["rng"])
+        self.w = tuple(float(x) for x in st["w"])
+
+    def save(self, path):
+        torch.save(self.state_dict(), path)
+
+    @classmethod
+    def load(cls, ctx: binding.Context, targets: dict, path, device=None) -> "GeneticFit":
+        st = torch.load(path, weights_only=False)
+        fit = cls(ctx, targets, st["lo"].numpy(), st["hi"].numpy(), n_pop=int(st["n_pop"]), n_par=int(st["n_par"]),
+                  w=st["w"], device=device)
+        fit.load_state_dict(st)
+        return fit
+
+
+def _newton_polish(ctx, g0, lo, hi, targets, w, loss, iters: int, h: float = 1e-4):
+    """Damped Newton (Levenberg-Marquardt damping) in gene space. Each iteration evaluates the loss
+    and its adjoint gradient at the point and at +-h along every gene in one batched call (13
+    parameter sets), takes the Hessian by central differences of the gradients, and solves
+    (H + lam diag(H)) d = -grad; a step that lowers the loss is taken and lam shrinks, else lam grows."""
+    span = hi - lo
+    eye = torch.eye(N_GENES, dtype=torch.float64, device=g0.device)
+
+    def batch(gg):
+        pts = torch.cat([gg[None, :], gg[None, :] + h * eye, gg[None, :] - h * eye], 0)
+        L, dL = ctx.param_grad((lo + pts * span).contiguous(), targets, w=w, loss=loss)
+        grad = dL * span                                  # d/dgene
+        H = (grad[1:1 + N_GENES] - grad[1 + N_GENES:]) / (2 * h)
+        return float(L[0]), grad[0], 0.5 * (H + H.T)
+
+    g = g0.clone()
+    L, grad, H = batch(g)
+    lam = 1e-3
+    for _ in range(iters):
+        d = None
+        for _ in range(30):
+            A = H + lam * torch.diag(torch.clamp(torch.diag(H), min=1e-12))
+            try:
+                d = torch.linalg.solve(A, -grad)
+            except RuntimeError:
+                d = None
+            if d is not None:
+                Ln = float(ctx.param_grad((lo + (g + d) * span)[None, :].contiguous(), targets, w=w, loss=loss)[0][0])
+                if Ln < L:
+                    break
+            lam *= 10.0
+            d = None
+        if d is None:
+            break
+        g = g + d
+        lam = max(lam / 10.0, 1e-12)
+        L, grad, H = batch(g)
+    return g
+
+
+def polish(ctx: binding.Context, params, targets: dict, lo, hi, steps: int = 30, lr: float = 2e-3,
+           w=(1.0, 1.0, 1.0), loss: int = binding.LOSS_SQ, method: str = "newton"):
+    """Refine one parameter set on the smooth loss L = sum_q w_q S_q / D_q in gene space, with
+    gradients from the adjoint kernel. The loss is a least-squares sum whose six directions are
+    badly scaled (beta and n trade off along a long valley), so the default is a damped Newton method
+    on a finite-difference Hessian of the adjoint gradient (`steps` iterations, one batched call of
+    13 parameter sets each); `method="lbfgs"` (strong-Wolfe line search) and `method="adam"` (rate
+    `lr`) are first-order alternatives. Returns (params, loss before, loss after)."""
     dev = torch.device("cuda")
     lo = torch.as_tensor(lo, dtype=torch.float64, device=dev)
     hi = torch.as_tensor(hi, dtype=torch.float64, device=dev)
     x0 = torch.as_tensor(params, dtype=torch.float64, device=dev).reshape(1, N_GENES)
-    g = ((x0 - lo) / (hi - lo)).clone().requires_grad_(True)
-    opt = torch.optim.Adam([g], lr=lr)
-    first = None
-    for _ in range(steps):
-        opt.zero_grad()
-        x = (lo + g * (hi - lo)).contiguous()
-        L = TersoffLoss.apply(x, ctx, targets, w, loss).sum()
-        if first is None:
-            first = float(L)
-        L.backward()
-        opt.step()
-    x = (lo + g.detach() * (hi - lo)).contiguous()
+    g0 = ((x0 - lo) / (hi - lo))
+    first = float(ctx.param_grad(x0.contiguous(), targets, w=w, loss=loss)[0][0])
+    if method == "newton":
+        g = _newton_polish(ctx, g0[0], lo, hi, targets, w, loss, int(steps)).reshape(1, N_GENES)
+    elif method in ("lbfgs", "adam"):
+        g = g0.clone().requires_grad_(True)
+
+        def value(gg):
+            return TersoffLoss.apply((lo + gg * (hi - lo)).contiguous(), ctx, targets, w, loss).sum()
+
+        if method == "lbfgs":
+            opt = torch.optim.LBFGS([g], lr=1.0, max_iter=int(steps), history_size=20, tolerance_grad=1e-14,
+                                    tolerance_change=1e-16, line_search_fn="strong_wolfe")
+
+            def closure():
+                opt.zero_grad()
+                L = value(g)
+                L.backward()
+                return L
+
+            opt.step(closure)
+        else:
+            opt = torch.optim.Adam([g], lr=lr)
+            for _ in range(steps):
+                opt.zero_grad()
+                value(g).backward()
+                opt.step()
+        g = g.detach()
+    else:
+        raise ValueError("method is 'newton', 'lbfgs' or 'adam'")
+    x = (lo + g * (hi - lo)).contiguous()
     L, _ = ctx.param_grad(x, targets, w=w, loss=loss)
     return x[0].cpu().numpy(), first, float(L[0])
