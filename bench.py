@@ -328,6 +328,7 @@ def run_ours(args):
             "uneven_batch": lambda: bench_uneven(dev, flush, stream),
             "md_force": lambda: bench_md(dev, flush, stream, steps=max(3, args.steps // 5)),
             "ga_fit": lambda: bench_ga(ctx, tg, w),
+            "elastic": bench_elastic,
         }
         pick = [r for r in args.rows.split(",") if r] or list(rows)
         unknown = [r for r in pick if r not in rows]
@@ -476,6 +477,24 @@ def bench_ga(ctx, tg, w):
             "max_rel_error_vs_hidden": round(float(np.abs(rel).max()), 6),
             "note": "targets carry noise, so the loss minimum sits near, not at, the hidden parameters",
             "paper": "1000 generations take a few minutes on one Tesla P100 (Sec. III.C; context only)"}
+
+
+def bench_elastic():
+    """Table 3 through the device path: lattice constant, C11, C12 and the relaxed C44 of the Table 2
+    parameters by zero-temperature stress-strain (batched FP64 evaluation of strained 8-atom cells)."""
+    import torch
+
+    from paper_1909_11474_gb300 import inputs as I
+    from paper_1909_11474_gb300.elastic import elastic_constants
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = elastic_constants(I.TABLE2_PARAMS)
+    wall = time.perf_counter() - t0
+    return {"workload": "8-atom conventional cell, strains +-1e-4, C44 with the internal shift relaxed",
+            "a0_A": round(c["a0"], 6), "C11_GPa": round(c["C11"], 3), "C12_GPa": round(c["C12"], 3),
+            "C44_GPa": round(c["C44"], 3), "C44_unrelaxed_GPa": round(c["C44_unrelaxed"], 3),
+            "device_calls": c["device_calls"], "wall_s": round(wall, 3),
+            "paper": {"C11": 148, "C12": 65, "C44": 75, "source": "Table 3, mini-Tersoff"}}
 
 
 def bench_md(dev, flush, stream, steps):

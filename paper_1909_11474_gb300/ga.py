@@ -124,9 +124,10 @@ def _newton_polish(ctx, g0, lo, hi, targets, w, loss, iters: int, h: float = 1e-
     g = g0.clone()
     L, grad, H = batch(g)
     lam = 1e-3
+    stalled = 0
     for _ in range(iters):
         d = None
-        for _ in range(30):
+        for _ in range(12):
             A = H + lam * torch.diag(torch.clamp(torch.diag(H), min=1e-12))
             try:
                 d = torch.linalg.solve(A, -grad)
@@ -142,6 +143,9 @@ def _newton_polish(ctx, g0, lo, hi, targets, w, loss, iters: int, h: float = 1e-
             break
         g = g + d
         lam = max(lam / 10.0, 1e-12)
+        stalled = stalled + 1 if L - Ln <= 1e-10 * L else 0
+        if stalled == 2:                               # at the rounding floor of the loss
+            break
         L, grad, H = batch(g)
     return g
 
