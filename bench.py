@@ -514,9 +514,31 @@ def bench_md(dev, flush, stream, steps):
              torch.empty(6, dtype=torch.float64, device=dev))
     t32 = _time(lambda: ctx.md_force(pos, cs.box[0], w["params"][0], precision=32, out=out32), steps, flush, stream)
     t64 = _time(lambda: ctx.md_force(pos, cs.box[0], w["params"][0], precision=64, out=out64), steps, flush, stream)
+    # velocity-Verlet NVE on the same cell at 300 K: 100 steps of 1 fs per call, FP32 forces
+    rng = np.random.default_rng(17)
+    m = np.full(N, I.SI_MASS)
+    vel0 = torch.tensor(I.thermal_velocities(rng, m, 300.0), device=dev)
+    mass = torch.tensor(m, device=dev)
+    p = pos.clone()
+    v = vel0.clone()
+    nst = 100
+    nve_out = (torch.empty(nst + 1, dtype=torch.float64, device=dev), torch.empty(nst + 1, dtype=torch.float64, device=dev),
+               torch.empty((N, 3), dtype=torch.float32, device=dev), torch.empty(6, dtype=torch.float64, device=dev))
+
+    def nve():
+        p.copy_(pos)
+        v.copy_(vel0)
+        ctx.md_nve(p, v, mass, cs.box[0], w["params"][0], 1.0, nst, precision=32, out=nve_out)
+
+    tn = _time(nve, max(2, steps // 2), flush, stream, warmup=1)
+    Et = (nve_out[0] + nve_out[1]).cpu().numpy()
     return {"workload": "40^3 conventional cells = 512,000 atoms, sigma = 0.08 A", "unit": "atom-steps/s",
             "fp32": {"value": round(N / t32, 1), "ms": round(1e3 * t32, 4)},
-            "fp64": {"value": round(N / t64, 1), "ms": round(1e3 * t64, 4)}}
+            "fp64": {"value": round(N / t64, 1), "ms": round(1e3 * t64, 4)},
+            "nve_fp32": {"steps_per_call": nst, "dt_fs": 1.0, "T0_K": 300.0,
+                         "value": round(N * nst / tn, 1), "ms_per_step": round(1e3 * tn / nst, 4),
+                         "max_energy_deviation_eV_per_atom": float(np.abs(Et - Et[0]).max() / N),
+                         "note": "one extra force call at the start of each call is included"}}
 
 
 def cpu_baseline(w, tg_host, budget_s=15.0):

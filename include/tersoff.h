@@ -244,6 +244,26 @@ int tersoff_md_force(tersoff_ctx *ctx, int32_t N, const double *pos, const doubl
                      const double *params, double R1, double R2, int32_t max_nbr, int32_t precision,
                      double *E, void *F, double *W, tersoff_stream stream);
 
+/* Velocity-Verlet NVE steps driven by the MD-scale force call. The integrator is not part of the
+ *  paper's method (its MD runs, Sec. IV, use an external code); it is the step toward them.
+ *  Units: eV, A, amu, fs.
+ *  - pos, vel: device [N][3] double, updated in place. Positions are never wrapped into the box.
+ *  - mass: device [N] double (amu).
+ *  - box, params, R1, R2, max_nbr, precision: as in tersoff_md_force.
+ *  - dt: the time step (fs, > 0); nsteps >= 0 steps.
+ *  The call evaluates the forces at the initial positions, then takes nsteps steps, each of
+ *  v += F dt / 2m, x += v dt, F = F(x), v += F dt / 2m.
+ *  Outputs (device):
+ *  - Epot, Ekin: [nsteps + 1] double, the potential and kinetic energy before the first step and
+ *    after every step. Ekin is summed in a fixed order, so it is deterministic.
+ *  - F: [N][3] float (precision 32) or double (64), the forces at the final positions.
+ *  - W: [6] double, the virial at the final positions.
+ *  Errors: TERSOFF_E_ARG for bad arguments (pos == vel, dt <= 0, nsteps < 0, ...); device problems
+ *  are flagged in the status word as for tersoff_md_force. */
+int tersoff_md_nve(tersoff_ctx *ctx, int32_t N, double *pos, double *vel, const double *mass, const double *box,
+                   const double *params, double R1, double R2, int32_t max_nbr, int32_t precision, double dt,
+                   int32_t nsteps, double *Epot, double *Ekin, void *F, double *W, tersoff_stream stream);
+
 /* Neighbour list of the last tersoff_md_force call, like tersoff_export_neighbors. Synchronous. */
 int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, int8_t *shift);
 

@@ -30,7 +30,7 @@ EXPORTED = (
     "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
     "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
     "tersoff_profile", "tersoff_profile_read", "tersoff_set_launch_mode", "tersoff_autotune",
-    "tersoff_set_schedule", "tersoff_schedule_info", "tersoff_ga_step",
+    "tersoff_set_schedule", "tersoff_schedule_info", "tersoff_ga_step", "tersoff_md_nve",
 )
 
 _vp = ctypes.c_void_p
@@ -75,6 +75,8 @@ def load():
         "tersoff_md_force": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _f64, _f64, _i32, _i32,
                                             _vp, _vp, _vp, _vp]),
         "tersoff_md_export_neighbors": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "tersoff_md_nve": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _f64, _i32, _i32, _f64, _i32,
+                                          _vp, _vp, _vp, _vp, _vp]),
         "tersoff_fitness_static": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _vp, _i32,
                                                   _vp, _vp, _vp, _vp]),
         "tersoff_kernel_launches": (ctypes.c_int64, []),
@@ -372,6 +374,31 @@ class Context:
                                               W.data_ptr(), _stream(stream)))
         self.md_N, self.md_M = N, max_nbr
         return E, F, W
+
+    def md_nve(self, pos: torch.Tensor, vel: torch.Tensor, mass: torch.Tensor, box, params, dt: float,
+               nsteps: int, R1: float = 2.8, R2: float = 3.2, max_nbr: int = 16, precision: int = 64,
+               stream=None, out=None):
+        """Velocity-Verlet NVE (tersoff_md_nve): pos, vel [N][3] float64 CUDA, updated in place; mass [N]
+        (amu); dt (fs). Returns Epot, Ekin [nsteps + 1] (eV), F [N][3] and W [6] at the end."""
+        N = pos.shape[0]
+        _cuda(pos, torch.float64, (N, 3), "pos")
+        _cuda(vel, torch.float64, (N, 3), "vel")
+        _cuda(mass, torch.float64, (N,), "mass")
+        boxh = np.ascontiguousarray(np.asarray(box, dtype=np.float64).reshape(3, 3))
+        ph = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(6))
+        dev = pos.device
+        if out is None:
+            out = (torch.empty(nsteps + 1, dtype=torch.float64, device=dev),
+                   torch.empty(nsteps + 1, dtype=torch.float64, device=dev),
+                   torch.empty((N, 3), dtype=torch.float32 if precision == 32 else torch.float64, device=dev),
+                   torch.empty(6, dtype=torch.float64, device=dev))
+        Ep, Ek, F, W = out
+        self._check(self.lib.tersoff_md_nve(self.h, N, pos.data_ptr(), vel.data_ptr(), mass.data_ptr(),
+                                            boxh.ctypes.data, ph.ctypes.data, R1, R2, max_nbr, precision, float(dt),
+                                            int(nsteps), Ep.data_ptr(), Ek.data_ptr(), F.data_ptr(), W.data_ptr(),
+                                            _stream(stream)))
+        self.md_N, self.md_M = N, max_nbr
+        return Ep, Ek, F, W
 
     def md_export_neighbors(self):
         N, M = self.md_N, self.md_M

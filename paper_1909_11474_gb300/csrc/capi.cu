@@ -351,7 +351,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
                          &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.outer, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart, &c.tew,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
-                         &c.md_keys, &c.md_boxd};
+                         &c.md_keys, &c.md_ke, &c.md_boxd};
   for (auto *b : bufs) b->release();
   c.hp_stage.release();
   if (c.stage_event) cudaEventDestroy(c.stage_event);
@@ -758,6 +758,28 @@ int tersoff_md_force(tersoff_ctx *ctx, int32_t N, const double *pos, const doubl
   cudaSetDevice(c.device);
   std::string err;
   const int rc = tsf::md_force(c, N, pos, box, params, R1, R2, max_nbr, precision, E, F, W, S(stream), err);
+  if (rc != TERSOFF_OK) return fail(ctx, rc, "%s", err.c_str());
+  return TERSOFF_OK;
+}
+
+int tersoff_md_nve(tersoff_ctx *ctx, int32_t N, double *pos, double *vel, const double *mass, const double *box,
+                   const double *params, double R1, double R2, int32_t max_nbr, int32_t precision, double dt,
+                   int32_t nsteps, double *Epot, double *Ekin, void *F, double *W, tersoff_stream stream) {
+  if (!ctx) return TERSOFF_E_ARG;
+  Ctx &c = ctx->c;
+  if (N < 1 || N > (1 << 24) || !pos || !vel || !mass || !box || !params || !Epot || !Ekin || !F || !W)
+    return fail(ctx, TERSOFF_E_ARG, "need 1 <= N <= 2^24 and non-null pointers%s");
+  if (pos == vel) return fail(ctx, TERSOFF_E_ARG, "pos and vel must be distinct arrays%s");
+  if (!(R1 > 0.0 && R2 > R1 && std::isfinite(R2))) return fail(ctx, TERSOFF_E_ARG, "need 0 < R1 < R2%s");
+  if (max_nbr < 1 || max_nbr > 32) return fail(ctx, TERSOFF_E_ARG, "max_nbr must be in [1, 32]%s");
+  if (precision != 32 && precision != 64) return fail(ctx, TERSOFF_E_ARG, "precision must be 32 or 64%s");
+  if (!(dt > 0.0 && std::isfinite(dt)) || nsteps < 0) return fail(ctx, TERSOFF_E_ARG, "need dt > 0 and nsteps >= 0%s");
+  for (int k = 0; k < 6; ++k)
+    if (!std::isfinite(params[k])) return fail(ctx, TERSOFF_E_ARG, "non-finite parameters%s");
+  cudaSetDevice(c.device);
+  std::string err;
+  const int rc = tsf::md_nve(c, N, pos, vel, mass, box, params, R1, R2, max_nbr, precision, dt, nsteps, Epot, Ekin,
+                             F, W, S(stream), err);
   if (rc != TERSOFF_OK) return fail(ctx, rc, "%s", err.c_str());
   return TERSOFF_OK;
 }

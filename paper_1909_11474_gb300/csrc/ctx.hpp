@@ -190,7 +190,7 @@ struct Ctx {
 
   // --- MD state ---
   int md_N = 0, md_M = 0;
-  DevBuf md_pos, md_cnt, md_nbr, md_shift, md_rev, md_cells, md_cellcnt, md_Pij, md_red, md_keys;
+  DevBuf md_pos, md_cnt, md_nbr, md_shift, md_rev, md_cells, md_cellcnt, md_Pij, md_red, md_keys, md_ke;
   DevBuf md_boxd;
 
   // --- measurement: CUDA events around each batched-kernel launch sequence, on its stream ---
@@ -263,6 +263,9 @@ int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s);
 // md.cu
 int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double *x, double R1, double R2,
              int M, int precision, double *E, void *F, double *W, cudaStream_t s, std::string &err);
+int md_nve(Ctx &c, int N, double *pos, double *vel, const double *mass, const double *boxh, const double *x,
+           double R1, double R2, int M, int precision, double dt, int nsteps, double *Epot, double *Ekin,
+           void *F, double *W, cudaStream_t s, std::string &err);
 
 // adjoint.cu
 size_t adjoint_smem_bytes(int nb, int nq, int nat);

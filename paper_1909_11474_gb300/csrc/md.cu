@@ -465,14 +465,15 @@ __device__ __forceinline__ void md_atom(const R (&ux)[kMdMaxM], const R (&uy)[kM
   }
 }
 
-// Fixed-order block sum of n values per quantity, src[k * stride + q] (q < n, k < 7): a strided sum
+// Fixed-order block sum of n values per quantity, src[k * stride + q] (q < n, k < K): a strided sum
 // per thread (loads in flight together), a butterfly over each warp's lanes, then the warps in order
-// (through `red`, [warps][7]); thread k < 7 returns quantity k.
-__device__ __forceinline__ double md_block_sum7(const double *src, size_t stride, int n, double (*red)[7]) {
+// (through `red`, [warps][>= K]); thread k < K returns quantity k.
+template <int K>
+__device__ __forceinline__ double md_block_sum(const double *src, size_t stride, int n, double (*red)[7]) {
   const int tid = threadIdx.x;
-  double acc[7];
+  double acc[K];
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < K; ++k) {
     acc[k] = 0.0;
 #pragma unroll 4
     for (int q = tid; q < n; q += kMdThreads) acc[k] += __ldcg(&src[k * stride + q]);
@@ -481,33 +482,35 @@ __device__ __forceinline__ double md_block_sum7(const double *src, size_t stride
   __syncthreads();                                 // earlier readers of red are done
   if ((tid & 31) == 0)
 #pragma unroll
-    for (int k = 0; k < 7; ++k) red[tid >> 5][k] = acc[k];
+    for (int k = 0; k < K; ++k) red[tid >> 5][k] = acc[k];
   __syncthreads();
   double s = 0.0;
-  if (tid < 7)
+  if (tid < K)
     for (int w = 0; w < kMdThreads / 32; ++w) s += red[w][tid];
   return s;
 }
 
-// Deterministic in-kernel sum of the per-block partials [7][nblk] (U and the six virial components,
-// FP64): the last block of each group of kMdGroup blocks to finish sums its group into [7][ngroups],
-// and the last group to finish sums the groups into E and W, both in a fixed order. Counters
-// [ngroups + 1] follow the group sums and are zeroed before the launch.
+// Deterministic in-kernel sum of per-block partials [K][nblk] (FP64; blocks of kMdThreads threads):
+// the last block of each group of kMdGroup blocks to finish sums its group into [K][ngroups], and
+// the last group to finish sums the groups, both in a fixed order; quantity 0 goes to *out0 and
+// quantity k >= 1 to out_rest[k - 1]. Counters [ngroups + 1] follow the group sums and are zeroed
+// before the launch. The threads that wrote the block's partials have fenced before the call.
 constexpr int kMdGroup = 64;
-__device__ __forceinline__ void md_grouped_sum(double *partial, int nblk, int b, double *E, double *W,
+template <int K>
+__device__ __forceinline__ void md_grouped_sum(double *partial, int nblk, int b, double *out0, double *out_rest,
                                                double (*red)[7]) {
   __shared__ int s_last;
   const int tid = threadIdx.x, ngroups = (nblk + kMdGroup - 1) / kMdGroup;
-  double *gpart = partial + (size_t)7 * nblk;
-  unsigned *counter = reinterpret_cast<unsigned *>(gpart + (size_t)7 * ngroups);
+  double *gpart = partial + (size_t)K * nblk;
+  unsigned *counter = reinterpret_cast<unsigned *>(gpart + (size_t)K * ngroups);
   const int g = b / kMdGroup, g0 = g * kMdGroup, gn = min(kMdGroup, nblk - g0);
-  __syncthreads();                                 // the writers of the partials have fenced
+  __syncthreads();
   if (tid == 0) s_last = atomicAdd(&counter[g], 1u) == (unsigned)(gn - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const double t = md_block_sum7(partial + g0, (size_t)nblk, gn, red);
-  if (tid < 7) {
+  const double t = md_block_sum<K>(partial + g0, (size_t)nblk, gn, red);
+  if (tid < K) {
     gpart[(size_t)tid * ngroups + g] = t;
     __threadfence();
   }
@@ -516,9 +519,19 @@ __device__ __forceinline__ void md_grouped_sum(double *partial, int nblk, int b,
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const double u = md_block_sum7(gpart, (size_t)ngroups, ngroups, red);
-  if (tid == 0) *E = u;
-  else if (tid < 7) W[tid - 1] = u;
+  const double u = md_block_sum<K>(gpart, (size_t)ngroups, ngroups, red);
+  if (tid == 0) *out0 = u;
+  else if (tid < K) out_rest[tid - 1] = u;
+}
+
+// Bytes of the partial-sum area of K quantities over nblk blocks: partials, group sums, counters.
+inline size_t md_sum_bytes(int K, int nblk) {
+  const int ngroups = (nblk + kMdGroup - 1) / kMdGroup;
+  return ((size_t)nblk + ngroups) * K * sizeof(double) + (ngroups + 1) * sizeof(unsigned);
+}
+inline size_t md_counter_offset(int K, int nblk) {
+  const int ngroups = (nblk + kMdGroup - 1) / kMdGroup;
+  return ((size_t)nblk + ngroups) * K * sizeof(double);
 }
 
 template <typename R>
@@ -635,7 +648,7 @@ __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 4 : 1) md_force_k
     partial[(size_t)tid * nblk + b] = s;
     __threadfence();                               // the partial before this block's count
   }
-  md_grouped_sum(partial, nblk, b, E, W, red);
+  md_grouped_sum<7>(partial, nblk, b, E, W, red);
 }
 
 template <typename R>
@@ -727,7 +740,7 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
       c.md_nbr.ensure((size_t)N * M * sizeof(int)) || c.md_shift.ensure((size_t)N * M * sizeof(char4)) ||
       c.md_keys.ensure((size_t)N * M * sizeof(unsigned)) ||
       c.md_rev.ensure((size_t)N * kMdMaxM * sizeof(int)) || c.md_Pij.ensure((size_t)N * kMdMaxM * 4 * rs) ||
-      c.md_red.ensure(((size_t)nblk + ngroups) * 7 * sizeof(double) + (ngroups + 1) * sizeof(unsigned))) {
+      c.md_red.ensure(md_sum_bytes(7, nblk))) {
     err = "device allocation failed";
     return TERSOFF_E_CUDA;
   }
@@ -737,7 +750,7 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   int4 *m4 = reinterpret_cast<int4 *>(u4 + N);
   unsigned *st = c.status.as<unsigned>();
   cudaMemsetAsync(c.md_cellcnt.p, 0, ncells * sizeof(int), s);
-  cudaMemsetAsync(c.md_red.as<double>() + ((size_t)nblk + ngroups) * 7, 0, (ngroups + 1) * sizeof(unsigned), s);
+  cudaMemsetAsync(static_cast<char *>(c.md_red.p) + md_counter_offset(7, nblk), 0, (ngroups + 1) * sizeof(unsigned), s);
   md_cells_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(), u4, m4,
                                               c.md_cnt.as<int>(), st);
   const long nbricks = (long)((G.nc[0] + kBrick - 1) / kBrick) * ((G.nc[1] + kBrick - 1) / kBrick) *
@@ -765,6 +778,98 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
                                                         c.md_Pij.as<float4>(), reinterpret_cast<float *>(F));
   }
   cudaError_t e = launched(5);   // cells, pairs, rows, force (with the sums), gather
+  if (e != cudaSuccess) {
+    err = std::string("CUDA error: ") + cudaGetErrorString(e);
+    return TERSOFF_E_CUDA;
+  }
+  return TERSOFF_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Velocity-Verlet NVE on the MD-scale force call (units eV, A, amu, fs). The integrator is not part
+// of the paper's method; it drives the force call the way an MD code does.
+constexpr double kAccel = 9.648533215665e-3;      // 1 eV / (A amu) in A / fs^2 (CODATA 2018)
+constexpr double kKinetic = 103.6426965268;       // 1 amu A^2 / fs^2 in eV
+
+// v += F / m * dt / 2, then x += v dt (FP64 state, forces in R).
+template <typename R>
+__global__ void md_kick_drift_kernel(int N, double *__restrict__ pos, double *__restrict__ vel,
+                                     const R *__restrict__ F, const double *__restrict__ mass, double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double h = 0.5 * dt * kAccel / mass[i];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double v = vel[3 * i + k] + h * (double)F[3 * i + k];
+    vel[3 * i + k] = v;
+    pos[3 * i + k] += v * dt;
+  }
+}
+
+// v += F / m * dt / 2 (dt = 0: no kick) and the kinetic energy sum_i m v^2 / 2 into *Ekin, in a
+// fixed order (per-block partials, then the grouped last-block sums).
+template <typename R>
+__global__ void __launch_bounds__(kMdThreads) md_kick_kernel(int N, double *__restrict__ vel,
+                                                             const R *__restrict__ F, const double *__restrict__ mass,
+                                                             double dt, double *__restrict__ partial,
+                                                             double *__restrict__ Ekin) {
+  __shared__ double red[kMdThreads / 32][7];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, tid = threadIdx.x;
+  double ke = 0.0;
+  if (i < N) {
+    const double m = mass[i], h = 0.5 * dt * kAccel / m;
+    double v2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double v = vel[3 * i + k] + h * (double)F[3 * i + k];
+      vel[3 * i + k] = v;
+      v2 += v * v;
+    }
+    ke = 0.5 * kKinetic * m * v2;
+  }
+  for (int off = 16; off > 0; off >>= 1) ke += __shfl_xor_sync(0xffffffffu, ke, off);
+  if ((tid & 31) == 0) red[tid >> 5][0] = ke;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < kMdThreads / 32; ++w) s += red[w][0];
+    partial[blockIdx.x] = s;
+    __threadfence();
+  }
+  md_grouped_sum<1>(partial, gridDim.x, blockIdx.x, Ekin, nullptr, red);
+}
+
+int md_nve(Ctx &c, int N, double *pos, double *vel, const double *mass, const double *boxh, const double *x,
+           double R1, double R2, int M, int precision, double dt, int nsteps, double *Epot, double *Ekin,
+           void *F, double *W, cudaStream_t s, std::string &err) {
+  const int nblk = (N + kMdThreads - 1) / kMdThreads;
+  const int ngroups = (nblk + kMdGroup - 1) / kMdGroup;
+  if (c.md_ke.ensure(md_sum_bytes(1, nblk))) {
+    err = "device allocation failed";
+    return TERSOFF_E_CUDA;
+  }
+  double *part = c.md_ke.as<double>();
+  char *counters = static_cast<char *>(c.md_ke.p) + md_counter_offset(1, nblk);
+  auto kick = [&](double h, int step) {
+    cudaMemsetAsync(counters, 0, (ngroups + 1) * sizeof(unsigned), s);
+    if (precision == 64)
+      md_kick_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, vel, static_cast<const double *>(F), mass, h, part, Ekin + step);
+    else
+      md_kick_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, vel, static_cast<const float *>(F), mass, h, part, Ekin + step);
+  };
+  int rc = md_force(c, N, pos, boxh, x, R1, R2, M, precision, Epot, F, W, s, err);
+  if (rc != TERSOFF_OK) return rc;
+  kick(0.0, 0);                                     // kinetic energy of the initial velocities
+  for (int k = 1; k <= nsteps; ++k) {
+    if (precision == 64)
+      md_kick_drift_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, pos, vel, static_cast<const double *>(F), mass, dt);
+    else
+      md_kick_drift_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, pos, vel, static_cast<const float *>(F), mass, dt);
+    rc = md_force(c, N, pos, boxh, x, R1, R2, M, precision, Epot + k, F, W, s, err);
+    if (rc != TERSOFF_OK) return rc;
+    kick(dt, k);
+  }
+  const cudaError_t e = launched(1 + 2 * nsteps);   // kicks and kick-drifts (the force calls count themselves)
   if (e != cudaSuccess) {
     err = std::string("CUDA error: ") + cudaGetErrorString(e);
     return TERSOFF_E_CUDA;

@@ -10,6 +10,7 @@ copied to the host inside the loop. A run can be saved and resumed bit for bit (
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import binding
@@ -109,39 +110,44 @@ class GeneticFit:
 def _newton_polish(ctx, g0, lo, hi, targets, w, loss, iters: int, h: float = 1e-4):
     """Damped Newton (Levenberg-Marquardt damping) in gene space. Each iteration evaluates the loss
     and its adjoint gradient at the point and at +-h along every gene in one batched call (13
-    parameter sets), takes the Hessian by central differences of the gradients, and solves
-    (H + lam diag(H)) d = -grad; a step that lowers the loss is taken and lam shrinks, else lam grows."""
+    parameter sets), takes the Hessian by central differences of the gradients, and solves the 6x6
+    system (H + lam diag(H)) d = -grad on the host; a step that lowers the loss is taken and lam
+    shrinks, else lam grows. Stops when two accepted steps in a row gain less than 1e-10 relative."""
     span = hi - lo
     eye = torch.eye(N_GENES, dtype=torch.float64, device=g0.device)
 
     def batch(gg):
         pts = torch.cat([gg[None, :], gg[None, :] + h * eye, gg[None, :] - h * eye], 0)
         L, dL = ctx.param_grad((lo + pts * span).contiguous(), targets, w=w, loss=loss)
-        grad = dL * span                                  # d/dgene
+        grad = (dL * span).cpu().numpy()                  # d/dgene
         H = (grad[1:1 + N_GENES] - grad[1 + N_GENES:]) / (2 * h)
         return float(L[0]), grad[0], 0.5 * (H + H.T)
+
+    def loss_at(gg):
+        return float(ctx.param_grad((lo + gg * span)[None, :].contiguous(), targets, w=w, loss=loss)[0][0])
 
     g = g0.clone()
     L, grad, H = batch(g)
     lam = 1e-3
     stalled = 0
     for _ in range(iters):
-        d = None
+        step = None
         for _ in range(12):
-            A = H + lam * torch.diag(torch.clamp(torch.diag(H), min=1e-12))
+            A = H + lam * np.diag(np.maximum(np.diag(H), 1e-12))
             try:
-                d = torch.linalg.solve(A, -grad)
-            except RuntimeError:
+                d = np.linalg.solve(A, -grad)
+            except np.linalg.LinAlgError:
                 d = None
-            if d is not None:
-                Ln = float(ctx.param_grad((lo + (g + d) * span)[None, :].contiguous(), targets, w=w, loss=loss)[0][0])
+            if d is not None and np.all(np.isfinite(d)):
+                dt = torch.as_tensor(d, dtype=torch.float64, device=g.device)
+                Ln = loss_at(g + dt)
                 if Ln < L:
+                    step = dt
                     break
             lam *= 10.0
-            d = None
-        if d is None:
+        if step is None:
             break
-        g = g + d
+        g = g + step
         lam = max(lam / 10.0, 1e-12)
         stalled = stalled + 1 if L - Ln <= 1e-10 * L else 0
         if stalled == 2:                               # at the rounding floor of the loss

@@ -60,6 +60,20 @@ def random_strain(rng: np.random.Generator, s: float) -> np.ndarray:
     return np.array([[e[0], e[3], e[5]], [e[3], e[1], e[4]], [e[5], e[4], e[2]]], dtype=np.float64)
 
 
+def thermal_velocities(rng: np.random.Generator, mass: np.ndarray, T: float) -> np.ndarray:
+    """Maxwell-Boltzmann velocities (A/fs) at temperature T (K) for masses in amu, with the
+    centre-of-mass velocity removed. Each component has variance kB T / m; kB T / m in eV/amu is
+    converted with 1 eV/amu = 9.648533215665e-3 A^2/fs^2 (CODATA 2018)."""
+    mass = np.asarray(mass, dtype=np.float64)
+    sd = np.sqrt(8.617333262e-5 * T / mass * 9.648533215665e-3)
+    v = rng.normal(0.0, 1.0, size=(len(mass), 3)) * sd[:, None]
+    v -= (mass[:, None] * v).sum(0) / mass.sum()
+    return v
+
+
+SI_MASS = 28.0855   # amu, standard atomic weight of Si
+
+
 def apply_strain(pos: np.ndarray, box: np.ndarray, eps: np.ndarray):
     m = np.eye(3) + eps
     return pos @ m.T, box @ m.T
