@@ -20,6 +20,9 @@ What it computes, in the paper's notation (all FP64, torch CPU tensors, autograd
   virial formulas to another reference (Sec. III.C);
 * fitness Z = w_e Z_e + w_v Z_v + w_f Z_f, each a relative RMS error          (Eq. 15, 17-19)
   over the parameter vector x = [D0, alpha, r0, beta, n, h]                    (Eq. 16)
+* the Tersoff form: a parameter vector of nine, x = [D0, alpha, r0, S, n, h, gamma, c, d], takes
+  the original angular function g^T = gamma (1 + c^2/d^2 - c^2/(d^2 + (cos - h)^2)) (Eq. 8) and a
+  free S in Eq. 11-14; everything else as above
 
 Readings where the paper is silent (also listed in the design notes):
 * zeta_ij == 0 gives b_ij = 1, the value Eq. 6 takes in that limit; the branch is taken without
@@ -176,22 +179,35 @@ def site_energy_sum(d: torch.Tensor, owner: torch.Tensor, ta: torch.Tensor, tb: 
 
     owner[e] = i of entry e; (ta, tb) = ordered entry pairs of the same atom (Eq. 7's k != j).
     """
-    D0, alpha, r0, beta, n, h = params.unbind()
-    S = S_FIXED
-    # Eq. 11-14
-    A = D0 / (S - 1.0) * torch.exp(alpha * r0 * math.sqrt(2.0 * S))
-    B = D0 * S / (S - 1.0) * torch.exp(alpha * r0 * math.sqrt(2.0 / S))
-    lam = alpha * math.sqrt(2.0 * S)
-    mu = alpha * math.sqrt(2.0 / S)
+    tersoff_form = params.numel() == 9
+    if tersoff_form:   # x = [D0, alpha, r0, S, n, h, gamma, c, d]: Eq. 8 angular function, free S
+        D0, alpha, r0, S, n, h, gamma, c, dd = params.unbind()
+        # Eq. 11-14
+        A = D0 / (S - 1.0) * torch.exp(alpha * r0 * torch.sqrt(2.0 * S))
+        B = D0 * S / (S - 1.0) * torch.exp(alpha * r0 * torch.sqrt(2.0 / S))
+        lam = alpha * torch.sqrt(2.0 * S)
+        mu = alpha * torch.sqrt(2.0 / S)
+    else:
+        D0, alpha, r0, beta, n, h = params.unbind()
+        S = S_FIXED
+        # Eq. 11-14
+        A = D0 / (S - 1.0) * torch.exp(alpha * r0 * math.sqrt(2.0 * S))
+        B = D0 * S / (S - 1.0) * torch.exp(alpha * r0 * math.sqrt(2.0 / S))
+        lam = alpha * math.sqrt(2.0 * S)
+        mu = alpha * math.sqrt(2.0 / S)
 
     r = torch.sqrt((d * d).sum(dim=1))
     fC = cutoff(r, R1, R2)
     fR = A * torch.exp(-lam * r)          # Eq. 4
     fA = B * torch.exp(-mu * r)           # Eq. 5
 
-    # Eq. 7 with Eq. 10: zeta_ij = sum_{k != j} f_C(r_ik) beta (cos theta_ijk - h)^2
+    # Eq. 7 with Eq. 10: zeta_ij = sum_{k != j} f_C(r_ik) beta (cos theta_ijk - h)^2, or with Eq. 8:
+    # g = gamma (1 + c^2/d^2 - c^2 / (d^2 + (cos theta_ijk - h)^2))
     cos_t = (d[ta] * d[tb]).sum(dim=1) / (r[ta] * r[tb])
-    g = beta * (cos_t - h) ** 2
+    if tersoff_form:
+        g = gamma * (1.0 + c ** 2 / dd ** 2 - c ** 2 / (dd ** 2 + (cos_t - h) ** 2))
+    else:
+        g = beta * (cos_t - h) ** 2
     zeta = torch.zeros(len(r), dtype=_F64).index_add(0, ta, fC[tb] * g)
 
     # Eq. 6, with b = 1 taken directly when zeta = 0
