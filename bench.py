@@ -329,6 +329,7 @@ def run_ours(args):
             "md_force": lambda: bench_md(dev, flush, stream, steps=max(3, args.steps // 5)),
             "ga_fit": lambda: bench_ga(ctx, tg, w),
             "elastic": bench_elastic,
+            "tersoff_form": lambda: bench_tersoff_form(dev, flush, stream, w, steps=max(3, args.steps // 5)),
         }
         pick = [r for r in args.rows.split(",") if r] or list(rows)
         unknown = [r for r in pick if r not in rows]
@@ -477,6 +478,37 @@ def bench_ga(ctx, tg, w):
             "max_rel_error_vs_hidden": round(float(np.abs(rel).max()), 6),
             "note": "targets carry noise, so the loss minimum sits near, not at, the hidden parameters",
             "paper": "1000 generations take a few minutes on one Tesla P100 (Sec. III.C; context only)"}
+
+
+def bench_tersoff_form(dev, flush, stream, w, steps):
+    """Fitness of P=200 parameter sets of the nine-parameter Tersoff form (Eq. 8 angular function, free S)
+    on the bench workload, against the minimal form on the same context and targets."""
+    import torch
+
+    from paper_1909_11474_gb300 import binding
+    cs = w["configs"]
+    ctx = binding.Context(dev.index or 0)
+    pos = torch.tensor(cs.pos, device=dev)
+    box = torch.tensor(cs.box, device=dev)
+    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+    rng = np.random.default_rng(23)
+    x9 = np.array([3.2, 1.45, 2.25, 1.9, 0.65, -0.6, 0.06, 20.0, 3.0])[None, :] * rng.uniform(0.9, 1.1, (200, 9))
+    p9 = torch.tensor(x9, device=dev)
+    p6 = torch.tensor(w["params"], device=dev)
+    Eh, Fh, Wh = ctx.eval(torch.tensor(w["hidden"][None, :], device=dev), precision=64)
+    natoms = torch.tensor(cs.natoms, device=dev, dtype=torch.float64)
+    tg = {"E": (Eh[0] / natoms).contiguous(), "W": (Wh[0] / natoms[:, None]).contiguous(), "F": Fh[0].contiguous(),
+          "mask": torch.full((cs.C,), 7, dtype=torch.uint8, device=dev)}
+    out = (torch.empty(200, dtype=torch.float64, device=dev), None, None)
+    t6 = _time(lambda: ctx.fitness(p6, tg, precision=32, out=out), steps, flush, stream)
+    ctx.set_form(binding.FORM_TERSOFF)
+    t9 = _time(lambda: ctx.fitness(p9, tg, precision=32, out=out), steps, flush, stream)
+    assert ctx.get_status() == 0
+    n = 200 * cs.Ntot
+    return {"workload": "P=200 x C=300 64-atom cells, FP32 fitness call (default schedule)", "unit": "atom-evals/s",
+            "tersoff_form": {"value": round(n / t9, 1), "ms": round(1e3 * t9, 4)},
+            "minimal_form": {"value": round(n / t6, 1), "ms": round(1e3 * t6, 4)},
+            "cost_ratio": round(t9 / t6, 3)}
 
 
 def bench_elastic():

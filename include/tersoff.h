@@ -114,7 +114,8 @@ int tersoff_build_info(tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t
 
 /* Energy, forces and virial for every (parameter set p, configuration c) of the last build
  * (Eq. 1-14; forces F_i = -dU/dx_i and the virial above).
- *  params    device [P][6] double (order of Eq. 16), P >= 1
+ *  params    device [P][6] double (order of Eq. 16), P >= 1; [P][9] in the Tersoff form
+ *            (tersoff_set_form)
  *  precision 32: per-pair arithmetic in FP32, energy and virial sums in FP64, F in float;
  *            64: everything in FP64, F in double
  *  E         device [P][C] double, total energy (eV)             -- may be NULL
@@ -138,7 +139,8 @@ typedef struct {
  *   over configs whose mask has the bit; D_q = the same sums over the targets alone;
  *   Zq[p][q] = sqrt(S_q / D_q) (0 if D_q = 0); Z[p] = sum_q w_q Zq[p][q]; +inf if any predicted
  *   value of parameter set p is not finite.
- *  params device [P][6]; w host [3] = (w_e, w_v, w_f); precision 32 or 64 as in tersoff_eval;
+ *  params device [P][6] ([P][9] in the Tersoff form); w host [3] = (w_e, w_v, w_f); precision 32
+ *  or 64 as in tersoff_eval;
  *  Z device [P] double; Zq device [P][3] double (may be NULL); S device [P][3] double (may be NULL).
  * Residual sums are accumulated in FP64 in a fixed order (deterministic). */
 int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
@@ -280,6 +282,20 @@ int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, in
 #define TERSOFF_LAUNCH_GRAPHS 1
 #define TERSOFF_LAUNCH_PDL 2
 int tersoff_set_launch_mode(tersoff_ctx *ctx, int32_t mode);
+
+/* Functional form of the potential for the context's later tersoff_eval and tersoff_fitness calls
+ * (Sec. II.A-B):
+ *  TERSOFF_FORM_MINIMAL (default): the minimal Tersoff potential, params [P][6] =
+ *    (D0, alpha, r0, beta, n, h) (Eq. 16), g = beta (cos - h)^2 (Eq. 10), S = 2.
+ *  TERSOFF_FORM_TERSOFF: the general form, params [P][9] = (D0, alpha, r0, S, n, h, gamma, c, d):
+ *    the original angular function g^T = gamma (1 + c^2/d^2 - c^2/(d^2 + (cos - h)^2)) (Eq. 8) and
+ *    a free S in Eq. 11-14 (S != 1).
+ * In the Tersoff form tersoff_autotune, tersoff_param_grad, tersoff_eval_plain,
+ * tersoff_fitness_static, tersoff_md_force and tersoff_md_nve return TERSOFF_E_UNSUPPORTED.
+ * Errors: TERSOFF_E_ARG for an unknown form. */
+#define TERSOFF_FORM_MINIMAL 0
+#define TERSOFF_FORM_TERSOFF 1
+int tersoff_set_form(tersoff_ctx *ctx, int32_t form);
 
 /* Measurement helpers; the paper has no counterpart.
  * tersoff_kernel_launches: number of kernels the library has launched in this process, all contexts

@@ -23,6 +23,7 @@ LOSS_SQ, LOSS_Z = 0, 1
 
 LAUNCH_GRAPHS = 1
 LAUNCH_PDL = 2
+FORM_MINIMAL, FORM_TERSOFF = 0, 1
 
 EXPORTED = (
     "tersoff_create", "tersoff_destroy", "tersoff_last_error", "tersoff_get_status",
@@ -30,7 +31,7 @@ EXPORTED = (
     "tersoff_fitness", "tersoff_param_grad", "tersoff_eval_plain", "tersoff_md_force",
     "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
     "tersoff_profile", "tersoff_profile_read", "tersoff_set_launch_mode", "tersoff_autotune",
-    "tersoff_set_schedule", "tersoff_schedule_info", "tersoff_ga_step", "tersoff_md_nve",
+    "tersoff_set_schedule", "tersoff_schedule_info", "tersoff_ga_step", "tersoff_md_nve", "tersoff_set_form",
 )
 
 _vp = ctypes.c_void_p
@@ -75,6 +76,7 @@ def load():
         "tersoff_md_force": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _f64, _f64, _i32, _i32,
                                             _vp, _vp, _vp, _vp]),
         "tersoff_md_export_neighbors": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+        "tersoff_set_form": (ctypes.c_int, [_vp, _i32]),
         "tersoff_md_nve": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _f64, _f64, _i32, _i32, _f64, _i32,
                                           _vp, _vp, _vp, _vp, _vp]),
         "tersoff_fitness_static": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _vp, _i32,
@@ -162,6 +164,7 @@ class Context:
         self.h = h
         self.C = 0
         self.Ntot = 0
+        self.form = FORM_MINIMAL
         self.atom_off = None
         self.max_nbr = 0
 
@@ -187,6 +190,16 @@ class Context:
     def kernel_launches(self) -> int:
         """Kernels launched by the library in this process so far (all contexts)."""
         return int(self.lib.tersoff_kernel_launches())
+
+    def set_form(self, form: int):
+        """FORM_MINIMAL (parameter vectors of 6, Eq. 16) or FORM_TERSOFF (9: D0, alpha, r0, S, n, h,
+        gamma, c, d; Eq. 8 angular function, free S) for later eval and fitness calls."""
+        self._check(self.lib.tersoff_set_form(self.h, int(form)))
+        self.form = int(form)
+
+    @property
+    def n_params(self) -> int:
+        return 9 if self.form == FORM_TERSOFF else 6
 
     def set_launch_mode(self, graphs: bool = True, pdl: bool = True):
         """Replay the fitness call's launch sequence from a cached CUDA graph (graphs) and/or launch its
@@ -239,7 +252,7 @@ class Context:
     def eval(self, params: torch.Tensor, precision: int = 32, want_F: bool = True, stream=None):
         """E [P][C], F [P][Ntot][3] (float32 or float64), W [P][C][6] on the params' device."""
         P = params.shape[0]
-        _cuda(params, torch.float64, (P, 6), "params")
+        _cuda(params, torch.float64, (P, self.n_params), "params")
         dev = params.device
         E = torch.empty((P, self.C), dtype=torch.float64, device=dev)
         W = torch.empty((P, self.C, 6), dtype=torch.float64, device=dev)
@@ -262,7 +275,7 @@ class Context:
                 stream=None, out=None):
         """Z [P], Zq [P][3], S [P][3] (FP64) of Eq. 15, 17-19."""
         P = params.shape[0]
-        _cuda(params, torch.float64, (P, 6), "params")
+        _cuda(params, torch.float64, (P, self.n_params), "params")
         dev = params.device
         if out is None:
             out = (torch.empty(P, dtype=torch.float64, device=dev),

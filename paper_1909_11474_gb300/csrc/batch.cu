@@ -5,11 +5,9 @@
 #include <algorithm>
 #include <vector>
 
-#include "batch_kernel.cuh"
+#include "batch_launch.cuh"
 
 namespace tsf {
-
-constexpr int kPT = 32;   // parameter sets per warp: one atom per warp
 
 size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster) {
   if (precision == 64)
@@ -29,70 +27,6 @@ int batch_max_smem_optin() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   return v;
-}
-
-template <int PTV, int MMAX, bool CLUSTER, int MINB, typename R, int NW = kNW>
-static cudaError_t launch_variant(BatchParams bp, const Bucket &b, bool pdl, cudaStream_t s) {
-  auto kern = batch_kernel<PTV, MMAX, CLUSTER, MINB, R, NW>;
-  const size_t smem = PTV != kPT ? b.smem16 : NW != kNW ? b.smem12 : b.smem;
-  int &per_sm = PTV != kPT ? b.per_sm16 : NW != kNW ? b.per_sm12 : b.per_sm;
-  constexpr int kThr = NW * kWarp;
-  bp.ntiles = (bp.P + PTV - 1) / PTV;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int cluster = CLUSTER ? b.cluster : 1, ncta = cluster;
-  // resident CTAs of this variant, rounded down to whole clusters
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (per_sm == 0) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThr, smem);
-    if (e != cudaSuccess) return e;
-  }
-  const int slots = std::max(1, per_sm * nsm / ncta);
-  const int nconf = b.nitems;
-  // work items: whole configurations when they are all alike and fit in one wave of CTAs (the
-  // geometry is then staged once per configuration); otherwise each configuration's tiles are split
-  // into chunks so that about four items per CTA slot balance the dynamically claimed work; the
-  // autotuner's choice for this (P, mode) overrides both
-  int per_conf = 1;
-  if (!(b.uniform && nconf <= slots)) per_conf = std::min(bp.ntiles, std::max(1, (4 * slots + nconf - 1) / nconf));
-  bp.narrow = 1;
-  if (b.tune_P == bp.P && b.tune_mode == bp.mode && b.tune_per_conf > 0) {
-    per_conf = std::min(bp.ntiles, b.tune_per_conf);
-    bp.narrow = b.tune_narrow;
-  }
-  bp.nconf = nconf;
-  bp.chunk_tiles = (bp.ntiles + per_conf - 1) / per_conf;
-  bp.nchunks = (bp.ntiles + bp.chunk_tiles - 1) / bp.chunk_tiles;
-  const int nitems = nconf * bp.nchunks;
-  const int grid_clusters = std::min(nitems, slots);
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(grid_clusters * ncta));
-  cfg.blockDim = dim3(kThr);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  // programmatic dependent launch: the kernel may start while its predecessor (the preparation kernel
-  // or the previous bucket) runs; it waits for it before reading the per-call constants
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if constexpr (CLUSTER) {
-    if (cluster > 8) {
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
-    }
-    attr[1].id = cudaLaunchAttributeClusterDimension;
-    attr[1].val.clusterDim.x = cluster;
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
-    cfg.numAttrs = 2;
-  }
-  const cudaError_t el = cudaLaunchKernelEx(&cfg, kern, bp);
-  if (el == cudaSuccess) count_launches(1);
-  return el;
 }
 
 // Side streams (at most kSide) and their events, created on first use.
@@ -126,12 +60,14 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
       prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts),
                                                  ctx.Ntot, nullptr, nullptr, ctx.C,
                                                  ctx.atom_off.as<int>(), out.tE, out.tW, out.tmask,
-                                                 tew ? reinterpret_cast<double *>(out.tEW) : nullptr, out.dpart);
+                                                 tew ? reinterpret_cast<double *>(out.tEW) : nullptr, out.dpart,
+                                                 out.form);
     else
       prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts),
                                                 ctx.Ntot, nullptr, nullptr, ctx.C,
                                                 ctx.atom_off.as<int>(), out.tE, out.tW, out.tmask,
-                                                tew ? reinterpret_cast<float *>(out.tEW) : nullptr, out.dpart);
+                                                tew ? reinterpret_cast<float *>(out.tEW) : nullptr, out.dpart,
+                                                out.form);
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
@@ -183,7 +119,9 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
     const cudaStream_t bs = s;
     cudaStream_t s = fork ? ctx.side[k % ctx.side.size()] : bs;
     const bool cl = b.cluster > 1;
-    if (!f64) {
+    if (out.form == kFormTersoff) {
+      e = launch_bucket_tersoff_form(bp, b, f64, out.pdl, s);
+    } else if (!f64) {
       const bool tuned = b.tune_P == P && b.tune_mode == mode;
       if (!cl && b.mmax <= 4 && tuned && b.tune_pt == 16 && b.smem16 > 0)
         e = launch_variant<16, 4, false, 3, float>(bp, b, out.pdl, s);

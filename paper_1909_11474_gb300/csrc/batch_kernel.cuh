@@ -72,13 +72,21 @@ __device__ __forceinline__ void sst(T *p, const T &v, int site) {
   if (smem_ok(p, site)) *p = v;
 }
 
-// Per-parameter-set constants (prepared once per call by prep_kernel from the FP64 parameters):
-// x = exp(-alpha (r - r0)) = 2^(k1 r + k0), f_R = D0 x^2, f_A = 2 D0 x (Eq. 4-5, 11-14 at S = 2);
-// mha = -alpha/2; inv2n = -1/(2n).
+// Per-parameter-set constants (prepared once per call by prep_kernel from the FP64 parameters).
+// Minimal form: x = exp(-alpha (r - r0)) = 2^(k1 r + k0), f_R = D0 x^2, f_A = 2 D0 x (Eq. 4-5,
+// 11-14 at S = 2); mha = -alpha/2; inv2n = -1/(2n).
+// Tersoff form (Eq. 8, free S): f_A / 2 = D0 2^(k1 (r - k0)) with D0 = D0 S / (2 (S - 1)),
+// k1 = -mu log2(e), mu = alpha sqrt(2/S), k0 = r0; f_R = cR 2^(kR1 (r - k0)) with cR = D0 / (S - 1),
+// kR1 = -lambda log2(e), lambda = alpha sqrt(2 S); mha = mu, hl = -lambda / 2. The angular function of Eq. 8,
+// gamma (1 + c^2/d^2 - c^2/(d^2 + u^2)) with u = cos - h, is evaluated as the equal
+// g = g0 + gcd u^2 / (d2 + u^2) (g0 = gamma, gcd = gamma c^2/d^2, d2 = d^2), which has no cancellation
+// of its large terms; g'/2 = gc2 u / (d2 + u^2)^2 with gc2 = gamma c^2.
 template <typename R>
 struct PConsts {
   R D0, k1, k0, mha, beta, h, n, inv2n;
+  R cR, kR1, kR0, hl, g0, gc2, d2, gcd;
 };
+constexpr int kFormMinimal = 0, kFormTersoff = 1;
 
 // b = (1 + zeta^n)^(-1/(2n)) and b' = db/dzeta = -1/2 b zeta^(n-1) / (1 + zeta^n)   (Eq. 6).
 // zeta is clamped to 1e-30 from below: at zeta = 0 this gives b = 1 to working precision, and b'
@@ -117,7 +125,7 @@ __host__ __device__ constexpr int stage_stride() {
 //   c_ij = dU_i/dzeta_ij = -1/2 f_C f_A b' = f_C (b h_A) zeta^n / (zeta u2),
 //   rad_ij = 1/2 [f_C' (f_R - b f_A) + f_C (f_R' - b f_A')],   f_R' - b f_A' = -alpha (2 f_R - b f_A),
 // the same quantities as Eq. 3-6 and their derivatives, with the constant factors folded.
-template <int M, bool INNER, typename T, typename R>
+template <int M, bool INNER, typename T, typename R, bool GEN = false>
 __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], const R (&uz)[M],
                                           const R (&r)[M], const R (&ir2)[M], const R (&fc)[M],
                                           const R (&fcp)[M], const R *cs, const PConsts<T> &K, T &U,
@@ -125,11 +133,18 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
   // ---- pass 1: pair functions (Eq. 4-5 with Eq. 11-14 at S = 2) and zeta (Eq. 7, 10)
   constexpr int NP = M * (M - 1) / 2;
   T fR[M], hA[M], zeta[M], tq[NP > 0 ? NP : 1];
+  T gq[GEN && NP > 0 ? NP : 1];                    // g itself (Tersoff form; the minimal form has g = t u)
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    const T x = ex2(r[j] * K.k1 + K.k0);
-    hA[j] = K.D0 * x;                              // f_A / 2
-    fR[j] = hA[j] * x;
+    if constexpr (GEN) {                           // exponents of r - r0 (exact in FP32 near r0)
+      const T dr = r[j] - K.k0;
+      hA[j] = K.D0 * ex2(dr * K.k1);               // f_A / 2
+      fR[j] = K.cR * ex2(dr * K.kR1);
+    } else {
+      const T x = ex2(r[j] * K.k1 + K.k0);
+      hA[j] = K.D0 * x;                            // f_A / 2
+      fR[j] = hA[j] * x;
+    }
     zeta[j] = T(0.0f);
   }
   {
@@ -139,9 +154,18 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
 #pragma unroll
       for (int k = j + 1; k < M; ++k) {
         const T u = cs[q] - K.h;
-        const T t = K.beta * u;                     // g = t u, g' = 2 t
-        const T g = t * u;
-        tq[q] = t;
+        T g;
+        if constexpr (GEN) {                       // Eq. 8, in the form without cancellation
+          const T u2 = u * u;
+          const T iv = rcp(u2 + K.d2);
+          g = K.g0 + K.gcd * u2 * iv;
+          tq[q] = K.gc2 * u * iv * iv;                // g' / 2
+          gq[q] = g;
+        } else {
+          const T t = K.beta * u;                   // g = t u, g' = 2 t
+          g = t * u;
+          tq[q] = t;
+        }
         zeta[j] += fc[k] * g;
         zeta[k] += fc[j] * g;
         ++q;
@@ -160,7 +184,9 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
     const T e = bh * R(-2) + fR[j];                // f_R - b f_A
     U += fc[j] * e;                                // Eq. 3 (the 1/2 of Eq. 2 is applied by callers)
     cc[j] = fc[j] * bh * zn * rcp(z * u2);         // dU_i / dzeta_ij
-    const T mde = K.mha * (fR[j] + e);             // (f_R' - b f_A') / 2
+    T mde;                                         // (f_R' - b f_A') / 2
+    if constexpr (GEN) mde = K.hl * fR[j] + K.mha * bh;   // (-lambda f_R + mu b f_A) / 2
+    else mde = K.mha * (fR[j] + e);
     rad[j] = R(0.5) * fcp[j] * e + fc[j] * mde;
   }
 
@@ -197,7 +223,9 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
     for (int j = 0; j < M; ++j) {
 #pragma unroll
       for (int k = j + 1; k < M; ++k) {
-        const T g = tq[q] * (cs[q] - K.h);
+        T g;
+        if constexpr (GEN) g = gq[q];
+        else g = tq[q] * (cs[q] - K.h);
         Rg[j] += cc[k] * g;
         Rg[k] += cc[j] * g;
         ++q;
@@ -220,7 +248,7 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
 // sA/sB: bond records (u_x, u_y, u_z, r), (2/r, f_C, f_C', rev | j << 16); sC: pair cosines; lb/lq: this
 // atom's first bond / pair in shared memory; m: its neighbour count (<= M). EXACT: every slot has
 // m == M, so no bond is a phantom.
-template <int M, int PT, bool EXACT, bool INNER, typename R>
+template <int M, int PT, bool EXACT, bool INNER, typename R, bool GEN = false>
 __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restrict__ sA,
                                              const typename Vec4<R>::T *__restrict__ sB,
                                              const R *__restrict__ sC, R *__restrict__ stage,
@@ -271,7 +299,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
 
   R U, Px[M], Py[M], Pz[M];
-  atom_core<M, INNER, R, R>(ux, uy, uz, r, ir2, fc, fcp, cs, K, U, Px, Py, Pz);
+  atom_core<M, INNER, R, R, GEN>(ux, uy, uz, r, ir2, fc, fcp, cs, K, U, Px, Py, Pz);
   R W0 = R(0), W1 = R(0), W2 = R(0), W3 = R(0), W4 = R(0), W5 = R(0);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
@@ -292,7 +320,7 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
 }
 
-template <int PT, int MMAX, bool EXACT, bool INNER, typename R>
+template <int PT, int MMAX, bool EXACT, bool INNER, typename R, bool GEN = false>
 __device__ __forceinline__ void atom_forward_dispatch(int Mw, const typename Vec4<R>::T *sA,
                                                       const typename Vec4<R>::T *sB, const R *sC,
                                                       R *stage, int lb, int lq, int m, bool store,
@@ -300,7 +328,7 @@ __device__ __forceinline__ void atom_forward_dispatch(int Mw, const typename Vec
 #define TSF_CASE(MM)                                                                          \
   case MM:                                                                                    \
     if constexpr (MMAX >= MM)                                                                 \
-      atom_forward<MM, PT, EXACT, INNER, R>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); \
+      atom_forward<MM, PT, EXACT, INNER, R, GEN>(sA, sB, sC, stage, lb, lq, m, store, pl, K, acc); \
     break;
   switch (Mw) {
     TSF_CASE(1) TSF_CASE(2) TSF_CASE(3) TSF_CASE(4) TSF_CASE(5) TSF_CASE(6) TSF_CASE(7) TSF_CASE(8)
@@ -494,7 +522,7 @@ struct TileEnv {
   const int *peer_b0;
 };
 
-template <int PTT, int PTW, int MMAX, bool CLUSTER, typename R, int NW>
+template <int PTT, int PTW, int MMAX, bool CLUSTER, typename R, int NW, bool GEN = false>
 __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R> &env, int tile) {
   using R4 = typename Vec4<R>::T;
   constexpr int APW = kWarp / PTT;
@@ -521,10 +549,16 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
   const bool active = p < a.P;
   PConsts<R> K;
   {
-    const R4 *kc = reinterpret_cast<const R4 *>(a.consts) + 2 * (active ? p : a.P - 1);
+    constexpr int kStride = GEN ? 4 : 2;          // R4 records of constants per parameter set
+    const R4 *kc = reinterpret_cast<const R4 *>(a.consts) + kStride * (active ? p : a.P - 1);
     const R4 k0 = kc[0], k1 = kc[1];
     K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.mha = k0.w;
     K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
+    if constexpr (GEN) {
+      const R4 k2 = kc[2], k3 = kc[3];
+      K.cR = k2.x; K.kR1 = k2.y; K.kR0 = k2.z; K.hl = k2.w;
+      K.g0 = k3.x; K.gc2 = k3.y; K.d2 = k3.z; K.gcd = k3.w;
+    }
   }
   AtomAcc<R> acc;
   acc.U = R(0);
@@ -544,9 +578,9 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
         continue;
       }
       if (sizeof(R) == 4 && at.w == 0)
-        atom_forward_dispatch<PTT, MMAX, true, sizeof(R) == 4, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+        atom_forward_dispatch<PTT, MMAX, true, sizeof(R) == 4, R, GEN>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
       else
-        atom_forward_dispatch<PTT, MMAX, true, false, R>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+        atom_forward_dispatch<PTT, MMAX, true, false, R, GEN>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
     } else {
       const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
       const bool uniform = __all_sync(0xffffffffu, m == Mw);
@@ -555,11 +589,11 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
         continue;
       }
       if (uniform && sizeof(R) == 4 && __all_sync(0xffffffffu, at.w == 0))
-        atom_forward_dispatch<PTT, MMAX, true, sizeof(R) == 4, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+        atom_forward_dispatch<PTT, MMAX, true, sizeof(R) == 4, R, GEN>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
       else if (uniform)
-        atom_forward_dispatch<PTT, MMAX, true, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+        atom_forward_dispatch<PTT, MMAX, true, false, R, GEN>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
       else
-        atom_forward_dispatch<PTT, MMAX, false, false, R>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
+        atom_forward_dispatch<PTT, MMAX, false, false, R, GEN>(Mw, sA, sB, sC, stage, at.x, at.y, m, valid, pl, K, acc);
     }
   }
   if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
@@ -710,7 +744,7 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 // split into nchunks chunks of chunk_tiles parameter tiles; a CTA (or cluster) claims the next item
 // from an atomic counter, stages the configuration's geometry once (single-CTA launches: one TMA
 // bulk copy per array, completed on an mbarrier) and runs the chunk's tiles.
-template <int PT, int MMAX, bool CLUSTER, int MINB, typename R, int NW = kNW>
+template <int PT, int MMAX, bool CLUSTER, int MINB, typename R, int NW = kNW, bool GEN = false>
 __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchParams a) {
   using R4 = typename Vec4<R>::T;
   extern __shared__ __align__(32) unsigned char smem[];
@@ -857,10 +891,10 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
     constexpr bool kNarrow = !CLUSTER && MMAX <= 4 && sizeof(R) == 4 && PT >= 16;
     for (int tile = tile0; tile < tile1; ++tile) {
       const int width = min(PT, a.P - tile * PT);
-      if (kNarrow && a.narrow && width <= 8) tile_pass<(kNarrow ? 8 : PT), PT, MMAX, CLUSTER, R, NW>(a, env, tile);
+      if (kNarrow && a.narrow && width <= 8) tile_pass<(kNarrow ? 8 : PT), PT, MMAX, CLUSTER, R, NW, GEN>(a, env, tile);
       else if (kNarrow && PT > 16 && a.narrow && width <= 16)
-        tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R, NW>(a, env, tile);
-      else tile_pass<PT, PT, MMAX, CLUSTER, R, NW>(a, env, tile);
+        tile_pass<(kNarrow ? 16 : PT), PT, MMAX, CLUSTER, R, NW, GEN>(a, env, tile);
+      else tile_pass<PT, PT, MMAX, CLUSTER, R, NW, GEN>(a, env, tile);
     }
   }
 }
@@ -875,7 +909,8 @@ __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restr
                             typename Vec4<R>::T *__restrict__ tF4, int C = 0,
                             const int *__restrict__ atom_off = nullptr, const double *__restrict__ tE = nullptr,
                             const double *__restrict__ tW = nullptr, const uint8_t *__restrict__ tmask = nullptr,
-                            R *__restrict__ tEW = nullptr, double *__restrict__ dpart = nullptr) {
+                            R *__restrict__ tEW = nullptr, double *__restrict__ dpart = nullptr,
+                            int form = kFormMinimal) {
   pdl_trigger();   // the batched kernel may start staging geometry; it waits before reading our output
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tEW && t < C) {
@@ -889,7 +924,7 @@ __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restr
     dpart[3 * t] = (m & 1) ? tE[t] * tE[t] : 0.0;
     dpart[3 * t + 1] = (m & 2) ? dv : 0.0;
   }
-  if (t < P) {
+  if (t < P && form == kFormMinimal) {
     const double *x = params + 6 * t;
     const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
     const double log2e = 1.4426950408889634;
@@ -902,6 +937,28 @@ __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restr
     o[5] = (R)h;
     o[6] = (R)n;
     o[7] = (R)(-0.5 / n);
+  } else if (t < P) {                              // Tersoff form: [D0, alpha, r0, S, n, h, gamma, c, d]
+    const double *x = params + 9 * t;
+    const double D0 = x[0], al = x[1], r0 = x[2], S = x[3], n = x[4], h = x[5], ga = x[6], c = x[7], d = x[8];
+    const double log2e = 1.4426950408889634;
+    const double lam = al * sqrt(2.0 * S), mu = al * sqrt(2.0 / S);   // Eq. 13-14
+    R *o = consts + 16 * t;
+    o[0] = (R)(0.5 * D0 * S / (S - 1.0));          // f_A / 2 prefactor (Eq. 12)
+    o[1] = (R)(-mu * log2e);
+    o[2] = (R)r0;
+    o[3] = (R)mu;
+    o[4] = (R)0.0;
+    o[5] = (R)h;
+    o[6] = (R)n;
+    o[7] = (R)(-0.5 / n);
+    o[8] = (R)(D0 / (S - 1.0));                    // f_R prefactor (Eq. 11)
+    o[9] = (R)(-lam * log2e);
+    o[10] = (R)0.0;
+    o[11] = (R)(-0.5 * lam);
+    o[12] = (R)ga;                                 // Eq. 8: g = gamma + gamma c^2/d^2 u^2 / (d^2 + u^2)
+    o[13] = (R)(ga * c * c);
+    o[14] = (R)(d * d);
+    o[15] = (R)(ga * c * c / (d * d));
   }
   if (tF && t < Ntot) {
     const double fx = tF[3 * t], fy = tF[3 * t + 1], fz = tF[3 * t + 2];

@@ -176,6 +176,7 @@ int run_graphed(tersoff_ctx *ctx, tsf::GraphCache &g, std::vector<uint64_t> key,
   }
   key.push_back(tsf::buffer_generation());
   key.push_back((uint64_t)c.device);
+  key.push_back((uint64_t)c.form);
   if (!g.exec || g.key != key) {
     if (g.exec) {
       cudaGraphExecDestroy(g.exec);
@@ -219,9 +220,10 @@ int queue_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const terso
   TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
   TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
-  TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
+  TSF_CUDA(c.work.ensure((size_t)P * (c.form ? 16 : 8) * sizeof(double)));
   TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
+  o.form = c.form;
   o.counters = c.counters.as<int>();
   o.consts = c.work.p;
   o.tEW = c.tew.p;
@@ -364,6 +366,13 @@ void tersoff_destroy(tersoff_ctx *ctx) {
 }
 
 int64_t tersoff_kernel_launches(void) { return (int64_t)tsf::g_launches.load(); }
+
+int tersoff_set_form(tersoff_ctx *ctx, int32_t form) {
+  if (!ctx) return TERSOFF_E_ARG;
+  if (form != TERSOFF_FORM_MINIMAL && form != TERSOFF_FORM_TERSOFF) return fail(ctx, TERSOFF_E_ARG, "unknown form%s");
+  ctx->c.form = form;
+  return TERSOFF_OK;
+}
 
 int tersoff_set_launch_mode(tersoff_ctx *ctx, int32_t mode) {
   if (!ctx) return TERSOFF_E_ARG;
@@ -575,9 +584,10 @@ int tersoff_eval(tersoff_ctx *ctx, const double *params, int32_t P, int32_t prec
   int rc = build_plan(ctx, precision);
   if (rc) return rc;
   if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
-  TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
+  TSF_CUDA(c.work.ensure((size_t)P * (c.form ? 16 : 8) * sizeof(double)));
   TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
+  o.form = c.form;
   o.counters = c.counters.as<int>();
   o.E = E;
   o.F = F;
@@ -620,6 +630,7 @@ int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const te
                      int32_t precision, int32_t reps, double *best_ms, int32_t *tried, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
+  if (c.form != 0) return fail(ctx, TERSOFF_E_UNSUPPORTED, "only the batched evaluation and fitness take the Tersoff form%s");
   if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !tg) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
   if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
@@ -633,9 +644,10 @@ int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const te
   TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
   TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
-  TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
+  TSF_CUDA(c.work.ensure((size_t)P * (c.form ? 16 : 8) * sizeof(double)));
   TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
+  o.form = c.form;
   o.counters = c.counters.as<int>();
   o.consts = c.work.p;
   o.tEW = c.tew.p;
@@ -712,6 +724,7 @@ int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const 
                        const double *w, int32_t loss, double *L, double *dL, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
+  if (c.form != 0) return fail(ctx, TERSOFF_E_UNSUPPORTED, "only the batched evaluation and fitness take the Tersoff form%s");
   if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !tg || !w || !L || !dL) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
   if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
@@ -735,6 +748,7 @@ int tersoff_eval_plain(tersoff_ctx *ctx, const double *params, int32_t P, double
                        double *W, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
+  if (c.form != 0) return fail(ctx, TERSOFF_E_UNSUPPORTED, "only the batched evaluation and fitness take the Tersoff form%s");
   if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !E || !F || !W) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
   if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
@@ -748,6 +762,7 @@ int tersoff_md_force(tersoff_ctx *ctx, int32_t N, const double *pos, const doubl
                      double *E, void *F, double *W, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
+  if (c.form != 0) return fail(ctx, TERSOFF_E_UNSUPPORTED, "only the batched evaluation and fitness take the Tersoff form%s");
   if (N < 1 || N > (1 << 24) || !pos || !box || !params || !E || !F || !W)
     return fail(ctx, TERSOFF_E_ARG, "need 1 <= N <= 2^24 and non-null pointers%s");
   if (!(R1 > 0.0 && R2 > R1 && std::isfinite(R2))) return fail(ctx, TERSOFF_E_ARG, "need 0 < R1 < R2%s");
@@ -767,6 +782,7 @@ int tersoff_md_nve(tersoff_ctx *ctx, int32_t N, double *pos, double *vel, const 
                    int32_t nsteps, double *Epot, double *Ekin, void *F, double *W, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
+  if (c.form != 0) return fail(ctx, TERSOFF_E_UNSUPPORTED, "only the batched evaluation and fitness take the Tersoff form%s");
   if (N < 1 || N > (1 << 24) || !pos || !vel || !mass || !box || !params || !Epot || !Ekin || !F || !W)
     return fail(ctx, TERSOFF_E_ARG, "need 1 <= N <= 2^24 and non-null pointers%s");
   if (pos == vel) return fail(ctx, TERSOFF_E_ARG, "pos and vel must be distinct arrays%s");

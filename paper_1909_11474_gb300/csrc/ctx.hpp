@@ -203,6 +203,7 @@ struct Ctx {
   // --- launch mode of the per-call launch sequences (CUDA graphs, programmatic dependent launch) ---
   bool graphs = true;
   bool pdl = true;
+  int form = 0;            // TERSOFF_FORM_*: parameter vectors of 6 (minimal) or 9 (Tersoff form)
   cudaStream_t cap_stream = nullptr;   // private stream the sequences are captured on
   GraphCache g_fitness;
 };
@@ -247,6 +248,7 @@ struct BatchOut {
   void *consts;       // workspace: [P][8] per-parameter-set constants (working precision)
   int *counters;      // workspace: one work counter per launch bucket
   bool pdl = false;   // launch the batched kernels with programmatic stream serialization
+  int form = 0;       // 0: minimal (6 parameters), 1: Tersoff form (9 parameters, Eq. 8, free S)
 };
 enum BatchMode { kModeEval = 0, kModeFitness = 1 };
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,

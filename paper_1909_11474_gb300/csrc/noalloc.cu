@@ -36,6 +36,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
                                       double *Z, double *Zq, double *S, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   tsf::Ctx &c = ctx->c;
+  if (c.form != 0) return set_error(ctx, TERSOFF_E_UNSUPPORTED, "the allocation-free fitness takes the minimal form only");
   if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !tg || !w || !Z) return set_error(ctx, TERSOFF_E_ARG, "null argument or P < 1");
   if (!tg->E || !tg->W || !tg->F || !tg->mask) return set_error(ctx, TERSOFF_E_ARG, "null target pointer");
