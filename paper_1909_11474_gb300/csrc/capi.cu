@@ -62,21 +62,24 @@ int build_plan(tersoff_ctx *ctx, int precision) {
   std::map<Key, size_t> smem, adj_smem, smem16, smem12;
   for (int cf = 0; cf < c.C; ++cf) {
     const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
+    // the smallest cluster whose CTAs fit two per SM; failing that, the smallest of 8 or 16 CTAs that
+    // fits at all (one CTA per SM)
     int chosen = 0;
     size_t need = 0;
-    for (int cl = 1; cl <= 16 && !chosen; cl *= 2) {
-      if (cl > 1 && (cl / 2) >= nat) break;
-      const int per = (nat + cl - 1) / cl;
-      size_t mx = 0;
-      for (int r = 0; r < cl; ++r) {
-        const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
-        const int nb = c.h_boff[s1] - c.h_boff[s0], nq = c.h_poff[s1] - c.h_poff[s0];
-        mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, s1 - s0, cl > 1));
-      }
-      const size_t lim = (cl >= 8) ? (size_t)optin : soft;
-      if (mx <= lim) {
-        chosen = cl;
-        need = mx;
+    for (int pass = 0; pass < 2 && !chosen; ++pass) {
+      for (int cl = pass == 0 ? 1 : 8; cl <= 16 && !chosen; cl *= 2) {
+        if (cl > 1 && (cl / 2) >= nat) break;
+        const int per = (nat + cl - 1) / cl;
+        size_t mx = 0;
+        for (int r = 0; r < cl; ++r) {
+          const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
+          const int nb = c.h_boff[s1] - c.h_boff[s0], nq = c.h_poff[s1] - c.h_poff[s0];
+          mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, s1 - s0, cl > 1));
+        }
+        if (mx <= (pass == 0 ? soft : (size_t)optin)) {
+          chosen = cl;
+          need = mx;
+        }
       }
     }
     if (!chosen) return fail(ctx, TERSOFF_E_UNSUPPORTED, "configuration too large for the batched kernels%s");

@@ -346,3 +346,21 @@ def test_fitness_queued_before_rebuild_check(ctx, change_counts):
     Z2, Zq2, S2 = fresh.fitness(params, tg)
     ref = torch.cat([Z2[:, None], Zq2, S2], 1).cpu().numpy()
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_large_cells_in_clusters_eval(ctx, precision):
+    """Cells of up to 512 atoms with up to 6 neighbours per atom (the uneven workload's largest): the
+    schedule spreads each over a thread-block cluster of up to 16 CTAs; E/F/W against the oracle."""
+    w = I.workload_uneven(P=2, C=24)
+    cs = w["configs"]
+    big = np.argsort(cs.natoms)[-6:]
+    pos_list = [cs.config(int(c))[0] for c in big]
+    box_list = [cs.config(int(c))[1] for c in big]
+    sub = I.pack_configs(pos_list, box_list)
+    assert sub.natoms.max() >= 380
+    _build(ctx, sub)
+    _compare_eval(ctx, sub, w["params"][:2], precision, TOL32 if precision == 32 else TOL64)
+    clusters = sorted({b["cluster"] for b in ctx.schedule_info(precision)})
+    print("cluster sizes", clusters)
+    assert max(clusters) >= 8
