@@ -63,7 +63,9 @@ int build_plan(tersoff_ctx *ctx, int precision) {
   for (int cf = 0; cf < c.C; ++cf) {
     const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
     // the smallest cluster whose CTAs fit two per SM; failing that, the smallest of 8 or 16 CTAs that
-    // fits at all (one CTA per SM)
+    // fits at all (one CTA per SM). FP64 variants run one CTA per SM whatever their shared memory
+    // (registers), so there clusters of 8 or more take the whole opt-in limit from the first pass.
+    const bool one_per_sm = precision == 64;
     int chosen = 0;
     size_t need = 0;
     for (int pass = 0; pass < 2 && !chosen; ++pass) {
@@ -76,7 +78,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
           const int nb = c.h_boff[s1] - c.h_boff[s0], nq = c.h_poff[s1] - c.h_poff[s0];
           mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, s1 - s0, cl > 1));
         }
-        if (mx <= (pass == 0 ? soft : (size_t)optin)) {
+        if (mx <= (pass == 0 && !(one_per_sm && cl >= 8) ? soft : (size_t)optin)) {
           chosen = cl;
           need = mx;
         }
