@@ -208,17 +208,19 @@ int tersoff_schedule_info(tersoff_ctx *ctx, int32_t precision, int32_t bucket, i
  * P - N_par children by uniform crossover (a child draws two parents uniformly from the N_par and
  * takes each gene from the first with probability 1/2), then replace each gene of every individual
  * but the elite with probability `rate` by a fresh uniform value.
- *  Z device [P] double; genes_in, genes_out device [P][6] double in [0, 1] (distinct buffers);
- *  uniforms device double in [0, 1): 8 (P - N_par) + 12 (P - 1) values laid out as: child c uses
- *  u[8c], u[8c+1] to pick its parents (index floor(u N_par)) and u[8c+2+g] < 1/2 to take gene g from
- *  the first; from base = 8 (P - N_par), individual i >= 1 uses u[base + 12(i-1) + 2g] < rate to
- *  mutate gene g and u[base + 12(i-1) + 2g + 1] as its new value;
- *  lo, hi device [6]: parameter limits, params_out device [P][6] = lo + genes_out (hi - lo) (Sec. III.B,
- *  step 1); order device [P] int32 (may be NULL): individuals from best to worst.
- * 1 <= N_par <= P <= 4096, 0 <= rate <= 1, else TERSOFF_E_ARG. Stream-ordered, one kernel. */
-int tersoff_ga_step(int32_t P, int32_t n_par, double rate, const double *Z, const double *genes_in,
-                    const double *uniforms, const double *lo, const double *hi, double *genes_out,
-                    double *params_out, int32_t *order, tersoff_stream stream);
+ *  n_genes = G: genes per individual, 1..16 (6 for the minimal potential, 9 for the Tersoff form).
+ *  Z device [P] double; genes_in, genes_out device [P][G] double in [0, 1] (distinct buffers);
+ *  uniforms device double in [0, 1): (G+2)(P - N_par) + 2G(P - 1) values laid out as: child c uses
+ *  u[(G+2)c], u[(G+2)c+1] to pick its parents (index floor(u N_par)) and u[(G+2)c+2+g] < 1/2 to
+ *  take gene g from the first; from base = (G+2)(P - N_par), individual i >= 1 uses
+ *  u[base + 2G(i-1) + 2g] < rate to mutate gene g and u[base + 2G(i-1) + 2g + 1] as its new value;
+ *  lo, hi device [G]: parameter limits, params_out device [P][G] = lo + genes_out (hi - lo)
+ *  (Sec. III.B, step 1); order device [P] int32 (may be NULL): individuals from best to worst.
+ * 1 <= N_par <= P <= 4096, 1 <= G <= 16, 0 <= rate <= 1, else TERSOFF_E_ARG. Stream-ordered, one
+ * kernel. */
+int tersoff_ga_step(int32_t P, int32_t n_genes, int32_t n_par, double rate, const double *Z,
+                    const double *genes_in, const double *uniforms, const double *lo, const double *hi,
+                    double *genes_out, double *params_out, int32_t *order, tersoff_stream stream);
 
 /* Loss and its gradient with respect to x = [D0, alpha, r0, beta, n, h] for every parameter set.
  *  loss TERSOFF_LOSS_SQ or TERSOFF_LOSS_Z (the latter has a zero gradient term where S_q = 0);

@@ -21,10 +21,11 @@ Readings where the paper is silent (also listed in the design notes):
   takes each gene from the first or the second with probability 1/2;
 * mutation visits every gene of every individual except the elite; with probability `rate` the gene
   is replaced by a fresh uniform value;
-* the random numbers are passed in, laid out as: for child c, u[8c], u[8c+1] pick the two parents
-  (index floor(u * N_par)) and u[8c+2+g] < 1/2 picks parent one for gene g; then, from
-  base = 8 (N_pop - N_par), individual i >= 1 uses u[base + 12(i-1) + 2g] < rate to decide a
-  mutation of gene g and u[base + 12(i-1) + 2g + 1] as its new value.
+* the random numbers are passed in, laid out for G genes per individual (G = 6 for the minimal
+  potential, 9 for the Tersoff form) as: for child c, u[(G+2)c], u[(G+2)c+1] pick the two parents
+  (index floor(u * N_par)) and u[(G+2)c+2+g] < 1/2 picks parent one for gene g; then, from
+  base = (G+2) (N_pop - N_par), individual i >= 1 uses u[base + 2G(i-1) + 2g] < rate to decide a
+  mutation of gene g and u[base + 2G(i-1) + 2g + 1] as its new value.
 """
 from __future__ import annotations
 
@@ -33,9 +34,9 @@ import numpy as np
 N_GENES = 6
 
 
-def n_uniforms(n_pop: int, n_par: int) -> int:
+def n_uniforms(n_pop: int, n_par: int, n_genes: int = N_GENES) -> int:
     """Uniform random numbers one generation consumes."""
-    return 8 * (n_pop - n_par) + 2 * N_GENES * (n_pop - 1)
+    return (n_genes + 2) * (n_pop - n_par) + 2 * n_genes * (n_pop - 1)
 
 
 def rank(Z: np.ndarray) -> np.ndarray:
@@ -46,25 +47,25 @@ def rank(Z: np.ndarray) -> np.ndarray:
 
 
 def ga_step(Z, genes, uniforms, n_par: int, rate: float):
-    """One generation (Sec. III.B, steps 2a-2e). Returns (new genes [N_pop][6], rank order)."""
+    """One generation (Sec. III.B, steps 2a-2e). Returns (new genes [N_pop][G], rank order)."""
     genes = np.asarray(genes, dtype=np.float64)
     u = np.asarray(uniforms, dtype=np.float64)
-    n_pop = genes.shape[0]
-    assert genes.shape == (n_pop, N_GENES) and 1 <= n_par <= n_pop
-    assert len(u) >= n_uniforms(n_pop, n_par)
+    n_pop, G = genes.shape
+    assert 1 <= n_par <= n_pop and G >= 1
+    assert len(u) >= n_uniforms(n_pop, n_par, G)
     order = rank(Z)
     ranked = genes[order]
     new = np.empty_like(genes)
     new[:n_par] = ranked[:n_par]                        # elite first, then the other parents
     for c in range(n_pop - n_par):                      # uniform crossover
-        a = min(int(u[8 * c] * n_par), n_par - 1)
-        b = min(int(u[8 * c + 1] * n_par), n_par - 1)
-        for g in range(N_GENES):
-            new[n_par + c, g] = ranked[a, g] if u[8 * c + 2 + g] < 0.5 else ranked[b, g]
-    base = 8 * (n_pop - n_par)
+        a = min(int(u[(G + 2) * c] * n_par), n_par - 1)
+        b = min(int(u[(G + 2) * c + 1] * n_par), n_par - 1)
+        for g in range(G):
+            new[n_par + c, g] = ranked[a, g] if u[(G + 2) * c + 2 + g] < 0.5 else ranked[b, g]
+    base = (G + 2) * (n_pop - n_par)
     for i in range(1, n_pop):                           # mutation, the elite excepted
-        for g in range(N_GENES):
-            k = base + 2 * N_GENES * (i - 1) + 2 * g
+        for g in range(G):
+            k = base + 2 * G * (i - 1) + 2 * g
             if u[k] < rate:
                 new[i, g] = u[k + 1]
     return new, order

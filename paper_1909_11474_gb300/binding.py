@@ -86,7 +86,7 @@ def load():
         "tersoff_set_launch_mode": (ctypes.c_int, [_vp, _i32]),
         "tersoff_set_schedule": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
         "tersoff_schedule_info": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
-        "tersoff_ga_step": (ctypes.c_int, [_i32, _i32, _f64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "tersoff_ga_step": (ctypes.c_int, [_i32, _i32, _i32, _f64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "tersoff_autotune": (ctypes.c_int, [_vp, _vp, _i32, ctypes.POINTER(_Targets), _i32, _i32,
                                             ctypes.POINTER(_f64), ctypes.POINTER(_i32), _vp]),
         "tersoff_profile_read": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_f64)]),
@@ -103,20 +103,22 @@ def load():
 
 def ga_step(Z: torch.Tensor, genes_in: torch.Tensor, uniforms: torch.Tensor, lo: torch.Tensor, hi: torch.Tensor,
             n_par: int, rate: float, genes_out: torch.Tensor, params_out: torch.Tensor, order=None, stream=None):
-    """One GA generation on the device (tersoff_ga_step); all tensors CUDA float64 (order int32)."""
+    """One GA generation on the device (tersoff_ga_step); all tensors CUDA float64 (order int32);
+    genes [P][G] with G = len(lo)."""
     P = genes_in.shape[0]
+    G = lo.shape[0]
     _cuda(Z, torch.float64, (P,), "Z")
-    _cuda(genes_in, torch.float64, (P, 6), "genes_in")
-    _cuda(genes_out, torch.float64, (P, 6), "genes_out")
-    _cuda(params_out, torch.float64, (P, 6), "params_out")
-    _cuda(lo, torch.float64, (6,), "lo")
-    _cuda(hi, torch.float64, (6,), "hi")
+    _cuda(genes_in, torch.float64, (P, G), "genes_in")
+    _cuda(genes_out, torch.float64, (P, G), "genes_out")
+    _cuda(params_out, torch.float64, (P, G), "params_out")
+    _cuda(lo, torch.float64, (G,), "lo")
+    _cuda(hi, torch.float64, (G,), "hi")
     _cuda(uniforms, torch.float64, None, "uniforms")
-    if uniforms.numel() < 8 * (P - n_par) + 12 * (P - 1):
+    if uniforms.numel() < (G + 2) * (P - n_par) + 2 * G * (P - 1):
         raise ValueError("too few uniform random numbers for one generation")
     if order is not None:
         _cuda(order, torch.int32, (P,), "order")
-    rc = load().tersoff_ga_step(P, n_par, float(rate), Z.data_ptr(), genes_in.data_ptr(), uniforms.data_ptr(),
+    rc = load().tersoff_ga_step(P, G, n_par, float(rate), Z.data_ptr(), genes_in.data_ptr(), uniforms.data_ptr(),
                                 lo.data_ptr(), hi.data_ptr(), genes_out.data_ptr(), params_out.data_ptr(),
                                 _ptr(order), _stream(stream))
     if rc != OK:

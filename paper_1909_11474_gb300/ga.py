@@ -21,8 +21,9 @@ N_GENES = 6
 
 class GeneticFit:
     """GA over the context's configurations and targets (Sec. III.B): n_pop individuals, n_par
-    parents, genes in [0, 1] mapped to [lo, hi] per parameter, mutation rate decreasing linearly from
-    rate0 to zero over the generations."""
+    parents, genes in [0, 1] mapped to [lo, hi] per parameter (6 limits for the minimal potential, 9
+    for a context in the Tersoff form), mutation rate decreasing linearly from rate0 to zero over the
+    generations."""
 
     def __init__(self, ctx: binding.Context, targets: dict, lo, hi, n_pop: int = 200, n_par: int = 100,
                  w=(1.0, 1.0, 1.0), seed: int = 0, device=None):
@@ -33,14 +34,17 @@ class GeneticFit:
             raise ValueError("need 1 <= n_par <= n_pop")
         self.lo = torch.as_tensor(lo, dtype=torch.float64, device=device).contiguous()
         self.hi = torch.as_tensor(hi, dtype=torch.float64, device=device).contiguous()
+        self.n_genes = G = int(self.lo.numel())       # 6 (minimal potential) or 9 (Tersoff form)
+        if G != getattr(ctx, "n_params", N_GENES):
+            raise ValueError(f"{G} parameter limits for a context that takes {ctx.n_params} parameters")
         self.gen = torch.Generator(device=device)
         self.gen.manual_seed(int(seed))
-        self.genes = [torch.rand((self.n_pop, N_GENES), generator=self.gen, dtype=torch.float64, device=device),
-                      torch.empty((self.n_pop, N_GENES), dtype=torch.float64, device=device)]
+        self.genes = [torch.rand((self.n_pop, G), generator=self.gen, dtype=torch.float64, device=device),
+                      torch.empty((self.n_pop, G), dtype=torch.float64, device=device)]
         self.params = (self.lo + self.genes[0] * (self.hi - self.lo)).contiguous()
         self.Z = torch.empty(self.n_pop, dtype=torch.float64, device=device)
         self.order = torch.empty(self.n_pop, dtype=torch.int32, device=device)
-        self.n_u = 8 * (self.n_pop - self.n_par) + 2 * N_GENES * (self.n_pop - 1)
+        self.n_u = (G + 2) * (self.n_pop - self.n_par) + 2 * G * (self.n_pop - 1)
         self.u = torch.empty(self.n_u, dtype=torch.float64, device=device)
         self.cur = 0
         self.k = 0                      # generations done

@@ -12,29 +12,37 @@ from ._util import targets_to_device, to_device
 pytestmark = pytest.mark.gpu
 
 
-def _case(seed, P, n_par, bad=0, ties=0):
+XG = np.array([3.2, 1.45, 2.25, 1.9, 0.65, -0.6, 0.06, 20.0, 3.0])   # a Tersoff-form parameter set
+
+
+def _case(seed, P, n_par, bad=0, ties=0, G=6):
     rng = np.random.default_rng(seed)
     Z = rng.uniform(0.0, 2.0, P)
     for k in range(ties):
         Z[(7 * k + 1) % P] = Z[(3 * k) % P]
     for k in range(bad):
         Z[(5 * k + 2) % P] = [np.nan, np.inf, -np.inf][k % 3]
-    genes = rng.uniform(0.0, 1.0, (P, 6))
-    u = rng.uniform(0.0, 1.0, oga.n_uniforms(P, n_par) + 5)
-    lo = I.TABLE2_PARAMS - 0.3 * np.abs(I.TABLE2_PARAMS)
-    hi = I.TABLE2_PARAMS + 0.3 * np.abs(I.TABLE2_PARAMS)
+    genes = rng.uniform(0.0, 1.0, (P, G))
+    u = rng.uniform(0.0, 1.0, oga.n_uniforms(P, n_par, G) + 5)
+    x = I.TABLE2_PARAMS if G == 6 else XG
+    lo = x - 0.3 * np.abs(x)
+    hi = x + 0.3 * np.abs(x)
     return Z, genes, u, lo, hi
 
 
-@pytest.mark.parametrize("P,n_par,rate,bad,ties", [(200, 100, 0.2, 0, 0), (200, 100, 0.05, 4, 6), (7, 3, 0.5, 1, 2),
-                                                    (33, 33, 0.3, 0, 3), (1, 1, 1.0, 0, 0), (4096, 1000, 0.1, 9, 20)])
-def test_ga_step_matches_the_oracle_bit_for_bit(P, n_par, rate, bad, ties):
+@pytest.mark.parametrize("P,n_par,rate,bad,ties,G", [(200, 100, 0.2, 0, 0, 6), (200, 100, 0.05, 4, 6, 6),
+                                                      (7, 3, 0.5, 1, 2, 6), (33, 33, 0.3, 0, 3, 6),
+                                                      (1, 1, 1.0, 0, 0, 6), (4096, 1000, 0.1, 9, 20, 6),
+                                                      (200, 100, 0.2, 3, 5, 9), (37, 11, 0.4, 1, 2, 1)])
+def test_ga_step_matches_the_oracle_bit_for_bit(P, n_par, rate, bad, ties, G):
     from paper_1909_11474_gb300 import binding
-    Z, genes, u, lo, hi = _case(P + n_par, P, n_par, bad, ties)
+    Z, genes, u, lo, hi = _case(P + n_par, P, n_par, bad, ties, G)
+    if G == 1:
+        lo, hi = lo[:1], hi[:1]
     want, order = oga.ga_step(Z, genes, u, n_par, rate)
     d = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
-    g_out = torch.empty((P, 6), dtype=torch.float64, device="cuda")
-    x_out = torch.empty((P, 6), dtype=torch.float64, device="cuda")
+    g_out = torch.empty((P, G), dtype=torch.float64, device="cuda")
+    x_out = torch.empty((P, G), dtype=torch.float64, device="cuda")
     o_out = torch.empty(P, dtype=torch.int32, device="cuda")
     binding.ga_step(d(Z), d(genes), d(u), d(lo), d(hi), n_par, rate, g_out, x_out, o_out)
     assert np.array_equal(o_out.cpu().numpy(), order)
@@ -124,3 +132,32 @@ def test_ga_checkpoint_resume_is_bit_exact(tmp_path):
     assert rc["Z"] == ra["Z"]
     with pytest.raises(ValueError):
         GeneticFit(ctx, tg, lo, hi, n_pop=32, n_par=16).load_state_dict(torch.load(tmp_path / "ga.pt", weights_only=False))
+
+
+def test_ga_fits_in_the_tersoff_form():
+    """Nine genes on a context in the Tersoff form: 200 generations on noise-free targets of a
+    Tersoff-form parameter set; the elite never worsens (up to FP32 rounding) and the best fitness
+    falls at least threefold."""
+    from paper_1909_11474_gb300 import binding
+    from paper_1909_11474_gb300.ga import GeneticFit
+    w = I.workload_ga_batch(P=4, C=10)
+    cs = w["configs"]
+    ctx = binding.Context(0)
+    ctx.set_form(binding.FORM_TERSOFF)
+    pos, box = to_device(cs)
+    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+    E, F, W = ctx.eval(torch.tensor(XG[None, :], device="cuda"), precision=64)
+    natoms = cs.natoms.astype(np.float64)
+    tg = targets_to_device({"E": E[0].cpu().numpy() / natoms, "W": W[0].cpu().numpy() / natoms[:, None],
+                            "F": F[0].cpu().numpy(), "mask": np.full(cs.C, 7, np.uint8)})
+    lo, hi = XG - 0.3 * np.abs(XG), XG + 0.3 * np.abs(XG)
+    with pytest.raises(ValueError):
+        GeneticFit(ctx, tg, lo[:6], hi[:6])                 # six limits for a nine-parameter context
+    fit = GeneticFit(ctx, tg, lo, hi, n_pop=100, n_par=50, seed=3)
+    first = float(fit.evaluate().min())
+    res = fit.run(n_gen=200, history=True)
+    h = res["history"]
+    assert float(np.max(h[1:] / h[:-1] - 1.0)) <= 1e-4
+    assert res["Z"] < first / 3
+    assert res["params"].shape == (9,)
+    assert ctx.get_status() == 0

@@ -25,6 +25,31 @@ def test_rank_is_the_brute_force_sort():
 def test_uniform_count_and_layout():
     assert ga.n_uniforms(200, 100) == 8 * 100 + 12 * 199
     assert ga.n_uniforms(5, 5) == 12 * 4
+    assert ga.n_uniforms(200, 100, 9) == 11 * 100 + 18 * 199
+
+
+def test_nine_genes_take_the_same_steps():
+    """G = 9 (the Tersoff form): children take each gene from one of their two drawn parents, the
+    mutation replaces exactly the drawn genes, the elite is kept."""
+    rng = np.random.default_rng(8)
+    n_pop, n_par, G, rate = 16, 6, 9, 0.25
+    Z = rng.uniform(0.0, 1.0, n_pop)
+    genes = rng.uniform(0.0, 1.0, (n_pop, G))
+    u = rng.uniform(0.0, 1.0, ga.n_uniforms(n_pop, n_par, G))
+    new, order = ga.ga_step(Z, genes, u, n_par, rate)
+    ranked = genes[order]
+    assert np.array_equal(new[0], ranked[0])
+    base = (G + 2) * (n_pop - n_par)
+    for i in range(n_pop):
+        for g in range(G):
+            if i >= 1 and u[base + 2 * G * (i - 1) + 2 * g] < rate:
+                assert new[i, g] == u[base + 2 * G * (i - 1) + 2 * g + 1]
+            elif i < n_par:
+                assert new[i, g] == ranked[i, g]
+            else:
+                c = i - n_par
+                a, b = int(u[(G + 2) * c] * n_par), int(u[(G + 2) * c + 1] * n_par)
+                assert new[i, g] == (ranked[a, g] if u[(G + 2) * c + 2 + g] < 0.5 else ranked[b, g])
 
 
 def test_parents_are_the_best_in_rank_order_and_the_elite_is_kept():
