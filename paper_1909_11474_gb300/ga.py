@@ -160,6 +160,78 @@ def _newton_polish(ctx, g0, lo, hi, targets, w, loss, iters: int, h: float = 1e-
     return g
 
 
+def _fd_newton_polish(ctx, g0, lo, hi, targets, w, iters: int, h: float = 1e-4):
+    """Damped Newton in gene space on L = sum_q w_q S_q / D_q from FP64 fitness values alone (no
+    gradient kernel): each iteration evaluates, in one batched call, the point, +-h along every gene
+    and +-h along every pair of genes (1 + 2G + 2G(G-1) parameter sets), and takes the gradient and
+    Hessian by central differences; steps as in `_newton_polish`."""
+    G = g0.numel()
+    span = hi - lo
+    dev = g0.device
+    offs = [np.zeros(G)]
+    for i in range(G):
+        for s in (1.0, -1.0):
+            e = np.zeros(G)
+            e[i] = s * h
+            offs.append(e)
+    pairs = [(i, j) for i in range(G) for j in range(i + 1, G)]
+    for i, j in pairs:
+        for si, sj in ((1, 1), (1, -1), (-1, 1), (-1, -1)):
+            e = np.zeros(G)
+            e[i], e[j] = si * h, sj * h
+            offs.append(e)
+    offs = torch.as_tensor(np.stack(offs), dtype=torch.float64, device=dev)
+    D = None
+
+    def losses(pts):
+        nonlocal D
+        Z, Zq, S = ctx.fitness((lo + pts * span).contiguous(), targets, w=(1.0, 1.0, 1.0), precision=64)
+        S, Zq = S.cpu().numpy(), Zq.cpu().numpy()
+        if D is None:                                  # D_q = S_q / Zq_q^2 (Eq. 17-19), from the first point
+            D = np.where(Zq[0] > 0, S[0] / np.maximum(Zq[0] ** 2, 1e-300), np.inf)
+        return (np.asarray(w)[None, :] * S / D[None, :]).sum(-1)
+
+    def batch(gg):
+        L = losses(gg[None, :] + offs)
+        L0, Lp, Lm = L[0], L[1:1 + 2 * G:2], L[2:2 + 2 * G:2]
+        grad = (Lp - Lm) / (2 * h)
+        H = np.diag((Lp - 2 * L0 + Lm) / (h * h))
+        base = 1 + 2 * G
+        for k, (i, j) in enumerate(pairs):
+            a, b, c, d = L[base + 4 * k: base + 4 * k + 4]
+            H[i, j] = H[j, i] = (a - b - c + d) / (4 * h * h)
+        return float(L0), grad, H
+
+    g = g0.clone()
+    L, grad, H = batch(g)
+    lam = 1e-3
+    stalled = 0
+    for _ in range(iters):
+        step = None
+        for _ in range(12):
+            A = H + lam * np.diag(np.maximum(np.abs(np.diag(H)), 1e-12))
+            try:
+                d = np.linalg.solve(A, -grad)
+            except np.linalg.LinAlgError:
+                d = None
+            if d is not None and np.all(np.isfinite(d)):
+                dt = torch.as_tensor(d, dtype=torch.float64, device=dev)
+                Ln = float(losses((g + dt)[None, :])[0])
+                if Ln < L:
+                    step = dt
+                    break
+            lam *= 10.0
+        if step is None:
+            break
+        g = g + step
+        lam = max(lam / 10.0, 1e-12)
+        stalled = stalled + 1 if L - Ln <= 1e-12 * L else 0
+        if stalled == 2:
+            break
+        L, grad, H = batch(g)
+    return g
+
+
 def polish(ctx: binding.Context, params, targets: dict, lo, hi, steps: int = 30, lr: float = 2e-3,
            w=(1.0, 1.0, 1.0), loss: int = binding.LOSS_SQ, method: str = "newton"):
     """Refine one parameter set on the smooth loss L = sum_q w_q S_q / D_q in gene space, with
@@ -167,12 +239,29 @@ def polish(ctx: binding.Context, params, targets: dict, lo, hi, steps: int = 30,
     badly scaled (beta and n trade off along a long valley), so the default is a damped Newton method
     on a finite-difference Hessian of the adjoint gradient (`steps` iterations, one batched call of
     13 parameter sets each); `method="lbfgs"` (strong-Wolfe line search) and `method="adam"` (rate
-    `lr`) are first-order alternatives. Returns (params, loss before, loss after)."""
+    `lr`) are first-order alternatives. On a context in the Tersoff form, which the gradient kernel
+    does not take (or with `method="fd-newton"`), the damped Newton step takes its gradient and
+    Hessian by central differences of the FP64 fitness instead. Returns (params, loss before, loss
+    after)."""
     dev = torch.device("cuda")
     lo = torch.as_tensor(lo, dtype=torch.float64, device=dev)
     hi = torch.as_tensor(hi, dtype=torch.float64, device=dev)
-    x0 = torch.as_tensor(params, dtype=torch.float64, device=dev).reshape(1, N_GENES)
+    G = int(lo.numel())
+    x0 = torch.as_tensor(params, dtype=torch.float64, device=dev).reshape(1, G)
     g0 = ((x0 - lo) / (hi - lo))
+    if getattr(ctx, "form", binding.FORM_MINIMAL) == binding.FORM_TERSOFF or method == "fd-newton":
+        if loss != binding.LOSS_SQ:
+            raise ValueError("the finite-difference polish minimises L_sq")
+
+        def L_of(x):
+            Z, Zq, S = ctx.fitness(x.contiguous(), targets, w=(1.0, 1.0, 1.0), precision=64)
+            D = (S / torch.clamp(Zq * Zq, min=1e-300)).cpu().numpy()[0]
+            return float((np.asarray(w) * S.cpu().numpy()[0] / D).sum())
+
+        first = L_of(x0)
+        g = _fd_newton_polish(ctx, g0[0], lo, hi, targets, w, int(steps)).reshape(1, G)
+        x = (lo + g * (hi - lo)).contiguous()
+        return x[0].cpu().numpy(), first, L_of(x)
     first = float(ctx.param_grad(x0.contiguous(), targets, w=w, loss=loss)[0][0])
     if method == "newton":
         g = _newton_polish(ctx, g0[0], lo, hi, targets, w, loss, int(steps)).reshape(1, N_GENES)

@@ -54,3 +54,30 @@ def test_newton_polish_never_raises_the_loss():
         g = _newton_polish(f, g0, lo, hi, None, None, None, iters=iters)
         L1 = float(f.param_grad((lo + g * (hi - lo))[None, :], None)[0][0])
         assert L1 <= L0
+
+
+class _ValleyFitness(_ValleyLoss):
+    """The same loss seen through a fitness call: S = (L, 0, 0) and Zq = (sqrt(L), 0, 0), so D = 1."""
+
+    def fitness(self, x, targets, w=None, precision=64):
+        L, _ = self.param_grad(x, targets)
+        S = torch.stack([L, torch.zeros_like(L), torch.zeros_like(L)], 1)
+        Zq = torch.sqrt(S)
+        return Zq.sum(1), Zq, S
+
+
+def test_finite_difference_newton_polish_reaches_the_minimum():
+    """The polish of the Tersoff form (gradient and Hessian from loss values in one batch) on the
+    same ill-conditioned valley: it reaches the minimum to finite-difference accuracy."""
+    from paper_1909_11474_gb300.ga import _fd_newton_polish
+    f = _ValleyFitness()
+    lo = f.xs - 0.3 * f.xs.abs()
+    hi = f.xs + 0.3 * f.xs.abs()
+    x0 = f.xs * torch.tensor([1.05, 0.97, 1.02, 1.2, 0.85, 1.1], dtype=torch.float64)
+    g0 = (x0 - lo) / (hi - lo)
+    g = _fd_newton_polish(f, g0, lo, hi, None, (1.0, 1.0, 1.0), iters=40)
+    x = lo + g * (hi - lo)
+    assert torch.allclose(x, f.xs, rtol=1e-5, atol=1e-6)
+    L1 = float(f.param_grad(x[None, :], None)[0][0])
+    L0 = float(f.param_grad(x0[None, :], None)[0][0])
+    assert L1 < 1e-10 * L0
