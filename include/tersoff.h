@@ -222,9 +222,10 @@ int tersoff_ga_step(int32_t P, int32_t n_genes, int32_t n_par, double rate, cons
                     const double *genes_in, const double *uniforms, const double *lo, const double *hi,
                     double *genes_out, double *params_out, int32_t *order, tersoff_stream stream);
 
-/* Loss and its gradient with respect to x = [D0, alpha, r0, beta, n, h] for every parameter set.
+/* Loss and its gradient with respect to x = [D0, alpha, r0, beta, n, h] for every parameter set
+ *  (x = [D0, alpha, r0, S, n, h, gamma, c, d] in the Tersoff form, tersoff_set_form).
  *  loss TERSOFF_LOSS_SQ or TERSOFF_LOSS_Z (the latter has a zero gradient term where S_q = 0);
- *  L device [P] double; dL device [P][6] double. FP32 per-pair arithmetic with FP64 accumulation of
+ *  L device [P] double; dL device [P][6] ([P][9] in the Tersoff form) double. FP32 per-pair arithmetic with FP64 accumulation of
  *  the residual sums and of the gradient. Forces enter through the directional derivative
  *  sum_i v_i . dF_i/dx = -d/dx [ sum_i sum_j (v_j - v_i) . dU_i/dd_ij ] with v_i = dL/dF_i. */
 int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const tersoff_targets *tg,
@@ -292,8 +293,9 @@ int tersoff_set_launch_mode(tersoff_ctx *ctx, int32_t mode);
  *  TERSOFF_FORM_TERSOFF: the general form, params [P][9] = (D0, alpha, r0, S, n, h, gamma, c, d):
  *    the original angular function g^T = gamma (1 + c^2/d^2 - c^2/(d^2 + (cos - h)^2)) (Eq. 8) and
  *    a free S in Eq. 11-14 (S != 1).
- * In the Tersoff form tersoff_autotune, tersoff_param_grad, tersoff_eval_plain,
- * tersoff_fitness_static, tersoff_md_force and tersoff_md_nve return TERSOFF_E_UNSUPPORTED.
+ * In the Tersoff form tersoff_param_grad returns dL [P][9], and tersoff_autotune,
+ * tersoff_eval_plain, tersoff_fitness_static, tersoff_md_force and tersoff_md_nve return
+ * TERSOFF_E_UNSUPPORTED.
  * Errors: TERSOFF_E_ARG for an unknown form. */
 #define TERSOFF_FORM_MINIMAL 0
 #define TERSOFF_FORM_TERSOFF 1

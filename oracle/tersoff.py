@@ -364,7 +364,8 @@ def fitness(configs, params, targets, w=(1.0, 1.0, 1.0), R1=R1_DEFAULT, R2=R2_DE
 
 def loss_and_grad(configs, params_row, targets, w=(1.0, 1.0, 1.0), loss: str = "sq",
                   R1=R1_DEFAULT, R2=R2_DEFAULT):
-    """Loss of one parameter set and its gradient over x = [D0, alpha, r0, beta, n, h].
+    """Loss of one parameter set and its gradient over x = [D0, alpha, r0, beta, n, h], or over the
+    nine parameters of the Tersoff form (x = [D0, alpha, r0, S, n, h, gamma, c, d]).
 
     loss = "sq": L = sum_q w_q S_q / D_q; loss = "z": Z of Eq. 15.  Forces enter through
     F = -dU/dx built with create_graph, so the gradient is exact reverse-over-reverse autograd.

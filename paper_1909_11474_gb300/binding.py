@@ -347,12 +347,12 @@ class Context:
 
     def param_grad(self, params: torch.Tensor, targets: dict, w=(1.0, 1.0, 1.0), loss: int = LOSS_SQ,
                    stream=None):
-        """L [P] and dL/dx [P][6] (FP64)."""
+        """L [P] and dL/dx [P][6] ([P][9] in the Tersoff form) (FP64)."""
         P = params.shape[0]
-        _cuda(params, torch.float64, (P, 6), "params")
+        _cuda(params, torch.float64, (P, self.n_params), "params")
         dev = params.device
         L = torch.empty(P, dtype=torch.float64, device=dev)
-        dL = torch.empty((P, 6), dtype=torch.float64, device=dev)
+        dL = torch.empty((P, self.n_params), dtype=torch.float64, device=dev)
         t = self._targets(targets)
         wv = (ctypes.c_double * 3)(*[float(x) for x in w])
         self._check(self.lib.tersoff_param_grad(self.h, params.data_ptr(), P, ctypes.byref(t), ctypes.addressof(wv),

@@ -1,5 +1,6 @@
-// adjoint.cu -- gradient of the fitness loss with respect to the six parameters
-// x = [D0, alpha, r0, beta, n, h] (Eq. 16) for many parameter sets at once.
+// adjoint.cu -- gradient of the fitness loss with respect to the parameters, x = [D0, alpha, r0,
+// beta, n, h] (Eq. 16) of the minimal potential or x = [D0, alpha, r0, S, n, h, gamma, c, d] of the
+// Tersoff form (Eq. 8, free S), for many parameter sets at once.
 //
 // For one parameter set the loss terms are S_e = sum_c (E_c/N_c - E*_c)^2,
 // S_v = sum_c sum_k (W_ck/N_c - W*_ck)^2 and S_f = sum_i |F_i - F*_i|^2 (Eq. 17-19 before the square
@@ -22,13 +23,14 @@
 namespace tsf {
 
 constexpr int kAdjPT = 32;
-constexpr int kAdjK = 2;          // parameter tangents carried per pass (3 passes for 6 parameters)
-constexpr int kAdjG = 18;         // accumulated gradient terms per lane: 3 loss terms x 6 parameters
+constexpr int kAdjK = 2;          // parameter tangents carried per pass (3 passes for 6 parameters, 5 for 9)
+constexpr int kAdjGMax = 27;      // accumulated gradient terms per lane: 3 loss terms x up to 9 parameters
 
 struct AdjParams {
   int P, C;
   int64_t Ntot;
-  const float *consts;            // [P][8] PConsts<float>
+  const float *consts;            // [P][8] PConsts<float> ([P][16] in the Tersoff form)
+  const double *params;           // [P][9] raw parameters of the Tersoff form (its tangent seeds)
   const int *boff, *poff;
   const float4 *gA, *gB;
   const float *gcos;
@@ -37,13 +39,13 @@ struct AdjParams {
   const double *tE, *tW;
   const float4 *tF4;
   const uint8_t *tmask;
-  double *part, *dpart, *gpart;   // [P][C][3], [C][3], [P][C][3][6]
+  double *part, *dpart, *gpart;   // [P][C][3], [C][3], [P][C][3][NX]
   unsigned *status;
 };
 
 __host__ __device__ inline size_t adj_region0(int nb) {
   const size_t st = (size_t)nb * 3 * kAdjPT;
-  const size_t rd = std::max<size_t>((size_t)(kNW + 1) * kNRed * kAdjPT, (size_t)kNW * kAdjG * kAdjPT);
+  const size_t rd = std::max<size_t>((size_t)(kNW + 1) * kNRed * kAdjPT, (size_t)kNW * kAdjGMax * kAdjPT);
   return ((st > rd ? st : rd) * sizeof(float) + 31) / 32 * 32 / sizeof(float);
 }
 size_t adjoint_smem_bytes(int nb, int nq, int nat) {
@@ -56,7 +58,7 @@ size_t adjoint_smem_bytes(int nb, int nq, int nat) {
 
 // Dual constants for tangents of parameters q0 .. q0+K-1 (order D0, alpha, r0, beta, n, h).
 template <int K>
-__device__ __forceinline__ PConsts<Dual<K, float>> seed_consts(const PConsts<float> &k, int q0) {
+__device__ __forceinline__ PConsts<Dual<K, float>> seed_consts_minimal(const PConsts<float> &k, int q0) {
   PConsts<Dual<K, float>> D;
   D.D0 = Dual<K, float>(k.D0);
   D.k1 = Dual<K, float>(k.k1);
@@ -88,13 +90,78 @@ __device__ __forceinline__ PConsts<Dual<K, float>> seed_consts(const PConsts<flo
   return D;
 }
 
+// Dual constants of the Tersoff form for tangents of parameters q0 .. q0+K-1 (order D0, alpha, r0, S,
+// n, h, gamma, c, d; tangents of q >= 9 stay zero). The constants (see PConsts) depend on them as
+// f_A/2 = D0 S/(2(S-1)) 2^(k1 (r - r0)), f_R = D0/(S-1) 2^(kR1 (r - r0)), k1 = -mu log2e,
+// kR1 = -lambda log2e, mu = alpha sqrt(2/S), lambda = alpha sqrt(2S), mha = mu, hl = -lambda/2,
+// g0 = gamma, gc2 = gamma c^2, d2 = d^2, gcd = gamma c^2 / d^2. x: the raw parameters.
+template <int K>
+__device__ __forceinline__ PConsts<Dual<K, float>> seed_consts_tersoff(const PConsts<float> &k, const float (&x)[9],
+                                                                      int q0) {
+  using DK = Dual<K, float>;
+  PConsts<DK> D;
+  D.D0 = DK(k.D0); D.k1 = DK(k.k1); D.k0 = DK(k.k0); D.mha = DK(k.mha);
+  D.beta = DK(k.beta); D.h = DK(k.h); D.n = DK(k.n); D.inv2n = DK(k.inv2n);
+  D.cR = DK(k.cR); D.kR1 = DK(k.kR1); D.kR0 = DK(k.kR0); D.hl = DK(k.hl);
+  D.g0 = DK(k.g0); D.gc2 = DK(k.gc2); D.d2 = DK(k.d2); D.gcd = DK(k.gcd);
+  const float D0 = x[0], alpha = x[1], S = x[3], ga = x[6], c = x[7], d = x[8];
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const int q = q0 + t;
+    if (q == 0) {                                  // f_A and f_R prefactors are proportional to D0
+      D.D0.d[t] = k.D0 / D0;
+      D.cR.d[t] = k.cR / D0;
+    }
+    if (q == 1) {                                  // mu and lambda are proportional to alpha
+      D.k1.d[t] = k.k1 / alpha;
+      D.mha.d[t] = k.mha / alpha;
+      D.kR1.d[t] = k.kR1 / alpha;
+      D.hl.d[t] = k.hl / alpha;
+    }
+    if (q == 2) D.k0.d[t] = 1.f;                   // the r0 slot
+    if (q == 3) {                                  // S: prefactors, mu ~ S^-1/2, lambda ~ S^1/2
+      D.D0.d[t] = -k.D0 / (S * (S - 1.f));
+      D.cR.d[t] = -k.cR / (S - 1.f);
+      D.k1.d[t] = -0.5f * k.k1 / S;
+      D.mha.d[t] = -0.5f * k.mha / S;
+      D.kR1.d[t] = 0.5f * k.kR1 / S;
+      D.hl.d[t] = 0.5f * k.hl / S;
+    }
+    if (q == 4) {
+      D.n.d[t] = 1.f;
+      D.inv2n.d[t] = 2.f * k.inv2n * k.inv2n;
+    }
+    if (q == 5) D.h.d[t] = 1.f;
+    if (q == 6) {                                  // gamma
+      D.g0.d[t] = 1.f;
+      D.gc2.d[t] = c * c;
+      D.gcd.d[t] = c * c / (d * d);
+    }
+    if (q == 7) {                                  // c
+      D.gc2.d[t] = 2.f * ga * c;
+      D.gcd.d[t] = 2.f * ga * c / (d * d);
+    }
+    if (q == 8) {                                  // d
+      D.d2.d[t] = 2.f * d;
+      D.gcd.d[t] = -2.f * ga * c * c / (d * d * d);
+    }
+  }
+  return D;
+}
+
+template <int K, bool GEN>
+__device__ __forceinline__ PConsts<Dual<K, float>> seed_consts(const PConsts<float> &k, const float (&x)[9], int q0) {
+  if constexpr (GEN) return seed_consts_tersoff<K>(k, x, q0);
+  else return seed_consts_minimal<K>(k, q0);
+}
+
 // One atom's tangent contribution for parameters q0.. (q0+K-1): accumulates dS_q/dx into G[q][x].
-template <int M, int K, int Q0>
+template <int M, int K, int Q0, bool GEN>
 __device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB, const float *sC, int lb,
                                              int lq, const float *vi, const float *vsm, int pl,
-                                             const float *aw, const PConsts<float> &Kf,
-                                             float (&G)[kAdjG]) {
-  constexpr int q0 = Q0;
+                                             const float *aw, const PConsts<float> &Kf, const float (&xr)[9],
+                                             float (&G)[3 * (GEN ? 9 : 6)]) {
+  constexpr int q0 = Q0, NX = GEN ? 9 : 6;
   float ux[M], uy[M], uz[M], r[M], ir2[M], fc[M], fcp[M];
   int jl[M];
 #pragma unroll
@@ -117,14 +184,15 @@ __device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB,
     }
   }
   using D = Dual<K, float>;
-  const PConsts<D> KD = seed_consts<K>(Kf, q0);
+  const PConsts<D> KD = seed_consts<K, GEN>(Kf, xr, q0);
   D U, Px[M], Py[M], Pz[M];
-  atom_core<M, false, D, float>(ux, uy, uz, r, ir2, fc, fcp, cs, KD, U, Px, Py, Pz);
+  atom_core<M, false, D, float, GEN>(ux, uy, uz, r, ir2, fc, fcp, cs, KD, U, Px, Py, Pz);
   const float ae = aw[0 * kAdjPT + pl];
   const float a0 = aw[1 * kAdjPT + pl], a1 = aw[2 * kAdjPT + pl], a2 = aw[3 * kAdjPT + pl];
   const float a3 = aw[4 * kAdjPT + pl], a4 = aw[5 * kAdjPT + pl], a5 = aw[6 * kAdjPT + pl];
 #pragma unroll
-  for (int t = 0; t < K; ++t) G[0 * 6 + q0 + t] += 0.5f * ae * U.d[t];
+  for (int t = 0; t < K; ++t)
+    if (q0 + t < NX) G[0 * NX + q0 + t] += 0.5f * ae * U.d[t];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     const float dx = r[j] * ux[j], dy = r[j] * uy[j], dz = r[j] * uz[j];
@@ -134,15 +202,16 @@ __device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB,
     const float fx = sld(&vj[0], 34) - vi[0], fy = sld(&vj[kAdjPT], 34) - vi[1], fz = sld(&vj[2 * kAdjPT], 34) - vi[2];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-      G[1 * 6 + q0 + t] -= Px[j].d[t] * bx + Py[j].d[t] * by + Pz[j].d[t] * bz;
-      G[2 * 6 + q0 + t] -= Px[j].d[t] * fx + Py[j].d[t] * fy + Pz[j].d[t] * fz;
+      if (q0 + t >= NX) continue;
+      G[1 * NX + q0 + t] -= Px[j].d[t] * bx + Py[j].d[t] * by + Pz[j].d[t] * bz;
+      G[2 * NX + q0 + t] -= Px[j].d[t] * fx + Py[j].d[t] * fy + Pz[j].d[t] * fz;
     }
   }
 }
 
-template <int MMAX>
+template <int MMAX, bool GEN = false>
 __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a) {
-  constexpr int PT = kAdjPT;
+  constexpr int PT = kAdjPT, NX = GEN ? 9 : 6, NG = 3 * NX;
   extern __shared__ __align__(32) unsigned char smem[];
   float *stage = reinterpret_cast<float *>(smem);
   const int tid = threadIdx.x, warp = tid >> 5, pl = tid & 31;
@@ -154,11 +223,20 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
   const bool active = p < a.P;
   PConsts<float> K;
   {
-    const float4 *kc = reinterpret_cast<const float4 *>(a.consts) + 2 * (active ? p : a.P - 1);
+    const float4 *kc = reinterpret_cast<const float4 *>(a.consts) + (GEN ? 4 : 2) * (active ? p : a.P - 1);
     const float4 k0 = kc[0], k1 = kc[1];
     K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.mha = k0.w;
     K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
+    if constexpr (GEN) {
+      const float4 k2 = kc[2], k3 = kc[3];
+      K.cR = k2.x; K.kR1 = k2.y; K.kR0 = k2.z; K.hl = k2.w;
+      K.g0 = k3.x; K.gc2 = k3.y; K.d2 = k3.z; K.gcd = k3.w;
+    }
   }
+  float xr[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if constexpr (GEN)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) xr[q] = (float)a.params[9 * (size_t)(active ? p : a.P - 1) + q];
   const int nat = rec.nat, s0 = rec.s0, ns = rec.ns;
   const int B0 = rec.B0, nb = rec.nb, Q0 = rec.Q0, nq = rec.nq;
   float4 *sA = reinterpret_cast<float4 *>(stage + adj_region0(nb));
@@ -194,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
       if (pl == 0) set_status(a.status, TERSOFF_STATUS_MANY_NBRS);
       continue;
     }
-    atom_forward_dispatch<PT, MMAX, true, false, float>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
+    atom_forward_dispatch<PT, MMAX, true, false, float, GEN>(m, sA, sB, sC, stage, at.x, at.y, m, true, pl, K, acc);
   }
   __syncthreads();
 
@@ -297,9 +375,9 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
   __syncthreads();
 
   // ---- tangent passes: K parameters at a time
-  float G[kAdjG];
+  float G[NG];
 #pragma unroll
-  for (int k = 0; k < kAdjG; ++k) G[k] = 0.f;
+  for (int k = 0; k < NG; ++k) G[k] = 0.f;
   for (int li = warp; li < ns; li += kNW) {
     const int4 at = sld(&satom[li], 21);
     const int m = at.z;
@@ -309,9 +387,13 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
 #define TSF_TAN(MM)                                                                           \
   case MM:                                                                                    \
     if constexpr (MMAX >= MM) {                                                               \
-      atom_tangent<MM, kAdjK, 0>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, G);              \
-      atom_tangent<MM, kAdjK, 2>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, G);              \
-      atom_tangent<MM, kAdjK, 4>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, G);              \
+      atom_tangent<MM, kAdjK, 0, GEN>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, xr, G);         \
+      atom_tangent<MM, kAdjK, 2, GEN>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, xr, G);         \
+      atom_tangent<MM, kAdjK, 4, GEN>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, xr, G);         \
+      if constexpr (GEN) {                                                                    \
+        atom_tangent<MM, kAdjK, 6, GEN>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, xr, G);       \
+        atom_tangent<MM, kAdjK, 8, GEN>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, xr, G);       \
+      }                                                                                       \
     }                                                                                         \
     break;
     switch (m) {
@@ -322,44 +404,46 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
   }
   // reduce G over warps (region0 is free again) and write the per-(p, c) gradient partial sums
   __syncthreads();
-  float *gred = stage;                                       // [kNW][kAdjG][PT]
+  float *gred = stage;                                       // [kNW][NG][PT]
 #pragma unroll
-  for (int k = 0; k < kAdjG; ++k) sst(&gred[(warp * kAdjG + k) * PT + pl], G[k], 23);
+  for (int k = 0; k < NG; ++k) sst(&gred[(warp * NG + k) * PT + pl], G[k], 23);
   __syncthreads();
-  for (int idx = tid; idx < kAdjG * PT; idx += kThreads) {
+  for (int idx = tid; idx < NG * PT; idx += kThreads) {
     const int k = idx / PT, lp = idx % PT;
     double t = 0.0;
 #pragma unroll
-    for (int w = 0; w < kNW; ++w) t += (double)sld(&gred[(w * kAdjG + k) * PT + lp], 24);
+    for (int w = 0; w < kNW; ++w) t += (double)sld(&gred[(w * NG + k) * PT + lp], 24);
     const int pp = tile * PT + lp;
-    if (pp < a.P) a.gpart[((size_t)pp * a.C + c) * kAdjG + k] = t;
+    if (pp < a.P) a.gpart[((size_t)pp * a.C + c) * NG + k] = t;
   }
 }
 
 // One warp per parameter set: S_q, D_q and G_q = dS_q/dx summed over configurations (FP64, fixed
 // order); L and dL/dx for the squared loss (w_q S_q / D_q) or Z (w_q sqrt(S_q / D_q)).
+template <int NX>
 __global__ void grad_finalize_kernel(int P, int C, const double *__restrict__ part,
                                      const double *__restrict__ dpart, const double *__restrict__ gpart,
                                      double we, double wv, double wf, int loss, double *__restrict__ L,
                                      double *__restrict__ dL) {
+  constexpr int NG = 3 * NX;
   const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (p >= P) return;
-  double s[3] = {0, 0, 0}, d[3] = {0, 0, 0}, g[kAdjG];
-  for (int k = 0; k < kAdjG; ++k) g[k] = 0.0;
+  double s[3] = {0, 0, 0}, d[3] = {0, 0, 0}, g[NG];
+  for (int k = 0; k < NG; ++k) g[k] = 0.0;
   for (int c = lane; c < C; c += 32) {
     for (int q = 0; q < 3; ++q) {
       s[q] += part[((size_t)p * C + c) * 3 + q];
       d[q] += dpart[(size_t)c * 3 + q];
     }
-    for (int k = 0; k < kAdjG; ++k) g[k] += gpart[((size_t)p * C + c) * kAdjG + k];
+    for (int k = 0; k < NG; ++k) g[k] += gpart[((size_t)p * C + c) * NG + k];
   }
   for (int off = 16; off > 0; off >>= 1) {
     for (int q = 0; q < 3; ++q) {
       s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
       d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
     }
-    for (int k = 0; k < kAdjG; ++k) g[k] += __shfl_xor_sync(0xffffffffu, g[k], off);
+    for (int k = 0; k < NG; ++k) g[k] += __shfl_xor_sync(0xffffffffu, g[k], off);
   }
   if (lane == 0) {
     const double w[3] = {we, wv, wf};
@@ -379,10 +463,10 @@ __global__ void grad_finalize_kernel(int P, int C, const double *__restrict__ pa
       }
     }
     L[p] = finite ? l : INFINITY;
-    for (int x = 0; x < 6; ++x) {
+    for (int x = 0; x < NX; ++x) {
       double gx = 0.0;
-      for (int q = 0; q < 3; ++q) gx += cq[q] * g[q * 6 + x];
-      dL[(size_t)p * 6 + x] = finite ? gx : __longlong_as_double(0x7ff8000000000000ll);
+      for (int q = 0; q < 3; ++q) gx += cq[q] * g[q * NX + x];
+      dL[(size_t)p * NX + x] = finite ? gx : __longlong_as_double(0x7ff8000000000000ll);
     }
   }
 }
@@ -392,10 +476,13 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
                               double *dL, void *consts, void *tf4, double *part, double *dpart, double *gpart,
                               cudaStream_t s) {
   const BatchPlan &plan = ctx.plan32;
+  const bool gen = ctx.form == kFormTersoff;
   {
     const int64_t n = std::max<int64_t>(P, ctx.Ntot);
     prep_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, params, reinterpret_cast<float *>(consts),
-                                                                   ctx.Ntot, tF, reinterpret_cast<float4 *>(tf4));
+                                                                   ctx.Ntot, tF, reinterpret_cast<float4 *>(tf4), 0,
+                                                                   nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                   nullptr, ctx.form);
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
@@ -404,6 +491,7 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
   ap.C = ctx.C;
   ap.Ntot = ctx.Ntot;
   ap.consts = reinterpret_cast<const float *>(consts);
+  ap.params = params;
   ap.boff = ctx.boff.as<int>();
   ap.poff = ctx.poff.as<int>();
   ap.gA = ctx.gA32.as<float4>();
@@ -423,14 +511,18 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
     if (b.cluster != 1) return cudaErrorNotSupported;   // the host rejects such builds first
     const size_t smem = b.adj_smem;
     ap.recs = plan.items.as<CtaRec>() + b.item_off;
-    auto kern = b.mmax <= 4 ? adjoint_kernel<4> : (b.mmax <= 6 ? adjoint_kernel<6> : adjoint_kernel<8>);
+    auto kern = gen ? (b.mmax <= 4 ? adjoint_kernel<4, true> : (b.mmax <= 6 ? adjoint_kernel<6, true> : adjoint_kernel<8, true>))
+                    : (b.mmax <= 4 ? adjoint_kernel<4> : (b.mmax <= 6 ? adjoint_kernel<6> : adjoint_kernel<8>));
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)(b.nitems * ap.ntiles), kThreads, smem, s>>>(ap);
     e = launched(1);
     if (e != cudaSuccess) return e;
   }
-  grad_finalize_kernel<<<(P + 7) / 8, 256, 0, s>>>(P, ctx.C, part, dpart, gpart, w[0], w[1], w[2], loss, L, dL);
+  if (gen)
+    grad_finalize_kernel<9><<<(P + 7) / 8, 256, 0, s>>>(P, ctx.C, part, dpart, gpart, w[0], w[1], w[2], loss, L, dL);
+  else
+    grad_finalize_kernel<6><<<(P + 7) / 8, 256, 0, s>>>(P, ctx.C, part, dpart, gpart, w[0], w[1], w[2], loss, L, dL);
   return launched(1);
 }
 

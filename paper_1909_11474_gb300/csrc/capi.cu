@@ -729,7 +729,6 @@ int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const 
                        const double *w, int32_t loss, double *L, double *dL, tersoff_stream stream) {
   if (!ctx) return TERSOFF_E_ARG;
   Ctx &c = ctx->c;
-  if (c.form != 0) return fail(ctx, TERSOFF_E_UNSUPPORTED, "only the batched evaluation and fitness take the Tersoff form%s");
   if (int rc = tsf::finish_build(ctx)) return rc;
   if (!params || P < 1 || !tg || !w || !L || !dL) return fail(ctx, TERSOFF_E_ARG, "null argument or P < 1%s");
   if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
@@ -741,7 +740,7 @@ int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const 
   cudaSetDevice(c.device);
   TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
-  TSF_CUDA(c.gpart.ensure((size_t)P * c.C * 18 * sizeof(double)));
+  TSF_CUDA(c.gpart.ensure((size_t)P * c.C * (c.form ? 27 : 18) * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
   TSF_CUDA(c.tf4.ensure((size_t)c.Ntot * sizeof(tsf::dvec4)));
   TSF_CUDA(tsf::launch_param_grad(c, params, P, tg->E, tg->W, tg->F, tg->mask, w, loss, L, dL, c.work.p, c.tf4.p,

@@ -118,13 +118,14 @@ def _newton_polish(ctx, g0, lo, hi, targets, w, loss, iters: int, h: float = 1e-
     system (H + lam diag(H)) d = -grad on the host; a step that lowers the loss is taken and lam
     shrinks, else lam grows. Stops when two accepted steps in a row gain less than 1e-10 relative."""
     span = hi - lo
-    eye = torch.eye(N_GENES, dtype=torch.float64, device=g0.device)
+    G = g0.numel()
+    eye = torch.eye(G, dtype=torch.float64, device=g0.device)
 
     def batch(gg):
         pts = torch.cat([gg[None, :], gg[None, :] + h * eye, gg[None, :] - h * eye], 0)
         L, dL = ctx.param_grad((lo + pts * span).contiguous(), targets, w=w, loss=loss)
         grad = (dL * span).cpu().numpy()                  # d/dgene
-        H = (grad[1:1 + N_GENES] - grad[1 + N_GENES:]) / (2 * h)
+        H = (grad[1:1 + G] - grad[1 + G:]) / (2 * h)
         return float(L[0]), grad[0], 0.5 * (H + H.T)
 
     def loss_at(gg):
@@ -233,23 +234,24 @@ def _fd_newton_polish(ctx, g0, lo, hi, targets, w, iters: int, h: float = 1e-4):
 
 
 def polish(ctx: binding.Context, params, targets: dict, lo, hi, steps: int = 30, lr: float = 2e-3,
-           w=(1.0, 1.0, 1.0), loss: int = binding.LOSS_SQ, method: str = "newton"):
+           w=(1.0, 1.0, 1.0), loss: int = binding.LOSS_SQ, method: str = "auto"):
     """Refine one parameter set on the smooth loss L = sum_q w_q S_q / D_q in gene space, with
     gradients from the adjoint kernel. The loss is a least-squares sum whose six directions are
     badly scaled (beta and n trade off along a long valley), so the default is a damped Newton method
     on a finite-difference Hessian of the adjoint gradient (`steps` iterations, one batched call of
     13 parameter sets each); `method="lbfgs"` (strong-Wolfe line search) and `method="adam"` (rate
-    `lr`) are first-order alternatives. On a context in the Tersoff form, which the gradient kernel
-    does not take (or with `method="fd-newton"`), the damped Newton step takes its gradient and
-    Hessian by central differences of the FP64 fitness instead. Returns (params, loss before, loss
-    after)."""
+    `lr`) are first-order alternatives. With `method="fd-newton"` the damped Newton step takes its
+    gradient and Hessian by central differences of the FP64 fitness instead (no gradient kernel).
+    "auto" is "newton", for either form. Returns (params, loss before, loss after)."""
     dev = torch.device("cuda")
     lo = torch.as_tensor(lo, dtype=torch.float64, device=dev)
     hi = torch.as_tensor(hi, dtype=torch.float64, device=dev)
     G = int(lo.numel())
     x0 = torch.as_tensor(params, dtype=torch.float64, device=dev).reshape(1, G)
     g0 = ((x0 - lo) / (hi - lo))
-    if getattr(ctx, "form", binding.FORM_MINIMAL) == binding.FORM_TERSOFF or method == "fd-newton":
+    if method == "auto":
+        method = "newton"
+    if method == "fd-newton":
         if loss != binding.LOSS_SQ:
             raise ValueError("the finite-difference polish minimises L_sq")
 
@@ -264,7 +266,7 @@ def polish(ctx: binding.Context, params, targets: dict, lo, hi, steps: int = 30,
         return x[0].cpu().numpy(), first, L_of(x)
     first = float(ctx.param_grad(x0.contiguous(), targets, w=w, loss=loss)[0][0])
     if method == "newton":
-        g = _newton_polish(ctx, g0[0], lo, hi, targets, w, loss, int(steps)).reshape(1, N_GENES)
+        g = _newton_polish(ctx, g0[0], lo, hi, targets, w, loss, int(steps)).reshape(1, G)
     elif method in ("lbfgs", "adam"):
         g = g0.clone().requires_grad_(True)
 
@@ -290,7 +292,7 @@ def polish(ctx: binding.Context, params, targets: dict, lo, hi, steps: int = 30,
                 opt.step()
         g = g.detach()
     else:
-        raise ValueError("method is 'newton', 'lbfgs' or 'adam'")
+        raise ValueError("method is 'auto', 'newton', 'fd-newton', 'lbfgs' or 'adam'")
     x = (lo + g * (hi - lo)).contiguous()
     L, _ = ctx.param_grad(x, targets, w=w, loss=loss)
     return x[0].cpu().numpy(), first, float(L[0])

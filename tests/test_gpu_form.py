@@ -104,7 +104,7 @@ def test_switching_forms_and_minimal_only_calls(ctx):
     ctx.set_form(binding.FORM_TERSOFF)
     z9 = ctx.fitness(p9, tg)[0].cpu().numpy()
     with pytest.raises(binding.TersoffError) as ei:
-        ctx.param_grad(p6, tg)
+        ctx.autotune(p6, tg)
     assert ei.value.code == binding.E_UNSUPPORTED
     with pytest.raises(binding.TersoffError):
         ctx.set_form(7)

@@ -94,3 +94,28 @@ def test_autograd_function_backward():
     (L * g).sum().backward()
     _, dL = ctx.param_grad(x.detach(), tg, w=WTS, loss=0)
     assert torch.allclose(x.grad, g[:, None] * dL, rtol=1e-12, atol=0)
+
+
+def test_param_grad_in_the_tersoff_form_matches_oracle():
+    """Nine parameters (Eq. 8 angular function, free S): the adjoint's loss and gradient against the
+    oracle's reverse-mode gradient, for sets spread around a Tersoff-form parameter set."""
+    from paper_1909_11474_gb300 import binding
+    xg = np.array([3.2, 1.45, 2.25, 1.9, 0.65, -0.6, 0.06, 20.0, 3.0])
+    w = I.workload_adjoint(P=4, C=3)
+    cs = w["configs"]
+    Eh, Wh, Fh = oracle.evaluate_batch(cs, xg[None, :])
+    t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0], mask=np.array([7, 3, 5], np.uint8))
+    params = xg[None, :] * (1 + 0.03 * np.random.default_rng(11).normal(size=(5, 9)))
+    ctx = binding.Context(0)
+    ctx.set_form(binding.FORM_TERSOFF)
+    pos, box = to_device(cs)
+    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+    L, dL = ctx.param_grad(torch.tensor(params, device="cuda"), targets_to_device(t), w=WTS, loss=0)
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+    L, dL = L.cpu().numpy(), dL.cpu().numpy()
+    assert dL.shape == (5, 9)
+    for p in range(len(params)):
+        Lr, gr = oracle.loss_and_grad(cs, params[p], t, w=WTS, loss="sq")
+        assert abs(L[p] - Lr) <= 1e-4 * abs(Lr) + 1e-9, (L[p], Lr)
+        assert (np.abs(dL[p] - gr) <= GRAD_TOL * np.abs(gr).max()).all(), (dL[p], gr)
