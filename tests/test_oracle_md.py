@@ -77,3 +77,14 @@ def test_verlet_conserves_energy_in_a_periodic_cell():
         assert np.abs(Ek - Ek[0]).max() > 1e-3                      # energy did move between the two
     assert dev[0] < 1.5e-4
     assert 3.0 < dev[0] / dev[1] < 5.5
+
+
+def test_thermal_velocities_have_zero_momentum_and_the_drawn_temperature():
+    """The seeded Maxwell-Boltzmann input draw: no centre-of-mass motion, and for 60,000 atoms the
+    kinetic temperature 2 E_k / (3 N kB) within 2 % of T (statistical spread ~0.3 %)."""
+    rng = np.random.default_rng(4)
+    m = np.full(60000, I.SI_MASS)
+    v = I.thermal_velocities(rng, m, 300.0)
+    assert np.abs((m[:, None] * v).sum(0)).max() < 1e-9
+    T = 2 * omd.kinetic_energy(v, m) / (3 * len(m) * omd.KB)
+    assert abs(T / 300.0 - 1) < 0.02
