@@ -104,7 +104,7 @@ class GeneticFit:
 
     @classmethod
     def load(cls, ctx: binding.Context, targets: dict, path, device=None) -> "GeneticFit":
-        st = torch.load(path, weights_only=False)
+        st = torch.load(path, weights_only=True)
         fit = cls(ctx, targets, st["lo"].numpy(), st["hi"].numpy(), n_pop=int(st["n_pop"]), n_par=int(st["n_par"]),
                   w=st["w"], device=device)
         fit.load_state_dict(st)

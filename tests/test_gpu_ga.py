@@ -131,7 +131,7 @@ def test_ga_checkpoint_resume_is_bit_exact(tmp_path):
     assert torch.equal(a.params, c.params)
     assert rc["Z"] == ra["Z"]
     with pytest.raises(ValueError):
-        GeneticFit(ctx, tg, lo, hi, n_pop=32, n_par=16).load_state_dict(torch.load(tmp_path / "ga.pt", weights_only=False))
+        GeneticFit(ctx, tg, lo, hi, n_pop=32, n_par=16).load_state_dict(torch.load(tmp_path / "ga.pt", weights_only=True))
 
 
 def test_ga_fits_in_the_tersoff_form():
