@@ -9,5 +9,5 @@ closed forms, the paper's printed values and brute force (no function is left un
 """
 from .tersoff import (  # noqa: F401
     R1_DEFAULT, R2_DEFAULT, neighbor_list, evaluate, evaluate_batch, fitness, loss_and_grad,
-    data_norms, site_energy_sum, fitness_from_predictions, padded, neighbor_list_subset,
+    data_norms, site_energy_sum, fitness_from_predictions, neighbor_list_subset,
 )

@@ -131,22 +131,6 @@ def neighbor_list_subset(pos, box, R2: float, atoms):
     return out
 
 
-def padded(nl, M: int):
-    """Neighbour list as fixed-width arrays: cnt [N], nbr [N][M] (-1 pad), shift [N][M][3]."""
-    off = nl["off"]
-    N = len(off) - 1
-    cnt = np.diff(off).astype(np.int32)
-    nbr = np.full((N, M), -1, dtype=np.int32)
-    shift = np.zeros((N, M, 3), dtype=np.int8)
-    for i in range(N):
-        m = cnt[i]
-        if m > M:
-            raise ValueError(f"atom {i} has {m} neighbours > {M}")
-        nbr[i, :m] = nl["j"][off[i]:off[i + 1]]
-        shift[i, :m] = nl["n"][off[i]:off[i + 1]]
-    return cnt, nbr, shift
-
-
 def _triplets(off: np.ndarray):
     """Ordered pairs (a, b), a != b, of neighbour entries of the same atom: the (ij, ik) terms of Eq. 7."""
     ta, tb = [], []
