@@ -1,0 +1,6 @@
+// adjoint_gen_m6.cu -- the parameter-gradient kernel for atoms of up to 6 neighbours, Tersoff form (Eq. 8, free S).
+#include "adjoint_kernel.cuh"
+
+namespace tsf {
+template cudaError_t launch_adjoint_variant<6, true>(const AdjParams &, size_t, unsigned, cudaStream_t);
+}  // namespace tsf

@@ -1,0 +1,6 @@
+// adjoint_m8.cu -- the parameter-gradient kernel for atoms of up to 8 neighbours, minimal form.
+#include "adjoint_kernel.cuh"
+
+namespace tsf {
+template cudaError_t launch_adjoint_variant<8, false>(const AdjParams &, size_t, unsigned, cudaStream_t);
+}  // namespace tsf
