@@ -116,7 +116,9 @@ int tersoff_build_info(tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t
  * (Eq. 1-14; forces F_i = -dU/dx_i and the virial above).
  *  params    device [P][6] double (order of Eq. 16), P >= 1; [P][9] in the Tersoff form
  *            (tersoff_set_form)
- *  precision 32: per-pair arithmetic in FP32, energy and virial sums in FP64, F in float;
+ *  precision 32: per-pair arithmetic in FP32; each warp sums its atoms' energy and virial terms in
+ *            FP32 and these per-warp partial sums are added in FP64 (over warps and cluster ranks,
+ *            in a fixed order); F in float;
  *            64: everything in FP64, F in double
  *  E         device [P][C] double, total energy (eV)             -- may be NULL
  *  F         device [P][Ntot][3] float or double (see precision) -- may be NULL
@@ -151,19 +153,22 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
  * for callers that cannot let a library call cudaMalloc: cudaMalloc stalls the whole device until it
  * returns, which a caller that keeps other streams busy or runs one generation after another cannot
  * afford, and a caller whose device memory was reserved up front by another allocator (a framework's
- * caching allocator, say) may have none left to give. The context's neighbour build and work
- * schedule are made by tersoff_build_neighbors, which does allocate; this call then uses only those
- * and one fixed 8 MiB scratch array in device memory that every device loading the library keeps
- * until the process exits.
+ * caching allocator, say) may have none left to give. tersoff_build_neighbors allocates every device
+ * buffer this call uses (the FP64 geometry records and the work-schedule records included), creates
+ * the side streams and loads the code of the kernels; tersoff_create looks up the device address of
+ * one fixed 8 MiB scratch array that every device loading the library keeps until the process exits.
+ * The call itself allocates nothing, also as the first call after a build: it may then wait for the
+ * build's neighbour counts, fill the schedule records with synchronous host-to-device copies and, in
+ * FP64, launch the kernels that compute the FP64 geometry into the buffers the build allocated.
  *  Arguments, results and arithmetic are those of tersoff_fitness, and so are the results.
- *  Limit: P*8*8 + P*C*24 + C*24 + C*64 + 256 bytes (each part rounded up to 256) must fit in 8 MiB, e.g.
- *  P = 200 parameter sets over C = 300 cells of 64 atoms needs 1.5 MB; a larger request returns
+ *  Limit: P*8*8 + P*C*64 + C*24 + C*64 + 256 bytes (each part rounded up to 256) must fit in 8 MiB,
+ *  e.g. P = 200 parameter sets over C = 300 cells of 64 atoms needs 3.9 MB; a larger request returns
  *  TERSOFF_E_ARG with the byte count in tersoff_last_error and launches nothing.
- *  The first call on a device looks up the scratch array's device address (once per device); make
- *  that first call before any stream capture. Every call shares the one array and leaves its
- *  contents behind; the call clears its work counters (the only part that must start at zero)
- *  itself with a cudaMemsetAsync on `stream`. Two calls whose work overlaps on the GPU
- *  (different streams, or different contexts on the same device) race on the array: serialise them. */
+ *  If the address look-up in tersoff_create failed, the first call on that device repeats it; make
+ *  that call before any stream capture. Every call shares the one array and leaves its contents
+ *  behind; the call clears its work counters (the only part that must start at zero) itself with a
+ *  cudaMemsetAsync on `stream`. Two calls whose work overlaps on the GPU (different streams, or
+ *  different contexts on the same device) race on the array: serialise them. */
 int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, int32_t P,
                            const tersoff_targets *tg, const double *w, int32_t precision, double *Z,
                            double *Zq, double *S, tersoff_stream stream);
@@ -285,6 +290,20 @@ int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, in
 #define TERSOFF_LAUNCH_GRAPHS 1
 #define TERSOFF_LAUNCH_PDL 2
 int tersoff_set_launch_mode(tersoff_ctx *ctx, int32_t mode);
+
+/* Bound of the device-side waits of this context's later calls; the paper has no counterpart. Two
+ * kernels wait on other work: the batched kernel waits for the bulk copies that stage a
+ * configuration's geometry in shared memory (tersoff_eval, tersoff_fitness, tersoff_fitness_static,
+ * tersoff_autotune), and the neighbour build waits at a grid-wide barrier for every CTA to finish its
+ * first phase (tersoff_build_neighbors). Each wait polls at most `spins` times (0: it gives up at once
+ * unless its condition already holds); a negative value restores the built-in bound (2^22 polls, far
+ * beyond any wait that can end). A wait that gives up sets TERSOFF_STATUS_TIMEOUT in the status word
+ * and its kernel stops without its results (the batched kernel first waits, with the built-in bound,
+ * for the copies already in flight): the call's outputs are then undefined, and a build that timed out
+ * is reported as TERSOFF_E_TIMEOUT by the next call that uses it and must be repeated. It exists so
+ * that the timeout paths can be exercised; nothing is left behind, and the next call with the default
+ * bound runs normally. Returns TERSOFF_E_ARG for a null context or spins >= 2^32. */
+int tersoff_set_wait_limit(tersoff_ctx *ctx, int64_t spins);
 
 /* Functional form of the potential for the context's later tersoff_eval and tersoff_fitness calls
  * (Sec. II.A-B):

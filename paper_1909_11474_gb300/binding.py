@@ -32,6 +32,7 @@ EXPORTED = (
     "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
     "tersoff_profile", "tersoff_profile_read", "tersoff_set_launch_mode", "tersoff_autotune",
     "tersoff_set_schedule", "tersoff_schedule_info", "tersoff_ga_step", "tersoff_md_nve", "tersoff_set_form",
+    "tersoff_set_wait_limit",
 )
 
 _vp = ctypes.c_void_p
@@ -84,6 +85,7 @@ def load():
         "tersoff_kernel_launches": (ctypes.c_int64, []),
         "tersoff_profile": (ctypes.c_int, [_vp, _i32]),
         "tersoff_set_launch_mode": (ctypes.c_int, [_vp, _i32]),
+        "tersoff_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),
         "tersoff_set_schedule": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
         "tersoff_schedule_info": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
         "tersoff_ga_step": (ctypes.c_int, [_i32, _i32, _i32, _f64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -208,6 +210,12 @@ class Context:
         kernels with programmatic dependent launch (pdl); both on by default."""
         self._check(self.lib.tersoff_set_launch_mode(self.h, (LAUNCH_GRAPHS if graphs else 0) | (LAUNCH_PDL if pdl else 0)))
 
+    def set_wait_limit(self, spins: int = -1):
+        """Bound (polls) of the device-side waits of later calls: the batched kernel's wait for its staged
+        geometry and the neighbour build's grid barrier (tersoff_set_wait_limit); negative restores the
+        built-in bound. A wait that gives up sets STATUS_TIMEOUT and its kernel stops early."""
+        self._check(self.lib.tersoff_set_wait_limit(self.h, int(spins)))
+
     def profile(self, enable: bool = True):
         """Start or stop CUDA-event timing of the batched E/F/W kernel (clears earlier records)."""
         self._check(self.lib.tersoff_profile(self.h, 1 if enable else 0))
@@ -298,7 +306,8 @@ class Context:
         memory is already reserved by another allocator). The output tensors here come from the
         caller (`out`) or from PyTorch's allocator in this wrapper, never from the library; the
         library's per-call scratch is a fixed 8 MiB device array shared by all calls, so calls that
-        overlap on the GPU race. The first call on a device sets up the array's address.
+        overlap on the GPU race. Every other buffer the call uses is allocated by build_neighbors, and
+        creating the context looks up the array's device address.
         """
         P = params.shape[0]
         _cuda(params, torch.float64, (P, 6), "params")

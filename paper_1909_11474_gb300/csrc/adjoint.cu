@@ -100,9 +100,9 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
   {
     const int64_t n = std::max<int64_t>(P, ctx.Ntot);
     prep_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, params, reinterpret_cast<float *>(consts),
-                                                                   ctx.Ntot, tF, reinterpret_cast<float4 *>(tf4), 0,
-                                                                   nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                   nullptr, ctx.form);
+                                                                   ctx.form, ctx.Ntot, tF,
+                                                                   reinterpret_cast<float4 *>(tf4), 0, nullptr,
+                                                                   nullptr, nullptr, nullptr, nullptr, nullptr);
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }

@@ -9,16 +9,17 @@
 
 namespace tsf {
 
-size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster) {
+size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, int ncta) {
+  const bool cl = ncta > 1;
   if (precision == 64)
-    return cluster ? batch_smem<kPT, true, double>(nb, nq, nat) : batch_smem<kPT, false, double>(nb, nq, nat);
-  return cluster ? batch_smem<kPT, true, float>(nb, nq, nat) : batch_smem<kPT, false, float>(nb, nq, nat);
+    return cl ? batch_smem<kPT, true, double>(nb, nq, nat, ncta) : batch_smem<kPT, false, double>(nb, nq, nat, 1);
+  return cl ? batch_smem<kPT, true, float>(nb, nq, nat, ncta) : batch_smem<kPT, false, float>(nb, nq, nat, 1);
 }
 
 int batch_param_tile() { return kPT; }
 
-size_t batch_smem_bytes_pt16(int nb, int nq, int nat) { return batch_smem<16, false, float>(nb, nq, nat); }
-size_t batch_smem_bytes_nw12(int nb, int nq, int nat) { return batch_smem<kPT, false, float, 12>(nb, nq, nat); }
+size_t batch_smem_bytes_pt16(int nb, int nq, int nat) { return batch_smem<16, false, float>(nb, nq, nat, 1); }
+size_t batch_smem_bytes_nw12(int nb, int nq, int nat) { return batch_smem<kPT, false, float, 12>(nb, nq, nat, 1); }
 
 static int precision_of(const BatchPlan &plan) { return plan.precision; }
 
@@ -48,26 +49,26 @@ static cudaError_t ensure_side(const Ctx &ctx, int nbuckets) {
   return cudaSuccess;
 }
 
+cudaError_t ensure_side_streams(const Ctx &ctx) { return ensure_side(ctx, kSide); }
+
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s) {
   const bool f64 = plan.precision == 64;
-  // per-call preparation: per-parameter-set constants and the target forces in the working precision
+  // per-call preparation: per-parameter-set constants; for the fitness, the FP64 targets, 1/N and the
+  // target-norm terms of every configuration (one warp each)
   {
-    const int64_t n = std::max<int64_t>(P, ctx.C);
-    const unsigned blocks = (unsigned)((n + 255) / 256);
     const bool tew = mode == kModeFitness && out.tEW;
+    const int64_t n = std::max<int64_t>(P, tew ? 32 * (int64_t)ctx.C : 0);
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    double *tEW = tew ? out.tEW : nullptr;
     if (f64)
-      prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts),
-                                                 ctx.Ntot, nullptr, nullptr, ctx.C,
-                                                 ctx.atom_off.as<int>(), out.tE, out.tW, out.tmask,
-                                                 tew ? reinterpret_cast<double *>(out.tEW) : nullptr, out.dpart,
-                                                 out.form);
+      prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts), out.form,
+                                                 ctx.Ntot, out.tF, nullptr, ctx.C, ctx.atom_off.as<int>(), out.tE,
+                                                 out.tW, out.tmask, tEW, out.dpart);
     else
-      prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts),
-                                                ctx.Ntot, nullptr, nullptr, ctx.C,
-                                                ctx.atom_off.as<int>(), out.tE, out.tW, out.tmask,
-                                                tew ? reinterpret_cast<float *>(out.tEW) : nullptr, out.dpart,
-                                                out.form);
+      prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts), out.form,
+                                                ctx.Ntot, out.tF, nullptr, ctx.C, ctx.atom_off.as<int>(), out.tE,
+                                                out.tW, out.tmask, tEW, out.dpart);
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
@@ -94,8 +95,8 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.tmask = out.tmask;
   bp.tEW = out.tEW;
   bp.part = out.part;
-  bp.dpart = out.dpart;
   bp.status = ctx.status.as<unsigned>();
+  bp.wait_spins = ctx.wait_spins < 0 ? kMbarSpins : (unsigned)std::min<int64_t>(ctx.wait_spins, 0xffffffffll);
   cudaError_t ez = cudaMemsetAsync(out.counters, 0, plan.buckets.size() * sizeof(int), s);
   if (ez != cudaSuccess) return ez;
   const bool timed = ctx.timer.begin(s);
@@ -228,8 +229,9 @@ cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params
 }
 
 // Fitness of every parameter set from the per-(p, c) residual terms of the batched kernel
-// (Eq. 15-19): S_q[p] = sum_c part[p][c][q] and D_q = sum_c dpart[c][q], both in FP64 in a fixed
-// order (lanes strided over c, then a fixed xor-shuffle tree). Zq = sqrt(S_q/D_q) (0 where D_q = 0),
+// (Eq. 15-19): S_e[p] = sum_c part[p][c][0], S_v[p] = sum_c sum_k part[p][c][1 + k] (k = xx .. zx),
+// S_f[p] = sum_c part[p][c][7], and D_q = sum_c dpart[c][q], all in FP64 in a fixed order (lanes
+// strided over c, then a fixed xor-shuffle tree). Zq = sqrt(S_q/D_q) (0 where D_q = 0),
 // Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not finite. One warp per parameter
 // set; small blocks spread the FP64 work over many SMs, and each block's first warp sums D_q once.
 constexpr int kFinWarps = 2;
@@ -256,11 +258,14 @@ __global__ void __launch_bounds__(kFinWarps * 32) fitness_finalize_kernel(
   const int p = blockIdx.x * kFinWarps + warp;
   if (p >= P) return;
   double s[3] = {0.0, 0.0, 0.0};
-  const double *pp = part + (size_t)p * C * 3;
-#pragma unroll 4
-  for (int c = lane; c < C; c += 32)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) s[q] += pp[3 * c + q];
+  const double *pp = part + (size_t)p * C * kNSum;
+#pragma unroll 2
+  for (int c = lane; c < C; c += 32) {
+    const double *t = pp + (size_t)c * kNSum;
+    s[0] += t[0];
+    s[1] += ((t[1] + t[2]) + (t[3] + t[4])) + (t[5] + t[6]);
+    s[2] += t[7];
+  }
 #pragma unroll
   for (int q = 0; q < 3; ++q)
     for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
@@ -297,6 +302,32 @@ cudaError_t launch_fitness_finalize(int P, int C, const double *part, const doub
   cfg.numAttrs = 1;
   const cudaError_t e = cudaLaunchKernelEx(&cfg, fitness_finalize_kernel, P, C, part, dpart, we, wv, wf, Z, Zq, S);
   if (e == cudaSuccess) count_launches(1);
+  return e;
+}
+
+// Force the module loading of every kernel the minimal-form fitness path launches (with lazy loading the
+// driver would otherwise load each on its first launch, allocating device memory for its code then).
+template <int PTV, int MMAX, bool CLUSTER, int MINB, typename R, int NW = kNW>
+static cudaError_t touch_variant() {
+  cudaFuncAttributes fa;
+  return cudaFuncGetAttributes(&fa, batch_kernel<PTV, MMAX, CLUSTER, MINB, R, NW, false>);
+}
+cudaError_t preload_fitness_kernels() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, prep_kernel<float>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, prep_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fitness_finalize_kernel);
+  if (e == cudaSuccess) e = touch_variant<16, 4, false, 3, float>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 4, false, 2, float, 12>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 4, false, 2, float>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 6, false, 2, float>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 8, false, 2, float>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 4, true, 2, float>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 6, true, 2, float>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 8, true, 2, float>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 8, false, 1, double>();
+  if (e == cudaSuccess) e = touch_variant<kPT, 8, true, 1, double>();
+  if (e == cudaSuccess) e = preload_geometry64_kernels();
   return e;
 }
 

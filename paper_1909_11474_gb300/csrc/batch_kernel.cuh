@@ -31,8 +31,12 @@ namespace tsf {
 
 constexpr int kNW = 8;           // warps per CTA
 constexpr int kThreads = kNW * kWarp;
-constexpr int kNRed = 10;        // reduced quantities: U, W[6], S_f, sum|F|^2, sum|F*|^2
-constexpr int kMaxCluster = 16;
+constexpr int kNRed = 10;        // quantities of the adjoint kernel's forward reductions (adjoint.cu)
+// Quantities the batched kernel reduces per (parameter set, configuration): U, W[6] and the force sum
+// (sum |F - F*|^2, or sum |F|^2 where the configuration has no force target, to test finiteness).
+// Per-warp partials are FP32 sums over the warp's atoms; sums over warps and cluster ranks are FP64.
+constexpr int kNSum = kResidualTerms;
+constexpr int kMaxCluster = kMaxClusterCtas;
 
 // ---- checked shared-memory access (TSF_DEBUG_BOUNDS builds) ----
 // In a debug build every shared-memory access of the batched kernel checks that it lies inside the
@@ -392,6 +396,7 @@ struct BatchParams {
   int nconf, nchunks, chunk_tiles; // work items: nconf configurations x nchunks chunks of tiles
   int narrow;                      // run a partly filled last tile with 2 or 4 atoms per warp
   int *counter;                    // work-claiming counter of the launch, zero at launch
+  unsigned wait_spins;             // polls of the staging wait before it gives up (a timeout)
   int mode;
   double *E;
   void *F;
@@ -399,29 +404,28 @@ struct BatchParams {
   const double *tE, *tW;
   const double *tF;                // [Ntot][3]: target forces (fitness)
   const uint8_t *tmask;
-  const void *tEW;                 // R [C][8]: E*, W*[6], 1/N of every configuration (fitness)
-  double *part;                    // [P][C][3]: S_e, S_v, S_f terms of every (p, c) (fitness)
-  double *dpart;                   // [C][3]: target-norm terms; [c][2] = sum of |F*|^2 (fitness)
+  const double *tEW;               // [C][8]: E*, W*[6], 1/N of every configuration (fitness)
+  double *part;                    // [P][C][kNSum]: residual terms of every (p, c) (fitness): e, v[6], f
   unsigned *status;
 };
 
 // Shared memory of one CTA (R = float or double, R4 its 4-vector):
-//   [region0: max(nb*3*PT, (kNW + (cluster ? 16 : 1)) * kNRed * PT) R]  stage of P_ij, later the
-//    per-warp partial sums and the CTA totals (one row per cluster rank)
+//   [region0: max(nb*stride(PT) R, (NW + (cluster ? ncta : 0)) * kNSum * PT double)]  stage of P_ij, later
+//    the per-warp FP64 partial sums and, in rank 0 of a cluster, one row of totals per rank
 //   [sA: nb R4][sB: nb R4][sC: nq R][satom: natoms int4][stF: natoms R4 (fitness only)]
 // region0 sits at offset 0 in every CTA, so a peer's stage is addressed by mapping this CTA's own
 // stage address to the peer rank.
 template <int PT, bool CLUSTER, typename R, int NW = kNW>
-__host__ __device__ inline size_t region0_elems(int nb) {
-  const size_t st = (size_t)nb * stage_stride<PT>();
-  const size_t rd = (size_t)(NW + (CLUSTER ? kMaxCluster : 1)) * kNRed * PT;
+__host__ __device__ inline size_t region0_bytes(int nb, int ncta) {
+  const size_t st = (size_t)nb * stage_stride<PT>() * sizeof(R);
+  const size_t rd = (size_t)(NW + (CLUSTER ? ncta : 0)) * kNSum * PT * sizeof(double);
   const size_t e = st > rd ? st : rd;
-  return (e * sizeof(R) + 31) / 32 * 32 / sizeof(R);
+  return (e + 31) / 32 * 32;
 }
 template <int PT, bool CLUSTER, typename R, int NW = kNW>
-__host__ __device__ inline size_t batch_smem(int nb, int nq, int nat) {
+__host__ __device__ inline size_t batch_smem(int nb, int nq, int nat, int ncta) {
   using R4 = typename Vec4<R>::T;
-  size_t b = region0_elems<PT, CLUSTER, R, NW>(nb) * sizeof(R) + (size_t)nb * 2 * sizeof(R4);
+  size_t b = region0_bytes<PT, CLUSTER, R, NW>(nb, ncta) + (size_t)nb * 2 * sizeof(R4);
   b += ((size_t)nq * sizeof(R) + 31) / 32 * 32;
   b += (size_t)nat * sizeof(int4);
   b += (size_t)nat * sizeof(R4);
@@ -599,7 +603,7 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
   if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
 
   // ---- pass 3: F_i = sum_j (P_ij - P_ji)
-  R sf = R(0), sF2 = R(0), sT = R(0);
+  R sf = R(0);   // sum |F - F*|^2 over the warp's atoms, or sum |F|^2 without a force target
   for (int base = warp * APW; base < ns; base += NW * APW) {
     const int li = base + slot;
     if (li >= ns) continue;
@@ -644,7 +648,6 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
         Fz -= sld(&sr[2 * PTT], 15);
       }
     }
-    if (!(mask & 4)) sF2 += Fx * Fx + Fy * Fy + Fz * Fz;   // finiteness of F when no residual checks it
     const int i = s0 + li;
     if (a.mode == kModeEval) {
       if (active && a.F) {
@@ -658,85 +661,70 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
       const R4 t = sld(&stF[li], 16);
       const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
       sf += ex * ex + ey * ey + ez * ez;
-      sT += t.w;
+    } else {
+      sf += Fx * Fx + Fy * Fy + Fz * Fz;   // finiteness of F where no residual checks it
     }
   }
 
-  // ---- reductions: over atom slots (shuffles), warps (shared memory, fixed order), ranks
-  R v[kNRed];
+  // ---- reductions: over atom slots (FP32 shuffles), then over warps and cluster ranks in FP64, each in
+  // a fixed order. Thread (k, lp) of the first kNSum * PTT threads forms quantity k of parameter set lp.
+  R v[kNSum];
   v[0] = acc.U;
 #pragma unroll
   for (int k = 0; k < 6; ++k) v[1 + k] = acc.W[k];
   v[7] = sf;
-  v[8] = sF2;
-  v[9] = sT;
 #pragma unroll
-  for (int k = 0; k < kNRed; ++k) v[k] = sum_over_atom_slots<PTT>(v[k]);
+  for (int k = 0; k < kNSum; ++k) v[k] = sum_over_atom_slots<PTT>(v[k]);
   if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();   // stages no longer read
-  R *red = stage;                                   // [NW][kNRed][PTT]
-  R *tot = stage + NW * kNRed * PTT;                // [ranks][kNRed][PTT] (rank 0 collects)
+  double *red = reinterpret_cast<double *>(stage);            // [NW][kNSum][PTT] per-warp partials
+  double *tot = red + NW * kNSum * PTT;                       // [ncta][kNSum][PTT] rank totals (rank 0)
   if (slot == 0) {
 #pragma unroll
-    for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PTT + pl], v[k], 17);
+    for (int k = 0; k < kNSum; ++k) sst(&red[(warp * kNSum + k) * PTT + pl], (double)v[k], 17);
   }
   __syncthreads();
-  for (int idx = tid; idx < kNRed * PTT; idx += (NW * kWarp)) {
-    R t = R(0);
-#pragma unroll
-    for (int w = 0; w < NW; ++w) t += sld(&red[w * kNRed * PTT + idx], 18);
-    if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(tot + rank * kNRed * PTT + idx), 0), t);
-    else sst(&tot[idx], t, 19);
+  const bool red_thread = tid < kNSum * PTT;
+  const int rk = tid / PTT, rl = tid % PTT;
+  double T = 0.0;
+  if (red_thread) {
+#pragma unroll 4
+    for (int w = 0; w < NW; ++w) T += sld(&red[(w * kNSum + rk) * PTT + rl], 18);
   }
-  if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();
-
-  if (rank == 0 && tid < PTT) {
-    const int pp = tile * PTW + tid;
-    R q[kNRed];
-#pragma unroll
-    for (int k = 0; k < kNRed; ++k) {
-      R s = R(0);
-      for (unsigned r = 0; r < ncta; ++r) s += sld(&tot[(r * kNRed + k) * PTT + tid], 20);
-      q[k] = s;
+  if constexpr (CLUSTER) {
+    if (red_thread) st_cluster(map_to_rank(smem_addr(tot + ((int)rank * kNSum + rk) * PTT + rl), 0), T);
+    cluster_sync_all();
+    if (rank == 0 && red_thread) {
+      T = 0.0;
+      for (unsigned r = 0; r < ncta; ++r) T += sld(&tot[((int)r * kNSum + rk) * PTT + rl], 20);
     }
+  }
+  if (rank == 0 && red_thread) {
+    const int pp = tile * PTW + rl;
     if (pp < a.P) {
+      const size_t pc = (size_t)pp * a.C + c;
       if (a.mode == kModeEval) {
-        if (a.E) a.E[(size_t)pp * a.C + c] = (double)q[0];
-        if (a.W)
-          for (int k = 0; k < 6; ++k) a.W[((size_t)pp * a.C + c) * 6 + k] = (double)q[1 + k];
+        if (rk == 0 && a.E) a.E[pc] = T;
+        if (rk >= 1 && rk <= 6 && a.W) a.W[pc * 6 + (rk - 1)] = T;
       } else {
-        // per-atom residuals of Eq. 17-18 in the working precision (the FP64 sums over
-        // configurations are formed by the finalize kernel)
-        const R *tw = reinterpret_cast<const R *>(a.tEW) + (size_t)c * 8;
-        const R invN = tw[7];
-        bool finite = isfinite(q[0]) && isfinite(q[8]);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);
-        R se = R(0), sv = R(0), sfv = R(0);
-        if (mask & 1) {
-          const R d = q[0] * invN - tw[0];
-          se = d * d;
+        // residual term of Eq. 17-19 in FP64: (E/N - E*)^2, (W_k/N - W*_k)^2 or the force sum; a quantity
+        // without a target contributes 0 when finite and NaN otherwise, so that any non-finite
+        // prediction makes Z infinite
+        const double *tw = a.tEW + (size_t)c * 8;
+        const int bit = rk == 0 ? 1 : (rk <= 6 ? 2 : 4);
+        double term;
+        if (rk == 7) term = T;
+        else {
+          const double d = T * tw[7] - tw[rk];
+          term = d * d;
         }
-        if (mask & 2) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            const R d = q[1 + k] * invN - tw[1 + k];
-            sv += d * d;
-          }
-        }
-        if (mask & 4) sfv = q[7];
-        if (!finite) se = sv = sfv = R(NAN);
-        double *o = a.part + ((size_t)pp * a.C + c) * 3;
-        o[0] = (double)se;
-        o[1] = (double)sv;
-        o[2] = (double)sfv;
+        if (!(mask & bit)) term = isfinite(T) ? 0.0 : T - T;
+        a.part[pc * kNSum + rk] = term;
       }
     }
-    if (fit && tile == 0 && tid == 0) a.dpart[3 * c + 2] = (mask & 4) ? (double)q[9] : 0.0;
   }
-  // the next tile (or item) reuses the stage, where rank 0 keeps the collected totals that its first
-  // warp reads above. A CTA barrier suffices in a cluster too: peers read a CTA's stage only between
-  // the next tile's first cluster barrier, which this CTA reaches after the barrier below, and its
-  // second, and they write rank 0's totals only after that
+  // the next tile (or item) reuses the stage, where the partial sums live. A CTA barrier suffices in
+  // a cluster too: peers touch a CTA's stage, and rank 0's totals, only after the next tile's first
+  // cluster barrier, which this CTA reaches after the barrier below
   __syncthreads();
 }
 
@@ -808,7 +796,7 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
     // atom slice of this CTA
     const int nat = rec.nat, s0 = rec.s0, ns = rec.ns, cb0 = rec.cb0;
     const int B0 = rec.B0, nb = rec.nb, Q0 = rec.Q0, nq = rec.nq;
-    R4 *sA = reinterpret_cast<R4 *>(stage + region0_elems<PT, CLUSTER, R, NW>(nb));
+    R4 *sA = reinterpret_cast<R4 *>(smem + region0_bytes<PT, CLUSTER, R, NW>(nb, (int)ncta));
     R4 *sB = sA + nb;
     R *sC = reinterpret_cast<R *>(sB + nb);
     int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) +
@@ -841,22 +829,23 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
       for (int t = tid; t < ns; t += (NW * kWarp)) {
         const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
         sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, a.outer[s0 + t]), 9);
-        if (fit) {   // target force in the working precision and |F*|^2 (from the FP64 components)
+        if (fit) {   // target force in the working precision
           const double *f = a.tF + 3 * (int64_t)(s0 + t);
-          const double fx = f[0], fy = f[1], fz = f[2];
           R4 v;
-          v.x = (R)fx;
-          v.y = (R)fy;
-          v.z = (R)fz;
-          v.w = (R)(fx * fx + fy * fy + fz * fz);
+          v.x = (R)f[0];
+          v.y = (R)f[1];
+          v.z = (R)f[2];
+          v.w = R(0);
           sst(&stF[t], v, 10);
         }
       }
       if constexpr (!CLUSTER) {
-        // thread 0 waits (bounded) for the bulk copies; the barrier below publishes them
+        // thread 0 waits (at most wait_spins polls) for the bulk copies; the barrier below publishes
+        // them. A wait that gives up reports a timeout, and the CTA stops after a second wait (with
+        // the built-in bound) for the copies still in flight, so that none lands after it exits
         if (tid == 0) {
           bool done = false;
-          for (unsigned k = 0; k < kMbarSpins && !done; ++k) done = mbar_try_wait(&mbar, phase);
+          for (unsigned k = 0; k < a.wait_spins && !done; ++k) done = mbar_try_wait(&mbar, phase);
           abort_flag = done ? 0 : 1;
           if (!done) {
             set_status(a.status, TERSOFF_STATUS_TIMEOUT);
@@ -899,30 +888,43 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
   }
 }
 
-// Per call: FP32/FP64 constants of every parameter set, when tF4 is given the target forces as R4
-// (x, y, z, |F|^2), and when tEW is given each configuration's targets and atom count as R [C][8] (E*, W*[6], 1/N) and its
-// terms of the target norms D_e and D_v of Eq. 17-18 in FP64 (dpart[c][0..1]; masked-off quantities
-// contribute 0).
+// Per call, one thread per parameter set: the FP32/FP64 constants of every parameter set (PConsts).
+// When tF4 is given (the adjoint kernel), one thread per atom: the target forces in the working precision
+// as R4 (x, y, z, |F|^2). When tEW is given (fitness), one warp per configuration: its targets and
+// 1/N in FP64 as [C][8] (E*, W*[6], 1/N), and its terms of the target norms of Eq. 17-19 in FP64,
+// dpart[c] = (E*^2, |W*|^2, sum_i |F*_i|^2) (a masked-off quantity contributes 0).
 template <typename R>
-__global__ void prep_kernel(int P, const double *__restrict__ params, R *__restrict__ consts,
-                            int64_t Ntot, const double *__restrict__ tF,
-                            typename Vec4<R>::T *__restrict__ tF4, int C = 0,
-                            const int *__restrict__ atom_off = nullptr, const double *__restrict__ tE = nullptr,
-                            const double *__restrict__ tW = nullptr, const uint8_t *__restrict__ tmask = nullptr,
-                            R *__restrict__ tEW = nullptr, double *__restrict__ dpart = nullptr,
-                            int form = kFormMinimal) {
+__global__ void prep_kernel(int P, const double *__restrict__ params, R *__restrict__ consts, int form,
+                            int64_t Ntot, const double *__restrict__ tF, typename Vec4<R>::T *__restrict__ tF4,
+                            int C, const int *__restrict__ atom_off, const double *__restrict__ tE,
+                            const double *__restrict__ tW, const uint8_t *__restrict__ tmask,
+                            double *__restrict__ tEW, double *__restrict__ dpart) {
   pdl_trigger();   // the batched kernel may start staging geometry; it waits before reading our output
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tEW && t < C) {
-    R *o = tEW + 8 * t;
-    o[0] = (R)tE[t];
-    for (int k = 0; k < 6; ++k) o[1 + k] = (R)tW[6 * t + k];
-    o[7] = (R)(1.0 / (double)(atom_off[t + 1] - atom_off[t]));
-    const uint8_t m = tmask[t];
-    double dv = 0.0;
-    for (int k = 0; k < 6; ++k) dv += tW[6 * t + k] * tW[6 * t + k];
-    dpart[3 * t] = (m & 1) ? tE[t] * tE[t] : 0.0;
-    dpart[3 * t + 1] = (m & 2) ? dv : 0.0;
+  if (tEW && t / 32 < C) {
+    const int c = (int)(t / 32), lane = (int)(t & 31);
+    const uint8_t m = tmask[c];
+    const int a0 = atom_off[c], a1 = atom_off[c + 1];
+    double f2 = 0.0;
+    if (m & 4)
+      for (int i = a0 + lane; i < a1; i += 32) {
+        const double *f = tF + 3 * (int64_t)i;
+        f2 += f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
+      }
+    for (int off = 16; off > 0; off >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, off);
+    if (lane == 0) {
+      double *o = tEW + 8 * (size_t)c;
+      o[0] = tE[c];
+      double dv = 0.0;
+      for (int k = 0; k < 6; ++k) {
+        o[1 + k] = tW[6 * c + k];
+        dv += tW[6 * c + k] * tW[6 * c + k];
+      }
+      o[7] = 1.0 / (double)(a1 - a0);
+      dpart[3 * c] = (m & 1) ? tE[c] * tE[c] : 0.0;
+      dpart[3 * c + 1] = (m & 2) ? dv : 0.0;
+      dpart[3 * c + 2] = f2;
+    }
   }
   if (t < P && form == kFormMinimal) {
     const double *x = params + 6 * t;
@@ -960,7 +962,7 @@ __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restr
     o[14] = (R)(d * d);
     o[15] = (R)(ga * c * c / (d * d));
   }
-  if (tF && t < Ntot) {
+  if (tF4 && t < Ntot) {
     const double fx = tF[3 * t], fy = tF[3 * t + 1], fz = tF[3 * t + 2];
     typename Vec4<R>::T v;
     v.x = (R)fx;

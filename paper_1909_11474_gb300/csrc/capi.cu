@@ -76,7 +76,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
         for (int r = 0; r < cl; ++r) {
           const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
           const int nb = c.h_boff[s1] - c.h_boff[s0], nq = c.h_poff[s1] - c.h_poff[s0];
-          mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, s1 - s0, cl > 1));
+          mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, s1 - s0, cl));
         }
         if (mx <= (pass == 0 && !(one_per_sm && cl >= 8) ? soft : (size_t)optin)) {
           chosen = cl;
@@ -222,7 +222,7 @@ int queue_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const terso
   int rc = build_plan(ctx, precision);
   if (rc) return rc;
   if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
-  TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.part.ensure((size_t)P * c.C * tsf::kResidualTerms * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
   TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * (c.form ? 16 : 8) * sizeof(double)));
@@ -231,7 +231,7 @@ int queue_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const terso
   o.form = c.form;
   o.counters = c.counters.as<int>();
   o.consts = c.work.p;
-  o.tEW = c.tew.p;
+  o.tEW = c.tew.as<double>();
   o.tE = tg->E;
   o.tW = tg->W;
   o.tF = tg->F;
@@ -246,7 +246,7 @@ int queue_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const terso
                                (uint64_t)(uintptr_t)t.E, (uint64_t)(uintptr_t)t.W, (uint64_t)(uintptr_t)t.F,
                                (uint64_t)(uintptr_t)t.mask, bits(w0), bits(w1), bits(w2), (uint64_t)(uintptr_t)Z,
                                (uint64_t)(uintptr_t)Zq, (uint64_t)(uintptr_t)Sq, plan.gen, (uint64_t)c.C,
-                               (uint64_t)c.Ntot, (uint64_t)c.pdl};
+                               (uint64_t)c.Ntot, (uint64_t)c.pdl, (uint64_t)c.wait_spins};
   return run_graphed(ctx, c.g_fitness, std::move(key), S(stream), [&](cudaStream_t s) {
     cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
     if (e == cudaSuccess)
@@ -344,6 +344,10 @@ int tersoff_create(tersoff_ctx **out, int device) {
     delete ctx;
     return TERSOFF_E_CUDA;
   }
+  // set-up of the allocation-free fitness call on this device: the device address of its scratch array
+  // (loads the array's module, which holds it); a failure here is reported by that call
+  void *scratch = nullptr;
+  (void)tsf::static_scratch_address(device, &scratch);
   *out = ctx;
   return TERSOFF_OK;
 }
@@ -376,6 +380,13 @@ int tersoff_set_form(tersoff_ctx *ctx, int32_t form) {
   if (!ctx) return TERSOFF_E_ARG;
   if (form != TERSOFF_FORM_MINIMAL && form != TERSOFF_FORM_TERSOFF) return fail(ctx, TERSOFF_E_ARG, "unknown form%s");
   ctx->c.form = form;
+  return TERSOFF_OK;
+}
+
+int tersoff_set_wait_limit(tersoff_ctx *ctx, int64_t spins) {
+  if (!ctx) return TERSOFF_E_ARG;
+  if (spins > 0xffffffffll) return fail(ctx, TERSOFF_E_ARG, "spins must be below 2^32%s");
+  ctx->c.wait_spins = spins < 0 ? -1 : spins;
   return TERSOFF_OK;
 }
 
@@ -504,6 +515,20 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.gA32.ensure(bond_cap * sizeof(float4)));
   TSF_CUDA(c.gB32.ensure(bond_cap * sizeof(float4)));
   TSF_CUDA(c.gcos32.ensure(slot_cap * sizeof(float)));
+  // everything the later calls of this build need is allocated here, so that those calls (the
+  // allocation-free fitness among them) allocate nothing: the FP64 geometry records (computed on the
+  // first FP64 use), the work-schedule records of both precisions, the side streams, and the code of
+  // the fitness kernels (loaded up front instead of lazily on their first launch)
+  TSF_CUDA(c.gA64.ensure(bond_cap * sizeof(tsf::dvec4)));
+  TSF_CUDA(c.gB64.ensure(bond_cap * sizeof(tsf::dvec4)));
+  TSF_CUDA(c.gcos64.ensure(slot_cap * sizeof(double)));
+  TSF_CUDA(c.plan32.items.ensure((size_t)C * tsf::kMaxClusterCtas * sizeof(tsf::CtaRec)));
+  TSF_CUDA(c.plan64.items.ensure((size_t)C * tsf::kMaxClusterCtas * sizeof(tsf::CtaRec)));
+  TSF_CUDA(tsf::ensure_side_streams(c));
+  if (!c.preloaded) {
+    TSF_CUDA(tsf::preload_fitness_kernels());
+    c.preloaded = true;
+  }
   if (c.build_resident <= 0) c.build_resident = tsf::build_batch_resident();
   if (c.build_resident <= 0) return fail(ctx, TERSOFF_E_CUDA, "occupancy query of the build kernel failed%s");
   TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
@@ -535,6 +560,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   L.barrier = c.grid_bar.as<unsigned>();
   L.status = st;
   L.resident = c.build_resident;
+  L.wait_spins = c.wait_spins;
   TSF_CUDA(tsf::launch_build_batch(L, s));
   // neighbour counts and status go back to pinned host memory; the host reads them (and builds or
   // keeps the work schedule) when the next call needs the build, so the caller's own work overlaps
@@ -646,7 +672,7 @@ int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const te
   int rc = build_plan(ctx, precision);
   if (rc) return rc;
   if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
-  TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
+  TSF_CUDA(c.part.ensure((size_t)P * c.C * tsf::kResidualTerms * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
   TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * (c.form ? 16 : 8) * sizeof(double)));
@@ -655,7 +681,7 @@ int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const te
   o.form = c.form;
   o.counters = c.counters.as<int>();
   o.consts = c.work.p;
-  o.tEW = c.tew.p;
+  o.tEW = c.tew.as<double>();
   o.tE = tg->E;
   o.tW = tg->W;
   o.tF = tg->F;

@@ -99,6 +99,12 @@ struct __align__(16) CtaRec {
   int cb0, nat, rec0, pad;
 };
 
+// Residual terms the batched fitness writes per (parameter set, configuration), in FP64: the energy
+// term, six virial terms and the force sum (Eq. 17-19 before the sums over configurations).
+constexpr int kResidualTerms = 8;
+// Largest thread-block cluster a configuration of the batched kernels is split over.
+constexpr int kMaxClusterCtas = 16;
+
 // Pair slots per atom: m(m-1)/2 cosines padded to a multiple of 4 (16-byte vector loads).
 __host__ __device__ inline int pair_slots(int m) { return ((m * (m - 1) / 2) + 3) & ~3; }
 
@@ -172,6 +178,10 @@ struct Ctx {
   bool pending = false;               // a build is queued whose counts the host has not checked yet
   bool pending_same_layout = false;   // that build has the previous build's layout
   bool geom64 = false;   // FP64 geometry records built for the current neighbour build
+  bool preloaded = false; // fitness kernels loaded on the device (module loading done up front)
+  // polls of the bounded device-side waits (batched kernel's staging wait, build's grid barrier);
+  // negative: the kernels' built-in bounds (tersoff_set_wait_limit)
+  int64_t wait_spins = -1;
   int C = 0;
   int64_t Ntot = 0, Btot = 0, Qtot = 0;
   int M = 0, max_m = 0;
@@ -226,6 +236,7 @@ struct BuildLaunch {
   int *outer;
   unsigned *barrier, *status;
   int resident;   // CTAs of the build kernel that can be resident at once (build_batch_resident)
+  int64_t wait_spins;   // polls of the grid barrier before it gives up (negative: the built-in bound)
 };
 cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s);
 int build_batch_resident();
@@ -242,12 +253,13 @@ struct BatchOut {
   double *W;          // [P][C][6]
   const double *tE, *tW, *tF;
   const uint8_t *tmask;
-  double *part;       // workspace: [P][C][3] residual terms per (p, c), formed in the working precision
+  double *part;       // workspace: [P][C][8] FP64 residual terms per (p, c): e, v[6], f
   double *dpart;      // workspace: [C][3] per-configuration terms of the target norms D_q (FP64)
-  void *tEW;          // workspace: [C][8] E*, W*[6], 1/N per configuration (working precision)
+  double *tEW;        // workspace: [C][8] E*, W*[6], 1/N per configuration (FP64)
   void *consts;       // workspace: [P][8] per-parameter-set constants (working precision)
   int *counters;      // workspace: one work counter per launch bucket
   bool pdl = false;   // launch the batched kernels with programmatic stream serialization
+  int64_t wait_spins = -1;   // polls of the staging wait before it gives up (negative: built-in bound)
   int form = 0;       // 0: minimal (6 parameters), 1: Tersoff form (9 parameters, Eq. 8, free S)
 };
 enum BatchMode { kModeEval = 0, kModeFitness = 1 };
@@ -255,12 +267,20 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
                          int mode, const BatchOut &out, cudaStream_t s);
 cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params, int P, int mode,
                            const BatchOut &out, int reps, cudaStream_t s, float *best_ms, int *tried);
+// Side streams of the launch buckets, and the module loading of every kernel a fitness call can launch
+// (so that later calls neither create resources nor load code on the device).
+cudaError_t ensure_side_streams(const Ctx &ctx);
+cudaError_t preload_fitness_kernels();
+cudaError_t preload_geometry64_kernels();   // neighbors.cu
 cudaError_t launch_fitness_finalize(int P, int C, const double *part, const double *dpart,
                                     double we, double wv, double wf, double *Z, double *Zq, double *S, bool pdl,
                                     cudaStream_t s);
 // capi.cu: host side of a queued neighbour build; FP64 geometry records on demand
 int finish_build(tersoff_ctx *ctx);
 int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s);
+// noalloc.cu: device address of the allocation-free fitness call's scratch array on `device` (looked up
+// once per device, with that device current); nonzero CUDA error code on failure
+int static_scratch_address(int device, void **out);
 
 // md.cu
 int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double *x, double R1, double R2,
@@ -280,7 +300,7 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
 cudaError_t launch_plain(const Ctx &ctx, const double *params, int P, double *E, double *F, double *W,
                          cudaStream_t s);
 
-size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, bool cluster);
+size_t batch_smem_bytes_pt(int precision, int nb, int nq, int nat, int ncta);   // ncta = cluster size
 size_t batch_smem_bytes_pt16(int nb, int nq, int nat);   // FP32 single-CTA, 16 parameter sets per tile
 size_t batch_smem_bytes_nw12(int nb, int nq, int nat);   // FP32 single-CTA, 12 warps per CTA
 int batch_param_tile();

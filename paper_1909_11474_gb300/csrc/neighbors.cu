@@ -187,6 +187,7 @@ struct BuildParams {
   int *outer;
   unsigned *barrier;               // zero at launch
   unsigned *status;
+  unsigned wait_spins;             // polls of the grid barrier before it gives up (a timeout)
 };
 
 // Sum / max / exclusive scan over the threads of a block (kBuildThreads), in a fixed order.
@@ -227,16 +228,18 @@ __device__ __forceinline__ int block_excl_scan(int v, int *red, int &total) {
   return before + incl - v;
 }
 
-// Grid-wide barrier of a cooperative launch; the wait is bounded, and a timeout is reported in the
-// status word (the second phase then runs on whatever the first phase has written, within bounds).
-__device__ __forceinline__ void grid_barrier(unsigned *ctr, unsigned *status) {
+// Grid-wide barrier of a cooperative launch; the wait is bounded (at most `spins` polls), and a timeout
+// is reported in the status word (the second phase then runs on whatever the first phase has written,
+// within bounds: every index it writes is checked against the capacities, so a build that timed out
+// writes nothing out of range; the host reports it as TERSOFF_E_TIMEOUT and keeps no result of it).
+__device__ __forceinline__ void grid_barrier(unsigned *ctr, unsigned *status, unsigned spins) {
   __threadfence();   // this thread's global writes, before the arrival below
   __syncthreads();
   if (threadIdx.x == 0) {
     atomicAdd(ctr, 1u);
     unsigned k = 0;
     while (*reinterpret_cast<volatile unsigned *>(ctr) < gridDim.x) {
-      if (++k >= kGridSpins) {
+      if (k++ >= spins) {
         set_status(status, TERSOFF_STATUS_TIMEOUT);
         break;
       }
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
     __syncthreads();
   }
 
-  grid_barrier(a.barrier, a.status);
+  grid_barrier(a.barrier, a.status, a.wait_spins);
 
   // ---- phase 2: bond CSR, reverse bonds, FP32 bond records, pair cosines
   long long base_b = 0, base_q = 0;
@@ -623,6 +626,7 @@ cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s) {
   a.gcos = L.gcos;
   a.outer = L.outer;
   a.barrier = L.barrier;
+  a.wait_spins = L.wait_spins < 0 ? kGridSpins : (unsigned)std::min<int64_t>(L.wait_spins, 0xffffffffll);
   a.status = L.status;
   cudaError_t e = cudaMemsetAsync(L.barrier, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
@@ -665,6 +669,13 @@ cudaError_t launch_geometry64(int64_t Ntot, int64_t Btot, int M, const int *atom
     geometry_pair_kernel<double><<<nblk(Ntot * max_slots, 256), 256, 0, s>>>(
         Ntot, max_slots, cnt, M, boff, poff, static_cast<const dvec4 *>(gA), static_cast<double *>(gcos));
   return launched((Btot > 0) + (max_slots > 0));
+}
+
+cudaError_t preload_geometry64_kernels() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, geometry_bond_kernel<double>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, geometry_pair_kernel<double>);
+  return e;
 }
 
 }  // namespace tsf

@@ -1,8 +1,8 @@
 // noalloc.cu -- tersoff_fitness_static: the fitness call of tersoff_fitness with no device
-// allocation at call time. Its per-call scratch (per-parameter-set constants, per-configuration targets
-// in the working precision, the per-(parameter set, configuration) residual terms and the
-// per-configuration target-norm terms) lives in one file-scope __device__ array of fixed size instead of context buffers that
-// grow on demand.
+// allocation at call time. Its per-call scratch (per-parameter-set constants, the FP64 targets of every
+// configuration, the per-(parameter set, configuration) residual terms and the per-configuration
+// target-norm terms) lives in one file-scope __device__ array of fixed size instead of context buffers
+// that grow on demand. Everything else it uses is allocated by tersoff_build_neighbors.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -31,6 +31,27 @@ int set_error(tersoff_ctx *ctx, int code, const char *msg) {
 
 }  // namespace
 
+namespace tsf {
+// Looked up by tersoff_create on its device, and again by the entry point if that failed.
+int static_scratch_address(int device, void **out) {
+  *out = nullptr;
+  if (device < 0 || device >= kMaxDevices) return (int)cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_addr[device]) {
+    int cur = 0;
+    cudaError_t e = cudaGetDevice(&cur);
+    if (e == cudaSuccess && cur != device) e = cudaSetDevice(device);
+    void *ptr = nullptr;
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&ptr, g_fitness_scratch);
+    if (cur != device) cudaSetDevice(cur);
+    if (e != cudaSuccess || !ptr) return (int)(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
+    g_scratch_addr[device] = ptr;
+  }
+  *out = g_scratch_addr[device];
+  return 0;
+}
+}  // namespace tsf
+
 extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, int32_t P,
                                       const tersoff_targets *tg, const double *w, int32_t precision,
                                       double *Z, double *Zq, double *S, tersoff_stream stream) {
@@ -48,7 +69,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
 
   // scratch layout, each part 256-byte aligned
   const size_t b_consts = align256((size_t)P * 8 * sizeof(double));
-  const size_t b_part = align256((size_t)P * c.C * 3 * sizeof(double));
+  const size_t b_part = align256((size_t)P * c.C * tsf::kResidualTerms * sizeof(double));
   const size_t b_dpart = align256((size_t)c.C * 3 * sizeof(double));
   const size_t b_tew = align256((size_t)c.C * 8 * sizeof(double));
   const size_t b_count = align256(64 * sizeof(int));
@@ -63,18 +84,15 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   if (cudaSetDevice(c.device) != cudaSuccess) return set_error(ctx, TERSOFF_E_CUDA, "cudaSetDevice failed");
   unsigned char *base = nullptr;
   {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[c.device]) {
-      void *ptr = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&ptr, g_fitness_scratch);
-      if (e != cudaSuccess || !ptr) {
-        char buf[160];
-        std::snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-        return set_error(ctx, TERSOFF_E_CUDA, buf);
-      }
-      g_scratch_addr[c.device] = ptr;
+    void *ptr = nullptr;
+    const int e = tsf::static_scratch_address(c.device, &ptr);
+    if (e != 0) {
+      char buf[160];
+      std::snprintf(buf, sizeof(buf), "cudaGetSymbolAddress of the static scratch failed: %s",
+                    cudaGetErrorString((cudaError_t)e));
+      return set_error(ctx, TERSOFF_E_CUDA, buf);
     }
-    base = static_cast<unsigned char *>(g_scratch_addr[c.device]);
+    base = static_cast<unsigned char *>(ptr);
   }
 
   // every scratch element read by the kernels is written earlier in the same call (constants and
@@ -88,12 +106,12 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   o.consts = base;
   o.part = reinterpret_cast<double *>(base + b_consts);
   o.dpart = reinterpret_cast<double *>(base + b_consts + b_part);
-  o.tEW = base + b_consts + b_part + b_dpart;
+  o.tEW = reinterpret_cast<double *>(base + b_consts + b_part + b_dpart);
   o.counters = reinterpret_cast<int *>(base + b_consts + b_part + b_dpart + b_tew);
   o.pdl = c.pdl;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (precision == 64) {
-    const int rc = tsf::ensure_geom64(ctx, s);   // kernels into buffers made by the neighbour build
+    const int rc = tsf::ensure_geom64(ctx, s);   // kernels into buffers allocated by the neighbour build
     if (rc) return rc;
   }
   cudaError_t e = tsf::launch_batch(c, plan, params, P, tsf::kModeFitness, o, s);
