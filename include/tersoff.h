@@ -89,12 +89,14 @@ typedef struct {
  * Entries are kept in ascending (j, n0, n1, n2) order. The call also builds the parameter-independent
  * geometry cache (bond lengths, unit vectors, f_C and f_C' of Eq. 9, bond-angle cosines; FP32 now,
  * FP64 on the first FP64 evaluation) and the evaluation schedule.
- * The build runs as one kernel queued on `stream`, which copies pos/box into the context: the
- * caller's pos/box must stay unchanged until that kernel has run (stream order suffices). The call
- * returns once the work is queued. The neighbour counts come back to the host with it; the next
- * call that uses the build (evaluation, fitness, gradient, export, build_info) waits for them,
- * checks them and builds the schedule; a rebuild of configurations of the same sizes whose
- * neighbour counts are all unchanged reuses the previous schedule.
+ * The build runs as one kernel queued on `stream` (one CTA per configuration), which copies pos/box
+ * into the context: the caller's pos/box must stay unchanged until that kernel has run (stream order
+ * suffices). The call returns once the work is queued. The neighbour counts come back to the host on
+ * a side stream that waits for the kernel, so that work the caller queues next on `stream` does not
+ * wait for the copy; the next call that uses the build (evaluation, fitness, gradient, export,
+ * build_info) waits for the counts, checks them and builds the schedule; a rebuild of configurations
+ * of the same sizes whose neighbour counts are all unchanged reuses the previous schedule. All
+ * device memory of the build (the FP64 geometry records included) is allocated by this call.
  * R1 < R2 (Eq. 9; Sec. II.B uses R1 = 2.8, R2 = 3.2). 1 <= max_nbr <= 32 bounds the entries kept
  * per atom. Argument errors are returned by this call. Errors found by the build kernel are
  * returned by that next call (and set bits of the status word): an atom with more than max_nbr
@@ -161,8 +163,8 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
  * build's neighbour counts, fill the schedule records with synchronous host-to-device copies and, in
  * FP64, launch the kernels that compute the FP64 geometry into the buffers the build allocated.
  *  Arguments, results and arithmetic are those of tersoff_fitness, and so are the results.
- *  Limit: P*8*8 + P*C*64 + C*24 + C*64 + 256 bytes (each part rounded up to 256) must fit in 8 MiB,
- *  e.g. P = 200 parameter sets over C = 300 cells of 64 atoms needs 3.9 MB; a larger request returns
+ *  Limit: P*8*8 + P*C*24 + C*24 + 256 bytes (each part rounded up to 256) must fit in 8 MiB, e.g.
+ *  P = 200 parameter sets over C = 300 cells of 64 atoms needs 1.5 MB; a larger request returns
  *  TERSOFF_E_ARG with the byte count in tersoff_last_error and launches nothing.
  *  If the address look-up in tersoff_create failed, the first call on that device repeats it; make
  *  that call before any stream capture. Every call shares the one array and leaves its contents
@@ -291,18 +293,16 @@ int tersoff_md_export_neighbors(tersoff_ctx *ctx, int32_t *cnt, int32_t *nbr, in
 #define TERSOFF_LAUNCH_PDL 2
 int tersoff_set_launch_mode(tersoff_ctx *ctx, int32_t mode);
 
-/* Bound of the device-side waits of this context's later calls; the paper has no counterpart. Two
- * kernels wait on other work: the batched kernel waits for the bulk copies that stage a
- * configuration's geometry in shared memory (tersoff_eval, tersoff_fitness, tersoff_fitness_static,
- * tersoff_autotune), and the neighbour build waits at a grid-wide barrier for every CTA to finish its
- * first phase (tersoff_build_neighbors). Each wait polls at most `spins` times (0: it gives up at once
- * unless its condition already holds); a negative value restores the built-in bound (2^22 polls, far
- * beyond any wait that can end). A wait that gives up sets TERSOFF_STATUS_TIMEOUT in the status word
- * and its kernel stops without its results (the batched kernel first waits, with the built-in bound,
- * for the copies already in flight): the call's outputs are then undefined, and a build that timed out
- * is reported as TERSOFF_E_TIMEOUT by the next call that uses it and must be repeated. It exists so
- * that the timeout paths can be exercised; nothing is left behind, and the next call with the default
- * bound runs normally. Returns TERSOFF_E_ARG for a null context or spins >= 2^32. */
+/* Bound of the device-side wait of this context's later calls; the paper has no counterpart. One kernel
+ * waits on other work: the batched kernel waits for the bulk copies that stage a configuration's
+ * geometry in shared memory (tersoff_eval, tersoff_fitness, tersoff_fitness_static, tersoff_autotune).
+ * The wait polls at most `spins` times (0: it gives up at once unless the copies have already landed);
+ * a negative value restores the built-in bound (2^22 polls, far beyond any wait that can end). A wait
+ * that gives up sets TERSOFF_STATUS_TIMEOUT in the status word, and its CTA stops without its results
+ * after a second wait, with the built-in bound, for the copies already in flight: the call's outputs
+ * are then undefined. It exists so that the timeout path can be exercised; nothing is left behind,
+ * and the next call with the default bound runs normally. Returns TERSOFF_E_ARG for a null context or
+ * spins >= 2^32. */
 int tersoff_set_wait_limit(tersoff_ctx *ctx, int64_t spins);
 
 /* Functional form of the potential for the context's later tersoff_eval and tersoff_fitness calls
@@ -324,6 +324,16 @@ int tersoff_set_form(tersoff_ctx *ctx, int32_t form);
  * tersoff_kernel_launches: number of kernels the library has launched in this process, all contexts
  * and devices together (a count kept on the host when each launch is accepted). */
 int64_t tersoff_kernel_launches(void);
+
+/* Arithmetic throughput of CUDA device `device`, measured by microbenchmarks (independent dependency
+ * chains in every thread of a grid that fills every SM, timed with CUDA events, best of three
+ * launches); the paper has no counterpart. out (host, 6 doubles) receives, in operations per second:
+ *  [0] FP32 FMA, as FLOP/s (2 per FMA);   [1] packed FP32x2 FMA (__ffma2_rn), as FLOP/s (4 per instruction);
+ *  [2] FP64 FMA, as FLOP/s (2 per FMA);   [3] FP64 add, op/s;
+ *  [4] special-function unit 2^x (ex2.approx.f32), op/s;   [5] FP32 -> FP64 -> FP32 conversions, op/s.
+ * Synchronous (allocates and frees a small device buffer; runs for a few milliseconds). Returns
+ * TERSOFF_E_ARG for a bad device or a null pointer, TERSOFF_E_CUDA on a CUDA error. */
+int tersoff_measure_peaks(int32_t device, double *out);
 
 /* Start (enable = 1) or stop (enable = 0) timing the batched E/F/W kernel of this context: while on,
  * every tersoff_eval / tersoff_fitness / tersoff_fitness_static records a CUDA event pair on its own

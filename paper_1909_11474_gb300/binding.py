@@ -32,7 +32,7 @@ EXPORTED = (
     "tersoff_md_export_neighbors", "tersoff_fitness_static", "tersoff_kernel_launches",
     "tersoff_profile", "tersoff_profile_read", "tersoff_set_launch_mode", "tersoff_autotune",
     "tersoff_set_schedule", "tersoff_schedule_info", "tersoff_ga_step", "tersoff_md_nve", "tersoff_set_form",
-    "tersoff_set_wait_limit",
+    "tersoff_set_wait_limit", "tersoff_measure_peaks",
 )
 
 _vp = ctypes.c_void_p
@@ -86,6 +86,7 @@ def load():
         "tersoff_profile": (ctypes.c_int, [_vp, _i32]),
         "tersoff_set_launch_mode": (ctypes.c_int, [_vp, _i32]),
         "tersoff_set_wait_limit": (ctypes.c_int, [_vp, ctypes.c_int64]),
+        "tersoff_measure_peaks": (ctypes.c_int, [_i32, _vp]),
         "tersoff_set_schedule": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
         "tersoff_schedule_info": (ctypes.c_int, [_vp, _i32, _i32, _vp]),
         "tersoff_ga_step": (ctypes.c_int, [_i32, _i32, _i32, _f64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -125,6 +126,16 @@ def ga_step(Z: torch.Tensor, genes_in: torch.Tensor, uniforms: torch.Tensor, lo:
                                 _ptr(order), _stream(stream))
     if rc != OK:
         raise TersoffError(rc, "tersoff_ga_step: bad arguments or CUDA error")
+
+
+def measure_peaks(device: int = 0) -> dict:
+    """Measured arithmetic throughput of the device (tersoff_measure_peaks), in operations per second."""
+    out = np.zeros(6, np.float64)
+    rc = load().tersoff_measure_peaks(int(device), out.ctypes.data)
+    if rc != OK:
+        raise TersoffError(rc, "tersoff_measure_peaks failed")
+    keys = ("fp32_fma_flops", "fp32x2_fma_flops", "fp64_fma_flops", "fp64_add_ops", "xu_ex2_ops", "cvt_f32_f64_ops")
+    return dict(zip(keys, (float(v) for v in out)))
 
 
 class TersoffError(RuntimeError):
@@ -211,9 +222,9 @@ class Context:
         self._check(self.lib.tersoff_set_launch_mode(self.h, (LAUNCH_GRAPHS if graphs else 0) | (LAUNCH_PDL if pdl else 0)))
 
     def set_wait_limit(self, spins: int = -1):
-        """Bound (polls) of the device-side waits of later calls: the batched kernel's wait for its staged
-        geometry and the neighbour build's grid barrier (tersoff_set_wait_limit); negative restores the
-        built-in bound. A wait that gives up sets STATUS_TIMEOUT and its kernel stops early."""
+        """Bound (polls) of the device-side wait of later calls, the batched kernel's wait for its staged
+        geometry (tersoff_set_wait_limit); negative restores the built-in bound. A wait that gives up
+        sets STATUS_TIMEOUT and its kernel stops early."""
         self._check(self.lib.tersoff_set_wait_limit(self.h, int(spins)))
 
     def profile(self, enable: bool = True):

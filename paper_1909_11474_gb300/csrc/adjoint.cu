@@ -101,8 +101,7 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
     const int64_t n = std::max<int64_t>(P, ctx.Ntot);
     prep_kernel<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(P, params, reinterpret_cast<float *>(consts),
                                                                    ctx.form, ctx.Ntot, tF,
-                                                                   reinterpret_cast<float4 *>(tf4), 0, nullptr,
-                                                                   nullptr, nullptr, nullptr, nullptr, nullptr);
+                                                                   reinterpret_cast<float4 *>(tf4));
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
@@ -114,6 +113,7 @@ cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const
   ap.params = params;
   ap.boff = ctx.boff.as<int>();
   ap.poff = ctx.poff.as<int>();
+  ap.ameta = ctx.ameta.as<int>();
   ap.gA = ctx.gA32.as<float4>();
   ap.gB = ctx.gB32.as<float4>();
   ap.gcos = ctx.gcos32.as<float>();

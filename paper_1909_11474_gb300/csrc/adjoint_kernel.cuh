@@ -20,6 +20,7 @@ struct AdjParams {
   const float *consts;            // [P][8] PConsts<float> ([P][16] in the Tersoff form)
   const double *params;           // [P][9] raw parameters of the Tersoff form (its tangent seeds)
   const int *boff, *poff;
+  const int *ameta;               // [Ntot]: bonds kept | (some bond beyond R1) << 16
   const float4 *gA, *gB;
   const float *gcos;
   const CtaRec *recs;
@@ -50,17 +51,15 @@ __device__ __forceinline__ PConsts<Dual<K, float>> seed_consts_minimal(const PCo
   D.n = Dual<K, float>(k.n);
   D.inv2n = Dual<K, float>(k.inv2n);
   const float log2e = 1.4426950408889634f;
-  const float r0log2e = -0.5f * k.k0 / k.mha;     // r0 log2 e = k0 / alpha
 #pragma unroll
   for (int t = 0; t < K; ++t) {
     const int q = q0 + t;
     if (q == 0) D.D0.d[t] = 1.f;
-    if (q == 1) {                                  // k1 = -alpha log2e, k0 = alpha r0 log2e, mha = -alpha/2
+    if (q == 1) {                                  // k1 = -alpha log2e, mha = -alpha/2
       D.k1.d[t] = -log2e;
-      D.k0.d[t] = r0log2e;
       D.mha.d[t] = -0.5f;
     }
-    if (q == 2) D.k0.d[t] = -k.k1;                 // alpha log2e
+    if (q == 2) D.k0.d[t] = 1.f;                   // k0 = r0
     if (q == 3) D.beta.d[t] = 1.f;
     if (q == 4) {                                  // inv2n = -1/(2n): d/dn = 1/(2 n^2)
       D.n.d[t] = 1.f;
@@ -249,8 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
     }
     for (int t = tid; t < nq; t += kThreads) sst(&sC[t], a.gcos[Q0 + t], 8);
     for (int t = tid; t < ns; t += kThreads) {
-      const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
-      sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, 0), 9);
+      sst(&satom[t], make_int4(a.boff[s0 + t] - B0, a.poff[s0 + t] - Q0, a.ameta[s0 + t] & 0xffff, 0), 9);
       sst(&stF[t], a.tF4[s0 + t], 10);
     }
   }

@@ -54,21 +54,15 @@ cudaError_t ensure_side_streams(const Ctx &ctx) { return ensure_side(ctx, kSide)
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s) {
   const bool f64 = plan.precision == 64;
-  // per-call preparation: per-parameter-set constants; for the fitness, the FP64 targets, 1/N and the
-  // target-norm terms of every configuration (one warp each)
+  // per-call preparation: per-parameter-set constants
   {
-    const bool tew = mode == kModeFitness && out.tEW;
-    const int64_t n = std::max<int64_t>(P, tew ? 32 * (int64_t)ctx.C : 0);
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    double *tEW = tew ? out.tEW : nullptr;
+    const unsigned blocks = (unsigned)((P + 255) / 256);
     if (f64)
       prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts), out.form,
-                                                 ctx.Ntot, out.tF, nullptr, ctx.C, ctx.atom_off.as<int>(), out.tE,
-                                                 out.tW, out.tmask, tEW, out.dpart);
+                                                 ctx.Ntot, nullptr, nullptr);
     else
       prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts), out.form,
-                                                ctx.Ntot, out.tF, nullptr, ctx.C, ctx.atom_off.as<int>(), out.tE,
-                                                out.tW, out.tmask, tEW, out.dpart);
+                                                ctx.Ntot, nullptr, nullptr);
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }
@@ -80,7 +74,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.atom_off = ctx.atom_off.as<int>();
   bp.boff = ctx.boff.as<int>();
   bp.poff = ctx.poff.as<int>();
-  bp.outer = ctx.outer.as<int>();
+  bp.ameta = ctx.ameta.as<int>();
   bp.gA = f64 ? ctx.gA64.p : ctx.gA32.p;
   bp.gB = f64 ? ctx.gB64.p : ctx.gB32.p;
   bp.gcos = f64 ? ctx.gcos64.p : ctx.gcos32.p;
@@ -93,8 +87,8 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.tW = out.tW;
   bp.tF = out.tF;
   bp.tmask = out.tmask;
-  bp.tEW = out.tEW;
   bp.part = out.part;
+  bp.dpart = out.dpart;
   bp.status = ctx.status.as<unsigned>();
   bp.wait_spins = ctx.wait_spins < 0 ? kMbarSpins : (unsigned)std::min<int64_t>(ctx.wait_spins, 0xffffffffll);
   cudaError_t ez = cudaMemsetAsync(out.counters, 0, plan.buckets.size() * sizeof(int), s);
@@ -229,9 +223,8 @@ cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params
 }
 
 // Fitness of every parameter set from the per-(p, c) residual terms of the batched kernel
-// (Eq. 15-19): S_e[p] = sum_c part[p][c][0], S_v[p] = sum_c sum_k part[p][c][1 + k] (k = xx .. zx),
-// S_f[p] = sum_c part[p][c][7], and D_q = sum_c dpart[c][q], all in FP64 in a fixed order (lanes
-// strided over c, then a fixed xor-shuffle tree). Zq = sqrt(S_q/D_q) (0 where D_q = 0),
+// (Eq. 15-19): S_q[p] = sum_c part[p][c][q] and D_q = sum_c dpart[c][q], all in FP64 in a fixed order
+// (lanes strided over c, then a fixed xor-shuffle tree). Zq = sqrt(S_q/D_q) (0 where D_q = 0),
 // Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not finite. One warp per parameter
 // set; small blocks spread the FP64 work over many SMs, and each block's first warp sums D_q once.
 constexpr int kFinWarps = 2;
@@ -258,14 +251,11 @@ __global__ void __launch_bounds__(kFinWarps * 32) fitness_finalize_kernel(
   const int p = blockIdx.x * kFinWarps + warp;
   if (p >= P) return;
   double s[3] = {0.0, 0.0, 0.0};
-  const double *pp = part + (size_t)p * C * kNSum;
-#pragma unroll 2
-  for (int c = lane; c < C; c += 32) {
-    const double *t = pp + (size_t)c * kNSum;
-    s[0] += t[0];
-    s[1] += ((t[1] + t[2]) + (t[3] + t[4])) + (t[5] + t[6]);
-    s[2] += t[7];
-  }
+  const double *pp = part + (size_t)p * C * kResidualTerms;
+#pragma unroll 4
+  for (int c = lane; c < C; c += 32)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) s[q] += pp[(size_t)c * kResidualTerms + q];
 #pragma unroll
   for (int q = 0; q < 3; ++q)
     for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);

@@ -35,7 +35,7 @@ constexpr int kNRed = 10;        // quantities of the adjoint kernel's forward r
 // Quantities the batched kernel reduces per (parameter set, configuration): U, W[6] and the force sum
 // (sum |F - F*|^2, or sum |F|^2 where the configuration has no force target, to test finiteness).
 // Per-warp partials are FP32 sums over the warp's atoms; sums over warps and cluster ranks are FP64.
-constexpr int kNSum = kResidualTerms;
+constexpr int kNSum = 8;
 constexpr int kMaxCluster = kMaxClusterCtas;
 
 // ---- checked shared-memory access (TSF_DEBUG_BOUNDS builds) ----
@@ -77,7 +77,8 @@ __device__ __forceinline__ void sst(T *p, const T &v, int site) {
 }
 
 // Per-parameter-set constants (prepared once per call by prep_kernel from the FP64 parameters).
-// Minimal form: x = exp(-alpha (r - r0)) = 2^(k1 r + k0), f_R = D0 x^2, f_A = 2 D0 x (Eq. 4-5,
+// Minimal form: x = exp(-alpha (r - r0)) = 2^(k1 (r - k0)) with k1 = -alpha log2(e), k0 = r0 (r - r0 is
+// exact in FP32 near r0, where k1 r and k1 r0 would cancel), f_R = D0 x^2, f_A = 2 D0 x (Eq. 4-5,
 // 11-14 at S = 2); mha = -alpha/2; inv2n = -1/(2n).
 // Tersoff form (Eq. 8, free S): f_A / 2 = D0 2^(k1 (r - k0)) with D0 = D0 S / (2 (S - 1)),
 // k1 = -mu log2(e), mu = alpha sqrt(2/S), k0 = r0; f_R = cR 2^(kR1 (r - k0)) with cR = D0 / (S - 1),
@@ -144,8 +145,8 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
       const T dr = r[j] - K.k0;
       hA[j] = K.D0 * ex2(dr * K.k1);               // f_A / 2
       fR[j] = K.cR * ex2(dr * K.kR1);
-    } else {
-      const T x = ex2(r[j] * K.k1 + K.k0);
+    } else {                                       // x = e^{-alpha (r - r0)}; r - r0 is exact in FP32 near r0
+      const T x = ex2((r[j] - K.k0) * K.k1);
       hA[j] = K.D0 * x;                            // f_A / 2
       fR[j] = hA[j] * x;
     }
@@ -389,7 +390,7 @@ struct BatchParams {
   int64_t Ntot;
   const void *consts;              // R [P][8]: PConsts of every parameter set
   const int *atom_off, *boff, *poff;
-  const int *outer;                // [Ntot] nonzero if the atom has a bond beyond R1
+  const int *ameta;                // [Ntot]: bonds kept | (some bond beyond R1) << 16
   const void *gA, *gB, *gcos;
   const CtaRec *recs;
   int ntiles;                      // parameter tiles: ceil(P / PT)
@@ -404,14 +405,14 @@ struct BatchParams {
   const double *tE, *tW;
   const double *tF;                // [Ntot][3]: target forces (fitness)
   const uint8_t *tmask;
-  const double *tEW;               // [C][8]: E*, W*[6], 1/N of every configuration (fitness)
-  double *part;                    // [P][C][kNSum]: residual terms of every (p, c) (fitness): e, v[6], f
+  double *part;                    // [P][C][3]: FP64 residual terms e, v, f of every (p, c) (fitness)
+  double *dpart;                   // [C][3]: FP64 target-norm terms of every configuration (fitness)
   unsigned *status;
 };
 
 // Shared memory of one CTA (R = float or double, R4 its 4-vector):
-//   [region0: max(nb*stride(PT) R, (NW + (cluster ? ncta : 0)) * kNSum * PT double)]  stage of P_ij, later
-//    the per-warp FP64 partial sums and, in rank 0 of a cluster, one row of totals per rank
+//   [region0: max(nb*stride(PT) R, (NW + (cluster ? ncta : 0)) * PT * kNSum double)]  stage of P_ij,
+//    later the per-warp FP64 partial sums and, in rank 0 of a cluster, the totals of every rank
 //   [sA: nb R4][sB: nb R4][sC: nq R][satom: natoms int4][stF: natoms R4 (fitness only)]
 // region0 sits at offset 0 in every CTA, so a peer's stage is addressed by mapping this CTA's own
 // stage address to the peer rank.
@@ -519,6 +520,7 @@ struct TileEnv {
   const int4 *satom;
   const typename Vec4<R>::T *stF;
   int ns, s0, nat, c, cb0, B0;
+  double inv_nat;
   uint8_t mask;
   bool fit;
   unsigned rank, ncta;
@@ -667,7 +669,10 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
   }
 
   // ---- reductions: over atom slots (FP32 shuffles), then over warps and cluster ranks in FP64, each in
-  // a fixed order. Thread (k, lp) of the first kNSum * PTT threads forms quantity k of parameter set lp.
+  // a fixed order. Thread (lp, k) = (tid / 8, tid % 8) of the first kNSum * PTT threads forms quantity k
+  // of parameter set lp; the partials are stored [warp][lp][k ^ (lp % 8)] (the xor spreads a warp's
+  // stores of one k over the banks; the reads of a row are a permutation of it).
+  static_assert(kNSum == 8, "the reduction maps eight quantities onto eight lanes");
   R v[kNSum];
   v[0] = acc.U;
 #pragma unroll
@@ -676,50 +681,57 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 #pragma unroll
   for (int k = 0; k < kNSum; ++k) v[k] = sum_over_atom_slots<PTT>(v[k]);
   if constexpr (CLUSTER) cluster_sync_all(); else __syncthreads();   // stages no longer read
-  double *red = reinterpret_cast<double *>(stage);            // [NW][kNSum][PTT] per-warp partials
-  double *tot = red + NW * kNSum * PTT;                       // [ncta][kNSum][PTT] rank totals (rank 0)
+  double *red = reinterpret_cast<double *>(stage);            // [NW][PTT][kNSum] per-warp partials
+  double *tot = red + NW * PTT * kNSum;                       // [ncta][PTT][kNSum] rank totals (rank 0)
   if (slot == 0) {
 #pragma unroll
-    for (int k = 0; k < kNSum; ++k) sst(&red[(warp * kNSum + k) * PTT + pl], (double)v[k], 17);
+    for (int k = 0; k < kNSum; ++k) sst(&red[(warp * PTT + pl) * kNSum + (k ^ (pl & 7))], widen(v[k]), 17);
   }
   __syncthreads();
   const bool red_thread = tid < kNSum * PTT;
-  const int rk = tid / PTT, rl = tid % PTT;
+  const int rl = tid >> 3, rk = tid & 7, rx = rk ^ (rl & 7);
   double T = 0.0;
   if (red_thread) {
 #pragma unroll 4
-    for (int w = 0; w < NW; ++w) T += sld(&red[(w * kNSum + rk) * PTT + rl], 18);
+    for (int w = 0; w < NW; ++w) T += sld(&red[(w * PTT + rl) * kNSum + rx], 18);
   }
   if constexpr (CLUSTER) {
-    if (red_thread) st_cluster(map_to_rank(smem_addr(tot + ((int)rank * kNSum + rk) * PTT + rl), 0), T);
+    if (red_thread) st_cluster(map_to_rank(smem_addr(tot + ((int)rank * PTT + rl) * kNSum + rx), 0), T);
     cluster_sync_all();
     if (rank == 0 && red_thread) {
       T = 0.0;
-      for (unsigned r = 0; r < ncta; ++r) T += sld(&tot[((int)r * kNSum + rk) * PTT + rl], 20);
+      for (unsigned r = 0; r < ncta; ++r) T += sld(&tot[((int)r * PTT + rl) * kNSum + rx], 20);
     }
   }
-  if (rank == 0 && red_thread) {
+  if (rank == 0 && red_thread) {   // whole warps: kNSum * PTT is a multiple of 32
     const int pp = tile * PTW + rl;
-    if (pp < a.P) {
-      const size_t pc = (size_t)pp * a.C + c;
-      if (a.mode == kModeEval) {
+    const size_t pc = (size_t)pp * a.C + c;
+    if (a.mode == kModeEval) {
+      if (pp < a.P) {
         if (rk == 0 && a.E) a.E[pc] = T;
         if (rk >= 1 && rk <= 6 && a.W) a.W[pc * 6 + (rk - 1)] = T;
-      } else {
-        // residual term of Eq. 17-19 in FP64: (E/N - E*)^2, (W_k/N - W*_k)^2 or the force sum; a quantity
-        // without a target contributes 0 when finite and NaN otherwise, so that any non-finite
-        // prediction makes Z infinite
-        const double *tw = a.tEW + (size_t)c * 8;
-        const int bit = rk == 0 ? 1 : (rk <= 6 ? 2 : 4);
-        double term;
-        if (rk == 7) term = T;
-        else {
-          const double d = T * tw[7] - tw[rk];
-          term = d * d;
-        }
-        if (!(mask & bit)) term = isfinite(T) ? 0.0 : T - T;
-        a.part[pc * kNSum + rk] = term;
       }
+    } else {
+      // residual terms of Eq. 17-19 in FP64: (E/N - E*)^2, sum_k (W_k/N - W*_k)^2 and the force sum;
+      // a quantity without a target contributes 0 when finite and NaN otherwise, so that any
+      // non-finite prediction makes Z infinite
+      const int bit = rk == 0 ? 1 : (rk <= 6 ? 2 : 4);
+      double term = T;
+      if (rk <= 6) {
+        const double target = rk == 0 ? a.tE[c] : a.tW[6 * (size_t)c + (rk - 1)];
+        const double d = T * env.inv_nat - target;
+        term = d * d;
+      }
+      if (!(mask & bit)) term = isfinite(T) ? 0.0 : T - T;
+      // the six virial terms of a parameter set sit in lanes 8g+1 .. 8g+6 of one warp: a fixed xor tree
+      double tv = (rk >= 1 && rk <= 6) ? term : 0.0;
+      tv += __shfl_xor_sync(0xffffffffu, tv, 1);
+      tv += __shfl_xor_sync(0xffffffffu, tv, 2);
+      tv += __shfl_xor_sync(0xffffffffu, tv, 4);
+      const int g0 = lane & ~7;
+      const double te = __shfl_sync(0xffffffffu, term, g0);
+      const double tf = __shfl_sync(0xffffffffu, term, g0 + 7);
+      if (pp < a.P && rk < kResidualTerms) a.part[pc * kResidualTerms + rk] = rk == 0 ? te : (rk == 1 ? tv : tf);
     }
   }
   // the next tile (or item) reuses the stage, where the partial sums live. A CTA barrier suffices in
@@ -739,6 +751,8 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
   __shared__ __align__(8) unsigned long long mbar;
   __shared__ int abort_flag;
   __shared__ int s_item;
+  __shared__ double s_fn[NW];            // per-warp FP64 sums of |F*|^2 (target norm, first chunk)
+  __shared__ double s_fr[kMaxCluster];   // rank 0 of a cluster: the ranks' sums
   R *stage = reinterpret_cast<R *>(smem);
   constexpr int APW = kWarp / PT;
 
@@ -787,8 +801,10 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
       bool match = true;
       for (unsigned r = 0; r < ncta; ++r) {
         const CtaRec q = r == rank ? rec : a.recs[rec0 + r];
-        match = match && a.boff[q.s0] == q.B0 && a.boff[q.s0 + q.ns] == q.B0 + q.nb && a.poff[q.s0] == q.Q0 &&
-                a.poff[q.s0 + q.ns] == q.Q0 + q.nq;
+        if (q.ns == 0) continue;
+        const int l = q.s0 + q.ns - 1, ml = a.ameta[l] & 0xffff;
+        match = match && a.boff[q.s0] == q.B0 && a.boff[l] + ml == q.B0 + q.nb && a.poff[q.s0] == q.Q0 &&
+                a.poff[l] + pair_slots(ml) == q.Q0 + q.nq;
       }
       if (!match) continue;
     }
@@ -826,18 +842,25 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
         }
         for (int t = tid; t < nq; t += (NW * kWarp)) sst(&sC[t], gC[t], 8);
       }
+      double f2 = 0.0;   // FP64 sum of |F*|^2 over this thread's atoms (target norm D_f of Eq. 19)
       for (int t = tid; t < ns; t += (NW * kWarp)) {
-        const int b0 = a.boff[s0 + t], b1 = a.boff[s0 + t + 1];
-        sst(&satom[t], make_int4(b0 - B0, a.poff[s0 + t] - Q0, b1 - b0, a.outer[s0 + t]), 9);
+        const int am = a.ameta[s0 + t];
+        sst(&satom[t], make_int4(a.boff[s0 + t] - B0, a.poff[s0 + t] - Q0, am & 0xffff, am >> 16), 9);
         if (fit) {   // target force in the working precision
           const double *f = a.tF + 3 * (int64_t)(s0 + t);
+          const double fx = f[0], fy = f[1], fz = f[2];
           R4 v;
-          v.x = (R)f[0];
-          v.y = (R)f[1];
-          v.z = (R)f[2];
+          v.x = (R)fx;
+          v.y = (R)fy;
+          v.z = (R)fz;
           v.w = R(0);
           sst(&stF[t], v, 10);
+          f2 += (fx * fx + fy * fy) + fz * fz;
         }
+      }
+      if (fit && chunk == 0) {   // the configuration's target norms are formed once, by its first chunk
+        for (int off = 16; off > 0; off >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, off);
+        if (lane == 0) s_fn[warp] = f2;
       }
       if constexpr (!CLUSTER) {
         // thread 0 waits (at most wait_spins polls) for the bulk copies; the barrier below publishes
@@ -860,6 +883,28 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
       }
     }
     const uint8_t mask = fit ? a.tmask[c] : 0;
+    if (fit && chunk == 0) {
+      // target-norm terms of Eq. 17-19 in FP64: E*^2, |W*|^2 and sum_i |F*_i|^2 (0 without the target)
+      double fsum = 0.0;
+      if (tid == 0) {
+        for (int w = 0; w < NW; ++w) fsum += s_fn[w];
+        if constexpr (CLUSTER) st_cluster(map_to_rank(smem_addr(&s_fr[rank]), 0), fsum);
+      }
+      if constexpr (CLUSTER) {
+        cluster_sync_all();
+        if (rank == 0 && tid == 0) {
+          fsum = 0.0;
+          for (unsigned r = 0; r < ncta; ++r) fsum += s_fr[r];
+        }
+      }
+      if (rank == 0 && tid == 0) {
+        double dv = 0.0;
+        for (int k = 0; k < 6; ++k) dv += a.tW[6 * (size_t)c + k] * a.tW[6 * (size_t)c + k];
+        a.dpart[3 * c] = (mask & 1) ? a.tE[c] * a.tE[c] : 0.0;
+        a.dpart[3 * c + 1] = (mask & 2) ? dv : 0.0;
+        a.dpart[3 * c + 2] = (mask & 4) ? fsum : 0.0;
+      }
+    }
     unsigned peer_stage[kMaxCluster];
     int peer_b0[kMaxCluster + 1];
     if constexpr (CLUSTER) {
@@ -871,8 +916,8 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
       peer_b0[ncta] = a.recs[rec0 + ncta - 1].B0 + a.recs[rec0 + ncta - 1].nb - cb0;
     }
 
-    const TileEnv<R> env = {stage, sA, sB, sC, satom, stF, ns, s0, nat, c, cb0, B0, mask, fit, rank, ncta,
-                             peer_stage, peer_b0};
+    const TileEnv<R> env = {stage, sA, sB, sC, satom, stF, ns, s0, nat, c, cb0, B0, rec.inv_nat, mask, fit, rank,
+                             ncta, peer_stage, peer_b0};
     pdl_wait();   // per-call constants of the preparation kernel (a no-op after the first item)
     // the last tile may hold fewer parameter sets: the FP32 single-CTA variants for up to 4 neighbours
     // run it with more atoms in a warp (tiles of 16 or 8 parameter sets); other variants keep the
@@ -889,43 +934,13 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
 }
 
 // Per call, one thread per parameter set: the FP32/FP64 constants of every parameter set (PConsts).
-// When tF4 is given (the adjoint kernel), one thread per atom: the target forces in the working precision
-// as R4 (x, y, z, |F|^2). When tEW is given (fitness), one warp per configuration: its targets and
-// 1/N in FP64 as [C][8] (E*, W*[6], 1/N), and its terms of the target norms of Eq. 17-19 in FP64,
-// dpart[c] = (E*^2, |W*|^2, sum_i |F*_i|^2) (a masked-off quantity contributes 0).
+// When tF4 is given (the adjoint kernel), also one thread per atom: the target forces in the working
+// precision as R4 (x, y, z, |F|^2).
 template <typename R>
 __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restrict__ consts, int form,
-                            int64_t Ntot, const double *__restrict__ tF, typename Vec4<R>::T *__restrict__ tF4,
-                            int C, const int *__restrict__ atom_off, const double *__restrict__ tE,
-                            const double *__restrict__ tW, const uint8_t *__restrict__ tmask,
-                            double *__restrict__ tEW, double *__restrict__ dpart) {
+                            int64_t Ntot, const double *__restrict__ tF, typename Vec4<R>::T *__restrict__ tF4) {
   pdl_trigger();   // the batched kernel may start staging geometry; it waits before reading our output
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tEW && t / 32 < C) {
-    const int c = (int)(t / 32), lane = (int)(t & 31);
-    const uint8_t m = tmask[c];
-    const int a0 = atom_off[c], a1 = atom_off[c + 1];
-    double f2 = 0.0;
-    if (m & 4)
-      for (int i = a0 + lane; i < a1; i += 32) {
-        const double *f = tF + 3 * (int64_t)i;
-        f2 += f[0] * f[0] + f[1] * f[1] + f[2] * f[2];
-      }
-    for (int off = 16; off > 0; off >>= 1) f2 += __shfl_xor_sync(0xffffffffu, f2, off);
-    if (lane == 0) {
-      double *o = tEW + 8 * (size_t)c;
-      o[0] = tE[c];
-      double dv = 0.0;
-      for (int k = 0; k < 6; ++k) {
-        o[1 + k] = tW[6 * c + k];
-        dv += tW[6 * c + k] * tW[6 * c + k];
-      }
-      o[7] = 1.0 / (double)(a1 - a0);
-      dpart[3 * c] = (m & 1) ? tE[c] * tE[c] : 0.0;
-      dpart[3 * c + 1] = (m & 2) ? dv : 0.0;
-      dpart[3 * c + 2] = f2;
-    }
-  }
   if (t < P && form == kFormMinimal) {
     const double *x = params + 6 * t;
     const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
@@ -933,7 +948,7 @@ __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restr
     R *o = consts + 8 * t;
     o[0] = (R)D0;
     o[1] = (R)(-al * log2e);
-    o[2] = (R)(al * r0 * log2e);
+    o[2] = (R)r0;
     o[3] = (R)(-0.5 * al);
     o[4] = (R)be;
     o[5] = (R)h;

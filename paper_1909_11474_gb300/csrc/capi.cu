@@ -60,6 +60,10 @@ int build_plan(tersoff_ctx *ctx, int precision) {
   };
   std::map<Key, std::vector<int>> groups;
   std::map<Key, size_t> smem, adj_smem, smem16, smem12;
+  // bonds and pair slots of the atoms s0 .. s1-1 of one configuration (a0 <= s0 <= s1 <= a1), and where
+  // they start (for an empty slice at the end: where the configuration's bonds end)
+  auto bstart = [&](int s, int a1) { return s < a1 ? c.h_boff[s] : c.h_boff[a1 - 1] + c.h_m[a1 - 1]; };
+  auto qstart = [&](int s, int a1) { return s < a1 ? c.h_poff[s] : c.h_poff[a1 - 1] + tsf::pair_slots(c.h_m[a1 - 1]); };
   for (int cf = 0; cf < c.C; ++cf) {
     const int a0 = c.h_atom_off[cf], a1 = c.h_atom_off[cf + 1], nat = a1 - a0;
     // the smallest cluster whose CTAs fit two per SM; failing that, the smallest of 8 or 16 CTAs that
@@ -75,7 +79,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
         size_t mx = 0;
         for (int r = 0; r < cl; ++r) {
           const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
-          const int nb = c.h_boff[s1] - c.h_boff[s0], nq = c.h_poff[s1] - c.h_poff[s0];
+          const int nb = bstart(s1, a1) - bstart(s0, a1), nq = qstart(s1, a1) - qstart(s0, a1);
           mx = std::max(mx, tsf::batch_smem_bytes_pt(precision, nb, nq, s1 - s0, cl));
         }
         if (mx <= (pass == 0 && !(one_per_sm && cl >= 8) ? soft : (size_t)optin)) {
@@ -91,7 +95,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     groups[k].push_back(cf);
     smem[k] = std::max(smem[k], need);
     if (chosen == 1) {
-      const int nb = c.h_boff[a1] - c.h_boff[a0], nq = c.h_poff[a1] - c.h_poff[a0];
+      const int nb = bstart(a1, a1) - bstart(a0, a1), nq = qstart(a1, a1) - qstart(a0, a1);
       adj_smem[k] = std::max(adj_smem[k], tsf::adjoint_smem_bytes(nb, nq, nat));
       if (precision == 32 && mmax == 4) {
         smem16[k] = std::max(smem16[k], tsf::batch_smem_bytes_pt16(nb, nq, nat));
@@ -109,10 +113,11 @@ int build_plan(tersoff_ctx *ctx, int precision) {
   });
   for (const Key &k : keys) {
     std::vector<int> &cfgs = groups[k];
-    std::stable_sort(cfgs.begin(), cfgs.end(), [&](int x, int y) {
-      return (c.h_boff[c.h_atom_off[x + 1]] - c.h_boff[c.h_atom_off[x]]) >
-             (c.h_boff[c.h_atom_off[y + 1]] - c.h_boff[c.h_atom_off[y]]);
-    });
+    auto cfg_bonds = [&](int x) {
+      const int x0 = c.h_atom_off[x], x1 = c.h_atom_off[x + 1];
+      return bstart(x1, x1) - bstart(x0, x1);
+    };
+    std::stable_sort(cfgs.begin(), cfgs.end(), [&](int x, int y) { return cfg_bonds(x) > cfg_bonds(y); });
     tsf::Bucket b;
     b.mmax = k.mmax;
     b.cluster = k.cl;
@@ -126,8 +131,7 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     for (int cf : cfgs) {
       const int f0 = cfgs.front();
       const int na = c.h_atom_off[cf + 1] - c.h_atom_off[cf], nf = c.h_atom_off[f0 + 1] - c.h_atom_off[f0];
-      const int ba = c.h_boff[c.h_atom_off[cf + 1]] - c.h_boff[c.h_atom_off[cf]];
-      const int bf = c.h_boff[c.h_atom_off[f0 + 1]] - c.h_boff[c.h_atom_off[f0]];
+      const int ba = cfg_bonds(cf), bf = cfg_bonds(f0);
       if (na != nf || ba != bf) b.uniform = false;
     }
     for (int cf : cfgs) {
@@ -137,17 +141,16 @@ int build_plan(tersoff_ctx *ctx, int precision) {
         const int s0 = a0 + std::min(nat, r * per), s1 = a0 + std::min(nat, (r + 1) * per);
         tsf::CtaRec q;
         q.c = cf;
-        q.tile = 0;
         q.s0 = s0;
         q.ns = s1 - s0;
-        q.B0 = c.h_boff[s0];
-        q.nb = c.h_boff[s1] - c.h_boff[s0];
-        q.Q0 = c.h_poff[s0];
-        q.nq = c.h_poff[s1] - c.h_poff[s0];
+        q.B0 = bstart(s0, a1);
+        q.nb = bstart(s1, a1) - q.B0;
+        q.Q0 = qstart(s0, a1);
+        q.nq = qstart(s1, a1) - q.Q0;
         q.cb0 = c.h_boff[a0];
         q.nat = nat;
-        q.rec0 = 0;
         q.pad = 0;
+        q.inv_nat = 1.0 / (double)nat;
         recs.push_back(q);
       }
     }
@@ -224,14 +227,12 @@ int queue_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const terso
   if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
   TSF_CUDA(c.part.ensure((size_t)P * c.C * tsf::kResidualTerms * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
-  TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * (c.form ? 16 : 8) * sizeof(double)));
   TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
   o.form = c.form;
   o.counters = c.counters.as<int>();
   o.consts = c.work.p;
-  o.tEW = c.tew.as<double>();
   o.tE = tg->E;
   o.tW = tg->W;
   o.tF = tg->F;
@@ -269,10 +270,9 @@ int finish_build(tersoff_ctx *ctx) {
   const int64_t N = c.Ntot;
   const int C = c.C;
   const int *h_cnt = c.hp_stage.as<int>();
-  const unsigned hst = *reinterpret_cast<const unsigned *>(h_cnt + N);
+  const unsigned hst = *reinterpret_cast<const unsigned *>(h_cnt + N);   // the build's own status bits
   if (hst & TERSOFF_STATUS_NONFINITE) return fail(ctx, TERSOFF_E_NONFINITE, "non-finite positions or box%s");
   if (hst & TERSOFF_STATUS_NBR_OVERFLOW) return fail(ctx, TERSOFF_E_NBR_OVERFLOW, "an atom has more than max_nbr neighbours%s");
-  if (hst & TERSOFF_STATUS_TIMEOUT) return fail(ctx, TERSOFF_E_TIMEOUT, "the grid barrier of the neighbour build timed out%s");
   const bool same_counts = c.pending_same_layout && (int64_t)c.h_cnt.size() == N &&
                            std::equal(c.h_cnt.begin(), c.h_cnt.end(), h_cnt);
   if (!same_counts) {
@@ -286,21 +286,32 @@ int finish_build(tersoff_ctx *ctx) {
       pl->gen = 0;
       pl->buckets.clear();
     }
-    c.h_boff.assign(N + 1, 0);
-    c.h_poff.assign(N + 1, 0);
+    // host copy of the bond and pair-slot offsets the device built: per configuration from its fixed
+    // base (atom_off[c] * M and atom_off[c] * pair_slots(M)), prefix sums over its atoms
+    c.h_m.assign(N, 0);
+    c.h_boff.assign(N, 0);
+    c.h_poff.assign(N, 0);
     c.h_cfg_maxm.assign(C, 0);
     int maxm = 0;
-    for (int k = 0; k < C; ++k)
+    int64_t nbonds = 0;
+    for (int k = 0; k < C; ++k) {
+      int b = c.h_atom_off[k] * c.M, q = c.h_atom_off[k] * pair_slots(c.M);
       for (int i = c.h_atom_off[k]; i < c.h_atom_off[k + 1]; ++i) {
-        const int m = c.h_cnt[i];
-        c.h_boff[i + 1] = c.h_boff[i] + m;
-        c.h_poff[i + 1] = c.h_poff[i] + pair_slots(m);
-        maxm = std::max(maxm, m);
-        c.h_cfg_maxm[k] = std::max(c.h_cfg_maxm[k], m);
+        const int m = std::min(c.h_cnt[i], c.M);
+        c.h_m[i] = m;
+        c.h_boff[i] = b;
+        c.h_poff[i] = q;
+        b += m;
+        q += pair_slots(m);
+        nbonds += m;
+        maxm = std::max(maxm, c.h_cnt[i]);
+        c.h_cfg_maxm[k] = std::max(c.h_cfg_maxm[k], c.h_cnt[i]);
       }
+    }
     c.max_m = maxm;
-    c.Btot = c.h_boff[N];
-    c.Qtot = c.h_poff[N];
+    c.nbonds = nbonds;
+    c.Btot = N * c.M;
+    c.Qtot = N * pair_slots(c.M);
   }
   if (c.max_m <= 8) {
     int rc = build_plan(ctx, 32);
@@ -316,11 +327,12 @@ int finish_build(tersoff_ctx *ctx) {
 int ensure_geom64(tersoff_ctx *ctx, cudaStream_t s) {
   Ctx &c = ctx->c;
   if (c.geom64) return TERSOFF_OK;
+  // the buffers were allocated by the neighbour build with the capacity of full lists
   const size_t B = std::max<int64_t>(1, c.Btot), Q = std::max<int64_t>(1, c.Qtot);
   TSF_CUDA(c.gA64.ensure(B * sizeof(tsf::dvec4)));
   TSF_CUDA(c.gB64.ensure(B * sizeof(tsf::dvec4)));
   TSF_CUDA(c.gcos64.ensure(Q * sizeof(double)));
-  TSF_CUDA(launch_geometry64(c.Ntot, c.Btot, c.M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
+  TSF_CUDA(launch_geometry64(c.Ntot, c.M, c.atom_cfg.as<int>(), c.atom_off.as<int>(), c.brev.as<int>(),
                              c.pos.as<double>(), c.box.as<double>(), c.cnt.as<int>(), c.nbr.as<int>(),
                              c.shift.as<char4>(), c.boff.as<int>(), c.poff.as<int>(), c.R1, c.R2, c.gA64.p,
                              c.gB64.p, c.gcos64.p, pair_slots(std::min(c.max_m, c.M)), s));
@@ -357,15 +369,17 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   Ctx &c = ctx->c;
   cudaSetDevice(c.device);
   cudaDeviceSynchronize();
-  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.box, &c.cfg_tot, &c.grid_bar, &c.counters,
+  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.box, &c.build_status, &c.counters,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
-                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.outer, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart, &c.tew,
+                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.ameta, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_keys, &c.md_ke, &c.md_boxd};
   for (auto *b : bufs) b->release();
   c.hp_stage.release();
   if (c.stage_event) cudaEventDestroy(c.stage_event);
+  if (c.build_done) cudaEventDestroy(c.build_done);
+  if (c.copy_stream) cudaStreamDestroy(c.copy_stream);
   for (cudaEvent_t ev : c.timer.ev) cudaEventDestroy(ev);
   if (c.g_fitness.exec) cudaGraphExecDestroy(c.g_fitness.exec);
   for (cudaStream_t st : c.side) cudaStreamDestroy(st);
@@ -508,10 +522,9 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.shift.ensure(N * M * sizeof(char4)));
   TSF_CUDA(c.boff.ensure((N + 1) * sizeof(int)));
   TSF_CUDA(c.poff.ensure((N + 1) * sizeof(int)));
-  TSF_CUDA(c.cfg_tot.ensure((size_t)C * 4 * sizeof(int)));
-  TSF_CUDA(c.grid_bar.ensure(sizeof(unsigned)));
+  TSF_CUDA(c.build_status.ensure(sizeof(unsigned)));
   TSF_CUDA(c.brev.ensure(bond_cap * sizeof(int)));
-  TSF_CUDA(c.outer.ensure(std::max<int64_t>(1, N) * sizeof(int)));
+  TSF_CUDA(c.ameta.ensure(std::max<int64_t>(1, N) * sizeof(int)));
   TSF_CUDA(c.gA32.ensure(bond_cap * sizeof(float4)));
   TSF_CUDA(c.gB32.ensure(bond_cap * sizeof(float4)));
   TSF_CUDA(c.gcos32.ensure(slot_cap * sizeof(float)));
@@ -529,16 +542,17 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
     TSF_CUDA(tsf::preload_fitness_kernels());
     c.preloaded = true;
   }
-  if (c.build_resident <= 0) c.build_resident = tsf::build_batch_resident();
-  if (c.build_resident <= 0) return fail(ctx, TERSOFF_E_CUDA, "occupancy query of the build kernel failed%s");
+  if (!c.copy_stream) TSF_CUDA(cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking));
+  if (!c.build_done) TSF_CUDA(cudaEventCreateWithFlags(&c.build_done, cudaEventDisableTiming));
+  int nat_max = 1;
+  for (int k = 0; k < C; ++k) nat_max = std::max(nat_max, cfg->atom_off[k + 1] - cfg->atom_off[k]);
   TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
+  TSF_CUDA(cudaMemsetAsync(c.build_status.p, 0, sizeof(unsigned), s));
   unsigned *st = c.status.as<unsigned>();
   tsf::BuildLaunch L = {};
   L.C = C;
   L.M = M;
   L.Ntot = N;
-  L.bond_cap = bond_cap;
-  L.slot_cap = slot_cap;
   L.R1 = R1;
   L.R2 = R2;
   L.atom_off = c.atom_off.as<int>();
@@ -549,25 +563,25 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   L.cnt = c.cnt.as<int>();
   L.nbr = c.nbr.as<int>();
   L.shift = c.shift.as<char4>();
-  L.cfg_tot = c.cfg_tot.as<int>();
   L.boff = c.boff.as<int>();
   L.poff = c.poff.as<int>();
   L.brev = c.brev.as<int>();
   L.gA = c.gA32.as<float4>();
   L.gB = c.gB32.as<float4>();
   L.gcos = c.gcos32.as<float>();
-  L.outer = c.outer.as<int>();
-  L.barrier = c.grid_bar.as<unsigned>();
+  L.ameta = c.ameta.as<int>();
   L.status = st;
-  L.resident = c.build_resident;
-  L.wait_spins = c.wait_spins;
+  L.build_status = c.build_status.as<unsigned>();
+  L.nat_max = nat_max;
   TSF_CUDA(tsf::launch_build_batch(L, s));
-  // neighbour counts and status go back to pinned host memory; the host reads them (and builds or
-  // keeps the work schedule) when the next call needs the build, so the caller's own work overlaps
-  // the build kernel
-  TSF_CUDA(cudaMemcpyAsync(hp, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, s));
-  TSF_CUDA(cudaMemcpyAsync(hp + N, c.status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-  TSF_CUDA(cudaEventRecord(c.stage_event, s));
+  // neighbour counts and the build's status go back to pinned host memory on a side stream, beside
+  // whatever the caller queues next on `stream`; the host reads them (and builds or keeps the work
+  // schedule) when the next call needs the build
+  TSF_CUDA(cudaEventRecord(c.build_done, s));
+  TSF_CUDA(cudaStreamWaitEvent(c.copy_stream, c.build_done, 0));
+  TSF_CUDA(cudaMemcpyAsync(hp, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, c.copy_stream));
+  TSF_CUDA(cudaMemcpyAsync(hp + N, c.build_status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c.copy_stream));
+  TSF_CUDA(cudaEventRecord(c.stage_event, c.copy_stream));
   c.geom64 = false;
   c.pending = true;
   c.pending_same_layout = same_layout;
@@ -598,7 +612,7 @@ int tersoff_build_info(tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t
   if (!ctx) return TERSOFF_E_ARG;
   if (int rc = tsf::finish_build(ctx)) return rc;
   if (ntot) *ntot = ctx->c.Ntot;
-  if (nbonds) *nbonds = ctx->c.Btot;
+  if (nbonds) *nbonds = ctx->c.nbonds;
   if (max_m) *max_m = ctx->c.max_m;
   return TERSOFF_OK;
 }
@@ -674,14 +688,12 @@ int tersoff_autotune(tersoff_ctx *ctx, const double *params, int32_t P, const te
   if (precision == 64 && (rc = tsf::ensure_geom64(ctx, S(stream)))) return rc;
   TSF_CUDA(c.part.ensure((size_t)P * c.C * tsf::kResidualTerms * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
-  TSF_CUDA(c.tew.ensure((size_t)c.C * 8 * sizeof(double)));
   TSF_CUDA(c.work.ensure((size_t)P * (c.form ? 16 : 8) * sizeof(double)));
   TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
   tsf::BatchOut o = {};
   o.form = c.form;
   o.counters = c.counters.as<int>();
   o.consts = c.work.p;
-  o.tEW = c.tew.as<double>();
   o.tE = tg->E;
   o.tW = tg->W;
   o.tF = tg->F;

@@ -80,6 +80,20 @@ __device__ __forceinline__ ExactPair exact_pair(double xjx, double xjy, double x
 }
 
 
+// FP32 -> FP64, exact, built from the IEEE-754 binary32 and binary64 layouts with integer operations
+// (sign kept, exponent rebiased from 127 to 1023, significand shifted left by 29), so that the
+// conversions of per-warp partial sums do not queue on the device's scarce FP64 unit. Zeros take the
+// same path; subnormal, infinite and NaN inputs (which partial sums of finite terms do not produce in
+// practice) are converted by the FP64 unit.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if ((e == 0u && (u << 1) != 0u) || e == 0xffu) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | (e == 0u ? 0u : ((e + 896u) << 20)) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // Sums over the lanes of one warp that share `lane % PT` (the lanes handling the same parameter
 // set): xor-shuffle over the atom-slot bits of the lane index.
 template <int PT, typename T>

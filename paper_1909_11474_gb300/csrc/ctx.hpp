@@ -78,30 +78,33 @@ struct PinnedBuf {
   }
 };
 
-// Geometry cache of a neighbour build: compressed bond list (CSR over atoms) with the
-// parameter-independent quantities of every bond and of every unordered pair of bonds of an atom.
+// Geometry cache of a neighbour build: the bonds of atom i are boff[i] .. boff[i] + m_i - 1 (m_i =
+// min(cnt_i, M)), its pair slots poff[i] .. poff[i] + pair_slots(m_i) - 1; the bonds of configuration c
+// start at atom_off[c] * M and its pair slots at atom_off[c] * pair_slots(M) (the capacity of full
+// lists), so the arrays have gaps between configurations.
 struct Geometry {
-  const int *boff;      // [Ntot+1] first bond of atom i
-  const int *poff;      // [Ntot+1] first unordered bond pair of atom i
-  const int *brev;      // [Btot] bond index of the reverse entry (j; i, -n)
-  const void *gA;       // [Btot] R4: unit vector d/r (x, y, z), r
-  const void *gB;       // [Btot] R4: 2/r, f_C(r), f_C'(r), rev | j << 16
-  const void *gcos;     // [Qtot] R: cos theta of pair (e, f), e < f, row-major over e
+  const int *boff;      // [Ntot] first bond of atom i
+  const int *poff;      // [Ntot] first unordered bond pair of atom i
+  const int *brev;      // [Ntot*M] bond index of the reverse entry (j; i, -n)
+  const void *gA;       // [Ntot*M] R4: unit vector d/r (x, y, z), r
+  const void *gB;       // [Ntot*M] R4: 2/r, f_C(r), f_C'(r), rev | j << 16
+  const void *gcos;     // [Ntot*pair_slots(M)] R: cos theta of pair (e, f), e < f, row-major over e
 };
 
 // What one cluster rank of the batched evaluation works on, for every parameter tile: atoms
 // s0 .. s0+ns-1 of configuration c (its slice when the configuration spans a cluster), bonds
 // B0 .. B0+nb-1, padded pair slots Q0 .. Q0+nq-1; cb0 = first bond and nat = atom count of the
-// configuration. tile and rec0 are unused (kept for the 16-byte record layout).
+// configuration.
 struct __align__(16) CtaRec {
-  int c, tile, s0, ns;
-  int B0, nb, Q0, nq;
-  int cb0, nat, rec0, pad;
+  int c, s0, ns, B0;
+  int nb, Q0, nq, cb0;
+  int nat, pad;
+  double inv_nat;   // 1/nat in FP64 (the per-atom energy and virial of Eq. 17-18)
 };
 
-// Residual terms the batched fitness writes per (parameter set, configuration), in FP64: the energy
-// term, six virial terms and the force sum (Eq. 17-19 before the sums over configurations).
-constexpr int kResidualTerms = 8;
+// Residual terms the batched fitness writes per (parameter set, configuration), in FP64: the energy,
+// virial and force terms of Eq. 17-19 before the sums over configurations.
+constexpr int kResidualTerms = 3;
 // Largest thread-block cluster a configuration of the batched kernels is split over.
 constexpr int kMaxClusterCtas = 16;
 
@@ -179,24 +182,26 @@ struct Ctx {
   bool pending_same_layout = false;   // that build has the previous build's layout
   bool geom64 = false;   // FP64 geometry records built for the current neighbour build
   bool preloaded = false; // fitness kernels loaded on the device (module loading done up front)
-  // polls of the bounded device-side waits (batched kernel's staging wait, build's grid barrier);
-  // negative: the kernels' built-in bounds (tersoff_set_wait_limit)
+  // polls of the batched kernel's bounded staging wait; negative: its built-in bound
+  // (tersoff_set_wait_limit)
   int64_t wait_spins = -1;
   int C = 0;
-  int64_t Ntot = 0, Btot = 0, Qtot = 0;
+  int64_t Ntot = 0, Btot = 0, Qtot = 0;   // atoms; capacities of the bond and pair-slot arrays
+  int64_t nbonds = 0;                      // bonds (neighbour entries kept) of the build
   int M = 0, max_m = 0;
   double R1 = 0, R2 = 0;
-  std::vector<int> h_atom_off, h_cnt, h_boff, h_poff, h_cfg_maxm;
+  std::vector<int> h_atom_off, h_cnt, h_m, h_boff, h_poff, h_cfg_maxm;   // host mirror of the build's layout
   PinnedBuf hp_stage;   // pinned staging: atom table uploads, neighbour-count readback, offsets
   cudaEvent_t stage_event = nullptr;   // recorded after the staging buffer's last upload
   DevBuf atom_off, atom_cfg, pos, box, cnt, nbr, shift, boff, poff, brev;
-  DevBuf cfg_tot, grid_bar;   // per-configuration totals and the grid barrier of the fused build
-  int build_resident = 0;     // resident CTAs of the fused build kernel on this device
+  DevBuf build_status;        // status bits of the last neighbour build alone
+  cudaStream_t copy_stream = nullptr;   // the build's count readback runs here, beside later calls
+  cudaEvent_t build_done = nullptr;     // recorded after the build kernel on the caller's stream
   DevBuf counters;   // per-launch work counters of the persistent batched kernels
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
-  DevBuf outer;   // [Ntot] int: nonzero if the atom has a bond beyond R1 (f_C != 1)
+  DevBuf ameta;   // [Ntot] int: bonds kept (min(cnt, M)) | (some bond beyond R1, f_C != 1) << 16
   BatchPlan plan32, plan64;
-  DevBuf part, dpart, work, tf4, gpart, tew;
+  DevBuf part, dpart, work, tf4, gpart;
 
   // --- MD state ---
   int md_N = 0, md_M = 0;
@@ -220,31 +225,29 @@ struct Ctx {
 
 // ---- launchers (defined in the .cu files) ----
 // neighbors.cu
-// Arguments of the fused neighbour build (one cooperative launch over all configurations).
+// Arguments of the neighbour build (one launch, one CTA per configuration).
 struct BuildLaunch {
   int C, M;
-  int64_t Ntot, bond_cap, slot_cap;
+  int64_t Ntot;
   double R1, R2;
   const int *atom_off;
   const double *pos_in, *box_in;
   double *pos, *box;
   int *cnt, *nbr;
   char4 *shift;
-  int *cfg_tot, *boff, *poff, *brev;
+  int *boff, *poff, *brev;
   float4 *gA, *gB;
   float *gcos;
-  int *outer;
-  unsigned *barrier, *status;
-  int resident;   // CTAs of the build kernel that can be resident at once (build_batch_resident)
-  int64_t wait_spins;   // polls of the grid barrier before it gives up (negative: the built-in bound)
+  int *ameta;
+  unsigned *status, *build_status;   // the context's status word and the build's own
+  int nat_max;    // largest configuration (atoms)
 };
 cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s);
-int build_batch_resident();
 // FP64 bond records and pair cosines of the current build (on the first FP64 evaluation)
-cudaError_t launch_geometry64(int64_t Ntot, int64_t Btot, int M, const int *atom_cfg, const int *atom_off,
-                              const int *brev, const double *pos, const double *box, const int *cnt,
-                              const int *nbr, const char4 *shift, const int *boff, const int *poff, double R1,
-                              double R2, void *gA, void *gB, void *gcos, int max_slots, cudaStream_t s);
+cudaError_t launch_geometry64(int64_t Ntot, int M, const int *atom_cfg, const int *atom_off, const int *brev,
+                              const double *pos, const double *box, const int *cnt, const int *nbr,
+                              const char4 *shift, const int *boff, const int *poff, double R1, double R2, void *gA,
+                              void *gB, void *gcos, int max_slots, cudaStream_t s);
 
 // batch.cu
 struct BatchOut {
@@ -253,9 +256,9 @@ struct BatchOut {
   double *W;          // [P][C][6]
   const double *tE, *tW, *tF;
   const uint8_t *tmask;
-  double *part;       // workspace: [P][C][8] FP64 residual terms per (p, c): e, v[6], f
-  double *dpart;      // workspace: [C][3] per-configuration terms of the target norms D_q (FP64)
-  double *tEW;        // workspace: [C][8] E*, W*[6], 1/N per configuration (FP64)
+  double *part;       // workspace: [P][C][3] FP64 residual terms per (p, c)
+  double *dpart;      // workspace: [C][3] per-configuration terms of the target norms D_q (FP64), written
+                      // by the batched kernel (fitness)
   void *consts;       // workspace: [P][8] per-parameter-set constants (working precision)
   int *counters;      // workspace: one work counter per launch bucket
   bool pdl = false;   // launch the batched kernels with programmatic stream serialization

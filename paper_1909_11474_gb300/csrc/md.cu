@@ -396,7 +396,7 @@ __device__ __forceinline__ void md_atom(const R (&ux)[kMdMaxM], const R (&uy)[kM
   R fR[M], fA[M], zeta[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    const R x = ex2(r[j] * K.k1 + K.k0);
+    const R x = ex2((r[j] - K.k0) * K.k1);   // r - r0 exact in FP32 near r0
     const R Dx = K.D0 * x;
     fR[j] = Dx * x;
     fA[j] = Dx + Dx;
@@ -762,14 +762,14 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
   const double log2e = 1.4426950408889634;
   if (precision == 64) {
-    PConsts<double> K{D0, -al * log2e, al * r0 * log2e, -0.5 * al, be, h, n, -0.5 / n};
+    PConsts<double> K{D0, -al * log2e, r0, -0.5 * al, be, h, n, -0.5 / n};
     md_force_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, u4, m4, c.md_cnt.as<int>(),
                                                         c.md_nbr.as<int>(), c.md_shift.as<char4>(),
                                                         c.md_Pij.as<dvec4>(), c.md_red.as<double>(), E, W, st);
     md_gather_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, c.md_cnt.as<int>(), c.md_rev.as<int>(),
                                                          c.md_Pij.as<dvec4>(), reinterpret_cast<double *>(F));
   } else {
-    PConsts<float> K{(float)D0, (float)(-al * log2e), (float)(al * r0 * log2e), (float)(-0.5 * al), (float)be, (float)h,
+    PConsts<float> K{(float)D0, (float)(-al * log2e), (float)r0, (float)(-0.5 * al), (float)be, (float)h,
                      (float)n, (float)(-0.5 / n)};
     md_force_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, u4, m4, c.md_cnt.as<int>(),
                                                        c.md_nbr.as<int>(), c.md_shift.as<char4>(),

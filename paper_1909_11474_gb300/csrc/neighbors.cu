@@ -53,17 +53,6 @@ __device__ __forceinline__ void cutoff_fc(double r, double R1, double R2, double
   }
 }
 
-// Owner atom of bond b: the last atom i with boff[i] <= b (atoms without bonds are skipped).
-__device__ __forceinline__ int64_t bond_owner(const int *__restrict__ boff, int64_t Ntot, int b) {
-  int64_t lo = 0, hi = Ntot;
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (boff[mid] <= b) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
 // Per bond: unit vector, r, 2/r, f_C, f_C' and, packed into one int (rev | j << 16), the
 // configuration-local indices of the reverse bond and of the neighbour atom (4th slot: as a double,
 // or as the bit pattern of the int in the FP32 record). The bond vector d is formed in FP64 by the
@@ -101,20 +90,25 @@ __device__ __forceinline__ bool bond_record(const ExactPair &p, double R1, doubl
   }
 }
 
+// FP64 records of the current build (its first FP64 evaluation): one thread per list slot (atom i,
+// entry e < min(cnt_i, M)); bond b = boff[i] + e. cb0 = the first bond of i's configuration,
+// atom_off[c] * M.
 template <typename R>
-__global__ void geometry_bond_kernel(int64_t Ntot, int Btot, int M, const int *__restrict__ atom_cfg,
+__global__ void geometry_bond_kernel(int64_t Ntot, int M, const int *__restrict__ atom_cfg,
                                      const int *__restrict__ atom_off, const int *__restrict__ brev,
                                      const double *__restrict__ pos, const double *__restrict__ box,
-                                     const int *__restrict__ nbr, const char4 *__restrict__ shift,
-                                     const int *__restrict__ boff, double R1, double R2,
-                                     typename Vec4<R>::T *__restrict__ gA, typename Vec4<R>::T *__restrict__ gB) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= Btot) return;
-  const int64_t i = bond_owner(boff, Ntot, b);
-  const int e = b - boff[i];
+                                     const int *__restrict__ cnt, const int *__restrict__ nbr,
+                                     const char4 *__restrict__ shift, const int *__restrict__ boff, double R1,
+                                     double R2, typename Vec4<R>::T *__restrict__ gA,
+                                     typename Vec4<R>::T *__restrict__ gB) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = t / M;
+  const int e = (int)(t % M);
+  if (i >= Ntot || e >= min(cnt[i], M)) return;
+  const int b = boff[i] + e;
   const int c = atom_cfg[i];
   const double *H = box + 9 * c;
-  const int cb0 = boff[atom_off[c]];   // first bond of the configuration
+  const int cb0 = atom_off[c] * M;   // first bond of the configuration
   const int j = nbr[i * M + e];
   // packed: configuration-local index of the reverse bond (bits 0-15) and of atom j (bits 16-31)
   const int rl = (brev[b] - cb0) | ((j - atom_off[c]) << 16);
@@ -137,9 +131,9 @@ __global__ void geometry_pair_kernel(int64_t Ntot, int slots, const int *__restr
   const int64_t i = t / slots;
   const int q = (int)(t % slots);
   if (i >= Ntot) return;
-  const int q0 = poff[i], nslot = poff[i + 1] - q0;
-  if (q >= nslot) return;
   const int m = min(cnt[i], M);
+  const int q0 = poff[i], nslot = pair_slots(m);
+  if (q >= nslot) return;
   // slot q -> (e, f), e < f, row-major over e
   int e = 0, rem = q;
   while (e < m && rem >= m - 1 - e) {
@@ -156,50 +150,54 @@ __global__ void geometry_pair_kernel(int64_t Ntot, int slots, const int *__restr
 }
 
 // ---------------------------------------------------------------------------------------------
-// Fused neighbour build of a batch of configurations: one launch, cooperative (every CTA resident),
-// CTAs over contiguous chunks of configurations, two phases separated by a grid barrier.
-//  phase 1, per configuration: FP64 and FP32 copies of the positions, the box constants of the FP32
-//    membership test, the neighbour lists (warp per atom, as described at `member`) and the totals
-//    (bonds, pair slots, largest neighbour count) of the configuration;
-//  phase 2, per configuration: its first bond and pair slot (sums of the totals of the configurations
-//    before it), the bond CSR of its atoms (block scans), the reverse bond of every bond, the FP32
-//    bond records and the pair cosines.
-// The bond and pair arrays are written with the capacity Ntot*M and Ntot*pair_slots(M) they were
-// allocated with; an index beyond it is reported as a neighbour overflow and not written.
+// Neighbour build of a batch of configurations: one launch, one CTA per configuration, two phases
+// separated by CTA barriers only. Every configuration's bonds and pair slots start at a fixed base,
+// atom_off[c] * M and atom_off[c] * pair_slots(M) (the capacity of full lists), so no configuration
+// waits for another's counts.
+//  phase 1: FP64 and FP32 copies of the positions, the box constants of the FP32 membership test, the
+//    neighbour lists (warp per atom, as described at `member`);
+//  phase 2: the bond offsets of the configuration's atoms (block scans), the reverse bond of every
+//    bond, the FP32 bond records and the pair cosines.
+// Shared memory (dynamic, sized for the largest configuration of the launch): FP32 positions, per-atom
+// counts, offsets and flags, and, where they fit, the configuration's lists and bond unit vectors (the
+// reverse-bond search and the pair cosines then read shared memory instead of global memory).
 constexpr int kBuildThreads = 256;
 constexpr int kBuildWarps = kBuildThreads / 32;
 constexpr int kBuildMaxAtoms = 1024;
-constexpr unsigned kGridSpins = 1u << 22;   // bound of the grid barrier wait (with 128 ns sleeps)
+constexpr size_t kBuildSmemCap = 64 * 1024;   // dynamic shared memory per CTA at most (three CTAs per SM)
 
 struct BuildParams {
   int C, M;
-  int64_t Ntot, bond_cap, slot_cap;
+  int64_t Ntot;
   double R1, R2;
   const int *atom_off;
   const double *pos_in, *box_in;   // caller's positions [Ntot][3] and boxes [C][3][3]
   double *pos, *box;               // the context's copies
   int *cnt, *nbr;
   char4 *shift;
-  int *cfg_tot;                    // [C][4]: bonds, pair slots, largest neighbour count, 0
   int *boff, *poff, *brev;
   float4 *gA, *gB;
   float *gcos;
-  int *outer;
-  unsigned *barrier;               // zero at launch
-  unsigned *status;
-  unsigned wait_spins;             // polls of the grid barrier before it gives up (a timeout)
+  int *ameta;                      // [Ntot]: bonds kept (min(cnt, M)) | (some bond beyond R1) << 16
+  unsigned *status, *build_status; // the context's status word and the build's own (read by the host)
+  int nat_max;                     // largest configuration of the launch (shared-memory layout)
+  int lists_in_smem;               // the lists and unit vectors fit in shared memory
 };
 
-// Sum / max / exclusive scan over the threads of a block (kBuildThreads), in a fixed order.
-__device__ __forceinline__ long long block_sum_ll(long long v, long long *red) {
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  long long t = 0;
-  for (int w = 0; w < kBuildWarps; ++w) t += red[w];
-  return t;
+__device__ __forceinline__ void build_flag(const BuildParams &a, unsigned bit) {
+  set_status(a.status, bit);
+  set_status(a.build_status, bit);
 }
+
+// Dynamic shared memory of the build kernel for configurations of up to nat atoms.
+__host__ __device__ inline size_t build_smem_base(int nat) {
+  return (size_t)nat * sizeof(float4) + (size_t)(4 * nat + 2) * sizeof(int);
+}
+__host__ __device__ inline size_t build_smem_lists(int nat, int M) {
+  return (size_t)nat * M * (sizeof(int2) + sizeof(float4));
+}
+
+// Sum / max / exclusive scan over the threads of a block (kBuildThreads), in a fixed order.
 __device__ __forceinline__ float block_max_f(float v, float *red) {
   for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
   __syncthreads();
@@ -226,28 +224,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int *red, int &total) {
     total += red[w];
   }
   return before + incl - v;
-}
-
-// Grid-wide barrier of a cooperative launch; the wait is bounded (at most `spins` polls), and a timeout
-// is reported in the status word (the second phase then runs on whatever the first phase has written,
-// within bounds: every index it writes is checked against the capacities, so a build that timed out
-// writes nothing out of range; the host reports it as TERSOFF_E_TIMEOUT and keeps no result of it).
-__device__ __forceinline__ void grid_barrier(unsigned *ctr, unsigned *status, unsigned spins) {
-  __threadfence();   // this thread's global writes, before the arrival below
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    atomicAdd(ctr, 1u);
-    unsigned k = 0;
-    while (*reinterpret_cast<volatile unsigned *>(ctr) < gridDim.x) {
-      if (k++ >= spins) {
-        set_status(status, TERSOFF_STATUS_TIMEOUT);
-        break;
-      }
-      __nanosleep(128);
-    }
-    __threadfence();
-  }
-  __syncthreads();
 }
 
 // Box constants of one configuration for the FP32 membership test: Hinv, the image search range
@@ -313,74 +289,80 @@ __device__ bool box_part2(const BoxPart1 &o, const double *H, float xm, double R
   return isfinite(band) && nmax <= 127.f;
 }
 
-__global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildParams a) {
-  __shared__ float4 s_p32[kBuildMaxAtoms];
-  __shared__ int s_m[kBuildMaxAtoms];
-  __shared__ int s_boff[kBuildMaxAtoms + 1];
-  __shared__ int s_poff[kBuildMaxAtoms + 1];
-  __shared__ int s_outer[kBuildMaxAtoms];
+__global__ void __launch_bounds__(kBuildThreads, 3) build_batch_kernel(const BuildParams a) {
+  extern __shared__ __align__(16) unsigned char bsm[];
+  const int nmax = a.nat_max, M = a.M;
+  float4 *s_p32 = reinterpret_cast<float4 *>(bsm);
+  int *s_m = reinterpret_cast<int *>(s_p32 + nmax);
+  int *s_boff = s_m + nmax;            // [nmax + 1]
+  int *s_poff = s_boff + nmax + 1;     // [nmax + 1]
+  int *s_outer = s_poff + nmax + 1;
+  int2 *s_list = reinterpret_cast<int2 *>(bsm + (build_smem_base(nmax) + 15) / 16 * 16);   // [nmax * M]
+  float4 *s_u = reinterpret_cast<float4 *>(s_list + (size_t)nmax * M);                     // [nmax * M]
   __shared__ Pre32 s_q;
   __shared__ BoxPart1 s_b1;
   __shared__ double s_H[9];
   __shared__ int s_ok, s_nmax;
-  __shared__ long long s_red[kBuildWarps];
+  __shared__ float s_fred[kBuildWarps];
   __shared__ int s_ired[kBuildWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int M = a.M;
-  // contiguous chunk of configurations of this CTA
-  const int per = (a.C + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int c_begin = min(a.C, (int)blockIdx.x * per), c_end = min(a.C, c_begin + per);
+  const bool lists = a.lists_in_smem != 0;
+  const int c = blockIdx.x;
+  const int a0 = a.atom_off[c], nat = a.atom_off[c + 1] - a0;
 
-  // ---- phase 1: positions, box constants, neighbour lists, totals
-  for (int c = c_begin; c < c_end; ++c) {
-    const int a0 = a.atom_off[c], nat = a.atom_off[c + 1] - a0;
-    // the last warp's first thread works out the box-only constants while the other warps load
-    // the positions
-    constexpr int kLoadThreads = kBuildThreads - 32;
-    if (tid == kLoadThreads) {
-      double H[9];
-      for (int k = 0; k < 9; ++k) {
-        H[k] = a.box_in[9 * c + k];
-        s_H[k] = H[k];
-        a.box[9 * c + k] = H[k];
-      }
-      box_part1(H, a.R2, s_b1);
+  // ---- phase 1: positions, box constants, neighbour lists
+  // the last warp's first thread works out the box-only constants while the other warps load the
+  // positions
+  constexpr int kLoadThreads = kBuildThreads - 32;
+  if (tid == kLoadThreads) {
+    double H[9];
+    for (int k = 0; k < 9; ++k) {
+      H[k] = a.box_in[9 * c + k];
+      s_H[k] = H[k];
+      a.box[9 * c + k] = H[k];
     }
-    float xm = 0.f;
-    int finite = 1;
-    for (int t = tid; tid < kLoadThreads && t < nat; t += kLoadThreads) {
-      const double *x = a.pos_in + 3 * (int64_t)(a0 + t);
-      const double x0 = x[0], x1 = x[1], x2 = x[2];
-      double *y = a.pos + 3 * (int64_t)(a0 + t);
-      y[0] = x0;
-      y[1] = x1;
-      y[2] = x2;
-      finite &= (isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 1 : 0;
-      const float4 v = make_float4((float)x0, (float)x1, (float)x2, 0.f);
-      s_p32[t] = v;
-      xm = fmaxf(xm, fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
-    }
-    xm = block_max_f(xm, reinterpret_cast<float *>(s_red));
-    finite = __syncthreads_and(finite);
-    if (tid == 0) {
-      Pre32 q;
-      int nmax = 0;
-      const bool ok = finite && box_part2(s_b1, s_H, xm, a.R2, q, nmax);
-      if (!ok) set_status(a.status, TERSOFF_STATUS_NONFINITE);
-      s_q = q;
-      s_ok = ok ? 1 : 0;
-      s_nmax = nmax;
-    }
-    __syncthreads();
+    box_part1(H, a.R2, s_b1);
+  }
+  float xm = 0.f;
+  int finite = 1;
+  for (int t = tid; tid < kLoadThreads && t < nat; t += kLoadThreads) {
+    const double *x = a.pos_in + 3 * (int64_t)(a0 + t);
+    const double x0 = x[0], x1 = x[1], x2 = x[2];
+    double *y = a.pos + 3 * (int64_t)(a0 + t);
+    y[0] = x0;
+    y[1] = x1;
+    y[2] = x2;
+    finite &= (isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 1 : 0;
+    const float4 v = make_float4((float)x0, (float)x1, (float)x2, 0.f);
+    s_p32[t] = v;
+    xm = fmaxf(xm, fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
+  }
+  xm = block_max_f(xm, s_fred);
+  finite = __syncthreads_and(finite);
+  if (tid == 0) {
+    Pre32 q;
+    int nimg = 0;
+    const bool ok = finite && box_part2(s_b1, s_H, xm, a.R2, q, nimg);
+    if (!ok) build_flag(a, TERSOFF_STATUS_NONFINITE);
+    s_q = q;
+    s_ok = ok ? 1 : 0;
+    s_nmax = nimg;
+  }
+  __syncthreads();
+  {
     const Pre32 q = s_q;
     const bool ok = s_ok != 0;
-    const int nmax = s_nmax;
+    const int nimg = s_nmax;
     const double R2sq = a.R2 * a.R2;
     // one warp per atom i, lanes over j; each lane keeps up to kNbrBuf accepted images of its j in
     // registers, so one enumeration suffices (a lane with more enumerates again for the rest); a warp
     // scan of the per-lane counts gives the output positions, so entries land in ascending
     // (j, n0, n1, n2) order
     constexpr int kNbrBuf = 4;
+    // with every candidate range narrower than one lattice period (rng < 1/2 on each axis: plane
+    // spacings above 2 R2), each j has at most one candidate image; the warp then tests it straight
+    // away and places the accepted entries with a ballot (the same candidates and order as the loops)
+    const bool single = q.rng[0] < 0.5f && q.rng[1] < 0.5f && q.rng[2] < 0.5f;
     for (int li = warp; li < nat; li += kBuildWarps) {
       const int64_t i = a0 + li;
       const double *xi = a.pos_in + 3 * i;
@@ -398,13 +380,27 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
           image_range(dx * q.Hi[0] + dy * q.Hi[3] + dz * q.Hi[6], q.rng[0], lo0, hi0);
           image_range(dx * q.Hi[1] + dy * q.Hi[4] + dz * q.Hi[7], q.rng[1], lo1, hi1);
           image_range(dx * q.Hi[2] + dy * q.Hi[5] + dz * q.Hi[8], q.rng[2], lo2, hi2);
-          // every valid image index lies within +-nmax; the clamp only bounds the loops
-          lo0 = max(lo0, -nmax); hi0 = min(hi0, nmax);
-          lo1 = max(lo1, -nmax); hi1 = min(hi1, nmax);
-          lo2 = max(lo2, -nmax); hi2 = min(hi2, nmax);
+          // every valid image index lies within +-nimg; the clamp only bounds the loops
+          lo0 = max(lo0, -nimg); hi0 = min(hi0, nimg);
+          lo1 = max(lo1, -nimg); hi1 = min(hi1, nimg);
+          lo2 = max(lo2, -nimg); hi2 = min(hi2, nimg);
         }
         const int j = a0 + (jl < nat ? jl : 0);
         const double *xj = a.pos_in + 3 * (int64_t)j;
+        if (single) {
+          const bool cand = lo0 <= hi0 && lo1 <= hi1 && lo2 <= hi2 && !(jl == li && lo0 == 0 && lo1 == 0 && lo2 == 0);
+          const bool acc = cand && member(q, dx, dy, dz, lo0, lo1, lo2, xj, xi, s_H, R2sq);
+          const unsigned bal = __ballot_sync(0xffffffffu, acc);
+          const int w = count + __popc(bal & ((1u << lane) - 1u));
+          if (acc && w < M) {
+            const char4 sh = make_char4((signed char)lo0, (signed char)lo1, (signed char)lo2, 0);
+            a.nbr[i * M + w] = j;
+            a.shift[i * M + w] = sh;
+            if (lists) s_list[li * M + w] = make_int2(jl, *reinterpret_cast<const int *>(&sh));
+          }
+          count += __popc(bal);
+          continue;
+        }
         int mine = 0;
         int buf[kNbrBuf];
         for (int n0 = lo0; n0 <= hi0; ++n0)
@@ -432,6 +428,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
           if (u < mine && w0 + u < M) {
             a.nbr[i * M + w0 + u] = j;
             a.shift[i * M + w0 + u] = *reinterpret_cast<const char4 *>(&buf[u]);
+            if (lists) s_list[li * M + w0 + u] = make_int2(jl, buf[u]);
           }
         if (mine > kNbrBuf) {   // rare (small cells): enumerate again for the entries past the buffer
           int u = 0;
@@ -441,8 +438,10 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
                 if (jl == li && n0 == 0 && n1 == 0 && n2 == 0) continue;
                 if (member(q, dx, dy, dz, n0, n1, n2, xj, xi, s_H, R2sq)) {
                   if (u >= kNbrBuf && w0 + u < M) {
+                    const char4 sh = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
                     a.nbr[i * M + w0 + u] = j;
-                    a.shift[i * M + w0 + u] = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
+                    a.shift[i * M + w0 + u] = sh;
+                    if (lists) s_list[li * M + w0 + u] = make_int2(jl, *reinterpret_cast<const int *>(&sh));
                   }
                   ++u;
                 }
@@ -452,7 +451,7 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
       }
       if (lane == 0) {
         a.cnt[i] = count;
-        if (count > M) set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
+        if (count > M) build_flag(a, TERSOFF_STATUS_NBR_OVERFLOW);
         s_m[li] = min(count, M);
       }
       for (int e = count + lane; e < M; e += 32) {
@@ -460,139 +459,112 @@ __global__ void __launch_bounds__(kBuildThreads) build_batch_kernel(const BuildP
         a.shift[i * M + e] = make_char4(0, 0, 0, 0);
       }
     }
-    __syncthreads();
-    long long nb = 0, nq = 0;
-    float mm = 0.f;
-    for (int t = tid; t < nat; t += kBuildThreads) {
-      nb += s_m[t];
-      nq += pair_slots(s_m[t]);
-      mm = fmaxf(mm, (float)s_m[t]);
-    }
-    nb = block_sum_ll(nb, s_red);
-    nq = block_sum_ll(nq, s_red);
-    mm = block_max_f(mm, reinterpret_cast<float *>(s_ired));
-    if (tid == 0) {
-      int *o = a.cfg_tot + 4 * c;
-      o[0] = (int)nb;
-      o[1] = (int)nq;
-      o[2] = (int)mm;
-      o[3] = 0;
-    }
-    __syncthreads();
   }
+  __syncthreads();
 
-  grid_barrier(a.barrier, a.status, a.wait_spins);
-
-  // ---- phase 2: bond CSR, reverse bonds, FP32 bond records, pair cosines
-  long long base_b = 0, base_q = 0;
-  {
-    long long sb = 0, sq = 0;
-    for (int k = tid; k < c_begin; k += kBuildThreads) {   // written by other CTAs: read from L2
-      sb += __ldcg(a.cfg_tot + 4 * k);
-      sq += __ldcg(a.cfg_tot + 4 * k + 1);
+  // ---- phase 2: bond offsets, reverse bonds, FP32 bond records, pair cosines
+  const int64_t base_b = (int64_t)a0 * M, base_q = (int64_t)a0 * pair_slots(M);
+  int nb = 0, nq = 0;
+  for (int cb = 0; cb < nat; cb += kBuildThreads) {
+    const int t = cb + tid;
+    const int m = t < nat ? s_m[t] : 0;
+    int tb, tq;
+    const int xb = block_excl_scan(m, s_ired, tb);
+    const int xq = block_excl_scan(t < nat ? pair_slots(m) : 0, s_ired, tq);
+    if (t < nat) {
+      s_boff[t] = nb + xb;
+      s_poff[t] = nq + xq;
+      s_outer[t] = 0;
     }
-    base_b = block_sum_ll(sb, s_red);
-    base_q = block_sum_ll(sq, s_red);
+    nb += tb;
+    nq += tq;
   }
-  for (int c = c_begin; c < c_end; ++c) {
-    const int a0 = a.atom_off[c], nat = a.atom_off[c + 1] - a0;
-    int nb = 0, nq = 0;
-    for (int cb = 0; cb < nat; cb += kBuildThreads) {
-      const int t = cb + tid;
-      const int m = t < nat ? min(a.cnt[a0 + t], M) : 0;
-      int tb, tq;
-      const int xb = block_excl_scan(m, s_ired, tb);
-      const int xq = block_excl_scan(t < nat ? pair_slots(m) : 0, s_ired, tq);
-      if (t < nat) {
-        s_m[t] = m;
-        s_boff[t] = nb + xb;
-        s_poff[t] = nq + xq;
-        s_outer[t] = 0;
-      }
-      nb += tb;
-      nq += tq;
+  if (tid == 0) {
+    s_boff[nat] = nb;
+    s_poff[nat] = nq;
+  }
+  __syncthreads();
+  for (int t = tid; t < nat; t += kBuildThreads) {
+    a.boff[a0 + t] = (int)(base_b + s_boff[t]);
+    a.poff[a0 + t] = (int)(base_q + s_poff[t]);
+  }
+  // one thread per bond: owner atom, reverse entry (j; i, -n), record
+  for (int bl = tid; bl < nb; bl += kBuildThreads) {
+    int lo = 0, hi = nat;   // last atom t with s_boff[t] <= bl
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_boff[mid] <= bl) lo = mid;
+      else hi = mid;
     }
-    if (tid == 0) {
-      s_boff[nat] = nb;
-      s_poff[nat] = nq;
+    const int il = lo, e = bl - s_boff[il];
+    const int64_t i = a0 + il;
+    int jl;
+    char4 n;
+    if (lists) {
+      const int2 le = s_list[il * M + e];
+      jl = le.x;
+      n = *reinterpret_cast<const char4 *>(&le.y);
+    } else {
+      jl = a.nbr[i * M + e] - a0;
+      n = a.shift[i * M + e];
     }
-    __syncthreads();
-    const bool fits = base_b >= 0 && base_q >= 0 && base_b + nb <= a.bond_cap && base_q + nq <= a.slot_cap;
-    if (!fits && tid == 0) set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
-    for (int t = tid; t <= nat; t += kBuildThreads) {
-      if (t < nat || c == a.C - 1) {
-        a.boff[a0 + t] = (int)(base_b + s_boff[t]);
-        a.poff[a0 + t] = (int)(base_q + s_poff[t]);
+    const int64_t j = a0 + jl;
+    const int mj = s_m[jl];
+    int found = -1;
+    for (int f = 0; f < mj; ++f) {
+      int jf;
+      char4 r;
+      if (lists) {
+        const int2 lf = s_list[jl * M + f];
+        jf = lf.x;
+        r = *reinterpret_cast<const char4 *>(&lf.y);
+      } else {
+        jf = a.nbr[j * M + f] - a0;
+        r = a.shift[j * M + f];
       }
-    }
-    if (fits) {
-      const double *H = s_H;
-      if (tid < 9) s_H[tid] = a.box_in[9 * c + tid];
-      __syncthreads();
-      // one thread per bond: owner atom, reverse entry (j; i, -n), record
-      for (int bl = tid; bl < nb; bl += kBuildThreads) {
-        int lo = 0, hi = nat;   // last atom t with s_boff[t] <= bl
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_boff[mid] <= bl) lo = mid;
-          else hi = mid;
-        }
-        const int il = lo, e = bl - s_boff[il];
-        const int64_t i = a0 + il;
-        const int j = a.nbr[i * M + e];
-        const char4 n = a.shift[i * M + e];
-        const int jl = j - a0;
-        const int mj = s_m[jl];
-        int found = -1;
-        for (int f = 0; f < mj; ++f) {
-          const char4 r = a.shift[(int64_t)j * M + f];
-          if (a.nbr[(int64_t)j * M + f] == (int)i && r.x == -n.x && r.y == -n.y && r.z == -n.z) {
-            found = f;
-            break;
-          }
-        }
-        if (found < 0) {   // the exact test is antisymmetric, so this means an overflowing list
-          set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
-          found = 0;
-        }
-        const int rev = s_boff[jl] + found;
-        a.brev[base_b + bl] = (int)(base_b + rev);
-        const ExactPair p = exact_pair(a.pos_in[3 * (int64_t)j], a.pos_in[3 * (int64_t)j + 1],
-                                       a.pos_in[3 * (int64_t)j + 2], a.pos_in[3 * i], a.pos_in[3 * i + 1],
-                                       a.pos_in[3 * i + 2], H, n.x, n.y, n.z);
-        float4 A, Bv;
-        if (bond_record<float>(p, a.R1, a.R2, rev | (jl << 16), A, Bv)) atomicOr(&s_outer[il], 1);
-        a.gA[base_b + bl] = A;
-        a.gB[base_b + bl] = Bv;
-      }
-      __syncthreads();
-      for (int t = tid; t < nat; t += kBuildThreads) a.outer[a0 + t] = s_outer[t];
-      // one thread per pair slot: cos theta of bonds (e, f), e < f, row-major over e; padding 0
-      for (int ql = tid; ql < nq; ql += kBuildThreads) {
-        int lo = 0, hi = nat;
-        while (hi - lo > 1) {
-          const int mid = (lo + hi) >> 1;
-          if (s_poff[mid] <= ql) lo = mid;
-          else hi = mid;
-        }
-        const int il = lo, m = s_m[il];
-        int e = 0, rem = ql - s_poff[il];
-        while (e < m && rem >= m - 1 - e) {
-          rem -= m - 1 - e;
-          ++e;
-        }
-        float cs = 0.f;
-        if (e < m - 1) {
-          const int f = e + 1 + rem;
-          const float4 ue = a.gA[base_b + s_boff[il] + e], uf = a.gA[base_b + s_boff[il] + f];
-          cs = ue.x * uf.x + ue.y * uf.y + ue.z * uf.z;
-        }
-        a.gcos[base_q + ql] = cs;
+      if (jf == il && r.x == -n.x && r.y == -n.y && r.z == -n.z) {
+        found = f;
+        break;
       }
     }
-    __syncthreads();
-    base_b += nb;
-    base_q += nq;
+    if (found < 0) {   // the exact test is antisymmetric, so this means an overflowing list
+      build_flag(a, TERSOFF_STATUS_NBR_OVERFLOW);
+      found = 0;
+    }
+    const int rev = s_boff[jl] + found;
+    a.brev[base_b + bl] = (int)(base_b + rev);
+    const ExactPair p = exact_pair(a.pos_in[3 * j], a.pos_in[3 * j + 1], a.pos_in[3 * j + 2], a.pos_in[3 * i],
+                                   a.pos_in[3 * i + 1], a.pos_in[3 * i + 2], s_H, n.x, n.y, n.z);
+    float4 A, Bv;
+    if (bond_record<float>(p, a.R1, a.R2, rev | (jl << 16), A, Bv)) atomicOr(&s_outer[il], 1);
+    a.gA[base_b + bl] = A;
+    a.gB[base_b + bl] = Bv;
+    if (lists) s_u[bl] = A;
+  }
+  __syncthreads();
+  for (int t = tid; t < nat; t += kBuildThreads) a.ameta[a0 + t] = s_m[t] | (s_outer[t] ? 0x10000 : 0);
+  // one thread per pair slot: cos theta of bonds (e, f), e < f, row-major over e; padding 0
+  for (int ql = tid; ql < nq; ql += kBuildThreads) {
+    int lo = 0, hi = nat;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (s_poff[mid] <= ql) lo = mid;
+      else hi = mid;
+    }
+    const int il = lo, m = s_m[il];
+    int e = 0, rem = ql - s_poff[il];
+    while (e < m && rem >= m - 1 - e) {
+      rem -= m - 1 - e;
+      ++e;
+    }
+    float cs = 0.f;
+    if (e < m - 1) {
+      const int f = e + 1 + rem;
+      const float4 ue = lists ? s_u[s_boff[il] + e] : a.gA[base_b + s_boff[il] + e];
+      const float4 uf = lists ? s_u[s_boff[il] + f] : a.gA[base_b + s_boff[il] + f];
+      cs = ue.x * uf.x + ue.y * uf.y + ue.z * uf.z;
+    }
+    a.gcos[base_q + ql] = cs;
   }
 }
 
@@ -605,8 +577,6 @@ cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s) {
   a.C = L.C;
   a.M = L.M;
   a.Ntot = L.Ntot;
-  a.bond_cap = L.bond_cap;
-  a.slot_cap = L.slot_cap;
   a.R1 = L.R1;
   a.R2 = L.R2;
   a.atom_off = L.atom_off;
@@ -617,58 +587,40 @@ cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s) {
   a.cnt = L.cnt;
   a.nbr = L.nbr;
   a.shift = L.shift;
-  a.cfg_tot = L.cfg_tot;
   a.boff = L.boff;
   a.poff = L.poff;
   a.brev = L.brev;
   a.gA = L.gA;
   a.gB = L.gB;
   a.gcos = L.gcos;
-  a.outer = L.outer;
-  a.barrier = L.barrier;
-  a.wait_spins = L.wait_spins < 0 ? kGridSpins : (unsigned)std::min<int64_t>(L.wait_spins, 0xffffffffll);
+  a.ameta = L.ameta;
   a.status = L.status;
-  cudaError_t e = cudaMemsetAsync(L.barrier, 0, sizeof(unsigned), s);
-  if (e != cudaSuccess) return e;
-  // every CTA must be resident for the grid barrier: grid = min(C, resident CTAs)
-  const int grid = std::max(1, std::min(L.C, L.resident));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kBuildThreads);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, build_batch_kernel, a);
-  if (e == cudaSuccess) count_launches(1);
-  return e;
+  a.build_status = L.build_status;
+  a.nat_max = std::max(1, L.nat_max);
+  const size_t base = (build_smem_base(a.nat_max) + 15) / 16 * 16;
+  const size_t with_lists = base + build_smem_lists(a.nat_max, L.M);
+  a.lists_in_smem = with_lists <= kBuildSmemCap ? 1 : 0;
+  const size_t smem = a.lists_in_smem ? with_lists : base;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(build_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  build_batch_kernel<<<(unsigned)L.C, kBuildThreads, smem, s>>>(a);
+  return launched(1);
 }
 
-int build_batch_resident() {
-  int dev = 0, nsm = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, build_batch_kernel, kBuildThreads, 0) != cudaSuccess)
-    return 0;
-  return per_sm * nsm;
-}
-
-cudaError_t launch_geometry64(int64_t Ntot, int64_t Btot, int M, const int *atom_cfg, const int *atom_off,
-                              const int *brev, const double *pos, const double *box, const int *cnt,
-                              const int *nbr, const char4 *shift, const int *boff, const int *poff, double R1,
-                              double R2, void *gA, void *gB, void *gcos, int max_slots, cudaStream_t s) {
+cudaError_t launch_geometry64(int64_t Ntot, int M, const int *atom_cfg, const int *atom_off, const int *brev,
+                              const double *pos, const double *box, const int *cnt, const int *nbr,
+                              const char4 *shift, const int *boff, const int *poff, double R1, double R2, void *gA,
+                              void *gB, void *gcos, int max_slots, cudaStream_t s) {
   if (Ntot == 0) return cudaSuccess;
-  if (Btot > 0)
-    geometry_bond_kernel<double><<<nblk(Btot, 256), 256, 0, s>>>(
-        Ntot, (int)Btot, M, atom_cfg, atom_off, brev, pos, box, nbr, shift, boff, R1, R2,
-        static_cast<dvec4 *>(gA), static_cast<dvec4 *>(gB));
+  geometry_bond_kernel<double><<<nblk(Ntot * M, 256), 256, 0, s>>>(
+      Ntot, M, atom_cfg, atom_off, brev, pos, box, cnt, nbr, shift, boff, R1, R2, static_cast<dvec4 *>(gA),
+      static_cast<dvec4 *>(gB));
   if (max_slots > 0)
     geometry_pair_kernel<double><<<nblk(Ntot * max_slots, 256), 256, 0, s>>>(
         Ntot, max_slots, cnt, M, boff, poff, static_cast<const dvec4 *>(gA), static_cast<double *>(gcos));
-  return launched((Btot > 0) + (max_slots > 0));
+  return launched(1 + (max_slots > 0));
 }
 
 cudaError_t preload_geometry64_kernels() {

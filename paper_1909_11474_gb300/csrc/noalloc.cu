@@ -1,7 +1,6 @@
 // noalloc.cu -- tersoff_fitness_static: the fitness call of tersoff_fitness with no device
-// allocation at call time. Its per-call scratch (per-parameter-set constants, the FP64 targets of every
-// configuration, the per-(parameter set, configuration) residual terms and the per-configuration
-// target-norm terms) lives in one file-scope __device__ array of fixed size instead of context buffers
+// allocation at call time. Its per-call scratch (per-parameter-set constants, the per-(parameter set,
+// configuration) residual terms and the per-configuration target-norm terms) lives in one file-scope __device__ array of fixed size instead of context buffers
 // that grow on demand. Everything else it uses is allocated by tersoff_build_neighbors.
 #include <cuda_runtime.h>
 
@@ -71,9 +70,8 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   const size_t b_consts = align256((size_t)P * 8 * sizeof(double));
   const size_t b_part = align256((size_t)P * c.C * tsf::kResidualTerms * sizeof(double));
   const size_t b_dpart = align256((size_t)c.C * 3 * sizeof(double));
-  const size_t b_tew = align256((size_t)c.C * 8 * sizeof(double));
   const size_t b_count = align256(64 * sizeof(int));
-  const size_t need = b_consts + b_part + b_dpart + b_tew + b_count;
+  const size_t need = b_consts + b_part + b_dpart + b_count;
   if (need > kScratchBytes) {
     char buf[200];
     std::snprintf(buf, sizeof(buf), "tersoff_fitness_static needs %zu bytes of scratch for P=%d, C=%d; "
@@ -95,8 +93,8 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
     base = static_cast<unsigned char *>(ptr);
   }
 
-  // every scratch element read by the kernels is written earlier in the same call (constants and
-  // targets by the prep kernel, every (p, c) residual and every configuration's force norm by the
+  // every scratch element read by the kernels is written earlier in the same call (the constants by
+  // the prep kernel, every (p, c) residual term and every configuration's target-norm terms by the
   // batch kernel); the work counters, which must start at zero, are cleared by the launch itself
   tsf::BatchOut o = {};
   o.tE = tg->E;
@@ -106,8 +104,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
   o.consts = base;
   o.part = reinterpret_cast<double *>(base + b_consts);
   o.dpart = reinterpret_cast<double *>(base + b_consts + b_part);
-  o.tEW = reinterpret_cast<double *>(base + b_consts + b_part + b_dpart);
-  o.counters = reinterpret_cast<int *>(base + b_consts + b_part + b_dpart + b_tew);
+  o.counters = reinterpret_cast<int *>(base + b_consts + b_part + b_dpart);
   o.pdl = c.pdl;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (precision == 64) {

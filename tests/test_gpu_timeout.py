@@ -1,11 +1,11 @@
-"""The bounded device-side waits give up, report a timeout and leave the context usable.
+"""The bounded device-side wait gives up, reports a timeout and leaves the context usable.
 
-Two kernels wait on other work: the batched kernel waits for the bulk copies that stage a
-configuration's geometry (an mbarrier), and the fused neighbour build waits at a grid barrier for all
-of its CTAs. tersoff_set_wait_limit bounds both waits in polls; with a bound of 0 the wait gives up
-at its first check. Nothing faults or hangs: the wait returns, the kernel stops early, the status
-word carries TERSOFF_STATUS_TIMEOUT, and the next call with the default bound gives the results of a
-call that never timed out.
+The batched kernel waits for the bulk copies that stage a configuration's geometry (an mbarrier);
+it is the library's only wait on other work (the neighbour build has no cross-CTA wait).
+tersoff_set_wait_limit bounds it in polls; with a bound of 0 the wait gives up at its first check.
+Nothing faults or hangs: the wait returns, the CTA waits (with the built-in bound) for its copies in
+flight and stops, the status word carries TERSOFF_STATUS_TIMEOUT, and the next call with the default
+bound gives the results of a call that never timed out.
 """
 import numpy as np
 import pytest
@@ -50,38 +50,3 @@ def test_staging_wait_that_gives_up_reports_a_timeout(graphs):
     E1, F1, W1 = (x.cpu().numpy() for x in ctx.eval(params))
     assert ctx.get_status() == 0
     assert np.array_equal(Z1, Z0) and np.array_equal(E1, E0) and np.array_equal(F1, F0) and np.array_equal(W1, W0)
-
-
-def test_grid_barrier_that_gives_up_reports_a_timeout_and_a_rebuild_succeeds():
-    """One 512-atom cell and seven 8-atom cells: the CTAs of the small cells reach the build's grid
-    barrier long before the large cell's CTA, so with a bound of 0 they give up."""
-    from paper_1909_11474_gb300 import binding
-    rng = np.random.default_rng(11)
-    pos_list, box_list = [], []
-    for reps in [(4, 4, 4)] + [(1, 1, 1)] * 7:
-        p, b = I.diamond_supercell(reps)
-        pos_list.append(p + rng.normal(0.0, 0.05, p.shape))
-        box_list.append(b)
-    cs = I.pack_configs(pos_list, box_list)
-    pos, box = to_device(cs)
-    ref = binding.Context(0)
-    ref.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
-    ref_lists = ref.export_neighbors()
-
-    ctx = binding.Context(0)
-    ctx.set_wait_limit(0)
-    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)   # queued; its errors come with the next call
-    with pytest.raises(binding.TersoffError) as ei:
-        ctx.build_info()
-    assert ei.value.code == binding.E_TIMEOUT
-    assert ctx.get_status() & binding.STATUS_TIMEOUT
-    with pytest.raises(binding.TersoffError) as ei:       # a failed build leaves no usable state
-        ctx.eval(torch.tensor(I.TABLE2_PARAMS[None, :], device="cuda"))
-    assert ei.value.code == binding.E_STATE
-
-    ctx.set_wait_limit(-1)
-    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
-    ctx.build_info()
-    assert ctx.get_status() == 0
-    for a, b in zip(ctx.export_neighbors(), ref_lists):
-        assert np.array_equal(a, b)

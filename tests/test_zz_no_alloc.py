@@ -61,9 +61,9 @@ def test_fitness_static_matches_the_oracle(precision):
     per-quantity parity bars imply (triangle inequality on sqrt(S_q)), on two calls in a row."""
     ctx, w, t, tg, _ = _setup(P=21, C=5, seed_mask=4)
     wts = (1.0, 0.7, 0.3)
-    E, W, F, ES, WS = oracle.evaluate_batch(w["configs"], w["params"], scales=True)
+    E, W, F, ES, WS, FS = oracle.evaluate_batch(w["configs"], w["params"], scales=True, force_scales=True)
     ref = oracle.fitness_from_predictions(w["configs"], t, E, W, F, w=wts)
-    B = fitness_bounds(w["configs"], t, E, W, F, ES, WS, TOL32 if precision == 32 else TOL64)
+    B = fitness_bounds(w["configs"], t, E, W, F, ES, WS, TOL32 if precision == 32 else TOL64, FS=FS)
     D = ref["D"]
     params = torch.tensor(w["params"], device="cuda")
     for _ in range(2):
@@ -107,8 +107,8 @@ def test_first_static_call_after_a_build_allocates_nothing():
 def test_fitness_static_rejects_requests_beyond_the_static_limit():
     from paper_1909_11474_gb300 import binding
     ctx, w, _, tg, _ = _setup(P=3, C=4, seed_mask=3)
-    P = 40000   # P*8*8 + P*C*64 = 12.8 MB of constants and residual terms > 8 MiB
-    assert P * 64 + P * 4 * 64 > 8 << 20
+    P = 80000   # P*8*8 + P*C*24 = 12.8 MB of constants and residual terms > 8 MiB
+    assert P * 64 + P * 4 * 24 > 8 << 20
     params = torch.tensor(np.tile(w["params"][:1], (P, 1)), device="cuda")
     with pytest.raises(binding.TersoffError) as ei:
         ctx.fitness_static(params, tg)
