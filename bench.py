@@ -35,15 +35,33 @@ METRIC = "atom-evals/sec (E+F+W)"
 UNIT = "atom-evals/s"
 L2_BYTES = 129 * 1024 * 1024
 
-# Algorithmic FP32 operations of one atom evaluation, counted from the formula listing of the
-# batched kernel (FMA = 2 FLOP; SFU transcendentals counted apart as XU ops):
-#   per bond: pair functions 5, bond order + energy terms 20, dU/dd + virial 28, force gather 6
-#   per unordered bond pair: zeta terms 7, dU/dd terms 23
-#   per atom: residual and reductions 16
-FLOP_PER_BOND = 59
-FLOP_PER_PAIR = 30
-FLOP_PER_ATOM = 16
+# Algorithmic operations of one atom evaluation, counted by running the formula listing of the method
+# (site terms of Eq. 2-10, the derivative of the site energy with respect to its bond vectors, the
+# force gather, the virial and the force residual) through an op-counting scalar (oracle/flops.py;
+# tests/test_flop_model.py checks these constants against it). +, -, *, / count 1 FLOP (an FMA 2);
+# exp and log are transcendental (XU) ops. For an atom with m bonds:
+#   FLOP = FLOP_PER_BOND m + FLOP_PER_TRIPLET m (m - 1) + FLOP_PER_ATOM, plus FLOP_PER_CONFIG per
+#   configuration; XU = XU_PER_BOND m.  Diamond (m = 4): 654 FLOP and 24 XU ops per atom-evaluation.
+FLOP_PER_BOND = 50.0
+FLOP_PER_TRIPLET = 37.0
+FLOP_PER_ATOM = 10.0
+FLOP_PER_CONFIG = -2
 XU_PER_BOND = 6
+# The MD-scale call computes the bond geometry every step (bond vector, length, unit vector, pair
+# cosines; its cells have every bond inside R1): 744 FLOP and 28 XU ops per 4-neighbour atom.
+MD_FLOP_PER_BOND = 65.0
+MD_FLOP_PER_TRIPLET = 39.5
+MD_FLOP_PER_ATOM = 10.0
+MD_XU_PER_BOND = 7
+# Algorithmic bytes of the MD-scale call per atom: FP64 positions in, forces out (FP32 or FP64).
+MD_BYTES_IN = 24
+# The parameter gradient as forward-mode dual arithmetic with the six parameter tangents over the same
+# listing (the plain method of Sec. III's loss gradient): 9398 FLOP per 4-neighbour atom-evaluation.
+ADJ_FLOP_PER_BOND = 718.0
+ADJ_FLOP_PER_TRIPLET = 541.0
+ADJ_FLOP_PER_ATOM = 34.0
+ADJ_FLOP_PER_CONFIG = -14
+ADJ_XU_PER_BOND = 6
 
 # ncu summary holding the batched kernel's DRAM bytes per launch, valid while these sources are unchanged
 TRAFFIC_PROFILE = "batch_kernel_ga_fitness_P200_C300.md"
@@ -142,13 +160,14 @@ def profiled_traffic():
 
 
 def flop_model(ctx, P):
-    """Algorithmic FP32 FLOP and XU ops of one fitness evaluation over all (p, c)."""
+    """Algorithmic FLOP and XU ops of one fitness evaluation over all (p, c), and the bond and ordered
+    bond-pair counts of the build."""
     N, B, _ = ctx.build_info()
-    cnt = ctx.export_neighbors()[0].astype(np.int64)
-    pairs = int((cnt * (cnt - 1) // 2).sum())
-    flop = P * (FLOP_PER_BOND * B + FLOP_PER_PAIR * pairs + FLOP_PER_ATOM * N)
+    cnt = np.minimum(ctx.export_neighbors()[0].astype(np.int64), ctx.max_nbr)
+    triplets = int((cnt * (cnt - 1)).sum())
+    flop = P * (FLOP_PER_BOND * B + FLOP_PER_TRIPLET * triplets + FLOP_PER_ATOM * N + FLOP_PER_CONFIG * ctx.C)
     xu = P * XU_PER_BOND * B
-    return flop, xu, B, pairs
+    return flop, xu, B, triplets
 
 
 def run_ours(args):
@@ -181,8 +200,21 @@ def run_ours(args):
           "W": (Wh[0] / natoms[:, None] + torch.tensor(nw, device=dev)).contiguous(),
           "F": (Fh[0] + torch.tensor(nf, device=dev)).contiguous(),
           "mask": torch.full((cs.C,), 7, dtype=torch.uint8, device=dev)}
-    flop, xu, nbonds, npairs = flop_model(ctx, P)
+    flop, xu, nbonds, ntrip = flop_model(ctx, P)
     atom_evals = P * cs.Ntot
+    # arithmetic throughput of this device by the library's microbenchmarks (FFMA, FP64, XU chains)
+    mpeaks = binding.measure_peaks(local)
+    # the library's E/F/W of every (p, c) in FP32 and FP64, compared with the oracle on the CPU baseline's
+    # sample after the timed region
+    want_cpu = rank == 0 and ws == 1 and not args.no_cpu
+    gpu_out = None
+    if want_cpu:
+        gpu_out = {}
+        for prec in (32, 64):
+            E_, F_, W_ = ctx.eval(params, precision=prec)
+            gpu_out[prec] = (E_.cpu().numpy(), F_.double().cpu().numpy(), W_.cpu().numpy())
+        E_, F_, W_ = ctx.eval(torch.tensor(w["hidden"][None, :], device=dev), precision=32)
+        gpu_out["hidden32"] = (E_.cpu().numpy(), F_.double().cpu().numpy(), W_.cpu().numpy())
     stream = torch.cuda.current_stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
     Zbuf = (torch.empty(P, dtype=torch.float64, device=dev), torch.empty((P, 3), dtype=torch.float64, device=dev),
@@ -239,6 +271,8 @@ def run_ours(args):
     n0 = ctx.kernel_launches()
     t_step = timed(step, args.steps)
     launches = ctx.kernel_launches() - n0
+    t_build = timed(lambda: ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16), args.steps)
+    ctx.build_info()                              # the host side of the last build
     ctx.profile(True)                             # CUDA events around the batched kernel alone
     t_fit = timed(fitness_only, args.steps)
     n_kern, ms_kern = ctx.profile_read()
@@ -290,26 +324,38 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+    nsm = props.multi_processor_count
+    fp32_peak = nsm * 128 * 2 * sm_max * 1e6 / 1e12   # TFLOP/s: SMs x FP32 lanes x 2 (FMA) x clock
     achieved = flop / b_time / 1e12
+    xu_rate = xu / b_time / 1e12
+    info = ctx.schedule_info(32)[0]
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(fp32_peak, 3), "unit": "TFLOP/s",
                 "frac": round(achieved / fp32_peak, 4), "traffic": profiled_traffic(),
                 "kernel": "tsf::batch_kernel<{t},4,0,{m},float,{w}> (every cell of the workload has m <= 4; "
                           "variant {how})".format(how="fixed by --schedule" if args.schedule else "chosen by the autotuner",
-                              t=ctx.schedule_info(32)[0]["tile"], w=ctx.schedule_info(32)[0]["warps"],
-                              m=3 if ctx.schedule_info(32)[0]["tile"] == 16 else 2),
+                                                  t=info["tile"], w=info["warps"], m=3 if info["tile"] == 16 else 2),
                 "kernel_ms": round(1e3 * b_time, 4), "flop_per_launch": flop,
-                "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                               f"(sm_max_mhz from MEASURED_PEAKS.json, {peak_src})",
-                "xu_tops_per_s": round(xu / b_time / 1e12, 4),
+                "flop_model": "op-counted formula listing: %g m + %g m(m-1) + %g per atom, %g per config "
+                              "(654 FLOP per 4-neighbour atom)" % (FLOP_PER_BOND, FLOP_PER_TRIPLET, FLOP_PER_ATOM,
+                                                                  FLOP_PER_CONFIG),
+                "peak_source": f"{nsm} SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (sm_max_mhz from "
+                               f"MEASURED_PEAKS.json, {peak_src}); measured FFMA chains "
+                               f"{mpeaks['fp32_fma_flops'] / 1e12:.2f} TFLOP/s",
+                "frac_of_measured_ffma": round(achieved * 1e12 / mpeaks["fp32_fma_flops"], 4),
+                "xu": {"achieved_tops": round(xu_rate, 4), "ops_per_launch": xu,
+                       "peak_tops": round(mpeaks["xu_ex2_ops"] / 1e12, 3),
+                       "frac": round(xu_rate * 1e12 / mpeaks["xu_ex2_ops"], 4),
+                       "peak_source": "measured ex2.approx chains (32 per SM per clock on this device)"},
                 "fitness_call_frac": round(flop / k_time / 1e12 / fp32_peak, 4)}
+    measured = {k: round(v / 1e12, 4) for k, v in mpeaks.items()}
+    measured["unit"] = "T op/s (FLOP/s for the FMA kinds)"
 
     out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "GA fitness batch: P=200 parameter sets x C=300 periodic 64-atom diamond Si "
                                   "cells (strain +-2%, sigma=0.1 A), neighbour build + geometry + E/F/W + Z per step",
-                      "P": P, "C": cs.C, "atoms": cs.Ntot, "bonds": nbonds, "bond_pairs": npairs,
+                      "P": P, "C": cs.C, "atoms": cs.Ntot, "bonds": nbonds, "ordered_bond_pairs": ntrip,
                       "precision": "FP32 pair math, FP64 reductions", "l2": "flushed between timed steps",
                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
            "fitness_evals_per_s": round(ws * P * args.steps / t_step, 1),
@@ -318,7 +364,9 @@ def run_ours(args):
                             "note": "per GA generation after the first: geometry cache resident"},
            "e2e": {"value": round(ws * atom_evals * args.steps / t_e2e, 1), "unit": UNIT,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-           "gpu_launches": int(launches), "roofline": roofline, "clocks": clocks,
+           "build_only": {"ms": round(1e3 * t_build / args.steps, 4),
+                          "note": "neighbour build and FP32 geometry of the 300 cells, counts read back beside it"},
+           "gpu_launches": int(launches), "roofline": roofline, "measured_peaks": measured, "clocks": clocks,
            "autotune": {"candidates": tuned_tried, "tuned_launch_ms": None if args.schedule else round(tuned_ms, 4),
                         "schedule": ctx.schedule_info(32)}}
     if not args.quick:
@@ -336,14 +384,27 @@ def run_ours(args):
         if unknown:
             raise SystemExit(f"unknown rows {unknown}; choose from {list(rows)}")
         out["rows"] = {r: rows[r]() for r in pick}
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        out["cpu_baseline"] = cpu_baseline(w, tg_host={k: v.cpu().numpy() for k, v in tg.items()},
-                                           budget_s=args.cpu_seconds)
+    if want_cpu:
+        out["cpu_baseline"], out["error_vs_oracle"] = cpu_baseline(w, gpu_out, budget_s=args.cpu_seconds)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _fp32_peak(dev):
+    """Nominal FP32 peak (TFLOP/s): SMs x 128 lanes x 2 (FMA) x sm_max_mhz of MEASURED_PEAKS.json."""
+    import torch
+    peaks, _ = measured_peaks()
+    return torch.cuda.get_device_properties(dev).multi_processor_count * 128 * 2 * \
+        float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def _counts(cnt, M):
+    """Bonds kept, ordered bond pairs and atoms of neighbour counts cnt (lists cut at M entries)."""
+    m = np.minimum(np.asarray(cnt, dtype=np.int64), M)
+    return int(m.sum()), int((m * (m - 1)).sum()), len(m)
 
 
 def _time(fn, k, flush, stream, warmup=2):
@@ -388,9 +449,18 @@ def bench_adjoint(ctx_dev, steps, flush, stream):
     t = _time(lambda: ctx.param_grad(params, tg), steps, flush, stream)
     tf = _time(lambda: ctx.fitness(params, tg), steps, flush, stream)
     P = len(w["params"])
+    B, T, N = _counts(ctx.export_neighbors()[0], ctx.max_nbr)
+    flop = P * (ADJ_FLOP_PER_BOND * B + ADJ_FLOP_PER_TRIPLET * T + ADJ_FLOP_PER_ATOM * N + ADJ_FLOP_PER_CONFIG * cs.C)
+    peak = _fp32_peak(ctx_dev)
     return {"workload": "P=64 x C=100 64-atom cells, dL/dx over 6 parameters", "ms": round(1e3 * t, 4),
             "value": round(P * cs.Ntot / t, 1), "unit": "atom-evals/s (forward + 6-parameter gradient)",
-            "gradients_per_s": round(P / t, 1), "cost_vs_fitness": round(t / tf, 2)}
+            "gradients_per_s": round(P / t, 1), "cost_vs_fitness": round(t / tf, 2),
+            "roofline": {"bound": "alu", "achieved": round(flop / t / 1e12, 3), "peak": round(peak, 3),
+                         "unit": "TFLOP/s", "frac": round(flop / t / 1e12 / peak, 4), "flop_per_call": flop,
+                         "flop_model": "forward-mode dual arithmetic (six tangents) over the op-counted listing: "
+                                       "%g m + %g m(m-1) + %g per atom" % (ADJ_FLOP_PER_BOND, ADJ_FLOP_PER_TRIPLET,
+                                                                           ADJ_FLOP_PER_ATOM),
+                         "timed": "whole call (preparation, forward and tangent passes, finalize)"}}
 
 
 def bench_plain(ctx, params, tg, dev, cs, flush, stream, t_fit32):
@@ -564,69 +634,181 @@ def bench_md(dev, flush, stream, steps):
 
     tn = _time(nve, max(2, steps // 2), flush, stream, warmup=1)
     Et = (nve_out[0] + nve_out[1]).cpu().numpy()
+    ctx.md_force(pos, cs.box[0], w["params"][0], precision=32, out=out32)
+    B, T, _ = _counts(ctx.md_export_neighbors()[0], ctx.md_M)
+    flop = MD_FLOP_PER_BOND * B + MD_FLOP_PER_TRIPLET * T + MD_FLOP_PER_ATOM * N
+    peaks, peak_src = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    fp32 = _fp32_peak(dev)
+
+    def roof(t, fbytes):
+        byt = N * (MD_BYTES_IN + fbytes)
+        return {"fp32": {"achieved": round(flop / t / 1e12, 3), "peak": round(fp32, 3), "unit": "TFLOP/s",
+                         "frac": round(flop / t / 1e12 / fp32, 4)},
+                "hbm": {"achieved": round(byt / t / 1e9, 1), "peak": hbm, "unit": "GB/s",
+                        "frac": round(byt / t / 1e9 / hbm, 4), "bytes_per_call": byt}}
     return {"workload": "40^3 conventional cells = 512,000 atoms, sigma = 0.08 A", "unit": "atom-steps/s",
-            "fp32": {"value": round(N / t32, 1), "ms": round(1e3 * t32, 4)},
-            "fp64": {"value": round(N / t64, 1), "ms": round(1e3 * t64, 4)},
+            "fp32": {"value": round(N / t32, 1), "ms": round(1e3 * t32, 4), "roofline": roof(t32, 12)},
+            "fp64": {"value": round(N / t64, 1), "ms": round(1e3 * t64, 4), "roofline": roof(t64, 24)},
+            "roofline_model": {"flop_per_call": flop, "bonds": B, "ordered_bond_pairs": T,
+                               "flop": "op-counted listing with the bond geometry computed in the call: "
+                                       "%g m + %g m(m-1) + %g per atom" % (MD_FLOP_PER_BOND, MD_FLOP_PER_TRIPLET,
+                                                                           MD_FLOP_PER_ATOM),
+                               "bytes": "algorithmic: FP64 positions in (24 B) and forces out (12 B FP32, "
+                                        "24 B FP64) per atom; HBM peak %s (MEASURED_PEAKS.json)" % peak_src},
             "nve_fp32": {"steps_per_call": nst, "dt_fs": 1.0, "T0_K": 300.0,
                          "value": round(N * nst / tn, 1), "ms_per_step": round(1e3 * tn / nst, 4),
                          "max_energy_deviation_eV_per_atom": float(np.abs(Et - Et[0]).max() / N),
                          "note": "one extra force call at the start of each call is included"}}
 
 
-def cpu_baseline(w, tg_host, budget_s=15.0):
-    """The FP64 oracle (as it stands) on the host cores, on a bounded sample of the same workload:
-    all P parameter sets on the first configurations, until the time budget is spent."""
-    import torch
+def host_cores():
+    """Host cores this process may run on, and the CPU model (lscpu, else /proc/cpuinfo)."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except AttributeError:
+        n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    return n, model or "unknown"
 
+
+def _oracle_worker_init():
+    import torch
+    torch.set_num_threads(1)                       # one core per worker process
+
+
+def _oracle_job(job):
+    """Evaluate (p, c, pos, box, x) items with the FP64 oracle: (p, c, E, W, F, E_scale, W_scale, F_scale)
+    each (the scales are the summed magnitudes of the terms of E, W and each atom's force)."""
     import oracle
+    out = []
+    for p, c, pos, box, x in job:
+        r = oracle.evaluate(pos, box, x)
+        out.append((p, c, r["E"], r["W"], r["F"], r["E_scale"], r["W_scale"], r["F_scale"]))
+    return out
+
+
+class OraclePool:
+    """The oracle (as it stands) on every host core: one spawned worker process per core, each with one
+    thread, over (parameter set, configuration) items; spawned, not forked, because CUDA is initialised
+    in the parent."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.cores, self.model = host_cores()
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init)
+
+    def run(self, items, chunk=8):
+        jobs = [items[k:k + chunk] for k in range(0, len(items), chunk)]
+        t0 = time.perf_counter()
+        res = [r for part in self.pool.map(_oracle_job, jobs, chunksize=1) for r in part]
+        return res, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _items(w, pairs, hidden=False):
+    cs = w["configs"]
+    out = []
+    for p, c in pairs:
+        pos, box = cs.config(c)
+        out.append((p, c, pos, box, w["hidden"] if hidden else w["params"][p]))
+    return out
+
+
+def cpu_baseline(w, gpu_out, budget_s=15.0):
+    """The FP64 oracle on all host cores over a bounded, seeded sample of the workload's (p, c) items
+    (sized from a calibration round to about budget_s of wall time), and the error of the library's
+    FP32 and FP64 E/F/W against it on that sample."""
     cs = w["configs"]
     P = len(w["params"])
-    t0 = time.time()
-    atoms = 0
-    pairs_done = 0
-    c = 0
-    while time.time() - t0 < budget_s and c < cs.C:
-        for p in range(P):
-            pos, box = cs.config(c)
-            oracle.evaluate(pos, box, w["params"][p])
-            atoms += len(pos)
-            pairs_done += 1
-            if time.time() - t0 >= budget_s:
-                break
-        c += 1
-    dt = time.time() - t0
-    return {"value": round(atoms / dt, 1), "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{pairs_done} (parameter set, 64-atom cell) evaluations of the same workload, "
-                      f"{dt:.1f} s, FP64 torch CPU with autograd forces/virial"}
+    pool = OraclePool()
+    try:
+        rng = np.random.default_rng(20191125)
+        order = [(int(k) % P, int(k) // P) for k in rng.permutation(P * cs.C)]
+        pool.run(_items(w, order[:pool.cores]), chunk=1)                 # start-up: imports in every worker
+        _, t_cal = pool.run(_items(w, order[:4 * pool.cores]), chunk=4)
+        n = int(min(len(order), max(pool.cores, 4 * pool.cores * budget_s / max(t_cal, 1e-3))))
+        res, dt = pool.run(_items(w, order[:n]))
+        hidden_pairs = [(0, c) for c in range(min(cs.C, pool.cores))]
+        res_h, _ = pool.run(_items(w, hidden_pairs, hidden=True), chunk=1)
+    finally:
+        pool.close()
+    atoms = sum(int(cs.natoms[c]) for _, c, *_ in res)
+    base = {"value": round(atoms / dt, 1), "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "cpu": pool.model,
+            "sample": f"{n} seeded (parameter set, 64-atom cell) evaluations of the same workload in {dt:.1f} s, "
+                      f"FP64 torch CPU with autograd forces/virial, one worker process per core"}
+    err = {}
+    FLOOR = 0.1
+    for prec in (32, 64):
+        E, F, W = gpu_out[prec]
+        e_rel = w_rel = f_abs = f_scl = 0.0
+        for p, c, Er, Wr, Fr, ES, WS, FS in res:
+            a = int(cs.atom_off[c])
+            e_rel = max(e_rel, abs(E[p, c] - Er) / max(abs(Er), FLOOR * ES))
+            w_rel = max(w_rel, float(np.linalg.norm(W[p, c] - Wr) / max(np.linalg.norm(Wr), FLOOR * WS)))
+            dF = np.abs(F[p, a:a + len(Fr)] - Fr)
+            f_abs = max(f_abs, float(dF.max()))
+            mag = np.maximum(np.abs(Fr).max(-1), FLOOR * FS)
+            f_scl = max(f_scl, float((dF.max(-1) / np.maximum(1.0, mag / 10.0)).max()))
+        err[f"fp{prec}"] = {"E_rel_max": e_rel, "W_rel_max": w_rel, "F_abs_max_eV_per_A": f_abs,
+                            "F_scaled_max": f_scl}
+    E, F, W = gpu_out["hidden32"]
+    f_h = e_h = 0.0
+    for _, c, Er, Wr, Fr, ES, WS, FS in res_h:
+        a = int(cs.atom_off[c])
+        f_h = max(f_h, float(np.abs(F[0, a:a + len(Fr)] - Fr).max()))
+        e_h = max(e_h, abs(E[0, c] - Er) / abs(Er))
+    err["fp32_table2_parameters"] = {"E_rel_max": e_h, "F_abs_max_eV_per_A": f_h, "configs": len(res_h)}
+    err["sample"] = f"{n} seeded (p, c) items of the workload ({len(res_h)} cells at the Table 2 parameters)"
+    err["bars"] = {"E_rel": 1e-5, "W_rel": 1e-5, "F_abs_eV_per_A": 1e-4, "F_scaled": 1e-4,
+                   "reading": "E and W relative to max(|X|, 0.1 x the summed magnitudes of their terms); "
+                              "F_scaled = |dF_i| / max(1, max(|F_i|, 0.1 x the summed magnitudes of atom i's "
+                              "bond terms) / 10 eV/A), so 1e-4 eV/A absolute up to 10 eV/A and 1e-5 relative "
+                              "above; F_abs against 1e-4 applies to the Table 2 parameters (physical forces)"}
+    return base, err
 
 
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return
-    import torch
-
-    import oracle
     from paper_1909_11474_gb300 import inputs as I
     w = I.workload_ga_batch(P=args.P, C=args.C)
     cs = w["configs"]
     P = len(w["params"])
     n_pairs = max(1, int(args.ref_pairs))
     order = [(p, c) for c in range(cs.C) for p in range(P)]
+    pool = OraclePool()
     times = []
-    k = 0
-    for s in range(args.warmup + args.steps):
-        t0 = time.time()
-        atoms = 0
-        for _ in range(n_pairs):
-            p, c = order[k % len(order)]
-            k += 1
-            pos, box = cs.config(c)
-            oracle.evaluate(pos, box, w["params"][p])
-            atoms += len(pos)
-        dt = time.time() - t0
-        if s >= args.warmup:
-            times.append((atoms, dt))
+    try:
+        pool.run(_items(w, order[:pool.cores]), chunk=1)       # start-up: imports in every worker
+        k = 0
+        for s in range(args.warmup + args.steps):
+            pairs = [order[(k + q) % len(order)] for q in range(n_pairs)]
+            k += n_pairs
+            res, dt = pool.run(_items(w, pairs))
+            if s >= args.warmup:
+                times.append((sum(int(cs.natoms[c]) for _, c, *_ in res), dt))
+    finally:
+        pool.close()
     atoms = sum(a for a, _ in times)
     dt = sum(t for _, t in times)
     v = atoms / dt
@@ -635,8 +817,10 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": "GA fitness batch: P=200 x C=300 64-atom cells; each step a bounded sample "
                                   f"of {n_pairs} (parameter set, cell) evaluations", "P": P, "C": cs.C},
-           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-                            "sample": f"{n_pairs} (parameter set, 64-atom cell) evaluations per step"},
+           "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+                            "cpu": pool.model,
+                            "sample": f"{n_pairs} (parameter set, 64-atom cell) evaluations per step, one "
+                                      "worker process per core"},
            "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -651,7 +835,7 @@ def main():
     ap.add_argument("--C", type=int, default=300)
     ap.add_argument("--soak", type=float, default=2.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-pairs", type=int, default=200)
+    ap.add_argument("--ref-pairs", type=int, default=800)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main step only (no per-row measurements)")
     ap.add_argument("--rows", default="", help="comma-separated subset of the extra rows (default: all)")

@@ -238,26 +238,31 @@ def _energy_graph(prep: _Prepared, params: torch.Tensor, R1, R2, create_graph=Fa
     W6 = torch.stack([Wm[0, 0], Wm[1, 1], Wm[2, 2], Wm[0, 1], Wm[1, 2], Wm[2, 0]])
     # magnitude of the summands of W = -sum_bonds dU/dd (x) d (conditioning scale, diagnostics only)
     wscale = (gd.detach().norm(dim=1) * d.detach().norm(dim=1)).sum()
-    return U, Ui, F, W6, Wm, scale.detach(), wscale
+    # per atom: summed magnitudes of the bond terms of its force, F_i = sum_{e from i} g_e - sum_{e to i} g_e
+    # (g_e = dU/dd_e), the conditioning scale of that sum (diagnostics only)
+    gn = gd.detach().norm(dim=1)
+    fscale = torch.zeros(prep.N, dtype=_F64).index_add(0, prep.owner, gn).index_add(0, prep.j, gn)
+    return U, Ui, F, W6, Wm, scale.detach(), wscale, fscale
 
 
 def evaluate(pos, box, params, R1: float = R1_DEFAULT, R2: float = R2_DEFAULT, prep=None):
     """E (eV, total), F [N][3] (eV/A), W [6] (eV, total; xx, yy, zz, xy, yz, zx), W3 [3][3], U_i [N]."""
     prep = prep or _Prepared(pos, box, R2)
     p = torch.as_tensor(np.asarray(params, dtype=np.float64))
-    U, Ui, F, W6, Wm, es, ws = _energy_graph(prep, p, R1, R2)
+    U, Ui, F, W6, Wm, es, ws, fs = _energy_graph(prep, p, R1, R2)
     return {"E": float(U.detach()), "F": F.detach().numpy(), "W": W6.detach().numpy(),
             "W3": Wm.detach().numpy(), "Ui": Ui.detach().numpy(),
-            "E_scale": float(es), "W_scale": float(ws)}
+            "E_scale": float(es), "W_scale": float(ws), "F_scale": fs.numpy()}
 
 
 def evaluate_batch(configs, params, R1: float = R1_DEFAULT, R2: float = R2_DEFAULT, pairs=None,
-                   scales: bool = False):
+                   scales: bool = False, force_scales: bool = False):
     """E [P][C], W [P][C][6], F [P][Ntot][3] for every (parameter set p, configuration c).
 
     `pairs` optionally restricts the work to a list of (p, c); other entries are left NaN.
     With scales=True also returns ES [P][C], WS [P][C]: the summed magnitudes of the summands of E
-    and of W, the conditioning scales of the two sums.
+    and of W, the conditioning scales of the two sums; with force_scales=True also FS [P][Ntot], the
+    summed magnitudes of the bond terms of each atom's force.
     """
     params = np.atleast_2d(np.asarray(params, dtype=np.float64))
     P, C = len(params), configs.C
@@ -266,6 +271,7 @@ def evaluate_batch(configs, params, R1: float = R1_DEFAULT, R2: float = R2_DEFAU
     F = np.full((P, configs.Ntot, 3), np.nan)
     ES = np.full((P, C), np.nan)
     WS = np.full((P, C), np.nan)
+    FS = np.full((P, configs.Ntot), np.nan)
     todo = {}
     for p, c in (pairs if pairs is not None else [(p, c) for c in range(C) for p in range(P)]):
         todo.setdefault(c, []).append(p)
@@ -280,6 +286,9 @@ def evaluate_batch(configs, params, R1: float = R1_DEFAULT, R2: float = R2_DEFAU
             F[p, a:a + len(pos)] = r["F"]
             ES[p, c] = r["E_scale"]
             WS[p, c] = r["W_scale"]
+            FS[p, a:a + len(pos)] = r["F_scale"]
+    if scales and force_scales:
+        return E, W, F, ES, WS, FS
     if scales:
         return E, W, F, ES, WS
     return E, W, F
@@ -364,7 +373,7 @@ def loss_and_grad(configs, params_row, targets, w=(1.0, 1.0, 1.0), loss: str = "
         N = len(pos)
         prep = _Prepared(pos, box, R2)
         need_graph = bool(mask[c] & 6)
-        U, _, F, W6, _, _, _ = _energy_graph(prep, p, R1, R2, create_graph=need_graph)
+        U, _, F, W6, _, _, _, _ = _energy_graph(prep, p, R1, R2, create_graph=need_graph)
         if mask[c] & 1:
             S[0] = S[0] + (U / N - float(targets["E"][c])) ** 2
         if mask[c] & 2:

@@ -77,11 +77,11 @@ def _compare_eval(ctx, cs, params, precision, tol):
     E, F, W = ctx.eval(pt, precision=precision)
     torch.cuda.synchronize()
     assert ctx.get_status() == 0
-    Er, Wr, Fr, ES, WS = oracle.evaluate_batch(cs, params, scales=True)
+    Er, Wr, Fr, ES, WS, FS = oracle.evaluate_batch(cs, params, scales=True, force_scales=True)
     E, F, W = E.cpu().numpy(), F.cpu().double().numpy(), W.cpu().numpy()
     eE = energy_rel_err(E, Er, ES).max()
     eW = virial_rel_err(W, Wr, WS).max()
-    eF = force_err(F, Fr)
+    eF = force_err(F, Fr, FS)
     assert eE < tol["E"], eE
     assert eW < tol["W"], eW
     assert eF < tol["F"], eF
@@ -137,13 +137,13 @@ def test_fitness_matches_oracle(ctx, precision):
     t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0],
                        mask=np.array([7, 3, 5, 6, 1], np.uint8))
     wts = (1.0, 0.7, 0.3)
-    E, W, F, ES, WS = oracle.evaluate_batch(cs, w["params"], scales=True)
+    E, W, F, ES, WS, FS = oracle.evaluate_batch(cs, w["params"], scales=True, force_scales=True)
     ref = oracle.fitness_from_predictions(cs, t, E, W, F, w=wts)
     _build(ctx, cs)
     Z, Zq, S = ctx.fitness(torch.tensor(w["params"], device="cuda"), targets_to_device(t),
                            w=wts, precision=precision)
     Z, Zq, S = Z.cpu().numpy(), Zq.cpu().numpy(), S.cpu().numpy()
-    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32 if precision == 32 else TOL64)
+    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32 if precision == 32 else TOL64, FS=FS)
     D = ref["D"]
     assert (np.abs(np.sqrt(S) - np.sqrt(ref["S"])) <= B).all()
     assert (np.abs(Zq - ref["Zq"]) <= B / np.sqrt(D)[None, :]).all()
@@ -179,11 +179,11 @@ def test_plain_fp64_path(ctx, which):
     Eb, Fb, Wb = ctx.eval(pt, precision=64)
     torch.cuda.synchronize()
     assert ctx.get_status() == 0
-    Er, Wr, Fr, ES, WS = oracle.evaluate_batch(cs, params, scales=True)
+    Er, Wr, Fr, ES, WS, FS = oracle.evaluate_batch(cs, params, scales=True, force_scales=True)
     E, F, W = E.cpu().numpy(), F.cpu().numpy(), W.cpu().numpy()
     assert energy_rel_err(E, Er, ES).max() < TOL64["E"]
     assert virial_rel_err(W, Wr, WS).max() < TOL64["W"]
-    assert force_err(F, Fr) < TOL64["F"]
+    assert force_err(F, Fr, FS) < TOL64["F"]
     assert np.allclose(E, Eb.cpu().numpy(), rtol=1e-12, atol=1e-12)
     assert np.allclose(F, Fb.cpu().numpy(), rtol=1e-10, atol=1e-11)
 
@@ -280,9 +280,9 @@ def test_autotune_keeps_results_within_the_bars(ctx):
     cs = w["configs"]
     Eh, Wh, Fh = oracle.evaluate_batch(cs, w["hidden"][None, :])
     t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0])
-    E, W, F, ES, WS = oracle.evaluate_batch(cs, w["params"], scales=True)
+    E, W, F, ES, WS, FS = oracle.evaluate_batch(cs, w["params"], scales=True, force_scales=True)
     ref = oracle.fitness_from_predictions(cs, t, E, W, F)
-    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32)
+    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32, FS=FS)
     _build(ctx, cs)
     params, tg = torch.tensor(w["params"], device="cuda"), targets_to_device(t)
     ms, tried = ctx.autotune(params, tg, reps=2)
@@ -303,9 +303,9 @@ def test_every_schedule_meets_the_oracle_bars(ctx, P, tile, warps, items, narrow
     cs = w["configs"]
     Eh, Wh, Fh = oracle.evaluate_batch(cs, w["hidden"][None, :])
     t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0])
-    E, W, F, ES, WS = oracle.evaluate_batch(cs, w["params"], scales=True)
+    E, W, F, ES, WS, FS = oracle.evaluate_batch(cs, w["params"], scales=True, force_scales=True)
     ref = oracle.fitness_from_predictions(cs, t, E, W, F)
-    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32)
+    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32, FS=FS)
     _build(ctx, cs)
     ctx.set_schedule(P, tile=tile, items_per_config=items, narrow=bool(narrow), warps=warps)
     Z, Zq, S = ctx.fitness(torch.tensor(w["params"], device="cuda"), targets_to_device(t))

@@ -47,11 +47,11 @@ def _compare(ctx, cs, params, precision):
     E, F, W = ctx.eval(torch.tensor(params, device="cuda"), precision=precision)
     torch.cuda.synchronize()
     assert ctx.get_status() == 0
-    Er, Wr, Fr, ES, WS = oracle.evaluate_batch(cs, params, scales=True)
+    Er, Wr, Fr, ES, WS, FS = oracle.evaluate_batch(cs, params, scales=True, force_scales=True)
     E, F, W = E.cpu().numpy(), F.cpu().double().numpy(), W.cpu().numpy()
     assert energy_rel_err(E, Er, ES).max() < tol["E"]
     assert virial_rel_err(W, Wr, WS).max() < tol["W"]
-    assert force_err(F, Fr) < tol["F"]
+    assert force_err(F, Fr, FS) < tol["F"]
 
 
 @pytest.mark.parametrize("precision", [32, 64])
@@ -75,13 +75,13 @@ def test_tersoff_form_fitness_matches_oracle(ctx):
     t = I.with_targets(w, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0],
                        mask=np.array([7, 3, 5, 6, 1], np.uint8))
     wts = (1.0, 0.7, 0.3)
-    E, W, F, ES, WS = oracle.evaluate_batch(cs, x, scales=True)
+    E, W, F, ES, WS, FS = oracle.evaluate_batch(cs, x, scales=True, force_scales=True)
     ref = oracle.fitness_from_predictions(cs, t, E, W, F, w=wts)
     pos, box = to_device(cs)
     ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
     Z, Zq, S = ctx.fitness(torch.tensor(x, device="cuda"), targets_to_device(t), w=wts, precision=32)
     Z, Zq, S = Z.cpu().numpy(), Zq.cpu().numpy(), S.cpu().numpy()
-    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32)
+    B = fitness_bounds(cs, t, E, W, F, ES, WS, TOL32, FS=FS)
     D = ref["D"]
     assert (np.abs(np.sqrt(S) - np.sqrt(ref["S"])) <= B).all()
     assert (np.abs(Z - ref["Z"]) <= (np.asarray(wts)[None, :] * B / np.sqrt(D)[None, :]).sum(-1)).all()

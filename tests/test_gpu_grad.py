@@ -34,9 +34,9 @@ def _setup(P, C, masks, near=None):
 
 def _loss_bound(cs, t, params, loss):
     """|dL| implied by the per-quantity parity bars: |d sqrt(S_q)| <= B_q (triangle inequality)."""
-    E, W, F, ES, WS = oracle.evaluate_batch(cs, params, scales=True)
+    E, W, F, ES, WS, FS = oracle.evaluate_batch(cs, params, scales=True, force_scales=True)
     ref = oracle.fitness_from_predictions(cs, t, E, W, F, w=WTS)
-    B = fitness_bounds(cs, t, E, W, F, ES, WS)
+    B = fitness_bounds(cs, t, E, W, F, ES, WS, FS=FS)
     D = ref["D"]
     rs = np.sqrt(ref["S"])
     w = np.asarray(WTS)[None, :]

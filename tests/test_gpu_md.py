@@ -61,7 +61,7 @@ def test_md_energy_forces_virial(ctx, precision, case):
     tol = TOL32 if precision == 32 else TOL64
     assert energy_rel_err(np.array([E]), np.array([r["E"]]), np.array([r["E_scale"]])).max() < tol["E"]
     assert virial_rel_err(W[None], r["W"][None], np.array([r["W_scale"]])).max() < tol["W"]
-    assert force_err(F, r["F"]) < tol["F"]
+    assert force_err(F, r["F"], r["F_scale"]) < tol["F"]
 
 
 def _cutout_force(pos, box, i, R2=3.2, pad=0.3):

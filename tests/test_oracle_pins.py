@@ -428,3 +428,18 @@ def test_neighbor_subset_matches_full_list():
     for i, (j, n) in zip(atoms, sub):
         e = slice(full["off"][i], full["off"][i + 1])
         assert np.array_equal(j, full["j"][e]) and np.array_equal(n, full["n"][e])
+
+
+def test_force_term_scale_dimer_and_triangle_inequality():
+    """The per-atom conditioning scale of the force bar, S_F,i = sum of |dU/dd| over the bonds from and to
+    atom i: for a dimer (zeta = 0, the two bond terms opposite and equal) it equals |F_i|; in any cell
+    it bounds |F_i| from above (triangle inequality), with equality nowhere guaranteed."""
+    x = I.TABLE2_PARAMS
+    pos = np.array([[0.0, 0.0, 0.0], [2.45, 0.0, 0.0]])
+    r = oracle.evaluate(pos, np.eye(3) * 20.0, x)
+    assert np.allclose(r["F_scale"], np.linalg.norm(r["F"], axis=1), rtol=1e-13, atol=0.0)
+    rng = np.random.default_rng(21)
+    p, b = I.diamond_supercell((1, 1, 1))
+    r = oracle.evaluate(p + rng.normal(0.0, 0.15, p.shape), b, x)
+    assert (r["F_scale"] >= np.linalg.norm(r["F"], axis=1) - 1e-12).all()
+    assert (r["F_scale"] > 1.5 * np.linalg.norm(r["F"], axis=1)).any()
