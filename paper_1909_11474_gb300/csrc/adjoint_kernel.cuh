@@ -277,16 +277,17 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
     const int4 at = sld(&satom[li], 12);
     const int m = at.z, lb = at.x;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f;
-    for (int e = 0; e < m; ++e) {
-      const float *st = stage + (size_t)(lb + e) * 3 * PT + pl;
-      Fx += sld(&st[0], 13);
-      Fy += sld(&st[PT], 13);
-      Fz += sld(&st[2 * PT], 13);
+    for (int e = 0; e < m; ++e) {   // the stage rows written by atom_forward (its layout: stage_store)
+      float x, y, z;
+      stage_load<PT, float>(stage, lb + e, pl, x, y, z, 13);
+      Fx += x;
+      Fy += y;
+      Fz += z;
       const int rb = __float_as_int(sld(&sB[lb + e].w, 14)) & 0xffff;
-      const float *sr = stage + (size_t)(rb + rec.cb0 - B0) * 3 * PT + pl;
-      Fx -= sld(&sr[0], 15);
-      Fy -= sld(&sr[PT], 15);
-      Fz -= sld(&sr[2 * PT], 15);
+      stage_load<PT, float>(stage, rb + rec.cb0 - B0, pl, x, y, z, 15);
+      Fx -= x;
+      Fy -= y;
+      Fz -= z;
     }
     sF2 += Fx * Fx + Fy * Fy + Fz * Fz;
     float vx = 0.f, vy = 0.f, vz = 0.f;

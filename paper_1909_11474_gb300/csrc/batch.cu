@@ -75,6 +75,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.boff = ctx.boff.as<int>();
   bp.poff = ctx.poff.as<int>();
   bp.ameta = ctx.ameta.as<int>();
+  bp.arev = ctx.arev.as<int4>();
   bp.gA = f64 ? ctx.gA64.p : ctx.gA32.p;
   bp.gB = f64 ? ctx.gB64.p : ctx.gB32.p;
   bp.gcos = f64 ? ctx.gcos64.p : ctx.gcos32.p;

@@ -119,6 +119,40 @@ __host__ __device__ constexpr int stage_stride() {
   return PT == 8 ? 26 : PT == 16 ? 52 : 3 * PT;
 }
 
+// Layout of one stage row (bond b, PT parameter sets). FP32 rows of 32 parameter sets hold the (x, y)
+// components as 32 float2 followed by the 32 z components, so that a warp stores and loads a row with
+// one 64-bit and one 32-bit access (each conflict-free); other rows hold x, y and z as three runs of PT.
+template <int PT, typename R>
+__host__ __device__ constexpr bool stage_packed() {
+  return PT == 32 && sizeof(R) == 4;
+}
+template <int PT, typename R>
+__device__ __forceinline__ void stage_store(R *stage, int row, int pl, R x, R y, R z) {
+  R *st = stage + (size_t)row * stage_stride<PT>();
+  if constexpr (stage_packed<PT, R>()) {
+    sst(reinterpret_cast<float2 *>(st) + pl, make_float2(x, y), 5);
+    sst(&st[2 * PT + pl], z, 5);
+  } else {
+    sst(&st[pl], x, 5);
+    sst(&st[PT + pl], y, 5);
+    sst(&st[2 * PT + pl], z, 5);
+  }
+}
+template <int PT, typename R>
+__device__ __forceinline__ void stage_load(const R *stage, int row, int pl, R &x, R &y, R &z, int site) {
+  const R *st = stage + (size_t)row * stage_stride<PT>();
+  if constexpr (stage_packed<PT, R>()) {
+    const float2 v = sld(reinterpret_cast<const float2 *>(st) + pl, site);
+    x = v.x;
+    y = v.y;
+    z = sld(&st[2 * PT + pl], site);
+  } else {
+    x = sld(&st[pl], site);
+    y = sld(&st[PT + pl], site);
+    z = sld(&st[2 * PT + pl], site);
+  }
+}
+
 // The per-atom core of passes 1 and 2: from the bond geometry (unit vectors, r, 2/r, f_C, f_C', the
 // cosines of the bond pairs; R) and the parameter constants (T: R itself, or a dual number carrying
 // parameter tangents), U = sum_j f_C (f_R - b f_A), which is twice the site energy U_i of Eq. 2,
@@ -305,24 +339,18 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
 
   R U, Px[M], Py[M], Pz[M];
   atom_core<M, INNER, R, R, GEN>(ux, uy, uz, r, ir2, fc, fcp, cs, K, U, Px, Py, Pz);
-  R W0 = R(0), W1 = R(0), W2 = R(0), W3 = R(0), W4 = R(0), W5 = R(0);
+  // the stage rows of this atom's bonds, and its terms of the virial -sum_j d_ij (x) P_ij added to the
+  // lane's running sums (a phantom bond has P = 0)
 #pragma unroll
   for (int j = 0; j < M; ++j) {
-    if (store && (EXACT || j < m)) {
-      R *st = stage + (size_t)(lb + j) * stage_stride<PT>() + pl;
-      sst(&st[0], Px[j], 5);
-      sst(&st[PT], Py[j], 5);
-      sst(&st[2 * PT], Pz[j], 5);
+    if (store && (EXACT || j < m)) stage_store<PT, R>(stage, lb + j, pl, Px[j], Py[j], Pz[j]);
+    if (store) {
+      const R dx = r[j] * ux[j], dy = r[j] * uy[j], dz = r[j] * uz[j];
+      acc.W[0] -= dx * Px[j]; acc.W[1] -= dy * Py[j]; acc.W[2] -= dz * Pz[j];
+      acc.W[3] -= dx * Py[j]; acc.W[4] -= dy * Pz[j]; acc.W[5] -= dz * Px[j];
     }
-    const R dx = r[j] * ux[j], dy = r[j] * uy[j], dz = r[j] * uz[j];
-    W0 -= dx * Px[j]; W1 -= dy * Py[j]; W2 -= dz * Pz[j];
-    W3 -= dx * Py[j]; W4 -= dy * Pz[j]; W5 -= dz * Px[j];
   }
-  if (store) {
-    acc.U += R(0.5) * U;
-    acc.W[0] += W0; acc.W[1] += W1; acc.W[2] += W2;
-    acc.W[3] += W3; acc.W[4] += W4; acc.W[5] += W5;
-  }
+  if (store) acc.U += R(0.5) * U;
 }
 
 template <int PT, int MMAX, bool EXACT, bool INNER, typename R, bool GEN = false>
@@ -370,6 +398,11 @@ __device__ __forceinline__ float ld_cluster(unsigned addr, float) {
   asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
   return v;
 }
+__device__ __forceinline__ float2 ld_cluster2(unsigned addr) {
+  float2 v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
 __device__ __forceinline__ double ld_cluster(unsigned addr, double) {
   double v;
   asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(addr));
@@ -391,6 +424,8 @@ struct BatchParams {
   const void *consts;              // R [P][8]: PConsts of every parameter set
   const int *atom_off, *boff, *poff;
   const int *ameta;                // [Ntot]: bonds kept | (some bond beyond R1) << 16
+  const int4 *arev;                // [Ntot]: reverse bonds of the atom's first 8 bonds, configuration-local,
+                                   // 16 bits each (bond e in bits 16 (e % 2) of component e / 2)
   const void *gA, *gB, *gcos;
   const CtaRec *recs;
   int ntiles;                      // parameter tiles: ceil(P / PT)
@@ -413,7 +448,7 @@ struct BatchParams {
 // Shared memory of one CTA (R = float or double, R4 its 4-vector):
 //   [region0: max(nb*stride(PT) R, (NW + (cluster ? ncta : 0)) * PT * kNSum double)]  stage of P_ij,
 //    later the per-warp FP64 partial sums and, in rank 0 of a cluster, the totals of every rank
-//   [sA: nb R4][sB: nb R4][sC: nq R][satom: natoms int4][stF: natoms R4 (fitness only)]
+//   [sA: nb R4][sB: nb R4][sC: nq R][satom: natoms int4][stF: natoms R4 (fitness only)][srev: natoms int4]
 // region0 sits at offset 0 in every CTA, so a peer's stage is addressed by mapping this CTA's own
 // stage address to the peer rank.
 template <int PT, bool CLUSTER, typename R, int NW = kNW>
@@ -430,6 +465,7 @@ __host__ __device__ inline size_t batch_smem(int nb, int nq, int nat, int ncta) 
   b += ((size_t)nq * sizeof(R) + 31) / 32 * 32;
   b += (size_t)nat * sizeof(int4);
   b += (size_t)nat * sizeof(R4);
+  b += (size_t)nat * sizeof(int4);
   return b;
 }
 
@@ -460,41 +496,38 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 constexpr unsigned kMbarSpins = 1u << 22;   // bound of a wait for one configuration's copies
 
 // Pass 3 of one atom with a compile-time neighbour count M from a single-CTA stage: F_i = sum_j P_ij
-// over the atom's own rows minus sum_j P_ji over the rows of the reverse bonds (roff maps a
-// configuration-local bond index to a stage row).
+// over the atom's own rows minus sum_j P_ji over the rows of the reverse bonds. rv: the reverse bonds'
+// configuration-local indices, 16 bits each (roff maps them to stage rows).
 template <int M, int PTT, typename R>
-__device__ __forceinline__ void gather_atom(const R *__restrict__ stage, const typename Vec4<R>::T *__restrict__ sB,
-                                            int lb, int roff, int pl, R &Fx, R &Fy, R &Fz) {
-  constexpr int S = stage_stride<PTT>();
-  int rb[M];
+__device__ __forceinline__ void gather_atom(const R *__restrict__ stage, int4 rv, int lb, int roff, int pl,
+                                            R &Fx, R &Fy, R &Fz) {
+  const int rw[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
   for (int e = 0; e < M; ++e) {
-    if constexpr (sizeof(R) == 4) rb[e] = __float_as_int((float)sld(&sB[lb + e].w, 14)) & 0xffff;
-    else rb[e] = (int)sld(&sB[lb + e].w, 14) & 0xffff;
-  }
-  const R *st = stage + (size_t)lb * S + pl;
-#pragma unroll
-  for (int e = 0; e < M; ++e) {
-    Fx += sld(&st[e * S], 13);
-    Fy += sld(&st[e * S + PTT], 13);
-    Fz += sld(&st[e * S + 2 * PTT], 13);
+    R x, y, z;
+    stage_load<PTT, R>(stage, lb + e, pl, x, y, z, 13);
+    Fx += x;
+    Fy += y;
+    Fz += z;
   }
 #pragma unroll
   for (int e = 0; e < M; ++e) {
-    const R *sr = stage + (size_t)(rb[e] + roff) * S + pl;
-    Fx -= sld(&sr[0], 15);
-    Fy -= sld(&sr[PTT], 15);
-    Fz -= sld(&sr[2 * PTT], 15);
+    const int rb = (rw[e >> 1] >> (16 * (e & 1))) & 0xffff;
+    R x, y, z;
+    stage_load<PTT, R>(stage, rb + roff, pl, x, y, z, 15);
+    Fx -= x;
+    Fy -= y;
+    Fz -= z;
   }
 }
 // Dispatch on the atom's neighbour count; false when it exceeds MMAX (the caller's loop handles it).
 template <int PTT, int MMAX, typename R>
-__device__ __forceinline__ bool gather_dispatch(int m, const R *stage, const typename Vec4<R>::T *sB, int lb,
-                                                int roff, int pl, R &Fx, R &Fy, R &Fz) {
+__device__ __forceinline__ bool gather_dispatch(int m, const R *stage, int4 rv, int lb, int roff, int pl, R &Fx,
+                                                R &Fy, R &Fz) {
 #define TSF_GCASE(MM)                                                              \
   case MM:                                                                         \
     if constexpr (MMAX >= MM) {                                                    \
-      gather_atom<MM, PTT, R>(stage, sB, lb, roff, pl, Fx, Fy, Fz);                \
+      gather_atom<MM, PTT, R>(stage, rv, lb, roff, pl, Fx, Fy, Fz);                \
       return true;                                                                 \
     }                                                                              \
     return false;
@@ -518,6 +551,7 @@ struct TileEnv {
   const typename Vec4<R>::T *sA, *sB;
   const R *sC;
   const int4 *satom;
+  const int4 *srev;                // per atom: the reverse bonds' configuration-local indices, 16 bits each
   const typename Vec4<R>::T *stF;
   int ns, s0, nat, c, cb0, B0;
   double inv_nat;
@@ -613,12 +647,16 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
     const int m = at.z, lb = at.x;
     R Fx = R(0), Fy = R(0), Fz = R(0);
     bool gathered = false;
-    if constexpr (APW == 1 && !CLUSTER) gathered = gather_dispatch<PTT, MMAX, R>(m, stage, sB, lb, cb0 - B0, pl, Fx, Fy, Fz);
+    if constexpr (APW == 1 && !CLUSTER)
+      gathered = gather_dispatch<PTT, MMAX, R>(m, stage, sld(&env.srev[li], 12), lb, cb0 - B0, pl, Fx, Fy, Fz);
     for (int e = 0; !gathered && e < m; ++e) {
-      const R *st = stage + (size_t)(lb + e) * stage_stride<PTT>() + pl;
-      Fx += sld(&st[0], 13);
-      Fy += sld(&st[PTT], 13);
-      Fz += sld(&st[2 * PTT], 13);
+      {
+        R x, y, z;
+        stage_load<PTT, R>(stage, lb + e, pl, x, y, z, 13);
+        Fx += x;
+        Fy += y;
+        Fz += z;
+      }
       int packed;  // configuration-local indices of the reverse entry (bits 0-15) and of atom j (16-31)
       if constexpr (sizeof(R) == 4) packed = __float_as_int((float)sld(&sB[lb + e].w, 14));
       else packed = (int)sld(&sB[lb + e].w, 14);
@@ -639,15 +677,23 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 #endif
           continue;
         }
-        const unsigned addr = peer_stage[r] + (unsigned)(((rb - peer_b0[r]) * stage_stride<PTT>() + pl) * sizeof(R));
-        Fx -= ld_cluster(addr, R(0));
-        Fy -= ld_cluster(addr + PTT * sizeof(R), R(0));
-        Fz -= ld_cluster(addr + 2 * PTT * sizeof(R), R(0));
+        const unsigned row = peer_stage[r] + (unsigned)((rb - peer_b0[r]) * stage_stride<PTT>() * sizeof(R));
+        if constexpr (stage_packed<PTT, R>()) {
+          const float2 xy = ld_cluster2(row + pl * sizeof(float2));
+          Fx -= xy.x;
+          Fy -= xy.y;
+          Fz -= ld_cluster(row + (2 * PTT + pl) * sizeof(R), R(0));
+        } else {
+          Fx -= ld_cluster(row + pl * sizeof(R), R(0));
+          Fy -= ld_cluster(row + (PTT + pl) * sizeof(R), R(0));
+          Fz -= ld_cluster(row + (2 * PTT + pl) * sizeof(R), R(0));
+        }
       } else {
-        const R *sr = stage + (size_t)(rb + cb0 - B0) * stage_stride<PTT>() + pl;
-        Fx -= sld(&sr[0], 15);
-        Fy -= sld(&sr[PTT], 15);
-        Fz -= sld(&sr[2 * PTT], 15);
+        R x, y, z;
+        stage_load<PTT, R>(stage, rb + cb0 - B0, pl, x, y, z, 15);
+        Fx -= x;
+        Fy -= y;
+        Fz -= z;
       }
     }
     const int i = s0 + li;
@@ -818,6 +864,7 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
     int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) +
                                            ((size_t)nq * sizeof(R) + 31) / 32 * 32);
     R4 *stF = reinterpret_cast<R4 *>(satom + ns);
+    int4 *srev = reinterpret_cast<int4 *>(stF + ns);
 
     // stage this slice's geometry, atom table and target forces in shared memory
     {
@@ -846,6 +893,7 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
       for (int t = tid; t < ns; t += (NW * kWarp)) {
         const int am = a.ameta[s0 + t];
         sst(&satom[t], make_int4(a.boff[s0 + t] - B0, a.poff[s0 + t] - Q0, am & 0xffff, am >> 16), 9);
+        sst(&srev[t], a.arev[s0 + t], 9);
         if (fit) {   // target force in the working precision
           const double *f = a.tF + 3 * (int64_t)(s0 + t);
           const double fx = f[0], fy = f[1], fz = f[2];
@@ -916,8 +964,8 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
       peer_b0[ncta] = a.recs[rec0 + ncta - 1].B0 + a.recs[rec0 + ncta - 1].nb - cb0;
     }
 
-    const TileEnv<R> env = {stage, sA, sB, sC, satom, stF, ns, s0, nat, c, cb0, B0, rec.inv_nat, mask, fit, rank,
-                             ncta, peer_stage, peer_b0};
+    const TileEnv<R> env = {stage, sA, sB, sC, satom, srev, stF, ns, s0, nat, c, cb0, B0, rec.inv_nat, mask, fit,
+                             rank, ncta, peer_stage, peer_b0};
     pdl_wait();   // per-call constants of the preparation kernel (a no-op after the first item)
     // the last tile may hold fewer parameter sets: the FP32 single-CTA variants for up to 4 neighbours
     // run it with more atoms in a warp (tiles of 16 or 8 parameter sets); other variants keep the

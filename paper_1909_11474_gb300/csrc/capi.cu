@@ -371,7 +371,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   cudaDeviceSynchronize();
   tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.box, &c.build_status, &c.counters,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
-                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.ameta, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
+                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.ameta, &c.arev, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_keys, &c.md_ke, &c.md_boxd};
@@ -525,6 +525,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.build_status.ensure(sizeof(unsigned)));
   TSF_CUDA(c.brev.ensure(bond_cap * sizeof(int)));
   TSF_CUDA(c.ameta.ensure(std::max<int64_t>(1, N) * sizeof(int)));
+  TSF_CUDA(c.arev.ensure(std::max<int64_t>(1, N) * sizeof(int4)));
   TSF_CUDA(c.gA32.ensure(bond_cap * sizeof(float4)));
   TSF_CUDA(c.gB32.ensure(bond_cap * sizeof(float4)));
   TSF_CUDA(c.gcos32.ensure(slot_cap * sizeof(float)));
@@ -570,6 +571,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   L.gB = c.gB32.as<float4>();
   L.gcos = c.gcos32.as<float>();
   L.ameta = c.ameta.as<int>();
+  L.arev = c.arev.as<int4>();
   L.status = st;
   L.build_status = c.build_status.as<unsigned>();
   L.nat_max = nat_max;

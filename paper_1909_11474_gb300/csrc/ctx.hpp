@@ -200,6 +200,7 @@ struct Ctx {
   DevBuf counters;   // per-launch work counters of the persistent batched kernels
   DevBuf gA32, gB32, gcos32, gA64, gB64, gcos64;
   DevBuf ameta;   // [Ntot] int: bonds kept (min(cnt, M)) | (some bond beyond R1, f_C != 1) << 16
+  DevBuf arev;    // [Ntot] int4: configuration-local reverse bonds of the first 8 bonds, 16 bits each
   BatchPlan plan32, plan64;
   DevBuf part, dpart, work, tf4, gpart;
 
@@ -239,6 +240,7 @@ struct BuildLaunch {
   float4 *gA, *gB;
   float *gcos;
   int *ameta;
+  int4 *arev;
   unsigned *status, *build_status;   // the context's status word and the build's own
   int nat_max;    // largest configuration (atoms)
 };

@@ -179,6 +179,7 @@ struct BuildParams {
   float4 *gA, *gB;
   float *gcos;
   int *ameta;                      // [Ntot]: bonds kept (min(cnt, M)) | (some bond beyond R1) << 16
+  int4 *arev;                      // [Ntot]: configuration-local reverse bonds of the first 8 bonds, 16 bits each
   unsigned *status, *build_status; // the context's status word and the build's own (read by the host)
   int nat_max;                     // largest configuration of the launch (shared-memory layout)
   int lists_in_smem;               // the lists and unit vectors fit in shared memory
@@ -533,6 +534,7 @@ __global__ void __launch_bounds__(kBuildThreads, 3) build_batch_kernel(const Bui
     }
     const int rev = s_boff[jl] + found;
     a.brev[base_b + bl] = (int)(base_b + rev);
+    if (e < 8) reinterpret_cast<unsigned short *>(a.arev + i)[e] = (unsigned short)rev;
     const ExactPair p = exact_pair(a.pos_in[3 * j], a.pos_in[3 * j + 1], a.pos_in[3 * j + 2], a.pos_in[3 * i],
                                    a.pos_in[3 * i + 1], a.pos_in[3 * i + 2], s_H, n.x, n.y, n.z);
     float4 A, Bv;
@@ -594,6 +596,7 @@ cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s) {
   a.gB = L.gB;
   a.gcos = L.gcos;
   a.ameta = L.ameta;
+  a.arev = L.arev;
   a.status = L.status;
   a.build_status = L.build_status;
   a.nat_max = std::max(1, L.nat_max);
