@@ -54,6 +54,10 @@ cudaError_t ensure_side_streams(const Ctx &ctx) { return ensure_side(ctx, kSide)
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s) {
   const bool f64 = plan.precision == 64;
+  // work counters first, so that the preparation kernel and the batched kernel are adjacent launches
+  // (programmatic dependent launch overlaps the latter's start with the former)
+  cudaError_t ez = cudaMemsetAsync(out.counters, 0, plan.buckets.size() * sizeof(int), s);
+  if (ez != cudaSuccess) return ez;
   // per-call preparation: per-parameter-set constants
   {
     const unsigned blocks = (unsigned)((P + 255) / 256);
@@ -92,8 +96,6 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.dpart = out.dpart;
   bp.status = ctx.status.as<unsigned>();
   bp.wait_spins = ctx.wait_spins < 0 ? kMbarSpins : (unsigned)std::min<int64_t>(ctx.wait_spins, 0xffffffffll);
-  cudaError_t ez = cudaMemsetAsync(out.counters, 0, plan.buckets.size() * sizeof(int), s);
-  if (ez != cudaSuccess) return ez;
   const bool timed = ctx.timer.begin(s);
   // several buckets run side by side on the context's side streams (forked from and joined back into
   // `s` by events), so one bucket's last items overlap the next bucket's first ones

@@ -555,6 +555,7 @@ struct TileEnv {
   const typename Vec4<R>::T *stF;
   int ns, s0, nat, c, cb0, B0;
   double inv_nat;
+  const double *tgt;               // fitness: the configuration's targets E*, W*_1..6 (shared memory)
   uint8_t mask;
   bool fit;
   unsigned rank, ncta;
@@ -738,8 +739,9 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
   const int rl = tid >> 3, rk = tid & 7, rx = rk ^ (rl & 7);
   double T = 0.0;
   if (red_thread) {
+    T = sld(&red[rl * kNSum + rx], 18);
 #pragma unroll 4
-    for (int w = 0; w < NW; ++w) T += sld(&red[(w * PTT + rl) * kNSum + rx], 18);
+    for (int w = 1; w < NW; ++w) T += sld(&red[(w * PTT + rl) * kNSum + rx], 18);
   }
   if constexpr (CLUSTER) {
     if (red_thread) st_cluster(map_to_rank(smem_addr(tot + ((int)rank * PTT + rl) * kNSum + rx), 0), T);
@@ -764,8 +766,7 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
       const int bit = rk == 0 ? 1 : (rk <= 6 ? 2 : 4);
       double term = T;
       if (rk <= 6) {
-        const double target = rk == 0 ? a.tE[c] : a.tW[6 * (size_t)c + (rk - 1)];
-        const double d = T * env.inv_nat - target;
+        const double d = T * env.inv_nat - env.tgt[rk];
         term = d * d;
       }
       if (!(mask & bit)) term = isfinite(T) ? 0.0 : T - T;
@@ -799,6 +800,7 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
   __shared__ int s_item;
   __shared__ double s_fn[NW];            // per-warp FP64 sums of |F*|^2 (target norm, first chunk)
   __shared__ double s_fr[kMaxCluster];   // rank 0 of a cluster: the ranks' sums
+  __shared__ double s_tgt[7];            // fitness: targets E*, W*_1..6 of the item's configuration
   R *stage = reinterpret_cast<R *>(smem);
   constexpr int APW = kWarp / PT;
 
@@ -889,6 +891,7 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
         }
         for (int t = tid; t < nq; t += (NW * kWarp)) sst(&sC[t], gC[t], 8);
       }
+      if (fit && tid < 7) s_tgt[tid] = tid == 0 ? a.tE[c] : a.tW[6 * (size_t)c + (tid - 1)];
       double f2 = 0.0;   // FP64 sum of |F*|^2 over this thread's atoms (target norm D_f of Eq. 19)
       for (int t = tid; t < ns; t += (NW * kWarp)) {
         const int am = a.ameta[s0 + t];
@@ -964,7 +967,7 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
       peer_b0[ncta] = a.recs[rec0 + ncta - 1].B0 + a.recs[rec0 + ncta - 1].nb - cb0;
     }
 
-    const TileEnv<R> env = {stage, sA, sB, sC, satom, srev, stF, ns, s0, nat, c, cb0, B0, rec.inv_nat, mask, fit,
+    const TileEnv<R> env = {stage, sA, sB, sC, satom, srev, stF, ns, s0, nat, c, cb0, B0, rec.inv_nat, s_tgt, mask, fit,
                              rank, ncta, peer_stage, peer_b0};
     pdl_wait();   // per-call constants of the preparation kernel (a no-op after the first item)
     // the last tile may hold fewer parameter sets: the FP32 single-CTA variants for up to 4 neighbours

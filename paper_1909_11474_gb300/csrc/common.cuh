@@ -80,6 +80,57 @@ __device__ __forceinline__ ExactPair exact_pair(double xjx, double xjy, double x
 }
 
 
+// x (FP64) as FP32 head + tail, by integer operations on the binary64 layout (the device's FP64 unit is
+// slow): the head keeps the top 24 bits of the significand (truncated), the tail is the remaining 29
+// bits converted to FP32 with one rounding, so |x - head - tail| <= 2^-48 |x|. |x| < 2^-60 gives
+// head = tail = 0 (off by less than 2^-60). Returns false for |x| > 2^60 and non-finite x, which the
+// caller takes through FP64 arithmetic.
+__device__ __forceinline__ bool split_f64(double x, float &hi, float &lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+  hi = 0.f;
+  lo = 0.f;
+  if (e < -60) return true;
+  if (e > 60) return false;
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const unsigned long long mant = b & 0xfffffffffffffull;
+  hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));
+  const float scale = __uint_as_float((unsigned)(e - 52 + 127 + 64) << 23);   // 2^(e - 52 + 64)
+  lo = __uint_as_float(__float_as_uint(__uint2float_rn((unsigned)(mant & 0x1fffffffu)) * scale) ^ sign) *
+       0x1p-64f;
+  return true;
+}
+
+// s + t = a + b exactly (FP32 two-sum, six additions).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &t) {
+  s = a + b;
+  const float bb = s - a;
+  t = (a - (s - bb)) + (b - bb);
+}
+
+// Component k of the bond vector d = x_j - x_i + n H from FP32 head + tail pairs of the positions
+// (split_f64) and of the box rows (H_a = h_a + l_a): the head difference and the head products n_a h_a
+// (exact by FMA; n_a is a small integer) are summed by two-sum, every rounding error and tail goes to
+// a running tail, and head + tail is rounded once at the end. The result is within ~2^-45 of
+// max(|x|, |n H|) of the exact value, so it equals the FP64 vector rounded to FP32 except where that
+// value lies within this distance of a rounding boundary.
+__device__ __forceinline__ float bond_component(float xjh, float xjl, float xih, float xil, float n0, float n1,
+                                                float n2, float h0, float l0, float h1, float l1, float h2,
+                                                float l2) {
+  float s, t;
+  two_sum(xjh, -xih, s, t);
+  float lo = t + (xjl - xil);
+  const float n[3] = {n0, n1, n2}, h[3] = {h0, h1, h2}, l[3] = {l0, l1, l2};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = n[a] * h[a];
+    const float e = __fmaf_rn(n[a], h[a], -p);
+    two_sum(s, p, s, t);
+    lo += (t + e) + n[a] * l[a];
+  }
+  return s + lo;
+}
+
 // FP32 -> FP64, exact, built from the IEEE-754 binary32 and binary64 layouts with integer operations
 // (sign kept, exponent rebiased from 127 to 1023, significand shifted left by 29), so that the
 // conversions of per-warp partial sums do not queue on the device's scarce FP64 unit. Zeros take the

@@ -37,6 +37,7 @@ struct MdGeom {
   int nc[3];
   int diag;                   // H (and so H^-1) diagonal: cell coordinates need 3 products, not 9
   double Hn[9];               // H^-1 with column k scaled by nc_k: x Hn = cell coordinates
+  float Hnh[9], Hnl[9];       // Hn as FP32 head + tail (Hn = Hnh + Hnl to ~2^-48 relative)
   float E[9];                 // cell edge vectors, row k = H_k / nc_k
   float cut2_lo, cut2_hi;     // FP32 decision band around R2^2
   double R1, R2, R2sq;
@@ -47,6 +48,11 @@ struct MdGeom {
 // Cell of every atom; the cell's slots hold (u, atom index) so the pair search reads one record per
 // candidate. Every atom's neighbour count starts at zero here; an atom that gets no slot (non-finite
 // position, full cell) keeps an empty list and the call is flagged.
+//
+// The cell coordinates w = x Hn are formed in FP32 head + tail arithmetic (products split exactly by
+// FMA, sums by two-sum), accurate to ~2^-44 |w|; below |w| = 2^16 cells that is under the FP32 rounding
+// of u itself. Other positions take FP64 arithmetic. The floor C is then that of head + tail, and
+// u = w - C is rounded once to FP32: any consistent (C, u) serves the search and the bond vectors.
 __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdGeom G,
                                 int *__restrict__ cellcnt, float4 *__restrict__ cellu,
                                 float4 *__restrict__ u4, int4 *__restrict__ m4, int *__restrict__ cnt,
@@ -55,32 +61,78 @@ __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdG
   if (i >= N) return;
   cnt[i] = 0;
   const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
-  // per dimension: the cell coordinate w = s nc (nc folded into the inverse box), its floor C, the
-  // in-cell coordinate u = w - C (exact in FP64), and the integer split C = m nc + c
-  double w[3];
-  bool ok = true;
+  float xh[3], xl[3];
+  bool fast = split_f64(x, xh[0], xl[0]);
+  fast = split_f64(y, xh[1], xl[1]) && fast;
+  fast = split_f64(z, xh[2], xl[2]) && fast;
+  int Ci[3];
+  float uu[3];
+  if (fast) {
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    w[k] = G.diag ? (k == 0 ? x : (k == 1 ? y : z)) * G.Hn[4 * k]
-                  : x * G.Hn[k] + y * G.Hn[3 + k] + z * G.Hn[6 + k];
-    ok = ok && fabs(w[k]) < 1e9;                   // false for NaN and inf
+    for (int k = 0; k < 3; ++k) {
+      float wh, wl;
+      if (G.diag) {
+        const float a = G.Hnh[4 * k], b = G.Hnl[4 * k];
+        const float p = xh[k] * a;
+        wl = __fmaf_rn(xh[k], a, -p) + __fmaf_rn(xh[k], b, xl[k] * a);
+        wh = p;
+      } else {
+        float p[3], q = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float h = G.Hnh[3 * a + k], l = G.Hnl[3 * a + k];
+          p[a] = xh[a] * h;
+          q += __fmaf_rn(xh[a], h, -p[a]) + __fmaf_rn(xh[a], l, xl[a] * h);
+        }
+        float s1, t1, s2, t2;
+        two_sum(p[0], p[1], s1, t1);
+        two_sum(s1, p[2], s2, t2);
+        wh = s2;
+        wl = q + t1 + t2;
+      }
+      // normalise (|wl| <= ulp(wh) / 2), then C = floor(wh) + floor(frac(wh) + wl)
+      float h2, t2;
+      two_sum(wh, wl, h2, t2);
+      wh = h2;
+      wl = t2;
+      fast = fast && fabsf(wh) < 65536.f;
+      const float ch = floorf(wh);
+      const float s = (wh - ch) + wl;
+      const float cl = floorf(s);
+      uu[k] = s - cl;
+      Ci[k] = (int)ch + (int)cl;
+    }
   }
-  if (!ok) {
-    set_status(status, TERSOFF_STATUS_NONFINITE);
-    u4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    m4[i] = make_int4(0, 0, 0, 0);
-    return;
+  if (!fast) {
+    // FP64 cell coordinates: w = s nc (nc folded into the inverse box), its floor C, u = w - C
+    double w[3];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      w[k] = G.diag ? (k == 0 ? x : (k == 1 ? y : z)) * G.Hn[4 * k]
+                    : x * G.Hn[k] + y * G.Hn[3 + k] + z * G.Hn[6 + k];
+      ok = ok && fabs(w[k]) < 1e9;                 // false for NaN and inf
+    }
+    if (!ok) {
+      set_status(status, TERSOFF_STATUS_NONFINITE);
+      u4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      m4[i] = make_int4(0, 0, 0, 0);
+      return;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double C = floor(w[k]);
+      uu[k] = (float)(w[k] - C);
+      Ci[k] = (int)C;
+    }
   }
   int mm[3], cc[3];
-  float uu[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const double C = floor(w[k]);
-    uu[k] = (float)(w[k] - C);
-    const int Ci = (int)C, n = G.nc[k];
-    const int m = Ci >= 0 ? Ci / n : -((n - 1 - Ci) / n);
+  for (int k = 0; k < 3; ++k) {   // the integer split C = m nc + c
+    const int n = G.nc[k];
+    const int m = Ci[k] >= 0 ? Ci[k] / n : -((n - 1 - Ci[k]) / n);
     mm[k] = m;
-    cc[k] = Ci - m * n;
+    cc[k] = Ci[k] - m * n;
   }
   const int cell = (cc[0] * G.nc[1] + cc[1]) * G.nc[2] + cc[2];
   u4[i] = make_float4(uu[0], uu[1], uu[2], 0.f);
@@ -715,7 +767,11 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
     for (int b = 0; b < 3; ++b)
       if (a != b && (H[3 * a + b] != 0.0 || G.Hinv[3 * a + b] != 0.0)) G.diag = 0;
   for (int a = 0; a < 3; ++a)
-    for (int k = 0; k < 3; ++k) G.Hn[3 * a + k] = G.Hinv[3 * a + k] * (double)G.nc[k];
+    for (int k = 0; k < 3; ++k) {
+      G.Hn[3 * a + k] = G.Hinv[3 * a + k] * (double)G.nc[k];
+      G.Hnh[3 * a + k] = (float)G.Hn[3 * a + k];
+      G.Hnl[3 * a + k] = (float)(G.Hn[3 * a + k] - (double)G.Hnh[3 * a + k]);
+    }
   G.R1 = R1;
   G.R2 = R2;
   G.R2sq = R2 * R2;
@@ -791,13 +847,19 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
 constexpr double kAccel = 9.648533215665e-3;      // 1 eV / (A amu) in A / fs^2 (CODATA 2018)
 constexpr double kKinetic = 103.6426965268;       // 1 amu A^2 / fs^2 in eV
 
-// v += F / m * dt / 2, then x += v dt (FP64 state, forces in R).
+// a_i = (1 eV / (A amu)) / m_i in A / fs^2 per eV / A, once per run (the device's FP64 divide is slow).
+__global__ void md_accel_kernel(int N, const double *__restrict__ mass, double *__restrict__ acc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) acc[i] = kAccel / mass[i];
+}
+
+// v += a F dt / 2, then x += v dt (FP64 state, forces in R).
 template <typename R>
 __global__ void md_kick_drift_kernel(int N, double *__restrict__ pos, double *__restrict__ vel,
-                                     const R *__restrict__ F, const double *__restrict__ mass, double dt) {
+                                     const R *__restrict__ F, const double *__restrict__ acc, double dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const double h = 0.5 * dt * kAccel / mass[i];
+  const double h = 0.5 * dt * acc[i];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double v = vel[3 * i + k] + h * (double)F[3 * i + k];
@@ -806,18 +868,18 @@ __global__ void md_kick_drift_kernel(int N, double *__restrict__ pos, double *__
   }
 }
 
-// v += F / m * dt / 2 (dt = 0: no kick) and the kinetic energy sum_i m v^2 / 2 into *Ekin, in a
-// fixed order (per-block partials, then the grouped last-block sums).
+// v += a F dt / 2 (dt = 0: no kick) and the kinetic energy sum_i m v^2 / 2 into *Ekin, in a fixed
+// order (per-block partials, then the grouped last-block sums).
 template <typename R>
 __global__ void __launch_bounds__(kMdThreads) md_kick_kernel(int N, double *__restrict__ vel,
                                                              const R *__restrict__ F, const double *__restrict__ mass,
-                                                             double dt, double *__restrict__ partial,
-                                                             double *__restrict__ Ekin) {
+                                                             const double *__restrict__ acc, double dt,
+                                                             double *__restrict__ partial, double *__restrict__ Ekin) {
   __shared__ double red[kMdThreads / 32][7];
   const int i = blockIdx.x * blockDim.x + threadIdx.x, tid = threadIdx.x;
   double ke = 0.0;
   if (i < N) {
-    const double m = mass[i], h = 0.5 * dt * kAccel / m;
+    const double h = 0.5 * dt * acc[i];
     double v2 = 0.0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -825,7 +887,7 @@ __global__ void __launch_bounds__(kMdThreads) md_kick_kernel(int N, double *__re
       vel[3 * i + k] = v;
       v2 += v * v;
     }
-    ke = 0.5 * kKinetic * m * v2;
+    ke = (0.5 * kKinetic) * mass[i] * v2;
   }
   for (int off = 16; off > 0; off >>= 1) ke += __shfl_xor_sync(0xffffffffu, ke, off);
   if ((tid & 31) == 0) red[tid >> 5][0] = ke;
@@ -844,32 +906,37 @@ int md_nve(Ctx &c, int N, double *pos, double *vel, const double *mass, const do
            void *F, double *W, cudaStream_t s, std::string &err) {
   const int nblk = (N + kMdThreads - 1) / kMdThreads;
   const int ngroups = (nblk + kMdGroup - 1) / kMdGroup;
-  if (c.md_ke.ensure(md_sum_bytes(1, nblk))) {
+  const size_t sum_bytes = (md_sum_bytes(1, nblk) + 15) / 16 * 16;
+  if (c.md_ke.ensure(sum_bytes + (size_t)N * sizeof(double))) {
     err = "device allocation failed";
     return TERSOFF_E_CUDA;
   }
   double *part = c.md_ke.as<double>();
   char *counters = static_cast<char *>(c.md_ke.p) + md_counter_offset(1, nblk);
+  double *acc = reinterpret_cast<double *>(static_cast<char *>(c.md_ke.p) + sum_bytes);
+  md_accel_kernel<<<nblk, kMdThreads, 0, s>>>(N, mass, acc);
   auto kick = [&](double h, int step) {
     cudaMemsetAsync(counters, 0, (ngroups + 1) * sizeof(unsigned), s);
     if (precision == 64)
-      md_kick_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, vel, static_cast<const double *>(F), mass, h, part, Ekin + step);
+      md_kick_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, vel, static_cast<const double *>(F), mass, acc, h, part,
+                                                         Ekin + step);
     else
-      md_kick_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, vel, static_cast<const float *>(F), mass, h, part, Ekin + step);
+      md_kick_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, vel, static_cast<const float *>(F), mass, acc, h, part,
+                                                        Ekin + step);
   };
   int rc = md_force(c, N, pos, boxh, x, R1, R2, M, precision, Epot, F, W, s, err);
   if (rc != TERSOFF_OK) return rc;
   kick(0.0, 0);                                     // kinetic energy of the initial velocities
   for (int k = 1; k <= nsteps; ++k) {
     if (precision == 64)
-      md_kick_drift_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, pos, vel, static_cast<const double *>(F), mass, dt);
+      md_kick_drift_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, pos, vel, static_cast<const double *>(F), acc, dt);
     else
-      md_kick_drift_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, pos, vel, static_cast<const float *>(F), mass, dt);
+      md_kick_drift_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, pos, vel, static_cast<const float *>(F), acc, dt);
     rc = md_force(c, N, pos, boxh, x, R1, R2, M, precision, Epot + k, F, W, s, err);
     if (rc != TERSOFF_OK) return rc;
     kick(dt, k);
   }
-  const cudaError_t e = launched(1 + 2 * nsteps);   // kicks and kick-drifts (the force calls count themselves)
+  const cudaError_t e = launched(2 + 2 * nsteps);   // accelerations, kicks and kick-drifts (the force calls count themselves)
   if (e != cudaSuccess) {
     err = std::string("CUDA error: ") + cudaGetErrorString(e);
     return TERSOFF_E_CUDA;

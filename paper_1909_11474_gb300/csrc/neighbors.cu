@@ -55,30 +55,40 @@ __device__ __forceinline__ void cutoff_fc(double r, double R1, double R2, double
 
 // Per bond: unit vector, r, 2/r, f_C, f_C' and, packed into one int (rev | j << 16), the
 // configuration-local indices of the reverse bond and of the neighbour atom (4th slot: as a double,
-// or as the bit pattern of the int in the FP32 record). The bond vector d is formed in FP64 by the
-// expression of the membership test (where the cancellation happens); FP32 records round it and then
-// normalise in FP32 (built by the fused build kernel), FP64 records stay in FP64 (built on the first
-// FP64 evaluation by geometry_bond_kernel, one thread per bond).
+// or as the bit pattern of the int in the FP32 record). FP64 records take the bond vector d of the
+// exact membership test and stay in FP64 (built on the first FP64 evaluation by geometry_bond_kernel,
+// one thread per bond). FP32 records (built by the fused build kernel) take d rounded to FP32 and
+// normalise in FP32; that kernel forms d from FP32 head + tail pairs of the positions and the box
+// (bond_component: the FP64 vector rounded to FP32, but for values within ~2^-45 |x| of a rounding
+// boundary), so that it needs the device's slow FP64 unit only for configurations whose coordinates
+// cannot be split (beyond 2^60).
+// FP32 bond record from the FP32 bond vector; R1f, R2f, Wf = R2 - R1 and Kf = -pi / (2 (R2 - R1)) are
+// the FP64 cut-off constants rounded to FP32. Returns whether the bond reaches beyond R1.
+__device__ __forceinline__ bool bond_record_f32(float dx, float dy, float dz, float R1f, float R2f, float Wf,
+                                                float Kf, int rl, float4 &A, float4 &Bv) {
+  const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+  const float r = (dx * dx + dy * dy + dz * dz) * ir;
+  float fc = 1.f, fcp = 0.f;
+  if (r >= R2f) {
+    fc = 0.f;
+  } else if (r > R1f) {
+    const float w = (r - R1f) / Wf;
+    fc = 0.5f * (1.f + cospif(w));
+    fcp = Kf * sinpif(w);
+  }
+  A = make_float4(dx * ir, dy * ir, dz * ir, r);
+  Bv = make_float4(ir + ir, fc, fcp, __int_as_float(rl));
+  return r > R1f;
+}
+
 // The record of one bond from its exact FP64 bond vector: A = (unit vector, r), B = (2/r, f_C, f_C',
 // packed indices rl). Returns whether r > R1 (f_C may differ from 1).
 template <typename R>
 __device__ __forceinline__ bool bond_record(const ExactPair &p, double R1, double R2, int rl,
                                             typename Vec4<R>::T &A, typename Vec4<R>::T &Bv) {
   if constexpr (sizeof(R) == 4) {
-    const float dx = (float)p.dx, dy = (float)p.dy, dz = (float)p.dz;
-    const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
-    const float r = (dx * dx + dy * dy + dz * dz) * ir;
-    float fc = 1.f, fcp = 0.f;
-    if (r >= (float)R2) {
-      fc = 0.f;
-    } else if (r > (float)R1) {
-      const float w = (r - (float)R1) / (float)(R2 - R1);
-      fc = 0.5f * (1.f + cospif(w));
-      fcp = (float)(-0.5 * M_PI / (R2 - R1)) * sinpif(w);
-    }
-    A = make_float4(dx * ir, dy * ir, dz * ir, r);
-    Bv = make_float4(ir + ir, fc, fcp, __int_as_float(rl));
-    return r > (float)R1;
+    return bond_record_f32((float)p.dx, (float)p.dy, (float)p.dz, (float)R1, (float)R2, (float)(R2 - R1),
+                           (float)(-0.5 * M_PI / (R2 - R1)), rl, A, Bv);
   } else {
     const double ir = rsqrt(p.r2);
     const double r = p.r2 * ir;
@@ -158,13 +168,14 @@ __global__ void geometry_pair_kernel(int64_t Ntot, int slots, const int *__restr
 //    neighbour lists (warp per atom, as described at `member`);
 //  phase 2: the bond offsets of the configuration's atoms (block scans), the reverse bond of every
 //    bond, the FP32 bond records and the pair cosines.
-// Shared memory (dynamic, sized for the largest configuration of the launch): FP32 positions, per-atom
-// counts, offsets and flags, and, where they fit, the configuration's lists and bond unit vectors (the
-// reverse-bond search and the pair cosines then read shared memory instead of global memory).
-constexpr int kBuildThreads = 256;
+// Shared memory (dynamic, sized for the largest configuration of the launch): FP32 positions (rounded,
+// and as head + tail pairs), per-atom counts, offsets and flags, and, where they fit, the
+// configuration's lists and bond unit vectors (the reverse-bond search and the pair cosines then read
+// shared memory instead of global memory). Twelve warps per CTA and two CTAs per SM: a 300-cell batch
+// runs in one wave.
+constexpr int kBuildThreads = 384;
 constexpr int kBuildWarps = kBuildThreads / 32;
-constexpr int kBuildMaxAtoms = 1024;
-constexpr size_t kBuildSmemCap = 64 * 1024;   // dynamic shared memory per CTA at most (three CTAs per SM)
+constexpr size_t kBuildSmemCap = 96 * 1024;   // dynamic shared memory per CTA at most (two CTAs per SM)
 
 struct BuildParams {
   int C, M;
@@ -183,6 +194,7 @@ struct BuildParams {
   unsigned *status, *build_status; // the context's status word and the build's own (read by the host)
   int nat_max;                     // largest configuration of the launch (shared-memory layout)
   int lists_in_smem;               // the lists and unit vectors fit in shared memory
+  float R1f, R2f, Wf, Kf;          // R1, R2, R2 - R1 and -pi / (2 (R2 - R1)) rounded to FP32
 };
 
 __device__ __forceinline__ void build_flag(const BuildParams &a, unsigned bit) {
@@ -192,7 +204,7 @@ __device__ __forceinline__ void build_flag(const BuildParams &a, unsigned bit) {
 
 // Dynamic shared memory of the build kernel for configurations of up to nat atoms.
 __host__ __device__ inline size_t build_smem_base(int nat) {
-  return (size_t)nat * sizeof(float4) + (size_t)(4 * nat + 2) * sizeof(int);
+  return (size_t)3 * nat * sizeof(float4) + (size_t)(4 * nat + 2) * sizeof(int);
 }
 __host__ __device__ inline size_t build_smem_lists(int nat, int M) {
   return (size_t)nat * M * (sizeof(int2) + sizeof(float4));
@@ -290,11 +302,13 @@ __device__ bool box_part2(const BoxPart1 &o, const double *H, float xm, double R
   return isfinite(band) && nmax <= 127.f;
 }
 
-__global__ void __launch_bounds__(kBuildThreads, 3) build_batch_kernel(const BuildParams a) {
+__global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const BuildParams a) {
   extern __shared__ __align__(16) unsigned char bsm[];
   const int nmax = a.nat_max, M = a.M;
-  float4 *s_p32 = reinterpret_cast<float4 *>(bsm);
-  int *s_m = reinterpret_cast<int *>(s_p32 + nmax);
+  float4 *s_p32 = reinterpret_cast<float4 *>(bsm);   // positions rounded to FP32 (membership test)
+  float4 *s_ph = s_p32 + nmax;                         // FP32 heads and tails of the positions (bond vectors)
+  float4 *s_pl = s_ph + nmax;
+  int *s_m = reinterpret_cast<int *>(s_pl + nmax);
   int *s_boff = s_m + nmax;            // [nmax + 1]
   int *s_poff = s_boff + nmax + 1;     // [nmax + 1]
   int *s_outer = s_poff + nmax + 1;
@@ -303,6 +317,7 @@ __global__ void __launch_bounds__(kBuildThreads, 3) build_batch_kernel(const Bui
   __shared__ Pre32 s_q;
   __shared__ BoxPart1 s_b1;
   __shared__ double s_H[9];
+  __shared__ float s_Hh[9], s_Hl[9];   // box as FP32 head + tail
   __shared__ int s_ok, s_nmax;
   __shared__ float s_fred[kBuildWarps];
   __shared__ int s_ired[kBuildWarps];
@@ -315,12 +330,17 @@ __global__ void __launch_bounds__(kBuildThreads, 3) build_batch_kernel(const Bui
   // the last warp's first thread works out the box-only constants while the other warps load the
   // positions
   constexpr int kLoadThreads = kBuildThreads - 32;
+  int split = 1;   // every coordinate has an FP32 head + tail (bond vectors without the FP64 unit)
   if (tid == kLoadThreads) {
     double H[9];
     for (int k = 0; k < 9; ++k) {
       H[k] = a.box_in[9 * c + k];
       s_H[k] = H[k];
       a.box[9 * c + k] = H[k];
+      float hh, hl;
+      split &= split_f64(H[k], hh, hl) ? 1 : 0;
+      s_Hh[k] = hh;
+      s_Hl[k] = hl;
     }
     box_part1(H, a.R2, s_b1);
   }
@@ -336,10 +356,15 @@ __global__ void __launch_bounds__(kBuildThreads, 3) build_batch_kernel(const Bui
     finite &= (isfinite(x0) && isfinite(x1) && isfinite(x2)) ? 1 : 0;
     const float4 v = make_float4((float)x0, (float)x1, (float)x2, 0.f);
     s_p32[t] = v;
+    float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+    split &= (split_f64(x0, h.x, l.x) && split_f64(x1, h.y, l.y) && split_f64(x2, h.z, l.z)) ? 1 : 0;
+    s_ph[t] = h;
+    s_pl[t] = l;
     xm = fmaxf(xm, fmaxf(fabsf(v.x), fmaxf(fabsf(v.y), fabsf(v.z))));
   }
   xm = block_max_f(xm, s_fred);
   finite = __syncthreads_and(finite);
+  split = __syncthreads_and(split);
   if (tid == 0) {
     Pre32 q;
     int nimg = 0;
@@ -535,10 +560,22 @@ __global__ void __launch_bounds__(kBuildThreads, 3) build_batch_kernel(const Bui
     const int rev = s_boff[jl] + found;
     a.brev[base_b + bl] = (int)(base_b + rev);
     if (e < 8) reinterpret_cast<unsigned short *>(a.arev + i)[e] = (unsigned short)rev;
-    const ExactPair p = exact_pair(a.pos_in[3 * j], a.pos_in[3 * j + 1], a.pos_in[3 * j + 2], a.pos_in[3 * i],
-                                   a.pos_in[3 * i + 1], a.pos_in[3 * i + 2], s_H, n.x, n.y, n.z);
+    float dx, dy, dz;
+    if (split) {
+      const float4 hj = s_ph[jl], lj = s_pl[jl], hi = s_ph[il], li = s_pl[il];
+      const float n0 = (float)n.x, n1 = (float)n.y, n2 = (float)n.z;
+      dx = bond_component(hj.x, lj.x, hi.x, li.x, n0, n1, n2, s_Hh[0], s_Hl[0], s_Hh[3], s_Hl[3], s_Hh[6], s_Hl[6]);
+      dy = bond_component(hj.y, lj.y, hi.y, li.y, n0, n1, n2, s_Hh[1], s_Hl[1], s_Hh[4], s_Hl[4], s_Hh[7], s_Hl[7]);
+      dz = bond_component(hj.z, lj.z, hi.z, li.z, n0, n1, n2, s_Hh[2], s_Hl[2], s_Hh[5], s_Hl[5], s_Hh[8], s_Hl[8]);
+    } else {
+      const ExactPair p = exact_pair(a.pos_in[3 * j], a.pos_in[3 * j + 1], a.pos_in[3 * j + 2], a.pos_in[3 * i],
+                                     a.pos_in[3 * i + 1], a.pos_in[3 * i + 2], s_H, n.x, n.y, n.z);
+      dx = (float)p.dx;
+      dy = (float)p.dy;
+      dz = (float)p.dz;
+    }
     float4 A, Bv;
-    if (bond_record<float>(p, a.R1, a.R2, rev | (jl << 16), A, Bv)) atomicOr(&s_outer[il], 1);
+    if (bond_record_f32(dx, dy, dz, a.R1f, a.R2f, a.Wf, a.Kf, rev | (jl << 16), A, Bv)) atomicOr(&s_outer[il], 1);
     a.gA[base_b + bl] = A;
     a.gB[base_b + bl] = Bv;
     if (lists) s_u[bl] = A;
@@ -581,6 +618,10 @@ cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s) {
   a.Ntot = L.Ntot;
   a.R1 = L.R1;
   a.R2 = L.R2;
+  a.R1f = (float)L.R1;
+  a.R2f = (float)L.R2;
+  a.Wf = (float)(L.R2 - L.R1);
+  a.Kf = (float)(-0.5 * M_PI / (L.R2 - L.R1));
   a.atom_off = L.atom_off;
   a.pos_in = L.pos_in;
   a.box_in = L.box_in;
