@@ -230,7 +230,9 @@ int tersoff_ga_step(int32_t P, int32_t n_genes, int32_t n_par, double rate, cons
                     double *genes_out, double *params_out, int32_t *order, tersoff_stream stream);
 
 /* Loss and its gradient with respect to x = [D0, alpha, r0, beta, n, h] for every parameter set
- *  (x = [D0, alpha, r0, S, n, h, gamma, c, d] in the Tersoff form, tersoff_set_form).
+ *  (x = [D0, alpha, r0, S, n, h, gamma, c, d] in the Tersoff form, tersoff_set_form), Eq. 15-19, for
+ *  configurations of every size the batched evaluation takes (large ones through a split path:
+ *  evaluation, residual weights, tangent passes per atom slice).
  *  loss TERSOFF_LOSS_SQ or TERSOFF_LOSS_Z (the latter has a zero gradient term where S_q = 0);
  *  L device [P] double; dL device [P][6] ([P][9] in the Tersoff form) double. FP32 per-pair arithmetic with FP64 accumulation of
  *  the residual sums and of the gradient. Forces enter through the directional derivative

@@ -3,4 +3,6 @@
 
 namespace tsf {
 template cudaError_t launch_adjoint_variant<4, true>(const AdjParams &, size_t, unsigned, cudaStream_t);
+template cudaError_t launch_tangent_split<4, true>(const AdjParams &, const AdjSplit &, size_t, unsigned,
+                                                     cudaStream_t);
 }  // namespace tsf

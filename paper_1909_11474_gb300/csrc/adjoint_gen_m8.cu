@@ -3,4 +3,6 @@
 
 namespace tsf {
 template cudaError_t launch_adjoint_variant<8, true>(const AdjParams &, size_t, unsigned, cudaStream_t);
+template cudaError_t launch_tangent_split<8, true>(const AdjParams &, const AdjSplit &, size_t, unsigned,
+                                                     cudaStream_t);
 }  // namespace tsf

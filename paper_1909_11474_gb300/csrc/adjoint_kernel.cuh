@@ -138,11 +138,13 @@ __device__ __forceinline__ PConsts<Dual<K, float>> seed_consts(const PConsts<flo
 // One atom's tangent contribution for parameters q0.. (q0+K-1): accumulates dS_q/dx into G[q][x].
 // gT[q][t] receives the tangent t of loss term q (e, v, f) for parameter q0 + t; q0 is a runtime value,
 // so one copy of the dual core per neighbour count serves every pass.
+// v_j of neighbour j (configuration-local index jl) is vb[jl * vsa + k * vsk] (vb: this lane's first
+// element; shared memory in the single-CTA kernel, global memory in the split path).
 template <int M, int K, bool GEN>
 __device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB, const float *sC, int lb,
-                                             int lq, const float *vi, const float *vsm, int pl,
-                                             const float *aw, const PConsts<float> &Kf, const float (&xr)[9],
-                                             int q0, float (&gT)[3][K]) {
+                                             int lq, const float *vi, const float *vb, int64_t vsa, int64_t vsk,
+                                             int pl, const float *aw, const PConsts<float> &Kf,
+                                             const float (&xr)[9], int q0, float (&gT)[3][K]) {
   float ux[M], uy[M], uz[M], r[M], ir2[M], fc[M], fcp[M];
   int jl[M];
 #pragma unroll
@@ -180,8 +182,8 @@ __device__ __forceinline__ void atom_tangent(const float4 *sA, const float4 *sB,
     const float dx = r[j] * ux[j], dy = r[j] * uy[j], dz = r[j] * uz[j];
     // virial direction B d: W_xx, W_yy, W_zz, W_xy, W_yz, W_zx = -sum d_mu P_nu
     const float bx = a0 * dx + a5 * dz, by = a1 * dy + a3 * dx, bz = a2 * dz + a4 * dy;
-    const float *vj = vsm + (size_t)jl[j] * 3 * kAdjPT + pl;
-    const float fx = sld(&vj[0], 34) - vi[0], fy = sld(&vj[kAdjPT], 34) - vi[1], fz = sld(&vj[2 * kAdjPT], 34) - vi[2];
+    const float *vj = vb + jl[j] * vsa;
+    const float fx = vj[0] - vi[0], fy = vj[vsk] - vi[1], fz = vj[2 * vsk] - vi[2];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
       gT[1][t] -= Px[j].d[t] * bx + Py[j].d[t] * by + Pz[j].d[t] * bz;
@@ -384,7 +386,7 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
     if constexpr (MMAX >= MM) {                                                               \
       _Pragma("unroll 1") for (int q0 = 0; q0 < NX; q0 += kAdjK) {                            \
         float gT[3][kAdjK];                                                                   \
-        atom_tangent<MM, kAdjK, GEN>(sA, sB, sC, at.x, at.y, vi, vsm, pl, aw, K, xr, q0, gT);  \
+        atom_tangent<MM, kAdjK, GEN>(sA, sB, sC, at.x, at.y, vi, vsm + pl, 3 * PT, PT, pl, aw, K, xr, q0, gT); \
         add_tangents<NX, kAdjK>(G, q0, gT);                                                   \
       }                                                                                       \
     }                                                                                         \
@@ -409,6 +411,134 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
     const int pp = tile * PT + lp;
     if (pp < a.P) a.gpart[((size_t)pp * a.C + c) * NG + k] = t;
   }
+}
+
+// ---- split path: configurations spread over a cluster of CTAs by the batched schedule, or beyond the
+// adjoint kernel's shared memory. The batched kernel in evaluation mode gives E, W and F (F laid out
+// [Ntot][3][ldP]); adj_weights_kernel turns F into v = 2 (F - F*) in place and forms the residual
+// terms and the weights a_e, a_k of every (p, c); adj_tangent_split_kernel runs the dual passes of
+// one atom slice of the schedule per CTA (the tangents need only the slice's own bonds; v_j of a
+// neighbour in another slice is read from global memory); adj_gsum_kernel adds the slices of each
+// configuration in a fixed order.
+struct AdjSplit {
+  int P, C, ntiles;
+  int64_t ldP;                    // parameter-set stride of v and aw (ntiles * 32)
+  const CtaRec *recs;             // the bucket's records: configuration ci, slice r at ci * cl + r
+  int cl;                         // slices per configuration
+  int nitems;                     // configurations of the bucket
+  const int *atom_off;
+  const double *E, *W;            // [P][C], [P][C][6] from the evaluation
+  float *v;                       // [Ntot][3][ldP]: F on entry to the weights kernel, then v
+  const float4 *tF4;              // target forces in FP32 (x, y, z, |F*|^2)
+  const double *tE, *tW, *tF;
+  const uint8_t *tmask;
+  float *aw;                      // [C][7][ldP]: a_e, a_k (k = xx .. zx)
+  double *part, *dpart;           // [P][C][3], [C][3]
+  double *gsplit;                 // [P][nslices][NG]: tangent sums of every slice
+  int64_t nslices, slice0;        // split slices of all buckets; this bucket's first
+  double *gpart;                  // [P][C][NG]
+};
+
+__host__ __device__ inline size_t adj_split_smem_bytes(int nb, int nq, int ns) {
+  size_t b = (size_t)kNW * kAdjGMax * kAdjPT * sizeof(float);   // per-warp gradient sums
+  b += (size_t)nb * 2 * sizeof(float4) + ((size_t)nq * sizeof(float) + 31) / 32 * 32;
+  b += (size_t)ns * sizeof(int4) + 7 * kAdjPT * sizeof(float);
+  return b;
+}
+
+// One CTA per (atom slice, parameter tile): the tangent passes of the slice's atoms.
+template <int MMAX, bool GEN>
+__global__ void __launch_bounds__(kThreads, 1) adj_tangent_split_kernel(const AdjParams ap, const AdjSplit a) {
+  constexpr int PT = kAdjPT, NX = GEN ? 9 : 6, NG = 3 * NX;
+  extern __shared__ __align__(32) unsigned char smem[];
+  float *gred = reinterpret_cast<float *>(smem);              // [kNW][NG][PT]
+  const int tid = threadIdx.x, warp = tid >> 5, pl = tid & 31;
+  const int slice = blockIdx.x / a.ntiles, tile = blockIdx.x % a.ntiles;
+  const CtaRec rec = a.recs[slice];
+  const int c = rec.c;
+  const int p = tile * PT + pl;
+  const bool active = p < a.P;
+  PConsts<float> K;
+  {
+    const float4 *kc = reinterpret_cast<const float4 *>(ap.consts) + (GEN ? 4 : 2) * (active ? p : a.P - 1);
+    const float4 k0 = kc[0], k1 = kc[1];
+    K.D0 = k0.x; K.k1 = k0.y; K.k0 = k0.z; K.mha = k0.w;
+    K.beta = k1.x; K.h = k1.y; K.n = k1.z; K.inv2n = k1.w;
+    if constexpr (GEN) {
+      const float4 k2 = kc[2], k3 = kc[3];
+      K.cR = k2.x; K.kR1 = k2.y; K.kR0 = k2.z; K.hl = k2.w;
+      K.g0 = k3.x; K.gc2 = k3.y; K.d2 = k3.z; K.gcd = k3.w;
+    }
+  }
+  float xr[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if constexpr (GEN)
+#pragma unroll
+    for (int q = 0; q < 9; ++q) xr[q] = (float)ap.params[9 * (size_t)(active ? p : a.P - 1) + q];
+  const int s0 = rec.s0, ns = rec.ns, B0 = rec.B0, nb = rec.nb, Q0 = rec.Q0, nq = rec.nq;
+  float4 *sA = reinterpret_cast<float4 *>(gred + (size_t)kNW * kAdjGMax * PT);
+  float4 *sB = sA + nb;
+  float *sC = reinterpret_cast<float *>(sB + nb);
+  int4 *satom = reinterpret_cast<int4 *>(reinterpret_cast<unsigned char *>(sC) + ((size_t)nq * 4 + 31) / 32 * 32);
+  float *aw = reinterpret_cast<float *>(satom + ns);          // [7][PT]
+  for (int t = tid; t < nb; t += kThreads) {
+    sA[t] = ap.gA[B0 + t];
+    sB[t] = ap.gB[B0 + t];
+  }
+  for (int t = tid; t < nq; t += kThreads) sC[t] = ap.gcos[Q0 + t];
+  for (int t = tid; t < ns; t += kThreads)
+    satom[t] = make_int4(ap.boff[s0 + t] - B0, ap.poff[s0 + t] - Q0, ap.ameta[s0 + t] & 0xffff, 0);
+  for (int t = tid; t < 7 * PT; t += kThreads)
+    aw[t] = a.aw[((size_t)c * 7 + t / PT) * a.ldP + (size_t)tile * PT + t % PT];
+  __syncthreads();
+  const int64_t a0c = a.atom_off[c];
+  const float *vb = a.v + a0c * 3 * a.ldP + (int64_t)tile * PT + pl;
+  float G[NG];
+#pragma unroll
+  for (int k = 0; k < NG; ++k) G[k] = 0.f;
+  for (int li = warp; li < ns; li += kNW) {
+    const int4 at = satom[li];
+    const int m = at.z;
+    if (m > MMAX) continue;                        // flagged by the evaluation
+    const float *vp = vb + (int64_t)(s0 - a0c + li) * 3 * a.ldP;
+    const float vi[3] = {vp[0], vp[a.ldP], vp[2 * a.ldP]};
+#define TSF_TAN_SPLIT(MM)                                                                                 \
+  case MM:                                                                                                \
+    if constexpr (MMAX >= MM) {                                                                           \
+      _Pragma("unroll 1") for (int q0 = 0; q0 < NX; q0 += kAdjK) {                                        \
+        float gT[3][kAdjK];                                                                               \
+        atom_tangent<MM, kAdjK, GEN>(sA, sB, sC, at.x, at.y, vi, vb, 3 * a.ldP, a.ldP, pl, aw, K, xr, q0, gT); \
+        add_tangents<NX, kAdjK>(G, q0, gT);                                                               \
+      }                                                                                                   \
+    }                                                                                                     \
+    break;
+    switch (m) {
+      TSF_TAN_SPLIT(1) TSF_TAN_SPLIT(2) TSF_TAN_SPLIT(3) TSF_TAN_SPLIT(4)
+      TSF_TAN_SPLIT(5) TSF_TAN_SPLIT(6) TSF_TAN_SPLIT(7) TSF_TAN_SPLIT(8)
+      default: break;
+    }
+#undef TSF_TAN_SPLIT
+  }
+#pragma unroll
+  for (int k = 0; k < NG; ++k) gred[(warp * NG + k) * PT + pl] = G[k];
+  __syncthreads();
+  for (int idx = tid; idx < NG * PT; idx += kThreads) {
+    const int k = idx / PT, lp = idx % PT;
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) t += widen(gred[(w * NG + k) * PT + lp]);
+    const int pp = tile * PT + lp;
+    if (pp < a.P) a.gsplit[((size_t)pp * a.nslices + a.slice0 + slice) * NG + k] = t;
+  }
+}
+
+template <int MMAX, bool GEN>
+cudaError_t launch_tangent_split(const AdjParams &ap, const AdjSplit &as, size_t smem, unsigned grid,
+                                 cudaStream_t s) {
+  auto kern = adj_tangent_split_kernel<MMAX, GEN>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, kThreads, smem, s>>>(ap, as);   // the caller checks the launch
+  return cudaSuccess;
 }
 
 // Launch of one bucket's adjoint kernel (grid = configurations x parameter tiles, one CTA each).

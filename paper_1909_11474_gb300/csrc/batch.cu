@@ -87,6 +87,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   bp.mode = mode;
   bp.E = out.E;
   bp.F = out.F;
+  bp.f_ld = out.f_ld;
   bp.W = out.W;
   bp.tE = out.tE;
   bp.tW = out.tW;
@@ -99,8 +100,9 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   const bool timed = ctx.timer.begin(s);
   // several buckets run side by side on the context's side streams (forked from and joined back into
   // `s` by events), so one bucket's last items overlap the next bucket's first ones
+  auto runs = [&](const Bucket &b) { return b.nitems > 0 && (!out.split_only || b.adj_split); };
   int nlaunch = 0;
-  for (const Bucket &b : plan.buckets) nlaunch += b.nitems > 0;
+  for (const Bucket &b : plan.buckets) nlaunch += runs(b);
   const bool fork = nlaunch > 1 && ensure_side(ctx, (int)plan.buckets.size()) == cudaSuccess;
   if (fork) {
     cudaError_t e = cudaEventRecord(ctx.side_ev[0], s);
@@ -111,7 +113,7 @@ cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *pa
   for (const Bucket &b : plan.buckets) {
     const int k = bi;
     bp.counter = out.counters + bi++;
-    if (b.nitems == 0) continue;
+    if (!runs(b)) continue;
     bp.recs = plan.items.as<CtaRec>() + b.item_off;
     cudaError_t e = cudaSuccess;
     const cudaStream_t bs = s;

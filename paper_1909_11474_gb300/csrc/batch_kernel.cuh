@@ -435,7 +435,8 @@ struct BatchParams {
   unsigned wait_spins;             // polls of the staging wait before it gives up (a timeout)
   int mode;
   double *E;
-  void *F;
+  void *F;                         // [P][Ntot][3], or [Ntot][3][f_ld] when f_ld > 0
+  int64_t f_ld;
   double *W;
   const double *tE, *tW;
   const double *tF;                // [Ntot][3]: target forces (fitness)
@@ -700,11 +701,18 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
     const int i = s0 + li;
     if (a.mode == kModeEval) {
       if (active && a.F) {
-        const size_t o = ((size_t)p * a.Ntot + i) * 3;
         R *F = reinterpret_cast<R *>(a.F);
-        F[o] = Fx;
-        F[o + 1] = Fy;
-        F[o + 2] = Fz;
+        if (a.f_ld > 0) {
+          const size_t o = (size_t)i * 3 * a.f_ld + p;
+          F[o] = Fx;
+          F[o + a.f_ld] = Fy;
+          F[o + 2 * a.f_ld] = Fz;
+        } else {
+          const size_t o = ((size_t)p * a.Ntot + i) * 3;
+          F[o] = Fx;
+          F[o + 1] = Fy;
+          F[o + 2] = Fz;
+        }
       }
     } else if (mask & 4) {
       const R4 t = sld(&stF[li], 16);

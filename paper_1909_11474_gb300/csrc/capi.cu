@@ -124,6 +124,9 @@ int build_plan(tersoff_ctx *ctx, int precision) {
     b.precision = precision;
     b.smem = smem[k];
     b.adj_smem = adj_smem[k];
+    // the gradient of configurations spread over a cluster, or beyond the adjoint kernel's shared
+    // memory, takes the split path (evaluation, weights, tangent passes per atom slice)
+    b.adj_split = k.cl > 1 || adj_smem[k] > (size_t)optin;
     b.smem16 = (k.cl == 1 && k.mmax == 4 && precision == 32) ? smem16[k] : 0;
     b.smem12 = (k.cl == 1 && k.mmax == 4 && precision == 32) ? smem12[k] : 0;
     b.item_off = (int)recs.size();
@@ -152,6 +155,8 @@ int build_plan(tersoff_ctx *ctx, int precision) {
         q.pad = 0;
         q.inv_nat = 1.0 / (double)nat;
         recs.push_back(q);
+        if (b.adj_split)
+          b.adj_split_smem = std::max(b.adj_split_smem, tsf::adjoint_split_smem_bytes(q.nb, q.nq, q.ns));
       }
     }
     b.nitems = ((int)recs.size() - b.item_off) / k.cl;   // configurations in the bucket
@@ -371,7 +376,8 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   cudaDeviceSynchronize();
   tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.box, &c.build_status, &c.counters,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
-                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.ameta, &c.arev, &c.part, &c.dpart, &c.work, &c.tf4, &c.gpart,
+                         &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.ameta, &c.arev, &c.part, &c.dpart, &c.work,
+                         &c.tf4, &c.gpart, &c.adj_v, &c.adj_ew, &c.adj_aw, &c.adj_gsplit,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
                          &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_keys, &c.md_ke, &c.md_boxd};
@@ -774,15 +780,29 @@ int tersoff_param_grad(tersoff_ctx *ctx, const double *params, int32_t P, const 
   if (!tg->E || !tg->W || !tg->F || !tg->mask) return fail(ctx, TERSOFF_E_ARG, "null target pointer%s");
   if (loss != TERSOFF_LOSS_SQ && loss != TERSOFF_LOSS_Z) return fail(ctx, TERSOFF_E_ARG, "unknown loss%s");
   if (c.max_m > 8) return fail(ctx, TERSOFF_E_UNSUPPORTED, "an atom has more than 8 neighbours%s");
-  for (const tsf::Bucket &b : c.plan32.buckets)
-    if (b.cluster != 1)
-      return fail(ctx, TERSOFF_E_UNSUPPORTED, "the gradient kernel needs every configuration to fit one CTA%s");
+  if (int rc = build_plan(ctx, 32)) return rc;
   cudaSetDevice(c.device);
+  const int NG = c.form ? 27 : 18;
   TSF_CUDA(c.part.ensure((size_t)P * c.C * 3 * sizeof(double)));
   TSF_CUDA(c.dpart.ensure((size_t)c.C * 3 * sizeof(double)));
-  TSF_CUDA(c.gpart.ensure((size_t)P * c.C * (c.form ? 27 : 18) * sizeof(double)));
-  TSF_CUDA(c.work.ensure((size_t)P * 8 * sizeof(double)));
+  TSF_CUDA(c.gpart.ensure((size_t)P * c.C * NG * sizeof(double)));
+  TSF_CUDA(c.work.ensure((size_t)P * 16 * sizeof(double)));
   TSF_CUDA(c.tf4.ensure((size_t)c.Ntot * sizeof(tsf::dvec4)));
+  TSF_CUDA(c.counters.ensure(64 * sizeof(int)));
+  {
+    // split-path workspaces: v = 2 (F - F*) [Ntot][3][ldP], E and W [P][C](1 + 6), the weights
+    // [C][7][ldP], the tangent sums of every atom slice [P][slices][NG]
+    const int64_t ldP = ((int64_t)P + 31) / 32 * 32;
+    int64_t slices = 0;
+    for (const tsf::Bucket &b : c.plan32.buckets)
+      if (b.adj_split) slices += (int64_t)b.nitems * b.cluster;
+    if (slices > 0) {
+      TSF_CUDA(c.adj_v.ensure((size_t)c.Ntot * 3 * ldP * sizeof(float)));
+      TSF_CUDA(c.adj_ew.ensure((size_t)P * c.C * 7 * sizeof(double)));
+      TSF_CUDA(c.adj_aw.ensure((size_t)c.C * 7 * ldP * sizeof(float)));
+      TSF_CUDA(c.adj_gsplit.ensure((size_t)P * slices * NG * sizeof(double)));
+    }
+  }
   TSF_CUDA(tsf::launch_param_grad(c, params, P, tg->E, tg->W, tg->F, tg->mask, w, loss, L, dL, c.work.p, c.tf4.p,
                                   c.part.as<double>(), c.dpart.as<double>(), c.gpart.as<double>(), S(stream)));
   return TERSOFF_OK;

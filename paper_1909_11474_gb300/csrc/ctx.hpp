@@ -118,6 +118,8 @@ struct Bucket {
   int precision;   // 32 or 64
   size_t smem;     // dynamic shared memory per CTA
   size_t adj_smem; // dynamic shared memory per CTA of the adjoint kernel (FP32, single-CTA buckets)
+  bool adj_split = false;   // gradient through the split path (clusters, or beyond the adjoint's memory)
+  size_t adj_split_smem = 0;  // dynamic shared memory per CTA of the split path's tangent kernel
   bool uniform;    // every configuration of the bucket has the same atom and bond counts
   int nitems;      // configurations in the bucket
   int item_off;    // first record of the bucket (records are per configuration and cluster rank)
@@ -203,6 +205,7 @@ struct Ctx {
   DevBuf arev;    // [Ntot] int4: configuration-local reverse bonds of the first 8 bonds, 16 bits each
   BatchPlan plan32, plan64;
   DevBuf part, dpart, work, tf4, gpart;
+  DevBuf adj_v, adj_ew, adj_aw, adj_gsplit;   // split-path gradient workspaces
 
   // --- MD state ---
   int md_N = 0, md_M = 0;
@@ -266,6 +269,8 @@ struct BatchOut {
   bool pdl = false;   // launch the batched kernels with programmatic stream serialization
   int64_t wait_spins = -1;   // polls of the staging wait before it gives up (negative: built-in bound)
   int form = 0;       // 0: minimal (6 parameters), 1: Tersoff form (9 parameters, Eq. 8, free S)
+  int64_t f_ld = 0;   // > 0: F is [Ntot][3][f_ld] (parameter sets fastest) instead of [P][Ntot][3]
+  bool split_only = false;   // launch only the buckets whose gradient takes the split path
 };
 enum BatchMode { kModeEval = 0, kModeFitness = 1 };
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
@@ -296,6 +301,7 @@ int md_nve(Ctx &c, int N, double *pos, double *vel, const double *mass, const do
 
 // adjoint.cu
 size_t adjoint_smem_bytes(int nb, int nq, int nat);
+size_t adjoint_split_smem_bytes(int nb, int nq, int ns);   // split-path tangent kernel
 cudaError_t launch_param_grad(const Ctx &ctx, const double *params, int P, const double *tE, const double *tW,
                               const double *tF, const uint8_t *tmask, const double *w, int loss, double *L,
                               double *dL, void *consts, void *tf4, double *part, double *dpart, double *gpart,

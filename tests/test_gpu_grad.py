@@ -119,3 +119,66 @@ def test_param_grad_in_the_tersoff_form_matches_oracle():
         Lr, gr = oracle.loss_and_grad(cs, params[p], t, w=WTS, loss="sq")
         assert abs(L[p] - Lr) <= 1e-4 * abs(Lr) + 1e-9, (L[p], Lr)
         assert (np.abs(dL[p] - gr) <= GRAD_TOL * np.abs(gr).max()).all(), (dL[p], gr)
+
+
+def _uneven_largest():
+    """The two largest cells of the uneven batch (512 and 511 atoms: clusters of CTAs in the batched
+    schedule), a middle one and the smallest (7 atoms), with targets from the hidden parameters."""
+    w = I.workload_uneven(P=4, C=500)
+    cs_all = w["configs"]
+    order = np.argsort(cs_all.natoms, kind="stable")[::-1]
+    pick = [int(order[0]), int(order[1]), int(order[len(order) // 2]), int(order[-1])]
+    cs = I.pack_configs(*zip(*[cs_all.config(k) for k in pick]))
+    rng = np.random.default_rng(11)
+    return cs, w["hidden"], rng
+
+
+@pytest.mark.parametrize("loss", [0, 1])
+def test_param_grad_on_the_largest_uneven_cells(loss):
+    """Configurations spread over clusters of CTAs take the split gradient path (evaluation, weights,
+    per-slice tangent passes): loss and gradient against the oracle on the largest uneven-batch cells,
+    mixed with cells that take the single-CTA adjoint kernel."""
+    from paper_1909_11474_gb300 import binding
+    cs, hidden, rng = _uneven_largest()
+    Eh, Wh, Fh = oracle.evaluate_batch(cs, hidden[None, :])
+    wd = {"configs": cs, "noise": I.target_noise(rng, cs.C, cs.natoms)}
+    t = I.with_targets(wd, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0],
+                       mask=np.array([7, 7, 3, 5], np.uint8))
+    params = hidden[None, :] * (1 + 0.02 * rng.normal(size=(3, 6)))
+    ctx = binding.Context(0)
+    pos, box = to_device(cs)
+    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+    assert max(b["cluster"] for b in ctx.schedule_info()) > 1
+    L, dL = ctx.param_grad(torch.tensor(params, device="cuda"), targets_to_device(t), w=WTS, loss=loss)
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+    L, dL = L.cpu().numpy(), dL.cpu().numpy()
+    bound = _loss_bound(cs, t, params, loss)
+    for p in range(len(params)):
+        Lr, gr = oracle.loss_and_grad(cs, params[p], t, w=WTS, loss="sq" if loss == 0 else "z")
+        assert abs(L[p] - Lr) <= bound[p], (L[p], Lr, bound[p])
+        assert (np.abs(dL[p] - gr) <= GRAD_TOL * np.abs(gr).max()).all(), (dL[p], gr)
+
+
+def test_param_grad_split_path_in_the_tersoff_form():
+    """Nine parameters on the largest uneven cells: the split path's dual passes in the Tersoff form."""
+    from paper_1909_11474_gb300 import binding
+    cs, _, rng = _uneven_largest()
+    xg = np.array([3.2, 1.45, 2.25, 1.9, 0.65, -0.6, 0.06, 20.0, 3.0])
+    Eh, Wh, Fh = oracle.evaluate_batch(cs, xg[None, :])
+    wd = {"configs": cs, "noise": I.target_noise(rng, cs.C, cs.natoms)}
+    t = I.with_targets(wd, Eh[0] / cs.natoms, Wh[0] / cs.natoms[:, None], Fh[0],
+                       mask=np.array([7, 3, 5, 7], np.uint8))
+    params = xg[None, :] * (1 + 0.03 * rng.normal(size=(2, 9)))
+    ctx = binding.Context(0)
+    ctx.set_form(binding.FORM_TERSOFF)
+    pos, box = to_device(cs)
+    ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16)
+    L, dL = ctx.param_grad(torch.tensor(params, device="cuda"), targets_to_device(t), w=WTS, loss=0)
+    torch.cuda.synchronize()
+    assert ctx.get_status() == 0
+    L, dL = L.cpu().numpy(), dL.cpu().numpy()
+    for p in range(len(params)):
+        Lr, gr = oracle.loss_and_grad(cs, params[p], t, w=WTS, loss="sq")
+        assert abs(L[p] - Lr) <= 1e-4 * abs(Lr) + 1e-9, (L[p], Lr)
+        assert (np.abs(dL[p] - gr) <= GRAD_TOL * np.abs(gr).max()).all(), (dL[p], gr)
