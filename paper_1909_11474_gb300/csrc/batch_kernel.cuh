@@ -283,6 +283,134 @@ __device__ __forceinline__ void atom_core(const R (&ux)[M], const R (&uy)[M], co
   }
 }
 
+// atom_core for FP32 and the minimal form with an even neighbour bound M: the per-bond work of pass 1
+// and of the bond-order loop runs on bond pairs (2e, 2e+1) in packed FP32 pairs (two lanes of the
+// pair per instruction; the SFU operations stay scalar), the x and y components of the pass-2 sums
+// A_ij likewise; the pair loops and the final per-bond step are those of atom_core. Each packed
+// operation rounds as its scalar counterpart; only the energy sum runs in two partial sums.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+template <int M, bool INNER>
+__device__ __forceinline__ void atom_core_x2(const float (&ux)[M], const float (&uy)[M], const float (&uz)[M],
+                                             const float (&r)[M], const float (&ir2)[M], const float (&fc)[M],
+                                             const float (&fcp)[M], const float *cs, const PConsts<float> &K,
+                                             float &U, float (&Px)[M], float (&Py)[M], float (&Pz)[M]) {
+  static_assert(M % 2 == 0, "bond pairs");
+  constexpr int H = M / 2, NP = M * (M - 1) / 2;
+  // ---- pass 1: pair functions on bond pairs, then zeta (Eq. 7, 10) as atom_core
+  float2 fR[H], hA[H];
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const float2 t = __fmul2_rn(__fadd2_rn(make_float2(r[2 * h], r[2 * h + 1]), f2(-K.k0)), f2(K.k1));
+    const float2 x = make_float2(ex2(t.x), ex2(t.y));
+    hA[h] = __fmul2_rn(f2(K.D0), x);               // f_A / 2
+    fR[h] = __fmul2_rn(hA[h], x);
+  }
+  float zeta[M], tq[NP > 0 ? NP : 1];
+#pragma unroll
+  for (int j = 0; j < M; ++j) zeta[j] = 0.0f;
+  {
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+#pragma unroll
+      for (int k = j + 1; k < M; ++k) {
+        const float u = cs[q] - K.h;
+        const float t = K.beta * u;                 // g = t u, g' = 2 t
+        const float g = t * u;
+        tq[q] = t;
+        zeta[j] += fc[k] * g;
+        zeta[k] += fc[j] * g;
+        ++q;
+      }
+  }
+  // ---- bond order and its derivative on bond pairs
+  float cc[M], rad[M];
+  float2 Uh = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const float z0 = zeta[2 * h] > 1e-30f ? zeta[2 * h] : 1e-30f;
+    const float z1 = zeta[2 * h + 1] > 1e-30f ? zeta[2 * h + 1] : 1e-30f;
+    const float2 z = make_float2(z0, z1);
+    const float2 a = __fmul2_rn(f2(K.n), make_float2(lg2(z0), lg2(z1)));
+    const float2 zn = make_float2(ex2(a.x), ex2(a.y));               // zeta^n
+    const float2 u2 = __ffma2_rn(zn, f2(2.f), f2(2.f));
+    const float2 bl = __ffma2_rn(f2(K.inv2n), make_float2(lg2(u2.x), lg2(u2.y)), f2(-K.inv2n));
+    const float2 b = make_float2(ex2(bl.x), ex2(bl.y));              // (1 + zeta^n)^(-1/(2n))
+    const float2 bh = __fmul2_rn(b, hA[h]);
+    const float2 e = __ffma2_rn(bh, f2(-2.f), fR[h]);                // f_R - b f_A
+    const float2 zu = __fmul2_rn(z, u2);
+    float2 c = __fmul2_rn(__fmul2_rn(bh, zn), make_float2(rcp(zu.x), rcp(zu.y)));
+    const float2 mde = __fmul2_rn(f2(K.mha), __fadd2_rn(fR[h], e));
+    float2 rd;
+    if constexpr (INNER) {
+      Uh = __fadd2_rn(Uh, e);
+      rd = mde;
+    } else {
+      const float2 fch = make_float2(fc[2 * h], fc[2 * h + 1]);
+      Uh = __ffma2_rn(fch, e, Uh);
+      c = __fmul2_rn(fch, c);
+      rd = __ffma2_rn(__fmul2_rn(f2(0.5f), make_float2(fcp[2 * h], fcp[2 * h + 1])), e, __fmul2_rn(fch, mde));
+    }
+    cc[2 * h] = c.x;
+    cc[2 * h + 1] = c.y;
+    rad[2 * h] = rd.x;
+    rad[2 * h + 1] = rd.y;
+  }
+  U = Uh.x + Uh.y;
+
+  // ---- pass 2: dU_i/dd_ij (atom_core's loops, the x and y sums packed)
+  float2 Axy[M];
+  float Az[M], Rg[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    Axy[j] = make_float2(0.f, 0.f);
+    Az[j] = 0.f;
+    Rg[j] = 0.f;
+  }
+  {
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+#pragma unroll
+      for (int k = j + 1; k < M; ++k) {
+        const float w = (cc[j] * fc[k] + cc[k] * fc[j]) * tq[q];
+        const float2 ww = f2(w);
+        Axy[j] = __ffma2_rn(ww, make_float2(ux[k], uy[k]), Axy[j]);
+        Az[j] = __fmaf_rn(w, uz[k], Az[j]);
+        Axy[k] = __ffma2_rn(ww, make_float2(ux[j], uy[j]), Axy[k]);
+        Az[k] = __fmaf_rn(w, uz[j], Az[k]);
+        ++q;
+      }
+  }
+  bool sw = false;
+  if constexpr (!INNER) {
+#pragma unroll
+    for (int j = 0; j < M; ++j) sw |= (fcp[j] != 0.f);
+    sw = __any_sync(0xffffffffu, sw);
+  }
+  if (sw) {
+    int q = 0;
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+#pragma unroll
+      for (int k = j + 1; k < M; ++k) {
+        const float g = tq[q] * (cs[q] - K.h);
+        Rg[j] += cc[k] * g;
+        Rg[k] += cc[j] * g;
+        ++q;
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const float sj = ux[j] * Axy[j].x + uy[j] * Axy[j].y + uz[j] * Az[j];
+    const float coef = rad[j] + fcp[j] * Rg[j] - sj * ir2[j];
+    Px[j] = coef * ux[j] + ir2[j] * Axy[j].x;
+    Py[j] = coef * uy[j] + ir2[j] * Axy[j].y;
+    Pz[j] = coef * uz[j] + ir2[j] * Az[j];
+  }
+}
+
 // Passes 1 and 2 for one atom per atom slot, M = the warp's largest neighbour count.
 // sA/sB: bond records (u_x, u_y, u_z, r), (2/r, f_C, f_C', rev | j << 16); sC: pair cosines; lb/lq: this
 // atom's first bond / pair in shared memory; m: its neighbour count (<= M). EXACT: every slot has
@@ -338,7 +466,10 @@ __device__ __forceinline__ void atom_forward(const typename Vec4<R>::T *__restri
   }
 
   R U, Px[M], Py[M], Pz[M];
-  atom_core<M, INNER, R, R, GEN>(ux, uy, uz, r, ir2, fc, fcp, cs, K, U, Px, Py, Pz);
+  if constexpr (sizeof(R) == 4 && !GEN && M % 2 == 0)
+    atom_core_x2<M, INNER>(ux, uy, uz, r, ir2, fc, fcp, cs, K, U, Px, Py, Pz);
+  else
+    atom_core<M, INNER, R, R, GEN>(ux, uy, uz, r, ir2, fc, fcp, cs, K, U, Px, Py, Pz);
   // the stage rows of this atom's bonds, and its terms of the virial -sum_j d_ij (x) P_ij added to the
   // lane's running sums (a phantom bond has P = 0)
 #pragma unroll
@@ -503,6 +634,29 @@ template <int M, int PTT, typename R>
 __device__ __forceinline__ void gather_atom(const R *__restrict__ stage, int4 rv, int lb, int roff, int pl,
                                             R &Fx, R &Fy, R &Fz) {
   const int rw[4] = {rv.x, rv.y, rv.z, rv.w};
+  if constexpr (stage_packed<PTT, R>()) {
+    // (x, y) rows as packed FP32 pairs: the own rows and the reverse rows summed apart, two lanes of
+    // the pair per instruction
+    float2 o = make_float2(0.f, 0.f), q = make_float2(0.f, 0.f);
+    float oz = 0.f, qz = 0.f;
+#pragma unroll
+    for (int e = 0; e < M; ++e) {
+      const float *st = stage + (size_t)(lb + e) * stage_stride<PTT>();
+      o = __fadd2_rn(o, sld(reinterpret_cast<const float2 *>(st) + pl, 13));
+      oz += sld(&st[2 * PTT + pl], 13);
+    }
+#pragma unroll
+    for (int e = 0; e < M; ++e) {
+      const int rb = (rw[e >> 1] >> (16 * (e & 1))) & 0xffff;
+      const float *st = stage + (size_t)(rb + roff) * stage_stride<PTT>();
+      q = __fadd2_rn(q, sld(reinterpret_cast<const float2 *>(st) + pl, 15));
+      qz += sld(&st[2 * PTT + pl], 15);
+    }
+    Fx += o.x - q.x;
+    Fy += o.y - q.y;
+    Fz += oz - qz;
+    return;
+  }
 #pragma unroll
   for (int e = 0; e < M; ++e) {
     R x, y, z;

@@ -356,8 +356,9 @@ int tersoff_create(tersoff_ctx **out, int device) {
   if (cudaSetDevice(device) != cudaSuccess) return TERSOFF_E_CUDA;
   tersoff_ctx *ctx = new tersoff_ctx();
   ctx->c.device = device;
-  if (ctx->c.status.ensure(sizeof(unsigned)) != cudaSuccess ||
-      cudaMemset(ctx->c.status.p, 0, sizeof(unsigned)) != cudaSuccess) {
+  // two words: the context's status, then the last neighbour build's own
+  if (ctx->c.status.ensure(2 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(ctx->c.status.p, 0, 2 * sizeof(unsigned)) != cudaSuccess) {
     delete ctx;
     return TERSOFF_E_CUDA;
   }
@@ -374,7 +375,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
   Ctx &c = ctx->c;
   cudaSetDevice(c.device);
   cudaDeviceSynchronize();
-  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.box, &c.build_status, &c.counters,
+  tsf::DevBuf *bufs[] = {&c.status, &c.atom_off, &c.atom_cfg, &c.pos, &c.box, &c.counters,
                          &c.cnt, &c.nbr, &c.shift, &c.boff, &c.poff, &c.brev, &c.gA32, &c.gB32,
                          &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.ameta, &c.arev, &c.part, &c.dpart, &c.work,
                          &c.tf4, &c.gpart, &c.adj_v, &c.adj_ew, &c.adj_aw, &c.adj_gsplit,
@@ -528,7 +529,6 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(c.shift.ensure(N * M * sizeof(char4)));
   TSF_CUDA(c.boff.ensure((N + 1) * sizeof(int)));
   TSF_CUDA(c.poff.ensure((N + 1) * sizeof(int)));
-  TSF_CUDA(c.build_status.ensure(sizeof(unsigned)));
   TSF_CUDA(c.brev.ensure(bond_cap * sizeof(int)));
   TSF_CUDA(c.ameta.ensure(std::max<int64_t>(1, N) * sizeof(int)));
   TSF_CUDA(c.arev.ensure(std::max<int64_t>(1, N) * sizeof(int4)));
@@ -553,8 +553,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   if (!c.build_done) TSF_CUDA(cudaEventCreateWithFlags(&c.build_done, cudaEventDisableTiming));
   int nat_max = 1;
   for (int k = 0; k < C; ++k) nat_max = std::max(nat_max, cfg->atom_off[k + 1] - cfg->atom_off[k]);
-  TSF_CUDA(cudaMemsetAsync(c.status.p, 0, sizeof(unsigned), s));
-  TSF_CUDA(cudaMemsetAsync(c.build_status.p, 0, sizeof(unsigned), s));
+  TSF_CUDA(cudaMemsetAsync(c.status.p, 0, 2 * sizeof(unsigned), s));   // status and build status
   unsigned *st = c.status.as<unsigned>();
   tsf::BuildLaunch L = {};
   L.C = C;
@@ -579,7 +578,7 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   L.ameta = c.ameta.as<int>();
   L.arev = c.arev.as<int4>();
   L.status = st;
-  L.build_status = c.build_status.as<unsigned>();
+  L.build_status = c.status.as<unsigned>() + 1;
   L.nat_max = nat_max;
   TSF_CUDA(tsf::launch_build_batch(L, s));
   // neighbour counts and the build's status go back to pinned host memory on a side stream, beside
@@ -588,7 +587,8 @@ int tersoff_build_neighbors(tersoff_ctx *ctx, const tersoff_configs *cfg, double
   TSF_CUDA(cudaEventRecord(c.build_done, s));
   TSF_CUDA(cudaStreamWaitEvent(c.copy_stream, c.build_done, 0));
   TSF_CUDA(cudaMemcpyAsync(hp, c.cnt.p, N * sizeof(int), cudaMemcpyDeviceToHost, c.copy_stream));
-  TSF_CUDA(cudaMemcpyAsync(hp + N, c.build_status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c.copy_stream));
+  TSF_CUDA(cudaMemcpyAsync(hp + N, c.status.as<unsigned>() + 1, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                           c.copy_stream));
   TSF_CUDA(cudaEventRecord(c.stage_event, c.copy_stream));
   c.geom64 = false;
   c.pending = true;

@@ -176,7 +176,7 @@ struct GraphCache {
 struct Ctx {
   int device = 0;
   std::string err;
-  DevBuf status;   // unsigned
+  DevBuf status;   // unsigned [2]: the context's status bits, then those of the last neighbour build alone
 
   // --- batch build state ---
   bool built = false;
@@ -196,7 +196,6 @@ struct Ctx {
   PinnedBuf hp_stage;   // pinned staging: atom table uploads, neighbour-count readback, offsets
   cudaEvent_t stage_event = nullptr;   // recorded after the staging buffer's last upload
   DevBuf atom_off, atom_cfg, pos, box, cnt, nbr, shift, boff, poff, brev;
-  DevBuf build_status;        // status bits of the last neighbour build alone
   cudaStream_t copy_stream = nullptr;   // the build's count readback runs here, beside later calls
   cudaEvent_t build_done = nullptr;     // recorded after the build kernel on the caller's stream
   DevBuf counters;   // per-launch work counters of the persistent batched kernels

@@ -26,16 +26,23 @@ __device__ __forceinline__ void image_range(float ds, float rng, int &lo, int &h
 struct Pre32 {
   float Hi[9], rng[3], H[9], band, R2sq;
 };
-__device__ __forceinline__ bool member(const Pre32 &q, float dx, float dy, float dz, int n0, int n1, int n2,
-                                       const double *xj, const double *xi, const double *H, double R2sq) {
-  const float tx = (n0 * q.H[0] + n1 * q.H[3]) + n2 * q.H[6];
-  const float ty = (n0 * q.H[1] + n1 * q.H[4]) + n2 * q.H[7];
-  const float tz = (n0 * q.H[2] + n1 * q.H[5]) + n2 * q.H[8];
+// The image indices come as floats (f0, f1, f2: exact small integers) for the FP32 products and as
+// ints for the exact test.
+__device__ __forceinline__ bool member(const Pre32 &q, float dx, float dy, float dz, float f0, float f1, float f2,
+                                       int n0, int n1, int n2, const double *xj, const double *xi, const double *H,
+                                       double R2sq) {
+  const float tx = (f0 * q.H[0] + f1 * q.H[3]) + f2 * q.H[6];
+  const float ty = (f0 * q.H[1] + f1 * q.H[4]) + f2 * q.H[7];
+  const float tz = (f0 * q.H[2] + f1 * q.H[5]) + f2 * q.H[8];
   const float ex = dx + tx, ey = dy + ty, ez = dz + tz;
   const float r2 = ex * ex + ey * ey + ez * ez;
   if (r2 < q.R2sq - q.band) return true;
   if (r2 > q.R2sq + q.band) return false;
   return exact_pair(xj[0], xj[1], xj[2], xi[0], xi[1], xi[2], H, n0, n1, n2).r2 < R2sq;
+}
+__device__ __forceinline__ bool member(const Pre32 &q, float dx, float dy, float dz, int n0, int n1, int n2,
+                                       const double *xj, const double *xi, const double *H, double R2sq) {
+  return member(q, dx, dy, dz, (float)n0, (float)n1, (float)n2, n0, n1, n2, xj, xi, H, R2sq);
 }
 
 // f_C of Eq. 9 and its derivative.
@@ -204,7 +211,7 @@ __device__ __forceinline__ void build_flag(const BuildParams &a, unsigned bit) {
 
 // Dynamic shared memory of the build kernel for configurations of up to nat atoms.
 __host__ __device__ inline size_t build_smem_base(int nat) {
-  return (size_t)3 * nat * sizeof(float4) + (size_t)(4 * nat + 2) * sizeof(int);
+  return (size_t)4 * nat * sizeof(float4) + (size_t)(4 * nat + 2) * sizeof(int);
 }
 __host__ __device__ inline size_t build_smem_lists(int nat, int M) {
   return (size_t)nat * M * (sizeof(int2) + sizeof(float4));
@@ -308,7 +315,8 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
   float4 *s_p32 = reinterpret_cast<float4 *>(bsm);   // positions rounded to FP32 (membership test)
   float4 *s_ph = s_p32 + nmax;                         // FP32 heads and tails of the positions (bond vectors)
   float4 *s_pl = s_ph + nmax;
-  int *s_m = reinterpret_cast<int *>(s_pl + nmax);
+  float4 *s_fr = s_pl + nmax;                          // fractional coordinates x H^-1 of the FP32 positions
+  int *s_m = reinterpret_cast<int *>(s_fr + nmax);
   int *s_boff = s_m + nmax;            // [nmax + 1]
   int *s_poff = s_boff + nmax + 1;     // [nmax + 1]
   int *s_outer = s_poff + nmax + 1;
@@ -375,6 +383,13 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
     s_nmax = nimg;
   }
   __syncthreads();
+  for (int t = tid; t < nat; t += kBuildThreads) {
+    const float4 v = s_p32[t];
+    const float *h = s_q.Hi;
+    s_fr[t] = make_float4(v.x * h[0] + v.y * h[3] + v.z * h[6], v.x * h[1] + v.y * h[4] + v.z * h[7],
+                          v.x * h[2] + v.y * h[5] + v.z * h[8], 0.f);
+  }
+  __syncthreads();
   {
     const Pre32 q = s_q;
     const bool ok = s_ok != 0;
@@ -394,7 +409,42 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
       const double *xi = a.pos_in + 3 * i;
       const float4 xi32 = s_p32[li];
       int count = 0;
-      for (int jb = 0; ok && jb < nat; jb += 32) {
+      const float4 si = s_fr[li];
+      for (int jb = 0; single && ok && jb < nat; jb += 32) {
+        // at most one candidate image per j: n = round(-(s_j - s_i)) where |s_j - s_i + n| <= rng on
+        // every axis (the integers of the closed range [-ds - rng, -ds + rng]), |n| <= nimg
+        const int jl = jb + lane;
+        float dx = 0.f, dy = 0.f, dz = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f;
+        bool cand = false;
+        if (jl < nat) {
+          const float4 xj = s_p32[jl], sj = s_fr[jl];
+          dx = xj.x - xi32.x;
+          dy = xj.y - xi32.y;
+          dz = xj.z - xi32.z;
+          const float d0 = sj.x - si.x, d1 = sj.y - si.y, d2 = sj.z - si.z;
+          f0 = rintf(-d0);
+          f1 = rintf(-d1);
+          f2 = rintf(-d2);
+          const float lim = (float)nimg;
+          cand = fabsf(d0 + f0) <= q.rng[0] && fabsf(d1 + f1) <= q.rng[1] && fabsf(d2 + f2) <= q.rng[2] &&
+                 fabsf(f0) <= lim && fabsf(f1) <= lim && fabsf(f2) <= lim &&
+                 !(jl == li && f0 == 0.f && f1 == 0.f && f2 == 0.f);
+        }
+        const int j = a0 + (jl < nat ? jl : 0);
+        const double *xj = a.pos_in + 3 * (int64_t)j;
+        const int n0 = (int)f0, n1 = (int)f1, n2 = (int)f2;
+        const bool acc = cand && member(q, dx, dy, dz, f0, f1, f2, n0, n1, n2, xj, xi, s_H, R2sq);
+        const unsigned bal = __ballot_sync(0xffffffffu, acc);
+        const int w = count + __popc(bal & ((1u << lane) - 1u));
+        if (acc && w < M) {
+          const char4 sh = make_char4((signed char)n0, (signed char)n1, (signed char)n2, 0);
+          a.nbr[i * M + w] = j;
+          a.shift[i * M + w] = sh;
+          if (lists) s_list[li * M + w] = make_int2(jl, *reinterpret_cast<const int *>(&sh));
+        }
+        count += __popc(bal);
+      }
+      for (int jb = 0; !single && ok && jb < nat; jb += 32) {
         const int jl = jb + lane;
         int lo0 = 1, hi0 = 0, lo1 = 1, hi1 = 0, lo2 = 1, hi2 = 0;
         float dx = 0.f, dy = 0.f, dz = 0.f;
@@ -413,20 +463,6 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
         }
         const int j = a0 + (jl < nat ? jl : 0);
         const double *xj = a.pos_in + 3 * (int64_t)j;
-        if (single) {
-          const bool cand = lo0 <= hi0 && lo1 <= hi1 && lo2 <= hi2 && !(jl == li && lo0 == 0 && lo1 == 0 && lo2 == 0);
-          const bool acc = cand && member(q, dx, dy, dz, lo0, lo1, lo2, xj, xi, s_H, R2sq);
-          const unsigned bal = __ballot_sync(0xffffffffu, acc);
-          const int w = count + __popc(bal & ((1u << lane) - 1u));
-          if (acc && w < M) {
-            const char4 sh = make_char4((signed char)lo0, (signed char)lo1, (signed char)lo2, 0);
-            a.nbr[i * M + w] = j;
-            a.shift[i * M + w] = sh;
-            if (lists) s_list[li * M + w] = make_int2(jl, *reinterpret_cast<const int *>(&sh));
-          }
-          count += __popc(bal);
-          continue;
-        }
         int mine = 0;
         int buf[kNbrBuf];
         for (int n0 = lo0; n0 <= hi0; ++n0)
