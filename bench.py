@@ -65,7 +65,7 @@ ADJ_XU_PER_BOND = 6
 
 # ncu summary holding the batched kernel's DRAM bytes per launch, valid while these sources are unchanged
 TRAFFIC_PROFILE = "batch_kernel_ga_fitness_P200_C300.md"
-TRAFFIC_SOURCES = ("batch_kernel.cuh", "batch.cu", "common.cuh")
+TRAFFIC_SOURCES = ("batch_kernel.cuh", "batch.cu", "batch_launch.cuh", "common.cuh", "dual.cuh", "ctx.hpp")
 
 
 def _dist():

@@ -34,7 +34,7 @@ struct AdjParams {
 
 __host__ __device__ inline size_t adj_region0(int nb) {
   const size_t st = (size_t)nb * 3 * kAdjPT;
-  const size_t rd = std::max<size_t>((size_t)(kNW + 1) * kNRed * kAdjPT, (size_t)kNW * kAdjGMax * kAdjPT);
+  const size_t rd = std::max<size_t>((size_t)(kNW + 2) * kNRed * kAdjPT, (size_t)kNW * kAdjGMax * kAdjPT);
   return ((st > rd ? st : rd) * sizeof(float) + 31) / 32 * 32 / sizeof(float);
 }
 
@@ -318,21 +318,21 @@ __global__ void __launch_bounds__(kThreads, 1) adjoint_kernel(const AdjParams a)
   v[9] = sT;
   __syncthreads();
   float *red = stage;
-  float *tot = stage + kNW * kNRed * PT;
+  double *tot = reinterpret_cast<double *>(stage + kNW * kNRed * PT);   // sums over warps, FP64
 #pragma unroll
   for (int k = 0; k < kNRed; ++k) sst(&red[(warp * kNRed + k) * PT + pl], v[k], 17);
   __syncthreads();
   for (int idx = tid; idx < kNRed * PT; idx += kThreads) {
-    float t = 0.f;
+    float xw[kNW];
 #pragma unroll
-    for (int w = 0; w < kNW; ++w) t += sld(&red[w * kNRed * PT + idx], 18);
-    sst(&tot[idx], t, 19);
+    for (int w = 0; w < kNW; ++w) xw[w] = sld(&red[w * kNRed * PT + idx], 18);
+    sst(&tot[idx], exact_sum<kNW>(xw), 19);
   }
   __syncthreads();
   if (tid < PT) {
     double q[kNRed];
 #pragma unroll
-    for (int k = 0; k < kNRed; ++k) q[k] = (double)sld(&tot[k * PT + tid], 20);
+    for (int k = 0; k < kNRed; ++k) q[k] = sld(&tot[k * PT + tid], 20);
     const double invN = 1.0 / (double)nat;
     bool finite = isfinite(q[0]) && isfinite(q[8]);
     for (int k = 0; k < 6; ++k) finite = finite && isfinite(q[1 + k]);

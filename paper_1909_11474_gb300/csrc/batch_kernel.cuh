@@ -894,16 +894,32 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
   double *tot = red + NW * PTT * kNSum;                       // [ncta][PTT][kNSum] rank totals (rank 0)
   if (slot == 0) {
 #pragma unroll
-    for (int k = 0; k < kNSum; ++k) sst(&red[(warp * PTT + pl) * kNSum + (k ^ (pl & 7))], widen(v[k]), 17);
+    for (int k = 0; k < kNSum; ++k) {
+      // FP32 partials are stored as they are (summed exactly below), FP64 ones as doubles
+      if constexpr (sizeof(R) == 4) sst(&reinterpret_cast<float *>(red)[(warp * PTT + pl) * kNSum + (k ^ (pl & 7))], v[k], 17);
+      else sst(&red[(warp * PTT + pl) * kNSum + (k ^ (pl & 7))], widen(v[k]), 17);
+    }
   }
   __syncthreads();
   const bool red_thread = tid < kNSum * PTT;
   const int rl = tid >> 3, rk = tid & 7, rx = rk ^ (rl & 7);
   double T = 0.0;
   if (red_thread) {
-    T = sld(&red[rl * kNSum + rx], 18);
-#pragma unroll 4
-    for (int w = 1; w < NW; ++w) T += sld(&red[(w * PTT + rl) * kNSum + rx], 18);
+    if constexpr (sizeof(R) == 4) {   // the FP32 partials' exact sum, rounded once to FP64
+      float xw[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) xw[w] = sld(&reinterpret_cast<const float *>(red)[(w * PTT + rl) * kNSum + rx], 18);
+      T = exact_sum<NW>(xw);
+    } else {                          // FP64 partials: a pairwise tree in a fixed order
+      double sw[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) sw[w] = sld(&red[(w * PTT + rl) * kNSum + rx], 18);
+#pragma unroll
+      for (int h = 1; h < NW; h <<= 1)
+#pragma unroll
+        for (int w = 0; w + h < NW; w += 2 * h) sw[w] += sw[w + h];
+      T = sw[0];
+    }
   }
   if constexpr (CLUSTER) {
     if (red_thread) st_cluster(map_to_rank(smem_addr(tot + ((int)rank * PTT + rl) * kNSum + rx), 0), T);

@@ -145,6 +145,51 @@ __device__ __forceinline__ double widen(float f) {
 }
 __device__ __forceinline__ double widen(double d) { return d; }
 
+// Sum of N FP32 values rounded once to FP64, by integer arithmetic (the device's FP64 unit does one
+// conversion): each value becomes a 64-bit fixed-point integer aligned to the largest exponent (its
+// leading bit at bit 57, so N <= 16 values cannot overflow), the integers are added exactly, and the
+// sum is converted and rescaled by a power of two. The result is the exact sum rounded to FP64,
+// except that bits of a value lying more than 2^34 below the largest value's last bit are dropped
+// (an error below 2^-57 of the largest value) -- at least as accurate as FP64 recursive summation,
+// which rounds at every step. Subnormal values take part; an infinite or NaN value makes the sum an
+// FP64 sum of the widened values, which propagates it.
+template <int N>
+__device__ __forceinline__ double exact_sum(const float (&x)[N]) {
+  static_assert(N >= 1 && N <= 16, "fixed-point headroom");
+  unsigned u[N];
+  int emax = 1;
+  bool special = false;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    u[k] = __float_as_uint(x[k]);
+    const int e = (int)((u[k] >> 23) & 0xffu);
+    special = special || e == 0xff;
+    emax = max(emax, e);
+  }
+  if (special) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) s += (double)x[k];
+    return s;
+  }
+  long long acc = 0;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    int e = (int)((u[k] >> 23) & 0xffu);
+    unsigned m = u[k] & 0x7fffffu;
+    if (e != 0) m |= 0x800000u;
+    else e = 1;                                   // subnormal: no implicit bit, exponent 1
+    const int sh = emax - e;
+    const unsigned long long v = sh >= 64 ? 0ull : ((unsigned long long)m << 34) >> sh;
+    acc += (u[k] >> 31) ? -(long long)v : (long long)v;
+  }
+  if (acc == 0) return 0.0;
+  // acc * 2^(emax - 127 - 23 - 34): the power of two added to the exponent field (no overflow or
+  // underflow: |acc| < 2^62 and emax is in [1, 254])
+  const long long bits = __double_as_longlong(__ll2double_rn(acc)) + ((long long)(emax - 184) << 52);
+  return __longlong_as_double(bits);
+}
+
 // Sums over the lanes of one warp that share `lane % PT` (the lanes handling the same parameter
 // set): xor-shuffle over the atom-slot bits of the lane index.
 template <int PT, typename T>
