@@ -229,55 +229,54 @@ cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params
 
 // Fitness of every parameter set from the per-(p, c) residual terms of the batched kernel
 // (Eq. 15-19): S_q[p] = sum_c part[p][c][q] and D_q = sum_c dpart[c][q], all in FP64 in a fixed order
-// (lanes strided over c, then a fixed xor-shuffle tree). Zq = sqrt(S_q/D_q) (0 where D_q = 0),
-// Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not finite. One warp per parameter
-// set; small blocks spread the FP64 work over many SMs, and each block's first warp sums D_q once.
-constexpr int kFinWarps = 2;
+// (threads strided over c, a fixed xor-shuffle tree per warp, then the warps in order). Zq =
+// sqrt(S_q/D_q) (0 where D_q = 0), Z = sum_q w_q Zq, and Z = +inf when any residual sum of p is not
+// finite. One block of kFinWarps warps per parameter set, so that each thread sums only a few
+// configurations; every block forms D_q alongside.
+constexpr int kFinWarps = 4;
 
 __global__ void __launch_bounds__(kFinWarps * 32) fitness_finalize_kernel(
     int P, int C, const double *__restrict__ part, const double *__restrict__ dpart, double we, double wv,
     double wf, double *__restrict__ Z, double *__restrict__ Zq, double *__restrict__ S) {
-  __shared__ double s_d[3];
+  __shared__ double s_red[kFinWarps][6];
   pdl_wait();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == 0) {
-    double d[3] = {0.0, 0.0, 0.0};
-#pragma unroll 4
-    for (int c = lane; c < C; c += 32)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) d[q] += dpart[3 * c + q];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int p = blockIdx.x;
+  double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // S_e, S_v, S_f, D_e, D_v, D_f
+  const double *pp = part + (size_t)p * C * kResidualTerms;
+#pragma unroll 2
+  for (int c = tid; c < C; c += kFinWarps * 32)
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      for (int off = 16; off > 0; off >>= 1) d[q] += __shfl_xor_sync(0xffffffffu, d[q], off);
-      if (lane == 0) s_d[q] = d[q];
+      v[q] += pp[(size_t)c * kResidualTerms + q];
+      v[3 + q] += dpart[3 * c + q];
     }
-  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+    for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s_red[warp][k] = v[k];
   __syncthreads();
-  const int p = blockIdx.x * kFinWarps + warp;
-  if (p >= P) return;
-  double s[3] = {0.0, 0.0, 0.0};
-  const double *pp = part + (size_t)p * C * kResidualTerms;
-#pragma unroll 4
-  for (int c = lane; c < C; c += 32)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) s[q] += pp[(size_t)c * kResidualTerms + q];
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-    for (int off = 16; off > 0; off >>= 1) s[q] += __shfl_xor_sync(0xffffffffu, s[q], off);
-  if (lane == 0) {
+  if (tid == 0) {
+    double t[6];
+    for (int k = 0; k < 6; ++k) {
+      t[k] = s_red[0][k];
+      for (int w = 1; w < kFinWarps; ++w) t[k] += s_red[w][k];
+    }
     const double wq[3] = {we, wv, wf};
     double z = 0.0, zq[3];
     bool finite = true;
     for (int q = 0; q < 3; ++q) {
-      finite = finite && isfinite(s[q]);
-      zq[q] = s_d[q] > 0.0 ? sqrt(s[q] / s_d[q]) : 0.0;
+      finite = finite && isfinite(t[q]);
+      zq[q] = t[3 + q] > 0.0 ? sqrt(t[q] / t[3 + q]) : 0.0;
       z += wq[q] * zq[q];
     }
     Z[p] = finite ? z : INFINITY;
     if (Zq)
       for (int q = 0; q < 3; ++q) Zq[(size_t)p * 3 + q] = zq[q];
     if (S)
-      for (int q = 0; q < 3; ++q) S[(size_t)p * 3 + q] = s[q];
+      for (int q = 0; q < 3; ++q) S[(size_t)p * 3 + q] = t[q];
   }
 }
 
@@ -285,7 +284,7 @@ cudaError_t launch_fitness_finalize(int P, int C, const double *part, const doub
                                     double we, double wv, double wf, double *Z, double *Zq, double *S, bool pdl,
                                     cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((P + kFinWarps - 1) / kFinWarps));
+  cfg.gridDim = dim3((unsigned)P);
   cfg.blockDim = dim3(kFinWarps * 32);
   cfg.stream = s;
   // the batched kernel gives no early trigger, so this launch starts when it completes; the attribute
