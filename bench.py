@@ -273,8 +273,9 @@ def run_ours(args):
     launches = ctx.kernel_launches() - n0
     t_build = timed(lambda: ctx.build_neighbors(cs.atom_off, pos, box, 2.8, 3.2, 16), args.steps)
     ctx.build_info()                              # the host side of the last build
+    t_fit = timed(fitness_only, args.steps)       # the fitness call as a user makes it (graph replay)
     ctx.profile(True)                             # CUDA events around the batched kernel alone
-    t_fit = timed(fitness_only, args.steps)
+    timed(fitness_only, args.steps)               # (direct launches while the events are on)
     n_kern, ms_kern = ctx.profile_read()
     ctx.profile(False)
     torch.cuda.synchronize()

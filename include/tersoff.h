@@ -119,8 +119,9 @@ int tersoff_build_info(tersoff_ctx *ctx, int64_t *ntot, int64_t *nbonds, int32_t
  *  params    device [P][6] double (order of Eq. 16), P >= 1; [P][9] in the Tersoff form
  *            (tersoff_set_form)
  *  precision 32: per-pair arithmetic in FP32; each warp sums its atoms' energy and virial terms in
- *            FP32 and these per-warp partial sums are added in FP64 (over warps and cluster ranks,
- *            in a fixed order); F in float;
+ *            FP32; the sum of a CTA's per-warp partial sums is their exact sum rounded once to FP64
+ *            (fixed-point integer accumulation), and the sums over cluster ranks are FP64 additions,
+ *            all in a fixed order; F in float;
  *            64: everything in FP64, F in double
  *  E         device [P][C] double, total energy (eV)             -- may be NULL
  *  F         device [P][Ntot][3] float or double (see precision) -- may be NULL

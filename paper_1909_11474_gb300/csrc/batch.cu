@@ -204,7 +204,9 @@ cudaError_t autotune_batch(const Ctx &ctx, BatchPlan &plan, const double *params
           float t = 0.f;
           e = time_launch(t);
           ++count;
-          if (e == cudaSuccess && t < bt) {
+          // a later candidate must be more than 1 % faster: the first (the built-in schedule) wins
+          // a tie within the timing noise
+          if (e == cudaSuccess && t < 0.99f * bt) {
             bt = t;
             best_pc = pc;
             best_nw = nw;
