@@ -634,29 +634,6 @@ template <int M, int PTT, typename R>
 __device__ __forceinline__ void gather_atom(const R *__restrict__ stage, int4 rv, int lb, int roff, int pl,
                                             R &Fx, R &Fy, R &Fz) {
   const int rw[4] = {rv.x, rv.y, rv.z, rv.w};
-  if constexpr (stage_packed<PTT, R>()) {
-    // (x, y) rows as packed FP32 pairs: the own rows and the reverse rows summed apart, two lanes of
-    // the pair per instruction
-    float2 o = make_float2(0.f, 0.f), q = make_float2(0.f, 0.f);
-    float oz = 0.f, qz = 0.f;
-#pragma unroll
-    for (int e = 0; e < M; ++e) {
-      const float *st = stage + (size_t)(lb + e) * stage_stride<PTT>();
-      o = __fadd2_rn(o, sld(reinterpret_cast<const float2 *>(st) + pl, 13));
-      oz += sld(&st[2 * PTT + pl], 13);
-    }
-#pragma unroll
-    for (int e = 0; e < M; ++e) {
-      const int rb = (rw[e >> 1] >> (16 * (e & 1))) & 0xffff;
-      const float *st = stage + (size_t)(rb + roff) * stage_stride<PTT>();
-      q = __fadd2_rn(q, sld(reinterpret_cast<const float2 *>(st) + pl, 15));
-      qz += sld(&st[2 * PTT + pl], 15);
-    }
-    Fx += o.x - q.x;
-    Fy += o.y - q.y;
-    Fz += oz - qz;
-    return;
-  }
 #pragma unroll
   for (int e = 0; e < M; ++e) {
     R x, y, z;
