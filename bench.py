@@ -159,6 +159,33 @@ def profiled_traffic():
     return None
 
 
+def executed_block(b_time, fp32_peak):
+    """The FP32 arithmetic the kernel executes (not the algorithmic model) against the same peak: how
+    busy the FP32 lanes are. The kernel folds the method's formulas (sums of unit vectors before the
+    projection, constants folded), so it executes fewer FLOP than the formula listing counts."""
+    ex = profiled_executed_flop()
+    if ex is None:
+        return None
+    a = ex / b_time / 1e12
+    return {"flop_per_launch": ex, "achieved": round(a, 3), "frac": round(a / fp32_peak, 4),
+            "source": "ncu thread-instruction counters of the committed profile (FFMA, FADD, FMUL and packed forms)"}
+
+
+def profiled_executed_flop():
+    """FP32 FLOP the batched kernel executes per launch (ncu instruction counters, committed in the
+    profile summary: 2 FFMA + FADD + FMUL + 4 FFMA2 + 2 FADD2 + 2 FMUL2 per thread instruction), or None
+    when the kernel's sources changed after that capture."""
+    p = os.path.join(ROOT, "profiles", TRAFFIC_PROFILE)
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        for line in f:
+            m = re.match(r"^executed_fp32: flop_per_launch=(\d+) kernel_sources_sha256=([0-9a-f]{64})\s*$", line)
+            if m:
+                return int(m.group(1)) if m.group(2) == kernel_sources_digest() else None
+    return None
+
+
 def flop_model(ctx, P):
     """Algorithmic FLOP and XU ops of one fitness evaluation over all (p, c), and the bond and ordered
     bond-pair counts of the build."""
@@ -343,6 +370,7 @@ def run_ours(args):
                                f"MEASURED_PEAKS.json, {peak_src}); measured FFMA chains "
                                f"{mpeaks['fp32_fma_flops'] / 1e12:.2f} TFLOP/s",
                 "frac_of_measured_ffma": round(achieved * 1e12 / mpeaks["fp32_fma_flops"], 4),
+                "executed": executed_block(b_time, fp32_peak),
                 "xu": {"achieved_tops": round(xu_rate, 4), "ops_per_launch": xu,
                        "peak_tops": round(mpeaks["xu_ex2_ops"] / 1e12, 3),
                        "frac": round(xu_rate * 1e12 / mpeaks["xu_ex2_ops"], 4),
