@@ -169,8 +169,8 @@ int tersoff_fitness(tersoff_ctx *ctx, const double *params, int32_t P, const ter
  *  TERSOFF_E_ARG with the byte count in tersoff_last_error and launches nothing.
  *  If the address look-up in tersoff_create failed, the first call on that device repeats it; make
  *  that call before any stream capture. Every call shares the one array and leaves its contents
- *  behind; the call clears its work counters (the only part that must start at zero) itself with a
- *  cudaMemsetAsync on `stream`. Two calls whose work overlaps on the GPU (different streams, or
+ *  behind; the call's first kernel zeroes its work counters (the only part that must start at zero)
+ *  on `stream`. Two calls whose work overlaps on the GPU (different streams, or
  *  different contexts on the same device) race on the array: serialise them. */
 int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, int32_t P,
                            const tersoff_targets *tg, const double *w, int32_t precision, double *Z,

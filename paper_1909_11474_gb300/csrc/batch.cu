@@ -54,19 +54,18 @@ cudaError_t ensure_side_streams(const Ctx &ctx) { return ensure_side(ctx, kSide)
 cudaError_t launch_batch(const Ctx &ctx, const BatchPlan &plan, const double *params, int P,
                          int mode, const BatchOut &out, cudaStream_t s) {
   const bool f64 = plan.precision == 64;
-  // work counters first, so that the preparation kernel and the batched kernel are adjacent launches
-  // (programmatic dependent launch overlaps the latter's start with the former)
-  cudaError_t ez = cudaMemsetAsync(out.counters, 0, plan.buckets.size() * sizeof(int), s);
-  if (ez != cudaSuccess) return ez;
-  // per-call preparation: per-parameter-set constants
+  // per-call preparation: per-parameter-set constants, and the launches' work counters set to zero
+  // (the batched kernel claims its first item without the counter and waits for this kernel before
+  // its first claim from it)
   {
-    const unsigned blocks = (unsigned)((P + 255) / 256);
+    const int ncounters = (int)plan.buckets.size();
+    const unsigned blocks = (unsigned)((std::max(P, ncounters) + 255) / 256);
     if (f64)
       prep_kernel<double><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<double *>(out.consts), out.form,
-                                                 ctx.Ntot, nullptr, nullptr);
+                                                 ctx.Ntot, nullptr, nullptr, out.counters, ncounters);
     else
       prep_kernel<float><<<blocks, 256, 0, s>>>(P, params, reinterpret_cast<float *>(out.consts), out.form,
-                                                ctx.Ntot, nullptr, nullptr);
+                                                ctx.Ntot, nullptr, nullptr, out.counters, ncounters);
     cudaError_t e = launched(1);
     if (e != cudaSuccess) return e;
   }

@@ -977,17 +977,33 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
   }
   unsigned phase = 0;
   const int nitems = a.nconf * a.nchunks;
+  // the first item of a CTA (cluster) is its index in the grid; later ones are claimed from the
+  // counter, which the preparation kernel zeroes: the claiming thread waits for it first
+  const int nclusters = (int)(gridDim.x / ncta);
+  bool first = true;
   for (;;) {
     if constexpr (CLUSTER) {
       if (rank == 0 && tid == 0) {
-        const int v = atomicAdd(a.counter, 1);
+        int v = (int)(blockIdx.x / ncta);
+        if (!first) {
+          pdl_wait();
+          v = nclusters + atomicAdd(a.counter, 1);
+        }
         for (unsigned r = 0; r < ncta; ++r) st_cluster(map_to_rank(smem_addr(&s_item), r), v);
       }
       cluster_sync_all();
     } else {
-      if (tid == 0) s_item = atomicAdd(a.counter, 1);
+      if (tid == 0) {
+        int v = (int)blockIdx.x;
+        if (!first) {
+          pdl_wait();
+          v = nclusters + atomicAdd(a.counter, 1);
+        }
+        s_item = v;
+      }
       __syncthreads();
     }
+    first = false;
     const int it = s_item;
     if (it >= nitems) break;
     const int ci = it / a.nchunks, chunk = it % a.nchunks;
@@ -1144,9 +1160,11 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
 // precision as R4 (x, y, z, |F|^2).
 template <typename R>
 __global__ void prep_kernel(int P, const double *__restrict__ params, R *__restrict__ consts, int form,
-                            int64_t Ntot, const double *__restrict__ tF, typename Vec4<R>::T *__restrict__ tF4) {
+                            int64_t Ntot, const double *__restrict__ tF, typename Vec4<R>::T *__restrict__ tF4,
+                            int *__restrict__ counters = nullptr, int ncounters = 0) {
   pdl_trigger();   // the batched kernel may start staging geometry; it waits before reading our output
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < ncounters) counters[t] = 0;   // the work counters of the batched launches that follow
   if (t < P && form == kFormMinimal) {
     const double *x = params + 6 * t;
     const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];

@@ -95,7 +95,7 @@ extern "C" int tersoff_fitness_static(tersoff_ctx *ctx, const double *params, in
 
   // every scratch element read by the kernels is written earlier in the same call (the constants by
   // the prep kernel, every (p, c) residual term and every configuration's target-norm terms by the
-  // batch kernel); the work counters, which must start at zero, are cleared by the launch itself
+  // batch kernel); the work counters, which must start at zero, are zeroed by the prep kernel
   tsf::BatchOut o = {};
   o.tE = tg->E;
   o.tW = tg->W;
