@@ -380,7 +380,7 @@ void tersoff_destroy(tersoff_ctx *ctx) {
                          &c.gcos32, &c.gA64, &c.gB64, &c.gcos64, &c.ameta, &c.arev, &c.part, &c.dpart, &c.work,
                          &c.tf4, &c.gpart, &c.adj_v, &c.adj_ew, &c.adj_aw, &c.adj_gsplit,
                          &c.plan32.items, &c.plan64.items, &c.md_pos, &c.md_cnt, &c.md_nbr,
-                         &c.md_shift, &c.md_rev, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
+                         &c.md_shift, &c.md_cells, &c.md_cellcnt, &c.md_Pij, &c.md_red,
                          &c.md_keys, &c.md_ke, &c.md_boxd};
   for (auto *b : bufs) b->release();
   c.hp_stage.release();

@@ -208,7 +208,7 @@ struct Ctx {
 
   // --- MD state ---
   int md_N = 0, md_M = 0;
-  DevBuf md_pos, md_cnt, md_nbr, md_shift, md_rev, md_cells, md_cellcnt, md_Pij, md_red, md_keys, md_ke;
+  DevBuf md_pos, md_cnt, md_nbr, md_shift, md_cells, md_cellcnt, md_Pij, md_red, md_keys, md_ke;
   DevBuf md_boxd;
 
   // --- measurement: CUDA events around each batched-kernel launch sequence, on its stream ---

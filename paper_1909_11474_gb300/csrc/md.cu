@@ -1,16 +1,16 @@
 // md.cu -- MD-scale force call: one large periodic cell, one parameter set, neighbour rebuild by a
 // cell list plus energy, forces and virial (Eq. 1-14 of arXiv:1909.11474), every call.
 //
-// Coordinates. Every atom's cell coordinate w = x H^-1 nc is split, in FP64, into its floor C and an
-// in-cell coordinate u = w - C in [0, 1), stored in FP32, and C into an integer wrap m and a cell
-// index c (C = m nc + c). The force kernel builds a bond to an atom of a neighbouring cell (offset o
-// in {-1,0,1}^3) as d = sum_k (o_k + u_j,k - u_i,k) E_k with the cell edge vectors E_k = H_k / nc_k,
-// all in FP32 and accurate to ~1e-6 A whatever the box size; its image shift is n = kw + m_i - m_j
-// (kw = the periodic wrap of the neighbouring cell). The pair search works in Cartesian coordinates
-// relative to a brick of cells (a few cell edges long, so equally accurate). Membership uses the FP32
-// distance where it is farther than a rounding margin from R2, and the exact FP64 test of the batched
-// build otherwise, so the lists equal the batched build's bit for bit; they are sorted to the same
-// (j, n) order.
+// Coordinates. Every atom's cell coordinate w = x H^-1 nc is split into its floor C and an in-cell
+// coordinate u = w - C in [0, 1), and C into an integer wrap m and a cell index c (C = m nc + c). The
+// atom is kept as its in-cell Cartesian position X = u E (FP32; E = the cell edge vectors H_k / nc_k
+// as rows). A bond to an atom of a neighbouring cell (offset o in {-1,0,1}^3) is d = o E + (X_j - X_i),
+// in FP32 and accurate to ~1e-6 A whatever the box size; its image shift is n = kw + m_i - m_j (kw =
+// the periodic wrap of the neighbouring cell). The FP32 d of (j, i) is exactly the negation of that of
+// (i, j), so the two atoms of a pair decide membership alike. Membership uses the FP32 distance where
+// it is farther than a rounding margin from R2, and the exact FP64 test of the batched build
+// otherwise, so the lists equal the batched build's bit for bit; they are sorted to the same (j, n)
+// order.
 #include <math.h>
 
 #include <algorithm>
@@ -45,21 +45,26 @@ struct MdGeom {
   float R1f, R2f, inv_wf, fcp_kf;
 };
 
-// Cell of every atom; the cell's slots hold (u, atom index) so the pair search reads one record per
-// candidate. Every atom's neighbour count starts at zero here; an atom that gets no slot (non-finite
-// position, full cell) keeps an empty list and the call is flagged.
+// Cartesian vector of a separation v in cell units: v0 E_0 + v1 E_1 + v2 E_2.
+__device__ __forceinline__ float3 md_cart(const MdGeom &G, float v0, float v1, float v2) {
+  return make_float3(v0 * G.E[0] + v1 * G.E[3] + v2 * G.E[6], v0 * G.E[1] + v1 * G.E[4] + v2 * G.E[7],
+                     v0 * G.E[2] + v1 * G.E[5] + v2 * G.E[8]);
+}
+
+// Cell of every atom; the cell's slots hold (X, atom index) so the search reads one record per
+// candidate. An atom that gets no slot (non-finite position, full cell) gets cell index -1 and an
+// empty list here; no other atom sees it, and the call is flagged. The search writes every other count.
 //
 // The cell coordinates w = x Hn are formed in FP32 head + tail arithmetic (products split exactly by
 // FMA, sums by two-sum), accurate to ~2^-44 |w|; below |w| = 2^16 cells that is under the FP32 rounding
 // of u itself. Other positions take FP64 arithmetic. The floor C is then that of head + tail, and
 // u = w - C is rounded once to FP32: any consistent (C, u) serves the search and the bond vectors.
 __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdGeom G,
-                                int *__restrict__ cellcnt, float4 *__restrict__ cellu,
-                                float4 *__restrict__ u4, int4 *__restrict__ m4, int *__restrict__ cnt,
+                                int *__restrict__ cellcnt, float4 *__restrict__ cellx,
+                                float4 *__restrict__ x4, int4 *__restrict__ m4, int *__restrict__ cnt,
                                 unsigned *status) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  cnt[i] = 0;
   const double x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
   float xh[3], xl[3];
   bool fast = split_f64(x, xh[0], xl[0]);
@@ -115,8 +120,9 @@ __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdG
     }
     if (!ok) {
       set_status(status, TERSOFF_STATUS_NONFINITE);
-      u4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      m4[i] = make_int4(0, 0, 0, 0);
+      x4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      m4[i] = make_int4(0, 0, 0, -1);
+      cnt[i] = 0;
       return;
     }
 #pragma unroll
@@ -135,79 +141,213 @@ __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdG
     cc[k] = Ci[k] - m * n;
   }
   const int cell = (cc[0] * G.nc[1] + cc[1]) * G.nc[2] + cc[2];
-  u4[i] = make_float4(uu[0], uu[1], uu[2], 0.f);
-  m4[i] = make_int4(mm[0], mm[1], mm[2], cell);
+  const float3 X = md_cart(G, uu[0], uu[1], uu[2]);
+  x4[i] = make_float4(X.x, X.y, X.z, 0.f);
   const int slot = atomicAdd(&cellcnt[cell], 1);
-  if (slot < kMdCap) cellu[cell * kMdCap + slot] = make_float4(uu[0], uu[1], uu[2], __int_as_float(i));
-  else set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+  if (slot < kMdCap) {
+    cellx[cell * kMdCap + slot] = make_float4(X.x, X.y, X.z, __int_as_float(i));
+  } else {
+    set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+    cnt[i] = 0;
+  }
+  m4[i] = make_int4(mm[0], mm[1], mm[2], slot < kMdCap ? cell : -1);
 }
 
-// Code of the periodic wrap of cell coordinates c (each in [-1, nc]): (w0+1) << 4 | (w1+1) << 2 | (w2+1).
-// The code of the opposite wrap is 42 - code.
-__device__ __forceinline__ unsigned wrap_code(const MdGeom &G, int c0, int c1, int c2) {
-  const int w0 = c0 < 0 ? 0 : (c0 >= G.nc[0] ? 2 : 1), w1 = c1 < 0 ? 0 : (c1 >= G.nc[1] ? 2 : 1),
-            w2 = c2 < 0 ? 0 : (c2 >= G.nc[2] ? 2 : 1);
-  return (unsigned)((w0 << 4) | (w1 << 2) | w2);
-}
-constexpr unsigned kWrapNeg = 42u;
+// Offset code of a neighbouring cell o in {-1,0,1}^3: (o0+1) << 4 | (o1+1) << 2 | (o2+1). The code of
+// -o is 42 - code.
+constexpr unsigned kOffNeg = 42u;
 
-// One candidate pair at Cartesian separation d (FP32): the FP32 distance decides outside the
-// rounding band, the exact FP64 test inside it. The test is symmetric (the FP64 separation of
-// (j, i, -n) is exactly the negated one of (i, j, n)), so deciding a pair once decides both entries.
+// FP32 separation d = o E + (X_j - X_i) of an atom j of the neighbouring cell with offset code `code`
+// (the products o_k E_k are exact, the sums rounded in a fixed order), so the d of (j, i) is exactly
+// the negation of that of (i, j).
+__device__ __forceinline__ float3 md_sep(const MdGeom &G, unsigned code, float4 xi, float4 xj) {
+  const float o0 = (float)((int)(code >> 4) - 1), o1 = (float)((int)((code >> 2) & 3u) - 1),
+              o2 = (float)((int)(code & 3u) - 1);
+  const float3 b = md_cart(G, o0, o1, o2);
+  return make_float3(__fadd_rn(b.x, __fsub_rn(xj.x, xi.x)), __fadd_rn(b.y, __fsub_rn(xj.y, xi.y)),
+                     __fadd_rn(b.z, __fsub_rn(xj.z, xi.z)));
+}
+
+// Periodic wrap of the coordinate a = c + o (o in {-1, 0, 1}) on an axis of n cells: -1, 0 or 1, and
+// the wrapped coordinate g.
+__device__ __forceinline__ int md_wrap(int a, int n, int &g) {
+  if (a < 0) {
+    g = a + n;
+    return -1;
+  }
+  if (a >= n) {
+    g = a - n;
+    return 1;
+  }
+  g = a;
+  return 0;
+}
+
+// Membership of a candidate at FP32 separation d: the FP32 distance decides outside the rounding band
+// around R2^2, the exact FP64 test of the batched build inside it (image shift n = wrap + m_i - m_j),
+// so that every decision is the exact one.
 __device__ __forceinline__ bool md_pair_in(const MdGeom &G, const double *__restrict__ pos,
-                                           const int4 *__restrict__ m4, int i, int j, unsigned code,
-                                           float dx, float dy, float dz) {
-  const float r2 = dx * dx + dy * dy + dz * dz;
+                                           const int4 *__restrict__ m4, int i, int j, int4 mi, int w0, int w1,
+                                           int w2, float3 d) {
+  const float r2 = __fmaf_rn(d.z, d.z, __fmaf_rn(d.y, d.y, __fmul_rn(d.x, d.x)));
   if (r2 > G.cut2_hi) return false;
   if (r2 < G.cut2_lo) return true;
-  const int4 mi = m4[i], mj = m4[j];
+  const int4 mj = m4[j];
   const ExactPair e = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], pos[3 * i], pos[3 * i + 1],
-                                 pos[3 * i + 2], G.H, (int)(code >> 4) - 1 + mi.x - mj.x,
-                                 (int)((code >> 2) & 3) - 1 + mi.y - mj.y, (int)(code & 3) - 1 + mi.z - mj.z);
+                                 pos[3 * i + 2], G.H, w0 + mi.x - mj.x, w1 + mi.y - mj.y, w2 + mi.z - mj.z);
   return e.r2 < G.R2sq;
 }
 
-// Cartesian vector of a separation v in cell units: v0 E_0 + v1 E_1 + v2 E_2.
-__device__ __forceinline__ float3 md_cart(const MdGeom &G, float v0, float v1, float v2) {
-  return make_float3(v0 * G.E[0] + v1 * G.E[3] + v2 * G.E[6], v0 * G.E[1] + v1 * G.E[4] + v2 * G.E[7],
-                     v0 * G.E[2] + v1 * G.E[5] + v2 * G.E[8]);
-}
-
-// The entries of the pairs one thread accepted, keys (partner << 6 | wrap code) in slot-major
-// [M][N] rows: the thread's own nf entries take one atomic on its count, each partner's entry one on
-// the partner's; all are issued after the search so that their round trips overlap. The order of
-// appends is undone by the sort of the rows kernel. A thread keeps at most kFwdCap pairs: more means
-// more than max_nbr (<= 32) neighbours, which the count records and the rows kernel flags.
-constexpr int kFwdCap = 32;
-__device__ __forceinline__ void md_flush_pairs(int i, int N, int M, const unsigned *list, int nf,
-                                               int *__restrict__ cnt, unsigned *__restrict__ keys) {
-  if (nf == 0) return;
-  const int kept = min(nf, kFwdCap);
-  const int p0 = atomicAdd(&cnt[i], nf);
-  for (int e = 0; e < kept && p0 + e < M; ++e) keys[(size_t)(p0 + e) * N + i] = list[e * kMdThreads];
-#pragma unroll 4
-  for (int e = 0; e < kept; ++e) {
-    const unsigned key = list[e * kMdThreads];
-    const int j = (int)(key >> 6);
-    const int q = atomicAdd(&cnt[j], 1);
-    if (q < M) keys[(size_t)q * N + j] = ((unsigned)i << 6) | (kWrapNeg - (key & 63u));
+// The full shell of atom i (cell index mi.w, in-cell position xi): every record of the 27 cells around
+// its own but i's own is a candidate; visit(key) is called for each member, key = j << 6 | offset code.
+// The shell runs as 9 rows (o0, o1) of three cells along the third axis, each row one loop over its
+// cells' records in turn (so that the lanes of a warp diverge by row lengths, not cell by cell). The
+// FP32 separation here is (o E - X_i) + X_j; any rounding within the band serves, since the band
+// sends every near-cutoff candidate to the exact test.
+template <typename Visit>
+__device__ __forceinline__ void md_shell(const MdGeom &G, const double *__restrict__ pos,
+                                         const int4 *__restrict__ m4, const int *__restrict__ cellcnt,
+                                         const float4 *__restrict__ cellx, int i, int4 mi, float4 xi,
+                                         Visit &&visit) {
+  const int nc0 = G.nc[0], nc1 = G.nc[1], nc2 = G.nc[2];
+  const int c2 = mi.w % nc2, c1 = (mi.w / nc2) % nc1, c0 = mi.w / (nc2 * nc1);
+  int g2[3], w2[3];
+#pragma unroll
+  for (int o = 0; o < 3; ++o) w2[o] = md_wrap(c2 + o - 1, nc2, g2[o]);
+#pragma unroll 1
+  for (int ab = 0; ab < 9; ++ab) {
+    const int a = ab / 3, b = ab - 3 * a;
+    int g0, g1;
+    const int w0 = md_wrap(c0 + a - 1, nc0, g0), w1 = md_wrap(c1 + b - 1, nc1, g1);
+    const int row = (g0 * nc1 + g1) * nc2;
+    const int n0 = min(cellcnt[row + g2[0]], kMdCap), n1 = min(cellcnt[row + g2[1]], kMdCap),
+              n2 = min(cellcnt[row + g2[2]], kMdCap);
+    // the row's offset o E for o2 = -1, less X_i; o2 = 0 and 1 add the third edge once and twice
+    const float fa = (float)(a - 1), fb = (float)(b - 1);
+    const float bx = fa * G.E[0] + fb * G.E[3] - G.E[6] - xi.x;
+    const float by = fa * G.E[1] + fb * G.E[4] - G.E[7] - xi.y;
+    const float bz = fa * G.E[2] + fb * G.E[5] - G.E[8] - xi.z;
+    const int n01 = n0 + n1, T = n01 + n2;
+    for (int q = 0; q < T; ++q) {
+      const int c = q < n0 ? 0 : (q < n01 ? 1 : 2);
+      const int slot = q - (c == 0 ? 0 : (c == 1 ? n0 : n01));
+      const float4 r = cellx[(size_t)(row + g2[c]) * kMdCap + slot];
+      const int j = __float_as_int(r.w);
+      const float fc = (float)c;
+      const float dx = __fadd_rn(__fmaf_rn(fc, G.E[6], bx), r.x);
+      const float dy = __fadd_rn(__fmaf_rn(fc, G.E[7], by), r.y);
+      const float dz = __fadd_rn(__fmaf_rn(fc, G.E[8], bz), r.z);
+      if (j != i && md_pair_in(G, pos, m4, i, j, mi, w0, w1, w2[c], make_float3(dx, dy, dz)))
+        visit(((unsigned)j << 6) | (unsigned)((a << 4) | (b << 2) | c));
+    }
   }
 }
 
-// Neighbour pairs by bricks of 4x4x4 cells: a CTA stages the records of its brick and of the cells
-// around it (6x6x6) in shared memory, as Cartesian brick coordinates X = (u + halo cell - 1) E with
-// the halo cell's periodic wrap packed above the atom index. One thread per atom of the brick tests the half
-// shell: the 13 forward cells (offset d0 = 1; d0 = 0, d1 = 1; d0 = d1 = 0, d2 = 1) and the records
-// after its own in its cell, each pair once. In the stage the three cells along z of one (d0, d1) are
-// consecutive, so the half shell is 5 runs of records. A brick whose surroundings hold more than
-// kStageCap atoms reads the records from global memory, cell by cell.
-__global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
-    int N, const double *__restrict__ pos, const MdGeom G, const int4 *__restrict__ m4,
-    const int *__restrict__ cellcnt, const float4 *__restrict__ cellu, int M, int *__restrict__ cnt,
-    unsigned *__restrict__ keys) {
+// List entry (j, n) of key (j << 6 | offset code) of atom i (wraps m_i, cell (c0, c1, c2)):
+// n = wrap + m_i - m_j.
+__device__ __forceinline__ void md_write_entry(const MdGeom &G, const int4 *__restrict__ m4, int4 mi, int c0, int c1,
+                                               int c2, unsigned key, size_t at, int *__restrict__ nbr,
+                                               char4 *__restrict__ shift) {
+  const int j = (int)(key >> 6);
+  const int4 mj = m4[j];
+  int g;
+  const int w0 = md_wrap(c0 + (int)((key >> 4) & 3u) - 1, G.nc[0], g);
+  const int w1 = md_wrap(c1 + (int)((key >> 2) & 3u) - 1, G.nc[1], g);
+  const int w2 = md_wrap(c2 + (int)(key & 3u) - 1, G.nc[2], g);
+  nbr[at] = j;
+  shift[at] = make_char4((signed char)(w0 + mi.x - mj.x), (signed char)(w1 + mi.y - mj.y),
+                         (signed char)(w2 + mi.z - mj.z), 0);
+}
+
+__device__ __forceinline__ void cas(unsigned &a, unsigned &b) {
+  const unsigned lo = min(a, b), hi = max(a, b);
+  a = lo;
+  b = hi;
+}
+
+// The list of atom i from its members' keys k (count of them; at most kMdMaxM kept, the rest ~0u):
+// the count, then the keys sorted (Batcher's odd-even merge sort of 8, 19 compare-exchanges; with at
+// most one image of any j, plane spacings of at least 3 R2, the key order is the (j, n) order) into
+// the rows of `keys` and the entries (j, n) into the lists.
+__device__ __forceinline__ void md_emit(int N, int M, int i, int4 mi, int c0, int c1, int c2, const MdGeom &G,
+                                        const int4 *__restrict__ m4, unsigned (&k)[kMdMaxM], int count,
+                                        int *__restrict__ cnt, unsigned *__restrict__ keys, int *__restrict__ nbr,
+                                        char4 *__restrict__ shift, unsigned *status) {
+  cnt[i] = count;
+  if (count > M) set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+  const int cm = min(count, M);
+  cas(k[0], k[1]); cas(k[2], k[3]); cas(k[4], k[5]); cas(k[6], k[7]);
+  cas(k[0], k[2]); cas(k[1], k[3]); cas(k[4], k[6]); cas(k[5], k[7]);
+  cas(k[1], k[2]); cas(k[5], k[6]);
+  cas(k[0], k[4]); cas(k[1], k[5]); cas(k[2], k[6]); cas(k[3], k[7]);
+  cas(k[2], k[4]); cas(k[3], k[5]);
+  cas(k[1], k[2]); cas(k[3], k[4]); cas(k[5], k[6]);
+#pragma unroll
+  for (int e = 0; e < kMdMaxM; ++e)
+    if (e < cm) {
+      keys[(size_t)e * N + i] = k[e];
+      md_write_entry(G, m4, mi, c0, c1, c2, k[e], (size_t)e * N + i, nbr, shift);
+    }
+}
+
+// The whole search of atom i from the cell arrays in global memory (md_shell): the path of bricks
+// whose surroundings exceed the stage and of atoms with more than kMdMaxM members. Such an atom
+// enumerates its shell a second time, keeps the first M members found in its row of `keys` and
+// writes each at its rank among them (the row itself stays in the order found: the force kernel
+// flags the atom and gives it no forces).
+__device__ __noinline__ void md_search_atom(int N, int M, int i, const double *__restrict__ pos, const MdGeom &G,
+                                               const float4 *__restrict__ x4, const int4 *__restrict__ m4,
+                                               const int *__restrict__ cellcnt, const float4 *__restrict__ cellx,
+                                               int *__restrict__ cnt, unsigned *__restrict__ keys,
+                                               int *__restrict__ nbr, char4 *__restrict__ shift, unsigned *status) {
+  const int4 mi = m4[i];
+  const float4 xi = x4[i];
+  const int nc2 = G.nc[2], nc1 = G.nc[1];
+  const int c2 = mi.w % nc2, c1 = (mi.w / nc2) % nc1, c0 = mi.w / (nc2 * nc1);
+  unsigned k[kMdMaxM];
+#pragma unroll
+  for (int u = 0; u < kMdMaxM; ++u) k[u] = 0xffffffffu;
+  int count = 0;
+  md_shell(G, pos, m4, cellcnt, cellx, i, mi, xi, [&](unsigned key) {
+#pragma unroll
+    for (int u = 0; u < kMdMaxM; ++u)
+      if (u == count) k[u] = key;
+    ++count;
+  });
+  if (count <= kMdMaxM) {
+    md_emit(N, M, i, mi, c0, c1, c2, G, m4, k, count, cnt, keys, nbr, shift, status);
+    return;
+  }
+  cnt[i] = count;
+  if (count > M) set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+  const int cm = min(count, M);
+  int p = 0;
+  md_shell(G, pos, m4, cellcnt, cellx, i, mi, xi, [&](unsigned key) {
+    if (p < M) keys[(size_t)p * N + i] = key;
+    ++p;
+  });
+  for (int e = 0; e < cm; ++e) {
+    const unsigned key = keys[(size_t)e * N + i];
+    int rank = 0;
+    for (int f = 0; f < cm; ++f) rank += keys[(size_t)f * N + i] < key ? 1 : 0;
+    md_write_entry(G, m4, mi, c0, c1, c2, key, (size_t)rank * N + i, nbr, shift);
+  }
+}
+
+// Neighbour lists by bricks of 4x4x4 cells, full shell, no atomics: a CTA stages the records of its
+// brick and of the cells around it (6x6x6) in shared memory as brick coordinates (the in-cell
+// position plus the halo cell's offset, (h - 1) E), with the halo cell index packed above the atom
+// index. One thread per atom of the brick tests the 9 rows (o0, o1) of its shell; the three cells of a
+// row lie consecutively in the stage, so a row is one run of records. Members (at most kMdMaxM kept in
+// registers) are sorted and written by md_emit. A brick whose surroundings hold more than kStageCap
+// atoms, and an atom with more than kMdMaxM members, take the global-memory path (md_search_atom).
+__global__ void __launch_bounds__(kMdThreads, 8) md_search_kernel(
+    int N, int M, const double *__restrict__ pos, const __grid_constant__ MdGeom G, const float4 *__restrict__ x4,
+    const int4 *__restrict__ m4, const int *__restrict__ cellcnt, const float4 *__restrict__ cellx,
+    int *__restrict__ cnt, unsigned *__restrict__ keys, int *__restrict__ nbr, char4 *__restrict__ shift,
+    unsigned *status) {
   __shared__ float4 s_u[kStageCap];
-  __shared__ unsigned s_list[kFwdCap * kMdThreads];
-  __shared__ int s_cnt[kHaloCells], s_start[kHaloCells], s_gcell[kHaloCells], s_info[kHaloCells];
+  __shared__ int s_cnt[kHaloCells], s_start[kHaloCells], s_gcell[kHaloCells];
   __shared__ int s_ipre[kBrickCells + 1];
   __shared__ int s_total;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -220,15 +360,15 @@ __global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
     const int c0 = o0 + h0 - 1, c1 = o1 + h1 - 1, c2 = o2 + h2 - 1;
     int n = 0, g = 0;
     if (c0 <= G.nc[0] && c1 <= G.nc[1] && c2 <= G.nc[2]) {
-      const int g0 = c0 < 0 ? c0 + G.nc[0] : (c0 >= G.nc[0] ? c0 - G.nc[0] : c0);
-      const int g1 = c1 < 0 ? c1 + G.nc[1] : (c1 >= G.nc[1] ? c1 - G.nc[1] : c1);
-      const int g2 = c2 < 0 ? c2 + G.nc[2] : (c2 >= G.nc[2] ? c2 - G.nc[2] : c2);
+      int g0, g1, g2;
+      md_wrap(c0, G.nc[0], g0);
+      md_wrap(c1, G.nc[1], g1);
+      md_wrap(c2, G.nc[2], g2);
       g = (g0 * G.nc[1] + g1) * G.nc[2] + g2;
       n = min(cellcnt[g], kMdCap);
     }
     s_cnt[h] = n;
     s_gcell[h] = g;
-    s_info[h] = h0 | (h1 << 3) | (h2 << 6) | (int)(wrap_code(G, c0, c1, c2) << 9);
   }
   __syncthreads();
   // 2. warp 0: exclusive sums over the halo cells (7 per lane) and over the interior cells (2 per lane)
@@ -279,19 +419,16 @@ __global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
       int h = 0;
       for (int step = 128; step > 0; step >>= 1)
         if (h + step < kHaloCells && s_start[h + step] <= t) h += step;
-      const int info = s_info[h];
-      const float4 r = cellu[s_gcell[h] * kMdCap + (t - s_start[h])];
-      const float3 X = md_cart(G, r.x + (float)((info & 7) - 1), r.y + (float)(((info >> 3) & 7) - 1),
-                               r.z + (float)(((info >> 6) & 7) - 1));
-      s_u[t] = make_float4(X.x, X.y, X.z, __int_as_float(__float_as_int(r.w) | ((info >> 9) << 24)));
+      const int h0 = h / (kHaloEdge * kHaloEdge), h1 = (h / kHaloEdge) % kHaloEdge, h2 = h % kHaloEdge;
+      const float4 r = cellx[(size_t)s_gcell[h] * kMdCap + (t - s_start[h])];
+      const float3 B = md_cart(G, (float)(h0 - 1), (float)(h1 - 1), (float)(h2 - 1));
+      s_u[t] = make_float4(B.x + r.x, B.y + r.y, B.z + r.z,
+                           __int_as_float(__float_as_int(r.w) | (h << 24)));
     }
-  } else {
-    for (int h = tid; h < kHaloCells; h += kMdThreads) s_start[h] = s_gcell[h] * kMdCap;
   }
   __syncthreads();
   // 4. one thread per atom of the brick
   const int A = s_ipre[kBrickCells];
-  unsigned *list = s_list + tid;
   for (int a = tid; a < A; a += kMdThreads) {
     int k = 0;                                     // interior cell of atom a
     for (int step = kBrickCells / 2; step > 0; step >>= 1)
@@ -299,150 +436,61 @@ __global__ void __launch_bounds__(kMdThreads) md_pairs_kernel(
     const int k0 = k / (kBrick * kBrick), k1 = (k / kBrick) % kBrick, k2 = k % kBrick;
     const int hi = ((k0 + 1) * kHaloEdge + k1 + 1) * kHaloEdge + k2 + 1;
     const int own = a - s_ipre[k];
-    if (staged) {
-      const int slot = s_start[hi] + own;
-      const float4 ei = s_u[slot];
-      const int i = __float_as_int(ei.w) & 0xffffff;
-      int run = 0, p = 0, pend = 0, nf = 0;
-      for (;;) {
-        while (p >= pend && run < 5) {
-          if (run < 4) {                           // (d0, d1) = (1,-1), (1,0), (1,1), (0,1)
-            const int h = hi + (run < 3 ? (kHaloEdge + run - 1) : 1) * kHaloEdge;
-            p = s_start[h - 1];
-            pend = s_start[h + 1] + s_cnt[h + 1];
-          } else {                                 // rest of the own cell, then (0, 0, 1)
-            p = slot + 1;
-            pend = s_start[hi + 1] + s_cnt[hi + 1];
-          }
-          ++run;
-        }
-        if (p >= pend) break;
-        const float4 ej = s_u[p++];
+    if (!staged) {
+      const int i = __float_as_int(cellx[(size_t)s_gcell[hi] * kMdCap + own].w);
+      md_search_atom(N, M, i, pos, G, x4, m4, cellcnt, cellx, cnt, keys, nbr, shift, status);
+      continue;
+    }
+    const int slot = s_start[hi] + own;
+    const float4 ei = s_u[slot];
+    const int i = __float_as_int(ei.w) & 0xffffff;
+    const int4 mi = m4[i];
+    const int c0 = o0 + k0, c1 = o1 + k1, c2 = o2 + k2;
+    unsigned kk[kMdMaxM];
+#pragma unroll
+    for (int u = 0; u < kMdMaxM; ++u) kk[u] = 0xffffffffu;
+    int count = 0;
+#pragma unroll 1
+    for (int ab = 0; ab < 9; ++ab) {
+      const int ra = ab / 3, rb = ab - 3 * ra;
+      const int hc = hi + ((ra - 1) * kHaloEdge + (rb - 1)) * kHaloEdge;   // the row's middle cell
+      const int pend = s_start[hc + 1] + s_cnt[hc + 1];
+      for (int p = s_start[hc - 1]; p < pend; ++p) {
+        const float4 ej = s_u[p];
+        const float dx = __fsub_rn(ej.x, ei.x), dy = __fsub_rn(ej.y, ei.y), dz = __fsub_rn(ej.z, ei.z);
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+        if (r2 > G.cut2_hi || p == slot) continue;
         const unsigned tag = (unsigned)__float_as_int(ej.w);
-        const int j = (int)(tag & 0xffffffu);
-        if (md_pair_in(G, pos, m4, i, j, tag >> 24, ej.x - ei.x, ej.y - ei.y, ej.z - ei.z)) {
-          if (nf < kFwdCap) list[nf * kMdThreads] = (tag & 0xffffffu) << 6 | (tag >> 24);
-          ++nf;
+        const int j = (int)(tag & 0xffffffu), hj = (int)(tag >> 24);
+        const int d0 = hj / (kHaloEdge * kHaloEdge) - (k0 + 1), d1 = (hj / kHaloEdge) % kHaloEdge - (k1 + 1),
+                  d2 = hj % kHaloEdge - (k2 + 1);
+        int g;
+        const int w0 = md_wrap(c0 + d0, G.nc[0], g), w1 = md_wrap(c1 + d1, G.nc[1], g),
+                  w2 = md_wrap(c2 + d2, G.nc[2], g);
+        if (md_pair_in(G, pos, m4, i, j, mi, w0, w1, w2, make_float3(dx, dy, dz))) {
+          const unsigned key = ((unsigned)j << 6) | (unsigned)(((d0 + 1) << 4) | ((d1 + 1) << 2) | (d2 + 1));
+#pragma unroll
+          for (int u = 0; u < kMdMaxM; ++u)
+            if (u == count) kk[u] = key;
+          ++count;
         }
       }
-      md_flush_pairs(i, N, M, list, nf, cnt, keys);
-    } else {
-      const float4 ei = cellu[s_start[hi] + own];
-      const int i = __float_as_int(ei.w);
-      int nf = 0;
-      for (int l = 0; l < 14; ++l) {
-        // l < 9: d0 = 1; l < 12: d0 = 0, d1 = 1; l = 12: (0, 0, 1); l = 13: own cell after own record
-        const int d0 = l < 9 ? 1 : 0, d1 = l < 9 ? l / 3 - 1 : (l < 12 ? 1 : 0),
-                  d2 = l < 9 ? l % 3 - 1 : (l < 12 ? l - 10 : (l == 12 ? 1 : 0));
-        const int h = hi + (d0 * kHaloEdge + d1) * kHaloEdge + d2;
-        const unsigned code = wrap_code(G, o0 + k0 + d0, o1 + k1 + d1, o2 + k2 + d2);
-        const int n = s_cnt[h], st = s_start[h];
-        for (int q = l == 13 ? own + 1 : 0; q < n; ++q) {
-          const float4 ej = cellu[st + q];
-          const int j = __float_as_int(ej.w);
-          const float3 d = md_cart(G, (float)d0 + (ej.x - ei.x), (float)d1 + (ej.y - ei.y), (float)d2 + (ej.z - ei.z));
-          if (md_pair_in(G, pos, m4, i, j, code, d.x, d.y, d.z)) {
-            if (nf < kFwdCap) list[nf * kMdThreads] = ((unsigned)j << 6) | code;
-            ++nf;
-          }
-        }
-      }
-      md_flush_pairs(i, N, M, list, nf, cnt, keys);
     }
-  }
-}
-
-__device__ __forceinline__ void cas(unsigned &a, unsigned &b) {
-  const unsigned lo = min(a, b), hi = max(a, b);
-  a = lo;
-  b = hi;
-}
-
-// Entry (j, n) of a key (j << 6 | wrap code), n = wrap + m_i - m_j.
-__device__ __forceinline__ void md_write_entry(const int4 *__restrict__ m4, int4 mi, unsigned key, size_t at,
-                                               int *__restrict__ nbr, char4 *__restrict__ shift) {
-  const int j = (int)(key >> 6);
-  const int4 mj = m4[j];
-  nbr[at] = j;
-  shift[at] = make_char4((signed char)((int)((key >> 4) & 3) - 1 + mi.x - mj.x),
-                         (signed char)((int)((key >> 2) & 3) - 1 + mi.y - mj.y),
-                         (signed char)((int)(key & 3) - 1 + mi.z - mj.z), 0);
-}
-
-// One thread per atom: the appended keys in ascending (j, n) order (for one j the shift is the wrap
-// plus a constant, so both orders agree) as the list (j, n); for an atom with at most kMdMaxM entries
-// also the slot of each reverse bond in the partner's list, i.e. the rank of (i, -wrap) among the
-// partner's keys.
-__global__ void md_rows_kernel(int N, int M, const int4 *__restrict__ m4, const int *__restrict__ cnt,
-                               const unsigned *__restrict__ keys, int *__restrict__ nbr,
-                               char4 *__restrict__ shift, int *__restrict__ rev, unsigned *status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int count = cnt[i];
-  if (count > M) set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
-  const int c = min(count, M);
-  const int4 mi = m4[i];
-  const unsigned *row = keys + i;                // entry e at row[e * N]
-  if (c <= kMdMaxM) {
-    unsigned k[kMdMaxM];
-#pragma unroll
-    for (int e = 0; e < kMdMaxM; ++e) k[e] = e < c ? row[(size_t)e * N] : 0xffffffffu;
-    // Batcher's odd-even merge sort of 8 keys (19 compare-exchanges)
-    cas(k[0], k[1]); cas(k[2], k[3]); cas(k[4], k[5]); cas(k[6], k[7]);
-    cas(k[0], k[2]); cas(k[1], k[3]); cas(k[4], k[6]); cas(k[5], k[7]);
-    cas(k[1], k[2]); cas(k[5], k[6]);
-    cas(k[0], k[4]); cas(k[1], k[5]); cas(k[2], k[6]); cas(k[3], k[7]);
-    cas(k[2], k[4]); cas(k[3], k[5]);
-    cas(k[1], k[2]); cas(k[3], k[4]); cas(k[5], k[6]);
-#pragma unroll
-    for (int e = 0; e < kMdMaxM; ++e) {
-      if (e < c) {
-        md_write_entry(m4, mi, k[e], (size_t)e * N + i, nbr, shift);
-        const int j = (int)(k[e] >> 6);
-        const int cj = min(cnt[j], M);
-        int slot = e * N + i;                      // partner beyond kMdMaxM: flagged by the force kernel
-        if (cj <= kMdMaxM) {
-          const unsigned want = ((unsigned)i << 6) | (kWrapNeg - (k[e] & 63u));
-          const unsigned *rj = keys + j;
-          int rank = 0;
-          bool found = false;
-#pragma unroll
-          for (int f = 0; f < kMdMaxM; ++f) {
-            if (f < cj) {
-              const unsigned q = rj[(size_t)f * N];
-              rank += q < want ? 1 : 0;
-              found = found || q == want;
-            }
-          }
-          if (!found) {
-            set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
-            rank = 0;
-          }
-          slot = rank * N + j;
-        }
-        rev[(size_t)e * N + i] = slot;
-      }
+    if (count > kMdMaxM) {
+      md_search_atom(N, M, i, pos, G, x4, m4, cellcnt, cellx, cnt, keys, nbr, shift, status);
+      continue;
     }
-  } else {
-    for (int e = 0; e < c; ++e) {                  // more than kMdMaxM entries: rank by counting
-      const unsigned key = row[(size_t)e * N];
-      int rank = 0;
-      for (int f = 0; f < c; ++f) rank += row[(size_t)f * N] < key ? 1 : 0;
-      md_write_entry(m4, mi, key, (size_t)rank * N + i, nbr, shift);
-    }
-#pragma unroll
-    for (int e = 0; e < kMdMaxM; ++e) rev[(size_t)e * N + i] = e * N + i;
+    md_emit(N, M, i, mi, c0, c1, c2, G, m4, kk, count, cnt, keys, nbr, shift, status);
   }
 }
 
 // Passes 1-2 of one atom per thread, M = the warp's largest neighbour count; bonds e >= m of this
 // thread are phantoms (f_C = f_C' = 0, unit vector 0), which contribute exactly zero.
 template <int M, typename R>
-__device__ __forceinline__ void md_atom(const R (&ux)[kMdMaxM], const R (&uy)[kMdMaxM],
-                                        const R (&uz)[kMdMaxM], const R (&r)[kMdMaxM],
-                                        const R (&ir)[kMdMaxM], const R (&fc)[kMdMaxM],
-                                        const R (&fcp)[kMdMaxM], const PConsts<R> &K, R &U,
-                                        R (&Wv)[6], R (&Px)[kMdMaxM], R (&Py)[kMdMaxM], R (&Pz)[kMdMaxM]) {
+__device__ __forceinline__ void md_atom(const R (&ux)[M], const R (&uy)[M], const R (&uz)[M], const R (&r)[M],
+                                        const R (&ir)[M], const R (&fc)[M], const R (&fcp)[M],
+                                        const PConsts<R> &K, R &U, R (&Wv)[6], R (&Px)[M], R (&Py)[M],
+                                        R (&Pz)[M]) {
   constexpr int NP = M * (M - 1) / 2;
   R cs[NP > 0 ? NP : 1], tq[NP > 0 ? NP : 1];
   R fR[M], fA[M], zeta[M];
@@ -586,48 +634,65 @@ inline size_t md_counter_offset(int K, int nblk) {
   return ((size_t)nblk + ngroups) * K * sizeof(double);
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 4 : 1) md_force_kernel(
-    int N, int M, const MdGeom G, const PConsts<R> K, const double *__restrict__ pos,
-    const float4 *__restrict__ u4, const int4 *__restrict__ m4, const int *__restrict__ cnt,
-    const int *__restrict__ nbr, const char4 *__restrict__ shift, typename Vec4<R>::T *__restrict__ Pst,
-    double *__restrict__ partial, double *__restrict__ E, double *__restrict__ W, unsigned *status) {
-  using R4 = typename Vec4<R>::T;
-  __shared__ double red[kMdThreads / 32][7];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = i < N;
-  int m = valid ? min(cnt[i], M) : 0;   // a truncated list (count > M) is flagged; its row holds M entries
-  if (m > kMdMaxM) {
-    set_status(status, TERSOFF_STATUS_MANY_NBRS);
-    m = 0;
-  }
-  R ux[kMdMaxM], uy[kMdMaxM], uz[kMdMaxM], r[kMdMaxM], ir[kMdMaxM], fc[kMdMaxM], fcp[kMdMaxM];
-  float4 ui = make_float4(0.f, 0.f, 0.f, 0.f);
-  int4 mi = make_int4(0, 0, 0, 0);
-  if (valid) {
-    ui = u4[i];
-    mi = m4[i];
-  }
-  const int ci2 = mi.w % G.nc[2], ci1 = (mi.w / G.nc[2]) % G.nc[1], ci0 = mi.w / (G.nc[2] * G.nc[1]);
+// Slot of the reverse entry of key (j << 6 | offset code) of atom i: rank * N + j, the rank of
+// (i, -o) among j's keys being its place in j's sorted list; -1 when j's list is not handled (more
+// than kMdMaxM entries: flagged by the force kernel) or does not hold it (a truncated list: flagged).
+__device__ __forceinline__ int md_reverse_slot(int N, int M, int i, unsigned key, const int *__restrict__ cnt,
+                                               const unsigned *__restrict__ keys, unsigned *status) {
+  const int j = (int)(key >> 6);
+  const int cj = cnt[j];
+  if (cj > kMdMaxM) return -1;
+  const int cjm = min(cj, M);
+  const unsigned want = ((unsigned)i << 6) | (kOffNeg - (key & 63u));
+  int rank = 0;
+  bool found = false;
 #pragma unroll
-  for (int e = 0; e < kMdMaxM; ++e) {
+  for (int f = 0; f < kMdMaxM; ++f)
+    if (f < cjm) {
+      const unsigned q = keys[(size_t)f * N + j];
+      rank += q < want ? 1 : 0;
+      found = found || q == want;
+    }
+  if (!found) {
+    set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
+    return -1;
+  }
+  return rank * N + j;
+}
+
+// Passes 1-2 of atom i (m entries) with arrays for M >= m bonds (Mw = the warp's largest count): the
+// bond geometry (FP32: the search's separation; FP64: the exact FP64 bond vector), md_atom, and the
+// P_ij of every entry, into Pst at the entry's own slot (e, i) and into Prev at the reverse entry's
+// slot (rank, j), so that the gather reads both rows of atom i in order.
+template <int Mw, typename R>
+__device__ __forceinline__ void md_force_atom(int N, int M, int i, int m, const MdGeom &G, const PConsts<R> &K,
+                                              const double *__restrict__ pos, const float4 *__restrict__ x4,
+                                              const unsigned *__restrict__ keys, const int *__restrict__ cnt,
+                                              const int *__restrict__ nbr, const char4 *__restrict__ shift,
+                                              float4 xi, typename Vec4<R>::T *__restrict__ Pst,
+                                              typename Vec4<R>::T *__restrict__ Prev, unsigned *status, R &U,
+                                              R (&Wv)[6]) {
+  using R4 = typename Vec4<R>::T;
+  constexpr int M_ = Mw;
+  R ux[M_], uy[M_], uz[M_], r[M_], ir[M_], fc[M_], fcp[M_];
+  int rs[M_];
+#pragma unroll
+  for (int e = 0; e < M_; ++e) {
     ux[e] = R(0); uy[e] = R(0); uz[e] = R(0); r[e] = R(1); ir[e] = R(0); fc[e] = R(0); fcp[e] = R(0);
+    rs[e] = -1;
     if (e < m) {
-      const int j = nbr[(size_t)e * N + i];
-      const char4 n = shift[(size_t)e * N + i];
       R dx, dy, dz;
+      const unsigned key = keys[(size_t)e * N + i];
+      rs[e] = md_reverse_slot(N, M, i, key, cnt, keys, status);
       if constexpr (sizeof(R) == 4) {
-        // cell offset of j's image relative to i's cell, then the in-cell FP32 construction
-        const float4 uj = u4[j];
-        const int4 mj = m4[j];
-        const int cj2 = mj.w % G.nc[2], cj1 = (mj.w / G.nc[2]) % G.nc[1], cj0 = mj.w / (G.nc[2] * G.nc[1]);
-        const float v0 = (float)(cj0 - ci0 + G.nc[0] * (n.x + mj.x - mi.x)) + (uj.x - ui.x);
-        const float v1 = (float)(cj1 - ci1 + G.nc[1] * (n.y + mj.y - mi.y)) + (uj.y - ui.y);
-        const float v2 = (float)(cj2 - ci2 + G.nc[2] * (n.z + mj.z - mi.z)) + (uj.z - ui.z);
-        dx = v0 * G.E[0] + v1 * G.E[3] + v2 * G.E[6];
-        dy = v0 * G.E[1] + v1 * G.E[4] + v2 * G.E[7];
-        dz = v0 * G.E[2] + v1 * G.E[5] + v2 * G.E[8];
+        // the search's FP32 separation: neighbouring-cell offset and in-cell positions
+        const float3 d = md_sep(G, key & 63u, xi, x4[key >> 6]);
+        dx = d.x;
+        dy = d.y;
+        dz = d.z;
       } else {
+        const int j = nbr[(size_t)e * N + i];
+        const char4 n = shift[(size_t)e * N + i];
         const ExactPair p = exact_pair(pos[3 * j], pos[3 * j + 1], pos[3 * j + 2], pos[3 * i], pos[3 * i + 1],
                                        pos[3 * i + 2], G.H, n.x, n.y, n.z);
         dx = p.dx;
@@ -659,22 +724,10 @@ __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 4 : 1) md_force_k
       }
     }
   }
-  R U = R(0), Wv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-  R Px[kMdMaxM], Py[kMdMaxM], Pz[kMdMaxM];
-  const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
-  switch (Mw) {
-    case 1: md_atom<1, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz); break;
-    case 2: md_atom<2, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz); break;
-    case 3: md_atom<3, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz); break;
-    case 4: md_atom<4, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz); break;
-    case 5: md_atom<5, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz); break;
-    case 6: md_atom<6, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz); break;
-    case 7: md_atom<7, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz); break;
-    case 8: md_atom<8, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz); break;
-    default: break;
-  }
+  R Px[M_], Py[M_], Pz[M_];
+  md_atom<M_, R>(ux, uy, uz, r, ir, fc, fcp, K, U, Wv, Px, Py, Pz);
 #pragma unroll
-  for (int e = 0; e < kMdMaxM; ++e)
+  for (int e = 0; e < M_; ++e)
     if (e < m) {
       R4 v;
       v.x = Px[e];
@@ -682,7 +735,69 @@ __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 4 : 1) md_force_k
       v.z = Pz[e];
       v.w = R(0);
       Pst[(size_t)e * N + i] = v;
+      if (rs[e] >= 0) Prev[rs[e]] = v;
     }
+}
+
+// The same for the long lists (5-8 entries) as a called function: its many live values do not raise
+// the register count of the kernel, which the short lists of solids need.
+template <typename R>
+struct MdSums {
+  R U, W[6];
+};
+template <int Mw, typename R>
+__device__ __noinline__ MdSums<R> md_force_atom_long(int N, int M, int i, int m, const MdGeom &G,
+                                                     const PConsts<R> &K, const double *__restrict__ pos,
+                                                     const float4 *__restrict__ x4, const unsigned *__restrict__ keys,
+                                                     const int *__restrict__ cnt, const int *__restrict__ nbr,
+                                                     const char4 *__restrict__ shift, float4 xi,
+                                                     typename Vec4<R>::T *__restrict__ Pst,
+                                                     typename Vec4<R>::T *__restrict__ Prev, unsigned *status) {
+  MdSums<R> o;
+  o.U = R(0);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) o.W[k] = R(0);
+  md_force_atom<Mw, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Pst, Prev, status, o.U, o.W);
+  return o;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 8 : 1) md_force_kernel(
+    int N, int M, const MdGeom G, const PConsts<R> K, const double *__restrict__ pos,
+    const float4 *__restrict__ x4, const unsigned *__restrict__ keys, const int *__restrict__ cnt,
+    const int *__restrict__ nbr, const char4 *__restrict__ shift, typename Vec4<R>::T *__restrict__ Pst,
+    typename Vec4<R>::T *__restrict__ Prev, double *__restrict__ partial, double *__restrict__ E,
+    double *__restrict__ W, unsigned *status) {
+  __shared__ double red[kMdThreads / 32][7];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < N;
+  int m = valid ? min(cnt[i], M) : 0;   // a truncated list (count > M) is flagged; its row holds M entries
+  if (m > kMdMaxM) {
+    set_status(status, TERSOFF_STATUS_MANY_NBRS);
+    m = 0;
+  }
+  float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (sizeof(R) == 4 && valid) xi = x4[i];
+  R U = R(0), Wv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  // arrays sized by the warp's largest neighbour count, so that the common short lists keep few
+  // values live
+  const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
+  switch (Mw) {
+#define TSF_MDCASE(MM) \
+    case MM: md_force_atom<MM, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Pst, Prev, status, U, Wv); break;
+#define TSF_MDLONG(MM)                                                                      \
+    case MM: {                                                                              \
+      const MdSums<R> o = md_force_atom_long<MM, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Pst, Prev, status); \
+      U = o.U;                                                                              \
+      for (int k = 0; k < 6; ++k) Wv[k] = o.W[k];                                           \
+      break;                                                                                \
+    }
+    TSF_MDCASE(1) TSF_MDCASE(2) TSF_MDCASE(3) TSF_MDCASE(4) TSF_MDLONG(5) TSF_MDLONG(6) TSF_MDLONG(7)
+    TSF_MDLONG(8)
+#undef TSF_MDCASE
+#undef TSF_MDLONG
+    default: break;
+  }
   // per-warp sums in R, per-block FP64 partial sums of U and W, stored [7][blocks]
   R v[7] = {U, Wv[0], Wv[1], Wv[2], Wv[3], Wv[4], Wv[5]};
 #pragma unroll
@@ -703,20 +818,26 @@ __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 4 : 1) md_force_k
   md_grouped_sum<7>(partial, nblk, b, E, W, red);
 }
 
+// F_i = sum_e (P_ij - P_ji) over atom i's entries e = (j, n): P_ij from Pst row e, P_ji from Prev row e
+// (written there by atom j). An atom with more than kMdMaxM entries has no P (the force kernel flags
+// it) and gets F = 0.
 template <typename R>
-__global__ void md_gather_kernel(int N, int M, const int *__restrict__ cnt, const int *__restrict__ rev,
-                                 const typename Vec4<R>::T *__restrict__ Pst, R *__restrict__ F) {
+__global__ void md_gather_kernel(int N, int M, const int *__restrict__ cnt, const typename Vec4<R>::T *__restrict__ Pst,
+                                 const typename Vec4<R>::T *__restrict__ Prev, R *__restrict__ F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const int m = min(min(cnt[i], M), kMdMaxM);
+  const int ci = cnt[i];
+  const int m = ci <= kMdMaxM ? min(ci, M) : 0;
   R Fx = R(0), Fy = R(0), Fz = R(0);
-  for (int e = 0; e < m; ++e) {
-    const auto a = Pst[(size_t)e * N + i];
-    const auto b = Pst[rev[(size_t)e * N + i]];
-    Fx += a.x - b.x;
-    Fy += a.y - b.y;
-    Fz += a.z - b.z;
-  }
+#pragma unroll
+  for (int e = 0; e < kMdMaxM; ++e)
+    if (e < m) {
+      const auto a = Pst[(size_t)e * N + i];
+      const auto b = Prev[(size_t)e * N + i];
+      Fx += a.x - b.x;
+      Fy += a.y - b.y;
+      Fz += a.z - b.z;
+    }
   F[3 * (size_t)i] = Fx;
   F[3 * (size_t)i + 1] = Fy;
   F[3 * (size_t)i + 2] = Fz;
@@ -759,8 +880,9 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
     }
     esum += std::sqrt(en);
   }
-  // FP32 distance error: brick coordinates of up to 6 cell edges, rounded once each and subtracted,
-  // stay within ~12 ulp of the cell edge lengths; the band is 128 ulp wide
+  // FP32 distance error: the in-cell positions X (at most the sum of the cell edges in size) and the
+  // offset o E, each rounded, then subtracted and added, stay within ~12 ulp of the cell edge
+  // lengths; the band is 128 ulp wide
   const double margin = 128.0 * 1.2e-7 * esum * 2.0 * R2 + 1e-6;
   G.diag = 1;
   for (int a = 0; a < 3; ++a)
@@ -794,46 +916,45 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   if (c.md_cellcnt.ensure(ncells * sizeof(int)) || c.md_cells.ensure(ncells * kMdCap * sizeof(float4)) ||
       c.md_pos.ensure((size_t)N * (sizeof(float4) + sizeof(int4))) || c.md_cnt.ensure((size_t)N * sizeof(int)) ||
       c.md_nbr.ensure((size_t)N * M * sizeof(int)) || c.md_shift.ensure((size_t)N * M * sizeof(char4)) ||
-      c.md_keys.ensure((size_t)N * M * sizeof(unsigned)) ||
-      c.md_rev.ensure((size_t)N * kMdMaxM * sizeof(int)) || c.md_Pij.ensure((size_t)N * kMdMaxM * 4 * rs) ||
+      c.md_keys.ensure((size_t)N * M * sizeof(unsigned)) || c.md_Pij.ensure((size_t)N * kMdMaxM * 8 * rs) ||
       c.md_red.ensure(md_sum_bytes(7, nblk))) {
     err = "device allocation failed";
     return TERSOFF_E_CUDA;
   }
   c.md_N = N;
   c.md_M = M;
-  float4 *u4 = reinterpret_cast<float4 *>(c.md_pos.p);
-  int4 *m4 = reinterpret_cast<int4 *>(u4 + N);
+  float4 *x4 = reinterpret_cast<float4 *>(c.md_pos.p);
+  int4 *m4 = reinterpret_cast<int4 *>(x4 + N);
   unsigned *st = c.status.as<unsigned>();
+  int *cnt = c.md_cnt.as<int>();
+  unsigned *keys = c.md_keys.as<unsigned>();
   cudaMemsetAsync(c.md_cellcnt.p, 0, ncells * sizeof(int), s);
   cudaMemsetAsync(static_cast<char *>(c.md_red.p) + md_counter_offset(7, nblk), 0, (ngroups + 1) * sizeof(unsigned), s);
-  md_cells_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(), u4, m4,
-                                              c.md_cnt.as<int>(), st);
+  md_cells_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(), x4, m4,
+                                              cnt, st);
   const long nbricks = (long)((G.nc[0] + kBrick - 1) / kBrick) * ((G.nc[1] + kBrick - 1) / kBrick) *
                        ((G.nc[2] + kBrick - 1) / kBrick);
-  md_pairs_kernel<<<(unsigned)nbricks, kMdThreads, 0, s>>>(N, pos, G, m4, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(),
-                                                           M, c.md_cnt.as<int>(), c.md_keys.as<unsigned>());
-  md_rows_kernel<<<nblk, kMdThreads, 0, s>>>(N, M, m4, c.md_cnt.as<int>(), c.md_keys.as<unsigned>(),
-                                             c.md_nbr.as<int>(), c.md_shift.as<char4>(), c.md_rev.as<int>(), st);
+  md_search_kernel<<<(unsigned)nbricks, kMdThreads, 0, s>>>(N, M, pos, G, x4, m4, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(),
+                                               cnt, keys, c.md_nbr.as<int>(), c.md_shift.as<char4>(), st);
   const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
   const double log2e = 1.4426950408889634;
   if (precision == 64) {
     PConsts<double> K{D0, -al * log2e, r0, -0.5 * al, be, h, n, -0.5 / n};
-    md_force_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, u4, m4, c.md_cnt.as<int>(),
-                                                        c.md_nbr.as<int>(), c.md_shift.as<char4>(),
-                                                        c.md_Pij.as<dvec4>(), c.md_red.as<double>(), E, W, st);
-    md_gather_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, c.md_cnt.as<int>(), c.md_rev.as<int>(),
-                                                         c.md_Pij.as<dvec4>(), reinterpret_cast<double *>(F));
+    dvec4 *Pst = c.md_Pij.as<dvec4>(), *Prev = Pst + (size_t)N * kMdMaxM;
+    md_force_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, x4, keys, cnt, c.md_nbr.as<int>(),
+                                                        c.md_shift.as<char4>(), Pst, Prev, c.md_red.as<double>(),
+                                                        E, W, st);
+    md_gather_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, cnt, Pst, Prev, reinterpret_cast<double *>(F));
   } else {
     PConsts<float> K{(float)D0, (float)(-al * log2e), (float)r0, (float)(-0.5 * al), (float)be, (float)h,
                      (float)n, (float)(-0.5 / n)};
-    md_force_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, u4, m4, c.md_cnt.as<int>(),
-                                                       c.md_nbr.as<int>(), c.md_shift.as<char4>(),
-                                                       c.md_Pij.as<float4>(), c.md_red.as<double>(), E, W, st);
-    md_gather_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, c.md_cnt.as<int>(), c.md_rev.as<int>(),
-                                                        c.md_Pij.as<float4>(), reinterpret_cast<float *>(F));
+    float4 *Pst = c.md_Pij.as<float4>(), *Prev = Pst + (size_t)N * kMdMaxM;
+    md_force_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, x4, keys, cnt, c.md_nbr.as<int>(),
+                                                       c.md_shift.as<char4>(), Pst, Prev, c.md_red.as<double>(),
+                                                       E, W, st);
+    md_gather_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, cnt, Pst, Prev, reinterpret_cast<float *>(F));
   }
-  cudaError_t e = launched(5);   // cells, pairs, rows, force (with the sums), gather
+  cudaError_t e = launched(4);   // cells, search, force (with the sums), gather
   if (e != cudaSuccess) {
     err = std::string("CUDA error: ") + cudaGetErrorString(e);
     return TERSOFF_E_CUDA;
