@@ -26,11 +26,15 @@ namespace tsf {
 constexpr int kMdCap = 16;    // atom slots per cell
 constexpr int kMdMaxM = 8;    // neighbours per atom handled by the force kernel
 constexpr int kMdThreads = 128;
-constexpr int kBrick = 4;                                      // interior cells per brick edge
-constexpr int kHaloEdge = kBrick + 2;                          // brick plus one cell on each side
-constexpr int kHaloCells = kHaloEdge * kHaloEdge * kHaloEdge;  // 216
-constexpr int kBrickCells = kBrick * kBrick * kBrick;          // 64
-constexpr int kStageCap = 1024;                                // halo atoms staged in shared memory
+// Bricks of the pair search: 4 x 4 x 6 interior cells (the third axis, along which cells are
+// consecutive, the longest), and the cells around them
+constexpr int kBX = 4, kBY = 4, kBZ = 6;
+constexpr int kHX = kBX + 2, kHY = kBY + 2, kHZ = kBZ + 2;
+constexpr int kHaloCells = kHX * kHY * kHZ;       // 288
+constexpr int kBrickCells = kBX * kBY * kBZ;      // 96
+constexpr int kStageCap = 1024;                   // halo atoms staged in shared memory
+constexpr int kSearchThreads = 192;               // about the atoms of a brick of a solid
+constexpr int kCandCap = 12;                      // candidates (r^2 below the band's upper edge) kept per atom
 
 struct MdGeom {
   double H[9], Hinv[9];
@@ -334,29 +338,31 @@ __device__ __noinline__ void md_search_atom(int N, int M, int i, const double *_
   }
 }
 
-// Neighbour lists by bricks of 4x4x4 cells, full shell, no atomics: a CTA stages the records of its
-// brick and of the cells around it (6x6x6) in shared memory as brick coordinates (the in-cell
-// position plus the halo cell's offset, (h - 1) E), with the halo cell index packed above the atom
-// index. One thread per atom of the brick tests the 9 rows (o0, o1) of its shell; the three cells of a
-// row lie consecutively in the stage, so a row is one run of records. Members (at most kMdMaxM kept in
+// Neighbour lists by bricks of 4x4x6 cells, full shell, no atomics: a CTA stages the records of its
+// brick and of the cells around it (6x6x8) in shared memory as brick coordinates (the in-cell
+// position plus the halo cell's offset, (h - 1) E), with each record's halo cell beside it. One
+// thread per atom of the brick tests the 9 rows (o0, o1) of its shell; the three cells of a row lie
+// consecutively in the stage, so a row is one run of records. Members (at most kMdMaxM kept in
 // registers) are sorted and written by md_emit. A brick whose surroundings hold more than kStageCap
 // atoms, and an atom with more than kMdMaxM members, take the global-memory path (md_search_atom).
-__global__ void __launch_bounds__(kMdThreads, 8) md_search_kernel(
+__global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
     int N, int M, const double *__restrict__ pos, const __grid_constant__ MdGeom G, const float4 *__restrict__ x4,
     const int4 *__restrict__ m4, const int *__restrict__ cellcnt, const float4 *__restrict__ cellx,
     int *__restrict__ cnt, unsigned *__restrict__ keys, int *__restrict__ nbr, char4 *__restrict__ shift,
     unsigned *status) {
   __shared__ float4 s_u[kStageCap];
+  __shared__ unsigned short s_h[kStageCap];        // halo cell of each staged record
+  __shared__ unsigned short s_cand[kCandCap * kSearchThreads];   // candidates of each thread, [u][tid]
   __shared__ int s_cnt[kHaloCells], s_start[kHaloCells], s_gcell[kHaloCells];
   __shared__ int s_ipre[kBrickCells + 1];
   __shared__ int s_total;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int nb2 = (G.nc[2] + kBrick - 1) / kBrick, nb1 = (G.nc[1] + kBrick - 1) / kBrick;
-  const int o0 = (blockIdx.x / (nb2 * nb1)) * kBrick, o1 = ((blockIdx.x / nb2) % nb1) * kBrick,
-            o2 = (blockIdx.x % nb2) * kBrick;   // first interior cell of the brick
+  const int nb2 = (G.nc[2] + kBZ - 1) / kBZ, nb1 = (G.nc[1] + kBY - 1) / kBY;
+  const int o0 = (blockIdx.x / (nb2 * nb1)) * kBX, o1 = ((blockIdx.x / nb2) % nb1) * kBY,
+            o2 = (blockIdx.x % nb2) * kBZ;   // first interior cell of the brick
   // 1. counts of the halo cells; a halo cell beyond nc is next to no interior cell and stays empty
-  for (int h = tid; h < kHaloCells; h += kMdThreads) {
-    const int h0 = h / (kHaloEdge * kHaloEdge), h1 = (h / kHaloEdge) % kHaloEdge, h2 = h % kHaloEdge;
+  for (int h = tid; h < kHaloCells; h += kSearchThreads) {
+    const int h0 = h / (kHY * kHZ), h1 = (h / kHZ) % kHY, h2 = h % kHZ;
     const int c0 = o0 + h0 - 1, c1 = o1 + h1 - 1, c2 = o2 + h2 - 1;
     int n = 0, g = 0;
     if (c0 <= G.nc[0] && c1 <= G.nc[1] && c2 <= G.nc[2]) {
@@ -371,12 +377,13 @@ __global__ void __launch_bounds__(kMdThreads, 8) md_search_kernel(
     s_gcell[h] = g;
   }
   __syncthreads();
-  // 2. warp 0: exclusive sums over the halo cells (7 per lane) and over the interior cells (2 per lane)
+  // 2. warp 0: exclusive sums over the halo cells (9 per lane) and over the interior cells (3 per lane)
+  static_assert(kHaloCells == 9 * 32 && kBrickCells == 3 * 32, "the scans map 9 and 3 cells onto each lane");
   if (tid < 32) {
-    int a[7], tot = 0;
+    int a[9], tot = 0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const int h = 7 * lane + k;
+    for (int k = 0; k < 9; ++k) {
+      const int h = 9 * lane + k;
       a[k] = h < kHaloCells ? s_cnt[h] : 0;
       tot += a[k];
     }
@@ -387,27 +394,28 @@ __global__ void __launch_bounds__(kMdThreads, 8) md_search_kernel(
     }
     int run = inc - tot;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const int h = 7 * lane + k;
+    for (int k = 0; k < 9; ++k) {
+      const int h = 9 * lane + k;
       if (h < kHaloCells) s_start[h] = run;
       run += a[k];
     }
     if (lane == 31) s_total = inc;
-    int b[2];
+    int b[3];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const int q = 2 * lane + k, q0 = q / (kBrick * kBrick), q1 = (q / kBrick) % kBrick, q2 = q % kBrick;
+    for (int k = 0; k < 3; ++k) {
+      const int q = 3 * lane + k, q0 = q / (kBY * kBZ), q1 = (q / kBZ) % kBY, q2 = q % kBZ;
       const bool in = o0 + q0 < G.nc[0] && o1 + q1 < G.nc[1] && o2 + q2 < G.nc[2];
-      b[k] = in ? s_cnt[((q0 + 1) * kHaloEdge + q1 + 1) * kHaloEdge + q2 + 1] : 0;
+      b[k] = in ? s_cnt[((q0 + 1) * kHY + q1 + 1) * kHZ + q2 + 1] : 0;
     }
-    const int t2 = b[0] + b[1];
+    const int t2 = b[0] + b[1] + b[2];
     int inc2 = t2;
     for (int off = 1; off < 32; off <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, inc2, off);
       if (lane >= off) inc2 += v;
     }
-    s_ipre[2 * lane] = inc2 - t2;
-    s_ipre[2 * lane + 1] = inc2 - t2 + b[0];
+    s_ipre[3 * lane] = inc2 - t2;
+    s_ipre[3 * lane + 1] = inc2 - t2 + b[0];
+    s_ipre[3 * lane + 2] = inc2 - t2 + b[0] + b[1];
     if (lane == 31) s_ipre[kBrickCells] = inc2;
   }
   __syncthreads();
@@ -415,26 +423,26 @@ __global__ void __launch_bounds__(kMdThreads, 8) md_search_kernel(
   const int total = s_total;
   const bool staged = total <= kStageCap;
   if (staged) {
-    for (int t = tid; t < total; t += kMdThreads) {
+    for (int t = tid; t < total; t += kSearchThreads) {
       int h = 0;
-      for (int step = 128; step > 0; step >>= 1)
+      for (int step = 256; step > 0; step >>= 1)
         if (h + step < kHaloCells && s_start[h + step] <= t) h += step;
-      const int h0 = h / (kHaloEdge * kHaloEdge), h1 = (h / kHaloEdge) % kHaloEdge, h2 = h % kHaloEdge;
+      const int h0 = h / (kHY * kHZ), h1 = (h / kHZ) % kHY, h2 = h % kHZ;
       const float4 r = cellx[(size_t)s_gcell[h] * kMdCap + (t - s_start[h])];
       const float3 B = md_cart(G, (float)(h0 - 1), (float)(h1 - 1), (float)(h2 - 1));
-      s_u[t] = make_float4(B.x + r.x, B.y + r.y, B.z + r.z,
-                           __int_as_float(__float_as_int(r.w) | (h << 24)));
+      s_u[t] = make_float4(B.x + r.x, B.y + r.y, B.z + r.z, r.w);
+      s_h[t] = (unsigned short)h;
     }
   }
   __syncthreads();
   // 4. one thread per atom of the brick
   const int A = s_ipre[kBrickCells];
-  for (int a = tid; a < A; a += kMdThreads) {
+  for (int a = tid; a < A; a += kSearchThreads) {
     int k = 0;                                     // interior cell of atom a
-    for (int step = kBrickCells / 2; step > 0; step >>= 1)
-      if (s_ipre[k + step] <= a) k += step;
-    const int k0 = k / (kBrick * kBrick), k1 = (k / kBrick) % kBrick, k2 = k % kBrick;
-    const int hi = ((k0 + 1) * kHaloEdge + k1 + 1) * kHaloEdge + k2 + 1;
+    for (int step = 64; step > 0; step >>= 1)
+      if (k + step < kBrickCells && s_ipre[k + step] <= a) k += step;
+    const int k0 = k / (kBY * kBZ), k1 = (k / kBZ) % kBY, k2 = k % kBZ;
+    const int hi = ((k0 + 1) * kHY + k1 + 1) * kHZ + k2 + 1;
     const int own = a - s_ipre[k];
     if (!staged) {
       const int i = __float_as_int(cellx[(size_t)s_gcell[hi] * kMdCap + own].w);
@@ -443,37 +451,52 @@ __global__ void __launch_bounds__(kMdThreads, 8) md_search_kernel(
     }
     const int slot = s_start[hi] + own;
     const float4 ei = s_u[slot];
-    const int i = __float_as_int(ei.w) & 0xffffff;
+    const int i = __float_as_int(ei.w);
+    // the scan keeps only the stage positions of the candidates within the band's upper edge (atom i's
+    // own record among them), so that the lanes of a warp that find one do little work
+    int nc = 0;
+#pragma unroll 1
+    for (int ab = 0; ab < 9; ++ab) {
+      const int ra = ab / 3, rb = ab - 3 * ra;
+      const int hc = hi + ((ra - 1) * kHY + (rb - 1)) * kHZ;   // the row's middle cell
+      const int pend = s_start[hc + 1] + s_cnt[hc + 1];
+      for (int p = s_start[hc - 1]; p < pend; ++p) {
+        const float4 ej = s_u[p];
+        const float dx = __fsub_rn(ej.x, ei.x), dy = __fsub_rn(ej.y, ei.y), dz = __fsub_rn(ej.z, ei.z);
+        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+        if (r2 <= G.cut2_hi) {
+          if (nc < kCandCap) s_cand[nc * kSearchThreads + tid] = (unsigned short)p;
+          ++nc;
+        }
+      }
+    }
+    if (nc > kCandCap) {
+      md_search_atom(N, M, i, pos, G, x4, m4, cellcnt, cellx, cnt, keys, nbr, shift, status);
+      continue;
+    }
+    // members among the candidates: the FP32 distance decides below the band, the exact test in it
     const int4 mi = m4[i];
     const int c0 = o0 + k0, c1 = o1 + k1, c2 = o2 + k2;
     unsigned kk[kMdMaxM];
 #pragma unroll
     for (int u = 0; u < kMdMaxM; ++u) kk[u] = 0xffffffffu;
     int count = 0;
-#pragma unroll 1
-    for (int ab = 0; ab < 9; ++ab) {
-      const int ra = ab / 3, rb = ab - 3 * ra;
-      const int hc = hi + ((ra - 1) * kHaloEdge + (rb - 1)) * kHaloEdge;   // the row's middle cell
-      const int pend = s_start[hc + 1] + s_cnt[hc + 1];
-      for (int p = s_start[hc - 1]; p < pend; ++p) {
-        const float4 ej = s_u[p];
-        const float dx = __fsub_rn(ej.x, ei.x), dy = __fsub_rn(ej.y, ei.y), dz = __fsub_rn(ej.z, ei.z);
-        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        if (r2 > G.cut2_hi || p == slot) continue;
-        const unsigned tag = (unsigned)__float_as_int(ej.w);
-        const int j = (int)(tag & 0xffffffu), hj = (int)(tag >> 24);
-        const int d0 = hj / (kHaloEdge * kHaloEdge) - (k0 + 1), d1 = (hj / kHaloEdge) % kHaloEdge - (k1 + 1),
-                  d2 = hj % kHaloEdge - (k2 + 1);
-        int g;
-        const int w0 = md_wrap(c0 + d0, G.nc[0], g), w1 = md_wrap(c1 + d1, G.nc[1], g),
-                  w2 = md_wrap(c2 + d2, G.nc[2], g);
-        if (md_pair_in(G, pos, m4, i, j, mi, w0, w1, w2, make_float3(dx, dy, dz))) {
-          const unsigned key = ((unsigned)j << 6) | (unsigned)(((d0 + 1) << 4) | ((d1 + 1) << 2) | (d2 + 1));
+    for (int u = 0; u < nc; ++u) {
+      const int p = s_cand[u * kSearchThreads + tid];
+      if (p == slot) continue;
+      const float4 ej = s_u[p];
+      const float dx = __fsub_rn(ej.x, ei.x), dy = __fsub_rn(ej.y, ei.y), dz = __fsub_rn(ej.z, ei.z);
+      const int j = __float_as_int(ej.w), hj = s_h[p];
+      const int d0 = hj / (kHY * kHZ) - (k0 + 1), d1 = (hj / kHZ) % kHY - (k1 + 1), d2 = hj % kHZ - (k2 + 1);
+      int g;
+      const int w0 = md_wrap(c0 + d0, G.nc[0], g), w1 = md_wrap(c1 + d1, G.nc[1], g),
+                w2 = md_wrap(c2 + d2, G.nc[2], g);
+      if (md_pair_in(G, pos, m4, i, j, mi, w0, w1, w2, make_float3(dx, dy, dz))) {
+        const unsigned key = ((unsigned)j << 6) | (unsigned)(((d0 + 1) << 4) | ((d1 + 1) << 2) | (d2 + 1));
 #pragma unroll
-          for (int u = 0; u < kMdMaxM; ++u)
-            if (u == count) kk[u] = key;
-          ++count;
-        }
+        for (int v = 0; v < kMdMaxM; ++v)
+          if (v == count) kk[v] = key;
+        ++count;
       }
     }
     if (count > kMdMaxM) {
@@ -932,9 +955,8 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   cudaMemsetAsync(static_cast<char *>(c.md_red.p) + md_counter_offset(7, nblk), 0, (ngroups + 1) * sizeof(unsigned), s);
   md_cells_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(), x4, m4,
                                               cnt, st);
-  const long nbricks = (long)((G.nc[0] + kBrick - 1) / kBrick) * ((G.nc[1] + kBrick - 1) / kBrick) *
-                       ((G.nc[2] + kBrick - 1) / kBrick);
-  md_search_kernel<<<(unsigned)nbricks, kMdThreads, 0, s>>>(N, M, pos, G, x4, m4, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(),
+  const long nbricks = (long)((G.nc[0] + kBX - 1) / kBX) * ((G.nc[1] + kBY - 1) / kBY) * ((G.nc[2] + kBZ - 1) / kBZ);
+  md_search_kernel<<<(unsigned)nbricks, kSearchThreads, 0, s>>>(N, M, pos, G, x4, m4, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(),
                                                cnt, keys, c.md_nbr.as<int>(), c.md_shift.as<char4>(), st);
   const double D0 = x[0], al = x[1], r0 = x[2], be = x[3], n = x[4], h = x[5];
   const double log2e = 1.4426950408889634;
