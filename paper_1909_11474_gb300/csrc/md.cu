@@ -663,18 +663,24 @@ inline size_t md_counter_offset(int K, int nblk) {
 __device__ __forceinline__ int md_reverse_slot(int N, int M, int i, unsigned key, const int *__restrict__ cnt,
                                                const unsigned *__restrict__ keys, unsigned *status) {
   const int j = (int)(key >> 6);
+  // the partner's first four keys are loaded beside its count, not after it (entries past the count
+  // are ignored below)
+  unsigned q[kMdMaxM];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) q[f] = f < M ? keys[(size_t)f * N + j] : 0xffffffffu;
   const int cj = cnt[j];
   if (cj > kMdMaxM) return -1;
   const int cjm = min(cj, M);
+#pragma unroll
+  for (int f = 4; f < kMdMaxM; ++f) q[f] = f < cjm ? keys[(size_t)f * N + j] : 0xffffffffu;
   const unsigned want = ((unsigned)i << 6) | (kOffNeg - (key & 63u));
   int rank = 0;
   bool found = false;
 #pragma unroll
   for (int f = 0; f < kMdMaxM; ++f)
     if (f < cjm) {
-      const unsigned q = keys[(size_t)f * N + j];
-      rank += q < want ? 1 : 0;
-      found = found || q == want;
+      rank += q[f] < want ? 1 : 0;
+      found = found || q[f] == want;
     }
   if (!found) {
     set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);

@@ -411,8 +411,9 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
       int count = 0;
       const float4 si = s_fr[li];
       for (int jb = 0; single && ok && jb < nat; jb += 32) {
-        // at most one candidate image per j: n = round(-(s_j - s_i)) where |s_j - s_i + n| <= rng on
-        // every axis (the integers of the closed range [-ds - rng, -ds + rng]), |n| <= nimg
+        // at most one candidate image per j: n = round(-(s_j - s_i)), |n| <= nimg. Whether it lies
+        // within the image range (|s_j - s_i + n| <= rng) need not be tested: an image outside it is
+        // farther than R2 by more than the band, and the membership test rejects it
         const int jl = jb + lane;
         float dx = 0.f, dy = 0.f, dz = 0.f, f0 = 0.f, f1 = 0.f, f2 = 0.f;
         bool cand = false;
@@ -426,8 +427,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
           f1 = rintf(-d1);
           f2 = rintf(-d2);
           const float lim = (float)nimg;
-          cand = fabsf(d0 + f0) <= q.rng[0] && fabsf(d1 + f1) <= q.rng[1] && fabsf(d2 + f2) <= q.rng[2] &&
-                 fabsf(f0) <= lim && fabsf(f1) <= lim && fabsf(f2) <= lim &&
+          cand = fabsf(f0) <= lim && fabsf(f1) <= lim && fabsf(f2) <= lim &&
                  !(jl == li && f0 == 0.f && f1 == 0.f && f2 == 0.f);
         }
         const int j = a0 + (jl < nat ? jl : 0);

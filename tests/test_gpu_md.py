@@ -152,3 +152,25 @@ def test_md_short_lists_flag_overflow_and_count_every_neighbour(ctx):
         full = {(int(j), tuple(n)) for j, n in zip(nl["j"][e], nl["n"][e])}
         kept = [(int(j), tuple(n)) for j, n in zip(nbr[i], shift[i])]
         assert all(k in full for k in kept) and kept == sorted(kept)
+
+
+def test_md_nonfinite_atom_is_flagged_and_left_out(ctx):
+    """An atom with a non-finite position gets no cell: the call flags it, its list is empty, and the
+    other atoms' lists are the oracle's lists of the cell without it."""
+    from paper_1909_11474_gb300 import binding
+    pos, box = _cell((3, 3, 3), 0.08, 0.0, 3)
+    bad = 17
+    pos_nan = pos.copy()
+    pos_nan[bad, 2] = np.nan
+    ctx.md_force(torch.tensor(pos_nan, device="cuda"), box, I.TABLE2_PARAMS)
+    assert ctx.get_status() & binding.STATUS_NONFINITE
+    cnt, nbr, shift = ctx.md_export_neighbors()
+    assert cnt[bad] == 0
+    idx = np.flatnonzero(np.arange(len(pos)) != bad)
+    nl = oracle.neighbor_list(pos[idx], box, 3.2)
+    for a, i in enumerate(idx):
+        e = slice(nl["off"][a], nl["off"][a + 1])
+        assert cnt[i] == nl["off"][a + 1] - nl["off"][a]
+        assert np.array_equal(nbr[i, :cnt[i]], idx[nl["j"][e]])
+        assert np.array_equal(shift[i, :cnt[i]], nl["n"][e])
+    _md(ctx, pos, box, I.TABLE2_PARAMS, 32)      # the next call on finite positions is clean
