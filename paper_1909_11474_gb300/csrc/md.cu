@@ -616,16 +616,15 @@ __device__ __forceinline__ double md_block_sum(const double *src, size_t stride,
 // Deterministic in-kernel sum of per-block partials [K][nblk] (FP64; blocks of kMdThreads threads):
 // the last block of each group of kMdGroup blocks to finish sums its group into [K][ngroups], and
 // the last group to finish sums the groups, both in a fixed order; quantity 0 goes to *out0 and
-// quantity k >= 1 to out_rest[k - 1]. Counters [ngroups + 1] follow the group sums and are zeroed
-// before the launch. The threads that wrote the block's partials have fenced before the call.
+// quantity k >= 1 to out_rest[k - 1]. The group sums follow the partials; the counters [ngroups + 1]
+// are zeroed before the launch. The threads that wrote the block's partials have fenced before the call.
 constexpr int kMdGroup = 64;
 template <int K>
-__device__ __forceinline__ void md_grouped_sum(double *partial, int nblk, int b, double *out0, double *out_rest,
-                                               double (*red)[7]) {
+__device__ __forceinline__ void md_grouped_sum(double *partial, unsigned *counter, int nblk, int b, double *out0,
+                                               double *out_rest, double (*red)[7]) {
   __shared__ int s_last;
   const int tid = threadIdx.x, ngroups = (nblk + kMdGroup - 1) / kMdGroup;
   double *gpart = partial + (size_t)K * nblk;
-  unsigned *counter = reinterpret_cast<unsigned *>(gpart + (size_t)K * ngroups);
   const int g = b / kMdGroup, g0 = g * kMdGroup, gn = min(kMdGroup, nblk - g0);
   __syncthreads();
   if (tid == 0) s_last = atomicAdd(&counter[g], 1u) == (unsigned)(gn - 1);
@@ -691,16 +690,15 @@ __device__ __forceinline__ int md_reverse_slot(int N, int M, int i, unsigned key
 
 // Passes 1-2 of atom i (m entries) with arrays for M >= m bonds (Mw = the warp's largest count): the
 // bond geometry (FP32: the search's separation; FP64: the exact FP64 bond vector), md_atom, and the
-// P_ij of every entry, into Pst at the entry's own slot (e, i) and into Prev at the reverse entry's
-// slot (rank, j), so that the gather reads both rows of atom i in order.
+// P_ij of every entry: summed over the entries in order into Fo (atom i's own part of F_i), and stored
+// at the reverse entry's slot (rank, j) of Prev, so that the gather reads atom i's rows in order.
 template <int Mw, typename R>
 __device__ __forceinline__ void md_force_atom(int N, int M, int i, int m, const MdGeom &G, const PConsts<R> &K,
                                               const double *__restrict__ pos, const float4 *__restrict__ x4,
                                               const unsigned *__restrict__ keys, const int *__restrict__ cnt,
                                               const int *__restrict__ nbr, const char4 *__restrict__ shift,
-                                              float4 xi, typename Vec4<R>::T *__restrict__ Pst,
-                                              typename Vec4<R>::T *__restrict__ Prev, unsigned *status, R &U,
-                                              R (&Wv)[6]) {
+                                              float4 xi, typename Vec4<R>::T *__restrict__ Prev,
+                                              unsigned *status, R &U, R (&Wv)[6], R (&Fo)[3]) {
   using R4 = typename Vec4<R>::T;
   constexpr int M_ = Mw;
   R ux[M_], uy[M_], uz[M_], r[M_], ir[M_], fc[M_], fcp[M_];
@@ -758,13 +756,17 @@ __device__ __forceinline__ void md_force_atom(int N, int M, int i, int m, const 
 #pragma unroll
   for (int e = 0; e < M_; ++e)
     if (e < m) {
-      R4 v;
-      v.x = Px[e];
-      v.y = Py[e];
-      v.z = Pz[e];
-      v.w = R(0);
-      Pst[(size_t)e * N + i] = v;
-      if (rs[e] >= 0) Prev[rs[e]] = v;
+      Fo[0] += Px[e];
+      Fo[1] += Py[e];
+      Fo[2] += Pz[e];
+      if (rs[e] >= 0) {
+        R4 v;
+        v.x = Px[e];
+        v.y = Py[e];
+        v.z = Pz[e];
+        v.w = R(0);
+        Prev[rs[e]] = v;
+      }
     }
 }
 
@@ -772,7 +774,7 @@ __device__ __forceinline__ void md_force_atom(int N, int M, int i, int m, const 
 // the register count of the kernel, which the short lists of solids need.
 template <typename R>
 struct MdSums {
-  R U, W[6];
+  R U, W[6], F[3];
 };
 template <int Mw, typename R>
 __device__ __noinline__ MdSums<R> md_force_atom_long(int N, int M, int i, int m, const MdGeom &G,
@@ -780,13 +782,13 @@ __device__ __noinline__ MdSums<R> md_force_atom_long(int N, int M, int i, int m,
                                                      const float4 *__restrict__ x4, const unsigned *__restrict__ keys,
                                                      const int *__restrict__ cnt, const int *__restrict__ nbr,
                                                      const char4 *__restrict__ shift, float4 xi,
-                                                     typename Vec4<R>::T *__restrict__ Pst,
                                                      typename Vec4<R>::T *__restrict__ Prev, unsigned *status) {
   MdSums<R> o;
   o.U = R(0);
 #pragma unroll
   for (int k = 0; k < 6; ++k) o.W[k] = R(0);
-  md_force_atom<Mw, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Pst, Prev, status, o.U, o.W);
+  o.F[0] = o.F[1] = o.F[2] = R(0);
+  md_force_atom<Mw, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Prev, status, o.U, o.W, o.F);
   return o;
 }
 
@@ -794,8 +796,8 @@ template <typename R>
 __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 8 : 1) md_force_kernel(
     int N, int M, const MdGeom G, const PConsts<R> K, const double *__restrict__ pos,
     const float4 *__restrict__ x4, const unsigned *__restrict__ keys, const int *__restrict__ cnt,
-    const int *__restrict__ nbr, const char4 *__restrict__ shift, typename Vec4<R>::T *__restrict__ Pst,
-    typename Vec4<R>::T *__restrict__ Prev, double *__restrict__ partial, double *__restrict__ E,
+    const int *__restrict__ nbr, const char4 *__restrict__ shift, typename Vec4<R>::T *__restrict__ Fown,
+    typename Vec4<R>::T *__restrict__ Prev, double *__restrict__ partial, unsigned *counters, double *__restrict__ E,
     double *__restrict__ W, unsigned *status) {
   __shared__ double red[kMdThreads / 32][7];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -807,18 +809,19 @@ __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 8 : 1) md_force_k
   }
   float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
   if (sizeof(R) == 4 && valid) xi = x4[i];
-  R U = R(0), Wv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  R U = R(0), Wv[6] = {R(0), R(0), R(0), R(0), R(0), R(0)}, Fo[3] = {R(0), R(0), R(0)};
   // arrays sized by the warp's largest neighbour count, so that the common short lists keep few
   // values live
   const int Mw = __reduce_max_sync(0xffffffffu, (unsigned)m);
   switch (Mw) {
 #define TSF_MDCASE(MM) \
-    case MM: md_force_atom<MM, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Pst, Prev, status, U, Wv); break;
+    case MM: md_force_atom<MM, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Prev, status, U, Wv, Fo); break;
 #define TSF_MDLONG(MM)                                                                      \
     case MM: {                                                                              \
-      const MdSums<R> o = md_force_atom_long<MM, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Pst, Prev, status); \
+      const MdSums<R> o = md_force_atom_long<MM, R>(N, M, i, m, G, K, pos, x4, keys, cnt, nbr, shift, xi, Prev, status); \
       U = o.U;                                                                              \
       for (int k = 0; k < 6; ++k) Wv[k] = o.W[k];                                           \
+      for (int k = 0; k < 3; ++k) Fo[k] = o.F[k];                                           \
       break;                                                                                \
     }
     TSF_MDCASE(1) TSF_MDCASE(2) TSF_MDCASE(3) TSF_MDCASE(4) TSF_MDLONG(5) TSF_MDLONG(6) TSF_MDLONG(7)
@@ -826,6 +829,14 @@ __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 8 : 1) md_force_k
 #undef TSF_MDCASE
 #undef TSF_MDLONG
     default: break;
+  }
+  if (valid) {
+    typename Vec4<R>::T f;
+    f.x = Fo[0];
+    f.y = Fo[1];
+    f.z = Fo[2];
+    f.w = R(0);
+    Fown[i] = f;
   }
   // per-warp sums in R, per-block FP64 partial sums of U and W, stored [7][blocks]
   R v[7] = {U, Wv[0], Wv[1], Wv[2], Wv[3], Wv[4], Wv[5]};
@@ -844,28 +855,28 @@ __global__ void __launch_bounds__(kMdThreads, sizeof(R) == 4 ? 8 : 1) md_force_k
     partial[(size_t)tid * nblk + b] = s;
     __threadfence();                               // the partial before this block's count
   }
-  md_grouped_sum<7>(partial, nblk, b, E, W, red);
+  md_grouped_sum<7>(partial, counters, nblk, b, E, W, red);
 }
 
-// F_i = sum_e (P_ij - P_ji) over atom i's entries e = (j, n): P_ij from Pst row e, P_ji from Prev row e
-// (written there by atom j). An atom with more than kMdMaxM entries has no P (the force kernel flags
-// it) and gets F = 0.
+// F_i = sum_e P_ij - sum_e P_ji over atom i's entries e = (j, n): the first sum from Fown (the force
+// kernel's), P_ji from Prev row e (written there by atom j). An atom with more than kMdMaxM entries
+// has no P (the force kernel flags it) and gets F = 0.
 template <typename R>
-__global__ void md_gather_kernel(int N, int M, const int *__restrict__ cnt, const typename Vec4<R>::T *__restrict__ Pst,
+__global__ void md_gather_kernel(int N, int M, const int *__restrict__ cnt, const typename Vec4<R>::T *__restrict__ Fown,
                                  const typename Vec4<R>::T *__restrict__ Prev, R *__restrict__ F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int ci = cnt[i];
   const int m = ci <= kMdMaxM ? min(ci, M) : 0;
-  R Fx = R(0), Fy = R(0), Fz = R(0);
+  const auto f = Fown[i];
+  R Fx = f.x, Fy = f.y, Fz = f.z;
 #pragma unroll
   for (int e = 0; e < kMdMaxM; ++e)
     if (e < m) {
-      const auto a = Pst[(size_t)e * N + i];
       const auto b = Prev[(size_t)e * N + i];
-      Fx += a.x - b.x;
-      Fy += a.y - b.y;
-      Fz += a.z - b.z;
+      Fx -= b.x;
+      Fy -= b.y;
+      Fz -= b.z;
     }
   F[3 * (size_t)i] = Fx;
   F[3 * (size_t)i + 1] = Fy;
@@ -942,10 +953,10 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   const int nblk = (N + kMdThreads - 1) / kMdThreads;
   const int ngroups = (nblk + kMdGroup - 1) / kMdGroup;
   const size_t rs = precision == 64 ? 8 : 4;
-  if (c.md_cellcnt.ensure(ncells * sizeof(int)) || c.md_cells.ensure(ncells * kMdCap * sizeof(float4)) ||
+  if (c.md_cellcnt.ensure((ncells + ngroups + 1) * sizeof(int)) || c.md_cells.ensure(ncells * kMdCap * sizeof(float4)) ||
       c.md_pos.ensure((size_t)N * (sizeof(float4) + sizeof(int4))) || c.md_cnt.ensure((size_t)N * sizeof(int)) ||
       c.md_nbr.ensure((size_t)N * M * sizeof(int)) || c.md_shift.ensure((size_t)N * M * sizeof(char4)) ||
-      c.md_keys.ensure((size_t)N * M * sizeof(unsigned)) || c.md_Pij.ensure((size_t)N * kMdMaxM * 8 * rs) ||
+      c.md_keys.ensure((size_t)N * M * sizeof(unsigned)) || c.md_Pij.ensure((size_t)N * (kMdMaxM + 1) * 4 * rs) ||
       c.md_red.ensure(md_sum_bytes(7, nblk))) {
     err = "device allocation failed";
     return TERSOFF_E_CUDA;
@@ -957,8 +968,9 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   unsigned *st = c.status.as<unsigned>();
   int *cnt = c.md_cnt.as<int>();
   unsigned *keys = c.md_keys.as<unsigned>();
-  cudaMemsetAsync(c.md_cellcnt.p, 0, ncells * sizeof(int), s);
-  cudaMemsetAsync(static_cast<char *>(c.md_red.p) + md_counter_offset(7, nblk), 0, (ngroups + 1) * sizeof(unsigned), s);
+  // cell counts and the force kernel's sum counters, both zero at the start of the call: one memset
+  unsigned *sum_counters = c.md_cellcnt.as<unsigned>() + ncells;
+  cudaMemsetAsync(c.md_cellcnt.p, 0, (ncells + ngroups + 1) * sizeof(int), s);
   md_cells_kernel<<<nblk, kMdThreads, 0, s>>>(N, pos, G, c.md_cellcnt.as<int>(), c.md_cells.as<float4>(), x4, m4,
                                               cnt, st);
   const long nbricks = (long)((G.nc[0] + kBX - 1) / kBX) * ((G.nc[1] + kBY - 1) / kBY) * ((G.nc[2] + kBZ - 1) / kBZ);
@@ -968,19 +980,19 @@ int md_force(Ctx &c, int N, const double *pos, const double *boxh, const double 
   const double log2e = 1.4426950408889634;
   if (precision == 64) {
     PConsts<double> K{D0, -al * log2e, r0, -0.5 * al, be, h, n, -0.5 / n};
-    dvec4 *Pst = c.md_Pij.as<dvec4>(), *Prev = Pst + (size_t)N * kMdMaxM;
+    dvec4 *Fown = c.md_Pij.as<dvec4>(), *Prev = Fown + N;
     md_force_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, x4, keys, cnt, c.md_nbr.as<int>(),
-                                                        c.md_shift.as<char4>(), Pst, Prev, c.md_red.as<double>(),
+                                                        c.md_shift.as<char4>(), Fown, Prev, c.md_red.as<double>(), sum_counters,
                                                         E, W, st);
-    md_gather_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, cnt, Pst, Prev, reinterpret_cast<double *>(F));
+    md_gather_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, M, cnt, Fown, Prev, reinterpret_cast<double *>(F));
   } else {
     PConsts<float> K{(float)D0, (float)(-al * log2e), (float)r0, (float)(-0.5 * al), (float)be, (float)h,
                      (float)n, (float)(-0.5 / n)};
-    float4 *Pst = c.md_Pij.as<float4>(), *Prev = Pst + (size_t)N * kMdMaxM;
+    float4 *Fown = c.md_Pij.as<float4>(), *Prev = Fown + N;
     md_force_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, G, K, pos, x4, keys, cnt, c.md_nbr.as<int>(),
-                                                       c.md_shift.as<char4>(), Pst, Prev, c.md_red.as<double>(),
+                                                       c.md_shift.as<char4>(), Fown, Prev, c.md_red.as<double>(), sum_counters,
                                                        E, W, st);
-    md_gather_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, cnt, Pst, Prev, reinterpret_cast<float *>(F));
+    md_gather_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, M, cnt, Fown, Prev, reinterpret_cast<float *>(F));
   }
   cudaError_t e = launched(4);   // cells, search, force (with the sums), gather
   if (e != cudaSuccess) {
@@ -1023,7 +1035,8 @@ template <typename R>
 __global__ void __launch_bounds__(kMdThreads) md_kick_kernel(int N, double *__restrict__ vel,
                                                              const R *__restrict__ F, const double *__restrict__ mass,
                                                              const double *__restrict__ acc, double dt,
-                                                             double *__restrict__ partial, double *__restrict__ Ekin) {
+                                                             double *__restrict__ partial, unsigned *counters,
+                                                             double *__restrict__ Ekin) {
   __shared__ double red[kMdThreads / 32][7];
   const int i = blockIdx.x * blockDim.x + threadIdx.x, tid = threadIdx.x;
   double ke = 0.0;
@@ -1047,7 +1060,7 @@ __global__ void __launch_bounds__(kMdThreads) md_kick_kernel(int N, double *__re
     partial[blockIdx.x] = s;
     __threadfence();
   }
-  md_grouped_sum<1>(partial, gridDim.x, blockIdx.x, Ekin, nullptr, red);
+  md_grouped_sum<1>(partial, counters, gridDim.x, blockIdx.x, Ekin, nullptr, red);
 }
 
 int md_nve(Ctx &c, int N, double *pos, double *vel, const double *mass, const double *boxh, const double *x,
@@ -1061,17 +1074,17 @@ int md_nve(Ctx &c, int N, double *pos, double *vel, const double *mass, const do
     return TERSOFF_E_CUDA;
   }
   double *part = c.md_ke.as<double>();
-  char *counters = static_cast<char *>(c.md_ke.p) + md_counter_offset(1, nblk);
+  unsigned *counters = reinterpret_cast<unsigned *>(static_cast<char *>(c.md_ke.p) + md_counter_offset(1, nblk));
   double *acc = reinterpret_cast<double *>(static_cast<char *>(c.md_ke.p) + sum_bytes);
   md_accel_kernel<<<nblk, kMdThreads, 0, s>>>(N, mass, acc);
   auto kick = [&](double h, int step) {
     cudaMemsetAsync(counters, 0, (ngroups + 1) * sizeof(unsigned), s);
     if (precision == 64)
       md_kick_kernel<double><<<nblk, kMdThreads, 0, s>>>(N, vel, static_cast<const double *>(F), mass, acc, h, part,
-                                                         Ekin + step);
+                                                         counters, Ekin + step);
     else
       md_kick_kernel<float><<<nblk, kMdThreads, 0, s>>>(N, vel, static_cast<const float *>(F), mass, acc, h, part,
-                                                        Ekin + step);
+                                                        counters, Ekin + step);
   };
   int rc = md_force(c, N, pos, boxh, x, R1, R2, M, precision, Epot, F, W, s, err);
   if (rc != TERSOFF_OK) return rc;
