@@ -419,19 +419,32 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
     if (lane == 31) s_ipre[kBrickCells] = inc2;
   }
   __syncthreads();
-  // 3. stage the records, one thread per record (its cell by binary search over the starts)
+  // 3. stage the records, one thread per halo cell (its first four records loaded together)
   const int total = s_total;
   const bool staged = total <= kStageCap;
   if (staged) {
-    for (int t = tid; t < total; t += kSearchThreads) {
-      int h = 0;
-      for (int step = 256; step > 0; step >>= 1)
-        if (h + step < kHaloCells && s_start[h + step] <= t) h += step;
+    for (int h = tid; h < kHaloCells; h += kSearchThreads) {
+      const int n = s_cnt[h];
+      if (n == 0) continue;
       const int h0 = h / (kHY * kHZ), h1 = (h / kHZ) % kHY, h2 = h % kHZ;
-      const float4 r = cellx[(size_t)s_gcell[h] * kMdCap + (t - s_start[h])];
       const float3 B = md_cart(G, (float)(h0 - 1), (float)(h1 - 1), (float)(h2 - 1));
-      s_u[t] = make_float4(B.x + r.x, B.y + r.y, B.z + r.z, r.w);
-      s_h[t] = (unsigned short)h;
+      const float4 *src = cellx + (size_t)s_gcell[h] * kMdCap;
+      const int t0 = s_start[h];
+      float4 r[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < n) r[q] = src[q];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < n) {
+          s_u[t0 + q] = make_float4(B.x + r[q].x, B.y + r[q].y, B.z + r[q].z, r[q].w);
+          s_h[t0 + q] = (unsigned short)h;
+        }
+      for (int q = 4; q < n; ++q) {
+        const float4 v = src[q];
+        s_u[t0 + q] = make_float4(B.x + v.x, B.y + v.y, B.z + v.z, v.w);
+        s_h[t0 + q] = (unsigned short)h;
+      }
     }
   }
   __syncthreads();
