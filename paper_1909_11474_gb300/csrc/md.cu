@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
     const int4 *__restrict__ m4, const int *__restrict__ cellcnt, const float4 *__restrict__ cellx,
     int *__restrict__ cnt, unsigned *__restrict__ keys, int *__restrict__ nbr, char4 *__restrict__ shift,
     unsigned *status) {
-  __shared__ float4 s_u[kStageCap];
+  __shared__ __align__(16) float s_sx[kStageCap], s_sy[kStageCap], s_sz[kStageCap];   // brick coordinates
+  __shared__ int s_sj[kStageCap];                                                       // atom index
   __shared__ unsigned short s_h[kStageCap];        // halo cell of each staged record
   __shared__ unsigned short s_cand[kCandCap * kSearchThreads];   // candidates of each thread, [u][tid]
   __shared__ int s_cnt[kHaloCells], s_start[kHaloCells], s_gcell[kHaloCells];
@@ -437,12 +438,18 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (q < n) {
-          s_u[t0 + q] = make_float4(B.x + r[q].x, B.y + r[q].y, B.z + r[q].z, r[q].w);
+          s_sx[t0 + q] = B.x + r[q].x;
+          s_sy[t0 + q] = B.y + r[q].y;
+          s_sz[t0 + q] = B.z + r[q].z;
+          s_sj[t0 + q] = __float_as_int(r[q].w);
           s_h[t0 + q] = (unsigned short)h;
         }
       for (int q = 4; q < n; ++q) {
         const float4 v = src[q];
-        s_u[t0 + q] = make_float4(B.x + v.x, B.y + v.y, B.z + v.z, v.w);
+        s_sx[t0 + q] = B.x + v.x;
+        s_sy[t0 + q] = B.y + v.y;
+        s_sz[t0 + q] = B.z + v.z;
+        s_sj[t0 + q] = __float_as_int(v.w);
         s_h[t0 + q] = (unsigned short)h;
       }
     }
@@ -463,22 +470,31 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
       continue;
     }
     const int slot = s_start[hi] + own;
-    const float4 ei = s_u[slot];
-    const int i = __float_as_int(ei.w);
+    const float4 ei = make_float4(s_sx[slot], s_sy[slot], s_sz[slot], 0.f);
+    const int i = s_sj[slot];
     // the scan keeps only the stage positions of the candidates within the band's upper edge (atom i's
-    // own record among them), so that the lanes of a warp that find one do little work
+    // own record among them), so that the lanes of a warp that find one do little work. It takes the
+    // records two at a time (aligned pairs of the stage, in packed FP32), masking the pair members
+    // outside the row's run; r^2 is the same as one at a time
+    const float2 nx = make_float2(-ei.x, -ei.x), ny = make_float2(-ei.y, -ei.y), nz = make_float2(-ei.z, -ei.z);
+    const float2 *sx2 = reinterpret_cast<const float2 *>(s_sx), *sy2 = reinterpret_cast<const float2 *>(s_sy),
+                 *sz2 = reinterpret_cast<const float2 *>(s_sz);
     int nc = 0;
 #pragma unroll 1
     for (int ab = 0; ab < 9; ++ab) {
       const int ra = ab / 3, rb = ab - 3 * ra;
       const int hc = hi + ((ra - 1) * kHY + (rb - 1)) * kHZ;   // the row's middle cell
-      const int pend = s_start[hc + 1] + s_cnt[hc + 1];
-      for (int p = s_start[hc - 1]; p < pend; ++p) {
-        const float4 ej = s_u[p];
-        const float dx = __fsub_rn(ej.x, ei.x), dy = __fsub_rn(ej.y, ei.y), dz = __fsub_rn(ej.z, ei.z);
-        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-        if (r2 <= G.cut2_hi) {
+      const int p0 = s_start[hc - 1], pend = s_start[hc + 1] + s_cnt[hc + 1];
+      for (int k2 = p0 >> 1; 2 * k2 < pend; ++k2) {
+        const float2 dx = __fadd2_rn(sx2[k2], nx), dy = __fadd2_rn(sy2[k2], ny), dz = __fadd2_rn(sz2[k2], nz);
+        const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        const int p = 2 * k2;
+        if (p >= p0 && r2.x <= G.cut2_hi) {
           if (nc < kCandCap) s_cand[nc * kSearchThreads + tid] = (unsigned short)p;
+          ++nc;
+        }
+        if (p + 1 < pend && r2.y <= G.cut2_hi) {
+          if (nc < kCandCap) s_cand[nc * kSearchThreads + tid] = (unsigned short)(p + 1);
           ++nc;
         }
       }
@@ -497,14 +513,18 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
     for (int u = 0; u < nc; ++u) {
       const int p = s_cand[u * kSearchThreads + tid];
       if (p == slot) continue;
-      const float4 ej = s_u[p];
-      const float dx = __fsub_rn(ej.x, ei.x), dy = __fsub_rn(ej.y, ei.y), dz = __fsub_rn(ej.z, ei.z);
-      const int j = __float_as_int(ej.w), hj = s_h[p];
+      const float dx = __fsub_rn(s_sx[p], ei.x), dy = __fsub_rn(s_sy[p], ei.y), dz = __fsub_rn(s_sz[p], ei.z);
+      const int j = s_sj[p], hj = s_h[p];
       const int d0 = hj / (kHY * kHZ) - (k0 + 1), d1 = (hj / kHZ) % kHY - (k1 + 1), d2 = hj % kHZ - (k2 + 1);
-      int g;
-      const int w0 = md_wrap(c0 + d0, G.nc[0], g), w1 = md_wrap(c1 + d1, G.nc[1], g),
-                w2 = md_wrap(c2 + d2, G.nc[2], g);
-      if (md_pair_in(G, pos, m4, i, j, mi, w0, w1, w2, make_float3(dx, dy, dz))) {
+      const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+      bool in = r2 < G.cut2_lo;
+      if (!in) {   // in the rounding band: the exact test, with the neighbouring cell's periodic wrap
+        int g;
+        const int w0 = md_wrap(c0 + d0, G.nc[0], g), w1 = md_wrap(c1 + d1, G.nc[1], g),
+                  w2 = md_wrap(c2 + d2, G.nc[2], g);
+        in = md_pair_in(G, pos, m4, i, j, mi, w0, w1, w2, make_float3(dx, dy, dz));
+      }
+      if (in) {
         const unsigned key = ((unsigned)j << 6) | (unsigned)(((d0 + 1) << 4) | ((d1 + 1) << 2) | (d2 + 1));
 #pragma unroll
         for (int v = 0; v < kMdMaxM; ++v)
