@@ -149,7 +149,10 @@ __global__ void md_cells_kernel(int N, const double *__restrict__ pos, const MdG
   x4[i] = make_float4(X.x, X.y, X.z, 0.f);
   const int slot = atomicAdd(&cellcnt[cell], 1);
   if (slot < kMdCap) {
-    cellx[cell * kMdCap + slot] = make_float4(X.x, X.y, X.z, __int_as_float(i));
+    // the record's index carries in its sign bit whether the atom has a nonzero wrap m (lies outside
+    // the primary box), so that the search loads m only for those atoms
+    const int tag = i | ((mm[0] | mm[1] | mm[2]) ? (int)0x80000000u : 0);
+    cellx[cell * kMdCap + slot] = make_float4(X.x, X.y, X.z, __int_as_float(tag));
   } else {
     set_status(status, TERSOFF_STATUS_NBR_OVERFLOW);
     cnt[i] = 0;
@@ -236,7 +239,7 @@ __device__ __forceinline__ void md_shell(const MdGeom &G, const double *__restri
       const int c = q < n0 ? 0 : (q < n01 ? 1 : 2);
       const int slot = q - (c == 0 ? 0 : (c == 1 ? n0 : n01));
       const float4 r = cellx[(size_t)(row + g2[c]) * kMdCap + slot];
-      const int j = __float_as_int(r.w);
+      const int j = __float_as_int(r.w) & 0x7fffffff;
       const float fc = (float)c;
       const float dx = __fadd_rn(__fmaf_rn(fc, G.E[6], bx), r.x);
       const float dy = __fadd_rn(__fmaf_rn(fc, G.E[7], by), r.y);
@@ -248,12 +251,12 @@ __device__ __forceinline__ void md_shell(const MdGeom &G, const double *__restri
 }
 
 // List entry (j, n) of key (j << 6 | offset code) of atom i (wraps m_i, cell (c0, c1, c2)):
-// n = wrap + m_i - m_j.
+// n = wrap + m_i - m_j. Bit 31 of the key marks a partner j with a nonzero m (it is loaded only then).
 __device__ __forceinline__ void md_write_entry(const MdGeom &G, const int4 *__restrict__ m4, int4 mi, int c0, int c1,
                                                int c2, unsigned key, size_t at, int *__restrict__ nbr,
                                                char4 *__restrict__ shift) {
-  const int j = (int)(key >> 6);
-  const int4 mj = m4[j];
+  const int j = (int)((key & 0x7fffffffu) >> 6);
+  const int4 mj = (key & 0x80000000u) ? m4[j] : make_int4(0, 0, 0, 0);
   int g;
   const int w0 = md_wrap(c0 + (int)((key >> 4) & 3u) - 1, G.nc[0], g);
   const int w1 = md_wrap(c1 + (int)((key >> 2) & 3u) - 1, G.nc[1], g);
@@ -263,8 +266,10 @@ __device__ __forceinline__ void md_write_entry(const MdGeom &G, const int4 *__re
                          (signed char)(w2 + mi.z - mj.z), 0);
 }
 
+// Compare-exchange of two keys by their low 31 bits (bit 31 is a mark that travels with the key).
 __device__ __forceinline__ void cas(unsigned &a, unsigned &b) {
-  const unsigned lo = min(a, b), hi = max(a, b);
+  const bool swap = (b << 1) < (a << 1);
+  const unsigned lo = swap ? b : a, hi = swap ? a : b;
   a = lo;
   b = hi;
 }
@@ -289,7 +294,7 @@ __device__ __forceinline__ void md_emit(int N, int M, int i, int4 mi, int c0, in
 #pragma unroll
   for (int e = 0; e < kMdMaxM; ++e)
     if (e < cm) {
-      keys[(size_t)e * N + i] = k[e];
+      keys[(size_t)e * N + i] = k[e] & 0x7fffffffu;
       md_write_entry(G, m4, mi, c0, c1, c2, k[e], (size_t)e * N + i, nbr, shift);
     }
 }
@@ -315,7 +320,7 @@ __device__ __noinline__ void md_search_atom(int N, int M, int i, const double *_
   md_shell(G, pos, m4, cellcnt, cellx, i, mi, xi, [&](unsigned key) {
 #pragma unroll
     for (int u = 0; u < kMdMaxM; ++u)
-      if (u == count) k[u] = key;
+      if (u == count) k[u] = key | 0x80000000u;   // the partner's m is loaded
     ++count;
   });
   if (count <= kMdMaxM) {
@@ -334,7 +339,7 @@ __device__ __noinline__ void md_search_atom(int N, int M, int i, const double *_
     const unsigned key = keys[(size_t)e * N + i];
     int rank = 0;
     for (int f = 0; f < cm; ++f) rank += keys[(size_t)f * N + i] < key ? 1 : 0;
-    md_write_entry(G, m4, mi, c0, c1, c2, key, (size_t)rank * N + i, nbr, shift);
+    md_write_entry(G, m4, mi, c0, c1, c2, key | 0x80000000u, (size_t)rank * N + i, nbr, shift);
   }
 }
 
@@ -351,7 +356,7 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
     int *__restrict__ cnt, unsigned *__restrict__ keys, int *__restrict__ nbr, char4 *__restrict__ shift,
     unsigned *status) {
   __shared__ __align__(16) float s_sx[kStageCap], s_sy[kStageCap], s_sz[kStageCap];   // brick coordinates
-  __shared__ int s_sj[kStageCap];                                                       // atom index
+  __shared__ int s_sj[kStageCap];   // atom index; sign bit: a nonzero wrap m
   __shared__ unsigned short s_h[kStageCap];        // halo cell of each staged record
   __shared__ unsigned short s_cand[kCandCap * kSearchThreads];   // candidates of each thread, [u][tid]
   __shared__ int s_cnt[kHaloCells], s_start[kHaloCells], s_gcell[kHaloCells];
@@ -465,13 +470,13 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
     const int hi = ((k0 + 1) * kHY + k1 + 1) * kHZ + k2 + 1;
     const int own = a - s_ipre[k];
     if (!staged) {
-      const int i = __float_as_int(cellx[(size_t)s_gcell[hi] * kMdCap + own].w);
+      const int i = __float_as_int(cellx[(size_t)s_gcell[hi] * kMdCap + own].w) & 0x7fffffff;
       md_search_atom(N, M, i, pos, G, x4, m4, cellcnt, cellx, cnt, keys, nbr, shift, status);
       continue;
     }
     const int slot = s_start[hi] + own;
     const float4 ei = make_float4(s_sx[slot], s_sy[slot], s_sz[slot], 0.f);
-    const int i = s_sj[slot];
+    const int itag = s_sj[slot], i = itag & 0x7fffffff;
     // the scan keeps only the stage positions of the candidates within the band's upper edge (atom i's
     // own record among them), so that the lanes of a warp that find one do little work. It takes the
     // records two at a time (aligned pairs of the stage, in packed FP32), masking the pair members
@@ -504,7 +509,7 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
       continue;
     }
     // members among the candidates: the FP32 distance decides below the band, the exact test in it
-    const int4 mi = m4[i];
+    const int4 mi = itag < 0 ? m4[i] : make_int4(0, 0, 0, 0);
     const int c0 = o0 + k0, c1 = o1 + k1, c2 = o2 + k2;
     unsigned kk[kMdMaxM];
 #pragma unroll
@@ -514,7 +519,7 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
       const int p = s_cand[u * kSearchThreads + tid];
       if (p == slot) continue;
       const float dx = __fsub_rn(s_sx[p], ei.x), dy = __fsub_rn(s_sy[p], ei.y), dz = __fsub_rn(s_sz[p], ei.z);
-      const int j = s_sj[p], hj = s_h[p];
+      const int jtag = s_sj[p], j = jtag & 0x7fffffff, hj = s_h[p];
       const int d0 = hj / (kHY * kHZ) - (k0 + 1), d1 = (hj / kHZ) % kHY - (k1 + 1), d2 = hj % kHZ - (k2 + 1);
       const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
       bool in = r2 < G.cut2_lo;
@@ -525,7 +530,8 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
         in = md_pair_in(G, pos, m4, i, j, mi, w0, w1, w2, make_float3(dx, dy, dz));
       }
       if (in) {
-        const unsigned key = ((unsigned)j << 6) | (unsigned)(((d0 + 1) << 4) | ((d1 + 1) << 2) | (d2 + 1));
+        const unsigned key = ((unsigned)j << 6) | (unsigned)(((d0 + 1) << 4) | ((d1 + 1) << 2) | (d2 + 1)) |
+                             ((unsigned)jtag & 0x80000000u);
 #pragma unroll
         for (int v = 0; v < kMdMaxM; ++v)
           if (v == count) kk[v] = key;
