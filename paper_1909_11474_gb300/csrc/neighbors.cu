@@ -201,6 +201,8 @@ struct BuildParams {
   unsigned *status, *build_status; // the context's status word and the build's own (read by the host)
   int nat_max;                     // largest configuration of the launch (shared-memory layout)
   int lists_in_smem;               // the lists and unit vectors fit in shared memory
+  int pairmask;                    // the pair-membership bit matrix fits in shared memory (at pm_off)
+  int pm_off;
   float R1f, R2f, Wf, Kf;          // R1, R2, R2 - R1 and -pi / (2 (R2 - R1)) rounded to FP32
 };
 
@@ -322,6 +324,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
   int *s_outer = s_poff + nmax + 1;
   int2 *s_list = reinterpret_cast<int2 *>(bsm + (build_smem_base(nmax) + 15) / 16 * 16);   // [nmax * M]
   float4 *s_u = reinterpret_cast<float4 *>(s_list + (size_t)nmax * M);                     // [nmax * M]
+  unsigned *s_pm = reinterpret_cast<unsigned *>(bsm + a.pm_off);   // [nmax][ceil(nmax / 32)] pair bits
   __shared__ Pre32 s_q;
   __shared__ BoxPart1 s_b1;
   __shared__ double s_H[9];
@@ -404,6 +407,65 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
     // spacings above 2 R2), each j has at most one candidate image; the warp then tests it straight
     // away and places the accepted entries with a ballot (the same candidates and order as the loops)
     const bool single = q.rng[0] < 0.5f && q.rng[1] < 0.5f && q.rng[2] < 0.5f;
+    if (single && ok && a.pairmask) {
+      // each unordered pair once (the test is symmetric: the FP32 separation of (j, i, -n) is exactly
+      // the negated one of (i, j, n), and so is the exact test's), its result a bit in both atoms'
+      // rows; then each atom's list from its row, j ascending. The pairs are (i, (i + d) mod nat) for
+      // d = 1 .. nat/2 (for an even nat, those of d = nat/2 only with i < nat/2), in blocks of 32
+      // consecutive i over the warps
+      const int nw = (nat + 31) >> 5, half = nat >> 1, nib = nw;
+      for (int t = tid; t < nat * nw; t += kBuildThreads) s_pm[t] = 0u;
+      __syncthreads();
+      const float lim = (float)nimg;
+      for (int b = warp; b < half * nib; b += kBuildWarps) {
+        const int d = 1 + b / nib, il = ((b % nib) << 5) + lane;
+        const bool act = il < nat && !(2 * d == nat && il >= half);
+        int jl = il + d;
+        if (jl >= nat) jl -= nat;
+        bool acc = false;
+        if (act) {
+          const float4 xi32 = s_p32[il], si = s_fr[il], xj = s_p32[jl], sj = s_fr[jl];
+          const float dx = xj.x - xi32.x, dy = xj.y - xi32.y, dz = xj.z - xi32.z;
+          const float f0 = rintf(-(sj.x - si.x)), f1 = rintf(-(sj.y - si.y)), f2 = rintf(-(sj.z - si.z));
+          if (fabsf(f0) <= lim && fabsf(f1) <= lim && fabsf(f2) <= lim)
+            acc = member(q, dx, dy, dz, f0, f1, f2, (int)f0, (int)f1, (int)f2, a.pos_in + 3 * (int64_t)(a0 + jl),
+                         a.pos_in + 3 * (int64_t)(a0 + il), s_H, R2sq);
+        }
+        if (acc) {
+          atomicOr(&s_pm[il * nw + (jl >> 5)], 1u << (jl & 31));
+          atomicOr(&s_pm[jl * nw + (il >> 5)], 1u << (il & 31));
+        }
+      }
+      __syncthreads();
+      for (int li = warp; li < nat; li += kBuildWarps) {
+        const int64_t i = a0 + li;
+        const float4 si = s_fr[li];
+        int count = 0;
+        for (int jb = 0; jb < nat; jb += 32) {
+          const unsigned word = s_pm[li * nw + (jb >> 5)];
+          const int jl = jb + lane;
+          const int w = count + __popc(word & ((1u << lane) - 1u));
+          if (((word >> lane) & 1u) && w < M) {
+            const float4 sj = s_fr[jl];   // the image of the test: n = round(-(s_j - s_i))
+            const char4 sh = make_char4((signed char)rintf(-(sj.x - si.x)), (signed char)rintf(-(sj.y - si.y)),
+                                        (signed char)rintf(-(sj.z - si.z)), 0);
+            a.nbr[i * M + w] = a0 + jl;
+            a.shift[i * M + w] = sh;
+            if (lists) s_list[li * M + w] = make_int2(jl, *reinterpret_cast<const int *>(&sh));
+          }
+          count += __popc(word);
+        }
+        if (lane == 0) {
+          a.cnt[i] = count;
+          if (count > M) build_flag(a, TERSOFF_STATUS_NBR_OVERFLOW);
+          s_m[li] = min(count, M);
+        }
+        for (int e = count + lane; e < M; e += 32) {
+          a.nbr[i * M + e] = -1;
+          a.shift[i * M + e] = make_char4(0, 0, 0, 0);
+        }
+      }
+    } else
     for (int li = warp; li < nat; li += kBuildWarps) {
       const int64_t i = a0 + li;
       const double *xi = a.pos_in + 3 * i;
@@ -680,8 +742,16 @@ cudaError_t launch_build_batch(const BuildLaunch &L, cudaStream_t s) {
   const size_t base = (build_smem_base(a.nat_max) + 15) / 16 * 16;
   const size_t with_lists = base + build_smem_lists(a.nat_max, L.M);
   a.lists_in_smem = with_lists <= kBuildSmemCap ? 1 : 0;
-  const size_t smem = a.lists_in_smem ? with_lists : base;
-  if (smem > 48 * 1024) {
+  size_t smem = a.lists_in_smem ? with_lists : base;
+  // the pair bit matrix after them, where it fits
+  const size_t pm_off = (smem + 15) / 16 * 16;
+  const size_t pm_bytes = (size_t)a.nat_max * ((a.nat_max + 31) / 32) * sizeof(unsigned);
+  a.pairmask = pm_off + pm_bytes <= kBuildSmemCap ? 1 : 0;
+  a.pm_off = (int)pm_off;
+  if (a.pairmask) smem = pm_off + pm_bytes;
+  // the default 48 KB limit covers the kernel's static shared memory too (a few hundred bytes): opt
+  // in with a margin for it
+  if (smem + 4096 > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(build_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
