@@ -629,28 +629,56 @@ constexpr unsigned kMbarSpins = 1u << 22;   // bound of a wait for one configura
 
 // Pass 3 of one atom with a compile-time neighbour count M from a single-CTA stage: F_i = sum_j P_ij
 // over the atom's own rows minus sum_j P_ji over the rows of the reverse bonds. rv: the reverse bonds'
-// configuration-local indices, 16 bits each (roff maps them to stage rows).
+// configuration-local indices, 16 bits each (roff maps them to stage rows). Every gather forms the two
+// sums separately, each over its rows in order, and subtracts them once (F = Fo - Fr), so that an
+// atom's force has the same rounding on every path; the rows are loaded before any is summed.
 template <int M, int PTT, typename R>
-__device__ __forceinline__ void gather_atom(const R *__restrict__ stage, int4 rv, int lb, int roff, int pl,
-                                            R &Fx, R &Fy, R &Fz) {
+struct GatherRows {
+  R o[M][3], r[M][3];
+};
+template <int M, int PTT, typename R>
+__device__ __forceinline__ void gather_load(const R *__restrict__ stage, int4 rv, int lb, int roff, int pl,
+                                            GatherRows<M, PTT, R> &g) {
   const int rw[4] = {rv.x, rv.y, rv.z, rv.w};
 #pragma unroll
-  for (int e = 0; e < M; ++e) {
-    R x, y, z;
-    stage_load<PTT, R>(stage, lb + e, pl, x, y, z, 13);
-    Fx += x;
-    Fy += y;
-    Fz += z;
-  }
+  for (int e = 0; e < M; ++e) stage_load<PTT, R>(stage, lb + e, pl, g.o[e][0], g.o[e][1], g.o[e][2], 13);
 #pragma unroll
   for (int e = 0; e < M; ++e) {
     const int rb = (rw[e >> 1] >> (16 * (e & 1))) & 0xffff;
-    R x, y, z;
-    stage_load<PTT, R>(stage, rb + roff, pl, x, y, z, 15);
-    Fx -= x;
-    Fy -= y;
-    Fz -= z;
+    stage_load<PTT, R>(stage, rb + roff, pl, g.r[e][0], g.r[e][1], g.r[e][2], 15);
   }
+}
+template <int M, int PTT, typename R>
+__device__ __forceinline__ void gather_sum(const GatherRows<M, PTT, R> &g, R &Fx, R &Fy, R &Fz) {
+  R o[3] = {g.o[0][0], g.o[0][1], g.o[0][2]}, r[3] = {g.r[0][0], g.r[0][1], g.r[0][2]};
+#pragma unroll
+  for (int e = 1; e < M; ++e)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      o[k] += g.o[e][k];
+      r[k] += g.r[e][k];
+    }
+  Fx = o[0] - r[0];
+  Fy = o[1] - r[1];
+  Fz = o[2] - r[2];
+}
+template <int M, int PTT, typename R>
+__device__ __forceinline__ void gather_atom(const R *__restrict__ stage, int4 rv, int lb, int roff, int pl,
+                                            R &Fx, R &Fy, R &Fz) {
+  GatherRows<M, PTT, R> g;
+  gather_load<M, PTT, R>(stage, rv, lb, roff, pl, g);
+  gather_sum<M, PTT, R>(g, Fx, Fy, Fz);
+}
+// Two atoms of the same neighbour count M, their loads issued together (one warp keeps both atoms'
+// rows in flight); each atom's arithmetic is that of gather_atom.
+template <int M, int PTT, typename R>
+__device__ __forceinline__ void gather_atom_pair(const R *__restrict__ stage, int4 rv0, int lb0, int4 rv1, int lb1,
+                                                 int roff, int pl, R (&F0)[3], R (&F1)[3]) {
+  GatherRows<M, PTT, R> g0, g1;
+  gather_load<M, PTT, R>(stage, rv0, lb0, roff, pl, g0);
+  gather_load<M, PTT, R>(stage, rv1, lb1, roff, pl, g1);
+  gather_sum<M, PTT, R>(g0, F0[0], F0[1], F0[2]);
+  gather_sum<M, PTT, R>(g1, F1[0], F1[1], F1[2]);
 }
 // Dispatch on the atom's neighbour count; false when it exceeds MMAX (the caller's loop handles it).
 template <int PTT, int MMAX, typename R>
@@ -671,6 +699,24 @@ __device__ __forceinline__ bool gather_dispatch(int m, const R *stage, int4 rv, 
       return false;
   }
 #undef TSF_GCASE
+}
+// Both atoms with neighbour count m; false when m is not a count with a pair variant.
+template <int PTT, int MMAX, typename R>
+__device__ __forceinline__ bool gather_pair_dispatch(int m, const R *stage, int4 rv0, int lb0, int4 rv1, int lb1,
+                                                     int roff, int pl, R (&F0)[3], R (&F1)[3]) {
+#define TSF_PCASE(MM)                                                                    \
+  case MM:                                                                               \
+    if constexpr (MMAX >= MM) {                                                          \
+      gather_atom_pair<MM, PTT, R>(stage, rv0, lb0, rv1, lb1, roff, pl, F0, F1);         \
+      return true;                                                                       \
+    }                                                                                    \
+    return false;
+  switch (m) {
+    TSF_PCASE(3) TSF_PCASE(4)
+    default:
+      return false;
+  }
+#undef TSF_PCASE
 }
 
 // One parameter tile of PTT parameter sets (PTT = 32: one atom per warp; 16 or 8: 2 or 4 atoms per
@@ -773,22 +819,18 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 
   // ---- pass 3: F_i = sum_j (P_ij - P_ji)
   R sf = R(0);   // sum |F - F*|^2 over the warp's atoms, or sum |F|^2 without a force target
-  for (int base = warp * APW; base < ns; base += NW * APW) {
-    const int li = base + slot;
-    if (li >= ns) continue;
-    const int4 at = sld(&satom[li], 12);
+  // F of atom li with a neighbour count beyond the compile-time gathers (and in the cluster and
+  // several-atoms-per-warp variants): the own and the reverse rows summed in order, as in gather_sum
+  auto gather_loop = [&](int li, const int4 &at, R (&F)[3]) {
     const int m = at.z, lb = at.x;
-    R Fx = R(0), Fy = R(0), Fz = R(0);
-    bool gathered = false;
-    if constexpr (APW == 1 && !CLUSTER)
-      gathered = gather_dispatch<PTT, MMAX, R>(m, stage, sld(&env.srev[li], 12), lb, cb0 - B0, pl, Fx, Fy, Fz);
-    for (int e = 0; !gathered && e < m; ++e) {
+    R o[3] = {R(0), R(0), R(0)}, r[3] = {R(0), R(0), R(0)};
+    for (int e = 0; e < m; ++e) {
       {
         R x, y, z;
         stage_load<PTT, R>(stage, lb + e, pl, x, y, z, 13);
-        Fx += x;
-        Fy += y;
-        Fz += z;
+        o[0] += x;
+        o[1] += y;
+        o[2] += z;
       }
       int packed;  // configuration-local indices of the reverse entry (bits 0-15) and of atom j (16-31)
       if constexpr (sizeof(R) == 4) packed = __float_as_int((float)sld(&sB[lb + e].w, 14));
@@ -796,10 +838,10 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
       const int rb = packed & 0xffff;
       if constexpr (CLUSTER) {
         // the reverse entry belongs to atom j, whose rank is its slice of the configuration's atoms
-        const unsigned r = min((unsigned)(packed >> 16) / (unsigned)per, ncta - 1);
+        const unsigned rk = min((unsigned)(packed >> 16) / (unsigned)per, ncta - 1);
         // a reverse bond outside the configuration's bond range is an inconsistent schedule:
         // flag it and skip the peer read rather than touch another CTA's shared memory
-        if (rb < peer_b0[r] || rb >= peer_b0[r + 1]) {
+        if (rb < peer_b0[rk] || rb >= peer_b0[rk + 1]) {
           set_status(a.status, TERSOFF_STATUS_NBR_OVERFLOW);
 #ifdef TSF_DEBUG_BOUNDS
           if (atomicCAS(&tsf_dbg[0], 0u, 1u) == 0u) {
@@ -810,47 +852,86 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
 #endif
           continue;
         }
-        const unsigned row = peer_stage[r] + (unsigned)((rb - peer_b0[r]) * stage_stride<PTT>() * sizeof(R));
+        const unsigned row = peer_stage[rk] + (unsigned)((rb - peer_b0[rk]) * stage_stride<PTT>() * sizeof(R));
         if constexpr (stage_packed<PTT, R>()) {
           const float2 xy = ld_cluster2(row + pl * sizeof(float2));
-          Fx -= xy.x;
-          Fy -= xy.y;
-          Fz -= ld_cluster(row + (2 * PTT + pl) * sizeof(R), R(0));
+          r[0] += xy.x;
+          r[1] += xy.y;
+          r[2] += ld_cluster(row + (2 * PTT + pl) * sizeof(R), R(0));
         } else {
-          Fx -= ld_cluster(row + pl * sizeof(R), R(0));
-          Fy -= ld_cluster(row + (PTT + pl) * sizeof(R), R(0));
-          Fz -= ld_cluster(row + (2 * PTT + pl) * sizeof(R), R(0));
+          r[0] += ld_cluster(row + pl * sizeof(R), R(0));
+          r[1] += ld_cluster(row + (PTT + pl) * sizeof(R), R(0));
+          r[2] += ld_cluster(row + (2 * PTT + pl) * sizeof(R), R(0));
         }
       } else {
         R x, y, z;
         stage_load<PTT, R>(stage, rb + cb0 - B0, pl, x, y, z, 15);
-        Fx -= x;
-        Fy -= y;
-        Fz -= z;
+        r[0] += x;
+        r[1] += y;
+        r[2] += z;
       }
     }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) F[k] = o[k] - r[k];
+  };
+  // the force of atom li: stored (evaluation) or its residual added to sf (fitness)
+  auto finish = [&](int li, const R (&F)[3]) {
     const int i = s0 + li;
     if (a.mode == kModeEval) {
       if (active && a.F) {
-        R *F = reinterpret_cast<R *>(a.F);
+        R *Fo = reinterpret_cast<R *>(a.F);
         if (a.f_ld > 0) {
           const size_t o = (size_t)i * 3 * a.f_ld + p;
-          F[o] = Fx;
-          F[o + a.f_ld] = Fy;
-          F[o + 2 * a.f_ld] = Fz;
+          Fo[o] = F[0];
+          Fo[o + a.f_ld] = F[1];
+          Fo[o + 2 * a.f_ld] = F[2];
         } else {
           const size_t o = ((size_t)p * a.Ntot + i) * 3;
-          F[o] = Fx;
-          F[o + 1] = Fy;
-          F[o + 2] = Fz;
+          Fo[o] = F[0];
+          Fo[o + 1] = F[1];
+          Fo[o + 2] = F[2];
         }
       }
     } else if (mask & 4) {
       const R4 t = sld(&stF[li], 16);
-      const R ex = Fx - t.x, ey = Fy - t.y, ez = Fz - t.z;
+      const R ex = F[0] - t.x, ey = F[1] - t.y, ez = F[2] - t.z;
       sf += ex * ex + ey * ey + ez * ez;
     } else {
-      sf += Fx * Fx + Fy * Fy + Fz * Fz;   // finiteness of F where no residual checks it
+      sf += F[0] * F[0] + F[1] * F[1] + F[2] * F[2];   // finiteness of F where no residual checks it
+    }
+  };
+  if constexpr (APW == 1 && !CLUSTER) {
+    // one atom per warp: two atoms (li and li + NW) per iteration, whose row loads are issued together;
+    // sf still takes the warp's atoms in ascending order
+    const int roff = cb0 - B0;
+    for (int l0 = warp; l0 < ns; l0 += 2 * NW) {
+      const int l1 = l0 + NW;
+      const int4 at0 = sld(&satom[l0], 12), rv0 = sld(&env.srev[l0], 12);
+      R F0[3] = {R(0), R(0), R(0)}, F1[3] = {R(0), R(0), R(0)};   // an atom without bonds keeps F = 0
+      if (l1 < ns) {
+        const int4 at1 = sld(&satom[l1], 12), rv1 = sld(&env.srev[l1], 12);
+        if (!(at0.z == at1.z &&
+              gather_pair_dispatch<PTT, MMAX, R>(at0.z, stage, rv0, at0.x, rv1, at1.x, roff, pl, F0, F1))) {
+          if (!gather_dispatch<PTT, MMAX, R>(at0.z, stage, rv0, at0.x, roff, pl, F0[0], F0[1], F0[2]))
+            gather_loop(l0, at0, F0);
+          if (!gather_dispatch<PTT, MMAX, R>(at1.z, stage, rv1, at1.x, roff, pl, F1[0], F1[1], F1[2]))
+            gather_loop(l1, at1, F1);
+        }
+        finish(l0, F0);
+        finish(l1, F1);
+      } else {
+        if (!gather_dispatch<PTT, MMAX, R>(at0.z, stage, rv0, at0.x, roff, pl, F0[0], F0[1], F0[2]))
+          gather_loop(l0, at0, F0);
+        finish(l0, F0);
+      }
+    }
+  } else {
+    for (int base = warp * APW; base < ns; base += NW * APW) {
+      const int li = base + slot;
+      if (li >= ns) continue;
+      R F[3];
+      gather_loop(li, sld(&satom[li], 12), F);   // F = 0 for an atom without bonds
+      finish(li, F);
     }
   }
 
