@@ -139,8 +139,7 @@ __device__ __forceinline__ void stage_store(R *stage, int row, int pl, R x, R y,
   }
 }
 template <int PT, typename R>
-__device__ __forceinline__ void stage_load(const R *stage, int row, int pl, R &x, R &y, R &z, int site) {
-  const R *st = stage + (size_t)row * stage_stride<PT>();
+__device__ __forceinline__ void stage_load_row(const R *st, int pl, R &x, R &y, R &z, int site) {
   if constexpr (stage_packed<PT, R>()) {
     const float2 v = sld(reinterpret_cast<const float2 *>(st) + pl, site);
     x = v.x;
@@ -151,6 +150,10 @@ __device__ __forceinline__ void stage_load(const R *stage, int row, int pl, R &x
     y = sld(&st[PT + pl], site);
     z = sld(&st[2 * PT + pl], site);
   }
+}
+template <int PT, typename R>
+__device__ __forceinline__ void stage_load(const R *stage, int row, int pl, R &x, R &y, R &z, int site) {
+  stage_load_row<PT, R>(stage + (size_t)row * stage_stride<PT>(), pl, x, y, z, site);
 }
 
 // The per-atom core of passes 1 and 2: from the bond geometry (unit vectors, r, 2/r, f_C, f_C', the
@@ -627,6 +630,13 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
 }
 constexpr unsigned kMbarSpins = 1u << 22;   // bound of a wait for one configuration's copies
 
+// Single-CTA kernels of up to four neighbours with one atom per warp keep each atom's reverse rows as
+// byte offsets in the stage (set when the item is staged), so the gather adds them to its base.
+template <int PTT, int MMAX, bool CLUSTER, typename R>
+__host__ __device__ constexpr bool kRevBytes() {
+  return PTT == 32 && MMAX <= 4 && !CLUSTER;
+}
+
 // Pass 3 of one atom with a compile-time neighbour count M from a single-CTA stage: F_i = sum_j P_ij
 // over the atom's own rows minus sum_j P_ji over the rows of the reverse bonds. rv: the reverse bonds'
 // configuration-local indices, 16 bits each (roff maps them to stage rows). Every gather forms the two
@@ -636,7 +646,9 @@ template <int M, int PTT, typename R>
 struct GatherRows {
   R o[M][3], r[M][3];
 };
-template <int M, int PTT, typename R>
+// REVB: rv holds the reverse rows' byte offsets in the stage (first four bonds; kernels of up to four
+// neighbours), otherwise their configuration-local indices, 16 bits each (roff maps them to stage rows).
+template <int M, int PTT, typename R, bool REVB>
 __device__ __forceinline__ void gather_load(const R *__restrict__ stage, int4 rv, int lb, int roff, int pl,
                                             GatherRows<M, PTT, R> &g) {
   const int rw[4] = {rv.x, rv.y, rv.z, rv.w};
@@ -644,8 +656,14 @@ __device__ __forceinline__ void gather_load(const R *__restrict__ stage, int4 rv
   for (int e = 0; e < M; ++e) stage_load<PTT, R>(stage, lb + e, pl, g.o[e][0], g.o[e][1], g.o[e][2], 13);
 #pragma unroll
   for (int e = 0; e < M; ++e) {
-    const int rb = (rw[e >> 1] >> (16 * (e & 1))) & 0xffff;
-    stage_load<PTT, R>(stage, rb + roff, pl, g.r[e][0], g.r[e][1], g.r[e][2], 15);
+    if constexpr (REVB) {
+      static_assert(M <= 4, "byte offsets of the first four reverse rows");
+      const R *st = reinterpret_cast<const R *>(reinterpret_cast<const unsigned char *>(stage) + rw[e]);
+      stage_load_row<PTT, R>(st, pl, g.r[e][0], g.r[e][1], g.r[e][2], 15);
+    } else {
+      const int rb = (rw[e >> 1] >> (16 * (e & 1))) & 0xffff;
+      stage_load<PTT, R>(stage, rb + roff, pl, g.r[e][0], g.r[e][1], g.r[e][2], 15);
+    }
   }
 }
 template <int M, int PTT, typename R>
@@ -662,32 +680,32 @@ __device__ __forceinline__ void gather_sum(const GatherRows<M, PTT, R> &g, R &Fx
   Fy = o[1] - r[1];
   Fz = o[2] - r[2];
 }
-template <int M, int PTT, typename R>
+template <int M, int PTT, typename R, bool REVB>
 __device__ __forceinline__ void gather_atom(const R *__restrict__ stage, int4 rv, int lb, int roff, int pl,
                                             R &Fx, R &Fy, R &Fz) {
   GatherRows<M, PTT, R> g;
-  gather_load<M, PTT, R>(stage, rv, lb, roff, pl, g);
+  gather_load<M, PTT, R, REVB>(stage, rv, lb, roff, pl, g);
   gather_sum<M, PTT, R>(g, Fx, Fy, Fz);
 }
 // Two atoms of the same neighbour count M, their loads issued together (one warp keeps both atoms'
 // rows in flight); each atom's arithmetic is that of gather_atom.
-template <int M, int PTT, typename R>
+template <int M, int PTT, typename R, bool REVB>
 __device__ __forceinline__ void gather_atom_pair(const R *__restrict__ stage, int4 rv0, int lb0, int4 rv1, int lb1,
                                                  int roff, int pl, R (&F0)[3], R (&F1)[3]) {
   GatherRows<M, PTT, R> g0, g1;
-  gather_load<M, PTT, R>(stage, rv0, lb0, roff, pl, g0);
-  gather_load<M, PTT, R>(stage, rv1, lb1, roff, pl, g1);
+  gather_load<M, PTT, R, REVB>(stage, rv0, lb0, roff, pl, g0);
+  gather_load<M, PTT, R, REVB>(stage, rv1, lb1, roff, pl, g1);
   gather_sum<M, PTT, R>(g0, F0[0], F0[1], F0[2]);
   gather_sum<M, PTT, R>(g1, F1[0], F1[1], F1[2]);
 }
 // Dispatch on the atom's neighbour count; false when it exceeds MMAX (the caller's loop handles it).
-template <int PTT, int MMAX, typename R>
+template <int PTT, int MMAX, typename R, bool REVB>
 __device__ __forceinline__ bool gather_dispatch(int m, const R *stage, int4 rv, int lb, int roff, int pl, R &Fx,
                                                 R &Fy, R &Fz) {
 #define TSF_GCASE(MM)                                                              \
   case MM:                                                                         \
     if constexpr (MMAX >= MM) {                                                    \
-      gather_atom<MM, PTT, R>(stage, rv, lb, roff, pl, Fx, Fy, Fz);                \
+      gather_atom<MM, PTT, R, REVB>(stage, rv, lb, roff, pl, Fx, Fy, Fz);          \
       return true;                                                                 \
     }                                                                              \
     return false;
@@ -701,13 +719,13 @@ __device__ __forceinline__ bool gather_dispatch(int m, const R *stage, int4 rv, 
 #undef TSF_GCASE
 }
 // Both atoms with neighbour count m; false when m is not a count with a pair variant.
-template <int PTT, int MMAX, typename R>
+template <int PTT, int MMAX, typename R, bool REVB>
 __device__ __forceinline__ bool gather_pair_dispatch(int m, const R *stage, int4 rv0, int lb0, int4 rv1, int lb1,
                                                      int roff, int pl, R (&F0)[3], R (&F1)[3]) {
 #define TSF_PCASE(MM)                                                                    \
   case MM:                                                                               \
     if constexpr (MMAX >= MM) {                                                          \
-      gather_atom_pair<MM, PTT, R>(stage, rv0, lb0, rv1, lb1, roff, pl, F0, F1);         \
+      gather_atom_pair<MM, PTT, R, REVB>(stage, rv0, lb0, rv1, lb1, roff, pl, F0, F1);   \
       return true;                                                                       \
     }                                                                                    \
     return false;
@@ -911,16 +929,16 @@ __device__ __forceinline__ void tile_pass(const BatchParams &a, const TileEnv<R>
       if (l1 < ns) {
         const int4 at1 = sld(&satom[l1], 12), rv1 = sld(&env.srev[l1], 12);
         if (!(at0.z == at1.z &&
-              gather_pair_dispatch<PTT, MMAX, R>(at0.z, stage, rv0, at0.x, rv1, at1.x, roff, pl, F0, F1))) {
-          if (!gather_dispatch<PTT, MMAX, R>(at0.z, stage, rv0, at0.x, roff, pl, F0[0], F0[1], F0[2]))
+              gather_pair_dispatch<PTT, MMAX, R, kRevBytes<PTT, MMAX, CLUSTER, R>()>(at0.z, stage, rv0, at0.x, rv1, at1.x, roff, pl, F0, F1))) {
+          if (!gather_dispatch<PTT, MMAX, R, kRevBytes<PTT, MMAX, CLUSTER, R>()>(at0.z, stage, rv0, at0.x, roff, pl, F0[0], F0[1], F0[2]))
             gather_loop(l0, at0, F0);
-          if (!gather_dispatch<PTT, MMAX, R>(at1.z, stage, rv1, at1.x, roff, pl, F1[0], F1[1], F1[2]))
+          if (!gather_dispatch<PTT, MMAX, R, kRevBytes<PTT, MMAX, CLUSTER, R>()>(at1.z, stage, rv1, at1.x, roff, pl, F1[0], F1[1], F1[2]))
             gather_loop(l1, at1, F1);
         }
         finish(l0, F0);
         finish(l1, F1);
       } else {
-        if (!gather_dispatch<PTT, MMAX, R>(at0.z, stage, rv0, at0.x, roff, pl, F0[0], F0[1], F0[2]))
+        if (!gather_dispatch<PTT, MMAX, R, kRevBytes<PTT, MMAX, CLUSTER, R>()>(at0.z, stage, rv0, at0.x, roff, pl, F0[0], F0[1], F0[2]))
           gather_loop(l0, at0, F0);
         finish(l0, F0);
       }
@@ -1148,7 +1166,16 @@ __global__ void __launch_bounds__(NW * kWarp, MINB) batch_kernel(const BatchPara
       for (int t = tid; t < ns; t += (NW * kWarp)) {
         const int am = a.ameta[s0 + t];
         sst(&satom[t], make_int4(a.boff[s0 + t] - B0, a.poff[s0 + t] - Q0, am & 0xffff, am >> 16), 9);
-        sst(&srev[t], a.arev[s0 + t], 9);
+        int4 rv = a.arev[s0 + t];
+        if constexpr (kRevBytes<PT, MMAX, CLUSTER, R>()) {   // rows of the full-width stage, in bytes
+          const int rw[2] = {rv.x, rv.y};
+          int off[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            off[e] = (((rw[e >> 1] >> (16 * (e & 1))) & 0xffff) + cb0 - B0) * (int)(stage_stride<PT>() * sizeof(R));
+          rv = make_int4(off[0], off[1], off[2], off[3]);
+        }
+        sst(&srev[t], rv, 9);
         if (fit) {   // target force in the working precision
           const double *f = a.tF + 3 * (int64_t)(s0 + t);
           const double fx = f[0], fy = f[1], fz = f[2];
