@@ -259,25 +259,27 @@ __global__ void __launch_bounds__(kFinWarps * 32) fitness_finalize_kernel(
 #pragma unroll
     for (int k = 0; k < 6; ++k) s_red[warp][k] = v[k];
   __syncthreads();
-  if (tid == 0) {
-    double t[6];
-    for (int k = 0; k < 6; ++k) {
-      t[k] = s_red[0][k];
-      for (int w = 1; w < kFinWarps; ++w) t[k] += s_red[w][k];
+  if (warp == 0) {
+    // lane k < 6 sums quantity k over the warps in order; lane q < 3 forms Zq of its quantity (the
+    // three divisions and square roots side by side), lane 0 sums w_q Zq in the order q = 0, 1, 2
+    double t = 0.0;
+    if (lane < 6) {
+      t = s_red[0][lane];
+      for (int w = 1; w < kFinWarps; ++w) t += s_red[w][lane];
     }
-    const double wq[3] = {we, wv, wf};
-    double z = 0.0, zq[3];
+    const double d = __shfl_down_sync(0xffffffffu, t, 3);   // lane q < 3: D_q
+    double zq = 0.0, z = 0.0;
     bool finite = true;
-    for (int q = 0; q < 3; ++q) {
-      finite = finite && isfinite(t[q]);
-      zq[q] = t[3 + q] > 0.0 ? sqrt(t[q] / t[3 + q]) : 0.0;
-      z += wq[q] * zq[q];
+    if (lane < 3) {
+      finite = isfinite(t);
+      zq = d > 0.0 ? sqrt(t / d) : 0.0;
+      z = (lane == 0 ? we : lane == 1 ? wv : wf) * zq;
     }
-    Z[p] = finite ? z : INFINITY;
-    if (Zq)
-      for (int q = 0; q < 3; ++q) Zq[(size_t)p * 3 + q] = zq[q];
-    if (S)
-      for (int q = 0; q < 3; ++q) S[(size_t)p * 3 + q] = t[q];
+    const double z1 = __shfl_sync(0xffffffffu, z, 1), z2 = __shfl_sync(0xffffffffu, z, 2);
+    finite = __all_sync(0xffffffffu, finite);
+    if (lane == 0) Z[p] = finite ? (z + z1) + z2 : INFINITY;
+    if (Zq && lane < 3) Zq[(size_t)p * 3 + lane] = zq;
+    if (S && lane < 3) S[(size_t)p * 3 + lane] = t;
   }
 }
 

@@ -219,7 +219,7 @@ __host__ __device__ inline size_t build_smem_lists(int nat, int M) {
   return (size_t)nat * M * (sizeof(int2) + sizeof(float4));
 }
 
-// Sum / max / exclusive scan over the threads of a block (kBuildThreads), in a fixed order.
+// Max and exclusive scans over the threads of a block (kBuildThreads), in a fixed order.
 __device__ __forceinline__ float block_max_f(float v, float *red) {
   for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
   __syncthreads();
@@ -229,23 +229,34 @@ __device__ __forceinline__ float block_max_f(float v, float *red) {
   for (int w = 0; w < kBuildWarps; ++w) t = fmaxf(t, red[w]);
   return t;
 }
-__device__ __forceinline__ int block_excl_scan(int v, int *red, int &total) {
+// Exclusive scans of two values at once (v, u), with their totals: one pass, two barriers.
+__device__ __forceinline__ int2 block_excl_scan2(int v, int u, int *red, int2 &total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = v;
+  int iv = v, iu = u;
   for (int off = 1; off < 32; off <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, incl, off);
-    if (lane >= off) incl += u;
+    const int a = __shfl_up_sync(0xffffffffu, iv, off), b = __shfl_up_sync(0xffffffffu, iu, off);
+    if (lane >= off) {
+      iv += a;
+      iu += b;
+    }
   }
   __syncthreads();
-  if (lane == 31) red[warp] = incl;
+  if (lane == 31) {
+    red[warp] = iv;
+    red[kBuildWarps + warp] = iu;
+  }
   __syncthreads();
-  int before = 0;
-  total = 0;
+  int bv = 0, bu = 0;
+  total = make_int2(0, 0);
   for (int w = 0; w < kBuildWarps; ++w) {
-    if (w < warp) before += red[w];
-    total += red[w];
+    if (w < warp) {
+      bv += red[w];
+      bu += red[kBuildWarps + w];
+    }
+    total.x += red[w];
+    total.y += red[kBuildWarps + w];
   }
-  return before + incl - v;
+  return make_int2(bv + iv - v, bu + iu - u);
 }
 
 // Box constants of one configuration for the FP32 membership test: Hinv, the image search range
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
   __shared__ float s_Hh[9], s_Hl[9];   // box as FP32 head + tail
   __shared__ int s_ok, s_nmax;
   __shared__ float s_fred[kBuildWarps];
-  __shared__ int s_ired[kBuildWarps];
+  __shared__ int s_ired[2 * kBuildWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool lists = a.lists_in_smem != 0;
   const int c = blockIdx.x;
@@ -437,30 +448,32 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
         }
       }
       __syncthreads();
-      for (int li = warp; li < nat; li += kBuildWarps) {
+      // each atom's list from its row, one thread per atom: the set bits in ascending j, each with the
+      // image of the test, n = round(-(s_j - s_i)); entries past M are counted, not written
+      for (int li = tid; li < nat; li += kBuildThreads) {
         const int64_t i = a0 + li;
         const float4 si = s_fr[li];
         int count = 0;
-        for (int jb = 0; jb < nat; jb += 32) {
-          const unsigned word = s_pm[li * nw + (jb >> 5)];
-          const int jl = jb + lane;
-          const int w = count + __popc(word & ((1u << lane) - 1u));
-          if (((word >> lane) & 1u) && w < M) {
-            const float4 sj = s_fr[jl];   // the image of the test: n = round(-(s_j - s_i))
-            const char4 sh = make_char4((signed char)rintf(-(sj.x - si.x)), (signed char)rintf(-(sj.y - si.y)),
-                                        (signed char)rintf(-(sj.z - si.z)), 0);
-            a.nbr[i * M + w] = a0 + jl;
-            a.shift[i * M + w] = sh;
-            if (lists) s_list[li * M + w] = make_int2(jl, *reinterpret_cast<const int *>(&sh));
+        for (int wd = 0; wd < nw; ++wd) {
+          unsigned word = s_pm[li * nw + wd];
+          while (word) {
+            const int jl = (wd << 5) + __ffs(word) - 1;
+            word &= word - 1u;
+            if (count < M) {
+              const float4 sj = s_fr[jl];
+              const char4 sh = make_char4((signed char)rintf(-(sj.x - si.x)), (signed char)rintf(-(sj.y - si.y)),
+                                          (signed char)rintf(-(sj.z - si.z)), 0);
+              a.nbr[i * M + count] = a0 + jl;
+              a.shift[i * M + count] = sh;
+              if (lists) s_list[li * M + count] = make_int2(jl, *reinterpret_cast<const int *>(&sh));
+            }
+            ++count;
           }
-          count += __popc(word);
         }
-        if (lane == 0) {
-          a.cnt[i] = count;
-          if (count > M) build_flag(a, TERSOFF_STATUS_NBR_OVERFLOW);
-          s_m[li] = min(count, M);
-        }
-        for (int e = count + lane; e < M; e += 32) {
+        a.cnt[i] = count;
+        if (count > M) build_flag(a, TERSOFF_STATUS_NBR_OVERFLOW);
+        s_m[li] = min(count, M);
+        for (int e = count; e < M; ++e) {
           a.nbr[i * M + e] = -1;
           a.shift[i * M + e] = make_char4(0, 0, 0, 0);
         }
@@ -592,9 +605,9 @@ __global__ void __launch_bounds__(kBuildThreads, 2) build_batch_kernel(const Bui
   for (int cb = 0; cb < nat; cb += kBuildThreads) {
     const int t = cb + tid;
     const int m = t < nat ? s_m[t] : 0;
-    int tb, tq;
-    const int xb = block_excl_scan(m, s_ired, tb);
-    const int xq = block_excl_scan(t < nat ? pair_slots(m) : 0, s_ired, tq);
+    int2 tot;
+    const int2 xs = block_excl_scan2(m, t < nat ? pair_slots(m) : 0, s_ired, tot);
+    const int xb = xs.x, xq = xs.y, tb = tot.x, tq = tot.y;
     if (t < nat) {
       s_boff[t] = nb + xb;
       s_poff[t] = nq + xq;
