@@ -358,7 +358,8 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
   __shared__ __align__(16) float s_sx[kStageCap], s_sy[kStageCap], s_sz[kStageCap];   // brick coordinates
   __shared__ int s_sj[kStageCap];   // atom index; sign bit: a nonzero wrap m
   __shared__ unsigned short s_h[kStageCap];        // halo cell of each staged record
-  __shared__ unsigned short s_cand[kCandCap * kSearchThreads];   // candidates of each thread, [u][tid]
+  // candidates of each thread, [u][tid]; slot kCandCap takes the writes once the list is full
+  __shared__ unsigned short s_cand[(kCandCap + 1) * kSearchThreads];
   __shared__ int s_cnt[kHaloCells], s_start[kHaloCells], s_gcell[kHaloCells];
   __shared__ int s_ipre[kBrickCells + 1];
   __shared__ int s_total;
@@ -494,14 +495,15 @@ __global__ void __launch_bounds__(kSearchThreads, 5) md_search_kernel(
         const float2 dx = __fadd2_rn(sx2[k2], nx), dy = __fadd2_rn(sy2[k2], ny), dz = __fadd2_rn(sz2[k2], nz);
         const float2 r2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         const int p = 2 * k2;
-        if (p >= p0 && r2.x <= G.cut2_hi) {
-          if (nc < kCandCap) s_cand[nc * kSearchThreads + tid] = (unsigned short)p;
-          ++nc;
-        }
-        if (p + 1 < pend && r2.y <= G.cut2_hi) {
-          if (nc < kCandCap) s_cand[nc * kSearchThreads + tid] = (unsigned short)(p + 1);
-          ++nc;
-        }
+        // appended without branches: each record's position is written at the next free slot (a spare
+        // slot once the list is full) and the count advances only for a candidate, so the lanes of a
+        // warp never diverge here
+        const int c0 = (p >= p0 && r2.x <= G.cut2_hi) ? 1 : 0;
+        s_cand[min(nc, kCandCap) * kSearchThreads + tid] = (unsigned short)p;
+        nc += c0;
+        const int c1 = (p + 1 < pend && r2.y <= G.cut2_hi) ? 1 : 0;
+        s_cand[min(nc, kCandCap) * kSearchThreads + tid] = (unsigned short)(p + 1);
+        nc += c1;
       }
     }
     if (nc > kCandCap) {
